@@ -1,0 +1,187 @@
+"""FP64 CPU oracle for finite element integration by direct quadrature.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product library
+never imports this package, and this package imports nothing from it.
+
+The arithmetic lives in ``fem_oracle.c`` (plain C, FP64, OpenMP over elements);
+this module compiles it with gcc and marshals numpy arrays through ctypes.
+
+What it computes (Knepley & Terrel, Sec. 3):
+  * ``integrate``: element matrices by quadrature of Eqs. 3-5 (Laplacian) and of
+    Eq. 10 scaled by the 1/4 of Eq. 14 / Eq. 24 (elasticity eps:eps), times a
+    per-element constant coefficient (piecewise-constant case of Eq. 20).
+  * ``integrate_vjp``: the hand-derived reverse mode of the same steps.
+  * ``simplex_rule`` / ``basis`` / ``element_matrix``: the building blocks,
+    exposed so the tests can pin each one separately.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+LAPLACE_P1, LAPLACE_P2, ELASTIC_P1 = 0, 1, 2
+FLAG_CONN, FLAG_DEGENERATE = 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fem_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libfem_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``fem_oracle.c`` into ``libfem_oracle.so`` next to it (gcc, -O2, OpenMP)."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-shared", "-fPIC", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True)  # no OpenMP runtime: single-threaded oracle
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        D = ctypes.c_double
+        lib.orc_max_threads.restype = I
+        lib.orc_gauss_legendre01.argtypes = [I, P, P]
+        lib.orc_simplex_rule.argtypes = [I, I, P, P]
+        lib.orc_basis.argtypes = [I, I, P, P, P]
+        lib.orc_n_basis.argtypes = [I, I]
+        lib.orc_form_n.argtypes = [I, I]
+        lib.orc_element_matrix.argtypes = [I, I, P, D, I, P, P]
+        lib.orc_element_vjp.argtypes = [I, I, P, D, I, P, P, P]
+        lib.orc_integrate.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
+        lib.orc_integrate_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
+        for name in ("orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
+                     "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
+                     "orc_integrate_vjp"):
+            getattr(lib, name).restype = I
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def max_threads() -> int:
+    return _load().orc_max_threads()
+
+
+def form_n(form: int, dim: int) -> int:
+    """Rows of the element matrix: basis functions times components."""
+    return _load().orc_form_n(form, dim)
+
+
+def gauss_legendre01(q: int):
+    x = np.zeros(q)
+    w = np.zeros(q)
+    if _load().orc_gauss_legendre01(q, _ptr(x), _ptr(w)) != 0:
+        raise ValueError("q out of range")
+    return x, w
+
+
+def simplex_rule(dim: int, q: int):
+    """Duffy-collapsed Gauss rule on the reference simplex: (points [np][dim], weights [np])."""
+    pts = np.zeros((q ** dim, dim))
+    wts = np.zeros(q ** dim)
+    n = _load().orc_simplex_rule(dim, q, _ptr(pts), _ptr(wts))
+    if n < 0:
+        raise ValueError("bad rule request")
+    return pts[:n], wts[:n]
+
+
+def basis(dim: int, degree: int, xi):
+    """Values [nb] and reference gradients [nb][dim] of the P1/P2 basis at xi."""
+    xi = _f64(xi)
+    nb = _load().orc_n_basis(dim, degree)
+    phi = np.zeros(nb)
+    grad = np.zeros((nb, dim))
+    _load().orc_basis(dim, degree, _ptr(xi), _ptr(phi), _ptr(grad))
+    return phi, grad
+
+
+def element_matrix(dim: int, form: int, X, coef: float = 1.0, q: int = 3):
+    """Element matrix of one element with vertex coordinates X [dim+1][dim]."""
+    X = _f64(X)
+    n = form_n(form, dim)
+    A = np.zeros((n, n))
+    det = np.zeros(1)
+    rc = _load().orc_element_matrix(dim, form, _ptr(X), float(coef), q, _ptr(A), _ptr(det))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return A, float(det[0]), rc
+
+
+def element_vjp(dim: int, form: int, X, Abar, coef: float = 1.0, q: int = 3):
+    X = _f64(X)
+    Abar = _f64(Abar)
+    Xbar = np.zeros_like(X)
+    cbar = np.zeros(1)
+    rc = _load().orc_element_vjp(dim, form, _ptr(X), float(coef), q, _ptr(Abar), _ptr(Xbar),
+                                 _ptr(cbar))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return Xbar, float(cbar[0])
+
+
+def integrate(dim: int, form: int, conn, coords, coef=None, q: int = 3, nthreads: int | None = None,
+              return_det: bool = False):
+    """Element matrices A [E][n][n] (FP64) and per-element flags [E] (int32).
+
+    coords are taken exactly as FP64 whatever their storage type."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    E = conn.shape[0]
+    V = coords.shape[0]
+    n = form_n(form, dim)
+    cf = None if coef is None else _f64(coef)
+    A = np.zeros((E, n, n))
+    flags = np.zeros(E, dtype=np.int32)
+    det = np.zeros(E)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(cf), q, _ptr(A),
+                               _ptr(flags), _ptr(det), nt)
+    if rc < 0:
+        raise ValueError("bad integrate request")
+    if return_det:
+        return A, flags, det
+    return A, flags
+
+
+def integrate_vjp(dim: int, form: int, conn, coords, dA, coef=None, q: int = 3,
+                  nthreads: int | None = None):
+    """Reverse mode: (dcoords [V][dim], dcoef [E]) for the upstream dA [E][n][n]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    dA = _f64(dA)
+    E = conn.shape[0]
+    V = coords.shape[0]
+    cf = None if coef is None else _f64(coef)
+    dcoords = np.zeros((V, dim))
+    dcoef = np.zeros(E)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_vjp(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(cf), q,
+                                   _ptr(dA), _ptr(dcoords), _ptr(dcoef), nt)
+    if rc < 0:
+        raise ValueError("bad vjp request")
+    return dcoords, dcoef
