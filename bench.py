@@ -1,0 +1,402 @@
+"""Benchmark: finite element integration by tensor contraction on GB300.
+
+Default workload: 3D P1 Laplacian on the 128^3 Kuhn cube (12,582,912 tets,
+2,775,835 vertices, 5% sliver elements), FP32 coordinates and element
+matrices, compensated-FP32 Jacobian.  One step = the whole hot path over the
+mesh: forward integration (gather, Jacobian, G, G:K, coalesced stores) and
+the adjoint for an upstream dA ~ N(0,1) (element pass + deterministic
+segmented vertex reduction).
+
+Prints ONE JSON line (rank 0).  Timing: W untimed warm-up steps, then K steps
+bracketed by barrier + synchronize, CUDA events on the launching stream,
+max over ranks.  The working set (~2.7 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload tet128|elastic128|adjoint64]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elements/s & HBM GB/s vs peak, fwd and fwd+adjoint, at stated error vs FP64"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic per launch from one ncu capture, valid only while the kernel
+# sources hash to `src`; otherwise reported as null.
+NCU_TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1103_0066_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001 - file absent on some machines
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:  # noqa: BLE001 - no nvidia-smi: clocks reported as unknown
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.out.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ distributed
+
+def dist_setup(gpus: int):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg, dev=None):
+    if pg is not None:
+        if dev is not None:
+            pg.barrier(device_ids=[dev.index])
+        else:
+            pg.barrier()
+
+
+def max_over_ranks(pg, x: float, dev) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ workloads
+
+def tet_workload(n=128, k=2):
+    from paper_1103_0066_gb300 import meshgen as mg
+    mesh = mg.workload_tet_slivers(n, k)
+    dA = mg.upstream(mg.rng_for(k + 10), mesh.n_elem, 4)
+    return mesh, dA
+
+
+def algorithmic_bytes(E, V, n, dim, coef):
+    """Each input read once, each output written once (vertex arrays once)."""
+    nv = dim + 1
+    fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0)) + V * 4 * dim
+    bwd_elem = E * (4 * n * n + 4 * nv + 4 * nv * dim + (8 if coef else 0)) + V * 4 * dim
+    reduce = E * (4 * nv + 4 * nv * dim) + V * (4 + 4 * dim)
+    return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
+
+
+def cpu_baseline_leg(mesh, dA, A_gpu, dcoords_gpu, sample_elems):
+    """Times the FP64 oracle (as it stands) on a bounded sample on the host
+    cores and, untimed, measures the GPU results' error on that sample."""
+    import oracle
+    oracle.build()
+    S = min(sample_elems, mesh.n_elem)
+    conn = mesh.conn[:S]
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    Ar, fl = oracle.integrate(3, oracle.LAPLACE_P1, conn, mesh.coords)
+    gx, _ = oracle.integrate_vjp(3, oracle.LAPLACE_P1, conn, mesh.coords, dA[:S])
+    dt = time.perf_counter() - t0
+    # error of the GPU outputs on the sample
+    Ag = A_gpu[:S].double().cpu().numpy()
+    num = np.abs(Ag - Ar).reshape(S, -1).max(1)
+    den = np.abs(Ar).reshape(S, -1).max(1)
+    fwd_err = float((num / den).max())
+    # dcoords is comparable where every incident element lies in the sample
+    inc_all = np.bincount(mesh.conn.ravel(), minlength=mesh.n_vert)
+    inc_s = np.bincount(conn.ravel(), minlength=mesh.n_vert)
+    full = (inc_s == inc_all) & (inc_all > 0)
+    gg = dcoords_gpu.double().cpu().numpy()[full]
+    bwd_err = float(np.abs(gg - gx[full]).max() / np.abs(gx[full]).max())
+    return {"value": S / dt, "unit": "elements/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {S:,} elements of the mesh (cell-major, slivers included): FP64 "
+                      f"quadrature forward + reverse mode, {dt:.1f} s wall on {cores} threads",
+            "seconds": dt}, {"fwd_max_rel": fwd_err, "dcoords_max_rel": bwd_err,
+                             "sample_elements": S, "dcoords_vertices_checked": int(full.sum())}
+
+
+def run_ours(args):
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_0066_gb300 as fem
+
+    ws_n, rank, local, pg = dist_setup(args.gpus)
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    mesh, dA_h = tet_workload()
+    E, V = mesh.n_elem, mesh.n_vert
+    coords = torch.from_numpy(mesh.coords).to(dev)
+    conn = torch.from_numpy(mesh.conn).to(dev)
+    dA = torch.from_numpy(dA_h).to(dev)
+    A = torch.empty((E, 4, 4), dtype=torch.float32, device=dev)
+    dcoords = torch.empty((V, 3), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ws = fem.Workspace(coords, conn)
+    torch.cuda.synchronize()
+    setup_ms = (time.perf_counter() - t0) * 1e3
+
+    def step(evs=None):
+        if evs is not None:
+            evs[0].record(stream)
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A)
+        if evs is not None:
+            evs[1].record(stream)
+        fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, ws=ws, reduce=fem.REDUCE_DEFERRED,
+                          dcoords=dcoords, need_dcoef=False)
+        if evs is not None:
+            evs[2].record(stream)
+        fem.adjoint_reduce(coords, conn, ws, dcoords)
+        if evs is not None:
+            evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(pg, start.elapsed_time(end), dev)
+    per = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
+           for i, name in enumerate(("fwd", "bwd_elem", "reduce"))}
+
+    byts = algorithmic_bytes(E, V, 4, 3, False)
+    peak, peak_kind = hbm_peak()
+    dom = max(per, key=per.get)
+    kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
+             "reduce": "vertex_reduce_kernel<3>"}
+    h = csrc_hash()
+    tr = NCU_TRAFFIC.get(kname[dom])
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == h else None
+    ach = byts[dom] / (per[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                "traffic": traffic, "algorithmic_bytes": byts[dom]}
+    kernels = {k: {"ms": per[k], "GB/s": byts[k] / (per[k] * 1e-3) / 1e9,
+                   "frac_of_peak": byts[k] / (per[k] * 1e-3) / 1e9 / peak} for k in per}
+    fwd_eps = E / (per["fwd"] * 1e-3)
+    ms_step = total_ms / K
+    value = ws_n * E / (ms_step * 1e-3)
+
+    # end to end through the public API: pinned host buffers, copies in the timed region
+    e2e_steps = max(3, min(K, 10))
+    coords_h = torch.from_numpy(mesh.coords).pin_memory()
+    conn_h = torch.from_numpy(mesh.conn).pin_memory()
+    dA_hp = torch.from_numpy(dA_h).pin_memory()
+    A_h = torch.empty_like(A, device="cpu").pin_memory()
+    dc_h = torch.empty_like(dcoords, device="cpu").pin_memory()
+
+    def e2e_step():
+        coords.copy_(coords_h, non_blocking=True)
+        conn.copy_(conn_h, non_blocking=True)
+        dA.copy_(dA_hp, non_blocking=True)
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A)
+        fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, ws=ws, dcoords=dcoords, need_dcoef=False)
+        A_h.copy_(A, non_blocking=True)
+        dc_h.copy_(dcoords, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s2.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(pg, s2.elapsed_time(e2), dev) / e2e_steps
+    h2d = coords_h.numel() * 4 + conn_h.numel() * 4 + dA_hp.numel() * 4
+    d2h = A_h.numel() * 4 + dc_h.numel() * 4
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws_n, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3D P1 Laplacian, 128^3 Kuhn cube, 6 tets/cell, jitter 0.15h, 5% slivers "
+                               "(12,582,912 tets, 2,775,835 vertices); FP32 coords and 4x4 FP32 element "
+                               "matrices, compensated-FP32 Jacobian; step = forward + adjoint "
+                               "(deterministic segmented reduction), dA ~ N(0,1)",
+                   "elements": E, "vertices": V, "form": "laplace_p1", "dim": 3,
+                   "l2": "no flush: inputs/outputs (~2.7 GB per step) far exceed the 129 MB L2",
+                   "parallelism": f"{ws_n} independent replicas (elements shard with no collective)"},
+        "roofline": roofline,
+        "kernels": kernels,
+        "fwd": {"elements_per_s": fwd_eps, "gflops_paper_convention": fwd_eps * 288 / 1e9,
+                "GB/s": kernels["fwd"]["GB/s"], "frac_of_peak": kernels["fwd"]["frac_of_peak"]},
+        "fwd_adjoint": {"elements_per_s": E / (ms_step * 1e-3),
+                        "GB/s": sum(byts.values()) / (ms_step * 1e-3) / 1e9,
+                        "frac_of_peak": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / peak},
+        "setup": {"incidence_build_ms": setup_ms},
+        "e2e": {"value": ws_n * E / (e2e_ms * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps},
+        "gpu_launches": 3 * K,
+        "clocks": clk,
+        "csrc_hash": h,
+    }
+    if rank == 0 and ws_n == 1 and not args.no_cpu:
+        cpu, err = cpu_baseline_leg(mesh, dA_h, A, dcoords, args.cpu_sample)
+        out["cpu_baseline"] = cpu
+        out["error_vs_fp64"] = err
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores, bounded sample per step."""
+    ws_n = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    mesh, dA = tet_workload()
+    S = args.ref_sample
+    nwin = max(1, mesh.n_elem // S)
+
+    def step(k):
+        w = k % nwin
+        conn = mesh.conn[w * S:(w + 1) * S]
+        oracle.integrate(3, oracle.LAPLACE_P1, conn, mesh.coords)
+        oracle.integrate_vjp(3, oracle.LAPLACE_P1, conn, mesh.coords, dA[w * S:(w + 1) * S])
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    v = S * args.steps / dt
+    cores = oracle.max_threads()
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "elements/s", "n_gpus": ws_n,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "3D P1 Laplacian, 128^3 Kuhn cube, 5% slivers (12,582,912 tets); "
+                                  "step = forward + adjoint, FP64 oracle by direct quadrature",
+                      "elements": mesh.n_elem, "vertices": mesh.n_vert, "form": "laplace_p1", "dim": 3},
+           "cpu_baseline": {"value": v, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{S:,} consecutive elements per step (rotating window)"},
+           "e2e": {"value": v, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle leg")
+    ap.add_argument("--cpu-sample", type=int, default=4_194_304)
+    ap.add_argument("--ref-sample", type=int, default=262_144)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * fem.h -- C ABI of libfem_gb300: low-order finite element integration by
+ * tensor contraction on NVIDIA GB300 (sm_103a).
+ *
+ * Method: Knepley & Terrel, "Finite Element Integration on GPUs" (TACC
+ * TR-11-01).  For every element e the library gathers the vertex
+ * coordinates, forms the Jacobian J of the affine map from the reference
+ * simplex, |J| = |det J| and J^{-1}, builds the geometric tensor G_e (Eq. 8,
+ * times an optional per-element coefficient w_e, the piecewise-constant case
+ * of Eq. 20) and contracts it with the precomputed reference tensor K
+ * (Eq. 7): A_e^{ij} = G_e^{mu nu} K^{ij}_{mu nu} (Eq. 1, Eq. 6).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named "device" are CUDA device (or managed) memory owned by the
+ *     caller; the library never allocates on the integration path and never
+ *     frees caller memory.  Host pointers are named "host".
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device work is enqueued asynchronously on it; the call returns once the
+ *     work is enqueued.
+ *   - Host-detectable errors (null pointers, bad sizes, unsupported
+ *     combinations) return a non-zero fem_status before anything is launched;
+ *     fem_last_error() then gives a one-line reason (thread-local).
+ *   - Device-detectable errors never trap: the element is skipped (its outputs
+ *     are written as zeros) and FEM_DEVERR_* bits are OR-ed into
+ *     options->dev_err when that pointer is non-NULL.
+ *   - Reference simplex vertices are 0, e_1, .., e_d; J_{a mu} = x_{mu+1,a} - x_{0,a}.
+ *   - Element matrices are [E][n][n] row-major.  P2 basis order: vertex
+ *     functions, then edge functions over edges in lexicographic order.
+ *     Vector (elasticity) DOF index = component * n_basis + basis.
+ */
+#ifndef FEM_GB300_H
+#define FEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FEM_API __attribute__((visibility("default")))
+#else
+#define FEM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FEM_OK = 0,
+  FEM_ERR_ARG = 1,         /* invalid argument (null pointer, bad size or enum) */
+  FEM_ERR_UNSUPPORTED = 2, /* valid but unsupported combination */
+  FEM_ERR_WORKSPACE = 3,   /* workspace missing or too small */
+  FEM_ERR_CUDA = 4         /* a CUDA runtime call failed (message in fem_last_error) */
+} fem_status;
+
+/* Weak forms (Sec. 3). */
+typedef enum {
+  FEM_LAPLACE_P1 = 0, /* Eqs. 2-8 with P1 Lagrange elements */
+  FEM_LAPLACE_P2 = 1, /* same form, P2 Lagrange elements */
+  FEM_ELASTIC_P1 = 2  /* eps(v):eps(u), Eq. 10 scaled by the 1/4 of Eqs. 14 and 24, P1 vector elements */
+} fem_form;
+
+typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
+
+/* Precision of the Jacobian steps (J, det J, J^{-1}, G). */
+typedef enum {
+  FEM_JAC_AUTO = 0,     /* COMP_F32 for FP32 coordinates and FP32 output, F64 otherwise */
+  FEM_JAC_F64 = 1,      /* FP64 */
+  FEM_JAC_COMP_F32 = 2, /* compensated FP32 (error-free transforms; accurate det on slivers) */
+  FEM_JAC_F32 = 3       /* plain FP32, for error studies */
+} fem_jac;
+
+/* Arithmetic of the G:K contraction. */
+typedef enum {
+  FEM_CONTRACT_F32 = 0,   /* FP32 FMAs with K as compile-time immediates (sparse) */
+  FEM_CONTRACT_BF16X3 = 1 /* tensor cores: G split into three bf16 terms, FP32 accumulate */
+} fem_contract;
+
+/* Vertex reduction of the adjoint. */
+typedef enum {
+  FEM_REDUCE_DETERMINISTIC = 0, /* per-element scratch + segmented sum in a fixed order */
+  FEM_REDUCE_ATOMIC = 1,        /* red.global.add into dcoords (order not fixed) */
+  FEM_REDUCE_DEFERRED = 2       /* element pass only: contributions stay in the workspace
+                                   scratch; fem_adjoint_reduce completes dcoords */
+} fem_reduce;
+
+/* Device error bits (OR-ed into options->dev_err). */
+#define FEM_DEVERR_CONN 1       /* a connectivity index is outside [0, n_vert) */
+#define FEM_DEVERR_DEGENERATE 2 /* det J == 0 */
+
+/* A simplex mesh.  conn: device int32 [n_elem][dim+1]; coords: device
+ * [n_vert][dim] of coord_dtype (FP32 or FP64), row-major. */
+typedef struct fem_mesh {
+  int32_t dim;         /* 2 (triangles) or 3 (tetrahedra) */
+  int32_t coord_dtype; /* fem_dtype */
+  int64_t n_vert;
+  int64_t n_elem;
+  const int32_t* conn;
+  const void* coords;
+} fem_mesh;
+
+/* Options; a zero-initialised struct (or NULL) selects the defaults. */
+typedef struct fem_options {
+  int32_t jac;           /* fem_jac */
+  int32_t contract;      /* fem_contract */
+  int32_t reduce;        /* fem_reduce */
+  int32_t warps_per_cta; /* 0 = default; else 1..16 warps (32-element tiles) per CTA */
+  int32_t ctas_per_sm;   /* 0 = one CTA per group of tiles; >0 = grid capped at this many CTAs per SM */
+  int32_t reserved;      /* must be 0 */
+  int32_t* dev_err;      /* optional device int32, OR-ed with FEM_DEVERR_* bits */
+} fem_options;
+
+/* Library version string (static storage). */
+FEM_API const char* fem_version(void);
+
+/* Name of a status code (static storage). */
+FEM_API const char* fem_status_string(fem_status s);
+
+/* Reason for the last non-OK status returned on the calling thread. */
+FEM_API const char* fem_last_error(void);
+
+/* Host.  Shape of a form: n = rows of A_e, n_geom = folded entries of G
+ * (d(d+1)/2 for the Laplacian, d^2(d^2+1)/2 for elasticity), den = the integer
+ * scale of fem_reference_tensor.  Any output pointer may be NULL. */
+FEM_API fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den);
+
+/* Host.  The reference tensor K of Eq. 7 (Eq. 14 with the symmetric gradient
+ * for elasticity), folded over the symmetric G slots and scaled to exact
+ * integers: K_host[g][i][j] = den * K'_g^{ij}, with A_e^{ij} = sum_g G_g K'_g^{ij}.
+ * K_host: host int32 array of at least n_geom*n*n entries (cap = entries). */
+FEM_API fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K_host, size_t cap);
+
+/* Forward element integration, Sec. 4 / Eq. 6: A[e] = G_e : K for every element.
+ *   coef : device FP32 [n_elem] per-element coefficient w_e, or NULL (w = 1)
+ *   A    : device [n_elem][n][n] of out_dtype (overwritten)
+ *   FP64 output or FP64 coordinates compute the Jacobian steps in FP64.
+ * Asynchronous on `stream`.  n_elem == 0 is a no-op. */
+FEM_API fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
+                             int32_t out_dtype, const fem_options* options, void* stream);
+
+/* Test hook for the Jacobian steps (Eqs. 5, 8): per element det J (detJ,
+ * device FP64 [n_elem]; the compensated mode returns its double-float value)
+ * and the Laplacian geometric tensor G^{mu nu} = w |J| sum_a Jinv_{mu a} Jinv_{nu a}
+ * (G, device FP32 [n_elem][d(d+1)/2], pairs mu <= nu in row-major order).
+ * Either output may be NULL.  Degenerate/invalid elements get 0. */
+FEM_API fem_status fem_geometry(const fem_mesh* mesh, const float* coef, const fem_options* options,
+                        double* detJ, float* G, void* stream);
+
+/* Bytes of device workspace fem_integrate_bwd needs for this mesh and form
+ * (vertex->incidence CSR plus per-element scratch for the deterministic
+ * reduction; 0 extra scratch for FEM_REDUCE_ATOMIC). */
+FEM_API fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_options* options,
+                                  size_t* bytes);
+
+/* Builds the vertex -> (element, local vertex) incidence CSR, sorted by
+ * (vertex, element, local vertex), into the workspace `ws` (device, caller
+ * owned, ws_bytes from fem_bwd_workspace_size).  Once per mesh connectivity;
+ * it must precede fem_integrate_bwd with FEM_REDUCE_DETERMINISTIC. */
+FEM_API fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of fem_integrate_fwd (FP32 coordinates): for the upstream
+ * dA = dL/dA (device FP32 [n_elem][n][n]) computes
+ *   dcoords = dL/dcoords  (device FP32 [n_vert][dim], overwritten; may be NULL)
+ *   dcoef   = dL/dcoef    (device FP32 [n_elem], overwritten; may be NULL)
+ * through dG = dA K^T, then d|J| and d adj(J), then the vertex sums.
+ * Deterministic reduction: bitwise reproducible, needs the built incidence in ws.
+ * Atomic reduction: ws may be NULL.  Deferred: the element pass only (dcoords
+ * must be non-NULL, is not written here; call fem_adjoint_reduce next). */
+FEM_API fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef,
+                             const float* dA, float* dcoords, float* dcoef, void* ws,
+                             size_t ws_bytes, const fem_options* options, void* stream);
+
+/* Second phase of a FEM_REDUCE_DEFERRED adjoint: dcoords[v] (device FP32
+ * [n_vert][dim], overwritten) = sum over the incidence segment of v, in
+ * (element, local vertex) order, of the per-element contributions the element
+ * pass left in `ws`.  Same result bits as FEM_REDUCE_DETERMINISTIC. */
+FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes,
+                                      float* dcoords, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEM_GB300_H */

@@ -1,0 +1,197 @@
+"""GB300-native finite element integration by tensor contraction.
+
+Knepley & Terrel, "Finite Element Integration on GPUs": element matrices
+A_e = G_e : K (Eq. 1, Eq. 6) for the P1/P2 Laplacian and P1 symmetric-gradient
+elasticity on triangles and tetrahedra, their adjoint, and batched launches.
+The computation runs in ``libfem_gb300.so`` (CUDA, sm_103a) behind the C ABI of
+``include/fem.h``; this package marshals torch tensors (device memory and
+streams) into that ABI.  There is no CPU fallback: without the built library
+every call raises.
+
+Quick use::
+
+    import paper_1103_0066_gb300 as fem
+    mesh = fem.Mesh(coords, conn)              # CUDA tensors: [V][d] float32, [E][d+1] int32
+    A = mesh.integrate(fem.LAPLACE_P1)         # [E][n][n]; differentiable in coords / coef
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _native as nat
+from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
+                      F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2,
+                      REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, FemError)
+
+__all__ = ["Mesh", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+           "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "JAC_AUTO",
+           "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
+           "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
+
+
+def form_info(form: int, dim: int):
+    """(n, n_geom, den): rows of A_e, folded G entries, integer scale of K."""
+    return nat.fem_form_info(form, dim)
+
+
+def reference_tensor(form: int, dim: int):
+    """Folded reference tensor K' * den as an int32 CPU tensor [n_geom][n][n] (host call)."""
+    n, ng, den = form_info(form, dim)
+    K = torch.empty((ng, n, n), dtype=torch.int32)
+    nat.fem_reference_tensor(form, dim, K.data_ptr(), K.numel())
+    return K, den
+
+
+def _stream_ptr(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _mesh_struct(coords: torch.Tensor, conn: torch.Tensor) -> nat.FemMesh:
+    if not (coords.is_cuda and conn.is_cuda):
+        raise ValueError("coords and conn must be CUDA tensors")
+    if conn.dtype != torch.int32 or conn.dim() != 2 or not conn.is_contiguous():
+        raise ValueError("conn must be a contiguous int32 tensor [E][d+1]")
+    if coords.dim() != 2 or not coords.is_contiguous() or coords.dtype not in (torch.float32, torch.float64):
+        raise ValueError("coords must be a contiguous float32/float64 tensor [V][d]")
+    dim = coords.shape[1]
+    if conn.shape[1] != dim + 1:
+        raise ValueError("conn must have d+1 columns")
+    return nat.mesh_struct(dim, F64 if coords.dtype == torch.float64 else F32, coords.shape[0],
+                           conn.shape[0], conn.data_ptr(), coords.data_ptr())
+
+
+def _coef_ptr(coef, E):
+    if coef is None:
+        return 0
+    if coef.dtype != torch.float32 or not coef.is_contiguous() or coef.numel() != E or not coef.is_cuda:
+        raise ValueError("coef must be a contiguous CUDA float32 tensor [E]")
+    return coef.data_ptr()
+
+
+def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float32, jac=JAC_AUTO,
+                  contract=CONTRACT_F32, warps_per_cta=0, ctas_per_sm=0, dev_err=None, stream=None):
+    """fem_integrate_fwd: element matrices [E][n][n] (not differentiable; see integrate)."""
+    m = _mesh_struct(coords, conn)
+    n, _, _ = form_info(form, m.dim)
+    E = conn.shape[0]
+    if out is None:
+        out = torch.empty((E, n, n), dtype=out_dtype, device=coords.device)
+    elif out.shape != (E, n, n) or not out.is_contiguous():
+        raise ValueError("out must be a contiguous [E][n][n] tensor")
+    od = F64 if out.dtype == torch.float64 else F32
+    opts = nat.options_struct(jac, contract, 0, warps_per_cta, ctas_per_sm,
+                              dev_err.data_ptr() if dev_err is not None else 0)
+    nat.fem_integrate_fwd(m, form, _coef_ptr(coef, E), out.data_ptr(), od, opts, _stream_ptr(stream))
+    return out
+
+
+def geometry(coords, conn, coef=None, jac=JAC_AUTO, dev_err=None, stream=None):
+    """fem_geometry test hook: (detJ [E] float64, G [E][d(d+1)/2] float32)."""
+    m = _mesh_struct(coords, conn)
+    E = conn.shape[0]
+    det = torch.empty(E, dtype=torch.float64, device=coords.device)
+    G = torch.empty((E, m.dim * (m.dim + 1) // 2), dtype=torch.float32, device=coords.device)
+    opts = nat.options_struct(jac, 0, 0, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
+    nat.fem_geometry(m, _coef_ptr(coef, E), opts, det.data_ptr(), G.data_ptr(), _stream_ptr(stream))
+    return det, G
+
+
+class Workspace:
+    """Device workspace of the adjoint for one connectivity (incidence CSR + scratch)."""
+
+    def __init__(self, coords, conn, form=LAPLACE_P1, stream=None):
+        self.m = _mesh_struct(coords, conn)
+        opts = nat.options_struct()
+        self.bytes = nat.fem_bwd_workspace_size(self.m, form, opts)
+        self.buf = torch.empty(max(self.bytes, 1), dtype=torch.uint8, device=coords.device)
+        nat.fem_incidence_build(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(stream))
+
+
+def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None,
+                  reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dcoef=True, jac=JAC_AUTO,
+                  warps_per_cta=0, ctas_per_sm=0, dcoords=None, dcoef=None, dev_err=None, stream=None):
+    """fem_integrate_bwd: (dcoords [V][d] or None, dcoef [E] or None) for the upstream dA."""
+    m = _mesh_struct(coords, conn)
+    E, V = conn.shape[0], coords.shape[0]
+    if dA.dtype != torch.float32 or not dA.is_contiguous():
+        raise ValueError("dA must be a contiguous float32 tensor")
+    if need_dcoords and dcoords is None:
+        dcoords = torch.empty((V, m.dim), dtype=torch.float32, device=coords.device)
+    if need_dcoef and dcoef is None:
+        dcoef = torch.empty(E, dtype=torch.float32, device=coords.device)
+    if not need_dcoords:
+        dcoords = None
+    if not need_dcoef:
+        dcoef = None
+    ws_ptr, ws_bytes = 0, 0
+    if dcoords is not None and reduce in (REDUCE_DETERMINISTIC, REDUCE_DEFERRED):
+        if ws is None:
+            ws = Workspace(coords, conn, form, stream)
+        ws_ptr, ws_bytes = ws.buf.data_ptr(), ws.bytes
+    opts = nat.options_struct(jac, 0, reduce, warps_per_cta, ctas_per_sm,
+                              dev_err.data_ptr() if dev_err is not None else 0)
+    nat.fem_integrate_bwd(m, form, _coef_ptr(coef, E), dA.data_ptr(),
+                          dcoords.data_ptr() if dcoords is not None else 0,
+                          dcoef.data_ptr() if dcoef is not None else 0, ws_ptr, ws_bytes, opts,
+                          _stream_ptr(stream))
+    return dcoords, dcoef
+
+
+def adjoint_reduce(coords, conn, ws: Workspace, dcoords, stream=None):
+    """fem_adjoint_reduce: completes a REDUCE_DEFERRED adjoint into dcoords."""
+    m = _mesh_struct(coords, conn)
+    nat.fem_adjoint_reduce(m, ws.buf.data_ptr(), ws.bytes, dcoords.data_ptr(), _stream_ptr(stream))
+    return dcoords
+
+
+class _IntegrateFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coords, coef, mesh, form, jac, reduce):
+        A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac)
+        ctx.save_for_backward(coords, coef if coef is not None else torch.empty(0))
+        ctx.mesh, ctx.form, ctx.jac, ctx.reduce = mesh, form, jac, reduce
+        ctx.has_coef = coef is not None
+        return A
+
+    @staticmethod
+    def backward(ctx, dA):
+        coords, coef = ctx.saved_tensors
+        coef = coef if ctx.has_coef else None
+        need_x = ctx.needs_input_grad[0]
+        need_w = ctx.has_coef and ctx.needs_input_grad[1]
+        ws = ctx.mesh.workspace(ctx.form) if (need_x and ctx.reduce == REDUCE_DETERMINISTIC) else None
+        dx, dw = integrate_bwd(coords.detach(), ctx.mesh.conn, ctx.form, dA.contiguous().float(), coef,
+                               ws=ws, reduce=ctx.reduce, need_dcoords=need_x, need_dcoef=need_w,
+                               jac=ctx.jac)
+        return dx, dw, None, None, None, None
+
+
+class Mesh:
+    """A simplex mesh on the GPU: coords [V][d] (float32/float64), conn [E][d+1] int32."""
+
+    def __init__(self, coords: torch.Tensor, conn: torch.Tensor):
+        self.coords = coords
+        self.conn = conn.contiguous()
+        self._ws = {}
+
+    @property
+    def dim(self):
+        return self.coords.shape[1]
+
+    def workspace(self, form=LAPLACE_P1) -> Workspace:
+        if "ws" not in self._ws:
+            self._ws["ws"] = Workspace(self.coords.detach(), self.conn, form)
+        return self._ws["ws"]
+
+    def integrate(self, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC, coords=None):
+        """Element matrices, differentiable with respect to coords and coef."""
+        x = self.coords if coords is None else coords
+        if x.dtype != torch.float32 and (x.requires_grad or (coef is not None and coef.requires_grad)):
+            raise ValueError("the adjoint takes float32 coordinates")
+        return _IntegrateFn.apply(x, coef, self, form, jac, reduce)
+
+
+def integrate(coords, conn, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC):
+    """Differentiable element matrices for a one-off mesh (builds the incidence on first backward)."""
+    return Mesh(coords, conn).integrate(form, coef, jac, reduce)

@@ -1,0 +1,152 @@
+"""ctypes binding of libfem_gb300 (the C ABI in include/fem.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  If the library is missing this module raises; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfem_gb300.so")
+
+FEM_OK, FEM_ERR_ARG, FEM_ERR_UNSUPPORTED, FEM_ERR_WORKSPACE, FEM_ERR_CUDA = range(5)
+LAPLACE_P1, LAPLACE_P2, ELASTIC_P1 = 0, 1, 2
+F32, F64 = 0, 1
+JAC_AUTO, JAC_F64, JAC_COMP_F32, JAC_F32 = 0, 1, 2, 3
+CONTRACT_F32, CONTRACT_BF16X3 = 0, 1
+REDUCE_DETERMINISTIC, REDUCE_ATOMIC, REDUCE_DEFERRED = 0, 1, 2
+DEVERR_CONN, DEVERR_DEGENERATE = 1, 2
+
+# every symbol include/fem.h declares
+EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info",
+           "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
+           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce")
+
+
+class FemError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class FemMesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("coord_dtype", ctypes.c_int32),
+                ("n_vert", ctypes.c_int64), ("n_elem", ctypes.c_int64),
+                ("conn", ctypes.c_void_p), ("coords", ctypes.c_void_p)]
+
+
+class FemOptions(ctypes.Structure):
+    _fields_ = [("jac", ctypes.c_int32), ("contract", ctypes.c_int32), ("reduce", ctypes.c_int32),
+                ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("dev_err", ctypes.c_void_p)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load():
+    """Loads the library (it must have been built, e.g. by __graft_entry__.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libfem_gb300.so is not built ({LIB_PATH}); run "
+                               "`python -m paper_1103_0066_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        MP, OP = ctypes.POINTER(FemMesh), ctypes.POINTER(FemOptions)
+        sig = {
+            "fem_version": ([], ctypes.c_char_p),
+            "fem_status_string": ([ctypes.c_int], ctypes.c_char_p),
+            "fem_last_error": ([], ctypes.c_char_p),
+            "fem_form_info": ([I32, I32, P, P, P], ctypes.c_int),
+            "fem_reference_tensor": ([I32, I32, P, SZ], ctypes.c_int),
+            "fem_integrate_fwd": ([MP, I32, P, P, I32, OP, P], ctypes.c_int),
+            "fem_geometry": ([MP, P, OP, P, P, P], ctypes.c_int),
+            "fem_bwd_workspace_size": ([MP, I32, OP, ctypes.POINTER(SZ)], ctypes.c_int),
+            "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
+            "fem_integrate_bwd": ([MP, I32, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
+            "fem_adjoint_reduce": ([MP, P, SZ, P, P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def _status_name(s: int) -> str:
+    try:
+        return load().fem_status_string(s).decode()
+    except Exception:  # noqa: BLE001 - used while formatting another error
+        return f"status {s}"
+
+
+def check(status: int) -> None:
+    if status != FEM_OK:
+        raise FemError(status, load().fem_last_error().decode())
+
+
+def mesh_struct(dim: int, coord_dtype: int, n_vert: int, n_elem: int, conn_ptr: int,
+                coords_ptr: int) -> FemMesh:
+    return FemMesh(dim, coord_dtype, n_vert, n_elem, conn_ptr or None, coords_ptr or None)
+
+
+def options_struct(jac=JAC_AUTO, contract=CONTRACT_F32, reduce=REDUCE_DETERMINISTIC, warps_per_cta=0,
+                   ctas_per_sm=0, dev_err_ptr=0) -> FemOptions:
+    return FemOptions(jac, contract, reduce, warps_per_cta, ctas_per_sm, 0, dev_err_ptr or None)
+
+
+def version() -> str:
+    return load().fem_version().decode()
+
+
+def fem_form_info(form: int, dim: int):
+    n, ng, den = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(load().fem_form_info(form, dim, ctypes.byref(n), ctypes.byref(ng), ctypes.byref(den)))
+    return n.value, ng.value, den.value
+
+
+def fem_reference_tensor(form: int, dim: int, out_ptr: int, cap: int) -> None:
+    check(load().fem_reference_tensor(form, dim, out_ptr, cap))
+
+
+def fem_integrate_fwd(mesh: FemMesh, form: int, coef_ptr: int, A_ptr: int, out_dtype: int,
+                      opts: FemOptions, stream: int) -> None:
+    check(load().fem_integrate_fwd(ctypes.byref(mesh), form, coef_ptr or None, A_ptr or None,
+                                   out_dtype, ctypes.byref(opts), stream or None))
+
+
+def fem_geometry(mesh: FemMesh, coef_ptr: int, opts: FemOptions, det_ptr: int, G_ptr: int,
+                 stream: int) -> None:
+    check(load().fem_geometry(ctypes.byref(mesh), coef_ptr or None, ctypes.byref(opts),
+                              det_ptr or None, G_ptr or None, stream or None))
+
+
+def fem_bwd_workspace_size(mesh: FemMesh, form: int, opts: FemOptions) -> int:
+    b = ctypes.c_size_t()
+    check(load().fem_bwd_workspace_size(ctypes.byref(mesh), form, ctypes.byref(opts), ctypes.byref(b)))
+    return b.value
+
+
+def fem_incidence_build(mesh: FemMesh, ws_ptr: int, ws_bytes: int, stream: int) -> None:
+    check(load().fem_incidence_build(ctypes.byref(mesh), ws_ptr or None, ws_bytes, stream or None))
+
+
+def fem_integrate_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoords_ptr: int,
+                      dcoef_ptr: int, ws_ptr: int, ws_bytes: int, opts: FemOptions, stream: int) -> None:
+    check(load().fem_integrate_bwd(ctypes.byref(mesh), form, coef_ptr or None, dA_ptr or None,
+                                   dcoords_ptr or None, dcoef_ptr or None, ws_ptr or None, ws_bytes,
+                                   ctypes.byref(opts), stream or None))
+
+
+def fem_adjoint_reduce(mesh: FemMesh, ws_ptr: int, ws_bytes: int, dcoords_ptr: int, stream: int) -> None:
+    check(load().fem_adjoint_reduce(ctypes.byref(mesh), ws_ptr or None, ws_bytes, dcoords_ptr or None,
+                                    stream or None))

@@ -1,0 +1,304 @@
+// fem_api.cu -- the C ABI of libfem_gb300 (declared in include/fem.h):
+// argument validation, defaults, dispatch to the kernels, status codes.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/fem.h"
+#include "fem_core.cuh"
+#include "fem_internal.h"
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+fem_status fail(fem_status s, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+fem_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(FEM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+fem_status ok() {
+  g_msg[0] = '\0';
+  return FEM_OK;
+}
+
+const fem_options kDefaults = {0, 0, 0, 0, 0, 0, nullptr};
+
+fem_status check_mesh(const fem_mesh* m) {
+  if (!m) return fail(FEM_ERR_ARG, "mesh is NULL");
+  if (m->dim != 2 && m->dim != 3) return fail(FEM_ERR_ARG, "mesh->dim must be 2 or 3 (got %d)", m->dim);
+  if (m->coord_dtype != FEM_F32 && m->coord_dtype != FEM_F64)
+    return fail(FEM_ERR_ARG, "mesh->coord_dtype must be FEM_F32 or FEM_F64");
+  if (m->n_elem < 0 || m->n_vert < 0) return fail(FEM_ERR_ARG, "negative mesh size");
+  if (m->n_elem > 0 && (!m->conn || !m->coords))
+    return fail(FEM_ERR_ARG, "mesh->conn and mesh->coords must be non-NULL when n_elem > 0");
+  if (m->n_vert > INT32_MAX) return fail(FEM_ERR_UNSUPPORTED, "n_vert exceeds the int32 index range");
+  return FEM_OK;
+}
+
+fem_status check_options(const fem_options* o) {
+  if (o->jac < FEM_JAC_AUTO || o->jac > FEM_JAC_F32) return fail(FEM_ERR_ARG, "options->jac out of range");
+  if (o->contract < FEM_CONTRACT_F32 || o->contract > FEM_CONTRACT_BF16X3)
+    return fail(FEM_ERR_ARG, "options->contract out of range");
+  if (o->reduce < FEM_REDUCE_DETERMINISTIC || o->reduce > FEM_REDUCE_DEFERRED)
+    return fail(FEM_ERR_ARG, "options->reduce out of range");
+  if (o->warps_per_cta < 0 || o->warps_per_cta > 16) return fail(FEM_ERR_ARG, "options->warps_per_cta must be 0..16");
+  if (o->ctas_per_sm < 0 || o->ctas_per_sm > 64) return fail(FEM_ERR_ARG, "options->ctas_per_sm must be 0..64");
+  if (o->reserved != 0) return fail(FEM_ERR_ARG, "options->reserved must be 0");
+  return FEM_OK;
+}
+
+int form_rows(int form, int dim) {
+  const int nb = form == FEM_LAPLACE_P2 ? (dim + 1) * (dim + 2) / 2 : dim + 1;
+  return nb * (form == FEM_ELASTIC_P1 ? dim : 1);
+}
+
+int resolve_jac(int jac, bool coord_f64, bool out_f64) {
+  if (jac == FEM_JAC_AUTO) return (coord_f64 || out_f64) ? fem::JAC_F64 : fem::JAC_COMP;
+  if (jac == FEM_JAC_F64) return fem::JAC_F64;
+  if (jac == FEM_JAC_COMP_F32) return fem::JAC_COMP;
+  return fem::JAC_F32;
+}
+
+template <int D, int FORM>
+void copy_ref(int32_t* K) {
+  using FT = fem::FormTraits<D, FORM>;
+  constexpr auto R = fem::make_ref_tensor<D, FORM>();
+  for (int g = 0; g < FT::NG; ++g)
+    for (int i = 0; i < FT::N; ++i)
+      for (int j = 0; j < FT::N; ++j) K[(g * FT::N + i) * FT::N + j] = R.v[g][i][j];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fem_version(void) { return "fem_gb300 0.1 (sm_103a)"; }
+
+const char* fem_status_string(fem_status s) {
+  switch (s) {
+    case FEM_OK: return "FEM_OK";
+    case FEM_ERR_ARG: return "FEM_ERR_ARG";
+    case FEM_ERR_UNSUPPORTED: return "FEM_ERR_UNSUPPORTED";
+    case FEM_ERR_WORKSPACE: return "FEM_ERR_WORKSPACE";
+    case FEM_ERR_CUDA: return "FEM_ERR_CUDA";
+  }
+  return "FEM_ERR_UNKNOWN";
+}
+
+const char* fem_last_error(void) { return g_msg; }
+
+fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den) {
+  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim must be 2 or 3");
+  const int np = form == FEM_ELASTIC_P1 ? dim * dim : dim;
+  if (n) *n = form_rows(form, dim);
+  if (n_geom) *n_geom = np * (np + 1) / 2;
+  if (den) *den = (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
+  return ok();
+}
+
+fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K, size_t cap) {
+  int32_t n = 0, ng = 0;
+  fem_status s = fem_form_info(form, dim, &n, &ng, nullptr);
+  if (s != FEM_OK) return s;
+  if (!K) return fail(FEM_ERR_ARG, "K is NULL");
+  if (cap < size_t(ng) * n * n) return fail(FEM_ERR_ARG, "K capacity %zu < %d", cap, ng * n * n);
+  if (dim == 2) {
+    if (form == FEM_LAPLACE_P1) copy_ref<2, fem::LAPLACE_P1>(K);
+    if (form == FEM_LAPLACE_P2) copy_ref<2, fem::LAPLACE_P2>(K);
+    if (form == FEM_ELASTIC_P1) copy_ref<2, fem::ELASTIC_P1>(K);
+  } else {
+    if (form == FEM_LAPLACE_P1) copy_ref<3, fem::LAPLACE_P1>(K);
+    if (form == FEM_LAPLACE_P2) copy_ref<3, fem::LAPLACE_P2>(K);
+    if (form == FEM_ELASTIC_P1) copy_ref<3, fem::ELASTIC_P1>(K);
+  }
+  return ok();
+}
+
+fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
+                             int32_t out_dtype, const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (out_dtype != FEM_F32 && out_dtype != FEM_F64) return fail(FEM_ERR_ARG, "out_dtype out of range");
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (mesh->n_elem == 0) return ok();
+  if (!A) return fail(FEM_ERR_ARG, "A is NULL");
+  const bool cf64 = mesh->coord_dtype == FEM_F64, of64 = out_dtype == FEM_F64;
+  if ((cf64 || of64) && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
+    return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates or FP64 output need FEM_JAC_F64");
+  if (o->contract != FEM_CONTRACT_F32)
+    return fail(FEM_ERR_UNSUPPORTED, "tensor-core contraction is not available for this form/output");
+  fem::FwdLaunch L{};
+  L.dim = mesh->dim;
+  L.form = form;
+  L.jac = resolve_jac(o->jac, cf64, of64);
+  L.coord_f64 = cf64;
+  L.out_f64 = of64;
+  L.conn = mesh->conn;
+  L.coords = mesh->coords;
+  L.coef = coef;
+  L.A = A;
+  L.n_elem = mesh->n_elem;
+  L.n_vert = mesh->n_vert;
+  L.dev_err = o->dev_err;
+  L.warps = o->warps_per_cta ? o->warps_per_cta : 4;
+  L.ctas_per_sm = o->ctas_per_sm;
+  L.stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (L.dim == 2)
+    e = fem::launch_fwd_d2(L);
+  else if (form == FEM_ELASTIC_P1)
+    e = fem::launch_fwd_d3_ela(L);
+  else
+    e = fem::launch_fwd_d3_lap(L);
+  if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_fwd launch");
+  return ok();
+}
+
+fem_status fem_geometry(const fem_mesh* mesh, const float* coef, const fem_options* options, double* detJ,
+                        float* G, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (mesh->n_elem == 0 || (!detJ && !G)) return ok();
+  const bool cf64 = mesh->coord_dtype == FEM_F64;
+  if (cf64 && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
+    return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates need FEM_JAC_F64");
+  fem::GeoLaunch L{};
+  L.dim = mesh->dim;
+  L.jac = resolve_jac(o->jac, cf64, false);
+  L.coord_f64 = cf64;
+  L.conn = mesh->conn;
+  L.coords = mesh->coords;
+  L.coef = coef;
+  L.detJ = detJ;
+  L.G = G;
+  L.n_elem = mesh->n_elem;
+  L.n_vert = mesh->n_vert;
+  L.dev_err = o->dev_err;
+  L.stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = fem::launch_geometry(L);
+  if (e != cudaSuccess) return cuda_fail(e, "fem_geometry launch");
+  return ok();
+}
+
+fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_options* options,
+                                  size_t* bytes) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (!bytes) return fail(FEM_ERR_ARG, "bytes is NULL");
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  *bytes = o->reduce == FEM_REDUCE_ATOMIC
+               ? 0
+               : fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, nullptr, nullptr);
+  return ok();
+}
+
+fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  fem::BwdWorkspace W{};
+  const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W);
+  if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
+  cudaError_t e = fem::launch_incidence_build(mesh->dim, mesh->conn, mesh->n_elem, mesh->n_vert, W,
+                                              static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "fem_incidence_build launch");
+  return ok();
+}
+
+fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
+                             float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
+                             const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");
+  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool atomic = o->reduce == FEM_REDUCE_ATOMIC;
+  if (o->reduce == FEM_REDUCE_DEFERRED && !dcoords)
+    return fail(FEM_ERR_ARG, "FEM_REDUCE_DEFERRED needs dcoords (written by fem_adjoint_reduce)");
+  fem::BwdWorkspace W{};
+  if (dcoords && !atomic) {
+    const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W);
+    if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
+  }
+  if (mesh->n_elem > 0 && !dA) return fail(FEM_ERR_ARG, "dA is NULL");
+  if (!dcoords && !dcoef) return ok();
+  cudaError_t e;
+  if (dcoords && atomic) {
+    e = fem::launch_zero_f32(dcoords, mesh->n_vert * mesh->dim, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing dcoords");
+  }
+  if (mesh->n_elem > 0) {
+    fem::BwdLaunch L{};
+    L.dim = mesh->dim;
+    L.form = form;
+    L.jac = resolve_jac(o->jac, false, false);
+    L.atomic = (dcoords && atomic) ? 1 : 0;
+    L.conn = mesh->conn;
+    L.coords = static_cast<const float*>(mesh->coords);
+    L.coef = coef;
+    L.dA = dA;
+    L.dcoef = dcoef;
+    L.xbar = (dcoords && !atomic) ? W.scratch : nullptr;
+    L.dcoords = dcoords;
+    L.n_elem = mesh->n_elem;
+    L.n_vert = mesh->n_vert;
+    L.dev_err = o->dev_err;
+    L.warps = o->warps_per_cta ? o->warps_per_cta : 4;
+    L.ctas_per_sm = o->ctas_per_sm;
+    L.stream = st;
+    e = fem::launch_bwd_elem(L);
+    if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd element launch");
+  }
+  if (dcoords && o->reduce == FEM_REDUCE_DETERMINISTIC) {
+    e = fem::launch_vertex_reduce(mesh->dim, W, mesh->n_vert, dcoords, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd reduction launch");
+  }
+  return ok();
+}
+
+fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes, float* dcoords,
+                              void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (!dcoords) return fail(FEM_ERR_ARG, "dcoords is NULL");
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  fem::BwdWorkspace W{};
+  const size_t need =
+      fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, const_cast<void*>(ws), &W);
+  if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
+  cudaError_t e = fem::launch_vertex_reduce(mesh->dim, W, mesh->n_vert, dcoords, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "fem_adjoint_reduce launch");
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// fem_forms.cuh -- reference (analytic) tensors K of the weak forms, built at
+// compile time in exact integer arithmetic.
+//
+// Knepley & Terrel, Sec. 3: the element tensor is the contraction
+// A^{ij} = G^{mu nu} K^{ij}_{mu nu} (Eq. 1, Eq. 6), where K depends only on
+// the form and the reference element (Eq. 7) and can be computed a priori
+// (end of Sec. 3.1).  Here K is generated by constexpr C++ from the basis
+// written in barycentric coordinates, so the CUDA kernels see every entry as
+// an immediate and skip the zero entries at compile time (sparse contraction
+// with no index arrays).
+//
+// Forms (ids match the C ABI):
+//   LAPLACE_P1 / LAPLACE_P2 : K^{ij}_{mu nu} = int_ref d_mu phi_i d_nu phi_j     (Eq. 7)
+//   ELASTIC_P1 : eps(v):eps(u), i.e. Eq. 10 scaled by the 1/4 of Eq. 14.  With the
+//     symmetric gradient the geometric tensor needs both spatial indices,
+//     G^{(mu a),(nu b)} = |J| Jinv_{mu a} Jinv_{nu b}, and
+//     K^{(c,i),(c',j)}_{(mu a),(nu b)} = Kref^{ij}_{mu nu} (d_{cc'} d_{ab} + d_{a c'} d_{b c}) / 2
+//     (reading of Eqs. 9-15: Eq. 15's d x d G as printed would give the vector
+//     Laplacian, which does not vanish on rigid rotations).
+//
+// Folding: G is symmetric under (p <-> q) for p, q its two index slots, so only
+// the pairs p <= q are kept (d(d+1)/2 Laplacian entries, d^2(d^2+1)/2 elasticity
+// entries); K is folded to K'_{pq} = K_{pq} + K_{qp} (p < q).  The folded K' is
+// symmetric in (i, j), so A is symmetric and only i <= j is computed.
+//
+// Integer scaling: every entry is stored as K' * DEN with DEN = (d+2)! (twice
+// that for elasticity), using  int_ref lambda^a = a! / (|a| + d)!.
+#pragma once
+#include <cstdint>
+
+namespace fem {
+
+enum FormId : int { LAPLACE_P1 = 0, LAPLACE_P2 = 1, ELASTIC_P1 = 2 };
+
+template <int D, int FORM>
+struct FormTraits {
+  static_assert(D == 2 || D == 3, "dimension");
+  static constexpr int NV = D + 1;                                // vertices
+  static constexpr int DEG = FORM == LAPLACE_P2 ? 2 : 1;
+  static constexpr int NB = DEG == 1 ? D + 1 : (D + 1) * (D + 2) / 2;  // scalar basis
+  static constexpr int NC = FORM == ELASTIC_P1 ? D : 1;           // components
+  static constexpr int N = NB * NC;                               // rows of A_e
+  static constexpr int NN = N * N;
+  static constexpr int NP = FORM == ELASTIC_P1 ? D * D : D;       // range of one G slot
+  static constexpr int NG = NP * (NP + 1) / 2;                    // folded G entries
+  static constexpr int NT = N * (N + 1) / 2;                      // unique A entries
+  static constexpr int DEN = (D == 2 ? 24 : 120) * (FORM == ELASTIC_P1 ? 2 : 1);
+};
+
+// index of the pair (p, q), p <= q, in row-major upper-triangle order
+constexpr int pair_index(int p, int q, int np) { return p * np - p * (p - 1) / 2 + (q - p); }
+constexpr int tri_row(int t, int n) {
+  int i = 0;
+  while (t >= n - i) { t -= n - i; ++i; }
+  return i;
+}
+constexpr int tri_col(int t, int n) {
+  int i = 0;
+  while (t >= n - i) { t -= n - i; ++i; }
+  return i + t;
+}
+
+// d lambda_k / d xi_mu on the reference simplex (lambda_0 = 1 - sum xi, lambda_k = xi_k)
+constexpr int dlam(int k, int mu) { return k == 0 ? -1 : (k - 1 == mu ? 1 : 0); }
+
+// d_mu phi_i as a linear polynomial c0 + sum_m c[m] lambda_m (integer coefficients)
+struct Lin {
+  int c0;
+  int c[4];
+};
+
+template <int D, int DEG>
+constexpr Lin basis_deriv(int i, int mu) {
+  Lin r{0, {0, 0, 0, 0}};
+  if (DEG == 1) {
+    r.c0 = dlam(i, mu);
+    return r;
+  }
+  if (i <= D) {  // vertex function lambda_i (2 lambda_i - 1): derivative (4 lambda_i - 1) dlam_i
+    r.c[i] = 4 * dlam(i, mu);
+    r.c0 = -dlam(i, mu);
+    return r;
+  }
+  int t = i - (D + 1);  // edge functions 4 lambda_a lambda_b, a < b lexicographic
+  for (int a = 0; a <= D; ++a)
+    for (int b = a + 1; b <= D; ++b) {
+      if (t == 0) {
+        r.c[b] += 4 * dlam(a, mu);
+        r.c[a] += 4 * dlam(b, mu);
+        return r;
+      }
+      --t;
+    }
+  return r;
+}
+
+// (d+2)! * int_ref (p)(q) dxi for two linear polynomials in the barycentrics
+template <int D>
+constexpr int integrate_lin_lin(const Lin& p, const Lin& q) {
+  int s = p.c0 * q.c0 * (D + 1) * (D + 2);
+  int sp = 0, sq = 0;
+  for (int m = 0; m <= D; ++m) { sp += p.c[m]; sq += q.c[m]; }
+  s += (p.c0 * sq + q.c0 * sp) * (D + 2);
+  for (int m = 0; m <= D; ++m)
+    for (int n = 0; n <= D; ++n) s += p.c[m] * q.c[n] * (m == n ? 2 : 1);
+  return s;
+}
+
+template <int D, int FORM>
+struct RefTensor {
+  using T = FormTraits<D, FORM>;
+  int v[T::NG][T::N][T::N];  // K' * DEN, folded
+};
+
+template <int D, int FORM>
+constexpr RefTensor<D, FORM> make_ref_tensor() {
+  using T = FormTraits<D, FORM>;
+  RefTensor<D, FORM> r{};
+  // scalar Laplacian tensor Kref[mu][nu][i][j] * (d+2)!
+  int kref[D][D][T::NB][T::NB] = {};
+  for (int mu = 0; mu < D; ++mu)
+    for (int nu = 0; nu < D; ++nu)
+      for (int i = 0; i < T::NB; ++i)
+        for (int j = 0; j < T::NB; ++j)
+          kref[mu][nu][i][j] = integrate_lin_lin<D>(basis_deriv<D, T::DEG>(i, mu),
+                                                    basis_deriv<D, T::DEG>(j, nu));
+  if constexpr (FORM != ELASTIC_P1) {
+    for (int mu = 0; mu < D; ++mu)
+      for (int nu = mu; nu < D; ++nu) {
+        int g = pair_index(mu, nu, D);
+        for (int i = 0; i < T::NB; ++i)
+          for (int j = 0; j < T::NB; ++j)
+            r.v[g][i][j] = kref[mu][nu][i][j] + (mu != nu ? kref[nu][mu][i][j] : 0);
+      }
+  } else {
+    // unfolded K_{(mu a),(nu b)}^{(c,i),(c',j)} * 2 (d+2)! = Kref * (d_cc' d_ab + d_ac' d_bc)
+    for (int p = 0; p < T::NP; ++p)
+      for (int q = p; q < T::NP; ++q) {
+        int g = pair_index(p, q, T::NP);
+        for (int I = 0; I < T::N; ++I)
+          for (int J = 0; J < T::N; ++J) {
+            int c = I / T::NB, i = I % T::NB, cp = J / T::NB, j = J % T::NB;
+            auto term = [&](int pp, int qq) {
+              int mu = pp / D, a = pp % D, nu = qq / D, b = qq % D;
+              int w = (c == cp && a == b ? 1 : 0) + (a == cp && b == c ? 1 : 0);
+              return kref[mu][nu][i][j] * w;
+            };
+            r.v[g][I][J] = term(p, q) + (p != q ? term(q, p) : 0);
+          }
+      }
+  }
+  return r;
+}
+
+template <int D, int FORM>
+struct Ref {
+  static constexpr RefTensor<D, FORM> K = make_ref_tensor<D, FORM>();
+};
+
+}  // namespace fem

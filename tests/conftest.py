@@ -17,3 +17,24 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gfem():
+    """The CUDA library (built in-tree) and its binding, for -m gpu tests."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_0066_gb300 as fem
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    fem.nat.load()
+    return fem
+
+
+def rel_err_per_element(A, Aref):
+    """Per element: max_ij |A - Aref| / max_ij |Aref| (FP64, numpy)."""
+    import numpy as np
+    A = np.asarray(A, dtype=np.float64)
+    d = np.abs(A - Aref).reshape(A.shape[0], -1).max(1)
+    s = np.abs(Aref).reshape(A.shape[0], -1).max(1)
+    return d / np.where(s > 0, s, 1.0)

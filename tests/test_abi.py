@@ -1,0 +1,126 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol the
+header declares, its host-side reference tensor K reproduces the oracle's
+direct quadrature through Eq. 6, and host-detectable errors return status
+codes before any launch."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LP1, LP2, EP1 = 0, 1, 2
+
+
+@pytest.fixture(scope="module")
+def fem():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_0066_gb300 as fem
+    return fem
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "fem.h")).read()
+    return sorted(set(re.findall(r"FEM_API\s+[\w\s\*]+?\b(fem_\w+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fem):
+    lib = fem.nat.load()
+    declared = _declared_symbols()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(fem.nat.EXPORTS) == declared
+    assert "sm_103a" in fem.nat.version()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_form_info(fem, dim):
+    assert fem.form_info(LP1, dim) == (dim + 1, dim * (dim + 1) // 2, 24 if dim == 2 else 120)
+    nb2 = (dim + 1) * (dim + 2) // 2
+    assert fem.form_info(LP2, dim)[0] == nb2
+    n, ng, den = fem.form_info(EP1, dim)
+    assert n == dim * (dim + 1) and ng == dim * dim * (dim * dim + 1) // 2 and den == 2 * (24 if dim == 2 else 120)
+
+
+def _G_true(form, X):
+    """Folded geometric tensor of Eq. 8 (and its symmetric-gradient analogue),
+    written out with numpy for one element: |J| Jinv Jinv^T."""
+    dim = X.shape[1]
+    J = (X[1:] - X[0]).T            # J[a][mu]
+    B = np.linalg.inv(J)            # B[mu][a] = d xi_mu / d x_a
+    s = abs(np.linalg.det(J))
+    if form != EP1:
+        M = s * B @ B.T
+        return np.array([M[m, n] for m in range(dim) for n in range(m, dim)])
+    b = B.ravel()                   # p = mu*d + a
+    M = s * np.outer(b, b)
+    npp = dim * dim
+    return np.array([M[p, q] for p in range(npp) for q in range(p, npp)])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [LP1, LP2, EP1])
+def test_reference_tensor_reproduces_quadrature(fem, orc, dim, form):
+    """Eq. 6: A = G : K with the library's K equals the oracle's direct quadrature."""
+    K, den = fem.reference_tensor(form, dim)
+    K = K.numpy().astype(np.float64)
+    n = K.shape[1]
+    assert np.array_equal(K, np.transpose(K, (0, 2, 1)))   # folded K' symmetric in (i, j)
+    rng = np.random.default_rng(12)
+    for trial in range(10):
+        X = rng.standard_normal((dim + 1, dim)) if trial else np.vstack([np.zeros(dim), np.eye(dim)])
+        if abs(np.linalg.det(X[1:] - X[0])) < 0.05:
+            continue
+        A = np.einsum("g,gij->ij", _G_true(form, X), K) / den
+        Ar, _, _ = orc.element_matrix(dim, form, X)
+        assert np.abs(A - Ar).max() < 1e-12 * np.abs(Ar).max()
+    if dim == 3 and form == EP1:
+        assert int((K != 0).sum()) == 513
+
+
+def _mesh(fem, dim=3, dtype=0, n_elem=10, conn=0x1000, coords=0x2000):
+    return fem.nat.mesh_struct(dim, dtype, 100, n_elem, conn, coords)
+
+
+def test_host_detected_errors(fem):
+    nat = fem.nat
+    lib = nat.load()
+    opts = nat.options_struct()
+    A = ctypes.c_void_p(0x3000)
+    # NULL mesh
+    assert lib.fem_integrate_fwd(None, LP1, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    assert "mesh" in lib.fem_last_error().decode()
+    # bad dim / form / dtype
+    m = _mesh(fem, dim=4)
+    assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    m = _mesh(fem)
+    assert lib.fem_integrate_fwd(ctypes.byref(m), 7, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 5, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    # NULL output / NULL conn with elements
+    assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, None, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    m0 = _mesh(fem, conn=0)
+    assert lib.fem_integrate_fwd(ctypes.byref(m0), LP1, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    # options out of range
+    for bad in (nat.options_struct(jac=9), nat.options_struct(warps_per_cta=17),
+                nat.options_struct(reduce=3), nat.FemOptions(0, 0, 0, 0, 0, 1, None)):
+        assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 0, ctypes.byref(bad), None) == nat.FEM_ERR_ARG
+    # FP64 coordinates with a FP32 Jacobian mode: unsupported combination
+    m64 = _mesh(fem, dtype=1)
+    o = nat.options_struct(jac=nat.JAC_COMP_F32)
+    assert lib.fem_integrate_fwd(ctypes.byref(m64), LP1, None, A, 0, ctypes.byref(o), None) == nat.FEM_ERR_UNSUPPORTED
+    # empty mesh: a no-op that launches nothing
+    me = _mesh(fem, n_elem=0)
+    assert lib.fem_integrate_fwd(ctypes.byref(me), LP1, None, None, 0, None, None) == nat.FEM_OK
+    # adjoint: FP64 coordinates unsupported, workspace checks
+    assert lib.fem_integrate_bwd(ctypes.byref(m64), LP1, None, A, A, None, None, 0, None, None) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_integrate_bwd(ctypes.byref(m), LP1, None, A, A, None, None, 0, None, None) == nat.FEM_ERR_WORKSPACE
+    big = fem.nat.mesh_struct(3, 0, 100, 2 ** 30, 0x1000, 0x2000)
+    b = ctypes.c_size_t()
+    assert lib.fem_bwd_workspace_size(ctypes.byref(big), LP1, None, ctypes.byref(b)) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_bwd_workspace_size(ctypes.byref(m), LP1, None, ctypes.byref(b)) == nat.FEM_OK
+    assert b.value >= 4 * (101 + 40) + 4 * 10 * 4 * 3
+    with pytest.raises(fem.FemError):
+        fem.nat.fem_form_info(5, 3)

@@ -1,0 +1,148 @@
+"""GPU parity of the adjoint against the oracle's reverse mode (-m gpu).
+
+Tolerance: max_v |g_gpu - g_ref| <= 1e-5 max_v |g_ref| for the coordinate
+gradient and the same, relative to max |dcoef_ref|, for the coefficient
+gradient.  The deterministic reduction must be bitwise reproducible; the
+atomic variant differs from it only by FP32 summation order."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1103_0066_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+LP1, LP2, EP1 = 0, 1, 2
+TOL = 1e-5
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _mesh(dim, n=None):
+    if dim == 2:
+        return mg.square_tri_mesh(n or 11, 0.2, mg.rng_for(41), np.float32)
+    return mg.cube_tet_mesh(n or 6, 0.15, mg.rng_for(41), 0.05, np.float32)
+
+
+def _rel(a, b):
+    return float(np.abs(np.asarray(a, np.float64) - b).max() / np.abs(b).max())
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [LP1, LP2, EP1])
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_adjoint_matches_oracle(gfem, orc, dim, form, reduce):
+    mesh = _mesh(dim)
+    n = mg.form_n(form, dim)
+    coef = mg.lognormal_coef(mg.rng_for(42), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(43), mesh.n_elem, n)
+    dx, dw = gfem.integrate_bwd(_t(mesh.coords), _t(mesh.conn), form, _t(dA), _t(coef), reduce=reduce)
+    gx, gw = orc.integrate_vjp(dim, form, mesh.conn, mesh.coords, dA, coef)
+    assert _rel(dx.cpu().numpy(), gx) <= TOL
+    assert _rel(dw.cpu().numpy(), gw) <= TOL
+
+
+def test_deterministic_is_bitwise_reproducible(gfem):
+    mesh = _mesh(3, 10)
+    dA = _t(mg.upstream(mg.rng_for(44), mesh.n_elem, 4))
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    ws = gfem.Workspace(coords, conn)
+    a, _ = gfem.integrate_bwd(coords, conn, LP1, dA, ws=ws, need_dcoef=False)
+    b, _ = gfem.integrate_bwd(coords, conn, LP1, dA, ws=ws, need_dcoef=False, warps_per_cta=8, ctas_per_sm=1)
+    ws2 = gfem.Workspace(coords, conn)  # rebuilt incidence: same sorted order
+    c, _ = gfem.integrate_bwd(coords, conn, LP1, dA, ws=ws2, need_dcoef=False)
+    assert torch.equal(a, b) and torch.equal(a, c)
+    d, _ = gfem.integrate_bwd(coords, conn, LP1, dA, reduce=1, need_dcoef=False)
+    assert _rel(d.cpu().numpy(), a.cpu().numpy().astype(np.float64)) <= 1e-6
+
+
+def test_incidence_csr_is_sorted_and_complete(gfem):
+    mesh = _mesh(3, 5)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    ws = gfem.Workspace(coords, conn)
+    V, E = mesh.n_vert, mesh.n_elem
+    raw = ws.buf.cpu().numpy().view(np.int32)
+    off = raw[: V + 1]
+    inc_start = ((4 * (V + 1) + 255) // 256) * 64
+    inc = raw[inc_start: inc_start + 4 * E]
+    slots = np.arange(4 * E)
+    vert = mesh.conn.ravel()
+    order = np.lexsort((slots, vert))
+    exp_off = np.concatenate([[0], np.cumsum(np.bincount(vert, minlength=V))])
+    assert np.array_equal(off, exp_off)
+    assert np.array_equal(inc, slots[order])
+
+
+def test_coefficient_only_and_coords_only(gfem, orc):
+    mesh = _mesh(3)
+    coef = mg.lognormal_coef(mg.rng_for(45), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(46), mesh.n_elem, 4)
+    gx, gw = orc.integrate_vjp(3, LP1, mesh.conn, mesh.coords, dA, coef)
+    dx, dw = gfem.integrate_bwd(_t(mesh.coords), _t(mesh.conn), LP1, _t(dA), _t(coef), need_dcoords=False)
+    assert dx is None and _rel(dw.cpu().numpy(), gw) <= TOL
+    dx, dw = gfem.integrate_bwd(_t(mesh.coords), _t(mesh.conn), LP1, _t(dA), _t(coef), need_dcoef=False)
+    assert dw is None and _rel(dx.cpu().numpy(), gx) <= TOL
+
+
+def test_autograd_function(gfem, orc):
+    mesh = _mesh(3)
+    coef0 = mg.lognormal_coef(mg.rng_for(47), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(48), mesh.n_elem, 12)
+    x = _t(mesh.coords).requires_grad_(True)
+    w = _t(coef0).requires_grad_(True)
+    A = gfem.Mesh(x, _t(mesh.conn)).integrate(EP1, w)
+    (A * _t(dA)).sum().backward()
+    gx, gw = orc.integrate_vjp(3, EP1, mesh.conn, mesh.coords, dA, coef0)
+    assert _rel(x.grad.cpu().numpy(), gx) <= TOL
+    assert _rel(w.grad.cpu().numpy(), gw) <= TOL
+
+
+def test_adjoint_against_fp64_finite_differences(gfem, orc):
+    """4^3 mesh with slivers: the GPU gradient against FP64 central differences of
+    the oracle's forward, per-vertex step 1e-4 x the smallest incident height."""
+    mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(4), 0.05, np.float32)
+    X = mesh.coords.astype(np.float64)
+    dA = mg.upstream(mg.rng_for(49), mesh.n_elem, 4).astype(np.float64)
+    dx, _ = gfem.integrate_bwd(_t(mesh.coords), _t(mesh.conn), LP1, _t(dA.astype(np.float32)),
+                               need_dcoef=False)
+    g = dx.cpu().numpy().astype(np.float64)
+    P = X[mesh.conn]
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1]))
+    fd = np.zeros_like(X)
+    for v in range(X.shape[0]):
+        inc = np.where((mesh.conn == v).any(1))[0]
+        if inc.size == 0:
+            continue
+        sub = mesh.conn[inc]
+        h = np.inf
+        for e in inc:
+            for k in range(4):
+                f = np.delete(P[e], k, axis=0)
+                area = np.linalg.norm(np.cross(f[1] - f[0], f[2] - f[0]))
+                h = min(h, vol[e] / area)
+        d = 1e-4 * h
+        for a in range(3):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[v, a] += d
+            Xm[v, a] -= d
+            Ap, _ = orc.integrate(3, LP1, sub, Xp)
+            Am, _ = orc.integrate(3, LP1, sub, Xm)
+            fd[v, a] = (np.sum(dA[inc] * Ap) - np.sum(dA[inc] * Am)) / (2 * d)
+    assert np.abs(g - fd).max() / np.abs(fd).max() <= TOL
+
+
+def test_full_adjoint_64_cube(gfem, orc):
+    """64^3 Kuhn cube with 5% slivers (1,572,864 tets), lognormal coefficient,
+    dA ~ N(0,1): the whole gradient against the oracle, both reductions."""
+    mesh = mg.workload_tet_slivers(64, k=4)
+    coef = mg.lognormal_coef(mg.rng_for(50), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(51), mesh.n_elem, 4)
+    gx, gw = orc.integrate_vjp(3, LP1, mesh.conn, mesh.coords, dA, coef)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    ws = gfem.Workspace(coords, conn)
+    for reduce in (0, 1):
+        dx, dw = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), ws=ws, reduce=reduce)
+        assert _rel(dx.cpu().numpy(), gx) <= TOL
+        assert _rel(dw.cpu().numpy(), gw) <= TOL
