@@ -160,12 +160,17 @@ def tet_workload(n=128, k=2):
     return mesh, dA
 
 
-def algorithmic_bytes(E, V, n, dim, coef):
-    """Each input read once, each output written once (vertex arrays once)."""
+def algorithmic_bytes(E, V, R, n, dim, coef):
+    """Bytes each kernel must move (every input read once, every output written
+    once, vertex arrays once).  R = records of the deterministic reduction (one
+    per distinct vertex of each 128-element tile)."""
     nv = dim + 1
     fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0)) + V * 4 * dim
-    bwd_elem = E * (4 * n * n + 4 * nv + 4 * nv * dim + (8 if coef else 0)) + V * 4 * dim
-    reduce = E * (4 * nv + 4 * nv * dim) + V * (4 + 4 * dim)
+    # dA, connectivity, the tile's sorted slot list (2 B/slot); record ends (2 B)
+    # and record sums (4 d B) written
+    bwd_elem = E * (4 * n * n + 4 * nv + 2 * nv + (8 if coef else 0)) + R * (2 + 4 * dim) + V * 4 * dim
+    # record sums and their vertex CSR read, dcoords written
+    reduce = R * (4 * dim + 4) + V * (4 + 4 * dim)
     return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
 
 
@@ -211,7 +216,7 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    mesh, dA_h = tet_workload()
+    mesh, dA_h = tet_workload(args.mesh_n)
     E, V = mesh.n_elem, mesh.n_vert
     coords = torch.from_numpy(mesh.coords).to(dev)
     conn = torch.from_numpy(mesh.conn).to(dev)
@@ -259,7 +264,9 @@ def run_ours(args):
     per = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
            for i, name in enumerate(("fwd", "bwd_elem", "reduce"))}
 
-    byts = algorithmic_bytes(E, V, 4, 3, False)
+    n_tiles = (E + 127) // 128
+    R = int(ws.buf[4 * n_tiles: 4 * n_tiles + 4].view(torch.int32).item())  # records (tile_rec[n_tiles])
+    byts = algorithmic_bytes(E, V, R, 4, 3, False)
     peak, peak_kind = hbm_peak()
     dom = max(per, key=per.get)
     kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
@@ -278,7 +285,7 @@ def run_ours(args):
     value = ws_n * E / (ms_step * 1e-3)
 
     # end to end through the public API: pinned host buffers, copies in the timed region
-    e2e_steps = max(3, min(K, 10))
+    e2e_steps = 0 if args.no_e2e else max(3, min(K, 10))
     coords_h = torch.from_numpy(mesh.coords).pin_memory()
     conn_h = torch.from_numpy(mesh.conn).pin_memory()
     dA_hp = torch.from_numpy(dA_h).pin_memory()
@@ -294,16 +301,18 @@ def run_ours(args):
         A_h.copy_(A, non_blocking=True)
         dc_h.copy_(dcoords, non_blocking=True)
 
-    e2e_step()
-    torch.cuda.synchronize()
-    barrier(pg, dev)
-    s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s2.record(stream)
-    for _ in range(e2e_steps):
+    e2e_ms = float("nan")
+    if e2e_steps:
         e2e_step()
-    e2.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(pg, s2.elapsed_time(e2), dev) / e2e_steps
+        torch.cuda.synchronize()
+        barrier(pg, dev)
+        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s2.record(stream)
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(pg, s2.elapsed_time(e2), dev) / e2e_steps
     h2d = coords_h.numel() * 4 + conn_h.numel() * 4 + dA_hp.numel() * 4
     d2h = A_h.numel() * 4 + dc_h.numel() * 4
 
@@ -311,8 +320,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws_n, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3D P1 Laplacian, 128^3 Kuhn cube, 6 tets/cell, jitter 0.15h, 5% slivers "
-                               "(12,582,912 tets, 2,775,835 vertices); FP32 coords and 4x4 FP32 element "
+        "config": {"workload": f"3D P1 Laplacian, {args.mesh_n}^3 Kuhn cube, 6 tets/cell, jitter 0.15h, "
+                               f"5% slivers ({E:,} tets, {V:,} vertices); FP32 coords and 4x4 FP32 element "
                                "matrices, compensated-FP32 Jacobian; step = forward + adjoint "
                                "(deterministic segmented reduction), dA ~ N(0,1)",
                    "elements": E, "vertices": V, "form": "laplace_p1", "dim": 3,
@@ -325,13 +334,15 @@ def run_ours(args):
         "fwd_adjoint": {"elements_per_s": E / (ms_step * 1e-3),
                         "GB/s": sum(byts.values()) / (ms_step * 1e-3) / 1e9,
                         "frac_of_peak": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / peak},
-        "setup": {"incidence_build_ms": setup_ms},
+        "setup": {"incidence_build_ms": setup_ms, "records": R, "slots": 4 * E},
         "e2e": {"value": ws_n * E / (e2e_ms * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps},
         "gpu_launches": 3 * K,
         "clocks": clk,
         "csrc_hash": h,
     }
+    if not e2e_steps:
+        out["e2e"] = None
     if rank == 0 and ws_n == 1 and not args.no_cpu:
         cpu, err = cpu_baseline_leg(mesh, dA_h, A, dcoords, args.cpu_sample)
         out["cpu_baseline"] = cpu
@@ -350,7 +361,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    mesh, dA = tet_workload()
+    mesh, dA = tet_workload(args.mesh_n)
     S = args.ref_sample
     nwin = max(1, mesh.n_elem // S)
 
@@ -388,7 +399,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle leg")
-    ap.add_argument("--cpu-sample", type=int, default=4_194_304)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
+    ap.add_argument("--cpu-sample", type=int, default=12_582_912)
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps

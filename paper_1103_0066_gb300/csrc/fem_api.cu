@@ -266,12 +266,15 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     L.coef = coef;
     L.dA = dA;
     L.dcoef = dcoef;
-    L.xbar = (dcoords && !atomic) ? W.scratch : nullptr;
+    const bool recs = dcoords && !atomic;
+    L.tile_rec = recs ? W.tile_rec : nullptr;
+    L.sorted = recs ? W.sorted : nullptr;
+    L.rec_end = recs ? W.rec_end : nullptr;
+    L.records = recs ? W.records : nullptr;
     L.dcoords = dcoords;
     L.n_elem = mesh->n_elem;
     L.n_vert = mesh->n_vert;
     L.dev_err = o->dev_err;
-    L.warps = o->warps_per_cta ? o->warps_per_cta : 4;
     L.ctas_per_sm = o->ctas_per_sm;
     L.stream = st;
     e = fem::launch_bwd_elem(L);

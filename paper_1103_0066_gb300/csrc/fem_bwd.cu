@@ -13,13 +13,19 @@
 //   4. |det J| enters as 1/|det J|:  d e_mu += -(L_e / det J) adj_mu   (d det / d e_mu = adj_mu)
 //   5. adj_mu = e_{mu+1} x e_{mu+2} (3D; rotated edges in 2D) is pulled back to the
 //      edge vectors, then x_{mu+1} += d e_mu and x_0 -= sum_mu d e_mu.
-// The per-vertex contributions go either to a per-element scratch buffer
-// [E][d+1][d] (deterministic segmented reduction afterwards) or straight into
-// dcoords with red.global.add (atomic variant).  dA is read through the same
-// per-warp shared-memory stage as the forward stores, with coalesced 16-byte loads.
+// A CTA of 4 warps owns a tile of 128 consecutive elements.  Each warp runs
+// the forward kernel's three-stage pipeline over its 32 elements (connectivity
+// two tiles ahead, coordinates one tile ahead in registers) and copies its
+// upstream dA (contiguous) with 16-byte cp.async into a padded stage.  In the
+// deterministic mode the CTA stages the (d+1) vertex contributions of its 128
+// elements in shared memory and writes one RECORD per distinct vertex of the
+// tile, summed in slot order (the tile's sorted slot list, built once per
+// mesh); the segmented reduction then adds the few records of each vertex.  The
+// atomic variant adds each contribution into dcoords with red.global.add.
 #include "fem_core.cuh"
 #include "fem_fwd.cuh"
 #include "fem_internal.h"
+#include "fem_pipe.cuh"
 
 namespace fem {
 
@@ -51,57 +57,78 @@ struct BwdParams {
   const float* coords;
   const float* coef;
   const float* dA;
+  const int32_t* tile_rec;  // first record of each tile (null: no coordinate records)
+  const uint16_t* sorted;   // per tile: slots sorted by (vertex, slot)
+  const uint16_t* rec_end;  // per record: end of its run in the tile's sorted list
+  float* records;           // [R][D]
   float* dcoef;
-  float* xbar;
-  float* dcoords;
+  float* dcoords;  // atomic mode
   int64_t n_elem;
   int64_t n_vert;
   int32_t* dev_err;
   int vec_conn;
   int vec_dA;
-  int vec_xbar;
 };
 
-template <int D, int FORM, int JAC, bool ATOMIC>
-__device__ __forceinline__ int bwd_warp_tile(const BwdParams& p, int64_t tile, int lane, float* st) {
-  using FT = FormTraits<D, FORM>;
-  using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
-  constexpr int N = FT::N, NN = FT::NN, NV = FT::NV;
-  constexpr int SST = stage_stride<NN>();
-  constexpr int NX = NV * D;
-  constexpr int SSX = NX | 1;
+template <int D, int FORM>
+struct BwdPlan {
+  static constexpr int NN = FormTraits<D, FORM>::NN;
+  static constexpr bool VEC = (NN % 4 == 0);
+  static constexpr int DST = VEC ? NN + 4 : (NN | 1);  // dA row stride in the stage
+  static constexpr int NV = D + 1;
+  static constexpr int NS = kTileElems * NV;  // slots per CTA tile
+  static constexpr int WARPS = kTileElems / 32;
+  static constexpr size_t da_bytes = align_up(size_t(2) * 32 * DST * 4, 128);  // per warp
+  static constexpr size_t xs_bytes = align_up(size_t(NS) * D * 4, 128);         // per CTA
+  static constexpr size_t sorted_bytes = align_up(size_t(2) * NS * 2, 128);     // per CTA
+  static constexpr size_t smem = WARPS * da_bytes + xs_bytes + sorted_bytes;
+};
+
+// Asynchronous copy of a tile's contiguous dA into the padded stage slot.
+template <int D, int FORM>
+__device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, int lane, float* dslot) {
+  using PL = BwdPlan<D, FORM>;
+  constexpr int NN = PL::NN;
   const int64_t e0 = tile * 32;
+  if (e0 >= p.n_elem) return;
   const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
-  // 1. stage the tile's upstream dA (contiguous cnt * NN floats)
-  {
-    const float* src = p.dA + e0 * NN;
-    bool done = false;
-    if constexpr (NN % 4 == 0) {
-      if (p.vec_dA) {
-        const int nq = cnt * (NN / 4);
-        for (int q = lane; q < nq; q += 32) {
-          float4 v = __ldcs(reinterpret_cast<const float4*>(src) + q);
-          const int idx = 4 * q;
-          const int el = idx / NN;
-          float* d = st + el * SST + (idx - el * NN);
-          d[0] = v.x;
-          d[1] = v.y;
-          d[2] = v.z;
-          d[3] = v.w;
-        }
-        done = true;
+  const float* src = p.dA + e0 * NN;
+  if constexpr (PL::VEC) {
+    if (p.vec_dA) {
+      constexpr int Q = NN / 4;
+      const int nq = cnt * Q;
+      for (int q = lane; q < nq; q += 32) {
+        const int el = q / Q;
+        cp_async<16>(dslot + el * PL::DST + 4 * (q - el * Q), src + 4 * q);
       }
-    }
-    if (!done) {
-      const int nw = cnt * NN;
-      for (int idx = lane; idx < nw; idx += 32) {
-        const int el = idx / NN;
-        st[el * SST + (idx - el * NN)] = __ldcs(src + idx);
-      }
+      return;
     }
   }
-  __syncwarp();
-  const int64_t e = e0 + lane;
+  const int nw = cnt * NN;
+  for (int idx = lane; idx < nw; idx += 32) {
+    const int el = idx / NN;
+    cp_async<4>(dslot + el * PL::DST + (idx - el * NN), src + idx);
+  }
+}
+
+// Asynchronous copy of tile `tile`'s sorted slot list (NS u16) by the CTA.
+template <int NS>
+__device__ __forceinline__ void copy_sorted(const uint16_t* sorted, int64_t tile, int tid, uint16_t* dst) {
+  static_assert((NS * 2) % 16 == 0, "sorted slot list in 16-byte chunks");
+  constexpr int NCH = NS * 2 / 16;
+  const uint16_t* src = sorted + tile * NS;
+  for (int c = tid; c < NCH; c += kTileElems) cp_async<16>(dst + 8 * c, src + 8 * c);
+}
+
+// Stage 3 of the adjoint for one element per lane.
+template <int D, int FORM, int JAC, bool ATOMIC>
+__device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags, float w,
+                                                const float (&X)[D + 1][D], const float* drow,
+                                                const int (&vc)[D + 1], float* xs_row) {
+  using FT = FormTraits<D, FORM>;
+  using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
+  constexpr int N = FT::N, NV = FT::NV;
+  const int64_t e = tile * 32 + lane;
   int err = 0;
   float xb[NV][D];
 #pragma unroll
@@ -109,204 +136,257 @@ __device__ __forceinline__ int bwd_warp_tile(const BwdParams& p, int64_t tile, i
 #pragma unroll
     for (int a = 0; a < D; ++a) xb[k][a] = 0.f;
   float dcoef = 0.f;
-  int v[D + 1];
   bool ok = false;
-  if (e < p.n_elem) {
-    float X[D + 1][D];
-    load_conn<D>(p.conn, e, p.vec_conn, v);
-    if (!gather<D>(p.coords, p.n_vert, v, X)) {
-      err |= DEVERR_CONN;
+  if (flags & GF_OK) {
+    Jac<D, GT> jac;
+    if (!jacobian<D, JAC>(X, jac)) {
+      err |= DEVERR_DEGENERATE;
     } else {
-      Jac<D, GT> jac;
-      if (!jacobian<D, JAC>(X, jac)) {
-        err |= DEVERR_DEGENERATE;
-      } else {
-        ok = true;
-        float adj[D][D], ed[D][D];
+      ok = true;
+      float adj[D][D], ed[D][D];
 #pragma unroll
-        for (int mu = 0; mu < D; ++mu)
-#pragma unroll
-          for (int a = 0; a < D; ++a) {
-            adj[mu][a] = float(jac.adj[mu][a]);
-            ed[mu][a] = float(jac.e[mu][a]);
-          }
-        const float det = float(jac.det);
-        const float scale0 = 1.f / (dev_abs(det) * float(FT::DEN));
-        float G0[FT::NG];
-        geometric_tensor<D, FORM>(adj, scale0, G0);
-        // 1. dG = transpose of the contraction applied to sym(dA)
-        SymVals<FT::NT> sym;
-        load_sym<N>(st + lane * SST, sym.s, std::make_integer_sequence<int, FT::NT>{});
-        float dG[FT::NG];
-        contract_adjoint<D, FORM>(sym, dG);
-        // 2. coefficient gradient
-#pragma unroll
-        for (int g = 0; g < FT::NG; ++g) dcoef = fmaf(dG[g], G0[g], dcoef);
-        const float w = p.coef ? __ldg(p.coef + e) : 1.f;
-        const float L = w * dcoef;
-        const float c2 = 2.f * w * scale0;
-        // 3. adjoint of G with respect to adj(J)
-        float adjb[D][D];
-        if constexpr (FORM != ELASTIC_P1) {
-#pragma unroll
-          for (int r = 0; r < D; ++r)
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-              float acc = 0.f;
-#pragma unroll
-              for (int nu = 0; nu < D; ++nu) {
-                const float Srn = (r == nu) ? dG[pair_index(r, nu, D)]
-                                            : 0.5f * dG[pair_index(r < nu ? r : nu, r < nu ? nu : r, D)];
-                acc = fmaf(Srn, adj[nu][a], acc);
-              }
-              adjb[r][a] = c2 * acc;
-            }
-        } else {
-          constexpr int NP = FT::NP;
-#pragma unroll
-          for (int pp = 0; pp < NP; ++pp) {
-            float acc = 0.f;
-#pragma unroll
-            for (int q = 0; q < NP; ++q) {
-              const float Spq = (pp == q) ? dG[pair_index(pp, q, NP)]
-                                          : 0.5f * dG[pair_index(pp < q ? pp : q, pp < q ? q : pp, NP)];
-              acc = fmaf(Spq, adj[q / D][q % D], acc);
-            }
-            adjb[pp / D][pp % D] = c2 * acc;
-          }
-        }
-        // 4. |det J| term and 5. adjugate pulled back to the edge vectors
-        float eb[D][D];
-        const float Ld = -L / det;
-#pragma unroll
-        for (int mu = 0; mu < D; ++mu)
-#pragma unroll
-          for (int a = 0; a < D; ++a) eb[mu][a] = Ld * adj[mu][a];
-        if constexpr (D == 3) {
-#pragma unroll
-          for (int mu = 0; mu < 3; ++mu) {
-            const int i1 = (mu + 1) % 3, i2 = (mu + 2) % 3;
-            const float* a = ed[i1];
-            const float* b = ed[i2];
-            const float* cb = adjb[mu];
-            // d a += b x cb ; d b += cb x a
-            eb[i1][0] += b[1] * cb[2] - b[2] * cb[1];
-            eb[i1][1] += b[2] * cb[0] - b[0] * cb[2];
-            eb[i1][2] += b[0] * cb[1] - b[1] * cb[0];
-            eb[i2][0] += cb[1] * a[2] - cb[2] * a[1];
-            eb[i2][1] += cb[2] * a[0] - cb[0] * a[2];
-            eb[i2][2] += cb[0] * a[1] - cb[1] * a[0];
-          }
-        } else {
-          eb[1][1] += adjb[0][0];
-          eb[1][0] -= adjb[0][1];
-          eb[0][1] -= adjb[1][0];
-          eb[0][0] += adjb[1][1];
-        }
+      for (int mu = 0; mu < D; ++mu)
 #pragma unroll
         for (int a = 0; a < D; ++a) {
-          float s = 0.f;
+          adj[mu][a] = float(jac.adj[mu][a]);
+          ed[mu][a] = float(jac.e[mu][a]);
+        }
+      const float det = float(jac.det);
+      const float scale0 = __frcp_rn(dev_abs(det) * float(FT::DEN));
+      float G0[FT::NG];
+      geometric_tensor<D, FORM>(adj, scale0, G0);
+      // 1. dG = transpose of the contraction applied to sym(dA)
+      SymVals<FT::NT> sym;
+      load_sym<N>(drow, sym.s, std::make_integer_sequence<int, FT::NT>{});
+      float dG[FT::NG];
+      contract_adjoint<D, FORM>(sym, dG);
+      // 2. coefficient gradient
 #pragma unroll
-          for (int mu = 0; mu < D; ++mu) {
-            xb[mu + 1][a] = eb[mu][a];
-            s += eb[mu][a];
+      for (int g = 0; g < FT::NG; ++g) dcoef = fmaf(dG[g], G0[g], dcoef);
+      const float L = w * dcoef;
+      const float c2 = 2.f * w * scale0;
+      // 3. adjoint of G with respect to adj(J)
+      float adjb[D][D];
+      if constexpr (FORM != ELASTIC_P1) {
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            float acc = 0.f;
+#pragma unroll
+            for (int nu = 0; nu < D; ++nu) {
+              const float Srn = (r == nu) ? dG[pair_index(r, nu, D)]
+                                          : 0.5f * dG[pair_index(r < nu ? r : nu, r < nu ? nu : r, D)];
+              acc = fmaf(Srn, adj[nu][a], acc);
+            }
+            adjb[r][a] = c2 * acc;
           }
-          xb[0][a] = -s;
+      } else {
+        constexpr int NP = FT::NP;
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+          float acc = 0.f;
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const float Spq = (pp == q) ? dG[pair_index(pp, q, NP)]
+                                        : 0.5f * dG[pair_index(pp < q ? pp : q, pp < q ? q : pp, NP)];
+            acc = fmaf(Spq, adj[q / D][q % D], acc);
+          }
+          adjb[pp / D][pp % D] = c2 * acc;
         }
       }
+      // 4. |det J| term and 5. adjugate pulled back to the edge vectors
+      float eb[D][D];
+      const float Ld = -__fdividef(L, det);
+#pragma unroll
+      for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+        for (int a = 0; a < D; ++a) eb[mu][a] = Ld * adj[mu][a];
+      if constexpr (D == 3) {
+#pragma unroll
+        for (int mu = 0; mu < 3; ++mu) {
+          const int i1 = (mu + 1) % 3, i2 = (mu + 2) % 3;
+          const float* a = ed[i1];
+          const float* b = ed[i2];
+          const float* cb = adjb[mu];
+          // d a += b x cb ; d b += cb x a
+          eb[i1][0] += b[1] * cb[2] - b[2] * cb[1];
+          eb[i1][1] += b[2] * cb[0] - b[0] * cb[2];
+          eb[i1][2] += b[0] * cb[1] - b[1] * cb[0];
+          eb[i2][0] += cb[1] * a[2] - cb[2] * a[1];
+          eb[i2][1] += cb[2] * a[0] - cb[0] * a[2];
+          eb[i2][2] += cb[0] * a[1] - cb[1] * a[0];
+        }
+      } else {
+        eb[1][1] += adjb[0][0];
+        eb[1][0] -= adjb[0][1];
+        eb[0][1] -= adjb[1][0];
+        eb[0][0] += adjb[1][1];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        float s = 0.f;
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu) {
+          xb[mu + 1][a] = eb[mu][a];
+          s += eb[mu][a];
+        }
+        xb[0][a] = -s;
+      }
     }
-    if (p.dcoef) __stcs(p.dcoef + e, dcoef);
+  } else if (flags & GF_ELEM) {
+    err |= DEVERR_CONN;
   }
-  if constexpr (ATOMIC) {
-    if (ok) {
+  if (flags & GF_ELEM) {
+    if (p.dcoef) __stcs(p.dcoef + e, dcoef);
+    if constexpr (ATOMIC) {
+      if (ok) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k)
+        for (int k = 0; k < NV; ++k)
 #pragma unroll
-        for (int a = 0; a < D; ++a) atomicAdd(p.dcoords + int64_t(v[k]) * D + a, xb[k][a]);
+          for (int a = 0; a < D; ++a) atomicAdd(p.dcoords + int64_t(vc[k]) * D + a, xb[k][a]);
+      }
     }
-    __syncwarp();
-  } else if (p.xbar) {
-    __syncwarp();  // every lane has read its dA row: reuse the stage for xbar
-    float* row = st + lane * SSX;
+  }
+  if constexpr (!ATOMIC) {
+    if (xs_row) {  // the element's slot contributions (zeros when it is skipped)
+      if constexpr ((NV * D) % 4 == 0) {
 #pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-      for (int a = 0; a < D; ++a) row[k * D + a] = xb[k][a];
-    __syncwarp();
-    float* dst = p.xbar + e0 * NX;
-    bool done = false;
-    if constexpr (NX % 4 == 0) {
-      if (p.vec_xbar) {
-        const int nq = cnt * (NX / 4);
-        for (int q = lane; q < nq; q += 32) {
-          const int idx = 4 * q;
-          const int el = idx / NX;
-          const float* s = st + el * SSX + (idx - el * NX);
-          reinterpret_cast<float4*>(dst)[q] = make_float4(s[0], s[1], s[2], s[3]);
+        for (int q = 0; q < NV * D / 4; ++q) {
+          float4 v;
+          v.x = xb[(4 * q) / D][(4 * q) % D];
+          v.y = xb[(4 * q + 1) / D][(4 * q + 1) % D];
+          v.z = xb[(4 * q + 2) / D][(4 * q + 2) % D];
+          v.w = xb[(4 * q + 3) / D][(4 * q + 3) % D];
+          reinterpret_cast<float4*>(xs_row)[q] = v;
         }
-        done = true;
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k)
+#pragma unroll
+          for (int a = 0; a < D; ++a) xs_row[k * D + a] = xb[k][a];
       }
     }
-    if (!done) {
-      const int nw = cnt * NX;
-      for (int idx = lane; idx < nw; idx += 32) {
-        const int el = idx / NX;
-        dst[idx] = st[el * SSX + (idx - el * NX)];
-      }
-    }
-    __syncwarp();
   }
   return err;
 }
 
 template <int D, int FORM, int JAC, bool ATOMIC>
-__global__ void __launch_bounds__(512) fem_bwd_elem_kernel(BwdParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  using FT = FormTraits<D, FORM>;
-  constexpr int SST = stage_stride<FT::NN>() > ((FT::NV * D) | 1) ? stage_stride<FT::NN>()
-                                                                   : ((FT::NV * D) | 1);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  float* st = reinterpret_cast<float*>(smem_raw) + warp * 32 * SST;
-  const int64_t ntiles = (p.n_elem + 31) / 32;
+__global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
+  using PL = BwdPlan<D, FORM>;
+  constexpr int W = PL::WARPS, NS = PL::NS, NV = PL::NV;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* dslots = reinterpret_cast<float*>(smem_raw + size_t(warp) * PL::da_bytes);  // [2][32][DST]
+  float* xs = reinterpret_cast<float*>(smem_raw + W * PL::da_bytes);                 // [NS][D]
+  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem_raw + W * PL::da_bytes + PL::xs_bytes);  // [2][NS]
+  const bool rec = !ATOMIC && p.tile_rec != nullptr;
+  const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
+  const int64_t G = gridDim.x;
+  int64_t T = blockIdx.x;
+  if (T >= nct) return;  // CTA-uniform
   int err = 0;
-  for (int64_t t = int64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += int64_t(gridDim.x) * nwarps)
-    err |= bwd_warp_tile<D, FORM, JAC, ATOMIC>(p, t, lane, st);
+  int v1[D + 1], v2[D + 1], vc[D + 1];
+  float Xc[D + 1][D], Xn[D + 1][D];
+  int64_t t = T * W + warp;  // this warp's 32-element sub-tile
+  load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
+  int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
+  copy_dA_async<D, FORM>(p, t, lane, dslots);
+  if (rec) copy_sorted<NS>(p.sorted, T, tid, sbuf);
+  float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  int32_t rb = 0, rn = 0;  // first record and record count of tile T
+  if (rec) {
+    rb = __ldg(p.tile_rec + T);
+    rn = __ldg(p.tile_rec + T + 1) - rb;
+  }
+  cp_async_commit();
+#pragma unroll
+  for (int k = 0; k <= D; ++k) vc[k] = v1[k];
+  load_conn<D>(p.conn, (t + W * G) * 32 + lane, p.n_elem, p.vec_conn, v1);
+  for (int i = 0; T < nct; ++i, T += G, t += W * G) {
+    const int64_t tn = t + W * G, en = tn * 32 + lane;
+    const int sn = (i + 1) & 1, sc = i & 1;
+    load_conn<D>(p.conn, (tn + W * G) * 32 + lane, p.n_elem, p.vec_conn, v2);
+    const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
+    copy_dA_async<D, FORM>(p, tn, lane, dslots + sn * 32 * PL::DST);
+    const bool has_next = T + G < nct;
+    if (rec && has_next) copy_sorted<NS>(p.sorted, T + G, tid, sbuf + sn * NS);
+    const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+    int32_t rbn = 0, rnn = 0;
+    if (rec && has_next) {
+      rbn = __ldg(p.tile_rec + T + G);
+      rnn = __ldg(p.tile_rec + T + G + 1) - rbn;
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncwarp();  // dA rows were copied by other lanes
+    err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslots + (sc * 32 + lane) * PL::DST,
+                                                  vc, rec ? xs + size_t(warp * 32 + lane) * NV * D : nullptr);
+    if (rec) {
+      __syncthreads();  // every warp's contributions and the sorted list are in shared memory
+      const uint16_t* srt = sbuf + sc * NS;
+      for (int r = tid; r < rn; r += kTileElems) {
+        const int beg = r == 0 ? 0 : int(__ldg(p.rec_end + rb + r - 1));
+        const int end = int(__ldg(p.rec_end + rb + r));
+        float acc[D];
+#pragma unroll
+        for (int a = 0; a < D; ++a) acc[a] = 0.f;
+        for (int j = beg; j < end; ++j) {
+          const float* x = xs + int(srt[j]) * D;
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc[a] += x[a];
+        }
+        float* dst = p.records + int64_t(rb + r) * D;
+#pragma unroll
+        for (int a = 0; a < D; ++a) dst[a] = acc[a];
+      }
+      __syncthreads();  // xs and the sorted slot buffer are refilled next
+    } else {
+      __syncwarp();  // the dA slot is refilled two tiles later
+    }
+    fcur = fnext;
+    wcur = wnext;
+    rb = rbn;
+    rn = rnn;
+#pragma unroll
+    for (int k = 0; k <= D; ++k) {
+      vc[k] = v1[k];
+      v1[k] = v2[k];
+#pragma unroll
+      for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+    }
+  }
+  cp_async_wait<0>();
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
 }
 
 template <int D, int FORM, int JAC, bool ATOMIC>
 static cudaError_t launch_bwd_t(const BwdLaunch& L) {
-  using FT = FormTraits<D, FORM>;
-  constexpr int SST = stage_stride<FT::NN>() > ((FT::NV * D) | 1) ? stage_stride<FT::NN>()
-                                                                   : ((FT::NV * D) | 1);
+  using PL = BwdPlan<D, FORM>;
   BwdParams p;
   p.conn = L.conn;
   p.coords = L.coords;
   p.coef = L.coef;
   p.dA = L.dA;
+  p.tile_rec = ATOMIC ? nullptr : L.tile_rec;
+  p.sorted = L.sorted;
+  p.rec_end = L.rec_end;
+  p.records = L.records;
   p.dcoef = L.dcoef;
-  p.xbar = L.xbar;
   p.dcoords = L.dcoords;
   p.n_elem = L.n_elem;
   p.n_vert = L.n_vert;
   p.dev_err = L.dev_err;
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_dA = reinterpret_cast<uintptr_t>(L.dA) % 16 == 0;
-  p.vec_xbar = reinterpret_cast<uintptr_t>(L.xbar) % 16 == 0;
   auto kern = fem_bwd_elem_kernel<D, FORM, JAC, ATOMIC>;
-  const int warps = clamp_warps(L.warps, size_t(32) * SST * sizeof(float));
-  const size_t smem = size_t(warps) * 32 * SST * sizeof(float);
+  const size_t smem = PL::smem;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
-  const int64_t ntiles = (L.n_elem + 31) / 32;
-  int64_t grid = (ntiles + warps - 1) / warps;
-  if (L.ctas_per_sm > 0) {
-    int64_t cap = int64_t(L.ctas_per_sm) * device_sm_count();
-    if (grid > cap) grid = cap;
-  }
-  if (grid < 1) grid = 1;
-  kern<<<unsigned(grid), warps * 32, smem, L.stream>>>(p);
+  const unsigned grid =
+      pipeline_grid(reinterpret_cast<const void*>(kern), PL::WARPS, smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, kTileElems, smem, L.stream>>>(p);
   return cudaGetLastError();
 }
 

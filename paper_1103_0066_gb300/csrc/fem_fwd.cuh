@@ -2,20 +2,23 @@
 //
 // Work decomposition (GB300 design, not the paper's GTX285 thread-per-entry
 // mapping): a warp owns a tile of 32 consecutive elements, one element per
-// lane.  Each lane gathers its connectivity (one 16-byte load for a tet) and
-// vertex coordinates (L2-resident), builds the Jacobian, the geometric tensor
-// and the sparse contraction with K as immediates, and writes its element
-// matrix into a per-warp shared-memory stage (odd row stride: conflict-free).
-// The warp then streams the tile's 32 * n^2 contiguous outputs to HBM with
-// coalesced 16-byte evict-first stores -- the paper's "fully coalesced write"
-// of element matrices (Sec. 4.3), done for a whole warp tile at once.  Warps
-// walk the tile space grid-stride; the grid is sized from the SM count.
-// Every element is integrated: the final tile is partial (no dropped tail).
+// lane, and walks its tiles grid-stride as a three-stage software pipeline:
+//   stage 1 (tile t+2): connectivity loaded into registers (one 16-byte load per tet)
+//   stage 2 (tile t+1): vertex coordinates gathered into registers (L2-resident)
+//   stage 3 (tile t)  : Jacobian, geometric tensor, sparse G:K contraction with
+//                       K as immediates, staging and coalesced 16-byte
+//                       evict-first stores of the tile's 32 * n^2 contiguous outputs
+// so the gather latency hides behind the previous tile's arithmetic.  For the
+// 4x4 element matrices the stage uses an XOR swizzle of the 16-byte row
+// chunks, which keeps both the row writes and the coalesced read-out free of
+// shared-memory bank conflicts; other shapes use an odd row stride.  Every
+// element is integrated: the final tile is partial (no dropped tail).
 #pragma once
 #include <cuda_runtime.h>
 
 #include "fem_core.cuh"
 #include "fem_internal.h"
+#include "fem_pipe.cuh"
 
 namespace fem {
 
@@ -29,13 +32,24 @@ struct FwdParams {
   int64_t n_vert;
   int32_t* dev_err;
   int vec_conn;   // conn rows are 16-byte aligned int4 (tets)
-  int vec_store;  // A is 16-byte aligned and n^2 % 4 == 0
+  int vec_store;  // A is 16-byte aligned
 };
 
 template <int NN>
 constexpr int stage_stride() {
   return NN | 1;
 }
+constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Shared-memory plan of one warp.
+template <int D, int FORM, class CT, class OT>
+struct FwdPlan {
+  static constexpr int NN = FormTraits<D, FORM>::NN;
+  static constexpr bool SWZ16 = (NN == 16 && sizeof(OT) == 4);  // swizzled float4 rows
+  static constexpr int SST = SWZ16 ? 16 : stage_stride<NN>();
+  static constexpr size_t stage_bytes = align_up(size_t(32) * SST * sizeof(OT), 128);
+  static constexpr size_t per_warp = stage_bytes;
+};
 
 template <int N, int SST, class OT>
 struct StageSink {
@@ -47,8 +61,25 @@ struct StageSink {
   }
 };
 
+template <int N, class T>
+struct RegSink {
+  T a[N * N];
+  template <int I, int J>
+  __device__ __forceinline__ void put(T v) {
+    a[I * N + J] = v;
+    if constexpr (I != J) a[J * N + I] = v;
+  }
+};
+
+// Connectivity of element e into registers (-1 marks "no element").
 template <int D>
-__device__ __forceinline__ void load_conn(const int32_t* conn, int64_t e, int vec, int (&v)[D + 1]) {
+__device__ __forceinline__ void load_conn(const int32_t* conn, int64_t e, int64_t n_elem, int vec,
+                                          int (&v)[D + 1]) {
+  if (e >= n_elem) {
+#pragma unroll
+    for (int k = 0; k <= D; ++k) v[k] = -1;
+    return;
+  }
   if constexpr (D == 3) {
     if (vec) {
       int4 c = __ldcs(reinterpret_cast<const int4*>(conn) + e);
@@ -63,6 +94,7 @@ __device__ __forceinline__ void load_conn(const int32_t* conn, int64_t e, int ve
   for (int k = 0; k <= D; ++k) v[k] = __ldcs(conn + e * (D + 1) + k);
 }
 
+// Synchronous gather (used by the geometry hook): false when a vertex id is out of range.
 template <int D, class CT>
 __device__ __forceinline__ bool gather(const CT* coords, int64_t n_vert, const int (&v)[D + 1],
                                        CT (&X)[D + 1][D]) {
@@ -77,63 +109,116 @@ __device__ __forceinline__ bool gather(const CT* coords, int64_t n_vert, const i
   return true;
 }
 
-// One warp tile: returns the device error bits of its elements.
+// Gather flags carried from stage 2 to stage 3.
+enum : int { GF_ELEM = 1, GF_OK = 2 };
+
+// Stage 2: validates the element's vertex ids and issues the loads of its
+// (d+1) x d coordinates into registers (consumed one pipeline step later).
+template <int D, class CT>
+__device__ __forceinline__ int gather_regs(const CT* coords, int64_t n_vert, int64_t e, int64_t n_elem,
+                                           const int (&v)[D + 1], CT (&X)[D + 1][D]) {
+  if (e >= n_elem) return 0;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k <= D; ++k) ok &= (v[k] >= 0) & (int64_t(v[k]) < n_vert);
+  if (!ok) return GF_ELEM;
+#pragma unroll
+  for (int k = 0; k <= D; ++k)
+#pragma unroll
+    for (int a = 0; a < D; ++a) X[k][a] = __ldg(coords + int64_t(v[k]) * D + a);
+  return GF_ELEM | GF_OK;
+}
+
+// Stage 3 for one tile: geometry, contraction, staging and the coalesced store.
 template <int D, int FORM, int JAC, class CT, class OT>
-__device__ __forceinline__ int fwd_warp_tile(const FwdParams<CT, OT>& p, int64_t tile, int lane,
-                                             OT* st) {
+__device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int64_t tile, int lane, int flags,
+                                                float w, const CT (&X)[D + 1][D], OT* st) {
   using FT = FormTraits<D, FORM>;
+  using PL = FwdPlan<D, FORM, CT, OT>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
   constexpr int NN = FT::NN;
-  constexpr int SST = stage_stride<NN>();
-  const int64_t e = tile * 32 + lane;
+  constexpr int SST = PL::SST;
   int err = 0;
   OT Gf[FT::NG];
 #pragma unroll
   for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(0);
-  if (e < p.n_elem) {
-    int v[D + 1];
-    CT X[D + 1][D];
-    load_conn<D>(p.conn, e, p.vec_conn, v);
-    if (!gather<D>(p.coords, p.n_vert, v, X)) {
-      err |= DEVERR_CONN;
+  if (flags & GF_OK) {
+    Jac<D, GT> jac;
+    if (!jacobian<D, JAC>(X, jac)) {
+      err |= DEVERR_DEGENERATE;
     } else {
-      Jac<D, GT> jac;
-      if (!jacobian<D, JAC>(X, jac)) {
-        err |= DEVERR_DEGENERATE;
-      } else {
-        GT w = p.coef ? GT(__ldg(p.coef + e)) : GT(1);
-        GT scale = w / (dev_abs(jac.det) * GT(FT::DEN));
-        GT Gt[FT::NG];
-        geometric_tensor<D, FORM>(jac.adj, scale, Gt);
+      GT scale;
+      if constexpr (sizeof(GT) == 4)
+        scale = __fdividef(w, dev_abs(jac.det) * float(FT::DEN));
+      else
+        scale = GT(w) / (dev_abs(jac.det) * GT(FT::DEN));
+      GT Gt[FT::NG];
+      geometric_tensor<D, FORM>(jac.adj, scale, Gt);
 #pragma unroll
-        for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(Gt[g]);
-      }
+      for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(Gt[g]);
     }
+  } else if (flags & GF_ELEM) {
+    err |= DEVERR_CONN;
   }
-  StageSink<FT::N, SST, OT> sink{st + lane * SST};
-  contract<D, FORM>(Gf, sink);
-  __syncwarp();
   const int64_t e0 = tile * 32;
   const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
   OT* dst = p.A + e0 * NN;
-  bool done = false;
-  if constexpr (sizeof(OT) == 4 && NN % 4 == 0) {
+  if constexpr (PL::SWZ16) {
+    // rows as float4 chunks, chunk index XOR-swizzled with (lane >> 1) & 3
+    RegSink<4, float> rs;
+    contract<D, FORM>(Gf, rs);
+    const int sw = (lane >> 1) & 3;
+    float* row = st + lane * 16;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      *reinterpret_cast<float4*>(row + 4 * (r ^ sw)) =
+          make_float4(rs.a[4 * r], rs.a[4 * r + 1], rs.a[4 * r + 2], rs.a[4 * r + 3]);
+    __syncwarp();
+    // chunk c = lane + 32 r holds element (lane >> 2) + 8 r, row lane & 3
+    const float* src = st + 16 * (lane >> 2) + 4 * ((lane & 3) ^ ((lane >> 3) & 3));
     if (p.vec_store) {
-      const int nq = cnt * (NN / 4);
-      for (int q = lane; q < nq; q += 32) {
-        const int idx = 4 * q;
-        const int el = idx / NN;
-        const OT* s = st + el * SST + (idx - el * NN);
-        __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(s[0], s[1], s[2], s[3]));
+      float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int c = lane + 32 * r;
+        if (c < 4 * cnt) __stcs(d4 + c, *reinterpret_cast<const float4*>(src + 128 * r));
       }
-      done = true;
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int c = lane + 32 * r;
+        if (c < 4 * cnt) {
+          const float4 v = *reinterpret_cast<const float4*>(src + 128 * r);
+          __stcs(dst + 4 * c, v.x);
+          __stcs(dst + 4 * c + 1, v.y);
+          __stcs(dst + 4 * c + 2, v.z);
+          __stcs(dst + 4 * c + 3, v.w);
+        }
+      }
     }
-  }
-  if (!done) {
-    const int nw = cnt * NN;
-    for (int idx = lane; idx < nw; idx += 32) {
-      const int el = idx / NN;
-      __stcs(dst + idx, st[el * SST + (idx - el * NN)]);
+  } else {
+    StageSink<FT::N, SST, OT> sink{st + lane * SST};
+    contract<D, FORM>(Gf, sink);
+    __syncwarp();
+    bool done = false;
+    if constexpr (sizeof(OT) == 4 && NN % 4 == 0) {
+      if (p.vec_store) {
+        const int nq = cnt * (NN / 4);
+        for (int q = lane; q < nq; q += 32) {
+          const int idx = 4 * q;
+          const int el = idx / NN;
+          const OT* s = st + el * SST + (idx - el * NN);
+          __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(s[0], s[1], s[2], s[3]));
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+      const int nw = cnt * NN;
+      for (int idx = lane; idx < nw; idx += 32) {
+        const int el = idx / NN;
+        __stcs(dst + idx, st[el * SST + (idx - el * NN)]);
+      }
     }
   }
   __syncwarp();
@@ -142,21 +227,44 @@ __device__ __forceinline__ int fwd_warp_tile(const FwdParams<CT, OT>& p, int64_t
 
 template <int D, int FORM, int JAC, class CT, class OT>
 __global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr int SST = stage_stride<FormTraits<D, FORM>::NN>();
+  using PL = FwdPlan<D, FORM, CT, OT>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  OT* st = reinterpret_cast<OT*>(smem_raw) + warp * 32 * SST;
+  OT* st = reinterpret_cast<OT*>(smem_raw + size_t(warp) * PL::per_warp);
   const int64_t ntiles = (p.n_elem + 31) / 32;
+  const int64_t stride = int64_t(gridDim.x) * nwarps;
+  int64_t t = int64_t(blockIdx.x) * nwarps + warp;
+  if (t >= ntiles) return;  // warp-uniform
   int err = 0;
-  for (int64_t t = int64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += int64_t(gridDim.x) * nwarps)
-    err |= fwd_warp_tile<D, FORM, JAC>(p, t, lane, st);
+  int v1[D + 1], v2[D + 1];
+  CT Xc[D + 1][D], Xn[D + 1][D];
+  // prologue: tile t gathered, tile t + stride connectivity in flight
+  load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
+  int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
+  float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  load_conn<D>(p.conn, (t + stride) * 32 + lane, p.n_elem, p.vec_conn, v1);
+  for (; t < ntiles; t += stride) {
+    const int64_t en = (t + stride) * 32 + lane;
+    load_conn<D>(p.conn, (t + 2 * stride) * 32 + lane, p.n_elem, p.vec_conn, v2);
+    const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
+    const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+    err |= fwd_compute_tile<D, FORM, JAC, CT, OT>(p, t, lane, fcur, wcur, Xc, st);
+    fcur = fnext;
+    wcur = wnext;
+#pragma unroll
+    for (int k = 0; k <= D; ++k) {
+      v1[k] = v2[k];
+#pragma unroll
+      for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+    }
+  }
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
 }
 
 template <int D, int FORM, int JAC, class CT, class OT>
 cudaError_t launch_fwd_t(const FwdLaunch& L) {
-  using FT = FormTraits<D, FORM>;
+  using PL = FwdPlan<D, FORM, CT, OT>;
   FwdParams<CT, OT> p;
   p.conn = L.conn;
   p.coords = static_cast<const CT*>(L.coords);
@@ -168,18 +276,12 @@ cudaError_t launch_fwd_t(const FwdLaunch& L) {
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_store = (reinterpret_cast<uintptr_t>(L.A) % 16 == 0);
   auto kern = fem_fwd_kernel<D, FORM, JAC, CT, OT>;
-  const int warps = clamp_warps(L.warps, size_t(32) * stage_stride<FT::NN>() * sizeof(OT));
-  const size_t smem = size_t(warps) * 32 * stage_stride<FT::NN>() * sizeof(OT);
+  const int warps = clamp_warps(L.warps, PL::per_warp);
+  const size_t smem = size_t(warps) * PL::per_warp;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
-  const int64_t ntiles = (L.n_elem + 31) / 32;
-  int64_t grid = (ntiles + warps - 1) / warps;
-  if (L.ctas_per_sm > 0) {
-    int64_t cap = int64_t(L.ctas_per_sm) * device_sm_count();
-    if (grid > cap) grid = cap;
-  }
-  if (grid < 1) grid = 1;
-  kern<<<unsigned(grid), warps * 32, smem, L.stream>>>(p);
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), warps, smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, warps * 32, smem, L.stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ __global__ void fem_geometry_kernel(const int32_t* conn, const CT* coords, const
     float g[NGL];
 #pragma unroll
     for (int k = 0; k < NGL; ++k) g[k] = 0.f;
-    load_conn<D>(conn, e, 0, v);
+    load_conn<D>(conn, e, n_elem, 0, v);
     if (!gather<D>(coords, n_vert, v, X)) {
       err |= DEVERR_CONN;
     } else {
@@ -111,6 +111,22 @@ int device_sm_count() {
     g_sm_count[dev] = n;
   }
   return g_sm_count[dev];
+}
+
+unsigned pipeline_grid(const void* kernel, int warps, size_t smem, int64_t n_elem, int ctas_per_sm) {
+  int per_sm = ctas_per_sm;
+  if (per_sm <= 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, warps * 32, smem) != cudaSuccess ||
+        per_sm <= 0) {
+      cudaGetLastError();
+      per_sm = 1;
+    }
+  }
+  const int64_t ntiles = (n_elem + 31) / 32;
+  int64_t grid = int64_t(per_sm) * device_sm_count();
+  const int64_t need = (ntiles + warps - 1) / warps;
+  if (grid > need) grid = need;
+  return unsigned(grid < 1 ? 1 : grid);
 }
 
 cudaError_t ensure_smem(const void* kernel, size_t bytes) {

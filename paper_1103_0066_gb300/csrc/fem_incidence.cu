@@ -1,13 +1,23 @@
-// fem_incidence.cu -- vertex -> (element, local vertex) incidence CSR and the
-// deterministic segmented reduction of the adjoint's per-element vertex
-// contributions into dcoords.
+// fem_incidence.cu -- the deterministic vertex reduction of the adjoint:
+// tile records, their vertex CSR, and the segmented sum into dcoords.
 //
-// The CSR lists, for every vertex v, the slots s = e*(d+1) + k with
-// conn[e][k] == v, sorted by s (i.e. by element, then local vertex).  The
-// reduction adds scratch[s][0..d) over each segment in that order, so the
-// result is bitwise reproducible run to run.  Built once per connectivity:
-// count (atomics) -> exclusive scan -> fill (atomics) -> per-segment sort.
+// The adjoint's element pass works on CTA tiles of kTileElems consecutive
+// elements.  Within a tile the (d+1) vertex contributions of every element
+// ("slots") that share a vertex are first summed in shared memory into one
+// RECORD, in increasing slot order; a structured mesh in cell-major order has
+// several times fewer records than slots, so only the records go to HBM.  The
+// records of each vertex are then summed in increasing record order (= tile
+// order).  Both orders are fixed by the mesh, so dcoords is bitwise
+// reproducible.
+//
+// Built once per connectivity (fem_incidence_build):
+//   per tile : bitonic sort of (vertex, slot) keys -> sorted slot list, record
+//              count; exclusive scan of the counts -> first record of each tile;
+//              record ends (positions in the sorted list) and record vertices
+//   global   : vertex -> records CSR (count, scan, fill, per-segment sort)
 #include <cuda_runtime.h>
+
+#include <cstdint>
 
 #include "fem_internal.h"
 
@@ -17,9 +27,9 @@ namespace {
 
 constexpr int kScanBlock = 1024;
 
-__global__ void zero_i32(int32_t* p, int64_t n) {
+__global__ void fill_i32(int32_t* p, int64_t n, int32_t value) {
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
-    p[i] = 0;
+    p[i] = value;
 }
 
 __global__ void zero_f32(float* p, int64_t n) {
@@ -27,10 +37,10 @@ __global__ void zero_f32(float* p, int64_t n) {
     p[i] = 0.f;
 }
 
-__global__ void count_kernel(const int32_t* conn, int64_t n_slots, int64_t n_vert, int32_t* cnt) {
-  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < n_slots;
-       s += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t v = conn[s];
+// cnt[key[i]] += 1 for every valid key
+__global__ void count_kernel(const int32_t* keys, int64_t n, int64_t n_vert, int32_t* cnt) {
+  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t v = keys[s];
     if (v >= 0 && v < n_vert) atomicAdd(cnt + v, 1);
   }
 }
@@ -105,49 +115,167 @@ __global__ void scan_apply_kernel(const int32_t* cnt, int64_t n, const int32_t* 
   if (blockIdx.x == 0 && threadIdx.x == 0) offsets[n] = partials[nb];
 }
 
-__global__ void fill_kernel(const int32_t* conn, int64_t n_slots, int64_t n_vert, const int32_t* offsets,
-                            int32_t* cursor, int32_t* incidence) {
-  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < n_slots;
-       s += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t v = conn[s];
-    if (v >= 0 && v < n_vert) incidence[offsets[v] + atomicAdd(cursor + v, 1)] = int32_t(s);
+__global__ void fill_kernel(const int32_t* keys, int64_t n, int64_t n_vert, const int32_t* offsets,
+                            int32_t* cursor, int32_t* list) {
+  for (int64_t s = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; s < n; s += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t v = keys[s];
+    if (v >= 0 && v < n_vert) list[offsets[v] + atomicAdd(cursor + v, 1)] = int32_t(s);
   }
 }
 
-// Sorts each vertex's segment (insertion sort: segments hold a few tens of slots).
-__global__ void sort_segments_kernel(const int32_t* offsets, int64_t n_vert, int32_t* incidence) {
-  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
-       v += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t b = offsets[v], en = offsets[v + 1];
-    for (int32_t i = b + 1; i < en; ++i) {
-      const int32_t key = incidence[i];
-      int32_t j = i - 1;
-      while (j >= b && incidence[j] > key) {
-        incidence[j + 1] = incidence[j];
-        --j;
+// Sorts each segment of a CSR list in increasing order: one warp per segment,
+// each lane takes one entry and moves it to its rank (entries are distinct);
+// segments longer than a warp fall back to an insertion sort by lane 0.
+__global__ void sort_segments_kernel(const int32_t* offsets, int64_t n_seg, int32_t* list) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_seg; v += warps) {
+    const int32_t b = offsets[v], n = offsets[v + 1] - b;
+    if (n <= 32) {
+      const int32_t key = lane < n ? list[b + lane] : INT32_MAX;
+      int rank = 0;
+#pragma unroll
+      for (int j = 0; j < 32; ++j) rank += (__shfl_sync(0xffffffffu, key, j) < key) ? 1 : 0;
+      __syncwarp();
+      if (lane < n) list[b + rank] = key;
+    } else if (lane == 0) {
+      for (int32_t i = b + 1; i < b + n; ++i) {
+        const int32_t key = list[i];
+        int32_t j = i - 1;
+        while (j >= b && list[j] > key) {
+          list[j + 1] = list[j];
+          --j;
+        }
+        list[j + 1] = key;
       }
-      incidence[j + 1] = key;
     }
+    __syncwarp();
   }
 }
 
+// ---------------------------------------------------------------- tile records
+
+constexpr int kBuildThreads = 128;
+constexpr int kSortCap = 512;  // power of two >= kTileElems * 4 slots
+static_assert(kSortCap >= kTileElems * 4, "tile slot capacity");
+constexpr uint64_t kNoVertex = 0xFFFFFFFFull;
+
+// Loads the tile's (vertex << 16 | slot) keys (absent or invalid slots get the
+// largest vertex) and sorts them in shared memory (bitonic network).
+__device__ void tile_sorted_keys(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t tile,
+                                 uint64_t* key) {
+  const int ns = kTileElems * nv;
+  const int64_t s0 = tile * kTileElems * nv;
+  const int64_t smax = n_elem * nv;
+  for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) {
+    uint64_t vtx = kNoVertex;
+    if (i < ns && s0 + i < smax) {
+      const int32_t v = conn[s0 + i];
+      if (v >= 0 && v < n_vert) vtx = uint64_t(uint32_t(v));
+    }
+    key[i] = (vtx << 16) | uint64_t(i);
+  }
+  __syncthreads();
+  for (int k = 2; k <= kSortCap; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool up = (i & k) == 0;
+          const uint64_t a = key[i], b = key[ixj];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__device__ __forceinline__ bool is_head(const uint64_t* key, int i) {
+  const uint64_t v = key[i] >> 16;
+  return v != kNoVertex && (i == 0 || (key[i - 1] >> 16) != v);
+}
+
+// Pass 1: sorted slot list of each tile and its record count.
+__global__ void __launch_bounds__(kBuildThreads)
+    tile_sort_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
+                     uint16_t* sorted, int32_t* nrec) {
+  __shared__ uint64_t key[kSortCap];
+  __shared__ int32_t cnt;
+  const int ns = kTileElems * nv;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (threadIdx.x == 0) cnt = 0;
+    tile_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
+    int c = 0;
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      sorted[tile * ns + i] = uint16_t(key[i] & 0xFFFF);
+      c += is_head(key, i) ? 1 : 0;
+    }
+    atomicAdd(&cnt, c);
+    __syncthreads();
+    if (threadIdx.x == 0) nrec[tile] = cnt;
+    __syncthreads();
+  }
+}
+
+// Pass 2: record ends (positions in the tile's sorted list) and record vertices.
+__global__ void __launch_bounds__(kBuildThreads)
+    tile_records_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
+                        const int32_t* tile_rec, uint16_t* rec_end, int32_t* rec_vertex) {
+  __shared__ uint64_t key[kSortCap];
+  __shared__ int32_t head_scan[kSortCap];
+  constexpr int kPer = kSortCap / kBuildThreads;
+  const int ns = kTileElems * nv;
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    tile_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
+    for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) head_scan[i] = (i < ns && is_head(key, i)) ? 1 : 0;
+    __syncthreads();
+    // inclusive Hillis-Steele scan of the head flags
+    for (int off = 1; off < kSortCap; off <<= 1) {
+      int32_t vals[kPer];
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) {
+        const int i = threadIdx.x + q * kBuildThreads;
+        vals[q] = head_scan[i] + (i >= off ? head_scan[i - off] : 0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kPer; ++q) head_scan[threadIdx.x + q * kBuildThreads] = vals[q];
+      __syncthreads();
+    }
+    const int32_t base = tile_rec[tile];
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+      const uint64_t v = key[i] >> 16;
+      if (v == kNoVertex) continue;
+      const int32_t r = base + head_scan[i] - 1;
+      if (is_head(key, i)) rec_vertex[r] = int32_t(v);
+      const bool last = (i + 1 == kSortCap) || ((key[i + 1] >> 16) != v);
+      if (last) rec_end[r] = uint16_t(i + 1);
+    }
+    __syncthreads();
+  }
+}
+
+// dcoords[v] = sum of the records of v in increasing record order.
 template <int D>
-__global__ void vertex_reduce_kernel(const int32_t* __restrict__ offsets, const int32_t* __restrict__ incidence,
-                                     const float* __restrict__ scratch, int64_t n_vert,
+__global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
+                                     const float* __restrict__ records, int64_t n_vert,
                                      float* __restrict__ dcoords) {
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t b = __ldg(offsets + v), en = __ldg(offsets + v + 1);
-    float s[D];
+    const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
+    float acc[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) s[a] = 0.f;
-    for (int32_t i = b; i < en; ++i) {
-      const int64_t slot = __ldg(incidence + i);
+    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int32_t k = b; k < e; ++k) {
+      const int64_t r = __ldg(vrec + k);
 #pragma unroll
-      for (int a = 0; a < D; ++a) s[a] += __ldcs(scratch + slot * D + a);
+      for (int a = 0; a < D; ++a) acc[a] += __ldcs(records + r * D + a);
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) dcoords[v * D + a] = s[a];
+    for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
   }
 }
 
@@ -158,6 +286,14 @@ unsigned grid_for(int64_t n, int block) {
   return unsigned(g < 1 ? 1 : g);
 }
 
+// offsets[0..n] = exclusive prefix sums of cnt[0..n) (offsets[n] = total).
+void exclusive_scan(const int32_t* cnt, int64_t n, int32_t* partials, int32_t* offsets, cudaStream_t stream) {
+  const int64_t nb = (n + kScanBlock - 1) / kScanBlock;
+  if (nb > 0) scan_partials_kernel<<<unsigned(nb), kScanBlock, 0, stream>>>(cnt, n, partials);
+  scan_top_kernel<<<1, kScanBlock, 0, stream>>>(partials, nb);
+  scan_apply_kernel<<<unsigned(nb > 0 ? nb : 1), kScanBlock, 0, stream>>>(cnt, n, partials, nb, offsets);
+}
+
 }  // namespace
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -165,25 +301,38 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
                             BwdWorkspace* ws) {
   const int64_t nv = dim + 1;
-  const int64_t nb = (n_vert + kScanBlock - 1) / kScanBlock;
+  const int64_t ns = kTileElems * nv;
+  const int64_t n_tiles = (n_elem + kTileElems - 1) / kTileElems;
+  const int64_t r_max = n_elem * nv;  // at most one record per slot
+  const int64_t n_cnt = n_vert > n_tiles ? n_vert : n_tiles;
+  const int64_t nb = (n_cnt + kScanBlock - 1) / kScanBlock;
   size_t off = 0;
-  const size_t o_offsets = off;
-  off = align256(off + sizeof(int32_t) * size_t(n_vert + 1));
-  const size_t o_inc = off;
-  off = align256(off + sizeof(int32_t) * size_t(n_elem * nv));
-  const size_t o_cursor = off;
-  off = align256(off + sizeof(int32_t) * size_t(n_vert));
-  const size_t o_part = off;
-  off = align256(off + sizeof(int32_t) * size_t(nb + 1));
-  const size_t o_scr = off;
-  if (with_scratch) off = align256(off + sizeof(float) * size_t(n_elem * nv * dim));
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = align256(off + bytes);
+    return o;
+  };
+  const size_t o_tile_rec = take(sizeof(int32_t) * size_t(n_tiles + 1));
+  const size_t o_sorted = take(sizeof(uint16_t) * size_t(n_tiles * ns));
+  const size_t o_rec_end = take(sizeof(uint16_t) * size_t(r_max));
+  const size_t o_rec_vertex = take(sizeof(int32_t) * size_t(r_max));
+  const size_t o_voff = take(sizeof(int32_t) * size_t(n_vert + 1));
+  const size_t o_vrec = take(sizeof(int32_t) * size_t(r_max));
+  const size_t o_cursor = take(sizeof(int32_t) * size_t(n_cnt + 1));
+  const size_t o_part = take(sizeof(int32_t) * size_t(nb + 1));
+  const size_t o_records = with_scratch ? take(sizeof(float) * size_t(r_max * dim)) : off;
   if (ws) {
     char* b = static_cast<char*>(base);
-    ws->offsets = reinterpret_cast<int32_t*>(b + o_offsets);
-    ws->incidence = reinterpret_cast<int32_t*>(b + o_inc);
+    ws->tile_rec = reinterpret_cast<int32_t*>(b + o_tile_rec);
+    ws->sorted = reinterpret_cast<uint16_t*>(b + o_sorted);
+    ws->rec_end = reinterpret_cast<uint16_t*>(b + o_rec_end);
+    ws->rec_vertex = reinterpret_cast<int32_t*>(b + o_rec_vertex);
+    ws->voff = reinterpret_cast<int32_t*>(b + o_voff);
+    ws->vrec = reinterpret_cast<int32_t*>(b + o_vrec);
     ws->cursor = reinterpret_cast<int32_t*>(b + o_cursor);
     ws->partials = reinterpret_cast<int32_t*>(b + o_part);
-    ws->scratch = with_scratch ? reinterpret_cast<float*>(b + o_scr) : nullptr;
+    ws->records = with_scratch ? reinterpret_cast<float*>(b + o_records) : nullptr;
+    ws->n_tiles = n_tiles;
     ws->bytes = off;
   }
   return off;
@@ -191,18 +340,23 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
 
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream) {
-  const int64_t n_slots = n_elem * (dim + 1);
-  const int64_t nb = (n_vert + kScanBlock - 1) / kScanBlock;
-  zero_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert);
-  count_kernel<<<grid_for(n_slots, 256), 256, 0, stream>>>(conn, n_slots, n_vert, ws.cursor);
-  if (nb > 0) scan_partials_kernel<<<unsigned(nb), kScanBlock, 0, stream>>>(ws.cursor, n_vert, ws.partials);
-  scan_top_kernel<<<1, kScanBlock, 0, stream>>>(ws.partials, nb);
-  scan_apply_kernel<<<unsigned(nb > 0 ? nb : 1), kScanBlock, 0, stream>>>(ws.cursor, n_vert, ws.partials, nb,
-                                                                          ws.offsets);
-  zero_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert);
-  fill_kernel<<<grid_for(n_slots, 256), 256, 0, stream>>>(conn, n_slots, n_vert, ws.offsets, ws.cursor,
-                                                           ws.incidence);
-  sort_segments_kernel<<<grid_for(n_vert, 128), 128, 0, stream>>>(ws.offsets, n_vert, ws.incidence);
+  const int nv = dim + 1;
+  const int64_t n_tiles = ws.n_tiles;
+  const int64_t r_max = n_elem * nv;
+  const unsigned tg = unsigned(n_tiles < 4 * 65535 ? (n_tiles > 0 ? n_tiles : 1) : 4 * 65535);
+  // tile records; record slots past the last record keep vertex -1
+  tile_sort_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.sorted, ws.cursor);
+  exclusive_scan(ws.cursor, n_tiles, ws.partials, ws.tile_rec, stream);
+  fill_i32<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, -1);
+  tile_records_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.tile_rec,
+                                                         ws.rec_end, ws.rec_vertex);
+  // vertex -> records CSR
+  fill_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert, 0);
+  count_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, n_vert, ws.cursor);
+  exclusive_scan(ws.cursor, n_vert, ws.partials, ws.voff, stream);
+  fill_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert, 0);
+  fill_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, n_vert, ws.voff, ws.cursor, ws.vrec);
+  sort_segments_kernel<<<grid_for((n_vert + 3) / 4, 128), 128, 0, stream>>>(ws.voff, n_vert, ws.vrec);
   return cudaGetLastError();
 }
 
@@ -216,13 +370,11 @@ cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert
                                  cudaStream_t stream) {
   if (n_vert == 0) return cudaSuccess;
   const int block = 256;
-  int64_t g = (n_vert + block - 1) / block;
+  const int64_t g = (n_vert + block - 1) / block;
   if (dim == 2)
-    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.offsets, ws.incidence, ws.scratch, n_vert,
-                                                               dcoords);
+    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.records, n_vert, dcoords);
   else
-    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.offsets, ws.incidence, ws.scratch, n_vert,
-                                                               dcoords);
+    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.records, n_vert, dcoords);
   return cudaGetLastError();
 }
 

@@ -33,6 +33,10 @@ struct GeoLaunch {
   cudaStream_t stream;
 };
 
+// Elements per CTA tile of the adjoint's element pass (4 warps x 32); the
+// deterministic reduction's tile records are built for this tile size.
+constexpr int kTileElems = 128;
+
 // Adjoint element pass (FP32 coordinates).
 struct BwdLaunch {
   int dim, form, jac, atomic;
@@ -40,22 +44,33 @@ struct BwdLaunch {
   const float* coords;
   const float* coef;
   const float* dA;
-  float* dcoef;     // may be null
-  float* xbar;      // deterministic: per-element scratch [E][dim+1][dim]
-  float* dcoords;   // atomic: accumulated with red.add (pre-zeroed)
+  float* dcoef;    // may be null
+  float* dcoords;  // atomic: accumulated with red.add (pre-zeroed)
+  // deterministic: tile records (null when only dcoef is wanted)
+  const int32_t* tile_rec;
+  const uint16_t* sorted;
+  const uint16_t* rec_end;
+  float* records;
   int64_t n_elem, n_vert;
   int32_t* dev_err;
-  int warps, ctas_per_sm;
+  int ctas_per_sm;
   cudaStream_t stream;
 };
 
-// Workspace of the adjoint: [offsets V+1][incidence E*(d+1)][cursor V][scan partials][scratch]
+// Workspace of the deterministic adjoint (see fem_incidence.cu):
+// [tile_rec T+1][sorted T*128*(d+1) u16][rec_end R u16][rec_vertex R][voff V+1][vrec R]
+// [cursor][scan partials][records R*d]   with R <= E*(d+1) records.
 struct BwdWorkspace {
-  int32_t* offsets;
-  int32_t* incidence;
+  int32_t* tile_rec;
+  uint16_t* sorted;
+  uint16_t* rec_end;
+  int32_t* rec_vertex;
+  int32_t* voff;
+  int32_t* vrec;
   int32_t* cursor;
   int32_t* partials;
-  float* scratch;
+  float* records;
+  int64_t n_tiles;
   size_t bytes;
 };
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
@@ -77,6 +92,9 @@ int device_sm_count();
 size_t device_smem_optin();
 // Largest warp count <= want whose per-warp stage (bytes_per_warp) fits the opt-in shared memory.
 int clamp_warps(int want, size_t bytes_per_warp);
+// Grid of a warp-tile pipeline kernel: one wave of resident CTAs (occupancy x SMs), or
+// ctas_per_sm x SMs when given, never more CTAs than the tiles need.
+unsigned pipeline_grid(const void* kernel, int warps, size_t smem, int64_t n_elem, int ctas_per_sm);
 // Raises the dynamic shared memory limit of a kernel when it needs more than 48 KB.
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
 

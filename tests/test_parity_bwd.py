@@ -58,21 +58,26 @@ def test_deterministic_is_bitwise_reproducible(gfem):
     assert _rel(d.cpu().numpy(), a.cpu().numpy().astype(np.float64)) <= 1e-6
 
 
-def test_incidence_csr_is_sorted_and_complete(gfem):
+def test_tile_records_structure(gfem):
+    """Workspace of the deterministic reduction: each 128-element tile has one
+    record per distinct vertex, and its slot list is sorted by (vertex, slot)."""
     mesh = _mesh(3, 5)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
     ws = gfem.Workspace(coords, conn)
-    V, E = mesh.n_vert, mesh.n_elem
-    raw = ws.buf.cpu().numpy().view(np.int32)
-    off = raw[: V + 1]
-    inc_start = ((4 * (V + 1) + 255) // 256) * 64
-    inc = raw[inc_start: inc_start + 4 * E]
-    slots = np.arange(4 * E)
-    vert = mesh.conn.ravel()
-    order = np.lexsort((slots, vert))
-    exp_off = np.concatenate([[0], np.cumsum(np.bincount(vert, minlength=V))])
-    assert np.array_equal(off, exp_off)
-    assert np.array_equal(inc, slots[order])
+    E, NS = mesh.n_elem, 128 * 4
+    T = (E + 127) // 128
+    raw = ws.buf.cpu().numpy()
+    tile_rec = raw[: 4 * (T + 1)].view(np.int32)
+    o_sorted = ((4 * (T + 1) + 255) // 256) * 256
+    srt = raw[o_sorted: o_sorted + 2 * T * NS].view(np.uint16).reshape(T, NS)
+    flat = mesh.conn.ravel()
+    assert tile_rec[0] == 0
+    for t in range(T):
+        slots = np.arange(t * NS, min((t + 1) * NS, 4 * E))
+        verts = flat[slots]
+        assert tile_rec[t + 1] - tile_rec[t] == len(np.unique(verts))
+        local = slots - t * NS
+        assert np.array_equal(srt[t, : len(slots)], local[np.lexsort((local, verts))])
 
 
 def test_coefficient_only_and_coords_only(gfem, orc):
