@@ -176,6 +176,33 @@ FEM_API fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const f
 FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes,
                                       float* dcoords, void* stream);
 
+/* Bytes of the scratch array built into the library for
+ * fem_integrate_bwd_noalloc (32 MiB: the deterministic adjoint of a tet mesh
+ * of up to roughly 300,000 elements). */
+#define FEM_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The adjoint of fem_integrate_bwd (deterministic reduction) for callers that
+ * cannot allocate device memory -- for example a host application that
+ * reserves all GPU memory at start-up and forbids allocation later, or a
+ * callback that only receives raw pointers from a framework owning the
+ * allocator.  The paper has no counterpart; it is an interface convenience.
+ *   Arguments, outputs and results are those of fem_integrate_bwd with
+ *   FEM_REDUCE_DETERMINISTIC; the caller passes no workspace.  Instead the
+ *   incidence records are rebuilt on every call inside a scratch array of
+ *   FEM_NOALLOC_SCRATCH_BYTES that the library holds in device memory of every
+ *   GPU that loads it, until the process exits.  Nothing is allocated.
+ *   - A mesh whose workspace (fem_bwd_workspace_size) exceeds that size is
+ *     rejected with FEM_ERR_UNSUPPORTED before anything is launched.
+ *   - options->reduce other than FEM_REDUCE_DETERMINISTIC: FEM_ERR_UNSUPPORTED.
+ *   - The first call on a device looks up the array's device address there
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array: calls whose GPU work may overlap (other
+ *     streams, other host threads on the same device) race and corrupt each
+ *     other's results.  Serialize them on one stream. */
+FEM_API fem_status fem_integrate_bwd_noalloc(const fem_mesh* mesh, int32_t form, const float* coef,
+                                             const float* dA, float* dcoords, float* dcoef,
+                                             const fem_options* options, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

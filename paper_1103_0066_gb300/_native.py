@@ -24,7 +24,8 @@ DEVERR_CONN, DEVERR_DEGENERATE = 1, 2
 # every symbol include/fem.h declares
 EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info",
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
-           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce")
+           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc")
+NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class FemError(RuntimeError):
@@ -73,6 +74,7 @@ def load():
             "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
             "fem_integrate_bwd": ([MP, I32, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
             "fem_adjoint_reduce": ([MP, P, SZ, P, P], ctypes.c_int),
+            "fem_integrate_bwd_noalloc": ([MP, I32, P, P, P, P, OP, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -150,3 +152,10 @@ def fem_integrate_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoo
 def fem_adjoint_reduce(mesh: FemMesh, ws_ptr: int, ws_bytes: int, dcoords_ptr: int, stream: int) -> None:
     check(load().fem_adjoint_reduce(ctypes.byref(mesh), ws_ptr or None, ws_bytes, dcoords_ptr or None,
                                     stream or None))
+
+
+def fem_integrate_bwd_noalloc(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoords_ptr: int,
+                              dcoef_ptr: int, opts: FemOptions, stream: int) -> None:
+    check(load().fem_integrate_bwd_noalloc(ctypes.byref(mesh), form, coef_ptr or None, dA_ptr or None,
+                                           dcoords_ptr or None, dcoef_ptr or None, ctypes.byref(opts),
+                                           stream or None))

@@ -80,6 +80,15 @@ void copy_ref(int32_t* K) {
 
 }  // namespace
 
+namespace fem {
+void set_last_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+}
+}  // namespace fem
+
 extern "C" {
 
 const char* fem_version(void) { return "fem_gb300 0.1 (sm_103a)"; }

@@ -87,6 +87,9 @@ cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t stream);
 cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert, float* dcoords,
                                  cudaStream_t stream);
 
+// Records the reason reported by fem_last_error() for the calling thread.
+void set_last_error(const char* fmt, ...);
+
 // Device facts of the current device (cached per device).
 int device_sm_count();
 size_t device_smem_optin();
