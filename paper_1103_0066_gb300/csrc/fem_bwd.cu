@@ -77,11 +77,14 @@ struct BwdPlan {
   static constexpr int DST = VEC ? NN + 4 : (NN | 1);  // dA row stride in the stage
   static constexpr int NV = D + 1;
   static constexpr int NS = kTileElems * NV;  // slots per CTA tile
+  static constexpr int XP = D == 3 ? 4 : 2;     // padded floats per staged slot (one vector store)
   static constexpr int WARPS = kTileElems / 32;
   static constexpr size_t da_bytes = align_up(size_t(2) * 32 * DST * 4, 128);  // per warp
-  static constexpr size_t xs_bytes = align_up(size_t(NS) * D * 4, 128);         // per CTA
+  static constexpr size_t xs_bytes = align_up(size_t(NS) * XP * 4, 128);        // per CTA
   static constexpr size_t sorted_bytes = align_up(size_t(2) * NS * 2, 128);     // per CTA
-  static constexpr size_t smem = WARPS * da_bytes + xs_bytes + sorted_bytes;
+  static constexpr int ENDS = NS + 16;  // record ends of a tile (<= NS) plus alignment slack
+  static constexpr size_t ends_bytes = align_up(size_t(2) * ENDS * 2, 128);     // per CTA
+  static constexpr size_t smem = WARPS * da_bytes + xs_bytes + sorted_bytes + ends_bytes;
 };
 
 // Asynchronous copy of a tile's contiguous dA into the padded stage slot.
@@ -120,11 +123,56 @@ __device__ __forceinline__ void copy_sorted(const uint16_t* sorted, int64_t tile
   for (int c = tid; c < NCH; c += kTileElems) cp_async<16>(dst + 8 * c, src + 8 * c);
 }
 
+// Asynchronous copy of the record ends rec_end[rb, rb + rn) of a tile into
+// dst[0, ...), starting at the 16-byte chunk that holds entry rb; returns the
+// offset of entry rb in dst.  The workspace pads rec_end so the last chunk
+// never leaves the array.
+template <int ENDS>
+__device__ __forceinline__ int copy_ends(const uint16_t* rec_end, int32_t rb, int32_t rn, int tid, uint16_t* dst) {
+  const int32_t c0 = rb & ~7;
+  const int nch = (rb + rn - c0 + 7) >> 3;
+  for (int c = tid; c < nch; c += kTileElems) cp_async<16>(dst + 8 * c, rec_end + c0 + 8 * c);
+  return rb - c0;
+}
+
+// Position of slot (element el of the CTA tile, local vertex k) in the padded
+// stage: the slot order within an element is rotated by (el >> 1), which keeps
+// the 16-byte writes of a quarter warp on distinct bank groups.
+template <int NV>
+__device__ __forceinline__ int stage_slot(int el, int k) {
+  if constexpr (NV == 4)
+    return el * 4 + ((k + (el >> 1)) & 3);
+  else
+    return el * NV + k;
+}
+
+// Upper triangle of sym(dA) from a staged row: 16-byte reads when the row is
+// 16-byte aligned and small enough to hold in registers, scalar reads otherwise.
+template <int D, int FORM>
+__device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTraits<D, FORM>::NT]) {
+  using FT = FormTraits<D, FORM>;
+  constexpr int N = FT::N, NN = FT::NN;
+  if constexpr (NN % 4 == 0 && NN <= 36) {
+    float r[NN];
+#pragma unroll
+    for (int q = 0; q < NN / 4; ++q) {
+      const float4 v = reinterpret_cast<const float4*>(drow)[q];
+      r[4 * q] = v.x;
+      r[4 * q + 1] = v.y;
+      r[4 * q + 2] = v.z;
+      r[4 * q + 3] = v.w;
+    }
+    load_sym<N>(r, s, std::make_integer_sequence<int, FT::NT>{});
+  } else {
+    load_sym<N>(drow, s, std::make_integer_sequence<int, FT::NT>{});
+  }
+}
+
 // Stage 3 of the adjoint for one element per lane.
 template <int D, int FORM, int JAC, bool ATOMIC>
 __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags, float w,
                                                 const float (&X)[D + 1][D], const float* drow,
-                                                const int (&vc)[D + 1], float* xs_row) {
+                                                const int (&vc)[D + 1], float* xs, int el) {
   using FT = FormTraits<D, FORM>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
   constexpr int N = FT::N, NV = FT::NV;
@@ -157,7 +205,7 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
       geometric_tensor<D, FORM>(adj, scale0, G0);
       // 1. dG = transpose of the contraction applied to sym(dA)
       SymVals<FT::NT> sym;
-      load_sym<N>(drow, sym.s, std::make_integer_sequence<int, FT::NT>{});
+      stage_sym<D, FORM>(drow, sym.s);
       float dG[FT::NG];
       contract_adjoint<D, FORM>(sym, dG);
       // 2. coefficient gradient
@@ -249,22 +297,14 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
     }
   }
   if constexpr (!ATOMIC) {
-    if (xs_row) {  // the element's slot contributions (zeros when it is skipped)
-      if constexpr ((NV * D) % 4 == 0) {
+    if (xs) {  // the element's slot contributions (zeros when it is skipped)
 #pragma unroll
-        for (int q = 0; q < NV * D / 4; ++q) {
-          float4 v;
-          v.x = xb[(4 * q) / D][(4 * q) % D];
-          v.y = xb[(4 * q + 1) / D][(4 * q + 1) % D];
-          v.z = xb[(4 * q + 2) / D][(4 * q + 2) % D];
-          v.w = xb[(4 * q + 3) / D][(4 * q + 3) % D];
-          reinterpret_cast<float4*>(xs_row)[q] = v;
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NV; ++k)
-#pragma unroll
-          for (int a = 0; a < D; ++a) xs_row[k * D + a] = xb[k][a];
+      for (int k = 0; k < NV; ++k) {
+        float* d = xs + stage_slot<NV>(el, k) * (D == 3 ? 4 : 2);
+        if constexpr (D == 3)
+          *reinterpret_cast<float4*>(d) = make_float4(xb[k][0], xb[k][1], xb[k][2], 0.f);
+        else
+          *reinterpret_cast<float2*>(d) = make_float2(xb[k][0], xb[k][1]);
       }
     }
   }
@@ -278,13 +318,17 @@ __global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* dslots = reinterpret_cast<float*>(smem_raw + size_t(warp) * PL::da_bytes);  // [2][32][DST]
-  float* xs = reinterpret_cast<float*>(smem_raw + W * PL::da_bytes);                 // [NS][D]
+  float* xs = reinterpret_cast<float*>(smem_raw + W * PL::da_bytes);                 // [NS][XP]
   uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem_raw + W * PL::da_bytes + PL::xs_bytes);  // [2][NS]
+  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem_raw + W * PL::da_bytes + PL::xs_bytes +
+                                               PL::sorted_bytes);  // [2][ENDS]
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
   const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
   const int64_t G = gridDim.x;
   int64_t T = blockIdx.x;
   if (T >= nct) return;  // CTA-uniform
+  const int el = warp * 32 + lane;  // element within the CTA tile
+  int eoff = 0;                     // position of the tile's first record end in its ebuf slot
   int err = 0;
   int v1[D + 1], v2[D + 1], vc[D + 1];
   float Xc[D + 1][D], Xn[D + 1][D];
@@ -298,6 +342,7 @@ __global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
   if (rec) {
     rb = __ldg(p.tile_rec + T);
     rn = __ldg(p.tile_rec + T + 1) - rb;
+    eoff = copy_ends<PL::ENDS>(p.rec_end, rb, rn, tid, ebuf);
   }
   cp_async_commit();
 #pragma unroll
@@ -312,29 +357,40 @@ __global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
     const bool has_next = T + G < nct;
     if (rec && has_next) copy_sorted<NS>(p.sorted, T + G, tid, sbuf + sn * NS);
     const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
-    int32_t rbn = 0, rnn = 0;
+    int32_t rbn = 0, rnn = 0, eoffn = 0;
     if (rec && has_next) {
       rbn = __ldg(p.tile_rec + T + G);
       rnn = __ldg(p.tile_rec + T + G + 1) - rbn;
+      eoffn = copy_ends<PL::ENDS>(p.rec_end, rbn, rnn, tid, ebuf + sn * PL::ENDS);
     }
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();  // dA rows were copied by other lanes
     err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslots + (sc * 32 + lane) * PL::DST,
-                                                  vc, rec ? xs + size_t(warp * 32 + lane) * NV * D : nullptr);
+                                                  vc, rec ? xs : nullptr, el);
     if (rec) {
       __syncthreads();  // every warp's contributions and the sorted list are in shared memory
       const uint16_t* srt = sbuf + sc * NS;
+      const uint16_t* ends = ebuf + sc * PL::ENDS + eoff;
       for (int r = tid; r < rn; r += kTileElems) {
-        const int beg = r == 0 ? 0 : int(__ldg(p.rec_end + rb + r - 1));
-        const int end = int(__ldg(p.rec_end + rb + r));
+        const int beg = r == 0 ? 0 : int(ends[r - 1]);
+        const int end = int(ends[r]);
         float acc[D];
 #pragma unroll
         for (int a = 0; a < D; ++a) acc[a] = 0.f;
         for (int j = beg; j < end; ++j) {
-          const float* x = xs + int(srt[j]) * D;
-#pragma unroll
-          for (int a = 0; a < D; ++a) acc[a] += x[a];
+          const int slot = srt[j];
+          const float* x = xs + stage_slot<NV>(slot / NV, slot % NV) * PL::XP;
+          if constexpr (D == 3) {
+            const float4 v = *reinterpret_cast<const float4*>(x);
+            acc[0] += v.x;
+            acc[1] += v.y;
+            acc[2] += v.z;
+          } else {
+            const float2 v = *reinterpret_cast<const float2*>(x);
+            acc[0] += v.x;
+            acc[1] += v.y;
+          }
         }
         float* dst = p.records + int64_t(rb + r) * D;
 #pragma unroll
@@ -348,6 +404,7 @@ __global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
     wcur = wnext;
     rb = rbn;
     rn = rnn;
+    eoff = eoffn;
 #pragma unroll
     for (int k = 0; k <= D; ++k) {
       vc[k] = v1[k];

@@ -118,14 +118,16 @@ template <int D, class CT>
 __device__ __forceinline__ int gather_regs(const CT* coords, int64_t n_vert, int64_t e, int64_t n_elem,
                                            const int (&v)[D + 1], CT (&X)[D + 1][D]) {
   if (e >= n_elem) return 0;
-  bool ok = true;
+  bool ok = true;  // n_vert <= INT32_MAX, so one unsigned compare covers v < 0
 #pragma unroll
-  for (int k = 0; k <= D; ++k) ok &= (v[k] >= 0) & (int64_t(v[k]) < n_vert);
+  for (int k = 0; k <= D; ++k) ok &= uint32_t(v[k]) < uint32_t(n_vert);
   if (!ok) return GF_ELEM;
 #pragma unroll
-  for (int k = 0; k <= D; ++k)
+  for (int k = 0; k <= D; ++k) {
+    const CT* c = coords + uint32_t(v[k]) * uint64_t(D);
 #pragma unroll
-    for (int a = 0; a < D; ++a) X[k][a] = __ldg(coords + int64_t(v[k]) * D + a);
+    for (int a = 0; a < D; ++a) X[k][a] = __ldg(c + a);
+  }
   return GF_ELEM | GF_OK;
 }
 
@@ -144,19 +146,17 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
   for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(0);
   if (flags & GF_OK) {
     Jac<D, GT> jac;
-    if (!jacobian<D, JAC>(X, jac)) {
-      err |= DEVERR_DEGENERATE;
-    } else {
-      GT scale;
-      if constexpr (sizeof(GT) == 4)
-        scale = __fdividef(w, dev_abs(jac.det) * float(FT::DEN));
-      else
-        scale = GT(w) / (dev_abs(jac.det) * GT(FT::DEN));
-      GT Gt[FT::NG];
-      geometric_tensor<D, FORM>(jac.adj, scale, Gt);
+    const bool nondeg = jacobian<D, JAC>(X, jac);
+    err |= nondeg ? 0 : DEVERR_DEGENERATE;
+    GT scale;  // zero for a degenerate element: its matrix is written as zeros
+    if constexpr (sizeof(GT) == 4)
+      scale = nondeg ? __fdividef(w, dev_abs(jac.det) * float(FT::DEN)) : 0.f;
+    else
+      scale = nondeg ? GT(w) / (dev_abs(jac.det) * GT(FT::DEN)) : GT(0);
+    GT Gt[FT::NG];
+    geometric_tensor<D, FORM>(jac.adj, scale, Gt);
 #pragma unroll
-      for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(Gt[g]);
-    }
+    for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(Gt[g]);
   } else if (flags & GF_ELEM) {
     err |= DEVERR_CONN;
   }
@@ -225,6 +225,22 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
   return err;
 }
 
+// One pipeline step: issue the loads of tiles t + 2S (connectivity) and t + S
+// (coordinates, coefficient), then compute and store tile t.  The kernel
+// calls it with the register buffers swapped on alternate steps, so the
+// pipeline rotates without register copies.
+template <int D, int FORM, int JAC, class CT, class OT>
+__device__ __forceinline__ void fwd_step(const FwdParams<CT, OT>& p, int64_t t, int64_t S, int lane,
+                                         const int (&vnext)[D + 1], int (&vload)[D + 1],
+                                         const CT (&Xcur)[D + 1][D], CT (&Xnext)[D + 1][D], int fcur,
+                                         float wcur, int& fnext, float& wnext, OT* st, int& err) {
+  const int64_t en = (t + S) * 32 + lane;
+  load_conn<D>(p.conn, (t + 2 * S) * 32 + lane, p.n_elem, p.vec_conn, vload);
+  fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vnext, Xnext);
+  wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+  err |= fwd_compute_tile<D, FORM, JAC, CT, OT>(p, t, lane, fcur, wcur, Xcur, st);
+}
+
 template <int D, int FORM, int JAC, class CT, class OT>
 __global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
   using PL = FwdPlan<D, FORM, CT, OT>;
@@ -232,31 +248,24 @@ __global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   OT* st = reinterpret_cast<OT*>(smem_raw + size_t(warp) * PL::per_warp);
   const int64_t ntiles = (p.n_elem + 31) / 32;
-  const int64_t stride = int64_t(gridDim.x) * nwarps;
+  const int64_t S = int64_t(gridDim.x) * nwarps;
   int64_t t = int64_t(blockIdx.x) * nwarps + warp;
   if (t >= ntiles) return;  // warp-uniform
   int err = 0;
-  int v1[D + 1], v2[D + 1];
-  CT Xc[D + 1][D], Xn[D + 1][D];
-  // prologue: tile t gathered, tile t + stride connectivity in flight
-  load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
-  int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
-  float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
-  load_conn<D>(p.conn, (t + stride) * 32 + lane, p.n_elem, p.vec_conn, v1);
-  for (; t < ntiles; t += stride) {
-    const int64_t en = (t + stride) * 32 + lane;
-    load_conn<D>(p.conn, (t + 2 * stride) * 32 + lane, p.n_elem, p.vec_conn, v2);
-    const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
-    const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
-    err |= fwd_compute_tile<D, FORM, JAC, CT, OT>(p, t, lane, fcur, wcur, Xc, st);
-    fcur = fnext;
-    wcur = wnext;
-#pragma unroll
-    for (int k = 0; k <= D; ++k) {
-      v1[k] = v2[k];
-#pragma unroll
-      for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
-    }
+  int va[D + 1], vb[D + 1];
+  CT Xa[D + 1][D], Xb[D + 1][D];
+  int fa, fb;
+  float wa, wb;
+  // prologue: tile t gathered, tile t + S connectivity in flight
+  load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, va);
+  fa = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, va, Xa);
+  wa = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  load_conn<D>(p.conn, (t + S) * 32 + lane, p.n_elem, p.vec_conn, va);
+  for (;;) {
+    fwd_step<D, FORM, JAC>(p, t, S, lane, va, vb, Xa, Xb, fa, wa, fb, wb, st, err);
+    if ((t += S) >= ntiles) break;
+    fwd_step<D, FORM, JAC>(p, t, S, lane, vb, va, Xb, Xa, fb, wb, fa, wa, st, err);
+    if ((t += S) >= ntiles) break;
   }
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);

@@ -314,7 +314,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   };
   const size_t o_tile_rec = take(sizeof(int32_t) * size_t(n_tiles + 1));
   const size_t o_sorted = take(sizeof(uint16_t) * size_t(n_tiles * ns));
-  const size_t o_rec_end = take(sizeof(uint16_t) * size_t(r_max));
+  const size_t o_rec_end = take(sizeof(uint16_t) * size_t(r_max + 16));  // +16: chunked reads
   const size_t o_rec_vertex = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_voff = take(sizeof(int32_t) * size_t(n_vert + 1));
   const size_t o_vrec = take(sizeof(int32_t) * size_t(r_max));
