@@ -38,7 +38,11 @@ FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic per launch from one ncu capture, valid only while the kernel
 # sources hash to `src`; otherwise reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1268.0e6, "src": "157a37f5ec22c8ea"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 975.1e6, "src": "157a37f5ec22c8ea"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 187.3e6, "src": "157a37f5ec22c8ea"},
+}
 
 
 def csrc_hash() -> str:
