@@ -176,6 +176,66 @@ FEM_API fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const f
 FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes,
                                       float* dcoords, void* stream);
 
+/* ------------------------------------------------------------------ batches
+ * Many meshes of uneven size and mixed forms integrated by ONE persistent
+ * kernel launch (an addition beside the method; the batch notion of Sec. 4
+ * is the paper's elementBatchSize within one mesh).  Persistent CTAs pull
+ * work items from a global counter: first 128-element tiles of any mesh
+ * (forward A and/or the adjoint's element pass), then per-mesh vertex ranges
+ * of the deterministic reduction, each of which waits (bounded) for its
+ * mesh's tiles.  fem_batch_run enqueues one memset and one kernel, so it can
+ * be captured in a CUDA graph. */
+
+#define FEM_PHASE_FWD 1 /* forward element matrices into item.A */
+#define FEM_PHASE_BWD 2 /* adjoint of item.dA into item.dcoords / item.dcoef */
+#define FEM_DEVERR_TIMEOUT 4 /* a bounded wait in a batched launch gave up (results incomplete) */
+
+/* One mesh of a batch (FP32 coordinates).  Pointers are device memory owned
+ * by the caller and must stay valid while the batch exists; NULL disables the
+ * matching output (A: no forward; dA / dcoords / dcoef: no adjoint part). */
+typedef struct fem_batch_item {
+  fem_mesh mesh;
+  int32_t form;
+  int32_t reserved; /* must be 0 */
+  const float* coef; /* [n_elem] or NULL */
+  float* A;          /* [n_elem][n][n] */
+  const float* dA;   /* [n_elem][n][n] */
+  float* dcoords;    /* [n_vert][dim] (deterministic reduction) */
+  float* dcoef;      /* [n_elem] */
+} fem_batch_item;
+
+typedef struct fem_batch fem_batch; /* opaque; host object */
+
+/* Device workspace bytes of a batch (descriptor table, counters, the
+ * per-mesh reduction records). */
+FEM_API fem_status fem_batch_workspace_size(const fem_batch_item* items, int32_t n_items, size_t* bytes);
+
+/* Creates a batch over caller-owned device workspace `ws` (256-byte aligned):
+ * builds every mesh's reduction records (once) and uploads the descriptor
+ * table, asynchronously on `stream`.  *out receives a host object to be
+ * released with fem_batch_destroy. */
+FEM_API fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* ws, size_t ws_bytes,
+                                    fem_batch** out, void* stream);
+
+/* Autotuner: times the persistent launch over candidate grids (CTAs per SM)
+ * and work-chunk sizes with CUDA events on `stream` (synchronizing it) and
+ * keeps the fastest for later fem_batch_run calls. */
+FEM_API fem_status fem_batch_tune(fem_batch* batch, int32_t phases, void* stream);
+
+/* The launch configuration in use (the tuner's choice, or the default). */
+FEM_API fem_status fem_batch_config(const fem_batch* batch, int32_t* ctas_per_sm, int32_t* chunk);
+
+/* One persistent launch over every mesh of the batch for `phases`
+ * (FEM_PHASE_FWD | FEM_PHASE_BWD).  Asynchronous; graph-capturable. */
+FEM_API fem_status fem_batch_run(fem_batch* batch, int32_t phases, void* stream);
+
+/* Device error word of the last fem_batch_run (FEM_DEVERR_* bits), copied
+ * synchronously to *err_host. */
+FEM_API fem_status fem_batch_errors(const fem_batch* batch, int32_t* err_host, void* stream);
+
+/* Releases the host object (the caller frees the workspace). */
+FEM_API void fem_batch_destroy(fem_batch* batch);
+
 /* Bytes of the scratch array built into the library for
  * fem_integrate_bwd_noalloc (32 MiB: the deterministic adjoint of a tet mesh
  * of up to roughly 300,000 elements). */

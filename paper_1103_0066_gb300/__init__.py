@@ -21,9 +21,9 @@ import torch
 from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
                       F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2,
-                      REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, FemError)
+                      REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError)
 
-__all__ = ["Mesh", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+__all__ = ["Mesh", "Batch", "PHASE_FWD", "PHASE_BWD", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
            "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
@@ -195,3 +195,59 @@ class Mesh:
 def integrate(coords, conn, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC):
     """Differentiable element matrices for a one-off mesh (builds the incidence on first backward)."""
     return Mesh(coords, conn).integrate(form, coef, jac, reduce)
+
+
+class Batch:
+    """Many meshes of mixed forms integrated by one persistent launch (fem_batch_*).
+
+    items: sequence of dicts with CUDA tensors ``coords`` [V][d] float32, ``conn``
+    [E][d+1] int32, ``form``, and optional ``coef``, ``A`` (forward output),
+    ``dA``, ``dcoords``, ``dcoef`` (adjoint).  The tensors must outlive the batch.
+    """
+
+    def __init__(self, items, stream=None):
+        self._keep = []
+        arr = (nat.FemBatchItem * len(items))()
+        for k, it in enumerate(items):
+            m = _mesh_struct(it["coords"], it["conn"])
+            if m.coord_dtype != F32:
+                raise ValueError("batched meshes take float32 coordinates")
+            E = it["conn"].shape[0]
+            ptr = {}
+            for name in ("coef", "A", "dA", "dcoords", "dcoef"):
+                t = it.get(name)
+                if t is not None:
+                    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                        raise ValueError(f"item {k}: {name} must be a contiguous CUDA float32 tensor")
+                    self._keep.append(t)
+                ptr[name] = t.data_ptr() if t is not None else None
+            if ptr["coef"] is not None and it["coef"].numel() != E:
+                raise ValueError(f"item {k}: coef must have n_elem entries")
+            self._keep += [it["coords"], it["conn"]]
+            arr[k] = nat.FemBatchItem(m, it["form"], 0, ptr["coef"], ptr["A"], ptr["dA"], ptr["dcoords"],
+                                      ptr["dcoef"])
+        self._items = arr
+        self.ws_bytes = nat.fem_batch_workspace_size(arr)
+        dev = items[0]["coords"].device
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.handle = nat.fem_batch_create(arr, self.ws.data_ptr(), self.ws_bytes, _stream_ptr(stream))
+
+    def tune(self, phases=PHASE_FWD | PHASE_BWD, stream=None):
+        nat.fem_batch_tune(self.handle, phases, _stream_ptr(stream))
+        return self.config()
+
+    def config(self):
+        """(CTAs per SM, work-chunk size) used by run()."""
+        return nat.fem_batch_config(self.handle)
+
+    def run(self, phases=PHASE_FWD | PHASE_BWD, stream=None):
+        nat.fem_batch_run(self.handle, phases, _stream_ptr(stream))
+
+    def errors(self, stream=None) -> int:
+        return nat.fem_batch_errors(self.handle, _stream_ptr(stream))
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            nat.fem_batch_destroy(h)
+            self.handle = None

@@ -24,7 +24,11 @@ DEVERR_CONN, DEVERR_DEGENERATE = 1, 2
 # every symbol include/fem.h declares
 EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info",
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
-           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc")
+           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
+           "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_run",
+           "fem_batch_errors", "fem_batch_destroy")
+PHASE_FWD, PHASE_BWD = 1, 2
+DEVERR_TIMEOUT = 4
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -44,6 +48,12 @@ class FemOptions(ctypes.Structure):
     _fields_ = [("jac", ctypes.c_int32), ("contract", ctypes.c_int32), ("reduce", ctypes.c_int32),
                 ("warps_per_cta", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("reserved", ctypes.c_int32), ("dev_err", ctypes.c_void_p)]
+
+
+class FemBatchItem(ctypes.Structure):
+    _fields_ = [("mesh", FemMesh), ("form", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("coef", ctypes.c_void_p), ("A", ctypes.c_void_p), ("dA", ctypes.c_void_p),
+                ("dcoords", ctypes.c_void_p), ("dcoef", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -75,6 +85,13 @@ def load():
             "fem_integrate_bwd": ([MP, I32, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
             "fem_adjoint_reduce": ([MP, P, SZ, P, P], ctypes.c_int),
             "fem_integrate_bwd_noalloc": ([MP, I32, P, P, P, P, OP, P], ctypes.c_int),
+            "fem_batch_workspace_size": ([ctypes.POINTER(FemBatchItem), I32, ctypes.POINTER(SZ)], ctypes.c_int),
+            "fem_batch_create": ([ctypes.POINTER(FemBatchItem), I32, P, SZ, ctypes.POINTER(P), P], ctypes.c_int),
+            "fem_batch_tune": ([P, I32, P], ctypes.c_int),
+            "fem_batch_config": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
+            "fem_batch_run": ([P, I32, P], ctypes.c_int),
+            "fem_batch_errors": ([P, ctypes.POINTER(I32), P], ctypes.c_int),
+            "fem_batch_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -159,3 +176,39 @@ def fem_integrate_bwd_noalloc(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: i
     check(load().fem_integrate_bwd_noalloc(ctypes.byref(mesh), form, coef_ptr or None, dA_ptr or None,
                                            dcoords_ptr or None, dcoef_ptr or None, ctypes.byref(opts),
                                            stream or None))
+
+
+def fem_batch_workspace_size(items) -> int:
+    b = ctypes.c_size_t()
+    check(load().fem_batch_workspace_size(items, len(items), ctypes.byref(b)))
+    return b.value
+
+
+def fem_batch_create(items, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    h = ctypes.c_void_p()
+    check(load().fem_batch_create(items, len(items), ws_ptr, ws_bytes, ctypes.byref(h), stream or None))
+    return h.value
+
+
+def fem_batch_tune(handle: int, phases: int, stream: int) -> None:
+    check(load().fem_batch_tune(handle, phases, stream or None))
+
+
+def fem_batch_config(handle: int):
+    c, k = ctypes.c_int32(), ctypes.c_int32()
+    check(load().fem_batch_config(handle, ctypes.byref(c), ctypes.byref(k)))
+    return c.value, k.value
+
+
+def fem_batch_run(handle: int, phases: int, stream: int) -> None:
+    check(load().fem_batch_run(handle, phases, stream or None))
+
+
+def fem_batch_errors(handle: int, stream: int) -> int:
+    e = ctypes.c_int32()
+    check(load().fem_batch_errors(handle, ctypes.byref(e), stream or None))
+    return e.value
+
+
+def fem_batch_destroy(handle: int) -> None:
+    load().fem_batch_destroy(handle)

@@ -1,0 +1,519 @@
+// fem_batch.cu -- many meshes of mixed forms in one persistent launch.
+//
+// Work items, in dispensing order:
+//   [0, n_tile_items)        one 128-element tile of some mesh: forward A
+//                            and/or the adjoint element pass with its records
+//   [n_tile_items, n_total)  a range of vertices of some mesh: the deterministic
+//                            reduction of that mesh's records into dcoords
+// Persistent CTAs (4 warps, one tile each time) take `chunk` consecutive items
+// per atomicAdd on a global counter.  A reduction item waits until every tile of
+// its mesh has been counted done.  All tiles precede all reduction items in the
+// dispensing order and a CTA holding a tile never waits, so every awaited tile
+// is held by a running CTA and the wait ends; it is nevertheless bounded and
+// reports FEM_DEVERR_TIMEOUT when it gives up.  The per-tile code is the
+// per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, write_records).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/fem.h"
+#include "fem_bwd.cuh"
+#include "fem_fwd.cuh"
+#include "fem_internal.h"
+
+namespace fem {
+
+struct BatchMesh {
+  int32_t kind;   // (dim - 2) * 3 + form
+  int32_t flags;  // BM_* bits
+  int64_t n_elem, n_vert;
+  const int32_t* conn;
+  const float* coords;
+  const float* coef;
+  const float* dA;
+  float* A;
+  float* dcoords;
+  float* dcoef;
+  const int32_t* tile_rec;
+  const uint16_t* sorted;
+  const uint16_t* rec_end;
+  const int32_t* voff;
+  const int32_t* vrec;
+  float* records;
+  int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space
+  int64_t red_begin, n_red;     // reduction items
+};
+enum : int { BM_FWD = 1, BM_BWD = 2, BM_REC = 4 };
+
+struct BatchCounters {
+  unsigned long long next;
+  int32_t err;
+  int32_t pad;
+  int32_t done[1];  // [n_items] tiles completed per mesh
+};
+
+constexpr int kRedVerts = 2048;  // vertices per reduction item
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+// Shared memory of one batch CTA: per-warp stage, then the tile's slot stage,
+// sorted slot list and record ends (sized for tets, which bound triangles).
+template <int D, int FORM>
+constexpr size_t batch_stage_bytes() {
+  return std::max(FwdPlan<D, FORM, float, float>::per_warp,
+                  align_up(size_t(32) * BwdPlan<D, FORM>::DST * 4, 128));
+}
+constexpr size_t kXsBytes = align_up(size_t(kTileElems) * 4 * 4 * 4, 128);
+constexpr size_t kSortedBytes = align_up(size_t(kTileElems) * 4 * 2, 128);
+constexpr size_t kEndsBytes = align_up(size_t(kTileElems * 4 + 16) * 2, 128);
+
+__device__ __forceinline__ int find_mesh(const BatchMesh* desc, int n, int64_t item, bool red) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {  // last mesh whose range begins at or before `item`
+    const int mid = (lo + hi + 1) >> 1;
+    const int64_t b = red ? desc[mid].red_begin : desc[mid].tile_begin;
+    if (b <= item)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int D, int FORM>
+__device__ void batch_tile(const BatchMesh& M, int64_t T, int phases, unsigned char* smem, size_t stage_bytes,
+                           int& err) {
+  using BPL = BwdPlan<D, FORM>;
+  constexpr int NS = BPL::NS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* wst = reinterpret_cast<float*>(smem + size_t(warp) * stage_bytes);
+  float* xs = reinterpret_cast<float*>(smem + 4 * stage_bytes);
+  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem + 4 * stage_bytes + kXsBytes);
+  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem + 4 * stage_bytes + kXsBytes + kSortedBytes);
+  const int64_t t = T * 4 + warp, e = t * 32 + lane;
+  const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
+  int v[D + 1];
+  float X[D + 1][D];
+  load_conn<D>(M.conn, e, M.n_elem, vec_conn, v);
+  const int f = gather_regs<D>(M.coords, M.n_vert, e, M.n_elem, v, X);
+  const float w = (M.coef && e < M.n_elem) ? __ldg(M.coef + e) : 1.f;
+  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD)) {
+    FwdParams<float, float> fp;
+    fp.conn = M.conn;
+    fp.coords = M.coords;
+    fp.coef = M.coef;
+    fp.A = M.A;
+    fp.n_elem = M.n_elem;
+    fp.n_vert = M.n_vert;
+    fp.dev_err = nullptr;
+    fp.vec_conn = vec_conn;
+    fp.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
+    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fp, t, lane, f, w, X, wst);
+  }
+  if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
+    const bool rec = (M.flags & BM_REC) != 0;
+    BwdParams bp;
+    bp.conn = M.conn;
+    bp.coords = M.coords;
+    bp.coef = M.coef;
+    bp.dA = M.dA;
+    bp.tile_rec = rec ? M.tile_rec : nullptr;
+    bp.sorted = M.sorted;
+    bp.rec_end = M.rec_end;
+    bp.records = M.records;
+    bp.dcoef = M.dcoef;
+    bp.dcoords = nullptr;
+    bp.n_elem = M.n_elem;
+    bp.n_vert = M.n_vert;
+    bp.dev_err = nullptr;
+    bp.vec_conn = vec_conn;
+    bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+    copy_dA_async<D, FORM>(bp, t, lane, wst);
+    int32_t rb = 0, rn = 0, eoff = 0;
+    if (rec) {
+      copy_sorted<NS>(M.sorted, T, tid, sbuf);
+      rb = __ldg(M.tile_rec + T);
+      rn = __ldg(M.tile_rec + T + 1) - rb;
+      eoff = copy_ends<BPL::ENDS>(M.rec_end, rb, rn, tid, ebuf);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    if (rec)
+      __syncthreads();  // sorted list and record ends were copied by all threads
+    else
+      __syncwarp();
+    err |= bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, w, X, wst + lane * BPL::DST, v,
+                                                      rec ? xs : nullptr, warp * 32 + lane);
+    if (rec) {
+      __syncthreads();
+      write_records<D>(sbuf, ebuf + eoff, xs, rb, rn, M.records, tid);
+    }
+  }
+  __threadfence();  // every thread's records are visible device-wide before the tile is counted
+  __syncthreads();  // (and the stages are reused by the next item)
+}
+
+template <int D>
+__device__ void batch_reduce(const BatchMesh& M, int64_t r) {
+  const int64_t v0 = r * kRedVerts;
+  const int64_t v1 = v0 + kRedVerts < M.n_vert ? v0 + kRedVerts : M.n_vert;
+  for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int32_t b = M.voff[v], e = M.voff[v + 1];
+    float acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int32_t k = b; k < e; ++k) {
+      const int64_t rr = M.vrec[k];
+#pragma unroll
+      for (int a = 0; a < D; ++a) acc[a] += __ldcg(M.records + rr * D + a);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) M.dcoords[v * D + a] = acc[a];
+  }
+}
+
+__global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* __restrict__ desc, int n_items,
+                                                               int64_t n_tile_items, int64_t n_total,
+                                                               BatchCounters* ctr, int phases, int chunk,
+                                                               size_t stage_bytes) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ long long s_item;
+  int err = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr->next, (unsigned long long)chunk);
+    __syncthreads();
+    const int64_t i0 = s_item;
+    __syncthreads();  // s_item is rewritten at the next grab
+    if (i0 >= n_total) break;
+    const int64_t i1 = i0 + chunk < n_total ? i0 + chunk : n_total;
+    for (int64_t it = i0; it < i1; ++it) {
+      if (it < n_tile_items) {
+        const int m = find_mesh(desc, n_items, it, false);
+        const BatchMesh& M = desc[m];
+        const int64_t T = it - M.tile_begin;
+        switch (M.kind) {
+          case 0: batch_tile<2, LAPLACE_P1>(M, T, phases, smem_raw, stage_bytes, err); break;
+          case 1: batch_tile<2, LAPLACE_P2>(M, T, phases, smem_raw, stage_bytes, err); break;
+          case 2: batch_tile<2, ELASTIC_P1>(M, T, phases, smem_raw, stage_bytes, err); break;
+          case 3: batch_tile<3, LAPLACE_P1>(M, T, phases, smem_raw, stage_bytes, err); break;
+          case 4: batch_tile<3, LAPLACE_P2>(M, T, phases, smem_raw, stage_bytes, err); break;
+          default: batch_tile<3, ELASTIC_P1>(M, T, phases, smem_raw, stage_bytes, err); break;
+        }
+        if (threadIdx.x == 0) atomicAdd(&ctr->done[m], 1);
+      } else {
+        const int64_t ir = it - n_tile_items;
+        const int m = find_mesh(desc, n_items, ir, true);
+        const BatchMesh& M = desc[m];
+        if (threadIdx.x == 0) {
+          const volatile int32_t* done = ctr->done + m;
+          uint32_t spins = 0;
+          while (*done < M.n_tiles && spins < kSpinLimit) {
+            __nanosleep(64);
+            ++spins;
+          }
+          if (*done < M.n_tiles) atomicOr(&ctr->err, DEVERR_TIMEOUT);
+          __threadfence();
+        }
+        __syncthreads();
+        if (M.kind < 3)
+          batch_reduce<2>(M, ir - M.red_begin);
+        else
+          batch_reduce<3>(M, ir - M.red_begin);
+        __syncthreads();
+      }
+    }
+  }
+  err = __reduce_or_sync(0xffffffffu, err);
+  if (err && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, err);
+}
+
+template <int D, int FORM>
+size_t kind_stage_bytes() {
+  return batch_stage_bytes<D, FORM>();
+}
+
+size_t stage_bytes_for_kind(int kind) {
+  switch (kind) {
+    case 0: return kind_stage_bytes<2, LAPLACE_P1>();
+    case 1: return kind_stage_bytes<2, LAPLACE_P2>();
+    case 2: return kind_stage_bytes<2, ELASTIC_P1>();
+    case 3: return kind_stage_bytes<3, LAPLACE_P1>();
+    case 4: return kind_stage_bytes<3, LAPLACE_P2>();
+    default: return kind_stage_bytes<3, ELASTIC_P1>();
+  }
+}
+
+}  // namespace fem
+
+// ------------------------------------------------------------------ host side
+
+struct fem_batch {
+  int n_items = 0;
+  std::vector<fem::BatchMesh> desc;
+  fem::BatchMesh* d_desc = nullptr;
+  fem::BatchCounters* d_ctr = nullptr;
+  size_t ctr_bytes = 0;
+  int64_t n_tile_items = 0, n_total_fwd = 0, n_total = 0;
+  size_t stage_bytes = 0, smem = 0;
+  int ctas_per_sm = 0, chunk = 1, max_ctas_per_sm = 1;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+fem_status check_items(const fem_batch_item* items, int32_t n) {
+  if (!items || n <= 0) {
+    fem::set_last_error("items must be a non-empty array");
+    return FEM_ERR_ARG;
+  }
+  for (int i = 0; i < n; ++i) {
+    const fem_batch_item& it = items[i];
+    const fem_mesh& m = it.mesh;
+    if ((m.dim != 2 && m.dim != 3) || m.coord_dtype != FEM_F32 || m.n_elem < 0 || m.n_vert < 0 ||
+        m.n_vert > INT32_MAX || (m.n_elem > 0 && (!m.conn || !m.coords))) {
+      fem::set_last_error("batch item %d: invalid mesh (dim 2/3, FP32 coordinates, non-NULL arrays)", i);
+      return FEM_ERR_ARG;
+    }
+    if (it.form < FEM_LAPLACE_P1 || it.form > FEM_ELASTIC_P1 || it.reserved != 0) {
+      fem::set_last_error("batch item %d: invalid form or reserved field", i);
+      return FEM_ERR_ARG;
+    }
+    if (m.n_elem * (m.dim + 1) > INT32_MAX) {
+      fem::set_last_error("batch item %d: n_elem * (dim + 1) exceeds the int32 slot range", i);
+      return FEM_ERR_UNSUPPORTED;
+    }
+  }
+  return FEM_OK;
+}
+
+size_t item_ws_bytes(const fem_batch_item& it) {
+  if (!it.dcoords) return 0;
+  return fem::bwd_workspace_layout(it.mesh.dim, it.mesh.n_elem, it.mesh.n_vert, true, nullptr, nullptr);
+}
+
+size_t head_bytes(int32_t n, size_t* ctr_off, size_t* ctr_bytes) {
+  const size_t desc_bytes = al256(sizeof(fem::BatchMesh) * size_t(n));
+  *ctr_off = desc_bytes;
+  *ctr_bytes = al256(offsetof(fem::BatchCounters, done) + sizeof(int32_t) * size_t(n));
+  return desc_bytes + *ctr_bytes;
+}
+
+cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
+  int64_t grid = int64_t(ctas_per_sm) * fem::device_sm_count();
+  const int64_t need = (total + chunk - 1) / chunk;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  fem::fem_batch_kernel<<<unsigned(grid), fem::kTileElems, b->smem, st>>>(
+      b->d_desc, b->n_items, b->n_tile_items, total, b->d_ctr, phases, chunk, b->stage_bytes);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+fem_status fem_batch_workspace_size(const fem_batch_item* items, int32_t n_items, size_t* bytes) {
+  fem_status s = check_items(items, n_items);
+  if (s != FEM_OK) return s;
+  if (!bytes) {
+    fem::set_last_error("bytes is NULL");
+    return FEM_ERR_ARG;
+  }
+  size_t co, cb;
+  size_t total = head_bytes(n_items, &co, &cb);
+  for (int i = 0; i < n_items; ++i) total += al256(item_ws_bytes(items[i]));
+  *bytes = total;
+  return FEM_OK;
+}
+
+fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* ws, size_t ws_bytes,
+                            fem_batch** out, void* stream) {
+  fem_status s = check_items(items, n_items);
+  if (s != FEM_OK) return s;
+  if (!out) {
+    fem::set_last_error("out is NULL");
+    return FEM_ERR_ARG;
+  }
+  size_t need = 0;
+  fem_batch_workspace_size(items, n_items, &need);
+  if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    fem::set_last_error("batch workspace needs %zu bytes, 256-byte aligned (got %zu)", need, ws_bytes);
+    return FEM_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fem_batch* b = new (std::nothrow) fem_batch();
+  if (!b) {
+    fem::set_last_error("out of host memory");
+    return FEM_ERR_ARG;
+  }
+  b->n_items = n_items;
+  b->desc.resize(size_t(n_items));
+  size_t ctr_off = 0;
+  size_t off = head_bytes(n_items, &ctr_off, &b->ctr_bytes);
+  char* base = static_cast<char*>(ws);
+  b->d_desc = reinterpret_cast<fem::BatchMesh*>(base);
+  b->d_ctr = reinterpret_cast<fem::BatchCounters*>(base + ctr_off);
+  int64_t tiles = 0, reds = 0;
+  size_t stage = 0;
+  for (int i = 0; i < n_items; ++i) {
+    const fem_batch_item& it = items[i];
+    fem::BatchMesh& M = b->desc[size_t(i)];
+    std::memset(&M, 0, sizeof(M));
+    M.kind = (it.mesh.dim - 2) * 3 + it.form;
+    M.n_elem = it.mesh.n_elem;
+    M.n_vert = it.mesh.n_vert;
+    M.conn = it.mesh.conn;
+    M.coords = static_cast<const float*>(it.mesh.coords);
+    M.coef = it.coef;
+    M.dA = it.dA;
+    M.A = it.A;
+    M.dcoords = it.dcoords;
+    M.dcoef = it.dcoef;
+    M.flags = (it.A ? fem::BM_FWD : 0) | ((it.dA && (it.dcoords || it.dcoef)) ? fem::BM_BWD : 0) |
+              ((it.dA && it.dcoords) ? fem::BM_REC : 0);
+    M.n_tiles = (M.n_elem + fem::kTileElems - 1) / fem::kTileElems;
+    M.tile_begin = tiles;
+    tiles += M.n_tiles;
+    stage = std::max(stage, fem::stage_bytes_for_kind(M.kind));
+    const size_t wsb = item_ws_bytes(it);
+    if (wsb) {
+      fem::BwdWorkspace W{};
+      fem::bwd_workspace_layout(it.mesh.dim, it.mesh.n_elem, it.mesh.n_vert, true, base + off, &W);
+      cudaError_t e = fem::launch_incidence_build(it.mesh.dim, it.mesh.conn, it.mesh.n_elem, it.mesh.n_vert, W, st);
+      if (e != cudaSuccess) {
+        delete b;
+        fem::set_last_error("batch item %d: incidence build: %s", i, cudaGetErrorString(e));
+        return FEM_ERR_CUDA;
+      }
+      M.tile_rec = W.tile_rec;
+      M.sorted = W.sorted;
+      M.rec_end = W.rec_end;
+      M.voff = W.voff;
+      M.vrec = W.vrec;
+      M.records = W.records;
+      off += al256(wsb);
+    }
+  }
+  for (int i = 0; i < n_items; ++i) {  // reduction items follow all tiles
+    fem::BatchMesh& M = b->desc[size_t(i)];
+    M.n_red = (M.flags & fem::BM_REC) ? (M.n_vert + fem::kRedVerts - 1) / fem::kRedVerts : 0;
+    M.red_begin = reds;
+    reds += M.n_red;
+  }
+  b->n_tile_items = tiles;
+  b->n_total_fwd = tiles;
+  b->n_total = tiles + reds;
+  b->stage_bytes = stage;
+  b->smem = 4 * stage + fem::kXsBytes + fem::kSortedBytes + fem::kEndsBytes;
+  cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(fem::BatchMesh) * size_t(n_items),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = fem::ensure_smem(reinterpret_cast<const void*>(fem::fem_batch_kernel), b->smem);
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fem::fem_batch_kernel, fem::kTileElems, b->smem);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table must outlive the copy
+  if (e != cudaSuccess) {
+    delete b;
+    fem::set_last_error("fem_batch_create: %s", cudaGetErrorString(e));
+    return FEM_ERR_CUDA;
+  }
+  b->max_ctas_per_sm = occ > 0 ? occ : 1;
+  b->ctas_per_sm = b->max_ctas_per_sm;
+  b->chunk = 1;
+  *out = b;
+  return FEM_OK;
+}
+
+fem_status fem_batch_run(fem_batch* b, int32_t phases, void* stream) {
+  if (!b || (phases & ~(FEM_PHASE_FWD | FEM_PHASE_BWD)) || !phases) {
+    fem::set_last_error("fem_batch_run: bad batch or phases");
+    return FEM_ERR_ARG;
+  }
+  cudaError_t e = launch_batch(b, phases, b->ctas_per_sm, b->chunk, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    fem::set_last_error("fem_batch_run: %s", cudaGetErrorString(e));
+    return FEM_ERR_CUDA;
+  }
+  return FEM_OK;
+}
+
+fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
+  if (!b || (phases & ~(FEM_PHASE_FWD | FEM_PHASE_BWD)) || !phases) {
+    fem::set_last_error("fem_batch_tune: bad batch or phases");
+    return FEM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    fem::set_last_error("fem_batch_tune: event creation failed");
+    return FEM_ERR_CUDA;
+  }
+  float best = 1e30f;
+  int best_c = b->ctas_per_sm, best_k = b->chunk;
+  const int chunks[] = {1, 2, 4, 8};
+  cudaError_t err = cudaSuccess;
+  for (int c = 1; c <= b->max_ctas_per_sm && err == cudaSuccess; ++c)
+    for (int k : chunks) {
+      err = launch_batch(b, phases, c, k, st);  // warm-up
+      float ms_best = 1e30f;
+      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+        cudaEventRecord(e0, st);
+        err = launch_batch(b, phases, c, k, st);
+        cudaEventRecord(e1, st);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        ms_best = std::min(ms_best, ms);
+      }
+      if (err != cudaSuccess) break;
+      if (ms_best < best) {
+        best = ms_best;
+        best_c = c;
+        best_k = k;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    fem::set_last_error("fem_batch_tune: %s", cudaGetErrorString(err));
+    return FEM_ERR_CUDA;
+  }
+  b->ctas_per_sm = best_c;
+  b->chunk = best_k;
+  return FEM_OK;
+}
+
+fem_status fem_batch_config(const fem_batch* b, int32_t* ctas_per_sm, int32_t* chunk) {
+  if (!b) {
+    fem::set_last_error("batch is NULL");
+    return FEM_ERR_ARG;
+  }
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  if (chunk) *chunk = b->chunk;
+  return FEM_OK;
+}
+
+fem_status fem_batch_errors(const fem_batch* b, int32_t* err_host, void* stream) {
+  if (!b || !err_host) {
+    fem::set_last_error("fem_batch_errors: NULL argument");
+    return FEM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(err_host, &b->d_ctr->err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    fem::set_last_error("fem_batch_errors: %s", cudaGetErrorString(e));
+    return FEM_ERR_CUDA;
+  }
+  return FEM_OK;
+}
+
+void fem_batch_destroy(fem_batch* b) { delete b; }
+
+}  // extern "C"

@@ -30,7 +30,7 @@
 namespace fem {
 
 enum JacMode : int { JAC_F64 = 1, JAC_COMP = 2, JAC_F32 = 3 };
-enum DevErr : int { DEVERR_CONN = 1, DEVERR_DEGENERATE = 2 };
+enum DevErr : int { DEVERR_CONN = 1, DEVERR_DEGENERATE = 2, DEVERR_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- error-free transforms
 // The _rn intrinsics are never contracted into FMAs or reordered by the compiler.
