@@ -461,6 +461,127 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def _sample_err(orc, dim, form, mesh, coef, A_dev, idx):
+    Ar, _ = orc.integrate(dim, form, mesh.conn[idx], mesh.coords, None if coef is None else coef[idx])
+    import torch
+    Ag = A_dev[torch.from_numpy(idx).to(A_dev.device)].double().cpu().numpy()
+    num = np.abs(Ag - Ar).reshape(len(idx), -1).max(1)
+    return float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())
+
+
+def run_elastic(args):
+    """Symmetric-gradient elasticity on the 128^3 sliver cube with a lognormal
+    coefficient: FP32 sparse contraction vs split-BF16 tensor-core contraction."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh = mg.workload_tet_slivers(args.mesh_n, 2)
+    coef_h = mg.lognormal_coef(mg.rng_for(3), mesh.n_elem)
+    E, V = mesh.n_elem, mesh.n_vert
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    coef = torch.from_numpy(coef_h).to(dev)
+    A = torch.empty((E, 12, 12), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, contract in (("fp32_sparse", fem.CONTRACT_F32), ("bf16x3_tensor_core", fem.CONTRACT_BF16X3)):
+        def step():
+            fem.integrate_fwd(coords, conn, fem.ELASTIC_P1, coef, out=A, contract=contract)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.steps
+        rng = np.random.default_rng(7)
+        idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 20000, replace=False),
+                                        rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
+        err = _sample_err(oracle, 3, fem.ELASTIC_P1, mesh, coef_h, A, idx)
+        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "max_rel_err_vs_fp64": err}
+    byts = algorithmic_bytes(E, V, 0, 12, 3, True)["fwd"]
+    peak, peak_kind = hbm_peak()
+    best = min(res, key=lambda k: res[k]["ms"])
+    for k in res:
+        res[k]["GB/s"] = byts / (res[k]["ms"] * 1e-3) / 1e9
+        res[k]["frac_of_peak"] = res[k]["GB/s"] / peak
+    out = {"metric": METRIC, "value": E / (res[best]["ms"] * 1e-3), "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[best]["ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"P1 symmetric-gradient elasticity, {args.mesh_n}^3 Kuhn cube with 5% slivers "
+                                  f"({E:,} tets), lognormal coefficient, 12x12 FP32 element matrices, forward",
+                      "elements": E, "l2": "no flush: 7.5 GB moved per step"},
+           "roofline": {"bound": "hbm", "kernel": best, "achieved": res[best]["GB/s"], "peak": peak, "unit": "GB/s",
+                        "frac": res[best]["frac_of_peak"], "peak_kind": f"{peak_kind} copy bandwidth",
+                        "traffic": None, "algorithmic_bytes": byts},
+           "paths": res, "gpu_launches": args.steps}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint64(args):
+    """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
+    lognormal coefficient (dcoords and dcoef), both reductions."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh = mg.workload_tet_slivers(64, k=4)
+    E, V = mesh.n_elem, mesh.n_vert
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    coef = torch.from_numpy(mg.lognormal_coef(mg.rng_for(50), E)).to(dev)
+    dA = torch.from_numpy(mg.upstream(mg.rng_for(51), E, 4)).to(dev)
+    A = torch.empty((E, 4, 4), device=dev)
+    dx = torch.empty((V, 3), device=dev)
+    dw = torch.empty(E, device=dev)
+    ws = fem.Workspace(coords, conn)
+    nt = (E + 127) // 128
+    R = int(ws.buf[4 * nt: 4 * nt + 4].view(torch.int32).item())
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, reduce in (("deterministic", fem.REDUCE_DETERMINISTIC), ("atomic", fem.REDUCE_ATOMIC)):
+        def step():
+            fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, coef, out=A)
+            fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, coef, ws=ws, reduce=reduce, dcoords=dx, dcoef=dw)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.steps
+        b = algorithmic_bytes(E, V, R if reduce == 0 else 0, 4, 3, True)
+        byts = b["fwd"] + (b["bwd_elem"] + b["reduce"] if reduce == 0 else
+                           E * (64 + 16 + 4 + 4) + V * 12 * 2)
+        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9}
+    peak, peak_kind = hbm_peak()
+    d = res["deterministic"]
+    out = {"metric": METRIC, "value": d["elements_per_s"], "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": d["ms"], "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"P1 Laplacian forward + adjoint (dcoords, dcoef), 64^3 Kuhn cube with 5% "
+                                  f"slivers ({E:,} tets), lognormal coefficient, dA ~ N(0,1)",
+                      "elements": E, "l2": "working set ~0.5 GB, L2 not flushed"},
+           "roofline": {"bound": "hbm", "kernel": "step", "achieved": d["GB/s"], "peak": peak, "unit": "GB/s",
+                        "frac": d["GB/s"] / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None},
+           "reductions": res, "gpu_launches": 3 * args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     """The FP64 oracle timed on the host cores, bounded sample per step."""
     ws_n = int(os.environ.get("WORLD_SIZE", "1"))
@@ -510,8 +631,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
-    ap.add_argument("--workload", choices=["tet128", "batch96"], default="tet128",
-                    help="tet128: the headline 128^3 sliver cube; batch96: the mixed 96-mesh batch")
+    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64"], default="tet128",
+                    help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
+                         "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -520,6 +642,10 @@ def main():
         run_reference(args)
     elif args.workload == "batch96":
         run_batch(args)
+    elif args.workload == "elastic128":
+        run_elastic(args)
+    elif args.workload == "adjoint64":
+        run_adjoint64(args)
     else:
         run_ours(args)
 

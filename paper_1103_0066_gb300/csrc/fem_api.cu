@@ -147,8 +147,11 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   const bool cf64 = mesh->coord_dtype == FEM_F64, of64 = out_dtype == FEM_F64;
   if ((cf64 || of64) && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
     return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates or FP64 output need FEM_JAC_F64");
-  if (o->contract != FEM_CONTRACT_F32)
-    return fail(FEM_ERR_UNSUPPORTED, "tensor-core contraction is not available for this form/output");
+  const bool tc = o->contract == FEM_CONTRACT_BF16X3;
+  if (tc && (form == FEM_LAPLACE_P1 || cf64 || of64 || (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
+    return fail(FEM_ERR_UNSUPPORTED,
+                "the tensor-core contraction serves P2 and elasticity with FP32 coordinates and output "
+                "and the compensated Jacobian");
   fem::FwdLaunch L{};
   L.dim = mesh->dim;
   L.form = form;
@@ -166,7 +169,9 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   L.ctas_per_sm = o->ctas_per_sm;
   L.stream = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-  if (L.dim == 2)
+  if (tc)
+    e = fem::launch_fwd_tc(L);
+  else if (L.dim == 2)
     e = fem::launch_fwd_d2(L);
   else if (form == FEM_ELASTIC_P1)
     e = fem::launch_fwd_d3_ela(L);

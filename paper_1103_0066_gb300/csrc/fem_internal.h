@@ -79,6 +79,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
 cudaError_t launch_fwd_d2(const FwdLaunch& L);
 cudaError_t launch_fwd_d3_lap(const FwdLaunch& L);
 cudaError_t launch_fwd_d3_ela(const FwdLaunch& L);
+cudaError_t launch_fwd_tc(const FwdLaunch& L);  // split-bf16 tensor-core contraction
 cudaError_t launch_geometry(const GeoLaunch& L);
 cudaError_t launch_bwd_elem(const BwdLaunch& L);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,

@@ -124,3 +124,16 @@ def test_host_detected_errors(fem):
     assert b.value >= 4 * (101 + 40) + 4 * 10 * 4 * 3
     with pytest.raises(fem.FemError):
         fem.nat.fem_form_info(5, 3)
+
+
+def test_tensor_core_combinations_rejected_on_host(fem):
+    nat = fem.nat
+    lib = nat.load()
+    A = ctypes.c_void_p(0x3000)
+    m = _mesh(fem)
+    tc = nat.options_struct(contract=nat.CONTRACT_BF16X3)
+    # P1 Laplacian has no tensor-core path; FP64 output neither; nor a plain-FP32 Jacobian
+    assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 0, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 1, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
+    tc32 = nat.options_struct(jac=nat.JAC_F32, contract=nat.CONTRACT_BF16X3)
+    assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 0, ctypes.byref(tc32), None) == nat.FEM_ERR_UNSUPPORTED
