@@ -192,6 +192,34 @@ __device__ __forceinline__ void tc_store_a_row(unsigned char* sa, int m, const f
   }
 }
 
+// Writes the 16 accumulator columns of chunk C (unique entries t = 16C + q) to
+// both (i, j) and (j, i) of the element's stage row; indices are compile-time.
+template <int N, int NT, int C, int... Qs>
+__device__ __forceinline__ void tc_mirror_chunk(const float (&r)[16], float* row, std::integer_sequence<int, Qs...>) {
+  (
+      [&] {
+        constexpr int t = C * 16 + Qs;
+        if constexpr (t < NT) {
+          constexpr int i = tri_row(t, N), j = tri_col(t, N);
+          row[i * N + j] = r[Qs];
+          if constexpr (i != j) row[j * N + i] = r[Qs];
+        }
+      }(),
+      ...);
+}
+
+template <int D, int FORM, int C>
+__device__ __forceinline__ void tc_epilogue_chunks(uint32_t tl, float* row) {
+  using TP = TcPlan<D, FORM>;
+  if constexpr (C < TP::N / 16) {
+    float r[16];
+    tmem_ld16(tl + uint32_t(C * 16), r);
+    tmem_ld_wait();
+    tc_mirror_chunk<FormTraits<D, FORM>::N, TP::NT, C>(r, row, std::make_integer_sequence<int, 16>{});
+    tc_epilogue_chunks<D, FORM, C + 1>(tl, row);
+  }
+}
+
 template <int D, int FORM>
 __global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float, float> p) {
   using TP = TcPlan<D, FORM>;
@@ -283,22 +311,7 @@ __global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float,
     // epilogue: this warp's 32 rows of D -> mirrored stage -> coalesced stores
     float* st = reinterpret_cast<float*>(region) + warp * 32 * SST;
     float* row = st + lane * SST;
-    const uint32_t tl = tmem + (uint32_t(warp * 32) << 16);
-#pragma unroll
-    for (int c = 0; c < TP::N / 16; ++c) {
-      float r[16];
-      tmem_ld16(tl + uint32_t(c * 16), r);
-      tmem_ld_wait();
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int t = c * 16 + q;
-        if (t < TP::NT) {
-          const int i = tri_row(t, N), j = tri_col(t, N);
-          row[i * N + j] = r[q];
-          row[j * N + i] = r[q];
-        }
-      }
-    }
+    tc_epilogue_chunks<D, FORM, 0>(tmem + (uint32_t(warp * 32) << 16), row);
     __syncwarp();
     const int64_t e0 = T * kTileElems + warp * 32;
     if (e0 < p.n_elem) {
