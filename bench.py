@@ -427,6 +427,19 @@ def run_batch(args):
         graph_ms = timed(g1.replay, args.steps)
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
+        mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
+                      fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent"}
+        per_mode = {}
+        for mode in mode_names:  # each mode at full occupancy, chunk 1, in a CUDA graph
+            bt.set_config(32, 1, mode)
+            bt.run(stream=stream)
+            torch.cuda.synchronize()
+            gm = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gm, stream=stream):
+                bt.run(stream=stream)
+            per_mode[mode_names[mode]] = timed(gm.replay, args.steps)
+            del gm
+        bt.set_config(*cfg)
         bt.run(stream=stream)
         torch.cuda.synchronize()
         g2 = torch.cuda.CUDAGraph()
@@ -439,6 +452,8 @@ def run_batch(args):
         clk = clocks.stop()
         err = bt.errors(stream=stream)
     peak, peak_kind = hbm_peak()
+    kinds = {(it["src"].mesh.dim, it["form"]) for it in items if it["src"].mesh.n_elem > 0}
+    launches = 1 if cfg[2] == fem.BATCH_SINGLE else len(kinds)
     byts = batch_bytes(items)
     ach = byts / (batch_ms * 1e-3) / 1e9
     out = {
@@ -447,16 +462,18 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"96 meshes, element counts log-uniform in [1e3, 2e6] x {args.batch_scale}, "
                                "tri/tet x P1/P2 Laplacian/P1 elasticity, lognormal coefficient, forward + "
-                               "adjoint (deterministic), one persistent launch in a CUDA graph",
+                               "adjoint (deterministic), tuned persistent launch(es) in a CUDA graph",
                    "elements": E, "meshes": len(items),
                    "l2": "no flush: ~%.1f GB moved per step" % (byts / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "fem_batch_kernel", "achieved": ach, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": "fem_batch_kernel" if cfg[2] == fem.BATCH_SINGLE
+                     else "fem_batch_kind_kernel (all kinds)", "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},
-        "comparison_ms": {"per_mesh_eager": eager_ms, "per_mesh_graph": graph_ms, "batched_graph": batch_ms},
+        "comparison_ms": {"per_mesh_eager": eager_ms, "per_mesh_graph": graph_ms, "batched_graph": batch_ms,
+                          "batched_mode_untuned": per_mode},
         "speedup_vs_eager": eager_ms / batch_ms, "speedup_vs_graph": graph_ms / batch_ms,
-        "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1]},
-        "gpu_launches": 1 * args.steps, "device_errors": err, "clocks": clk,
+        "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": mode_names[cfg[2]]},
+        "gpu_launches": launches * args.steps, "device_errors": err, "clocks": clk,
     }
     print(json.dumps(out), flush=True)
 

@@ -177,14 +177,23 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
                                       float* dcoords, void* stream);
 
 /* ------------------------------------------------------------------ batches
- * Many meshes of uneven size and mixed forms integrated by ONE persistent
- * kernel launch (an addition beside the method; the batch notion of Sec. 4
- * is the paper's elementBatchSize within one mesh).  Persistent CTAs pull
- * work items from a global counter: first 128-element tiles of any mesh
- * (forward A and/or the adjoint's element pass), then per-mesh vertex ranges
- * of the deterministic reduction, each of which waits (bounded) for its
- * mesh's tiles.  fem_batch_run enqueues one memset and one kernel, so it can
- * be captured in a CUDA graph. */
+ * Many meshes of uneven size and mixed forms integrated by persistent kernel
+ * launches (an addition beside the method; the batch notion of Sec. 4 is the
+ * paper's elementBatchSize within one mesh).  Persistent CTAs pull work items
+ * from a global counter: first 128-element tiles (forward A and/or the
+ * adjoint's element pass), then per-mesh vertex ranges of the deterministic
+ * reduction, each of which waits (bounded) for its mesh's tiles.  Modes:
+ *   FEM_BATCH_SINGLE      one kernel over every mesh of every kind
+ *   FEM_BATCH_GROUPED     one kind-specialised, pipelined kernel per
+ *                         (dim, form) kind present, in order on `stream`
+ *   FEM_BATCH_GROUPED_CONCURRENT  the same kernels, the largest group on
+ *                         `stream` and the others forked onto side streams
+ *                         (event fork/join, so the whole run is still
+ *                         captured by a CUDA graph on `stream`)
+ * Every mode gives the same result bits as the per-mesh entry points. */
+#define FEM_BATCH_SINGLE 0
+#define FEM_BATCH_GROUPED 1
+#define FEM_BATCH_GROUPED_CONCURRENT 2
 
 #define FEM_PHASE_FWD 1 /* forward element matrices into item.A */
 #define FEM_PHASE_BWD 2 /* adjoint of item.dA into item.dcoords / item.dcoef */
@@ -217,16 +226,23 @@ FEM_API fem_status fem_batch_workspace_size(const fem_batch_item* items, int32_t
 FEM_API fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* ws, size_t ws_bytes,
                                     fem_batch** out, void* stream);
 
-/* Autotuner: times the persistent launch over candidate grids (CTAs per SM)
- * and work-chunk sizes with CUDA events on `stream` (synchronizing it) and
- * keeps the fastest for later fem_batch_run calls. */
+/* Autotuner: times every mode x grid (CTAs per SM, capped per kernel at its
+ * occupancy) x work-chunk size with CUDA events on `stream` (synchronizing
+ * it) and keeps the fastest for later fem_batch_run calls.  The tuning
+ * launches write the batch's outputs. */
 FEM_API fem_status fem_batch_tune(fem_batch* batch, int32_t phases, void* stream);
 
-/* The launch configuration in use (the tuner's choice, or the default). */
-FEM_API fem_status fem_batch_config(const fem_batch* batch, int32_t* ctas_per_sm, int32_t* chunk);
+/* The launch configuration in use (the tuner's choice, or the default:
+ * FEM_BATCH_GROUPED at full occupancy, chunk 1).  NULL outputs are skipped. */
+FEM_API fem_status fem_batch_config(const fem_batch* batch, int32_t* ctas_per_sm, int32_t* chunk, int32_t* mode);
 
-/* One persistent launch over every mesh of the batch for `phases`
- * (FEM_PHASE_FWD | FEM_PHASE_BWD).  Asynchronous; graph-capturable. */
+/* Sets the launch configuration: ctas_per_sm 1..32 (capped at each kernel's
+ * occupancy), chunk 1..64, mode FEM_BATCH_*; FEM_ERR_ARG otherwise. */
+FEM_API fem_status fem_batch_set_config(fem_batch* batch, int32_t ctas_per_sm, int32_t chunk, int32_t mode);
+
+/* The persistent launch(es) over every mesh of the batch for `phases`
+ * (FEM_PHASE_FWD | FEM_PHASE_BWD), preceded by one memset of the counters.
+ * Asynchronous; graph-capturable. */
 FEM_API fem_status fem_batch_run(fem_batch* batch, int32_t phases, void* stream);
 
 /* Device error word of the last fem_batch_run (FEM_DEVERR_* bits), copied

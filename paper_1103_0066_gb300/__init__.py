@@ -21,9 +21,10 @@ import torch
 from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
                       F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2,
-                      REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError)
+                      REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
+                      BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT)
 
-__all__ = ["Mesh", "Batch", "PHASE_FWD", "PHASE_BWD", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+__all__ = ["Mesh", "Batch", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
            "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
@@ -237,8 +238,12 @@ class Batch:
         return self.config()
 
     def config(self):
-        """(CTAs per SM, work-chunk size) used by run()."""
+        """(CTAs per SM, work-chunk size, mode) used by run(); mode is one of
+        BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT."""
         return nat.fem_batch_config(self.handle)
+
+    def set_config(self, ctas_per_sm, chunk, mode):
+        nat.fem_batch_set_config(self.handle, ctas_per_sm, chunk, mode)
 
     def run(self, phases=PHASE_FWD | PHASE_BWD, stream=None):
         nat.fem_batch_run(self.handle, phases, _stream_ptr(stream))

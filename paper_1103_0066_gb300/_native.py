@@ -25,9 +25,10 @@ DEVERR_CONN, DEVERR_DEGENERATE = 1, 2
 EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info",
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
            "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
-           "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_run",
+           "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_destroy")
 PHASE_FWD, PHASE_BWD = 1, 2
+BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT = 0, 1, 2
 DEVERR_TIMEOUT = 4
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -88,7 +89,8 @@ def load():
             "fem_batch_workspace_size": ([ctypes.POINTER(FemBatchItem), I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_batch_create": ([ctypes.POINTER(FemBatchItem), I32, P, SZ, ctypes.POINTER(P), P], ctypes.c_int),
             "fem_batch_tune": ([P, I32, P], ctypes.c_int),
-            "fem_batch_config": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
+            "fem_batch_config": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32), ctypes.POINTER(I32)], ctypes.c_int),
+            "fem_batch_set_config": ([P, I32, I32, I32], ctypes.c_int),
             "fem_batch_run": ([P, I32, P], ctypes.c_int),
             "fem_batch_errors": ([P, ctypes.POINTER(I32), P], ctypes.c_int),
             "fem_batch_destroy": ([P], None),
@@ -195,9 +197,13 @@ def fem_batch_tune(handle: int, phases: int, stream: int) -> None:
 
 
 def fem_batch_config(handle: int):
-    c, k = ctypes.c_int32(), ctypes.c_int32()
-    check(load().fem_batch_config(handle, ctypes.byref(c), ctypes.byref(k)))
-    return c.value, k.value
+    c, k, m = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    check(load().fem_batch_config(handle, ctypes.byref(c), ctypes.byref(k), ctypes.byref(m)))
+    return c.value, k.value, m.value
+
+
+def fem_batch_set_config(handle: int, ctas_per_sm: int, chunk: int, mode: int) -> None:
+    check(load().fem_batch_set_config(handle, ctas_per_sm, chunk, mode))
 
 
 def fem_batch_run(handle: int, phases: int, stream: int) -> None:

@@ -1,6 +1,6 @@
-// fem_batch.cu -- many meshes of mixed forms in one persistent launch.
+// fem_batch.cu -- many meshes of mixed forms in persistent launches.
 //
-// Work items, in dispensing order:
+// Single-kernel mode (FEM_BATCH_SINGLE).  Work items, in dispensing order:
 //   [0, n_tile_items)        one 128-element tile of some mesh: forward A
 //                            and/or the adjoint element pass with its records
 //   [n_tile_items, n_total)  a range of vertices of some mesh: the deterministic
@@ -12,6 +12,10 @@
 // is held by a running CTA and the wait ends; it is nevertheless bounded and
 // reports FEM_DEVERR_TIMEOUT when it gives up.  The per-tile code is the
 // per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, write_records).
+//
+// Grouped modes (FEM_BATCH_GROUPED, FEM_BATCH_GROUPED_CONCURRENT): the same
+// item scheme per (dim, form) kind, one kind-specialised pipelined kernel per
+// kind present, launched in order on one stream or forked onto side streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -43,13 +47,14 @@ struct BatchMesh {
   const int32_t* voff;
   const int32_t* vrec;
   float* records;
-  int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space
-  int64_t red_begin, n_red;     // reduction items
+  int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space (all meshes)
+  int64_t red_begin, n_red;     // reduction items (all meshes)
+  int64_t ktile_begin, kred_begin;  // the same within its kind group (grouped launches)
 };
 enum : int { BM_FWD = 1, BM_BWD = 2, BM_REC = 4 };
 
 struct BatchCounters {
-  unsigned long long next;
+  unsigned long long next[8];  // [0]: single-kernel launch, [1 + kind]: grouped launches
   int32_t err;
   int32_t pad;
   int32_t done[1];  // [n_items] tiles completed per mesh
@@ -69,11 +74,12 @@ constexpr size_t kXsBytes = align_up(size_t(kTileElems) * 4 * 4 * 4, 128);
 constexpr size_t kSortedBytes = align_up(size_t(kTileElems) * 4 * 2, 128);
 constexpr size_t kEndsBytes = align_up(size_t(kTileElems * 4 + 16) * 2, 128);
 
-__device__ __forceinline__ int find_mesh(const BatchMesh* desc, int n, int64_t item, bool red) {
+__device__ __forceinline__ int find_mesh(const BatchMesh* desc, int n, int64_t item, bool red, bool local = false) {
   int lo = 0, hi = n - 1;
   while (lo < hi) {  // last mesh whose range begins at or before `item`
     const int mid = (lo + hi + 1) >> 1;
-    const int64_t b = red ? desc[mid].red_begin : desc[mid].tile_begin;
+    const int64_t b = local ? (red ? desc[mid].kred_begin : desc[mid].ktile_begin)
+                            : (red ? desc[mid].red_begin : desc[mid].tile_begin);
     if (b <= item)
       lo = mid;
     else
@@ -182,7 +188,7 @@ __global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* 
   __shared__ long long s_item;
   int err = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr->next, (unsigned long long)chunk);
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(&ctr->next[0], (unsigned long long)chunk);
     __syncthreads();
     const int64_t i0 = s_item;
     __syncthreads();  // s_item is rewritten at the next grab
@@ -229,19 +235,263 @@ __global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* 
   if (err && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, err);
 }
 
+
+// ------------------------------------------------------------------ grouped launches
+// One persistent kernel per (dim, form) kind over that kind's meshes, with
+// registers and shared memory sized for the kind, the forward and the adjoint
+// element pass fused (one gather per element) and a two-deep item pipeline: the
+// next item's connectivity and coordinates (registers) and its dA, sorted slot
+// list and record ends (cp.async) are fetched while the current tile computes.
+
 template <int D, int FORM>
-size_t kind_stage_bytes() {
-  return batch_stage_bytes<D, FORM>();
+struct KindPlan {
+  using FP = FwdPlan<D, FORM, float, float>;
+  using BP = BwdPlan<D, FORM>;
+  static constexpr size_t da_slot = align_up(size_t(32) * BP::DST * 4, 128);
+  static constexpr size_t tail = BP::xs_bytes + BP::sorted_bytes + BP::ends_bytes;
+  // Two dA slots beside the forward stage while that keeps two CTAs per SM;
+  // otherwise (P2 and elasticity on tets) one slot that the forward stage
+  // aliases, filled after the forward tile.
+  static constexpr int DA_SLOTS = (4 * (FP::per_warp + 2 * da_slot) + tail <= size_t(100) * 1024) ? 2 : 1;
+  static constexpr size_t fst_bytes = DA_SLOTS == 2 ? FP::per_warp : 0;
+  static constexpr size_t per_warp =
+      DA_SLOTS == 2 ? FP::per_warp + 2 * da_slot : (FP::per_warp > da_slot ? FP::per_warp : da_slot);
+  static constexpr size_t smem = 4 * per_warp + tail;
+};
+
+template <int D>
+struct KindItem {
+  int m;       // mesh within the kind group
+  int64_t T;   // CTA tile within the mesh
+  int f;       // gather flags
+  float w;
+  int v[D + 1];
+  float X[D + 1][D];
+  int32_t rb, rn, eoff;
+};
+
+template <int D, int FORM>
+__device__ __forceinline__ void kind_prefetch(const BatchMesh* desc, int n, int64_t item, int phases, int s,
+                                              KindItem<D>& it, float* dslots, uint16_t* sbuf, uint16_t* ebuf) {
+  using KP = KindPlan<D, FORM>;
+  using BP = BwdPlan<D, FORM>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  it.m = find_mesh(desc, n, item, false, true);
+  const BatchMesh& M = desc[it.m];
+  it.T = item - M.ktile_begin;
+  const int64_t t = it.T * 4 + warp, e = t * 32 + lane;
+  const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
+  load_conn<D>(M.conn, e, M.n_elem, vec_conn, it.v);
+  it.f = gather_regs<D>(M.coords, M.n_vert, e, M.n_elem, it.v, it.X);
+  it.w = (M.coef && e < M.n_elem) ? __ldg(M.coef + e) : 1.f;
+  it.rb = it.rn = it.eoff = 0;
+  if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
+    if constexpr (KP::DA_SLOTS == 2) {
+      BwdParams bp;
+      bp.dA = M.dA;
+      bp.n_elem = M.n_elem;
+      bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+      copy_dA_async<D, FORM>(bp, t, lane, dslots + s * (KP::da_slot / 4));
+    }
+    if (M.flags & BM_REC) {
+      copy_sorted<BP::NS>(M.sorted, it.T, tid, sbuf + s * BP::NS);
+      it.rb = __ldg(M.tile_rec + it.T);
+      it.rn = __ldg(M.tile_rec + it.T + 1) - it.rb;
+      it.eoff = copy_ends<BP::ENDS>(M.rec_end, it.rb, it.rn, tid, ebuf + s * BP::ENDS);
+    }
+  }
+}
+
+template <int D, int FORM>
+__device__ __forceinline__ void kind_tile(const BatchMesh& M, const KindItem<D>& it, int phases, int s,
+                                          float* fst, float* dslots, float* xs, uint16_t* sbuf, uint16_t* ebuf,
+                                          int& err) {
+  using KP = KindPlan<D, FORM>;
+  using BP = BwdPlan<D, FORM>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t t = it.T * 4 + warp;
+  const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
+  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD)) {
+    FwdParams<float, float> fp;
+    fp.conn = M.conn;
+    fp.coords = M.coords;
+    fp.coef = M.coef;
+    fp.A = M.A;
+    fp.n_elem = M.n_elem;
+    fp.n_vert = M.n_vert;
+    fp.dev_err = nullptr;
+    fp.vec_conn = vec_conn;
+    fp.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
+    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fp, t, lane, it.f, it.w, it.X, fst);
+  }
+  if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
+    const bool rec = (M.flags & BM_REC) != 0;
+    BwdParams bp;
+    bp.conn = M.conn;
+    bp.coords = M.coords;
+    bp.coef = M.coef;
+    bp.dA = M.dA;
+    bp.tile_rec = rec ? M.tile_rec : nullptr;
+    bp.sorted = M.sorted;
+    bp.rec_end = M.rec_end;
+    bp.records = M.records;
+    bp.dcoef = M.dcoef;
+    bp.dcoords = nullptr;
+    bp.n_elem = M.n_elem;
+    bp.n_vert = M.n_vert;
+    bp.dev_err = nullptr;
+    bp.vec_conn = vec_conn;
+    bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+    float* dslot = dslots + (KP::DA_SLOTS == 2 ? s : 0) * (KP::da_slot / 4);
+    if constexpr (KP::DA_SLOTS == 1) {  // no room to prefetch: fetch now, into the forward stage
+      __syncwarp();
+      copy_dA_async<D, FORM>(bp, t, lane, dslot);
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncwarp();
+    }
+    err |= bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, it.f, it.w, it.X, dslot + lane * BP::DST, it.v,
+                                                      rec ? xs : nullptr, warp * 32 + lane);
+    if (rec) {
+      __syncthreads();
+      write_records<D>(sbuf + s * BP::NS, ebuf + s * BP::ENDS + it.eoff, xs, it.rb, it.rn, M.records, tid);
+    }
+  }
+  __threadfence();  // every thread's records are visible device-wide before the tile is counted
+  __syncthreads();
+}
+
+template <int D, int FORM>
+__global__ void __launch_bounds__(kTileElems)
+    fem_batch_kind_kernel(const BatchMesh* __restrict__ desc, int n, int m_base, int64_t n_tile_items,
+                          int64_t n_total, BatchCounters* ctr, int slot, int phases, int chunk) {
+  using KP = KindPlan<D, FORM>;
+  using BP = BwdPlan<D, FORM>;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ long long s_next;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  unsigned char* wbase = smem_raw + size_t(warp) * KP::per_warp;
+  float* fst = reinterpret_cast<float*>(wbase);
+  float* dslots = reinterpret_cast<float*>(wbase + KP::fst_bytes);
+  float* xs = reinterpret_cast<float*>(smem_raw + 4 * KP::per_warp);
+  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem_raw + 4 * KP::per_warp + BP::xs_bytes);
+  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem_raw + 4 * KP::per_warp + BP::xs_bytes + BP::sorted_bytes);
+  int err = 0;
+  auto grab = [&]() -> int64_t {
+    if (tid == 0) s_next = (long long)atomicAdd(&ctr->next[slot], (unsigned long long)chunk);
+    __syncthreads();
+    const int64_t g = s_next;
+    __syncthreads();
+    return g;
+  };
+  int64_t cur = grab();
+  int64_t cend = cur + chunk < n_total ? cur + chunk : n_total;
+  KindItem<D> a, b;
+  int s = 0;
+  if (cur < n_tile_items) kind_prefetch<D, FORM>(desc, n, cur, phases, 0, a, dslots, sbuf, ebuf);
+  cp_async_commit();
+  while (cur < n_total) {
+    int64_t nxt = cur + 1;
+    if (nxt >= cend) {
+      nxt = grab();
+      cend = nxt + chunk < n_total ? nxt + chunk : n_total;
+    }
+    if (nxt < n_tile_items) kind_prefetch<D, FORM>(desc, n, nxt, phases, s ^ 1, b, dslots, sbuf, ebuf);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();  // the current item's asynchronous copies (by all threads) are visible
+    if (cur < n_tile_items) {
+      kind_tile<D, FORM>(desc[a.m], a, phases, s, fst, dslots, xs, sbuf, ebuf, err);
+      if (tid == 0) atomicAdd(&ctr->done[m_base + a.m], 1);
+    } else {
+      const int64_t ir = cur - n_tile_items;
+      const int m = find_mesh(desc, n, ir, true, true);
+      const BatchMesh& M = desc[m];
+      __shared__ int s_timeout;
+      if (tid == 0) {
+        const volatile int32_t* done = ctr->done + m_base + m;
+        uint32_t spins = 0;
+        while (*done < M.n_tiles && spins < kSpinLimit) {
+          __nanosleep(64);
+          ++spins;
+        }
+        s_timeout = *done < M.n_tiles;
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_timeout) {
+        err |= DEVERR_TIMEOUT;
+      } else {
+        batch_reduce<D>(M, ir - M.kred_begin);
+      }
+      __syncthreads();
+    }
+    a = b;
+    s ^= 1;
+    cur = nxt;
+  }
+  cp_async_wait<0>();
+  err = __reduce_or_sync(0xffffffffu, err);
+  if (err && (threadIdx.x & 31) == 0) atomicOr(&ctr->err, err);
 }
 
 size_t stage_bytes_for_kind(int kind) {
   switch (kind) {
-    case 0: return kind_stage_bytes<2, LAPLACE_P1>();
-    case 1: return kind_stage_bytes<2, LAPLACE_P2>();
-    case 2: return kind_stage_bytes<2, ELASTIC_P1>();
-    case 3: return kind_stage_bytes<3, LAPLACE_P1>();
-    case 4: return kind_stage_bytes<3, LAPLACE_P2>();
-    default: return kind_stage_bytes<3, ELASTIC_P1>();
+    case 0: return batch_stage_bytes<2, LAPLACE_P1>();
+    case 1: return batch_stage_bytes<2, LAPLACE_P2>();
+    case 2: return batch_stage_bytes<2, ELASTIC_P1>();
+    case 3: return batch_stage_bytes<3, LAPLACE_P1>();
+    case 4: return batch_stage_bytes<3, LAPLACE_P2>();
+    default: return batch_stage_bytes<3, ELASTIC_P1>();
+  }
+}
+
+struct KindLaunch {
+  const BatchMesh* desc;
+  int n, m_base;
+  int64_t n_tile_items, n_total;
+  BatchCounters* ctr;
+  int slot, phases, chunk;
+  int64_t grid;
+};
+
+template <int D, int FORM>
+cudaError_t kind_setup_t(int* occ, size_t* smem) {
+  using KP = KindPlan<D, FORM>;
+  const void* fn = reinterpret_cast<const void*>(fem_batch_kind_kernel<D, FORM>);
+  cudaError_t e = ensure_smem(fn, KP::smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, fem_batch_kind_kernel<D, FORM>, kTileElems, KP::smem);
+  *smem = KP::smem;
+  return e;
+}
+
+template <int D, int FORM>
+cudaError_t kind_launch_t(const KindLaunch& L, cudaStream_t st) {
+  fem_batch_kind_kernel<D, FORM><<<unsigned(L.grid), kTileElems, KindPlan<D, FORM>::smem, st>>>(
+      L.desc, L.n, L.m_base, L.n_tile_items, L.n_total, L.ctr, L.slot, L.phases, L.chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t kind_setup(int kind, int* occ, size_t* smem) {
+  switch (kind) {
+    case 0: return kind_setup_t<2, LAPLACE_P1>(occ, smem);
+    case 1: return kind_setup_t<2, LAPLACE_P2>(occ, smem);
+    case 2: return kind_setup_t<2, ELASTIC_P1>(occ, smem);
+    case 3: return kind_setup_t<3, LAPLACE_P1>(occ, smem);
+    case 4: return kind_setup_t<3, LAPLACE_P2>(occ, smem);
+    default: return kind_setup_t<3, ELASTIC_P1>(occ, smem);
+  }
+}
+
+cudaError_t kind_launch(int kind, const KindLaunch& L, cudaStream_t st) {
+  switch (kind) {
+    case 0: return kind_launch_t<2, LAPLACE_P1>(L, st);
+    case 1: return kind_launch_t<2, LAPLACE_P2>(L, st);
+    case 2: return kind_launch_t<2, ELASTIC_P1>(L, st);
+    case 3: return kind_launch_t<3, LAPLACE_P1>(L, st);
+    case 4: return kind_launch_t<3, LAPLACE_P2>(L, st);
+    default: return kind_launch_t<3, ELASTIC_P1>(L, st);
   }
 }
 
@@ -251,13 +501,30 @@ size_t stage_bytes_for_kind(int kind) {
 
 struct fem_batch {
   int n_items = 0;
-  std::vector<fem::BatchMesh> desc;
+  std::vector<fem::BatchMesh> desc;   // caller's order (single-kernel mode)
+  std::vector<fem::BatchMesh> kdesc;  // grouped by kind, kind-local item ranges
   fem::BatchMesh* d_desc = nullptr;
+  fem::BatchMesh* d_kdesc = nullptr;
   fem::BatchCounters* d_ctr = nullptr;
   size_t ctr_bytes = 0;
   int64_t n_tile_items = 0, n_total_fwd = 0, n_total = 0;
   size_t stage_bytes = 0, smem = 0;
-  int ctas_per_sm = 0, chunk = 1, max_ctas_per_sm = 1;
+  int ctas_per_sm = 0, chunk = 1, max_ctas_per_sm = 1, mode = FEM_BATCH_SINGLE;
+  struct Group {
+    int kind, first, count;
+    int64_t n_tile_items, n_total, work;
+    int occ;
+  };
+  std::vector<Group> groups;  // non-empty kinds, largest work first
+  cudaStream_t aux[6] = {};
+  cudaEvent_t fork = nullptr, join[6] = {};
+  ~fem_batch() {
+    for (cudaStream_t s : aux)
+      if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+  }
 };
 
 namespace {
@@ -294,24 +561,71 @@ size_t item_ws_bytes(const fem_batch_item& it) {
   return fem::bwd_workspace_layout(it.mesh.dim, it.mesh.n_elem, it.mesh.n_vert, true, nullptr, nullptr);
 }
 
-size_t head_bytes(int32_t n, size_t* ctr_off, size_t* ctr_bytes) {
+// [descriptors, caller order][descriptors, grouped by kind][counters]
+size_t head_bytes(int32_t n, size_t* kdesc_off, size_t* ctr_off, size_t* ctr_bytes) {
   const size_t desc_bytes = al256(sizeof(fem::BatchMesh) * size_t(n));
-  *ctr_off = desc_bytes;
+  *kdesc_off = desc_bytes;
+  *ctr_off = 2 * desc_bytes;
   *ctr_bytes = al256(offsetof(fem::BatchCounters, done) + sizeof(int32_t) * size_t(n));
-  return desc_bytes + *ctr_bytes;
+  return 2 * desc_bytes + *ctr_bytes;
 }
 
-cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
-  if (e != cudaSuccess) return e;
-  const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
+int64_t grid_for(int ctas_per_sm, int64_t total, int chunk) {
   int64_t grid = int64_t(ctas_per_sm) * fem::device_sm_count();
   const int64_t need = (total + chunk - 1) / chunk;
   if (grid > need) grid = need;
-  if (grid < 1) grid = 1;
-  fem::fem_batch_kernel<<<unsigned(grid), fem::kTileElems, b->smem, st>>>(
-      b->d_desc, b->n_items, b->n_tile_items, total, b->d_ctr, phases, chunk, b->stage_bytes);
-  return cudaGetLastError();
+  return grid < 1 ? 1 : grid;
+}
+
+cudaError_t launch_group(fem_batch* b, const fem_batch::Group& g, int phases, int ctas_per_sm, int chunk,
+                         cudaStream_t st) {
+  const int64_t total = (phases & FEM_PHASE_BWD) ? g.n_total : g.n_tile_items;
+  if (total == 0) return cudaSuccess;
+  fem::KindLaunch L;
+  L.desc = b->d_kdesc + g.first;
+  L.n = g.count;
+  L.m_base = g.first;
+  L.n_tile_items = g.n_tile_items;
+  L.n_total = total;
+  L.ctr = b->d_ctr;
+  L.slot = 1 + g.kind;
+  L.phases = phases;
+  L.chunk = chunk;
+  L.grid = grid_for(std::min(ctas_per_sm, g.occ), total, chunk);
+  return fem::kind_launch(g.kind, L, st);
+}
+
+cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, int mode, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
+  if (e != cudaSuccess) return e;
+  if (mode == FEM_BATCH_SINGLE) {
+    const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
+    fem::fem_batch_kernel<<<unsigned(grid_for(ctas_per_sm, total, chunk)), fem::kTileElems, b->smem, st>>>(
+        b->d_desc, b->n_items, b->n_tile_items, total, b->d_ctr, phases, chunk, b->stage_bytes);
+    return cudaGetLastError();
+  }
+  if (mode == FEM_BATCH_GROUPED || b->groups.size() < 2) {
+    for (const auto& g : b->groups)
+      if ((e = launch_group(b, g, phases, ctas_per_sm, chunk, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  // concurrent: the largest group on `st`, the others forked onto side
+  // streams and joined back, so one group's tail overlaps the next ones
+  if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
+  for (size_t k = 1; k < b->groups.size(); ++k) {
+    if ((e = cudaStreamWaitEvent(b->aux[k], b->fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_group(b, b->groups[k], phases, ctas_per_sm, chunk, b->aux[k])) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->join[k], b->aux[k])) != cudaSuccess) return e;
+  }
+  if ((e = launch_group(b, b->groups[0], phases, ctas_per_sm, chunk, st)) != cudaSuccess) return e;
+  for (size_t k = 1; k < b->groups.size(); ++k)
+    if ((e = cudaStreamWaitEvent(st, b->join[k], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+bool valid_config(int ctas_per_sm, int chunk, int mode) {
+  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_GROUPED_CONCURRENT && chunk >= 1 && chunk <= 64 &&
+         ctas_per_sm >= 1 && ctas_per_sm <= 32;
 }
 
 }  // namespace
@@ -325,8 +639,8 @@ fem_status fem_batch_workspace_size(const fem_batch_item* items, int32_t n_items
     fem::set_last_error("bytes is NULL");
     return FEM_ERR_ARG;
   }
-  size_t co, cb;
-  size_t total = head_bytes(n_items, &co, &cb);
+  size_t ko, co, cb;
+  size_t total = head_bytes(n_items, &ko, &co, &cb);
   for (int i = 0; i < n_items; ++i) total += al256(item_ws_bytes(items[i]));
   *bytes = total;
   return FEM_OK;
@@ -354,10 +668,11 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   }
   b->n_items = n_items;
   b->desc.resize(size_t(n_items));
-  size_t ctr_off = 0;
-  size_t off = head_bytes(n_items, &ctr_off, &b->ctr_bytes);
+  size_t kdesc_off = 0, ctr_off = 0;
+  size_t off = head_bytes(n_items, &kdesc_off, &ctr_off, &b->ctr_bytes);
   char* base = static_cast<char*>(ws);
   b->d_desc = reinterpret_cast<fem::BatchMesh*>(base);
+  b->d_kdesc = reinterpret_cast<fem::BatchMesh*>(base + kdesc_off);
   b->d_ctr = reinterpret_cast<fem::BatchCounters*>(base + ctr_off);
   int64_t tiles = 0, reds = 0;
   size_t stage = 0;
@@ -411,21 +726,60 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   b->n_total = tiles + reds;
   b->stage_bytes = stage;
   b->smem = 4 * stage + fem::kXsBytes + fem::kSortedBytes + fem::kEndsBytes;
-  cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(fem::BatchMesh) * size_t(n_items),
-                                  cudaMemcpyHostToDevice, st);
+  // kind groups: the same descriptors ordered by kind, item ranges local to the kind
+  cudaError_t e = cudaSuccess;
+  for (int kind = 0; kind < 6 && e == cudaSuccess; ++kind) {
+    fem_batch::Group g{kind, int(b->kdesc.size()), 0, 0, 0, 0, 1};
+    int64_t kt = 0, kr = 0;
+    for (const auto& M0 : b->desc) {
+      if (M0.kind != kind) continue;
+      fem::BatchMesh M = M0;
+      M.ktile_begin = kt;
+      kt += M.n_tiles;
+      b->kdesc.push_back(M);
+      ++g.count;
+      g.work += M.n_elem;
+    }
+    for (int j = g.first; j < g.first + g.count; ++j) {
+      b->kdesc[size_t(j)].kred_begin = kr;
+      kr += b->kdesc[size_t(j)].n_red;
+    }
+    if (g.count == 0 || kt + kr == 0) continue;  // (meshes without elements still get dcoords = 0)
+    g.n_tile_items = kt;
+    g.n_total = kt + kr;
+    size_t ksmem = 0;
+    e = fem::kind_setup(kind, &g.occ, &ksmem);
+    g.occ = std::max(g.occ, 1);
+    b->groups.push_back(g);
+  }
+  std::stable_sort(b->groups.begin(), b->groups.end(),
+                   [](const fem_batch::Group& x, const fem_batch::Group& y) { return x.work > y.work; });
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; ++k) {
+    e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(fem::BatchMesh) * size_t(n_items), cudaMemcpyHostToDevice,
+                        st);
+  if (e == cudaSuccess && !b->kdesc.empty())
+    e = cudaMemcpyAsync(b->d_kdesc, b->kdesc.data(), sizeof(fem::BatchMesh) * b->kdesc.size(),
+                        cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = fem::ensure_smem(reinterpret_cast<const void*>(fem::fem_batch_kernel), b->smem);
   int occ = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fem::fem_batch_kernel, fem::kTileElems, b->smem);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host table must outlive the copy
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables must outlive the copies
   if (e != cudaSuccess) {
     delete b;
     fem::set_last_error("fem_batch_create: %s", cudaGetErrorString(e));
     return FEM_ERR_CUDA;
   }
   b->max_ctas_per_sm = occ > 0 ? occ : 1;
+  for (const auto& g : b->groups) b->max_ctas_per_sm = std::max(b->max_ctas_per_sm, g.occ);
   b->ctas_per_sm = b->max_ctas_per_sm;
   b->chunk = 1;
+  b->mode = b->groups.empty() ? FEM_BATCH_SINGLE : FEM_BATCH_GROUPED;
   *out = b;
   return FEM_OK;
 }
@@ -435,7 +789,7 @@ fem_status fem_batch_run(fem_batch* b, int32_t phases, void* stream) {
     fem::set_last_error("fem_batch_run: bad batch or phases");
     return FEM_ERR_ARG;
   }
-  cudaError_t e = launch_batch(b, phases, b->ctas_per_sm, b->chunk, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_batch(b, phases, b->ctas_per_sm, b->chunk, b->mode, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
     fem::set_last_error("fem_batch_run: %s", cudaGetErrorString(e));
     return FEM_ERR_CUDA;
@@ -455,29 +809,33 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
     return FEM_ERR_CUDA;
   }
   float best = 1e30f;
-  int best_c = b->ctas_per_sm, best_k = b->chunk;
+  int best_c = b->ctas_per_sm, best_k = b->chunk, best_m = b->mode;
   const int chunks[] = {1, 2, 4, 8};
   cudaError_t err = cudaSuccess;
-  for (int c = 1; c <= b->max_ctas_per_sm && err == cudaSuccess; ++c)
-    for (int k : chunks) {
-      err = launch_batch(b, phases, c, k, st);  // warm-up
-      float ms_best = 1e30f;
-      for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
-        cudaEventRecord(e0, st);
-        err = launch_batch(b, phases, c, k, st);
-        cudaEventRecord(e1, st);
-        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        ms_best = std::min(ms_best, ms);
+  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_GROUPED_CONCURRENT && err == cudaSuccess; ++mode) {
+    if (mode != FEM_BATCH_SINGLE && b->groups.empty()) break;
+    for (int c = 1; c <= b->max_ctas_per_sm && err == cudaSuccess; ++c)
+      for (int k : chunks) {
+        err = launch_batch(b, phases, c, k, mode, st);  // warm-up
+        float ms_best = 1e30f;
+        for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
+          cudaEventRecord(e0, st);
+          err = launch_batch(b, phases, c, k, mode, st);
+          cudaEventRecord(e1, st);
+          if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (err == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+          ms_best = std::min(ms_best, ms);
+        }
+        if (err != cudaSuccess) break;
+        if (ms_best < best) {
+          best = ms_best;
+          best_c = c;
+          best_k = k;
+          best_m = mode;
+        }
       }
-      if (err != cudaSuccess) break;
-      if (ms_best < best) {
-        best = ms_best;
-        best_c = c;
-        best_k = k;
-      }
-    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) {
@@ -486,16 +844,31 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
   }
   b->ctas_per_sm = best_c;
   b->chunk = best_k;
+  b->mode = best_m;
   return FEM_OK;
 }
 
-fem_status fem_batch_config(const fem_batch* b, int32_t* ctas_per_sm, int32_t* chunk) {
+fem_status fem_batch_config(const fem_batch* b, int32_t* ctas_per_sm, int32_t* chunk, int32_t* mode) {
   if (!b) {
     fem::set_last_error("batch is NULL");
     return FEM_ERR_ARG;
   }
   if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
   if (chunk) *chunk = b->chunk;
+  if (mode) *mode = b->mode;
+  return FEM_OK;
+}
+
+fem_status fem_batch_set_config(fem_batch* b, int32_t ctas_per_sm, int32_t chunk, int32_t mode) {
+  if (!b || !valid_config(ctas_per_sm, chunk, mode)) {
+    fem::set_last_error("fem_batch_set_config: bad batch or configuration (ctas_per_sm 1..32, chunk 1..64, "
+                        "mode FEM_BATCH_*)");
+    return FEM_ERR_ARG;
+  }
+  if (mode != FEM_BATCH_SINGLE && b->groups.empty()) mode = FEM_BATCH_SINGLE;
+  b->ctas_per_sm = ctas_per_sm;
+  b->chunk = chunk;
+  b->mode = mode;
   return FEM_OK;
 }
 

@@ -1,6 +1,8 @@
-"""Batched mixed-mesh launch (-m gpu): one persistent kernel over many meshes
-of mixed forms must reproduce the per-mesh entry points and the oracle, be
-capturable in a CUDA graph, and survive autotuning."""
+"""Batched mixed-mesh launch (-m gpu): the persistent kernel over many meshes
+of mixed forms, in each mode (one kernel for all kinds; one kind-specialised
+kernel per kind, serial or forked onto side streams), must reproduce the
+per-mesh entry points bit for bit and the oracle, be capturable in a CUDA
+graph, and survive autotuning."""
 import numpy as np
 import pytest
 import torch
@@ -40,9 +42,21 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def test_batch_matches_per_mesh_and_oracle(gfem, orc):
+MODES = ["single", "grouped", "concurrent"]
+
+
+def _mode(gfem, name):
+    return {"single": gfem.BATCH_SINGLE, "grouped": gfem.BATCH_GROUPED,
+            "concurrent": gfem.BATCH_GROUPED_CONCURRENT}[name]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("chunk", [1, 3])
+def test_batch_matches_per_mesh_and_oracle(gfem, orc, mode, chunk):
     items = _items(scale=0.003)  # 96 meshes of ~3 to ~6,000 elements, all six kinds
     batch = gfem.Batch(items)
+    batch.set_config(batch.config()[0], chunk, _mode(gfem, mode))
+    assert batch.config()[1:] == (chunk, _mode(gfem, mode))
     batch.run(gfem.PHASE_FWD | gfem.PHASE_BWD)
     torch.cuda.synchronize()
     assert batch.errors() == 0
@@ -54,16 +68,18 @@ def test_batch_matches_per_mesh_and_oracle(gfem, orc):
         assert torch.equal(it["A"], A_ref), k             # same per-tile code, same bits
         assert torch.equal(it["dcoords"], dx_ref), k      # same records, same order
         assert torch.equal(it["dcoef"], dw_ref), k
-        if k % 8 == 0:  # oracle parity on a spread of meshes and kinds
+        if k % 8 == 0 and mode == "grouped" and chunk == 1:  # oracle parity on a spread of meshes and kinds
             Ar, fl = orc.integrate(dim, it["form"], src.mesh.conn, src.mesh.coords, src.coef)
             assert rel_err_per_element(it["A"].cpu().numpy(), Ar).max() <= TOL
             gx, gw = orc.integrate_vjp(dim, it["form"], src.mesh.conn, src.mesh.coords, src.dA, src.coef)
             assert _rel(it["dcoords"], gx) <= TOL and _rel(it["dcoef"], gw) <= TOL
 
 
-def test_batch_phases_separately(gfem):
+@pytest.mark.parametrize("mode", MODES)
+def test_batch_phases_separately(gfem, mode):
     items = _items(scale=0.002, n_meshes=24)
     batch = gfem.Batch(items)
+    batch.set_config(1, 2, _mode(gfem, mode))
     batch.run(gfem.PHASE_FWD)
     torch.cuda.synchronize()
     for it in items:
@@ -75,14 +91,18 @@ def test_batch_phases_separately(gfem):
         assert not torch.isnan(it["dcoords"]).any() and not torch.isnan(it["dcoef"]).any()
 
 
-def test_batch_graph_capture_and_tuning(gfem):
+@pytest.mark.parametrize("mode", ["tuned", "concurrent"])
+def test_batch_graph_capture_and_tuning(gfem, mode):
     items = _items(scale=0.002, n_meshes=48)
     batch = gfem.Batch(items)
     batch.run()
     torch.cuda.synchronize()
     ref = [(it["A"].clone(), it["dcoords"].clone()) for it in items]
     cfg = batch.tune()
-    assert cfg[0] >= 1 and cfg[1] >= 1
+    assert cfg[0] >= 1 and cfg[1] >= 1 and cfg[2] in (gfem.BATCH_SINGLE, gfem.BATCH_GROUPED,
+                                                       gfem.BATCH_GROUPED_CONCURRENT)
+    if mode == "concurrent":  # fork/join side streams inside the capture
+        batch.set_config(cfg[0], cfg[1], gfem.BATCH_GROUPED_CONCURRENT)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -110,3 +130,26 @@ def test_batch_argument_errors(gfem):
     b = ctypes.c_size_t()
     assert nat.load().fem_batch_workspace_size(arr, 1, ctypes.byref(b)) == nat.FEM_ERR_ARG
     assert nat.load().fem_batch_run(None, 3, None) == nat.FEM_ERR_ARG
+
+
+def test_batch_empty_meshes_and_single_kind(gfem):
+    """Meshes without elements, and a batch of one kind (one group, so the
+    concurrent mode has nothing to fork), in every mode."""
+    big = _items(scale=0.002, n_meshes=6)
+    keep = [it for it in big if it["form"] == 0 and it["src"].mesh.dim == 3][:1] or big[:1]
+    empty = {"coords": keep[0]["coords"], "conn": keep[0]["conn"][:0], "form": keep[0]["form"],
+             "coef": keep[0]["coef"][:0], "A": keep[0]["A"][:0], "dA": keep[0]["dA"][:0],
+             "dcoords": torch.zeros_like(keep[0]["dcoords"]), "dcoef": keep[0]["dcoef"][:0]}
+    items = [empty] + keep + [dict(empty, dcoords=torch.zeros_like(keep[0]["dcoords"]))]
+    it = keep[0]
+    A_ref = gfem.integrate_fwd(it["coords"], it["conn"], it["form"], it["coef"])
+    dx_ref, _ = gfem.integrate_bwd(it["coords"], it["conn"], it["form"], it["dA"], it["coef"])
+    for mode in MODES:
+        batch = gfem.Batch(items)
+        batch.set_config(2, 1, _mode(gfem, mode))
+        it["A"].fill_(float("nan"))
+        batch.run()
+        torch.cuda.synchronize()
+        assert batch.errors() == 0
+        assert torch.equal(it["A"], A_ref) and torch.equal(it["dcoords"], dx_ref)
+        assert (items[0]["dcoords"] == 0).all() and (items[2]["dcoords"] == 0).all()  # no tiles: sum of nothing
