@@ -19,7 +19,6 @@ from __future__ import annotations
 
 import argparse
 import hashlib
-import glob
 import json
 import os
 import statistics
@@ -36,21 +35,29 @@ sys.path.insert(0, ROOT)
 METRIC = "elements/s & HBM GB/s vs peak, fwd and fwd+adjoint, at stated error vs FP64"
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch from one ncu capture, valid only while the kernel
-# sources hash to `src`; otherwise reported as null.
+# Sources each timed kernel is compiled from; a traffic figure is reported only
+# while the hash of its kernel's sources equals the one it was captured with.
+KERNEL_SOURCES = {
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": ("fem_fwd.cuh", "fem_fwd_d3_lap.cu", "fem_core.cuh", "fem_forms.cuh",
+                                              "fem_pipe.cuh", "fem_internal.h", "fem_geometry.cu"),
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": ("fem_bwd.cuh", "fem_bwd.cu", "fem_fwd.cuh", "fem_core.cuh",
+                                                   "fem_forms.cuh", "fem_pipe.cuh", "fem_internal.h",
+                                                   "fem_geometry.cu"),
+    "vertex_reduce_kernel<3>": ("fem_incidence.cu", "fem_internal.h"),
+}
+
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1268.0e6, "src": "157a37f5ec22c8ea"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 975.1e6, "src": "157a37f5ec22c8ea"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 187.3e6, "src": "157a37f5ec22c8ea"},
 }
 
 
-def csrc_hash() -> str:
+def kernel_src_hash(name: str) -> str:
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1103_0066_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
-            h.update(f.read())
+    for f in KERNEL_SOURCES[name]:
+        with open(os.path.join(ROOT, "paper_1103_0066_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -167,12 +174,12 @@ def tet_workload(n=128, k=2):
 def algorithmic_bytes(E, V, R, n, dim, coef):
     """Bytes each kernel must move (every input read once, every output written
     once, vertex arrays once).  R = records of the deterministic reduction (one
-    per distinct vertex of each 128-element tile)."""
+    per distinct vertex of each 32-element tile)."""
     nv = dim + 1
     fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0)) + V * 4 * dim
-    # dA, connectivity, the tile's sorted slot list (2 B/slot); record ends (2 B)
-    # and record sums (4 d B) written
-    bwd_elem = E * (4 * n * n + 4 * nv + 2 * nv + (8 if coef else 0)) + R * (2 + 4 * dim) + V * 4 * dim
+    # dA, connectivity, the slot ranks (one 4-byte word per element); record
+    # ends (1 B) read and record sums (4 d B) written
+    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0)) + R * (1 + 4 * dim) + V * 4 * dim
     # record sums and their vertex CSR read, dcoords written
     reduce = R * (4 * dim + 4) + V * (4 + 4 * dim)
     return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
@@ -268,16 +275,15 @@ def run_ours(args):
     per = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
            for i, name in enumerate(("fwd", "bwd_elem", "reduce"))}
 
-    n_tiles = (E + 127) // 128
-    R = int(ws.buf[4 * n_tiles: 4 * n_tiles + 4].view(torch.int32).item())  # records (tile_rec[n_tiles])
+    R = ws.n_records()
     byts = algorithmic_bytes(E, V, R, 4, 3, False)
     peak, peak_kind = hbm_peak()
     dom = max(per, key=per.get)
     kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
              "reduce": "vertex_reduce_kernel<3>"}
-    h = csrc_hash()
+    h = {k: kernel_src_hash(v) for k, v in kname.items()}
     tr = NCU_TRAFFIC.get(kname[dom])
-    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == h else None
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == h[dom] else None
     ach = byts[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -343,7 +349,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps},
         "gpu_launches": 3 * K,
         "clocks": clk,
-        "csrc_hash": h,
+        "kernel_src_hash": h,
     }
     if not e2e_steps:
         out["e2e"] = None
@@ -395,8 +401,7 @@ def run_batch(args):
     E = sum(it["src"].mesh.n_elem for it in items)
     wss = [fem.Workspace(it["coords"], it["conn"], it["form"]) for it in items]
     for it, ws in zip(items, wss):
-        nt = (it["src"].mesh.n_elem + 127) // 128
-        it["records"] = int(ws.buf[4 * nt: 4 * nt + 4].view(torch.int32).item())
+        it["records"] = ws.n_records()
     stream = torch.cuda.Stream(dev)
 
     def per_mesh():

@@ -108,6 +108,12 @@ class Workspace:
         self.buf = torch.empty(max(self.bytes, 1), dtype=torch.uint8, device=coords.device)
         nat.fem_incidence_build(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(stream))
 
+    def n_records(self) -> int:
+        """Records of the deterministic reduction: the first word past the
+        per-tile record offsets (32-element record tiles).  Synchronizes."""
+        T = (self.m.n_elem + 31) // 32
+        return int(self.buf[4 * T: 4 * T + 4].view(torch.int32).item())
+
 
 def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None,
                   reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dcoef=True, jac=JAC_AUTO,

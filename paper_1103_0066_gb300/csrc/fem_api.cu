@@ -282,8 +282,9 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     L.dcoef = dcoef;
     const bool recs = dcoords && !atomic;
     L.tile_rec = recs ? W.tile_rec : nullptr;
-    L.sorted = recs ? W.sorted : nullptr;
+    L.rank = recs ? W.rank : nullptr;
     L.rec_end = recs ? W.rec_end : nullptr;
+    L.rec_dest = recs ? W.rec_dest : nullptr;
     L.records = recs ? W.records : nullptr;
     L.dcoords = dcoords;
     L.n_elem = mesh->n_elem;

@@ -11,7 +11,7 @@
 // dispensing order and a CTA holding a tile never waits, so every awaited tile
 // is held by a running CTA and the wait ends; it is nevertheless bounded and
 // reports FEM_DEVERR_TIMEOUT when it gives up.  The per-tile code is the
-// per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, write_records).
+// per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, warp_records).
 //
 // Grouped modes (FEM_BATCH_GROUPED, FEM_BATCH_GROUPED_CONCURRENT): the same
 // item scheme per (dim, form) kind, one kind-specialised pipelined kernel per
@@ -41,12 +41,12 @@ struct BatchMesh {
   float* A;
   float* dcoords;
   float* dcoef;
-  const int32_t* tile_rec;
-  const uint16_t* sorted;
-  const uint16_t* rec_end;
+  const int32_t* tile_rec;  // per 32-element record tile
+  const uint32_t* rank;
+  const uint8_t* rec_end;
+  const int32_t* rec_dest;
   const int32_t* voff;
-  const int32_t* vrec;
-  float* records;
+  float* records;  // vertex-major
   int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space (all meshes)
   int64_t red_begin, n_red;     // reduction items (all meshes)
   int64_t ktile_begin, kred_begin;  // the same within its kind group (grouped launches)
@@ -63,16 +63,13 @@ struct BatchCounters {
 constexpr int kRedVerts = 2048;  // vertices per reduction item
 constexpr uint32_t kSpinLimit = 1u << 24;
 
-// Shared memory of one batch CTA: per-warp stage, then the tile's slot stage,
-// sorted slot list and record ends (sized for tets, which bound triangles).
+// Shared memory of one batch warp: a stage shared by the forward tile and the
+// dA rows, then the slot stage of the warp's records (sized for tets).
 template <int D, int FORM>
 constexpr size_t batch_stage_bytes() {
-  return std::max(FwdPlan<D, FORM, float, float>::per_warp,
-                  align_up(size_t(32) * BwdPlan<D, FORM>::DST * 4, 128));
+  return std::max(FwdPlan<D, FORM, float, float>::per_warp, BwdPlan<D, FORM>::da_slot);
 }
-constexpr size_t kXsBytes = align_up(size_t(kTileElems) * 4 * 4 * 4, 128);
-constexpr size_t kSortedBytes = align_up(size_t(kTileElems) * 4 * 2, 128);
-constexpr size_t kEndsBytes = align_up(size_t(kTileElems * 4 + 16) * 2, 128);
+constexpr size_t kXsWarpBytes = BwdPlan<3, LAPLACE_P1>::xs_bytes;
 
 __device__ __forceinline__ int find_mesh(const BatchMesh* desc, int n, int64_t item, bool red, bool local = false) {
   int lo = 0, hi = n - 1;
@@ -88,16 +85,82 @@ __device__ __forceinline__ int find_mesh(const BatchMesh* desc, int n, int64_t i
   return lo;
 }
 
+// Record range of the warp's 32-element tile t (rank word of its lane, first
+// record, record count); zeros past the mesh.
+struct WarpRec {
+  uint32_t rk;
+  int32_t rb, rn;
+};
+
+__device__ __forceinline__ WarpRec load_warp_rec(const BatchMesh& M, int64_t t, int lane) {
+  WarpRec r{0u, 0, 0};
+  if ((M.flags & BM_REC) && t * 32 < M.n_elem) {
+    r.rk = __ldg(M.rank + t * 32 + lane);
+    r.rb = __ldg(M.tile_rec + t);
+    r.rn = __ldg(M.tile_rec + t + 1) - r.rb;
+  }
+  return r;
+}
+
+__device__ __forceinline__ BwdParams bwd_params(const BatchMesh& M, int vec_conn) {
+  BwdParams bp;
+  bp.conn = M.conn;
+  bp.coords = M.coords;
+  bp.coef = M.coef;
+  bp.dA = M.dA;
+  bp.tile_rec = (M.flags & BM_REC) ? M.tile_rec : nullptr;
+  bp.rank = M.rank;
+  bp.rec_end = M.rec_end;
+  bp.rec_dest = M.rec_dest;
+  bp.records = M.records;
+  bp.dcoef = M.dcoef;
+  bp.dcoords = nullptr;
+  bp.n_elem = M.n_elem;
+  bp.n_vert = M.n_vert;
+  bp.dev_err = nullptr;
+  bp.vec_conn = vec_conn;
+  bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+  return bp;
+}
+
+__device__ __forceinline__ FwdParams<float, float> fwd_params(const BatchMesh& M, int vec_conn) {
+  FwdParams<float, float> fp;
+  fp.conn = M.conn;
+  fp.coords = M.coords;
+  fp.coef = M.coef;
+  fp.A = M.A;
+  fp.n_elem = M.n_elem;
+  fp.n_vert = M.n_vert;
+  fp.dev_err = nullptr;
+  fp.vec_conn = vec_conn;
+  fp.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
+  return fp;
+}
+
+// Adjoint element pass of one warp's tile and its records (dA already staged in drow_base).
+template <int D, int FORM>
+__device__ __forceinline__ int warp_bwd(const BatchMesh& M, const BwdParams& bp, int64_t t, int lane, int f, float w,
+                                        const float (&X)[D + 1][D], const int (&v)[D + 1], const float* dstage,
+                                        float* xs, const WarpRec& wr) {
+  const bool rec = (M.flags & BM_REC) != 0;
+  const RecAhead ah = rec ? load_rec_ahead(M.rec_end, M.rec_dest, wr.rb, wr.rn, lane) : RecAhead{0, 0};
+  const int err = bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, w, X,
+                                                            dstage + lane * BwdPlan<D, FORM>::DST, v,
+                                                            rec ? xs : nullptr, wr.rk);
+  if (rec) {
+    __syncwarp();
+    warp_records<D>(xs, M.rec_end, M.rec_dest, wr.rb, wr.rn, ah, M.records, lane);
+  }
+  return err;
+}
+
 template <int D, int FORM>
 __device__ void batch_tile(const BatchMesh& M, int64_t T, int phases, unsigned char* smem, size_t stage_bytes,
                            int& err) {
-  using BPL = BwdPlan<D, FORM>;
-  constexpr int NS = BPL::NS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* wst = reinterpret_cast<float*>(smem + size_t(warp) * stage_bytes);
-  float* xs = reinterpret_cast<float*>(smem + 4 * stage_bytes);
-  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem + 4 * stage_bytes + kXsBytes);
-  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem + 4 * stage_bytes + kXsBytes + kSortedBytes);
+  unsigned char* wbase = smem + size_t(warp) * (stage_bytes + kXsWarpBytes);
+  float* wst = reinterpret_cast<float*>(wbase);
+  float* xs = reinterpret_cast<float*>(wbase + stage_bytes);
   const int64_t t = T * 4 + warp, e = t * 32 + lane;
   const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
   int v[D + 1];
@@ -105,57 +168,17 @@ __device__ void batch_tile(const BatchMesh& M, int64_t T, int phases, unsigned c
   load_conn<D>(M.conn, e, M.n_elem, vec_conn, v);
   const int f = gather_regs<D>(M.coords, M.n_vert, e, M.n_elem, v, X);
   const float w = (M.coef && e < M.n_elem) ? __ldg(M.coef + e) : 1.f;
-  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD)) {
-    FwdParams<float, float> fp;
-    fp.conn = M.conn;
-    fp.coords = M.coords;
-    fp.coef = M.coef;
-    fp.A = M.A;
-    fp.n_elem = M.n_elem;
-    fp.n_vert = M.n_vert;
-    fp.dev_err = nullptr;
-    fp.vec_conn = vec_conn;
-    fp.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
-    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fp, t, lane, f, w, X, wst);
-  }
+  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD))
+    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fwd_params(M, vec_conn), t, lane, f, w, X, wst);
   if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
-    const bool rec = (M.flags & BM_REC) != 0;
-    BwdParams bp;
-    bp.conn = M.conn;
-    bp.coords = M.coords;
-    bp.coef = M.coef;
-    bp.dA = M.dA;
-    bp.tile_rec = rec ? M.tile_rec : nullptr;
-    bp.sorted = M.sorted;
-    bp.rec_end = M.rec_end;
-    bp.records = M.records;
-    bp.dcoef = M.dcoef;
-    bp.dcoords = nullptr;
-    bp.n_elem = M.n_elem;
-    bp.n_vert = M.n_vert;
-    bp.dev_err = nullptr;
-    bp.vec_conn = vec_conn;
-    bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+    const BwdParams bp = bwd_params(M, vec_conn);
+    const WarpRec wr = load_warp_rec(M, t, lane);
+    __syncwarp();  // the forward tile's stage reads are done
     copy_dA_async<D, FORM>(bp, t, lane, wst);
-    int32_t rb = 0, rn = 0, eoff = 0;
-    if (rec) {
-      copy_sorted<NS>(M.sorted, T, tid, sbuf);
-      rb = __ldg(M.tile_rec + T);
-      rn = __ldg(M.tile_rec + T + 1) - rb;
-      eoff = copy_ends<BPL::ENDS>(M.rec_end, rb, rn, tid, ebuf);
-    }
     cp_async_commit();
     cp_async_wait<0>();
-    if (rec)
-      __syncthreads();  // sorted list and record ends were copied by all threads
-    else
-      __syncwarp();
-    err |= bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, w, X, wst + lane * BPL::DST, v,
-                                                      rec ? xs : nullptr, warp * 32 + lane);
-    if (rec) {
-      __syncthreads();
-      write_records<D>(sbuf, ebuf + eoff, xs, rb, rn, M.records, tid);
-    }
+    __syncwarp();
+    err |= warp_bwd<D, FORM>(M, bp, t, lane, f, w, X, v, wst, xs, wr);
   }
   __threadfence();  // every thread's records are visible device-wide before the tile is counted
   __syncthreads();  // (and the stages are reused by the next item)
@@ -171,9 +194,8 @@ __device__ void batch_reduce(const BatchMesh& M, int64_t r) {
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = 0.f;
     for (int32_t k = b; k < e; ++k) {
-      const int64_t rr = M.vrec[k];
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] += __ldcg(M.records + rr * D + a);
+      for (int a = 0; a < D; ++a) acc[a] += __ldcg(M.records + int64_t(k) * D + a);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) M.dcoords[v * D + a] = acc[a];
@@ -240,23 +262,24 @@ __global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* 
 // One persistent kernel per (dim, form) kind over that kind's meshes, with
 // registers and shared memory sized for the kind, the forward and the adjoint
 // element pass fused (one gather per element) and a two-deep item pipeline: the
-// next item's connectivity and coordinates (registers) and its dA, sorted slot
-// list and record ends (cp.async) are fetched while the current tile computes.
+// next item's connectivity, coordinates, slot ranks and record range
+// (registers) and its dA (cp.async) are fetched while the current tile
+// computes.
 
 template <int D, int FORM>
 struct KindPlan {
   using FP = FwdPlan<D, FORM, float, float>;
   using BP = BwdPlan<D, FORM>;
-  static constexpr size_t da_slot = align_up(size_t(32) * BP::DST * 4, 128);
-  static constexpr size_t tail = BP::xs_bytes + BP::sorted_bytes + BP::ends_bytes;
+  static constexpr size_t da_slot = BP::da_slot;
   // Two dA slots beside the forward stage while that keeps two CTAs per SM;
   // otherwise (P2 and elasticity on tets) one slot that the forward stage
   // aliases, filled after the forward tile.
-  static constexpr int DA_SLOTS = (4 * (FP::per_warp + 2 * da_slot) + tail <= size_t(100) * 1024) ? 2 : 1;
+  static constexpr int DA_SLOTS = (4 * (FP::per_warp + 2 * da_slot + BP::xs_bytes) <= size_t(100) * 1024) ? 2 : 1;
   static constexpr size_t fst_bytes = DA_SLOTS == 2 ? FP::per_warp : 0;
-  static constexpr size_t per_warp =
+  static constexpr size_t stage =
       DA_SLOTS == 2 ? FP::per_warp + 2 * da_slot : (FP::per_warp > da_slot ? FP::per_warp : da_slot);
-  static constexpr size_t smem = 4 * per_warp + tail;
+  static constexpr size_t per_warp = stage + BP::xs_bytes;
+  static constexpr size_t smem = 4 * per_warp;
 };
 
 template <int D>
@@ -267,15 +290,14 @@ struct KindItem {
   float w;
   int v[D + 1];
   float X[D + 1][D];
-  int32_t rb, rn, eoff;
+  WarpRec wr;
 };
 
 template <int D, int FORM>
 __device__ __forceinline__ void kind_prefetch(const BatchMesh* desc, int n, int64_t item, int phases, int s,
-                                              KindItem<D>& it, float* dslots, uint16_t* sbuf, uint16_t* ebuf) {
+                                              KindItem<D>& it, float* dslots) {
   using KP = KindPlan<D, FORM>;
-  using BP = BwdPlan<D, FORM>;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   it.m = find_mesh(desc, n, item, false, true);
   const BatchMesh& M = desc[it.m];
   it.T = item - M.ktile_begin;
@@ -284,7 +306,7 @@ __device__ __forceinline__ void kind_prefetch(const BatchMesh* desc, int n, int6
   load_conn<D>(M.conn, e, M.n_elem, vec_conn, it.v);
   it.f = gather_regs<D>(M.coords, M.n_vert, e, M.n_elem, it.v, it.X);
   it.w = (M.coef && e < M.n_elem) ? __ldg(M.coef + e) : 1.f;
-  it.rb = it.rn = it.eoff = 0;
+  it.wr = WarpRec{0u, 0, 0};
   if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
     if constexpr (KP::DA_SLOTS == 2) {
       BwdParams bp;
@@ -293,55 +315,22 @@ __device__ __forceinline__ void kind_prefetch(const BatchMesh* desc, int n, int6
       bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
       copy_dA_async<D, FORM>(bp, t, lane, dslots + s * (KP::da_slot / 4));
     }
-    if (M.flags & BM_REC) {
-      copy_sorted<BP::NS>(M.sorted, it.T, tid, sbuf + s * BP::NS);
-      it.rb = __ldg(M.tile_rec + it.T);
-      it.rn = __ldg(M.tile_rec + it.T + 1) - it.rb;
-      it.eoff = copy_ends<BP::ENDS>(M.rec_end, it.rb, it.rn, tid, ebuf + s * BP::ENDS);
-    }
+    it.wr = load_warp_rec(M, t, lane);
   }
 }
 
 template <int D, int FORM>
 __device__ __forceinline__ void kind_tile(const BatchMesh& M, const KindItem<D>& it, int phases, int s,
-                                          float* fst, float* dslots, float* xs, uint16_t* sbuf, uint16_t* ebuf,
-                                          int& err) {
+                                          float* fst, float* dslots, float* xs, int& err) {
   using KP = KindPlan<D, FORM>;
-  using BP = BwdPlan<D, FORM>;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t t = it.T * 4 + warp;
   const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
-  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD)) {
-    FwdParams<float, float> fp;
-    fp.conn = M.conn;
-    fp.coords = M.coords;
-    fp.coef = M.coef;
-    fp.A = M.A;
-    fp.n_elem = M.n_elem;
-    fp.n_vert = M.n_vert;
-    fp.dev_err = nullptr;
-    fp.vec_conn = vec_conn;
-    fp.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
-    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fp, t, lane, it.f, it.w, it.X, fst);
-  }
+  if ((phases & FEM_PHASE_FWD) && (M.flags & BM_FWD))
+    err |= fwd_compute_tile<D, FORM, JAC_COMP, float, float>(fwd_params(M, vec_conn), t, lane, it.f, it.w, it.X,
+                                                             fst);
   if ((phases & FEM_PHASE_BWD) && (M.flags & BM_BWD)) {
-    const bool rec = (M.flags & BM_REC) != 0;
-    BwdParams bp;
-    bp.conn = M.conn;
-    bp.coords = M.coords;
-    bp.coef = M.coef;
-    bp.dA = M.dA;
-    bp.tile_rec = rec ? M.tile_rec : nullptr;
-    bp.sorted = M.sorted;
-    bp.rec_end = M.rec_end;
-    bp.records = M.records;
-    bp.dcoef = M.dcoef;
-    bp.dcoords = nullptr;
-    bp.n_elem = M.n_elem;
-    bp.n_vert = M.n_vert;
-    bp.dev_err = nullptr;
-    bp.vec_conn = vec_conn;
-    bp.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+    const BwdParams bp = bwd_params(M, vec_conn);
     float* dslot = dslots + (KP::DA_SLOTS == 2 ? s : 0) * (KP::da_slot / 4);
     if constexpr (KP::DA_SLOTS == 1) {  // no room to prefetch: fetch now, into the forward stage
       __syncwarp();
@@ -350,12 +339,7 @@ __device__ __forceinline__ void kind_tile(const BatchMesh& M, const KindItem<D>&
       cp_async_wait<0>();
       __syncwarp();
     }
-    err |= bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, it.f, it.w, it.X, dslot + lane * BP::DST, it.v,
-                                                      rec ? xs : nullptr, warp * 32 + lane);
-    if (rec) {
-      __syncthreads();
-      write_records<D>(sbuf + s * BP::NS, ebuf + s * BP::ENDS + it.eoff, xs, it.rb, it.rn, M.records, tid);
-    }
+    err |= warp_bwd<D, FORM>(M, bp, t, lane, it.f, it.w, it.X, it.v, dslot, xs, it.wr);
   }
   __threadfence();  // every thread's records are visible device-wide before the tile is counted
   __syncthreads();
@@ -366,16 +350,13 @@ __global__ void __launch_bounds__(kTileElems)
     fem_batch_kind_kernel(const BatchMesh* __restrict__ desc, int n, int m_base, int64_t n_tile_items,
                           int64_t n_total, BatchCounters* ctr, int slot, int phases, int chunk) {
   using KP = KindPlan<D, FORM>;
-  using BP = BwdPlan<D, FORM>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_next;
   const int tid = threadIdx.x, warp = tid >> 5;
   unsigned char* wbase = smem_raw + size_t(warp) * KP::per_warp;
   float* fst = reinterpret_cast<float*>(wbase);
   float* dslots = reinterpret_cast<float*>(wbase + KP::fst_bytes);
-  float* xs = reinterpret_cast<float*>(smem_raw + 4 * KP::per_warp);
-  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem_raw + 4 * KP::per_warp + BP::xs_bytes);
-  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem_raw + 4 * KP::per_warp + BP::xs_bytes + BP::sorted_bytes);
+  float* xs = reinterpret_cast<float*>(wbase + KP::stage);
   int err = 0;
   auto grab = [&]() -> int64_t {
     if (tid == 0) s_next = (long long)atomicAdd(&ctr->next[slot], (unsigned long long)chunk);
@@ -388,7 +369,7 @@ __global__ void __launch_bounds__(kTileElems)
   int64_t cend = cur + chunk < n_total ? cur + chunk : n_total;
   KindItem<D> a, b;
   int s = 0;
-  if (cur < n_tile_items) kind_prefetch<D, FORM>(desc, n, cur, phases, 0, a, dslots, sbuf, ebuf);
+  if (cur < n_tile_items) kind_prefetch<D, FORM>(desc, n, cur, phases, 0, a, dslots);
   cp_async_commit();
   while (cur < n_total) {
     int64_t nxt = cur + 1;
@@ -396,12 +377,12 @@ __global__ void __launch_bounds__(kTileElems)
       nxt = grab();
       cend = nxt + chunk < n_total ? nxt + chunk : n_total;
     }
-    if (nxt < n_tile_items) kind_prefetch<D, FORM>(desc, n, nxt, phases, s ^ 1, b, dslots, sbuf, ebuf);
+    if (nxt < n_tile_items) kind_prefetch<D, FORM>(desc, n, nxt, phases, s ^ 1, b, dslots);
     cp_async_commit();
     cp_async_wait<1>();
-    __syncthreads();  // the current item's asynchronous copies (by all threads) are visible
+    __syncwarp();  // the current item's dA rows (copied by the warp's lanes) are visible
     if (cur < n_tile_items) {
-      kind_tile<D, FORM>(desc[a.m], a, phases, s, fst, dslots, xs, sbuf, ebuf, err);
+      kind_tile<D, FORM>(desc[a.m], a, phases, s, fst, dslots, xs, err);
       if (tid == 0) atomicAdd(&ctr->done[m_base + a.m], 1);
     } else {
       const int64_t ir = cur - n_tile_items;
@@ -707,10 +688,10 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
         return FEM_ERR_CUDA;
       }
       M.tile_rec = W.tile_rec;
-      M.sorted = W.sorted;
+      M.rank = W.rank;
       M.rec_end = W.rec_end;
+      M.rec_dest = W.rec_dest;
       M.voff = W.voff;
-      M.vrec = W.vrec;
       M.records = W.records;
       off += al256(wsb);
     }
@@ -725,7 +706,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   b->n_total_fwd = tiles;
   b->n_total = tiles + reds;
   b->stage_bytes = stage;
-  b->smem = 4 * stage + fem::kXsBytes + fem::kSortedBytes + fem::kEndsBytes;
+  b->smem = 4 * (stage + fem::kXsWarpBytes);
   // kind groups: the same descriptors ordered by kind, item ranges local to the kind
   cudaError_t e = cudaSuccess;
   for (int kind = 0; kind < 6 && e == cudaSuccess; ++kind) {

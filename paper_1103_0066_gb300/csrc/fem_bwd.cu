@@ -12,8 +12,9 @@ static cudaError_t launch_bwd_t(const BwdLaunch& L) {
   p.coef = L.coef;
   p.dA = L.dA;
   p.tile_rec = ATOMIC ? nullptr : L.tile_rec;
-  p.sorted = L.sorted;
+  p.rank = L.rank;
   p.rec_end = L.rec_end;
+  p.rec_dest = L.rec_dest;
   p.records = L.records;
   p.dcoef = L.dcoef;
   p.dcoords = L.dcoords;

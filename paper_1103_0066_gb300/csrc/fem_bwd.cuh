@@ -13,15 +13,17 @@
 //   4. |det J| enters as 1/|det J|:  d e_mu += -(L_e / det J) adj_mu   (d det / d e_mu = adj_mu)
 //   5. adj_mu = e_{mu+1} x e_{mu+2} (3D; rotated edges in 2D) is pulled back to the
 //      edge vectors, then x_{mu+1} += d e_mu and x_0 -= sum_mu d e_mu.
-// A CTA of 4 warps owns a tile of 128 consecutive elements.  Each warp runs
-// the forward kernel's three-stage pipeline over its 32 elements (connectivity
-// two tiles ahead, coordinates one tile ahead in registers) and copies its
-// upstream dA (contiguous) with 16-byte cp.async into a padded stage.  In the
-// deterministic mode the CTA stages the (d+1) vertex contributions of its 128
-// elements in shared memory and writes one RECORD per distinct vertex of the
-// tile, summed in slot order (the tile's sorted slot list, built once per
-// mesh); the segmented reduction then adds the few records of each vertex.  The
-// atomic variant adds each contribution into dcoords with red.global.add.
+// Each warp runs the forward kernel's three-stage pipeline over tiles of 32
+// elements (connectivity two tiles ahead; coordinates, slot ranks and the
+// tile's record range one tile ahead in registers) and copies its upstream dA
+// (contiguous) with 16-byte cp.async into a padded stage.  In the deterministic
+// mode each lane writes the (d+1) vertex contributions of its element into the
+// warp's slot stage at their ranks in the tile's (vertex, slot) order (built
+// once per mesh), so the contributions to one vertex form a contiguous run;
+// lane r then sums run r in order into RECORD r of the tile, and the segmented
+// reduction adds the few records of each vertex.  Warps never wait for one
+// another.  The atomic variant adds each contribution into dcoords with
+// red.global.add.
 #pragma once
 #include "fem_core.cuh"
 #include "fem_fwd.cuh"
@@ -58,10 +60,11 @@ struct BwdParams {
   const float* coords;
   const float* coef;
   const float* dA;
-  const int32_t* tile_rec;  // first record of each tile (null: no coordinate records)
-  const uint16_t* sorted;   // per tile: slots sorted by (vertex, slot)
-  const uint16_t* rec_end;  // per record: end of its run in the tile's sorted list
-  float* records;           // [R][D]
+  const int32_t* tile_rec;  // first record of each 32-element tile (null: no coordinate records)
+  const uint32_t* rank;     // per element: byte k = rank of slot k in its tile's (vertex, slot) order
+  const uint8_t* rec_end;   // per record: end of its run in that order
+  const int32_t* rec_dest;  // per record: its row in the vertex-major records array
+  float* records;           // [R][D], vertex-major
   float* dcoef;
   float* dcoords;  // atomic mode
   int64_t n_elem;
@@ -77,15 +80,14 @@ struct BwdPlan {
   static constexpr bool VEC = (NN % 4 == 0);
   static constexpr int DST = VEC ? NN + 4 : (NN | 1);  // dA row stride in the stage
   static constexpr int NV = D + 1;
-  static constexpr int NS = kTileElems * NV;  // slots per CTA tile
-  static constexpr int XP = D == 3 ? 4 : 2;     // padded floats per staged slot (one vector store)
+  static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
+  static constexpr int XP = D == 3 ? 4 : 2;  // padded floats per staged slot (one vector store)
   static constexpr int WARPS = kTileElems / 32;
-  static constexpr size_t da_bytes = align_up(size_t(2) * 32 * DST * 4, 128);  // per warp
-  static constexpr size_t xs_bytes = align_up(size_t(NS) * XP * 4, 128);        // per CTA
-  static constexpr size_t sorted_bytes = align_up(size_t(2) * NS * 2, 128);     // per CTA
-  static constexpr int ENDS = NS + 16;  // record ends of a tile (<= NS) plus alignment slack
-  static constexpr size_t ends_bytes = align_up(size_t(2) * ENDS * 2, 128);     // per CTA
-  static constexpr size_t smem = WARPS * da_bytes + xs_bytes + sorted_bytes + ends_bytes;
+  static constexpr size_t da_slot = align_up(size_t(32) * DST * 4, 128);    // one tile of dA rows
+  static constexpr size_t da_bytes = 2 * da_slot;                           // per warp, double buffered
+  static constexpr size_t xs_bytes = align_up(size_t(NSW) * XP * 4, 128);   // per warp
+  static constexpr size_t per_warp = da_bytes + xs_bytes;
+  static constexpr size_t smem = WARPS * per_warp;
 };
 
 // Asynchronous copy of a tile's contiguous dA into the padded stage slot.
@@ -115,38 +117,6 @@ __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, 
   }
 }
 
-// Asynchronous copy of tile `tile`'s sorted slot list (NS u16) by the CTA.
-template <int NS>
-__device__ __forceinline__ void copy_sorted(const uint16_t* sorted, int64_t tile, int tid, uint16_t* dst) {
-  static_assert((NS * 2) % 16 == 0, "sorted slot list in 16-byte chunks");
-  constexpr int NCH = NS * 2 / 16;
-  const uint16_t* src = sorted + tile * NS;
-  for (int c = tid; c < NCH; c += kTileElems) cp_async<16>(dst + 8 * c, src + 8 * c);
-}
-
-// Asynchronous copy of the record ends rec_end[rb, rb + rn) of a tile into
-// dst[0, ...), starting at the 16-byte chunk that holds entry rb; returns the
-// offset of entry rb in dst.  The workspace pads rec_end so the last chunk
-// never leaves the array.
-template <int ENDS>
-__device__ __forceinline__ int copy_ends(const uint16_t* rec_end, int32_t rb, int32_t rn, int tid, uint16_t* dst) {
-  const int32_t c0 = rb & ~7;
-  const int nch = (rb + rn - c0 + 7) >> 3;
-  for (int c = tid; c < nch; c += kTileElems) cp_async<16>(dst + 8 * c, rec_end + c0 + 8 * c);
-  return rb - c0;
-}
-
-// Position of slot (element el of the CTA tile, local vertex k) in the padded
-// stage: the slot order within an element is rotated by (el >> 1), which keeps
-// the 16-byte writes of a quarter warp on distinct bank groups.
-template <int NV>
-__device__ __forceinline__ int stage_slot(int el, int k) {
-  if constexpr (NV == 4)
-    return el * 4 + ((k + (el >> 1)) & 3);
-  else
-    return el * NV + k;
-}
-
 // Upper triangle of sym(dA) from a staged row: 16-byte reads when the row is
 // 16-byte aligned and small enough to hold in registers, scalar reads otherwise.
 template <int D, int FORM>
@@ -169,35 +139,59 @@ __device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTrai
   }
 }
 
-// Record phase of a CTA tile: record r (r < rn) sums the staged contributions
-// of its slots srt[ends[r-1] .. ends[r]) in order and writes records[rb + r].
+// Records of one warp's 32-element tile.  Record r (r < rn) sums the staged
+// contributions at positions [end(r-1), end(r)) of the tile's (vertex, slot)
+// order -- the slots of its vertex, in increasing slot order -- and writes row
+// rec_dest[rb + r] of the vertex-major records.  end0 = rec_end[rb + lane] and
+// dest0 = rec_dest[rb + lane] for lane < rn (loaded ahead by the caller),
+// anything for the other lanes.
+struct RecAhead {
+  int end0, dest0;
+};
+
+__device__ __forceinline__ RecAhead load_rec_ahead(const uint8_t* rec_end, const int32_t* rec_dest, int32_t rb,
+                                                   int32_t rn, int lane) {
+  RecAhead a{0, 0};
+  if (lane < rn) {
+    a.end0 = int(__ldg(rec_end + rb + lane));
+    a.dest0 = __ldg(rec_dest + rb + lane);
+  }
+  return a;
+}
+
 template <int D>
-__device__ __forceinline__ void write_records(const uint16_t* srt, const uint16_t* ends, const float* xs, int32_t rb,
-                                              int32_t rn, float* records, int tid) {
-  constexpr int NV = D + 1, XP = D == 3 ? 4 : 2;
-  for (int r = tid; r < rn; r += kTileElems) {
-    const int beg = r == 0 ? 0 : int(ends[r - 1]);
-    const int end = int(ends[r]);
-    float acc[D];
+__device__ __forceinline__ void warp_records(const float* xs, const uint8_t* rec_end, const int32_t* rec_dest,
+                                             int32_t rb, int32_t rn, RecAhead ah, float* records, int lane) {
+  constexpr int XP = D == 3 ? 4 : 2;
+  int prev = 0;  // end of the record before lane 0's
+  for (int r0 = 0; r0 < rn; r0 += 32) {
+    const int r = r0 + lane;
+    const bool live = r < rn;
+    const int end = r0 == 0 ? ah.end0 : (live ? int(__ldg(rec_end + rb + r)) : 0);
+    const int dest = r0 == 0 ? ah.dest0 : (live ? __ldg(rec_dest + rb + r) : 0);
+    int beg = __shfl_up_sync(0xffffffffu, end, 1);
+    if (lane == 0) beg = prev;
+    prev = __shfl_sync(0xffffffffu, end, 31);
+    if (live) {
+      float acc[D];
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = 0.f;
-    for (int j = beg; j < end; ++j) {
-      const int slot = srt[j];
-      const float* x = xs + stage_slot<NV>(slot / NV, slot % NV) * XP;
-      if constexpr (D == 3) {
-        const float4 v = *reinterpret_cast<const float4*>(x);
-        acc[0] += v.x;
-        acc[1] += v.y;
-        acc[2] += v.z;
-      } else {
-        const float2 v = *reinterpret_cast<const float2*>(x);
-        acc[0] += v.x;
-        acc[1] += v.y;
+      for (int a = 0; a < D; ++a) acc[a] = 0.f;
+      for (int j = beg; j < end; ++j) {
+        if constexpr (D == 3) {
+          const float4 v = *reinterpret_cast<const float4*>(xs + j * XP);
+          acc[0] += v.x;
+          acc[1] += v.y;
+          acc[2] += v.z;
+        } else {
+          const float2 v = *reinterpret_cast<const float2*>(xs + j * XP);
+          acc[0] += v.x;
+          acc[1] += v.y;
+        }
       }
-    }
-    float* dst = records + int64_t(rb + r) * D;
+      float* dst = records + int64_t(dest) * D;
 #pragma unroll
-    for (int a = 0; a < D; ++a) dst[a] = acc[a];
+      for (int a = 0; a < D; ++a) dst[a] = acc[a];
+    }
   }
 }
 
@@ -205,7 +199,7 @@ __device__ __forceinline__ void write_records(const uint16_t* srt, const uint16_
 template <int D, int FORM, int JAC, bool ATOMIC>
 __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags, float w,
                                                 const float (&X)[D + 1][D], const float* drow,
-                                                const int (&vc)[D + 1], float* xs, int el) {
+                                                const int (&vc)[D + 1], float* xs, uint32_t rk) {
   using FT = FormTraits<D, FORM>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
   constexpr int N = FT::N, NV = FT::NV;
@@ -330,10 +324,10 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
     }
   }
   if constexpr (!ATOMIC) {
-    if (xs) {  // the element's slot contributions (zeros when it is skipped)
+    if (xs) {  // the element's slot contributions at their ranks (zeros when it is skipped)
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
-        float* d = xs + stage_slot<NV>(el, k) * (D == 3 ? 4 : 2);
+        float* d = xs + ((rk >> (8 * k)) & 0xFFu) * (D == 3 ? 4 : 2);
         if constexpr (D == 3)
           *reinterpret_cast<float4*>(d) = make_float4(xb[k][0], xb[k][1], xb[k][2], 0.f);
         else
@@ -347,72 +341,65 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
 template <int D, int FORM, int JAC, bool ATOMIC>
 __global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
   using PL = BwdPlan<D, FORM>;
-  constexpr int W = PL::WARPS, NS = PL::NS, NV = PL::NV;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* dslots = reinterpret_cast<float*>(smem_raw + size_t(warp) * PL::da_bytes);  // [2][32][DST]
-  float* xs = reinterpret_cast<float*>(smem_raw + W * PL::da_bytes);                 // [NS][XP]
-  uint16_t* sbuf = reinterpret_cast<uint16_t*>(smem_raw + W * PL::da_bytes + PL::xs_bytes);  // [2][NS]
-  uint16_t* ebuf = reinterpret_cast<uint16_t*>(smem_raw + W * PL::da_bytes + PL::xs_bytes +
-                                               PL::sorted_bytes);  // [2][ENDS]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wbase = smem_raw + size_t(warp) * PL::per_warp;
+  float* dslots = reinterpret_cast<float*>(wbase);               // [2][32][DST]
+  float* xs = reinterpret_cast<float*>(wbase + PL::da_bytes);    // [32 (d+1)][XP]
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
-  const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
-  const int64_t G = gridDim.x;
-  int64_t T = blockIdx.x;
-  if (T >= nct) return;  // CTA-uniform
-  const int el = warp * 32 + lane;  // element within the CTA tile
-  int eoff = 0;                     // position of the tile's first record end in its ebuf slot
+  const int64_t ntiles = (p.n_elem + 31) / 32;
+  const int64_t S = int64_t(gridDim.x) * PL::WARPS;  // warp-tile stride
+  int64_t t = int64_t(blockIdx.x) * PL::WARPS + warp;
+  if (t >= ntiles) return;  // warp-uniform: the kernel has no CTA-wide barrier
   int err = 0;
   int v1[D + 1], v2[D + 1], vc[D + 1];
   float Xc[D + 1][D], Xn[D + 1][D];
-  int64_t t = T * W + warp;  // this warp's 32-element sub-tile
   load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
   int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
   copy_dA_async<D, FORM>(p, t, lane, dslots);
-  if (rec) copy_sorted<NS>(p.sorted, T, tid, sbuf);
   float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
-  int32_t rb = 0, rn = 0;  // first record and record count of tile T
+  uint32_t rkcur = 0;
+  int32_t rb = 0, rn = 0;  // first record and record count of tile t
   if (rec) {
-    rb = __ldg(p.tile_rec + T);
-    rn = __ldg(p.tile_rec + T + 1) - rb;
-    eoff = copy_ends<PL::ENDS>(p.rec_end, rb, rn, tid, ebuf);
+    rkcur = __ldg(p.rank + t * 32 + lane);
+    rb = __ldg(p.tile_rec + t);
+    rn = __ldg(p.tile_rec + t + 1) - rb;
   }
   cp_async_commit();
 #pragma unroll
   for (int k = 0; k <= D; ++k) vc[k] = v1[k];
-  load_conn<D>(p.conn, (t + W * G) * 32 + lane, p.n_elem, p.vec_conn, v1);
-  for (int i = 0; T < nct; ++i, T += G, t += W * G) {
-    const int64_t tn = t + W * G, en = tn * 32 + lane;
+  load_conn<D>(p.conn, (t + S) * 32 + lane, p.n_elem, p.vec_conn, v1);
+  for (int i = 0; t < ntiles; ++i, t += S) {
+    const int64_t tn = t + S, en = tn * 32 + lane;
     const int sn = (i + 1) & 1, sc = i & 1;
-    load_conn<D>(p.conn, (tn + W * G) * 32 + lane, p.n_elem, p.vec_conn, v2);
+    load_conn<D>(p.conn, (tn + S) * 32 + lane, p.n_elem, p.vec_conn, v2);
     const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
     copy_dA_async<D, FORM>(p, tn, lane, dslots + sn * 32 * PL::DST);
-    const bool has_next = T + G < nct;
-    if (rec && has_next) copy_sorted<NS>(p.sorted, T + G, tid, sbuf + sn * NS);
     const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
-    int32_t rbn = 0, rnn = 0, eoffn = 0;
-    if (rec && has_next) {
-      rbn = __ldg(p.tile_rec + T + G);
-      rnn = __ldg(p.tile_rec + T + G + 1) - rbn;
-      eoffn = copy_ends<PL::ENDS>(p.rec_end, rbn, rnn, tid, ebuf + sn * PL::ENDS);
+    uint32_t rknext = 0;
+    int32_t rbn = 0, rnn = 0;
+    if (rec && tn < ntiles) {
+      rknext = __ldg(p.rank + en);
+      rbn = __ldg(p.tile_rec + tn);
+      rnn = __ldg(p.tile_rec + tn + 1) - rbn;
     }
+    // this tile's record ends and destinations: in flight while the element math runs
+    const RecAhead ah = rec ? load_rec_ahead(p.rec_end, p.rec_dest, rb, rn, lane) : RecAhead{0, 0};
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();  // dA rows were copied by other lanes
     err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslots + (sc * 32 + lane) * PL::DST,
-                                                  vc, rec ? xs : nullptr, el);
+                                                  vc, rec ? xs : nullptr, rkcur);
     if (rec) {
-      __syncthreads();  // every warp's contributions and the sorted list are in shared memory
-      write_records<D>(sbuf + sc * NS, ebuf + sc * PL::ENDS + eoff, xs, rb, rn, p.records, tid);
-      __syncthreads();  // xs and the sorted slot buffer are refilled next
-    } else {
-      __syncwarp();  // the dA slot is refilled two tiles later
+      __syncwarp();  // every lane's contributions are staged
+      warp_records<D>(xs, p.rec_end, p.rec_dest, rb, rn, ah, p.records, lane);
     }
+    __syncwarp();  // the slot stage is rewritten next tile, the dA slot two tiles later
     fcur = fnext;
     wcur = wnext;
+    rkcur = rknext;
     rb = rbn;
     rn = rnn;
-    eoff = eoffn;
 #pragma unroll
     for (int k = 0; k <= D; ++k) {
       vc[k] = v1[k];

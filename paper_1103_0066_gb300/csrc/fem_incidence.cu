@@ -1,20 +1,26 @@
 // fem_incidence.cu -- the deterministic vertex reduction of the adjoint:
 // tile records, their vertex CSR, and the segmented sum into dcoords.
 //
-// The adjoint's element pass works on CTA tiles of kTileElems consecutive
-// elements.  Within a tile the (d+1) vertex contributions of every element
-// ("slots") that share a vertex are first summed in shared memory into one
-// RECORD, in increasing slot order; a structured mesh in cell-major order has
-// several times fewer records than slots, so only the records go to HBM.  The
-// records of each vertex are then summed in increasing record order (= tile
-// order).  Both orders are fixed by the mesh, so dcoords is bitwise
-// reproducible.
+// The adjoint's element pass works on record tiles of kRecTile = 32
+// consecutive elements, one per warp.  Within a tile the (d+1) vertex
+// contributions of every element ("slots") that share a vertex are first
+// summed in shared memory into one RECORD, in increasing slot order; a
+// structured mesh in cell-major order has several times fewer records than
+// slots, so only the records go to HBM.  The records of each vertex are then
+// summed in increasing record order (= tile order).  Both orders are fixed by
+// the mesh, so dcoords is bitwise reproducible.
 //
-// Built once per connectivity (fem_incidence_build):
-//   per tile : bitonic sort of (vertex, slot) keys -> sorted slot list, record
-//              count; exclusive scan of the counts -> first record of each tile;
-//              record ends (positions in the sorted list) and record vertices
-//   global   : vertex -> records CSR (count, scan, fill, per-segment sort)
+// Built once per connectivity (fem_incidence_build), one warp per tile:
+//   per tile : bitonic sort of (vertex, slot) keys -> the rank of every slot
+//              in that order (one byte; the element pass writes each
+//              contribution at its rank, so a record is a contiguous run) and
+//              the record count; exclusive scan of the counts -> first record
+//              of each tile; record ends (one byte, end of the run) and record
+//              vertices
+//   global   : vertex -> records CSR (count, scan, fill, per-segment sort),
+//              then each record's position in it (rec_dest): the element pass
+//              writes record r straight to records[rec_dest[r]], so the
+//              reduction reads each vertex's records as one contiguous run
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -155,19 +161,23 @@ __global__ void sort_segments_kernel(const int32_t* offsets, int64_t n_seg, int3
 
 // ---------------------------------------------------------------- tile records
 
-constexpr int kBuildThreads = 128;
-constexpr int kSortCap = 512;  // power of two >= kTileElems * 4 slots
-static_assert(kSortCap >= kTileElems * 4, "tile slot capacity");
+constexpr int kBuildThreads = 128;              // 4 warps, one record tile each
+constexpr int kSortCap = 128;                   // power of two >= kRecTile * 4 slots
+constexpr int kKeysPerLane = kSortCap / 32;
+static_assert(kSortCap >= kRecTile * 4, "tile slot capacity");
 constexpr uint64_t kNoVertex = 0xFFFFFFFFull;
 
-// Loads the tile's (vertex << 16 | slot) keys (absent or invalid slots get the
-// largest vertex) and sorts them in shared memory (bitonic network).
-__device__ void tile_sorted_keys(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t tile,
+// The warp's tile keys (vertex << 16 | slot), absent or invalid slots with the
+// largest vertex, sorted in shared memory by a bitonic network (one warp).
+__device__ void warp_sorted_keys(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t tile,
                                  uint64_t* key) {
-  const int ns = kTileElems * nv;
-  const int64_t s0 = tile * kTileElems * nv;
+  const int lane = threadIdx.x & 31;
+  const int ns = kRecTile * nv;
+  const int64_t s0 = tile * kRecTile * nv;
   const int64_t smax = n_elem * nv;
-  for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) {
+#pragma unroll
+  for (int q = 0; q < kKeysPerLane; ++q) {
+    const int i = lane + 32 * q;
     uint64_t vtx = kNoVertex;
     if (i < ns && s0 + i < smax) {
       const int32_t v = conn[s0 + i];
@@ -175,10 +185,12 @@ __device__ void tile_sorted_keys(const int32_t* conn, int nv, int64_t n_elem, in
     }
     key[i] = (vtx << 16) | uint64_t(i);
   }
-  __syncthreads();
+  __syncwarp();
   for (int k = 2; k <= kSortCap; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) {
+#pragma unroll
+      for (int q = 0; q < kKeysPerLane; ++q) {
+        const int i = lane + 32 * q;
         const int ixj = i ^ j;
         if (ixj > i) {
           const bool up = (i & k) == 0;
@@ -189,7 +201,7 @@ __device__ void tile_sorted_keys(const int32_t* conn, int nv, int64_t n_elem, in
           }
         }
       }
-      __syncthreads();
+      __syncwarp();
     }
 }
 
@@ -198,81 +210,98 @@ __device__ __forceinline__ bool is_head(const uint64_t* key, int i) {
   return v != kNoVertex && (i == 0 || (key[i - 1] >> 16) != v);
 }
 
-// Pass 1: sorted slot list of each tile and its record count.
+// Pass 1: the rank of every slot of each tile and the tile's record count.
+// Slots of the tile past the last element keep ranks too (zero contributions
+// are written there and never read).
 __global__ void __launch_bounds__(kBuildThreads)
     tile_sort_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
-                     uint16_t* sorted, int32_t* nrec) {
-  __shared__ uint64_t key[kSortCap];
-  __shared__ int32_t cnt;
-  const int ns = kTileElems * nv;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    if (threadIdx.x == 0) cnt = 0;
-    tile_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
+                     uint8_t* rank, int32_t* nrec) {
+  __shared__ uint64_t keys[kBuildThreads / 32][kSortCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* key = keys[warp];
+  const int ns = kRecTile * nv;
+  const int64_t stride = int64_t(gridDim.x) * (kBuildThreads / 32);
+  for (int64_t tile = blockIdx.x * int64_t(kBuildThreads / 32) + warp; tile < n_tiles; tile += stride) {
+    warp_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
     int c = 0;
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-      sorted[tile * ns + i] = uint16_t(key[i] & 0xFFFF);
-      c += is_head(key, i) ? 1 : 0;
+#pragma unroll
+    for (int q = 0; q < kKeysPerLane; ++q) {
+      const int i = lane + 32 * q;
+      if (i < ns) {
+        const int slot = int(key[i] & 0xFFFF);
+        // element slot / nv of the tile, local vertex slot % nv; 4 bytes per element
+        rank[(tile * kRecTile + slot / nv) * 4 + slot % nv] = uint8_t(i);
+        c += is_head(key, i) ? 1 : 0;
+      }
     }
-    atomicAdd(&cnt, c);
-    __syncthreads();
-    if (threadIdx.x == 0) nrec[tile] = cnt;
-    __syncthreads();
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) nrec[tile] = c;
+    __syncwarp();  // the key buffer is refilled for the next tile
   }
 }
 
-// Pass 2: record ends (positions in the tile's sorted list) and record vertices.
+// Pass 2: record ends (end of each record's run in the tile's order) and
+// record vertices.
 __global__ void __launch_bounds__(kBuildThreads)
     tile_records_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
-                        const int32_t* tile_rec, uint16_t* rec_end, int32_t* rec_vertex) {
-  __shared__ uint64_t key[kSortCap];
-  __shared__ int32_t head_scan[kSortCap];
-  constexpr int kPer = kSortCap / kBuildThreads;
-  const int ns = kTileElems * nv;
-  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    tile_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
-    for (int i = threadIdx.x; i < kSortCap; i += blockDim.x) head_scan[i] = (i < ns && is_head(key, i)) ? 1 : 0;
-    __syncthreads();
-    // inclusive Hillis-Steele scan of the head flags
-    for (int off = 1; off < kSortCap; off <<= 1) {
-      int32_t vals[kPer];
+                        const int32_t* tile_rec, uint8_t* rec_end, int32_t* rec_vertex) {
+  __shared__ uint64_t keys[kBuildThreads / 32][kSortCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* key = keys[warp];
+  const int64_t stride = int64_t(gridDim.x) * (kBuildThreads / 32);
+  for (int64_t tile = blockIdx.x * int64_t(kBuildThreads / 32) + warp; tile < n_tiles; tile += stride) {
+    warp_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
+    // lane owns the consecutive entries [kKeysPerLane * lane, kKeysPerLane * (lane + 1))
+    int heads = 0;
 #pragma unroll
-      for (int q = 0; q < kPer; ++q) {
-        const int i = threadIdx.x + q * kBuildThreads;
-        vals[q] = head_scan[i] + (i >= off ? head_scan[i - off] : 0);
-      }
-      __syncthreads();
+    for (int q = 0; q < kKeysPerLane; ++q) heads += is_head(key, kKeysPerLane * lane + q) ? 1 : 0;
+    int incl = heads;  // inclusive warp scan of the head counts
 #pragma unroll
-      for (int q = 0; q < kPer; ++q) head_scan[threadIdx.x + q * kBuildThreads] = vals[q];
-      __syncthreads();
+    for (int off = 1; off < 32; off <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += y;
     }
-    const int32_t base = tile_rec[tile];
-    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+    int32_t r = tile_rec[tile] + incl - heads - 1;  // record of the entry before the lane's first
+#pragma unroll
+    for (int q = 0; q < kKeysPerLane; ++q) {
+      const int i = kKeysPerLane * lane + q;
       const uint64_t v = key[i] >> 16;
       if (v == kNoVertex) continue;
-      const int32_t r = base + head_scan[i] - 1;
-      if (is_head(key, i)) rec_vertex[r] = int32_t(v);
+      if (is_head(key, i)) {
+        ++r;
+        rec_vertex[r] = int32_t(v);
+      }
       const bool last = (i + 1 == kSortCap) || ((key[i + 1] >> 16) != v);
-      if (last) rec_end[r] = uint16_t(i + 1);
+      if (last) rec_end[r] = uint8_t(i + 1);
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-// dcoords[v] = sum of the records of v in increasing record order.
+// rec_dest[vrec[k]] = k for the R = voff[n_vert] records: the vertex-major
+// position of every record (vrec[0, R) is a permutation of [0, R): every
+// record has a valid vertex).
+__global__ void dest_kernel(const int32_t* voff, int64_t n_vert, const int32_t* vrec, int32_t* rec_dest) {
+  const int64_t R = voff[n_vert];
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < R; k += int64_t(gridDim.x) * blockDim.x)
+    rec_dest[vrec[k]] = int32_t(k);
+}
+
+// dcoords[v] = sum of the records of v (a contiguous run of the vertex-major
+// record array) in increasing record order.
 template <int D>
-__global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
-                                     const float* __restrict__ records, int64_t n_vert,
-                                     float* __restrict__ dcoords) {
+__global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const float* __restrict__ records,
+                                     int64_t n_vert, float* __restrict__ dcoords) {
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
     const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
     float acc[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = 0.f;
+#pragma unroll 4
     for (int32_t k = b; k < e; ++k) {
-      const int64_t r = __ldg(vrec + k);
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] += __ldcs(records + r * D + a);
+      for (int a = 0; a < D; ++a) acc[a] += __ldg(records + int64_t(k) * D + a);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
@@ -301,8 +330,7 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
                             BwdWorkspace* ws) {
   const int64_t nv = dim + 1;
-  const int64_t ns = kTileElems * nv;
-  const int64_t n_tiles = (n_elem + kTileElems - 1) / kTileElems;
+  const int64_t n_tiles = (n_elem + kRecTile - 1) / kRecTile;
   const int64_t r_max = n_elem * nv;  // at most one record per slot
   const int64_t n_cnt = n_vert > n_tiles ? n_vert : n_tiles;
   const int64_t nb = (n_cnt + kScanBlock - 1) / kScanBlock;
@@ -313,8 +341,9 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
     return o;
   };
   const size_t o_tile_rec = take(sizeof(int32_t) * size_t(n_tiles + 1));
-  const size_t o_sorted = take(sizeof(uint16_t) * size_t(n_tiles * ns));
-  const size_t o_rec_end = take(sizeof(uint16_t) * size_t(r_max + 16));  // +16: chunked reads
+  const size_t o_rank = take(sizeof(uint32_t) * size_t(n_tiles * kRecTile));
+  const size_t o_rec_end = take(sizeof(uint8_t) * size_t(r_max));
+  const size_t o_rec_dest = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_rec_vertex = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_voff = take(sizeof(int32_t) * size_t(n_vert + 1));
   const size_t o_vrec = take(sizeof(int32_t) * size_t(r_max));
@@ -324,8 +353,9 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   if (ws) {
     char* b = static_cast<char*>(base);
     ws->tile_rec = reinterpret_cast<int32_t*>(b + o_tile_rec);
-    ws->sorted = reinterpret_cast<uint16_t*>(b + o_sorted);
-    ws->rec_end = reinterpret_cast<uint16_t*>(b + o_rec_end);
+    ws->rank = reinterpret_cast<uint32_t*>(b + o_rank);
+    ws->rec_end = reinterpret_cast<uint8_t*>(b + o_rec_end);
+    ws->rec_dest = reinterpret_cast<int32_t*>(b + o_rec_dest);
     ws->rec_vertex = reinterpret_cast<int32_t*>(b + o_rec_vertex);
     ws->voff = reinterpret_cast<int32_t*>(b + o_voff);
     ws->vrec = reinterpret_cast<int32_t*>(b + o_vrec);
@@ -343,9 +373,11 @@ cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem,
   const int nv = dim + 1;
   const int64_t n_tiles = ws.n_tiles;
   const int64_t r_max = n_elem * nv;
-  const unsigned tg = unsigned(n_tiles < 4 * 65535 ? (n_tiles > 0 ? n_tiles : 1) : 4 * 65535);
+  const int64_t tb = (n_tiles + kBuildThreads / 32 - 1) / (kBuildThreads / 32);
+  const unsigned tg = unsigned(tb < 4 * 65535 ? (tb > 0 ? tb : 1) : 4 * 65535);
   // tile records; record slots past the last record keep vertex -1
-  tile_sort_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.sorted, ws.cursor);
+  tile_sort_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles,
+                                                     reinterpret_cast<uint8_t*>(ws.rank), ws.cursor);
   exclusive_scan(ws.cursor, n_tiles, ws.partials, ws.tile_rec, stream);
   fill_i32<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, -1);
   tile_records_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.tile_rec,
@@ -357,6 +389,7 @@ cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem,
   fill_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert, 0);
   fill_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, n_vert, ws.voff, ws.cursor, ws.vrec);
   sort_segments_kernel<<<grid_for((n_vert + 3) / 4, 128), 128, 0, stream>>>(ws.voff, n_vert, ws.vrec);
+  dest_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.voff, n_vert, ws.vrec, ws.rec_dest);
   return cudaGetLastError();
 }
 
@@ -372,9 +405,9 @@ cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert
   const int block = 256;
   const int64_t g = (n_vert + block - 1) / block;
   if (dim == 2)
-    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.records, n_vert, dcoords);
+    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.records, n_vert, dcoords);
   else
-    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.records, n_vert, dcoords);
+    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.records, n_vert, dcoords);
   return cudaGetLastError();
 }
 

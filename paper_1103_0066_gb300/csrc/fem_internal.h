@@ -33,9 +33,11 @@ struct GeoLaunch {
   cudaStream_t stream;
 };
 
-// Elements per CTA tile of the adjoint's element pass (4 warps x 32); the
-// deterministic reduction's tile records are built for this tile size.
+// Elements per CTA tile (4 warps x 32) of the persistent and batched kernels.
 constexpr int kTileElems = 128;
+// Elements per record tile of the deterministic reduction: one warp's 32
+// elements, so a warp forms its records without any CTA-wide barrier.
+constexpr int kRecTile = 32;
 
 // Adjoint element pass (FP32 coordinates).
 struct BwdLaunch {
@@ -48,8 +50,9 @@ struct BwdLaunch {
   float* dcoords;  // atomic: accumulated with red.add (pre-zeroed)
   // deterministic: tile records (null when only dcoef is wanted)
   const int32_t* tile_rec;
-  const uint16_t* sorted;
-  const uint16_t* rec_end;
+  const uint32_t* rank;
+  const uint8_t* rec_end;
+  const int32_t* rec_dest;
   float* records;
   int64_t n_elem, n_vert;
   int32_t* dev_err;
@@ -58,12 +61,15 @@ struct BwdLaunch {
 };
 
 // Workspace of the deterministic adjoint (see fem_incidence.cu):
-// [tile_rec T+1][sorted T*128*(d+1) u16][rec_end R u16][rec_vertex R][voff V+1][vrec R]
-// [cursor][scan partials][records R*d]   with R <= E*(d+1) records.
+// [tile_rec T+1][rank T*32 u32][rec_end R u8][rec_dest R][rec_vertex R][voff V+1]
+// [vrec R][cursor][scan partials][records R*d]   with T = ceil(E/32) record
+// tiles and R <= E*(d+1) records; records are stored vertex-major (record r at
+// rec_dest[r]), so the records of vertex v are records[voff[v], voff[v+1]).
 struct BwdWorkspace {
   int32_t* tile_rec;
-  uint16_t* sorted;
-  uint16_t* rec_end;
+  uint32_t* rank;  // per element: byte k = rank of its local vertex k in its tile's (vertex, slot) order
+  uint8_t* rec_end;
+  int32_t* rec_dest;  // per record: its position in the vertex-major record array
   int32_t* rec_vertex;
   int32_t* voff;
   int32_t* vrec;

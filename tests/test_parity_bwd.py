@@ -59,25 +59,49 @@ def test_deterministic_is_bitwise_reproducible(gfem):
 
 
 def test_tile_records_structure(gfem):
-    """Workspace of the deterministic reduction: each 128-element tile has one
-    record per distinct vertex, and its slot list is sorted by (vertex, slot)."""
+    """Workspace of the deterministic reduction: each 32-element record tile has
+    one record per distinct vertex; every slot's rank is its position in the
+    tile's (vertex, slot) order; each record ends where its vertex's run of
+    slots ends; and rec_dest places the records of every vertex, in record
+    order, in that vertex's run [voff[v], voff[v+1]) of the vertex-major array."""
     mesh = _mesh(3, 5)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
     ws = gfem.Workspace(coords, conn)
-    E, NS = mesh.n_elem, 128 * 4
-    T = (E + 127) // 128
+    E, NV, TS = mesh.n_elem, 4, 32
+    T = (E + TS - 1) // TS
+    al = lambda x: ((x + 255) // 256) * 256
     raw = ws.buf.cpu().numpy()
     tile_rec = raw[: 4 * (T + 1)].view(np.int32)
-    o_sorted = ((4 * (T + 1) + 255) // 256) * 256
-    srt = raw[o_sorted: o_sorted + 2 * T * NS].view(np.uint16).reshape(T, NS)
+    o_rank = al(4 * (T + 1))
+    rank = raw[o_rank: o_rank + 4 * T * TS].reshape(T * TS, 4)
+    o_end = al(o_rank + 4 * T * TS)
+    R = int(tile_rec[T])
+    rec_end = raw[o_end: o_end + R]
+    o_dest = al(o_end + NV * E)
+    rec_dest = raw[o_dest: o_dest + 4 * R].view(np.int32)
+    o_voff = al(al(o_dest + 4 * NV * E) + 4 * NV * E)
+    voff = raw[o_voff: o_voff + 4 * (mesh.n_vert + 1)].view(np.int32)
     flat = mesh.conn.ravel()
     assert tile_rec[0] == 0
+    assert np.array_equal(np.sort(rec_dest), np.arange(R))      # a permutation of the records
+    rec_vtx = np.empty(R, np.int64)
     for t in range(T):
-        slots = np.arange(t * NS, min((t + 1) * NS, 4 * E))
+        slots = np.arange(t * TS * NV, min((t + 1) * TS * NV, NV * E))
         verts = flat[slots]
-        assert tile_rec[t + 1] - tile_rec[t] == len(np.unique(verts))
-        local = slots - t * NS
-        assert np.array_equal(srt[t, : len(slots)], local[np.lexsort((local, verts))])
+        local = slots - t * TS * NV
+        order = local[np.lexsort((local, verts))]              # slots in (vertex, slot) order
+        rk = rank[t * TS + local // NV, local % NV].astype(np.int64)
+        assert np.array_equal(rk[order], np.arange(len(slots)))  # rank = position in that order
+        u, counts = np.unique(verts, return_counts=True)
+        assert tile_rec[t + 1] - tile_rec[t] == len(u)
+        ends = rec_end[tile_rec[t]: tile_rec[t + 1]].astype(np.int64)
+        assert np.array_equal(ends, np.cumsum(counts))
+        rec_vtx[tile_rec[t]: tile_rec[t + 1]] = u
+    assert np.array_equal(np.diff(voff), np.bincount(rec_vtx, minlength=mesh.n_vert))
+    order = np.argsort(rec_dest)                                 # record stored at each row
+    assert np.array_equal(rec_vtx[order], np.repeat(np.arange(mesh.n_vert), np.diff(voff)))
+    for v in range(mesh.n_vert):                                  # record order within a vertex
+        assert np.all(np.diff(order[voff[v]: voff[v + 1]]) > 0)
 
 
 def test_coefficient_only_and_coords_only(gfem, orc):
