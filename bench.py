@@ -49,6 +49,9 @@ KERNEL_SOURCES = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1278.5e6, "src": "3c4282340f8b02f6"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 975.2e6, "src": "6821a74b0aa1b8ae"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.7e6, "src": "c0c9bd793c40989a"},
 }
 
 
@@ -178,10 +181,10 @@ def algorithmic_bytes(E, V, R, n, dim, coef):
     nv = dim + 1
     fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0)) + V * 4 * dim
     # dA, connectivity, the slot ranks (one 4-byte word per element); record
-    # ends (1 B) read and record sums (4 d B) written
-    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0)) + R * (1 + 4 * dim) + V * 4 * dim
-    # record sums and their vertex CSR read, dcoords written
-    reduce = R * (4 * dim + 4) + V * (4 + 4 * dim)
+    # ends (1 B) and destinations (4 B) read, record sums (4 d B) written
+    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0)) + R * (1 + 4 + 4 * dim) + V * 4 * dim
+    # vertex-major record sums and the vertex offsets read, dcoords written
+    reduce = R * 4 * dim + V * (4 + 4 * dim)
     return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
 
 
@@ -282,7 +285,7 @@ def run_ours(args):
     kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
              "reduce": "vertex_reduce_kernel<3>"}
     h = {k: kernel_src_hash(v) for k, v in kname.items()}
-    tr = NCU_TRAFFIC.get(kname[dom])
+    tr = NCU_TRAFFIC.get(kname[dom])  # valid only for the sources it was captured with
     traffic = tr["bytes_per_launch"] if tr and tr.get("src") == h[dom] else None
     ach = byts[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -548,6 +551,71 @@ def run_elastic(args):
     print(json.dumps(out), flush=True)
 
 
+def run_coef_p1(args):
+    """P2 Laplacian with a P1 coefficient (vertex values, Eqs. 20-23) on the
+    128^3 sliver cube, forward; the per-element-coefficient P2 Laplacian timed
+    beside it on the same mesh."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh = mg.workload_tet_slivers(args.mesh_n, 2)
+    E, V = mesh.n_elem, mesh.n_vert
+    wv_h = mg.lognormal_coef(mg.rng_for(6), V)
+    we_h = mg.lognormal_coef(mg.rng_for(7), E)
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    wv, we = torch.from_numpy(wv_h).to(dev), torch.from_numpy(we_h).to(dev)
+    A = torch.empty((E, 10, 10), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, form, coef in (("p1_coefficient", fem.LAPLACE_P2_W1, wv), ("p0_coefficient", fem.LAPLACE_P2, we)):
+        def step():
+            fem.integrate_fwd(coords, conn, form, coef, out=A)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.steps
+        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3)}
+        if name == "p1_coefficient":
+            rng = np.random.default_rng(8)
+            idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 20000, replace=False),
+                                            rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
+            Ar, _ = oracle.integrate_w1(3, oracle.LAPLACE_P2, mesh.conn[idx], mesh.coords, wv_h)
+            Ag = A[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+            num = np.abs(Ag - Ar).reshape(len(idx), -1).max(1)
+            res[name]["max_rel_err_vs_fp64"] = float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())
+            res[name]["error_sample"] = f"{len(idx):,} elements (20,000 slivers, 20,000 uniform, the last 40)"
+    byts = {"p1_coefficient": E * (16 + 400) + V * (12 + 4), "p0_coefficient": E * (16 + 400 + 4) + V * 12}
+    peak, peak_kind = hbm_peak()
+    for k in res:
+        res[k]["GB/s"] = byts[k] / (res[k]["ms"] * 1e-3) / 1e9
+        res[k]["frac_of_peak"] = res[k]["GB/s"] / peak
+    r = res["p1_coefficient"]
+    out = {"metric": METRIC, "value": r["elements_per_s"], "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": r["ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"P2 Laplacian with a P1 coefficient (vertex values ~ lognormal), {args.mesh_n}^3 "
+                                  f"Kuhn cube with 5% slivers ({E:,} tets), 10x10 FP32 element matrices, forward",
+                      "elements": E, "l2": "no flush: 5.2 GB moved per step"},
+           "roofline": {"bound": "hbm", "kernel": "fem_fwd_kernel<3,LAPLACE_P2_W1,JAC_COMP>", "achieved": r["GB/s"],
+                        "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],
+                        "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
+                        "algorithmic_bytes": byts["p1_coefficient"]},
+           "paths": res, "gpu_launches": args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint64(args):
     """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
     lognormal coefficient (dcoords and dcoef), both reductions."""
@@ -653,9 +721,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
-    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64"], default="tet128",
+    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1"],
+                    default="tet128",
                     help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
-                         "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint")
+                         "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
+                         "coef_p1: P2 Laplacian with a P1 coefficient")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -668,6 +738,8 @@ def main():
         run_elastic(args)
     elif args.workload == "adjoint64":
         run_adjoint64(args)
+    elif args.workload == "coef_p1":
+        run_coef_p1(args)
     else:
         run_ours(args)
 

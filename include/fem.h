@@ -52,11 +52,17 @@ typedef enum {
   FEM_ERR_CUDA = 4         /* a CUDA runtime call failed (message in fem_last_error) */
 } fem_status;
 
-/* Weak forms (Sec. 3). */
+/* Weak forms (Sec. 3).  The first three take an optional per-element
+ * coefficient w_e; the _W1 forms take a P1 coefficient w = sum_k w_k lambda_k
+ * given by its values at the mesh vertices (Eqs. 20-23), so `coef` is
+ * [n_vert] for them.  The _W1 forms have a forward path only (no adjoint, no
+ * batched or tensor-core path: FEM_ERR_UNSUPPORTED). */
 typedef enum {
-  FEM_LAPLACE_P1 = 0, /* Eqs. 2-8 with P1 Lagrange elements */
-  FEM_LAPLACE_P2 = 1, /* same form, P2 Lagrange elements */
-  FEM_ELASTIC_P1 = 2  /* eps(v):eps(u), Eq. 10 scaled by the 1/4 of Eqs. 14 and 24, P1 vector elements */
+  FEM_LAPLACE_P1 = 0,    /* Eqs. 2-8 with P1 Lagrange elements */
+  FEM_LAPLACE_P2 = 1,    /* same form, P2 Lagrange elements */
+  FEM_ELASTIC_P1 = 2,    /* eps(v):eps(u), Eq. 10 scaled by the 1/4 of Eqs. 14 and 24, P1 vector elements */
+  FEM_LAPLACE_P1_W1 = 3, /* int w grad v . grad u with w in P1 (Eqs. 20-23), P1 elements */
+  FEM_LAPLACE_P2_W1 = 4  /* the same with P2 elements: K gains the coefficient's index (Eq. 21) */
 } fem_form;
 
 typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
@@ -119,7 +125,8 @@ FEM_API const char* fem_status_string(fem_status s);
 FEM_API const char* fem_last_error(void);
 
 /* Host.  Shape of a form: n = rows of A_e, n_geom = folded entries of G
- * (d(d+1)/2 for the Laplacian, d^2(d^2+1)/2 for elasticity), den = the integer
+ * (d(d+1)/2 for the Laplacian, d^2(d^2+1)/2 for elasticity, (d+1) d(d+1)/2
+ * for the _W1 forms: slot k*d(d+1)/2 + g holds w_k G_g), den = the integer
  * scale of fem_reference_tensor.  Any output pointer may be NULL. */
 FEM_API fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den);
 
@@ -130,7 +137,8 @@ FEM_API fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t*
 FEM_API fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K_host, size_t cap);
 
 /* Forward element integration, Sec. 4 / Eq. 6: A[e] = G_e : K for every element.
- *   coef : device FP32 [n_elem] per-element coefficient w_e, or NULL (w = 1)
+ *   coef : device FP32 [n_elem] per-element coefficient w_e, or NULL (w = 1);
+ *          for the _W1 forms FP32 [n_vert] vertex values of the P1 coefficient
  *   A    : device [n_elem][n][n] of out_dtype (overwritten)
  *   FP64 output or FP64 coordinates compute the Jacobian steps in FP64.
  * Asynchronous on `stream`.  n_elem == 0 is a no-op. */

@@ -67,9 +67,11 @@ def _load():
         lib.orc_element_vjp.argtypes = [I, I, P, D, I, P, P, P]
         lib.orc_integrate.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
         lib.orc_integrate_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
+        lib.orc_element_matrix_w1.argtypes = [I, I, P, P, I, P, P]
+        lib.orc_integrate_w1.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
         for name in ("orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
                      "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
-                     "orc_integrate_vjp"):
+                     "orc_integrate_vjp", "orc_element_matrix_w1", "orc_integrate_w1"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -130,6 +132,40 @@ def element_matrix(dim: int, form: int, X, coef: float = 1.0, q: int = 3):
     if rc < 0:
         raise ValueError("bad element request")
     return A, float(det[0]), rc
+
+
+def element_matrix_w1(dim: int, form: int, X, wv, q: int = 3):
+    """Element matrix of a Laplacian form (LAPLACE_P1 or LAPLACE_P2) with the P1
+    coefficient of vertex values wv [dim+1] (Eqs. 20-23)."""
+    X = _f64(X)
+    wv = _f64(wv)
+    n = form_n(form, dim)
+    A = np.zeros((n, n))
+    det = np.zeros(1)
+    rc = _load().orc_element_matrix_w1(dim, form, _ptr(X), _ptr(wv), q, _ptr(A), _ptr(det))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return A, float(det[0]), rc
+
+
+def integrate_w1(dim: int, form: int, conn, coords, wvert, q: int = 3, nthreads: int | None = None):
+    """Element matrices [E][n][n] (FP64) and flags of a Laplacian form with the P1
+    coefficient whose values at the mesh vertices are wvert [V]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    wvert = _f64(wvert)
+    E, V = conn.shape[0], coords.shape[0]
+    if wvert.shape != (V,):
+        raise ValueError("wvert must have one value per vertex")
+    n = form_n(form, dim)
+    A = np.zeros((E, n, n))
+    flags = np.zeros(E, dtype=np.int32)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_w1(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(wvert), q, _ptr(A),
+                                  _ptr(flags), nt)
+    if rc < 0:
+        raise ValueError("bad integrate request")
+    return A, flags
 
 
 def element_vjp(dim: int, form: int, X, Abar, coef: float = 1.0, q: int = 3):

@@ -15,6 +15,9 @@
  *         eps(v):eps(u):  A_IJ = sum_q w_q |J| c_e  eps(Phi_I):eps(Phi_J)
  *       - c_e is a per-element constant coefficient (the piecewise-constant
  *         case of the coefficient of Eq. 20); c_e = 1 when none is given.
+ *       - or, for the P1 coefficient of Eqs. 20-23, c(xi) = sum_k w_k lambda_k(xi)
+ *         evaluated at every quadrature point from the element's vertex
+ *         values w_k (orc_integrate_w1); the Laplacian forms only.
  *   * Physical gradients grad(phi) = J^{-T} grad_ref(phi) (the chain rule of
  *     Eq. 5, d xi_mu / d x_alpha = (J^{-1})_{mu alpha} as in Eq. 8) obtained
  *     by an LU solve with partial pivoting in FP64.
@@ -289,11 +292,13 @@ static double ddot_mat(int dim, double x[3][3], double y[3][3]) {
   return s;
 }
 
-/* Element matrix of one element with vertex coordinates X[(dim+1)*dim] and
- * coefficient coef, by q^dim-point quadrature.  Returns 0, or ORC_FLAG_DEGENERATE
- * (A zeroed) when det J == 0.  detJ_out (may be NULL) receives det J. */
-int orc_element_matrix(int dim, int form, const double* X, double coef, int q, double* A,
-                       double* detJ_out) {
+/* Element matrix of one element with vertex coordinates X[(dim+1)*dim], by
+ * q^dim-point quadrature, with the coefficient either the constant coef
+ * (wv == NULL) or the P1 function sum_k wv[k] lambda_k (wv = its d+1 vertex
+ * values).  Returns 0, or ORC_FLAG_DEGENERATE (A zeroed) when det J == 0.
+ * detJ_out (may be NULL) receives det J. */
+static int element_matrix(int dim, int form, const double* X, double coef, const double* wv, int q, double* A,
+                          double* detJ_out) {
   int n = orc_form_n(form, dim);
   if (n < 0) return -1;
   int deg = form_degree(form), nb = orc_n_basis(dim, deg), nc = form_ncomp(form, dim);
@@ -315,7 +320,18 @@ int orc_element_matrix(int dim, int form, const double* X, double coef, int q, d
     double phi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3];
     orc_basis(dim, deg, pts + p * dim, phi, gref);
     physical_gradients(dim, &fJt, nb, gref, g);
-    double scale = wts[p] * absdet * coef;
+    double c = coef;
+    if (wv) { /* barycentrics of the point: lambda_0 = 1 - sum xi, lambda_k = xi_k */
+      const double* xi = pts + p * dim;
+      double l0 = 1.0;
+      c = 0.0;
+      for (int k = 1; k <= dim; ++k) {
+        c += wv[k] * xi[k - 1];
+        l0 -= xi[k - 1];
+      }
+      c += wv[0] * l0;
+    }
+    double scale = wts[p] * absdet * c;
     if (form != ORC_ELASTIC_P1) {
       for (int i = 0; i < nb; ++i)
         for (int j = 0; j < nb; ++j) {
@@ -325,13 +341,27 @@ int orc_element_matrix(int dim, int form, const double* X, double coef, int q, d
         }
     } else {
       double eps[ORC_MAXN][3][3];
-      for (int c = 0; c < nc; ++c)
-        for (int i = 0; i < nb; ++i) sym_grad(dim, c, g[i], eps[c * nb + i]);
+      for (int cc = 0; cc < nc; ++cc)
+        for (int i = 0; i < nb; ++i) sym_grad(dim, cc, g[i], eps[cc * nb + i]);
       for (int I = 0; I < n; ++I)
         for (int K = 0; K < n; ++K) A[I * n + K] += scale * ddot_mat(dim, eps[I], eps[K]);
     }
   }
   return 0;
+}
+
+/* Element matrix with a per-element constant coefficient coef. */
+int orc_element_matrix(int dim, int form, const double* X, double coef, int q, double* A,
+                       double* detJ_out) {
+  return element_matrix(dim, form, X, coef, NULL, q, A, detJ_out);
+}
+
+/* Element matrix of a Laplacian form with the P1 coefficient of vertex values
+ * wv[0..dim] (Eqs. 20-23). */
+int orc_element_matrix_w1(int dim, int form, const double* X, const double* wv, int q, double* A,
+                          double* detJ_out) {
+  if (form == ORC_ELASTIC_P1 || !wv) return -1;
+  return element_matrix(dim, form, X, 1.0, wv, q, A, detJ_out);
 }
 
 /* Reverse mode of orc_element_matrix: given Abar = dL/dA, returns
@@ -475,6 +505,33 @@ int orc_integrate(int dim, int form, int64_t n_elem, int64_t n_vert, const int32
     }
     if (flags) flags[e] = f;
     if (detJ) detJ[e] = det;
+    any |= f;
+  }
+  return any;
+}
+
+/* A[e] for every element of a Laplacian form with the P1 coefficient whose
+ * vertex values are wvert [V] (Eqs. 20-23).  Flags as in orc_integrate. */
+int orc_integrate_w1(int dim, int form, int64_t n_elem, int64_t n_vert, const int32_t* conn,
+                     const double* coords, const double* wvert, int q, double* A, int32_t* flags,
+                     int nthreads) {
+  int n = orc_form_n(form, dim);
+  if (n < 0 || form == ORC_ELASTIC_P1 || !wvert) return -1;
+  int any = 0;
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12], wv[4];
+    double* Ae = A + e * (int64_t)n * n;
+    const int32_t* ce = conn + e * (dim + 1);
+    int f = gather(dim, n_vert, ce, coords, X);
+    if (f == 0) {
+      for (int k = 0; k <= dim; ++k) wv[k] = wvert[ce[k]];
+      f = element_matrix(dim, form, X, 1.0, wv, q, Ae, NULL);
+    } else {
+      memset(Ae, 0, sizeof(double) * n * n);
+    }
+    if (flags) flags[e] = f;
     any |= f;
   }
   return any;

@@ -20,12 +20,13 @@ import torch
 
 from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
-                      F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2,
+                      F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2, LAPLACE_P1_W1, LAPLACE_P2_W1,
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT)
 
 __all__ = ["Mesh", "Batch", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
-           "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "JAC_AUTO",
+           "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
+           "LAPLACE_P2_W1", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
            "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
 
@@ -62,20 +63,22 @@ def _mesh_struct(coords: torch.Tensor, conn: torch.Tensor) -> nat.FemMesh:
                            conn.shape[0], conn.data_ptr(), coords.data_ptr())
 
 
-def _coef_ptr(coef, E):
+def _coef_ptr(coef, E, what="[E]"):
     if coef is None:
         return 0
     if coef.dtype != torch.float32 or not coef.is_contiguous() or coef.numel() != E or not coef.is_cuda:
-        raise ValueError("coef must be a contiguous CUDA float32 tensor [E]")
+        raise ValueError(f"coef must be a contiguous CUDA float32 tensor {what}")
     return coef.data_ptr()
 
 
 def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float32, jac=JAC_AUTO,
                   contract=CONTRACT_F32, warps_per_cta=0, ctas_per_sm=0, dev_err=None, stream=None):
-    """fem_integrate_fwd: element matrices [E][n][n] (not differentiable; see integrate)."""
+    """fem_integrate_fwd: element matrices [E][n][n] (not differentiable; see integrate).
+    coef: [E] per-element values, or [V] vertex values for LAPLACE_P1_W1 / LAPLACE_P2_W1."""
     m = _mesh_struct(coords, conn)
     n, _, _ = form_info(form, m.dim)
     E = conn.shape[0]
+    w1 = form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
     if out is None:
         out = torch.empty((E, n, n), dtype=out_dtype, device=coords.device)
     elif out.shape != (E, n, n) or not out.is_contiguous():
@@ -83,7 +86,8 @@ def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float
     od = F64 if out.dtype == torch.float64 else F32
     opts = nat.options_struct(jac, contract, 0, warps_per_cta, ctas_per_sm,
                               dev_err.data_ptr() if dev_err is not None else 0)
-    nat.fem_integrate_fwd(m, form, _coef_ptr(coef, E), out.data_ptr(), od, opts, _stream_ptr(stream))
+    cp = _coef_ptr(coef, coords.shape[0], "[V]") if w1 else _coef_ptr(coef, E)
+    nat.fem_integrate_fwd(m, form, cp, out.data_ptr(), od, opts, _stream_ptr(stream))
     return out
 
 

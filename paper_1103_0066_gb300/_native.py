@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfem_gb300.so")
 
 FEM_OK, FEM_ERR_ARG, FEM_ERR_UNSUPPORTED, FEM_ERR_WORKSPACE, FEM_ERR_CUDA = range(5)
-LAPLACE_P1, LAPLACE_P2, ELASTIC_P1 = 0, 1, 2
+LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, LAPLACE_P1_W1, LAPLACE_P2_W1 = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 JAC_AUTO, JAC_F64, JAC_COMP_F32, JAC_F32 = 0, 1, 2, 3
 CONTRACT_F32, CONTRACT_BF16X3 = 0, 1

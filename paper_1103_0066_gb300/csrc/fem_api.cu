@@ -58,9 +58,12 @@ fem_status check_options(const fem_options* o) {
 }
 
 int form_rows(int form, int dim) {
-  const int nb = form == FEM_LAPLACE_P2 ? (dim + 1) * (dim + 2) / 2 : dim + 1;
+  const int nb = (form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1) ? (dim + 1) * (dim + 2) / 2 : dim + 1;
   return nb * (form == FEM_ELASTIC_P1 ? dim : 1);
 }
+
+bool valid_form(int form) { return form >= FEM_LAPLACE_P1 && form <= FEM_LAPLACE_P2_W1; }
+bool coef_p1(int form) { return form == FEM_LAPLACE_P1_W1 || form == FEM_LAPLACE_P2_W1; }
 
 int resolve_jac(int jac, bool coord_f64, bool out_f64) {
   if (jac == FEM_JAC_AUTO) return (coord_f64 || out_f64) ? fem::JAC_F64 : fem::JAC_COMP;
@@ -107,12 +110,13 @@ const char* fem_status_string(fem_status s) {
 const char* fem_last_error(void) { return g_msg; }
 
 fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den) {
-  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
   if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim must be 2 or 3");
   const int np = form == FEM_ELASTIC_P1 ? dim * dim : dim;
   if (n) *n = form_rows(form, dim);
-  if (n_geom) *n_geom = np * (np + 1) / 2;
-  if (den) *den = (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
+  if (n_geom) *n_geom = np * (np + 1) / 2 * (coef_p1(form) ? dim + 1 : 1);
+  if (den)
+    *den = coef_p1(form) ? (dim == 2 ? 120 : 720) : (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
   return ok();
 }
 
@@ -126,10 +130,14 @@ fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K, size_t ca
     if (form == FEM_LAPLACE_P1) copy_ref<2, fem::LAPLACE_P1>(K);
     if (form == FEM_LAPLACE_P2) copy_ref<2, fem::LAPLACE_P2>(K);
     if (form == FEM_ELASTIC_P1) copy_ref<2, fem::ELASTIC_P1>(K);
+    if (form == FEM_LAPLACE_P1_W1) copy_ref<2, fem::LAPLACE_P1_W1>(K);
+    if (form == FEM_LAPLACE_P2_W1) copy_ref<2, fem::LAPLACE_P2_W1>(K);
   } else {
     if (form == FEM_LAPLACE_P1) copy_ref<3, fem::LAPLACE_P1>(K);
     if (form == FEM_LAPLACE_P2) copy_ref<3, fem::LAPLACE_P2>(K);
     if (form == FEM_ELASTIC_P1) copy_ref<3, fem::ELASTIC_P1>(K);
+    if (form == FEM_LAPLACE_P1_W1) copy_ref<3, fem::LAPLACE_P1_W1>(K);
+    if (form == FEM_LAPLACE_P2_W1) copy_ref<3, fem::LAPLACE_P2_W1>(K);
   }
   return ok();
 }
@@ -138,7 +146,7 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
                              int32_t out_dtype, const fem_options* options, void* stream) {
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
-  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
   if (out_dtype != FEM_F32 && out_dtype != FEM_F64) return fail(FEM_ERR_ARG, "out_dtype out of range");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
@@ -148,10 +156,11 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   if ((cf64 || of64) && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
     return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates or FP64 output need FEM_JAC_F64");
   const bool tc = o->contract == FEM_CONTRACT_BF16X3;
-  if (tc && (form == FEM_LAPLACE_P1 || cf64 || of64 || (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
+  if (tc && (form == FEM_LAPLACE_P1 || coef_p1(form) || cf64 || of64 ||
+             (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
     return fail(FEM_ERR_UNSUPPORTED,
-                "the tensor-core contraction serves P2 and elasticity with FP32 coordinates and output "
-                "and the compensated Jacobian");
+                "the tensor-core contraction serves P2 and elasticity (per-element coefficient) with FP32 "
+                "coordinates and output and the compensated Jacobian");
   fem::FwdLaunch L{};
   L.dim = mesh->dim;
   L.form = form;
@@ -171,6 +180,8 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   cudaError_t e;
   if (tc)
     e = fem::launch_fwd_tc(L);
+  else if (coef_p1(form))
+    e = fem::launch_fwd_w1(L);
   else if (L.dim == 2)
     e = fem::launch_fwd_d2(L);
   else if (form == FEM_ELASTIC_P1)
@@ -213,7 +224,8 @@ fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_
                                   size_t* bytes) {
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
-  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
+  if (coef_p1(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the per-element-coefficient forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (!bytes) return fail(FEM_ERR_ARG, "bytes is NULL");
@@ -245,7 +257,8 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
                              const fem_options* options, void* stream) {
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
-  if (form < FEM_LAPLACE_P1 || form > FEM_ELASTIC_P1) return fail(FEM_ERR_ARG, "form out of range");
+  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
+  if (coef_p1(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the per-element-coefficient forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");

@@ -23,28 +23,40 @@
 // entries); K is folded to K'_{pq} = K_{pq} + K_{qp} (p < q).  The folded K' is
 // symmetric in (i, j), so A is symmetric and only i <= j is computed.
 //
+//   LAPLACE_P1_W1 / LAPLACE_P2_W1 : the Laplacian with a P1 coefficient
+//     w = sum_k w_k lambda_k given by its vertex values (Eqs. 20-23): the
+//     reference tensor gains the coefficient's index,
+//     K^{ij k}_{mu nu} = int_ref lambda_k d_mu phi_i d_nu phi_j   (Eq. 21),
+//     and the geometric tensor becomes w_k G^{mu nu} (Eq. 22), so the
+//     contraction runs over (d+1) x d(d+1)/2 slots, slot k * NGB + g.
+//
 // Integer scaling: every entry is stored as K' * DEN with DEN = (d+2)! (twice
-// that for elasticity), using  int_ref lambda^a = a! / (|a| + d)!.
+// that for elasticity; (d+3)! for the P1-coefficient forms, whose integrands
+// have one more linear factor), using  int_ref lambda^a = a! / (|a| + d)!.
 #pragma once
 #include <cstdint>
 
 namespace fem {
 
-enum FormId : int { LAPLACE_P1 = 0, LAPLACE_P2 = 1, ELASTIC_P1 = 2 };
+enum FormId : int { LAPLACE_P1 = 0, LAPLACE_P2 = 1, ELASTIC_P1 = 2, LAPLACE_P1_W1 = 3, LAPLACE_P2_W1 = 4 };
 
 template <int D, int FORM>
 struct FormTraits {
   static_assert(D == 2 || D == 3, "dimension");
+  static constexpr bool W1 = FORM == LAPLACE_P1_W1 || FORM == LAPLACE_P2_W1;  // P1 coefficient
+  static constexpr int BASE = FORM == LAPLACE_P1_W1 ? LAPLACE_P1 : FORM == LAPLACE_P2_W1 ? LAPLACE_P2 : FORM;
   static constexpr int NV = D + 1;                                // vertices
-  static constexpr int DEG = FORM == LAPLACE_P2 ? 2 : 1;
+  static constexpr int DEG = BASE == LAPLACE_P2 ? 2 : 1;
   static constexpr int NB = DEG == 1 ? D + 1 : (D + 1) * (D + 2) / 2;  // scalar basis
   static constexpr int NC = FORM == ELASTIC_P1 ? D : 1;           // components
   static constexpr int N = NB * NC;                               // rows of A_e
   static constexpr int NN = N * N;
   static constexpr int NP = FORM == ELASTIC_P1 ? D * D : D;       // range of one G slot
-  static constexpr int NG = NP * (NP + 1) / 2;                    // folded G entries
+  static constexpr int NGB = NP * (NP + 1) / 2;                   // folded G entries of the base form
+  static constexpr int NW = W1 ? NV : 1;                          // coefficient values per element
+  static constexpr int NG = NW * NGB;                             // contraction slots
   static constexpr int NT = N * (N + 1) / 2;                      // unique A entries
-  static constexpr int DEN = (D == 2 ? 24 : 120) * (FORM == ELASTIC_P1 ? 2 : 1);
+  static constexpr int DEN = W1 ? (D == 2 ? 120 : 720) : (D == 2 ? 24 : 120) * (FORM == ELASTIC_P1 ? 2 : 1);
 };
 
 // index of the pair (p, q), p <= q, in row-major upper-triangle order
@@ -106,6 +118,23 @@ constexpr int integrate_lin_lin(const Lin& p, const Lin& q) {
   return s;
 }
 
+// (d+3)! * int_ref lambda_k (p)(q) dxi.  Each linear polynomial is made
+// homogeneous (c0 = c0 sum_m lambda_m), and (d+3)! int_ref lambda_a lambda_b
+// lambda_c = a!b!c!-style multiplicity: 6 when a = b = c, 2 when exactly two
+// indices agree, 1 otherwise.
+template <int D>
+constexpr int integrate_lam_lin_lin(int k, const Lin& p, const Lin& q) {
+  int s = 0;
+  for (int a = 0; a <= D; ++a)
+    for (int b = 0; b <= D; ++b) {
+      const int pa = p.c[a] + p.c0, qb = q.c[b] + q.c0;
+      if (pa == 0 || qb == 0) continue;
+      const int m = (a == k && b == k) ? 6 : (a == k || b == k || a == b) ? 2 : 1;
+      s += pa * qb * m;
+    }
+  return s;
+}
+
 template <int D, int FORM>
 struct RefTensor {
   using T = FormTraits<D, FORM>;
@@ -124,7 +153,21 @@ constexpr RefTensor<D, FORM> make_ref_tensor() {
         for (int j = 0; j < T::NB; ++j)
           kref[mu][nu][i][j] = integrate_lin_lin<D>(basis_deriv<D, T::DEG>(i, mu),
                                                     basis_deriv<D, T::DEG>(j, nu));
-  if constexpr (FORM != ELASTIC_P1) {
+  if constexpr (T::W1) {
+    for (int k = 0; k <= D; ++k)
+      for (int mu = 0; mu < D; ++mu)
+        for (int nu = mu; nu < D; ++nu) {
+          int g = k * T::NGB + pair_index(mu, nu, D);
+          for (int i = 0; i < T::NB; ++i)
+            for (int j = 0; j < T::NB; ++j) {
+              const Lin di = basis_deriv<D, T::DEG>(i, mu), dj = basis_deriv<D, T::DEG>(j, nu);
+              int v = integrate_lam_lin_lin<D>(k, di, dj);
+              if (mu != nu)
+                v += integrate_lam_lin_lin<D>(k, basis_deriv<D, T::DEG>(i, nu), basis_deriv<D, T::DEG>(j, mu));
+              r.v[g][i][j] = v;
+            }
+        }
+  } else if constexpr (FORM != ELASTIC_P1) {
     for (int mu = 0; mu < D; ++mu)
       for (int nu = mu; nu < D; ++nu) {
         int g = pair_index(mu, nu, D);

@@ -131,10 +131,30 @@ __device__ __forceinline__ int gather_regs(const CT* coords, int64_t n_vert, int
   return GF_ELEM | GF_OK;
 }
 
+// The element's coefficient: one value (per-element coefficient) or the
+// d+1 vertex values of a P1 coefficient (gathered like the coordinates).
+template <int NW>
+struct Coef {
+  float v[NW];
+};
+
+template <int D, int FORM>
+__device__ __forceinline__ void load_coef(const float* coef, int64_t e, int64_t n_elem, int64_t n_vert,
+                                          const int (&vid)[D + 1], Coef<FormTraits<D, FORM>::NW>& w) {
+  if constexpr (FormTraits<D, FORM>::W1) {
+#pragma unroll
+    for (int k = 0; k <= D; ++k)
+      w.v[k] = (coef && e < n_elem && uint32_t(vid[k]) < uint32_t(n_vert)) ? __ldg(coef + vid[k]) : 1.f;
+  } else {
+    w.v[0] = (coef && e < n_elem) ? __ldg(coef + e) : 1.f;
+  }
+}
+
 // Stage 3 for one tile: geometry, contraction, staging and the coalesced store.
 template <int D, int FORM, int JAC, class CT, class OT>
 __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int64_t tile, int lane, int flags,
-                                                float w, const CT (&X)[D + 1][D], OT* st) {
+                                                const Coef<FormTraits<D, FORM>::NW>& w, const CT (&X)[D + 1][D],
+                                                OT* st) {
   using FT = FormTraits<D, FORM>;
   using PL = FwdPlan<D, FORM, CT, OT>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
@@ -148,15 +168,18 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
     Jac<D, GT> jac;
     const bool nondeg = jacobian<D, JAC>(X, jac);
     err |= nondeg ? 0 : DEVERR_DEGENERATE;
+    const float w0 = FT::W1 ? 1.f : w.v[0];  // a P1 coefficient multiplies the slots below
     GT scale;  // zero for a degenerate element: its matrix is written as zeros
     if constexpr (sizeof(GT) == 4)
-      scale = nondeg ? __fdividef(w, dev_abs(jac.det) * float(FT::DEN)) : 0.f;
+      scale = nondeg ? __fdividef(w0, dev_abs(jac.det) * float(FT::DEN)) : 0.f;
     else
-      scale = nondeg ? GT(w) / (dev_abs(jac.det) * GT(FT::DEN)) : GT(0);
-    GT Gt[FT::NG];
-    geometric_tensor<D, FORM>(jac.adj, scale, Gt);
+      scale = nondeg ? GT(w0) / (dev_abs(jac.det) * GT(FT::DEN)) : GT(0);
+    GT Gt[FT::NGB];
+    geometric_tensor<D, FT::BASE>(jac.adj, scale, Gt);
 #pragma unroll
-    for (int g = 0; g < FT::NG; ++g) Gf[g] = OT(Gt[g]);
+    for (int k = 0; k < FT::NW; ++k)
+#pragma unroll
+      for (int g = 0; g < FT::NGB; ++g) Gf[k * FT::NGB + g] = OT(FT::W1 ? GT(w.v[k]) * Gt[g] : Gt[g]);
   } else if (flags & GF_ELEM) {
     err |= DEVERR_CONN;
   }
@@ -225,6 +248,13 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
   return err;
 }
 
+template <int D, int FORM, int JAC, class CT, class OT>
+__device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int64_t tile, int lane, int flags,
+                                                float w, const CT (&X)[D + 1][D], OT* st) {
+  static_assert(FormTraits<D, FORM>::NW == 1, "one coefficient value per element");
+  return fwd_compute_tile<D, FORM, JAC, CT, OT>(p, tile, lane, flags, Coef<1>{{w}}, X, st);
+}
+
 // One pipeline step: issue the loads of tiles t + 2S (connectivity) and t + S
 // (coordinates, coefficient), then compute and store tile t.  The kernel
 // calls it with the register buffers swapped on alternate steps, so the
@@ -233,11 +263,12 @@ template <int D, int FORM, int JAC, class CT, class OT>
 __device__ __forceinline__ void fwd_step(const FwdParams<CT, OT>& p, int64_t t, int64_t S, int lane,
                                          const int (&vnext)[D + 1], int (&vload)[D + 1],
                                          const CT (&Xcur)[D + 1][D], CT (&Xnext)[D + 1][D], int fcur,
-                                         float wcur, int& fnext, float& wnext, OT* st, int& err) {
+                                         const Coef<FormTraits<D, FORM>::NW>& wcur, int& fnext,
+                                         Coef<FormTraits<D, FORM>::NW>& wnext, OT* st, int& err) {
   const int64_t en = (t + S) * 32 + lane;
   load_conn<D>(p.conn, (t + 2 * S) * 32 + lane, p.n_elem, p.vec_conn, vload);
   fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vnext, Xnext);
-  wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+  load_coef<D, FORM>(p.coef, en, p.n_elem, p.n_vert, vnext, wnext);
   err |= fwd_compute_tile<D, FORM, JAC, CT, OT>(p, t, lane, fcur, wcur, Xcur, st);
 }
 
@@ -255,11 +286,11 @@ __global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
   int va[D + 1], vb[D + 1];
   CT Xa[D + 1][D], Xb[D + 1][D];
   int fa, fb;
-  float wa, wb;
+  Coef<FormTraits<D, FORM>::NW> wa, wb;
   // prologue: tile t gathered, tile t + S connectivity in flight
   load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, va);
   fa = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, va, Xa);
-  wa = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  load_coef<D, FORM>(p.coef, t * 32 + lane, p.n_elem, p.n_vert, va, wa);
   load_conn<D>(p.conn, (t + S) * 32 + lane, p.n_elem, p.vec_conn, va);
   for (;;) {
     fwd_step<D, FORM, JAC>(p, t, S, lane, va, vb, Xa, Xb, fa, wa, fb, wb, st, err);

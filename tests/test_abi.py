@@ -37,6 +37,28 @@ def test_exports_every_declared_symbol(fem):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [3, 4])
+def test_reference_tensor_p1_coefficient(fem, orc, dim, form):
+    """Eq. 22: A = sum_k w_k G : K^{.. k} with the library's arity-3 K equals the
+    oracle's direct quadrature with the P1 coefficient of vertex values w_k."""
+    K, den = fem.reference_tensor(form, dim)
+    K = K.numpy().astype(np.float64)
+    n, ng, _ = fem.form_info(form, dim)
+    ngb = dim * (dim + 1) // 2
+    assert ng == (dim + 1) * ngb and K.shape == (ng, n, n) and den == (120 if dim == 2 else 720)
+    rng = np.random.default_rng(13)
+    for trial in range(8):
+        X = rng.standard_normal((dim + 1, dim)) if trial else np.vstack([np.zeros(dim), np.eye(dim)])
+        if abs(np.linalg.det(X[1:] - X[0])) < 0.05:
+            continue
+        wv = np.exp(rng.standard_normal(dim + 1))
+        G = np.concatenate([wv[k] * _G_true(LP1, X) for k in range(dim + 1)])
+        A = np.einsum("g,gij->ij", G, K) / den
+        Ar, _, _ = orc.element_matrix_w1(dim, form - 3, X, wv)
+        assert np.abs(A - Ar).max() < 1e-12 * np.abs(Ar).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_form_info(fem, dim):
     assert fem.form_info(LP1, dim) == (dim + 1, dim * (dim + 1) // 2, 24 if dim == 2 else 120)
     nb2 = (dim + 1) * (dim + 2) // 2

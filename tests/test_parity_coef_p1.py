@@ -1,0 +1,103 @@
+"""GPU parity of the Laplacian with a P1 coefficient (Eqs. 20-23) against the
+FP64 oracle (-m gpu).  The coefficient is given by its vertex values; the
+library contracts w_k G^{mu nu} with the arity-3 reference tensor.
+
+Tolerance as for the other forms: per element, every element, slivers
+included, max_ij |A_gpu - A_ref| <= tol * max_ij |A_ref| with tol = 1e-5 for
+FP32 output and 1e-12 for the FP64 path."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1103_0066_gb300 import meshgen as mg
+from conftest import rel_err_per_element
+
+pytestmark = pytest.mark.gpu
+LP1, LP2, LP1W, LP2W = 0, 1, 3, 4
+TOL32, TOL64 = 1e-5, 1e-12
+DEV = "cuda:0"
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _mesh(dim, seed=31):
+    if dim == 2:
+        return mg.square_tri_mesh(13, 0.2, mg.rng_for(seed), np.float32)
+    return mg.cube_tet_mesh(7, 0.15, mg.rng_for(seed), 0.05, np.float32)
+
+
+def _wvert(n, seed=32):
+    return mg.lognormal_coef(mg.rng_for(seed), n)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [LP1W, LP2W])
+@pytest.mark.parametrize("jac", [0, 1])
+def test_coef_p1_matches_oracle(gfem, orc, dim, form, jac):
+    mesh = _mesh(dim)
+    w = _wvert(mesh.n_vert)
+    A = gfem.integrate_fwd(_t(mesh.coords), _t(mesh.conn), form, _t(w), jac=jac)
+    torch.cuda.synchronize()
+    Ar, fl = orc.integrate_w1(dim, form - 3, mesh.conn, mesh.coords, w)
+    assert not fl.any()
+    err = rel_err_per_element(A.cpu().numpy(), Ar)
+    assert err.max() <= TOL32, (err.max(), int(err.argmax()))
+    if dim == 3:
+        assert err[mesh.sliver].max() <= TOL32
+
+
+def test_coef_p1_fp64_path(gfem, orc):
+    mesh = mg.workload_tri_p1_fp64()
+    w = _wvert(mesh.n_vert, 33).astype(np.float32)
+    for form in (LP1W, LP2W):
+        A = gfem.integrate_fwd(_t(mesh.coords), _t(mesh.conn), form, _t(w), out_dtype=torch.float64)
+        Ar, _ = orc.integrate_w1(2, form - 3, mesh.conn, mesh.coords, w)
+        assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL64
+
+
+@pytest.mark.parametrize("E", [1, 31, 33, 1000])
+def test_coef_p1_ragged_and_reductions(gfem, orc, E):
+    """Ragged element counts; constant vertex values equal the per-element
+    coefficient path, and the P1 form equals it with the vertex mean."""
+    full = mg.cube_tet_mesh(6, 0.15, mg.rng_for(34), 0.05, np.float32)
+    conn = full.conn[:E]
+    coords, c = _t(full.coords), _t(conn)
+    w = _wvert(full.n_vert, 35)
+    A = gfem.integrate_fwd(coords, c, LP2W, _t(w))
+    Ar, _ = orc.integrate_w1(3, LP2, conn, full.coords, w)
+    assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL32
+    const = np.full(full.n_vert, 1.7, np.float32)
+    A1 = gfem.integrate_fwd(coords, c, LP2W, _t(const))
+    A0 = gfem.integrate_fwd(coords, c, LP2, _t(np.full(E, 1.7, np.float32)))
+    assert rel_err_per_element(A1.cpu().numpy(), A0.cpu().numpy().astype(np.float64)).max() <= 1e-6
+    mean = w[conn].mean(1).astype(np.float32)
+    B1 = gfem.integrate_fwd(coords, c, LP1W, _t(w))
+    B0 = gfem.integrate_fwd(coords, c, LP1, _t(mean))
+    assert rel_err_per_element(B1.cpu().numpy(), B0.cpu().numpy().astype(np.float64)).max() <= 1e-6
+
+
+def test_coef_p1_bad_connectivity_and_no_coefficient(gfem, orc):
+    mesh = _mesh(3)
+    conn = mesh.conn.copy()
+    conn[5, 2] = mesh.n_vert + 3
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    A = gfem.integrate_fwd(_t(mesh.coords), _t(conn), LP2W, _t(_wvert(mesh.n_vert)), dev_err=err)
+    assert int(err.item()) & 1 and torch.all(A[5] == 0)
+    # no coefficient: w = 1, the plain P2 Laplacian
+    A1 = gfem.integrate_fwd(_t(mesh.coords), _t(mesh.conn), LP2W)
+    A0 = gfem.integrate_fwd(_t(mesh.coords), _t(mesh.conn), LP2)
+    assert rel_err_per_element(A1.cpu().numpy(), A0.cpu().numpy().astype(np.float64)).max() <= 1e-6
+
+
+def test_coef_p1_unsupported_paths(gfem):
+    mesh = _mesh(3)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    w = _t(_wvert(mesh.n_vert))
+    with pytest.raises(gfem.FemError):
+        gfem.integrate_bwd(coords, conn, LP2W, torch.zeros(mesh.n_elem, 10, 10, device=DEV), w)
+    with pytest.raises(gfem.FemError):
+        gfem.integrate_fwd(coords, conn, LP2W, w, contract=gfem.CONTRACT_BF16X3)
+    with pytest.raises(ValueError):
+        gfem.integrate_fwd(coords, conn, LP2W, _t(np.ones(mesh.n_elem, np.float32)))  # [E], not [V]
