@@ -49,9 +49,9 @@ KERNEL_SOURCES = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1278.5e6, "src": "3c4282340f8b02f6"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 975.2e6, "src": "6821a74b0aa1b8ae"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.7e6, "src": "c0c9bd793c40989a"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1281.5e6, "src": "5f653bc691601701"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 983.0e6, "src": "a0fce85e3765de45"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.8e6, "src": "c0c9bd793c40989a"},
 }
 
 

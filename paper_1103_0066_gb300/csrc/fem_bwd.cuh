@@ -172,22 +172,33 @@ __device__ __forceinline__ void warp_records(const float* xs, const uint8_t* rec
     int beg = __shfl_up_sync(0xffffffffu, end, 1);
     if (lane == 0) beg = prev;
     prev = __shfl_sync(0xffffffffu, end, 31);
-    if (live) {
-      float acc[D];
+    // Runs have different lengths; the warp steps to its longest run in
+    // blocks of 8 predicated loads, so the loads of a lane are in flight
+    // together.  Each run is still summed in increasing position order.
+    const int len = live ? end - beg : 0;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    float acc[D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] = 0.f;
-      for (int j = beg; j < end; ++j) {
-        if constexpr (D == 3) {
-          const float4 v = *reinterpret_cast<const float4*>(xs + j * XP);
-          acc[0] += v.x;
-          acc[1] += v.y;
-          acc[2] += v.z;
-        } else {
-          const float2 v = *reinterpret_cast<const float2*>(xs + j * XP);
-          acc[0] += v.x;
-          acc[1] += v.y;
+    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int m0 = 0; m0 < maxlen; m0 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (m0 + u < len) {
+          const float* x = xs + (beg + m0 + u) * XP;
+          if constexpr (D == 3) {
+            const float4 v = *reinterpret_cast<const float4*>(x);
+            acc[0] += v.x;
+            acc[1] += v.y;
+            acc[2] += v.z;
+          } else {
+            const float2 v = *reinterpret_cast<const float2*>(x);
+            acc[0] += v.x;
+            acc[1] += v.y;
+          }
         }
       }
+    }
+    if (live) {
       float* dst = records + int64_t(dest) * D;
 #pragma unroll
       for (int a = 0; a < D; ++a) dst[a] = acc[a];

@@ -9,10 +9,14 @@
 //                       K as immediates, staging and coalesced 16-byte
 //                       evict-first stores of the tile's 32 * n^2 contiguous outputs
 // so the gather latency hides behind the previous tile's arithmetic.  For the
-// 4x4 element matrices the stage uses an XOR swizzle of the 16-byte row
-// chunks, which keeps both the row writes and the coalesced read-out free of
-// shared-memory bank conflicts; other shapes use an odd row stride.  Every
-// element is integrated: the final tile is partial (no dropped tail).
+// 4x4 FP32 element matrices the stage is the 64-byte-swizzled image of the
+// tile's 32 rows (16-byte chunk q of row l at q ^ ((l >> 1) & 3): bank-
+// conflict-free row writes), double buffered, and one lane stores the whole
+// tile with a TMA tensor store that undoes the swizzle; without a tensor map
+// (unaligned A) the warp reads the stage back into coalesced 16-byte
+// evict-first stores.  Other shapes use an odd row stride and the coalesced
+// read-out.  Every element is integrated: the final tile is partial (no
+// dropped tail; the tensor store clips rows past the end).
 #pragma once
 #include <cuda_runtime.h>
 
@@ -49,6 +53,8 @@ struct FwdPlan {
   static constexpr int SST = SWZ16 ? 16 : stage_stride<NN>();
   static constexpr size_t stage_bytes = align_up(size_t(32) * SST * sizeof(OT), 128);
   static constexpr size_t per_warp = stage_bytes;
+  // TMA store variant (SWZ16 only): two 2 KB stages per warp, 1024-byte aligned
+  static constexpr size_t tma_per_warp = 2 * 2048;
 };
 
 template <int N, int SST, class OT>
@@ -150,11 +156,12 @@ __device__ __forceinline__ void load_coef(const float* coef, int64_t e, int64_t 
   }
 }
 
-// Stage 3 for one tile: geometry, contraction, staging and the coalesced store.
-template <int D, int FORM, int JAC, class CT, class OT>
+// Stage 3 for one tile: geometry, contraction, staging and the coalesced store
+// (TMA: the tensor store of the stage through tmap).
+template <int D, int FORM, int JAC, class CT, class OT, bool TMA = false>
 __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int64_t tile, int lane, int flags,
                                                 const Coef<FormTraits<D, FORM>::NW>& w, const CT (&X)[D + 1][D],
-                                                OT* st) {
+                                                OT* st, const CUtensorMap* tmap = nullptr) {
   using FT = FormTraits<D, FORM>;
   using PL = FwdPlan<D, FORM, CT, OT>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
@@ -192,10 +199,23 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
     contract<D, FORM>(Gf, rs);
     const int sw = (lane >> 1) & 3;
     float* row = st + lane * 16;
+    if constexpr (TMA) {
+      if (lane == 0) bulk_wait_read<1>();  // the store that last read this stage (two tiles ago) is done
+      __syncwarp();
+    }
 #pragma unroll
     for (int r = 0; r < 4; ++r)
       *reinterpret_cast<float4*>(row + 4 * (r ^ sw)) =
           make_float4(rs.a[4 * r], rs.a[4 * r + 1], rs.a[4 * r + 2], rs.a[4 * r + 3]);
+    if constexpr (TMA) {
+      fence_proxy_async_smem();  // the rows are visible to the tensor store
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(tmap, 0, int(e0), smem_u32(st));
+        bulk_commit();
+      }
+      return err;
+    }
     __syncwarp();
     // chunk c = lane + 32 r holds element (lane >> 2) + 8 r, row lane & 3
     const float* src = st + 16 * (lane >> 2) + 4 * ((lane & 3) ^ ((lane >> 3) & 3));
@@ -259,25 +279,31 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
 // (coordinates, coefficient), then compute and store tile t.  The kernel
 // calls it with the register buffers swapped on alternate steps, so the
 // pipeline rotates without register copies.
-template <int D, int FORM, int JAC, class CT, class OT>
+template <int D, int FORM, int JAC, class CT, class OT, bool TMA>
 __device__ __forceinline__ void fwd_step(const FwdParams<CT, OT>& p, int64_t t, int64_t S, int lane,
                                          const int (&vnext)[D + 1], int (&vload)[D + 1],
                                          const CT (&Xcur)[D + 1][D], CT (&Xnext)[D + 1][D], int fcur,
                                          const Coef<FormTraits<D, FORM>::NW>& wcur, int& fnext,
-                                         Coef<FormTraits<D, FORM>::NW>& wnext, OT* st, int& err) {
+                                         Coef<FormTraits<D, FORM>::NW>& wnext, OT* st, const CUtensorMap* tmap,
+                                         int& err) {
   const int64_t en = (t + S) * 32 + lane;
   load_conn<D>(p.conn, (t + 2 * S) * 32 + lane, p.n_elem, p.vec_conn, vload);
   fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vnext, Xnext);
   load_coef<D, FORM>(p.coef, en, p.n_elem, p.n_vert, vnext, wnext);
-  err |= fwd_compute_tile<D, FORM, JAC, CT, OT>(p, t, lane, fcur, wcur, Xcur, st);
+  err |= fwd_compute_tile<D, FORM, JAC, CT, OT, TMA>(p, t, lane, fcur, wcur, Xcur, st, tmap);
 }
 
-template <int D, int FORM, int JAC, class CT, class OT>
-__global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
+template <int D, int FORM, int JAC, class CT, class OT, bool TMA>
+__global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p, const __grid_constant__ CUtensorMap tmap) {
   using PL = FwdPlan<D, FORM, CT, OT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  OT* st = reinterpret_cast<OT*>(smem_raw + size_t(warp) * PL::per_warp);
+  // TMA: two 1024-byte-aligned stages per warp (the swizzle follows the shared address)
+  unsigned char* sbase =
+      TMA ? reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023))
+          : smem_raw;
+  OT* st = reinterpret_cast<OT*>(sbase + size_t(warp) * (TMA ? PL::tma_per_warp : PL::per_warp));
+  OT* st2 = TMA ? st + 2048 / sizeof(OT) : st;
   const int64_t ntiles = (p.n_elem + 31) / 32;
   const int64_t S = int64_t(gridDim.x) * nwarps;
   int64_t t = int64_t(blockIdx.x) * nwarps + warp;
@@ -293,10 +319,13 @@ __global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p) {
   load_coef<D, FORM>(p.coef, t * 32 + lane, p.n_elem, p.n_vert, va, wa);
   load_conn<D>(p.conn, (t + S) * 32 + lane, p.n_elem, p.vec_conn, va);
   for (;;) {
-    fwd_step<D, FORM, JAC>(p, t, S, lane, va, vb, Xa, Xb, fa, wa, fb, wb, st, err);
+    fwd_step<D, FORM, JAC, CT, OT, TMA>(p, t, S, lane, va, vb, Xa, Xb, fa, wa, fb, wb, st, &tmap, err);
     if ((t += S) >= ntiles) break;
-    fwd_step<D, FORM, JAC>(p, t, S, lane, vb, va, Xb, Xa, fb, wb, fa, wa, st, err);
+    fwd_step<D, FORM, JAC, CT, OT, TMA>(p, t, S, lane, vb, va, Xb, Xa, fb, wb, fa, wa, st2, &tmap, err);
     if ((t += S) >= ntiles) break;
+  }
+  if constexpr (TMA) {
+    if (lane == 0) bulk_wait<0>();  // the stages outlive every tensor store that reads them
   }
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
@@ -315,13 +344,22 @@ cudaError_t launch_fwd_t(const FwdLaunch& L) {
   p.dev_err = L.dev_err;
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_store = (reinterpret_cast<uintptr_t>(L.A) % 16 == 0);
-  auto kern = fem_fwd_kernel<D, FORM, JAC, CT, OT>;
-  const int warps = clamp_warps(L.warps, PL::per_warp);
-  const size_t smem = size_t(warps) * PL::per_warp;
+  CUtensorMap tmap{};
+  bool tma = false;
+  auto kern = fem_fwd_kernel<D, FORM, JAC, CT, OT, false>;
+  if constexpr (PL::SWZ16) {
+    if (encode_rows16_map(&tmap, L.A, L.n_elem)) {
+      tma = true;
+      kern = fem_fwd_kernel<D, FORM, JAC, CT, OT, true>;
+    }
+  }
+  const size_t per_warp = tma ? PL::tma_per_warp : PL::per_warp;
+  const int warps = clamp_warps(L.warps, per_warp);
+  const size_t smem = size_t(warps) * per_warp + (tma ? 1024 : 0);
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
   const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), warps, smem, L.n_elem, L.ctas_per_sm);
-  kern<<<grid, warps * 32, smem, L.stream>>>(p);
+  kern<<<grid, warps * 32, smem, L.stream>>>(p, tmap);
   return cudaGetLastError();
 }
 

@@ -2,6 +2,8 @@
 // element, Eqs. 5 and 8) and host-side device queries.
 #include <mutex>
 
+#include <cudaTypedefs.h>
+
 #include "fem_core.cuh"
 #include "fem_fwd.cuh"
 #include "fem_internal.h"
@@ -136,6 +138,35 @@ cudaError_t ensure_smem(const void* kernel, size_t bytes) {
   // prefer the largest shared-memory carveout so that several such CTAs fit on an SM
   return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                               int(cudaSharedmemCarveoutMaxShared));
+}
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+}  // namespace
+
+bool encode_rows16_map(CUtensorMap* map, const void* base, int64_t rows) {
+  if (!base || rows <= 0 || rows > (int64_t(1) << 32) || reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {16, cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {64};  // bytes between rows
+  const cuuint32_t box[2] = {16, 32};  // one warp's tile
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace fem

@@ -1,14 +1,21 @@
 // fem_pipe.cuh -- asynchronous data movement used by the element kernels:
-// per-lane cp.async (LDGSTS) gathers into shared memory, TMA 1D bulk stores
-// (cp.async.bulk shared::cta -> global) and their completion waits.
+// per-lane cp.async (LDGSTS) copies into shared memory, TMA bulk and tiled
+// tensor stores (cp.async.bulk[.tensor]) with their bulk-group completion, and
+// the host-side encoding of the tensor maps.
 //
-// The element kernels run a software pipeline per warp over their tiles
-// (32 consecutive elements): the connectivity of tile t+2 is loaded into
-// registers, the vertex coordinates of tile t+1 are copied asynchronously into
-// lane-private shared-memory slots, and tile t is computed from its slot.  The
-// gather latency (HBM for the connectivity, L2 for the coordinates) is thus
-// covered by the arithmetic of the previous tile instead of by occupancy.
+// Tiled tensor stores serve arrays of 64-byte rows (16 FP32: the 4x4 element
+// matrices of P1 tetrahedra): one 2D box of 16 x 32 values is one warp's tile,
+// staged in shared memory with the 64-byte swizzle, i.e. 16-byte chunk q of
+// row l at chunk q ^ ((l >> 1) & 3), so that lane l writing its own row chunk
+// by chunk hits eight distinct bank groups per quarter warp.  The swizzle is a
+// function of the shared address, so such buffers are 1024-byte aligned.
+// (A tensor load of the adjoint's dA tiles in the same layout was measured
+// slower than per-lane 16-byte cp.async, 411 against 350 us at 128^3, and is
+// not used.)
 #pragma once
+#include <cuda.h>  // CUtensorMap and its enums (types only; the driver is reached through the runtime)
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace fem {
@@ -58,5 +65,24 @@ template <int N>
 __device__ __forceinline__ void bulk_wait() {
   asm volatile("cp.async.bulk.wait_group %0;\n" ::"n"(N) : "memory");
 }
+
+// ------------------------------------------------------------------ TMA tensor copies
+
+// 2D tiled store of box (x, y) from shared memory (bulk group of this thread);
+// rows outside the tensor are not written.  The output is streamed (L2
+// evict-first), like the per-lane evict-first stores it replaces.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, uint32_t src) {
+  asm volatile(
+      "{\n .reg .b64 pol;\n createpolicy.fractional.L2::evict_first.b64 pol, 1.0;\n"
+      " cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], pol;\n}\n"
+      ::"l"(map), "r"(x), "r"(y), "r"(src)
+      : "memory");
+}
+
+// Host: tensor map of a row-major [rows][16] FP32 array (64-byte rows) with
+// boxes of 16 x 32 values and the 64-byte shared-memory swizzle.  false when
+// the array cannot be described (base not 16-byte aligned, too many rows, or
+// no driver entry point).
+bool encode_rows16_map(CUtensorMap* map, const void* base, int64_t rows);
 
 }  // namespace fem
