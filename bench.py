@@ -616,6 +616,65 @@ def run_coef_p1(args):
     print(json.dumps(out), flush=True)
 
 
+def run_tri64_fp64(args):
+    """The 64x64 jittered square (8,192 triangles), FP64 coordinates and FP64
+    3x3 element matrices: launch-bound, reported in microseconds per launch
+    (eager) and per replay of a CUDA graph of 100 launches."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh = mg.workload_tri_p1_fp64()
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    A = torch.empty((mesh.n_elem, 3, 3), dtype=torch.float64, device=dev)
+    stream = torch.cuda.Stream(dev)
+
+    def step():
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        eager_us = s0.elapsed_time(s1) / args.steps * 1e3
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            for _ in range(100):
+                step()
+        g.replay()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(max(1, args.steps // 100)):
+            g.replay()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        graph_us = s0.elapsed_time(s1) / (100 * max(1, args.steps // 100)) * 1e3
+    Ar, _ = oracle.integrate(2, oracle.LAPLACE_P1, mesh.conn, mesh.coords)
+    Ag = A.cpu().numpy()
+    err = float((np.abs(Ag - Ar).reshape(mesh.n_elem, -1).max(1) / np.abs(Ar).reshape(mesh.n_elem, -1).max(1)).max())
+    E = mesh.n_elem
+    out = {"metric": METRIC, "value": E / (graph_us * 1e-6), "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": graph_us * 1e-3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2D P1 Laplacian, 64x64 jittered square (8,192 triangles), FP64 coordinates "
+                                  "and 3x3 FP64 element matrices, forward; launch-bound",
+                      "elements": E, "l2": "inputs and outputs (0.8 MB) are L2-resident"},
+           "us_per_launch": {"eager": eager_us, "cuda_graph": graph_us},
+           "max_rel_err_vs_fp64_oracle": err, "roofline": None, "gpu_launches": args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint64(args):
     """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
     lognormal coefficient (dcoords and dcoef), both reductions."""
@@ -721,11 +780,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
-    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1"],
+    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64"],
                     default="tet128",
                     help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
                          "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
-                         "coef_p1: P2 Laplacian with a P1 coefficient")
+                         "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -740,6 +799,8 @@ def main():
         run_adjoint64(args)
     elif args.workload == "coef_p1":
         run_coef_p1(args)
+    elif args.workload == "tri64_fp64":
+        run_tri64_fp64(args)
     else:
         run_ours(args)
 
