@@ -675,6 +675,85 @@ def run_tri64_fp64(args):
     print(json.dumps(out), flush=True)
 
 
+def run_assemble(args):
+    """Global assembly of the 128^3 sliver cube's P1 Laplacian element matrices
+    into CSR (vertex graph), deterministic: element integration then assembly,
+    each timed."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1103_0066_gb300 as fem
+
+    dev = torch.device("cuda:0")
+    mesh, _ = tet_workload(args.mesh_n)
+    E, V = mesh.n_elem, mesh.n_vert
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    asm = fem.Assembly(coords, conn, fem.LAPLACE_P1)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    A = fem.integrate_fwd(coords, conn, fem.LAPLACE_P1)
+    vals = torch.empty(asm.nnz, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / args.steps
+
+    asm_ms = timed(lambda: asm.assemble(A, out=vals))
+    fwd_ms = timed(lambda: fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A))
+    # rows checked against the FP64 oracle: every row of a sample of vertices
+    rng = np.random.default_rng(9)
+    rows = np.unique(rng.choice(V, 2000, replace=False))
+    rp = asm.row_ptr.cpu().numpy()
+    ci = asm.col_idx.cpu().numpy()
+    vh = vals.cpu().numpy()
+    inc = np.zeros(V, bool)
+    inc[rows] = True
+    el = np.where(inc[mesh.conn].any(1))[0]
+    Ar, _ = oracle.integrate(3, oracle.LAPLACE_P1, mesh.conn[el], mesh.coords)
+    Mr = oracle.assemble(3, oracle.LAPLACE_P1, mesh.conn[el], V, Ar)
+    elmax = np.abs(Ar).reshape(len(el), -1).max(1)
+    bound = np.zeros(V)
+    for i in range(4):
+        np.add.at(bound, mesh.conn[el, i], elmax)
+    err = 0.0
+    for v in rows:
+        ref = dict(zip(Mr.indices[Mr.indptr[v]:Mr.indptr[v + 1]], Mr.data[Mr.indptr[v]:Mr.indptr[v + 1]]))
+        got = dict(zip(ci[rp[v]:rp[v + 1]], vh[rp[v]:rp[v + 1]]))
+        if not ref:
+            continue
+        err = max(err, max(abs(got.get(k, 0.0) - ref[k]) for k in ref) / bound[v])
+    nnz = asm.nnz
+    byts = E * 16 * 4 + E * 4 * 4 + E * 16 + 2 * (V + 1) * 4 + nnz * 4  # A, incidences, colpos, offsets, values
+    peak, peak_kind = hbm_peak()
+    gbs = byts / (asm_ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": E / (asm_ms * 1e-3), "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": asm_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"global CSR assembly of the P1 Laplacian element matrices, {args.mesh_n}^3 "
+                                  f"Kuhn cube with 5% slivers ({E:,} tets, {V:,} vertices, {nnz:,} nonzeros), "
+                                  "deterministic (element order)",
+                      "elements": E, "nnz": nnz, "l2": "no flush: 1.4 GB moved per step"},
+           "roofline": {"bound": "hbm", "kernel": "assemble_kernel<4,1>", "achieved": gbs, "peak": peak,
+                        "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                        "traffic": None, "algorithmic_bytes": byts},
+           "forward_ms": fwd_ms, "build_ms": build_ms, "max_row_err_vs_fp64": err,
+           "error_metric": "per row v: max |a - a_fp64| / (sum over the elements at v of max |A_e|)",
+           "error_sample": f"all entries of {len(rows):,} random rows", "gpu_launches": args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint64(args):
     """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
     lognormal coefficient (dcoords and dcoef), both reductions."""
@@ -780,11 +859,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
-    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64"],
+    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64",
+                                           "assemble128"],
                     default="tet128",
                     help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
                          "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
-                         "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh")
+                         "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh; "
+                         "assemble128: global CSR assembly")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -801,6 +882,8 @@ def main():
         run_coef_p1(args)
     elif args.workload == "tri64_fp64":
         run_tri64_fp64(args)
+    elif args.workload == "assemble128":
+        run_assemble(args)
     else:
         run_ours(args)
 

@@ -260,6 +260,42 @@ FEM_API fem_status fem_batch_errors(const fem_batch* batch, int32_t* err_host, v
 /* Releases the host object (the caller frees the workspace). */
 FEM_API void fem_batch_destroy(fem_batch* batch);
 
+/* ------------------------------------------------------------------ assembly
+ * Global sparse assembly, the step after the element integration:
+ * A = sum_e P_e^T A_e P_e over the vertex graph of the mesh.  The scalar P1
+ * forms (FEM_LAPLACE_P1, FEM_LAPLACE_P1_W1) give CSR; FEM_ELASTIC_P1 gives BSR
+ * with d x d blocks over the same pattern (node-major unknowns v*d + c; block
+ * (c, c') of entry (v, w) sums A_e[(c,i),(c',j)] over the elements with
+ * conn[e][i] = v, conn[e][j] = w, local unknown (c, i) being row c*(d+1) + i
+ * of A_e).  The P2 forms are not assembled (FEM_ERR_UNSUPPORTED): their
+ * unknowns include the edges.  Every entry is the sum of its element
+ * contributions in increasing element order, so values are bitwise
+ * reproducible.  Rows have at most 255 columns and 128 incident elements
+ * (FEM_ERR_UNSUPPORTED otherwise). */
+
+/* Device workspace bytes of the assembly maps of this mesh (depends on the
+ * connectivity only; the capacity of the column array is every entry distinct). */
+FEM_API fem_status fem_assembly_workspace_size(const fem_mesh* mesh, int32_t form, size_t* bytes);
+
+/* Builds the row pattern (row_ptr [n_vert+1], col_idx [nnz], columns increasing)
+ * and the incidence maps into `ws` (device, caller owned, 256-byte aligned),
+ * once per connectivity, on `stream`, which it synchronizes; *nnz (may be NULL)
+ * receives the number of nonzero entries (blocks).  A connectivity entry outside
+ * [0, n_vert) is FEM_ERR_ARG. */
+FEM_API fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size_t ws_bytes, int64_t* nnz,
+                                      void* stream);
+
+/* Device pointers to the pattern inside a built workspace (row_ptr [n_vert+1],
+ * col_idx [nnz]); either output may be NULL. */
+FEM_API fem_status fem_assembly_pattern(const fem_mesh* mesh, int32_t form, const void* ws, size_t ws_bytes,
+                                        const int32_t** row_ptr, const int32_t** col_idx);
+
+/* Assembles the FP32 element matrices A (device [n_elem][n][n], as written by
+ * fem_integrate_fwd) into values (device FP32 [nnz][b][b], b = 1 or d; overwritten),
+ * asynchronously on `stream`. */
+FEM_API fem_status fem_assemble(const fem_mesh* mesh, int32_t form, const float* A, const void* ws, size_t ws_bytes,
+                                float* values, void* stream);
+
 /* Bytes of the scratch array built into the library for
  * fem_integrate_bwd_noalloc (32 MiB: the deterministic adjoint of a tet mesh
  * of up to roughly 300,000 elements). */

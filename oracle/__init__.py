@@ -221,3 +221,33 @@ def integrate_vjp(dim: int, form: int, conn, coords, dA, coef=None, q: int = 3,
     if rc < 0:
         raise ValueError("bad vjp request")
     return dcoords, dcoef
+
+
+def assemble(dim: int, form: int, conn, n_vert: int, A):
+    """Global matrix sum_e P_e^T A_e P_e of the element matrices A [E][n][n]
+    (FP64 scipy CSR over scalar unknowns): every element entry is placed at its
+    global (row, column) and duplicates are summed (scipy's COO -> CSR
+    conversion).  P1 forms only: unknown v for the Laplacian; for P1 elasticity
+    the node-major unknown v*dim + c of the local unknown (c, i) = row
+    c*(dim+1) + i of A_e."""
+    import scipy.sparse as sps
+    conn = np.asarray(conn, dtype=np.int64)
+    A = np.asarray(A, dtype=np.float64)
+    E, nv = conn.shape
+    if form == ELASTIC_P1:
+        g = (conn[:, None, :] * dim + np.arange(dim)[None, :, None]).reshape(E, dim * nv)
+        N = n_vert * dim
+    elif form == LAPLACE_P1:
+        g = conn
+        N = n_vert
+    else:
+        raise ValueError("assembly of the P1 forms only")
+    n = g.shape[1]
+    if A.shape != (E, n, n):
+        raise ValueError("A must be [E][n][n]")
+    rows = np.repeat(g, n, axis=1).ravel()
+    cols = np.tile(g, (1, n)).ravel()
+    M = sps.coo_matrix((A.reshape(-1), (rows, cols)), shape=(N, N)).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return M

@@ -24,7 +24,7 @@ from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENER
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT)
 
-__all__ = ["Mesh", "Batch", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+__all__ = ["Mesh", "Batch", "Assembly", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
            "LAPLACE_P2_W1", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
@@ -117,6 +117,41 @@ class Workspace:
         per-tile record offsets (32-element record tiles).  Synchronizes."""
         T = (self.m.n_elem + 31) // 32
         return int(self.buf[4 * T: 4 * T + 4].view(torch.int32).item())
+
+
+class Assembly:
+    """Global sparse assembly (fem_assembly_*) of the element matrices of one
+    connectivity: CSR for the scalar P1 forms, BSR with d x d blocks for
+    ELASTIC_P1 (node-major unknowns v*d + c).
+
+    row_ptr [V+1] and col_idx [nnz] (int32, device) describe the pattern;
+    assemble(A) returns the values [nnz] (or [nnz][d][d]) of sum_e P_e^T A_e P_e,
+    each entry summed in increasing element order."""
+
+    def __init__(self, coords, conn, form=LAPLACE_P1, stream=None):
+        self.m = _mesh_struct(coords, conn)
+        self.form = form
+        self.block = self.m.dim if form == ELASTIC_P1 else 1
+        self.bytes = nat.fem_assembly_workspace_size(self.m, form)
+        self.buf = torch.empty(max(self.bytes, 256), dtype=torch.uint8, device=coords.device)
+        self._keep = (coords, conn)
+        self.nnz = nat.fem_assembly_build(self.m, form, self.buf.data_ptr(), self.bytes, _stream_ptr(stream))
+        rp, ci = nat.fem_assembly_pattern(self.m, form, self.buf.data_ptr(), self.bytes)
+        V = coords.shape[0]
+        base = self.buf.data_ptr()
+        self.row_ptr = self.buf[rp - base: rp - base + 4 * (V + 1)].view(torch.int32)
+        self.col_idx = self.buf[ci - base: ci - base + 4 * self.nnz].view(torch.int32)
+
+    def assemble(self, A, out=None, stream=None):
+        b = self.block
+        shape = (self.nnz,) if b == 1 else (self.nnz, b, b)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=A.device)
+        if A.dtype != torch.float32 or not A.is_contiguous() or out.shape != shape or not out.is_contiguous():
+            raise ValueError("A must be contiguous float32 [E][n][n]; out float32 " + str(shape))
+        nat.fem_assemble(self.m, self.form, A.data_ptr(), self.buf.data_ptr(), self.bytes, out.data_ptr(),
+                         _stream_ptr(stream))
+        return out
 
 
 def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None,

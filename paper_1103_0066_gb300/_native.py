@@ -26,7 +26,8 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
            "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
-           "fem_batch_errors", "fem_batch_destroy")
+           "fem_batch_errors", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
+           "fem_assembly_pattern", "fem_assemble")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT = 0, 1, 2
 DEVERR_TIMEOUT = 4
@@ -94,6 +95,10 @@ def load():
             "fem_batch_run": ([P, I32, P], ctypes.c_int),
             "fem_batch_errors": ([P, ctypes.POINTER(I32), P], ctypes.c_int),
             "fem_batch_destroy": ([P], None),
+            "fem_assembly_workspace_size": ([MP, I32, ctypes.POINTER(SZ)], ctypes.c_int),
+            "fem_assembly_build": ([MP, I32, P, SZ, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
+            "fem_assembly_pattern": ([MP, I32, P, SZ, ctypes.POINTER(P), ctypes.POINTER(P)], ctypes.c_int),
+            "fem_assemble": ([MP, I32, P, P, SZ, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -218,3 +223,27 @@ def fem_batch_errors(handle: int, stream: int) -> int:
 
 def fem_batch_destroy(handle: int) -> None:
     load().fem_batch_destroy(handle)
+
+
+def fem_assembly_workspace_size(mesh: FemMesh, form: int) -> int:
+    b = ctypes.c_size_t()
+    check(load().fem_assembly_workspace_size(ctypes.byref(mesh), form, ctypes.byref(b)))
+    return b.value
+
+
+def fem_assembly_build(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    nnz = ctypes.c_int64()
+    check(load().fem_assembly_build(ctypes.byref(mesh), form, ws_ptr, ws_bytes, ctypes.byref(nnz), stream or None))
+    return nnz.value
+
+
+def fem_assembly_pattern(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int):
+    rp, ci = ctypes.c_void_p(), ctypes.c_void_p()
+    check(load().fem_assembly_pattern(ctypes.byref(mesh), form, ws_ptr, ws_bytes, ctypes.byref(rp), ctypes.byref(ci)))
+    return rp.value or 0, ci.value or 0
+
+
+def fem_assemble(mesh: FemMesh, form: int, A_ptr: int, ws_ptr: int, ws_bytes: int, values_ptr: int,
+                 stream: int) -> None:
+    check(load().fem_assemble(ctypes.byref(mesh), form, A_ptr or None, ws_ptr, ws_bytes, values_ptr or None,
+                              stream or None))

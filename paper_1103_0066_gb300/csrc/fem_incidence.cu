@@ -368,6 +368,25 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   return off;
 }
 
+size_t scan_partials_count(int64_t n) { return size_t((n + kScanBlock - 1) / kScanBlock + 1); }
+
+cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, int32_t* partials, int32_t* offsets,
+                                  cudaStream_t stream) {
+  exclusive_scan(cnt, n, partials, offsets, stream);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_key_csr(const int32_t* keys, int64_t n_keys, int64_t n_seg, int32_t* off, int32_t* list,
+                           int32_t* cursor, int32_t* partials, cudaStream_t stream) {
+  fill_i32<<<grid_for(n_seg, 256), 256, 0, stream>>>(cursor, n_seg, 0);
+  count_kernel<<<grid_for(n_keys, 256), 256, 0, stream>>>(keys, n_keys, n_seg, cursor);
+  exclusive_scan(cursor, n_seg, partials, off, stream);
+  fill_i32<<<grid_for(n_seg, 256), 256, 0, stream>>>(cursor, n_seg, 0);
+  fill_kernel<<<grid_for(n_keys, 256), 256, 0, stream>>>(keys, n_keys, n_seg, off, cursor, list);
+  sort_segments_kernel<<<grid_for((n_seg + 3) / 4, 128), 128, 0, stream>>>(off, n_seg, list);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream) {
   const int nv = dim + 1;
@@ -383,12 +402,7 @@ cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem,
   tile_records_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.tile_rec,
                                                          ws.rec_end, ws.rec_vertex);
   // vertex -> records CSR
-  fill_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert, 0);
-  count_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, n_vert, ws.cursor);
-  exclusive_scan(ws.cursor, n_vert, ws.partials, ws.voff, stream);
-  fill_i32<<<grid_for(n_vert, 256), 256, 0, stream>>>(ws.cursor, n_vert, 0);
-  fill_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, n_vert, ws.voff, ws.cursor, ws.vrec);
-  sort_segments_kernel<<<grid_for((n_vert + 3) / 4, 128), 128, 0, stream>>>(ws.voff, n_vert, ws.vrec);
+  launch_key_csr(ws.rec_vertex, r_max, n_vert, ws.voff, ws.vrec, ws.cursor, ws.partials, stream);
   dest_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.voff, n_vert, ws.vrec, ws.rec_dest);
   return cudaGetLastError();
 }

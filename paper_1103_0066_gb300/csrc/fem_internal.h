@@ -92,6 +92,15 @@ cudaError_t launch_bwd_elem(const BwdLaunch& L);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t stream);
+// off[0..n_seg] and list[0..n_keys) = the CSR of the indices s with keys[s] in
+// [0, n_seg), each segment sorted increasingly (keys out of range are left
+// out).  cursor: n_seg + 1 ints of scratch; partials: scan_partials_count(n_seg).
+cudaError_t launch_key_csr(const int32_t* keys, int64_t n_keys, int64_t n_seg, int32_t* off, int32_t* list,
+                           int32_t* cursor, int32_t* partials, cudaStream_t stream);
+size_t scan_partials_count(int64_t n);
+// offsets[0..n] = exclusive prefix sums of cnt[0..n) (offsets[n] = total).
+cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, int32_t* partials, int32_t* offsets,
+                                  cudaStream_t stream);
 cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert, float* dcoords,
                                  cudaStream_t stream);
 
