@@ -143,11 +143,18 @@ __global__ void __launch_bounds__(kPatWarps * 32)
 }
 
 // N = rows of A_e = NV * B; local unknown (c, i) is row c * NV + i.
+// Incidences are taken in groups of kAsmBatch: all their loads (incidence,
+// column positions, element rows) are issued before the group's additions,
+// which then run in increasing incidence order.  For tets the four column
+// positions are one 4-byte load and an element row of a scalar form is one
+// 16-byte load.
+constexpr int kAsmBatch = 4;
+
 template <int NV, int B>
 __global__ void __launch_bounds__(kAsmThreads)
     assemble_kernel(const int32_t* __restrict__ inc_off, const int32_t* __restrict__ inc,
                     const uint8_t* __restrict__ colpos, const int32_t* __restrict__ row_ptr,
-                    const float* __restrict__ A, int64_t n_vert, float* __restrict__ val) {
+                    const float* __restrict__ A, int64_t n_vert, float* __restrict__ val, int vec_A) {
   constexpr int N = NV * B, BB = B * B;
   extern __shared__ float acc_s[];  // [kAsmThreads][kFastCols * BB + 1]
   float* acc = acc_s + threadIdx.x * (kFastCols * BB + 1);
@@ -159,20 +166,54 @@ __global__ void __launch_bounds__(kAsmThreads)
     float* dst = fast ? acc : val + int64_t(rp) * BB;
     for (int q = 0; q < len * BB; ++q) dst[q] = 0.f;
     const int32_t t1 = inc_off[v + 1];
-    for (int32_t t = inc_off[v]; t < t1; ++t) {
-      const int32_t s = __ldg(inc + t);
-      const int i = s % NV;
-      const float* Ae = A + int64_t(s / NV) * (N * N);
-      uint8_t pos[NV];
+    for (int32_t t0 = inc_off[v]; t0 < t1; t0 += kAsmBatch) {
+      int32_t s[kAsmBatch];
+      uint8_t pos[kAsmBatch][NV];
+      float a[kAsmBatch][B][B][NV];
 #pragma unroll
-      for (int j = 0; j < NV; ++j) pos[j] = __ldg(colpos + int64_t(t) * NV + j);
+      for (int u = 0; u < kAsmBatch; ++u) s[u] = t0 + u < t1 ? __ldg(inc + t0 + u) : 0;
 #pragma unroll
-      for (int c = 0; c < B; ++c)
+      for (int u = 0; u < kAsmBatch; ++u) {
+        const int32_t t = t0 + u < t1 ? t0 + u : t0;
+        if constexpr (NV == 4) {
+          const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(colpos) + t);
 #pragma unroll
-        for (int j = 0; j < NV; ++j)
+          for (int j = 0; j < 4; ++j) pos[u][j] = uint8_t(w >> (8 * j));
+        } else {
 #pragma unroll
-          for (int c2 = 0; c2 < B; ++c2)
-            dst[pos[j] * BB + c * B + c2] += __ldg(Ae + (c * NV + i) * N + c2 * NV + j);
+          for (int j = 0; j < NV; ++j) pos[u][j] = __ldg(colpos + int64_t(t) * NV + j);
+        }
+        const int i = s[u] % NV;
+        const float* Ae = A + int64_t(s[u] / NV) * (N * N);
+#pragma unroll
+        for (int c = 0; c < B; ++c)
+#pragma unroll
+          for (int c2 = 0; c2 < B; ++c2) {
+            const float* src = Ae + (c * NV + i) * N + c2 * NV;
+            if constexpr (NV == 4) {
+              if (vec_A) {  // 16-byte aligned: (c*NV + i)*N + c2*NV is a multiple of 4
+                const float4 q = __ldg(reinterpret_cast<const float4*>(src));
+                a[u][c][c2][0] = q.x;
+                a[u][c][c2][1] = q.y;
+                a[u][c][c2][2] = q.z;
+                a[u][c][c2][3] = q.w;
+                continue;
+              }
+            }
+#pragma unroll
+            for (int j = 0; j < NV; ++j) a[u][c][c2][j] = __ldg(src + j);
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < kAsmBatch; ++u) {
+        if (t0 + u >= t1) break;
+#pragma unroll
+        for (int c = 0; c < B; ++c)
+#pragma unroll
+          for (int j = 0; j < NV; ++j)
+#pragma unroll
+            for (int c2 = 0; c2 < B; ++c2) dst[pos[u][j] * BB + c * B + c2] += a[u][c][c2][j];
+      }
     }
     if (fast) {
       float* out = val + int64_t(rp) * BB;
@@ -244,8 +285,9 @@ cudaError_t launch_assemble_t(const AsmLayout& L, const float* A, int64_t n_vert
   auto kern = assemble_kernel<NV, B>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
+  const int vec_A = reinterpret_cast<uintptr_t>(A) % 16 == 0;
   kern<<<grid_of(n_vert, kAsmThreads), kAsmThreads, smem, st>>>(L.inc_off, L.inc, L.colpos, L.row_ptr, A, n_vert,
-                                                                 val);
+                                                                 val, vec_A);
   return cudaGetLastError();
 }
 
