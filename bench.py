@@ -436,7 +436,7 @@ def run_batch(args):
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
         mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
-                      fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent"}
+                      fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item"}
         per_mode = {}
         for mode in mode_names:  # each mode at full occupancy, chunk 1, in a CUDA graph
             bt.set_config(32, 1, mode)
@@ -461,7 +461,7 @@ def run_batch(args):
         err = bt.errors(stream=stream)
     peak, peak_kind = hbm_peak()
     kinds = {(it["src"].mesh.dim, it["form"]) for it in items if it["src"].mesh.n_elem > 0}
-    launches = 1 if cfg[2] == fem.BATCH_SINGLE else len(kinds)
+    launches = {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 3 * len(items)}.get(cfg[2], len(kinds))
     byts = batch_bytes(items)
     ach = byts / (batch_ms * 1e-3) / 1e9
     out = {
@@ -473,8 +473,9 @@ def run_batch(args):
                                "adjoint (deterministic), tuned persistent launch(es) in a CUDA graph",
                    "elements": E, "meshes": len(items),
                    "l2": "no flush: ~%.1f GB moved per step" % (byts / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "fem_batch_kernel" if cfg[2] == fem.BATCH_SINGLE
-                     else "fem_batch_kind_kernel (all kinds)", "achieved": ach, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": {fem.BATCH_SINGLE: "fem_batch_kernel",
+                                                fem.BATCH_PER_ITEM: "per-mesh kernels"}.get(
+                         cfg[2], "fem_batch_kind_kernel (all kinds)"), "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},
         "comparison_ms": {"per_mesh_eager": eager_ms, "per_mesh_graph": graph_ms, "batched_graph": batch_ms,
@@ -754,6 +755,87 @@ def run_assemble(args):
     print(json.dumps(out), flush=True)
 
 
+def run_multiphysics(args):
+    """Diagonal blocks of a coupled system on the 128^3 sliver cube: P1
+    elasticity (displacement), P1 Laplacian and P2 Laplacian (two scalar
+    fields), forward + adjoint, as three items of one tuned batched launch in a
+    CUDA graph, against the same blocks launched per form."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh = mg.workload_tet_slivers(args.mesh_n, 2)
+    E, V = mesh.n_elem, mesh.n_vert
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    coef = torch.from_numpy(mg.lognormal_coef(mg.rng_for(3), E)).to(dev)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    items, wss = [], []
+    for form in (fem.ELASTIC_P1, fem.LAPLACE_P1, fem.LAPLACE_P2):
+        n = mg.form_n(form, 3)
+        items.append({"coords": coords, "conn": conn, "form": form, "coef": coef,
+                      "A": torch.empty((E, n, n), device=dev),
+                      "dA": torch.randn((E, n, n), device=dev, generator=gen),
+                      "dcoords": torch.empty((V, 3), device=dev), "dcoef": torch.empty(E, device=dev)})
+        wss.append(fem.Workspace(coords, conn, form))
+    stream = torch.cuda.Stream(dev)
+
+    def per_form():
+        for it, ws in zip(items, wss):
+            fem.integrate_fwd(coords, conn, it["form"], coef, out=it["A"], stream=stream)
+            fem.integrate_bwd(coords, conn, it["form"], it["dA"], coef, ws=ws, dcoords=it["dcoords"],
+                              dcoef=it["dcoef"], stream=stream)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1) / args.steps
+
+    with torch.cuda.stream(stream):
+        eager_ms = timed(per_form)
+        bt = fem.Batch(items, stream=stream)
+        cfg = bt.tune(stream=stream)
+        bt.run(stream=stream)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            bt.run(stream=stream)
+        batch_ms = timed(g.replay)
+        err = bt.errors(stream=stream)
+    R = wss[0].n_records()  # the records depend on the connectivity only
+    byts = 0
+    for it in items:
+        b = algorithmic_bytes(E, V, R, int(it["A"].shape[1]), 3, True)
+        byts += b["fwd"] + b["bwd_elem"] + b["reduce"]
+    peak, peak_kind = hbm_peak()
+    gbs = byts / (batch_ms * 1e-3) / 1e9
+    out = {"metric": METRIC, "value": 3 * E / (batch_ms * 1e-3), "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": batch_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"three diagonal blocks (P1 elasticity, P1 and P2 Laplacian) of a coupled system "
+                                  f"on the {args.mesh_n}^3 sliver cube ({E:,} tets), lognormal coefficient, forward + "
+                                  "adjoint, one tuned batched launch in a CUDA graph",
+                      "elements": E, "blocks": 3, "l2": "no flush"},
+           "roofline": {"bound": "hbm", "kernel": "fem_batch_kind_kernel", "achieved": gbs, "peak": peak,
+                        "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                        "traffic": None, "algorithmic_bytes": byts},
+           "comparison_ms": {"per_form_eager": eager_ms, "batched_graph": batch_ms},
+           "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": cfg[2]},
+           "device_errors": err,
+           "gpu_launches": args.steps * {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 9}.get(cfg[2], 3)}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint64(args):
     """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
     lognormal coefficient (dcoords and dcoef), both reductions."""
@@ -860,12 +942,12 @@ def main():
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
     ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64",
-                                           "assemble128"],
+                                           "assemble128", "multiphysics128"],
                     default="tet128",
                     help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
                          "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
                          "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh; "
-                         "assemble128: global CSR assembly")
+                         "assemble128: global CSR assembly; multiphysics128: three blocks on one mesh")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -884,6 +966,8 @@ def main():
         run_tri64_fp64(args)
     elif args.workload == "assemble128":
         run_assemble(args)
+    elif args.workload == "multiphysics128":
+        run_multiphysics(args)
     else:
         run_ours(args)
 

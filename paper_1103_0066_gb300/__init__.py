@@ -22,9 +22,10 @@ from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
                       F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2, LAPLACE_P1_W1, LAPLACE_P2_W1,
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
-                      BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT)
+                      BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM)
 
-__all__ = ["Mesh", "Batch", "Assembly", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+__all__ = ["Mesh", "Batch", "Assembly", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
+           "BATCH_PER_ITEM", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
            "LAPLACE_P2_W1", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
@@ -284,7 +285,7 @@ class Batch:
 
     def config(self):
         """(CTAs per SM, work-chunk size, mode) used by run(); mode is one of
-        BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT."""
+        BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM."""
         return nat.fem_batch_config(self.handle)
 
     def set_config(self, ctas_per_sm, chunk, mode):

@@ -29,7 +29,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_errors", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble")
 PHASE_FWD, PHASE_BWD = 1, 2
-BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT = 0, 1, 2
+BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM = 0, 1, 2, 3
 DEVERR_TIMEOUT = 4
 NOALLOC_SCRATCH_BYTES = 32 << 20
 

@@ -13,6 +13,9 @@
 // reports FEM_DEVERR_TIMEOUT when it gives up.  The per-tile code is the
 // per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, warp_records).
 //
+// Per-item mode (FEM_BATCH_PER_ITEM): every item through the single-mesh
+// kernels, on the records this batch built.
+//
 // Grouped modes (FEM_BATCH_GROUPED, FEM_BATCH_GROUPED_CONCURRENT): the same
 // item scheme per (dim, form) kind, one kind-specialised pipelined kernel per
 // kind present, launched in order on one stream or forked onto side streams.
@@ -497,6 +500,8 @@ struct fem_batch {
     int occ;
   };
   std::vector<Group> groups;  // non-empty kinds, largest work first
+  std::vector<fem_batch_item> items;        // the caller's items (per-item mode)
+  std::vector<fem::BwdWorkspace> item_ws;  // their record workspaces (valid when the item has records)
   cudaStream_t aux[6] = {};
   cudaEvent_t fork = nullptr, join[6] = {};
   ~fem_batch() {
@@ -576,9 +581,67 @@ cudaError_t launch_group(fem_batch* b, const fem_batch::Group& g, int phases, in
   return fem::kind_launch(g.kind, L, st);
 }
 
+cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; k < b->items.size() && e == cudaSuccess; ++k) {
+    const fem_batch_item& it = b->items[k];
+    const fem::BatchMesh& M = b->desc[k];
+    if (M.n_elem == 0) {
+      if ((phases & FEM_PHASE_BWD) && (M.flags & fem::BM_REC) && M.n_vert > 0)
+        e = fem::launch_zero_f32(it.dcoords, M.n_vert * it.mesh.dim, st);  // no element: dcoords = 0
+      continue;
+    }
+    if ((phases & FEM_PHASE_FWD) && (M.flags & fem::BM_FWD)) {
+      fem::FwdLaunch L{};
+      L.dim = it.mesh.dim;
+      L.form = it.form;
+      L.jac = fem::JAC_COMP;
+      L.conn = it.mesh.conn;
+      L.coords = it.mesh.coords;
+      L.coef = it.coef;
+      L.A = it.A;
+      L.n_elem = M.n_elem;
+      L.n_vert = M.n_vert;
+      L.dev_err = &b->d_ctr->err;
+      L.warps = 4;
+      L.stream = st;
+      e = L.dim == 2 ? fem::launch_fwd_d2(L)
+                     : (it.form == FEM_ELASTIC_P1 ? fem::launch_fwd_d3_ela(L) : fem::launch_fwd_d3_lap(L));
+    }
+    if (e == cudaSuccess && (phases & FEM_PHASE_BWD) && (M.flags & fem::BM_BWD)) {
+      const bool rec = (M.flags & fem::BM_REC) != 0;
+      const fem::BwdWorkspace& W = b->item_ws[k];
+      fem::BwdLaunch L{};
+      L.dim = it.mesh.dim;
+      L.form = it.form;
+      L.jac = fem::JAC_COMP;
+      L.atomic = 0;
+      L.conn = it.mesh.conn;
+      L.coords = static_cast<const float*>(it.mesh.coords);
+      L.coef = it.coef;
+      L.dA = it.dA;
+      L.dcoef = it.dcoef;
+      L.tile_rec = rec ? W.tile_rec : nullptr;
+      L.rank = rec ? W.rank : nullptr;
+      L.rec_end = rec ? W.rec_end : nullptr;
+      L.rec_dest = rec ? W.rec_dest : nullptr;
+      L.records = rec ? W.records : nullptr;
+      L.dcoords = it.dcoords;
+      L.n_elem = M.n_elem;
+      L.n_vert = M.n_vert;
+      L.dev_err = &b->d_ctr->err;
+      L.stream = st;
+      e = fem::launch_bwd_elem(L);
+      if (e == cudaSuccess && rec) e = fem::launch_vertex_reduce(it.mesh.dim, W, M.n_vert, it.dcoords, st);
+    }
+  }
+  return e;
+}
+
 cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, int mode, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
   if (e != cudaSuccess) return e;
+  if (mode == FEM_BATCH_PER_ITEM) return launch_per_item(b, phases, st);
   if (mode == FEM_BATCH_SINGLE) {
     const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
     fem::fem_batch_kernel<<<unsigned(grid_for(ctas_per_sm, total, chunk)), fem::kTileElems, b->smem, st>>>(
@@ -605,7 +668,7 @@ cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, i
 }
 
 bool valid_config(int ctas_per_sm, int chunk, int mode) {
-  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_GROUPED_CONCURRENT && chunk >= 1 && chunk <= 64 &&
+  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_PER_ITEM && chunk >= 1 && chunk <= 64 &&
          ctas_per_sm >= 1 && ctas_per_sm <= 32;
 }
 
@@ -649,6 +712,8 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   }
   b->n_items = n_items;
   b->desc.resize(size_t(n_items));
+  b->items.assign(items, items + n_items);
+  b->item_ws.assign(size_t(n_items), fem::BwdWorkspace{});
   size_t kdesc_off = 0, ctr_off = 0;
   size_t off = head_bytes(n_items, &kdesc_off, &ctr_off, &b->ctr_bytes);
   char* base = static_cast<char*>(ws);
@@ -687,6 +752,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
         fem::set_last_error("batch item %d: incidence build: %s", i, cudaGetErrorString(e));
         return FEM_ERR_CUDA;
       }
+      b->item_ws[size_t(i)] = W;
       M.tile_rec = W.tile_rec;
       M.rank = W.rank;
       M.rec_end = W.rec_end;
@@ -793,10 +859,13 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
   int best_c = b->ctas_per_sm, best_k = b->chunk, best_m = b->mode;
   const int chunks[] = {1, 2, 4, 8};
   cudaError_t err = cudaSuccess;
-  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_GROUPED_CONCURRENT && err == cudaSuccess; ++mode) {
-    if (mode != FEM_BATCH_SINGLE && b->groups.empty()) break;
-    for (int c = 1; c <= b->max_ctas_per_sm && err == cudaSuccess; ++c)
+  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_PER_ITEM && err == cudaSuccess; ++mode) {
+    const bool grouped = mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT;
+    if (grouped && b->groups.empty()) continue;
+    const int c_hi = mode == FEM_BATCH_PER_ITEM ? 1 : b->max_ctas_per_sm;  // per item: no grid or chunk to tune
+    for (int c = 1; c <= c_hi && err == cudaSuccess; ++c)
       for (int k : chunks) {
+        if (mode == FEM_BATCH_PER_ITEM && k != 1) continue;
         err = launch_batch(b, phases, c, k, mode, st);  // warm-up
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {
@@ -846,7 +915,8 @@ fem_status fem_batch_set_config(fem_batch* b, int32_t ctas_per_sm, int32_t chunk
                         "mode FEM_BATCH_*)");
     return FEM_ERR_ARG;
   }
-  if (mode != FEM_BATCH_SINGLE && b->groups.empty()) mode = FEM_BATCH_SINGLE;
+  if ((mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT) && b->groups.empty())
+    mode = FEM_BATCH_SINGLE;
   b->ctas_per_sm = ctas_per_sm;
   b->chunk = chunk;
   b->mode = mode;

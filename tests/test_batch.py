@@ -42,12 +42,12 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-MODES = ["single", "grouped", "concurrent"]
+MODES = ["single", "grouped", "concurrent", "per_item"]
 
 
 def _mode(gfem, name):
     return {"single": gfem.BATCH_SINGLE, "grouped": gfem.BATCH_GROUPED,
-            "concurrent": gfem.BATCH_GROUPED_CONCURRENT}[name]
+            "concurrent": gfem.BATCH_GROUPED_CONCURRENT, "per_item": gfem.BATCH_PER_ITEM}[name]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -100,7 +100,7 @@ def test_batch_graph_capture_and_tuning(gfem, mode):
     ref = [(it["A"].clone(), it["dcoords"].clone()) for it in items]
     cfg = batch.tune()
     assert cfg[0] >= 1 and cfg[1] >= 1 and cfg[2] in (gfem.BATCH_SINGLE, gfem.BATCH_GROUPED,
-                                                       gfem.BATCH_GROUPED_CONCURRENT)
+                                                       gfem.BATCH_GROUPED_CONCURRENT, gfem.BATCH_PER_ITEM)
     if mode == "concurrent":  # fork/join side streams inside the capture
         batch.set_config(cfg[0], cfg[1], gfem.BATCH_GROUPED_CONCURRENT)
     g = torch.cuda.CUDAGraph()
@@ -153,3 +153,30 @@ def test_batch_empty_meshes_and_single_kind(gfem):
         assert batch.errors() == 0
         assert torch.equal(it["A"], A_ref) and torch.equal(it["dcoords"], dx_ref)
         assert (items[0]["dcoords"] == 0).all() and (items[2]["dcoords"] == 0).all()  # no tiles: sum of nothing
+
+
+def test_multiphysics_blocks_share_one_mesh(gfem):
+    """Diagonal blocks of a coupled system on one mesh (P1 elasticity for the
+    displacement, P1 and P2 Laplacians for two scalar fields) in one batched
+    launch: the items share the coordinate and connectivity tensors, and each
+    block equals its per-form call bit for bit."""
+    mesh = mg.cube_tet_mesh(6, 0.15, mg.rng_for(81), 0.05, np.float32)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    coef = _t(mg.lognormal_coef(mg.rng_for(82), mesh.n_elem))
+    items = []
+    for form in (2, 0, 1):
+        n = mg.form_n(form, 3)
+        items.append({"coords": coords, "conn": conn, "form": form, "coef": coef,
+                      "A": torch.full((mesh.n_elem, n, n), float("nan"), device=DEV),
+                      "dA": _t(mg.upstream(mg.rng_for(83 + form), mesh.n_elem, n)),
+                      "dcoords": torch.empty((mesh.n_vert, 3), device=DEV),
+                      "dcoef": torch.empty(mesh.n_elem, device=DEV)})
+    batch = gfem.Batch(items)
+    batch.tune()
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.errors() == 0
+    for it in items:
+        A_ref = gfem.integrate_fwd(coords, conn, it["form"], coef)
+        dx_ref, dw_ref = gfem.integrate_bwd(coords, conn, it["form"], it["dA"], coef)
+        assert torch.equal(it["A"], A_ref) and torch.equal(it["dcoords"], dx_ref) and torch.equal(it["dcoef"], dw_ref)
