@@ -69,9 +69,12 @@ def _load():
         lib.orc_integrate_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
         lib.orc_element_matrix_w1.argtypes = [I, I, P, P, I, P, P]
         lib.orc_integrate_w1.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
+        lib.orc_element_matrix_iso.argtypes = [I, I, P, P, D, I, P, P]
+        lib.orc_integrate_iso.argtypes = [I, I, I64, I64, P, P, P, P, I, P, P, I]
         for name in ("orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
                      "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
-                     "orc_integrate_vjp", "orc_element_matrix_w1", "orc_integrate_w1"):
+                     "orc_integrate_vjp", "orc_element_matrix_w1", "orc_integrate_w1",
+                     "orc_element_matrix_iso", "orc_integrate_iso"):
             getattr(lib, name).restype = I
         _lib = lib
         return lib
@@ -163,6 +166,43 @@ def integrate_w1(dim: int, form: int, conn, coords, wvert, q: int = 3, nthreads:
     nt = max_threads() if nthreads is None else nthreads
     rc = _load().orc_integrate_w1(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(wvert), q, _ptr(A),
                                   _ptr(flags), nt)
+    if rc < 0:
+        raise ValueError("bad integrate request")
+    return A, flags
+
+
+def element_matrix_iso(dim: int, form: int, X, mid, coef: float = 1.0, q: int = 4):
+    """Element matrix of a Laplacian form on a non-affine element (Eqs. 16-19):
+    X [dim+1][dim] vertices, mid [n_edges][dim] edge-midpoint nodes (P2 edge
+    order).  Returns (A, det J at the centroid, flags)."""
+    X = _f64(X)
+    mid = _f64(mid)
+    n = form_n(form, dim)
+    A = np.zeros((n, n))
+    det = np.zeros(1)
+    rc = _load().orc_element_matrix_iso(dim, form, _ptr(X), _ptr(mid), float(coef), q, _ptr(A), _ptr(det))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return A, float(det[0]), rc
+
+
+def integrate_iso(dim: int, form: int, conn, coords, mid, coef=None, q: int = 4, nthreads: int | None = None):
+    """Element matrices [E][n][n] (FP64) and flags of a Laplacian form on
+    non-affine elements whose edge-midpoint nodes are mid [E][n_edges][dim]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    mid = _f64(mid)
+    E, V = conn.shape[0], coords.shape[0]
+    ne = 3 if dim == 2 else 6
+    if mid.shape != (E, ne, dim):
+        raise ValueError("mid must be [E][n_edges][dim]")
+    n = form_n(form, dim)
+    cf = None if coef is None else _f64(coef)
+    A = np.zeros((E, n, n))
+    flags = np.zeros(E, dtype=np.int32)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_iso(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(mid), _ptr(cf), q, _ptr(A),
+                                   _ptr(flags), nt)
     if rc < 0:
         raise ValueError("bad integrate request")
     return A, flags

@@ -18,6 +18,12 @@
  *       - or, for the P1 coefficient of Eqs. 20-23, c(xi) = sum_k w_k lambda_k(xi)
  *         evaluated at every quadrature point from the element's vertex
  *         values w_k (orc_integrate_w1); the Laplacian forms only.
+ *   * Non-affine (isoparametric) elements, Eqs. 16-19 (orc_integrate_iso): the
+ *     element has quadratic geometry (its vertices and edge-midpoint nodes);
+ *     J^{-1} is projected onto P1 by its values at the vertices, J^{-1}(xi) =
+ *     sum_k lambda_k(xi) J^{-1}(vertex k), and |J| is taken out of the
+ *     integral as |det J| at the element centroid (Eq. 17), so
+ *       A_ij = |J_c| c_e int_ref sum_a (J^{-1}(xi)^T grad_ref phi_i)_a (J^{-1}(xi)^T grad_ref phi_j)_a.
  *   * Physical gradients grad(phi) = J^{-T} grad_ref(phi) (the chain rule of
  *     Eq. 5, d xi_mu / d x_alpha = (J^{-1})_{mu alpha} as in Eq. 8) obtained
  *     by an LU solve with partial pivoting in FP64.
@@ -364,6 +370,102 @@ int orc_element_matrix_w1(int dim, int form, const double* X, const double* wv, 
   return element_matrix(dim, form, X, 1.0, wv, q, A, detJ_out);
 }
 
+/* Jacobian J[alpha][mu] = d x_alpha / d xi_mu of the quadratic geometry map
+ * x(xi) = sum_a node_a psi_a(xi) at the reference point xi (nodes: vertices,
+ * then edge midpoints in the P2 order). */
+static void iso_jacobian(int dim, const double* nodes, const double* xi, double J[3][3]) {
+  double psi[ORC_MAXB], gpsi[ORC_MAXB * 3];
+  int nn = orc_basis(dim, 2, xi, psi, gpsi);
+  memset(J, 0, sizeof(double) * 9);
+  for (int a = 0; a < nn; ++a)
+    for (int al = 0; al < dim; ++al)
+      for (int mu = 0; mu < dim; ++mu) J[al][mu] += nodes[a * dim + al] * gpsi[a * dim + mu];
+}
+
+static double det3(int dim, double J[3][3]) {
+  if (dim == 2) return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  return J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+         J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+}
+
+/* Element matrix of a Laplacian form on a non-affine element (Eqs. 16-19):
+ * X[(dim+1)*dim] vertices, Mid[n_edges*dim] edge-midpoint nodes (P2 edge
+ * order), per-element coefficient coef.  Returns 0, or ORC_FLAG_DEGENERATE (A
+ * zeroed) when J is singular at a vertex or at the centroid. */
+int orc_element_matrix_iso(int dim, int form, const double* X, const double* Mid, double coef, int q, double* A,
+                           double* detc_out) {
+  if (form == ORC_ELASTIC_P1) return -1;
+  int n = orc_form_n(form, dim);
+  if (n < 0) return -1;
+  int deg = form_degree(form), nb = orc_n_basis(dim, deg), nv = dim + 1;
+  int ne = dim == 2 ? 3 : 6;
+  memset(A, 0, sizeof(double) * n * n);
+  double nodes[ORC_MAXB * 3];
+  for (int k = 0; k < nv * dim; ++k) nodes[k] = X[k];
+  for (int k = 0; k < ne * dim; ++k) nodes[nv * dim + k] = Mid[k];
+  /* J^{-1} at the vertices: Jinv_k[mu][alpha] = (J(vertex k)^{-1})[mu][alpha] */
+  double Jinv[4][3][3];
+  for (int k = 0; k < nv; ++k) {
+    double xi[3] = {0, 0, 0};
+    if (k > 0) xi[k - 1] = 1.0;
+    double J[3][3];
+    iso_jacobian(dim, nodes, xi, J);
+    lu3 f;
+    lu_factor(dim, J, &f);
+    if (f.det == 0.0) {
+      if (detc_out) *detc_out = 0.0;
+      return ORC_FLAG_DEGENERATE;
+    }
+    for (int al = 0; al < dim; ++al) {
+      double b[3] = {0, 0, 0};
+      b[al] = 1.0;
+      lu_solve(&f, b); /* J b = e_alpha: b is column alpha of J^{-1}, b[mu] = (J^{-1})[mu][alpha] */
+      for (int mu = 0; mu < dim; ++mu) Jinv[k][mu][al] = b[mu];
+    }
+  }
+  double xc[3] = {0, 0, 0};
+  for (int mu = 0; mu < dim; ++mu) xc[mu] = 1.0 / nv;
+  double Jc[3][3];
+  iso_jacobian(dim, nodes, xc, Jc);
+  double detc = det3(dim, Jc);
+  if (detc_out) *detc_out = detc;
+  if (detc == 0.0) return ORC_FLAG_DEGENERATE;
+  double absdet = fabs(detc);
+  double pts[ORC_MAXPTS * 3], wts[ORC_MAXPTS];
+  int np = orc_simplex_rule(dim, q, pts, wts);
+  if (np < 0) return -1;
+  for (int p = 0; p < np; ++p) {
+    const double* xi = pts + p * dim;
+    double lam[4];
+    lam[0] = 1.0;
+    for (int k = 1; k <= dim; ++k) {
+      lam[k] = xi[k - 1];
+      lam[0] -= xi[k - 1];
+    }
+    double Ji[3][3] = {{0}};
+    for (int k = 0; k < nv; ++k)
+      for (int mu = 0; mu < dim; ++mu)
+        for (int al = 0; al < dim; ++al) Ji[mu][al] += lam[k] * Jinv[k][mu][al];
+    double phi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3];
+    orc_basis(dim, deg, xi, phi, gref);
+    for (int i = 0; i < nb; ++i)
+      for (int al = 0; al < 3; ++al) {
+        double s = 0.0;
+        if (al < dim)
+          for (int mu = 0; mu < dim; ++mu) s += Ji[mu][al] * gref[i * dim + mu];
+        g[i][al] = s;
+      }
+    double scale = wts[p] * absdet * coef;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < dim; ++a) s += g[i][a] * g[j][a];
+        A[i * n + j] += scale * s;
+      }
+  }
+  return 0;
+}
+
 /* Reverse mode of orc_element_matrix: given Abar = dL/dA, returns
  * Xbar[(dim+1)*dim] = dL/dX and *cbar = dL/dcoef.  Derivation, per quadrature
  * point with s = |det J|, c = coef:
@@ -528,6 +630,32 @@ int orc_integrate_w1(int dim, int form, int64_t n_elem, int64_t n_vert, const in
     if (f == 0) {
       for (int k = 0; k <= dim; ++k) wv[k] = wvert[ce[k]];
       f = element_matrix(dim, form, X, 1.0, wv, q, Ae, NULL);
+    } else {
+      memset(Ae, 0, sizeof(double) * n * n);
+    }
+    if (flags) flags[e] = f;
+    any |= f;
+  }
+  return any;
+}
+
+/* A[e] for every element of a Laplacian form on non-affine elements: mid
+ * [E][n_edges][dim] holds each element's edge-midpoint nodes.  Flags as in
+ * orc_integrate. */
+int orc_integrate_iso(int dim, int form, int64_t n_elem, int64_t n_vert, const int32_t* conn, const double* coords,
+                      const double* mid, const double* coef, int q, double* A, int32_t* flags, int nthreads) {
+  int n = orc_form_n(form, dim);
+  if (n < 0 || form == ORC_ELASTIC_P1) return -1;
+  int ne = dim == 2 ? 3 : 6;
+  int any = 0;
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12];
+    double* Ae = A + e * (int64_t)n * n;
+    int f = gather(dim, n_vert, conn + e * (dim + 1), coords, X);
+    if (f == 0) {
+      f = orc_element_matrix_iso(dim, form, X, mid + e * (int64_t)ne * dim, coef ? coef[e] : 1.0, q, Ae, NULL);
     } else {
       memset(Ae, 0, sizeof(double) * n * n);
     }

@@ -207,6 +207,47 @@ def workload_tet_slivers(n: int = 128, k: int = 2) -> Mesh:
     return cube_tet_mesh(n, 0.15, rng_for(k), 0.05, np.float32)
 
 
+def _warp(x: np.ndarray, eps: float) -> np.ndarray:
+    """A smooth map of the unit square / cube onto itself plus a bulge:
+    x + eps * (product of sines of the other coordinates), per component."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.sin(np.pi * x)
+    out = x.copy()
+    if x.shape[-1] == 2:
+        out[..., 0] += eps * s[..., 1]
+        out[..., 1] += eps * s[..., 0]
+    else:
+        out[..., 0] += eps * s[..., 1] * s[..., 2]
+        out[..., 1] += eps * s[..., 2] * s[..., 0]
+        out[..., 2] += eps * s[..., 0] * s[..., 1]
+    return out
+
+
+def edge_pairs(dim: int):
+    """Local vertex pairs of the element's edges, in the P2 (lexicographic) order."""
+    return [(a, b) for a in range(dim + 1) for b in range(a + 1, dim + 1)]
+
+
+def curved_mesh(mesh: Mesh, eps: float = 0.05, dtype=np.float32) -> tuple[Mesh, np.ndarray]:
+    """Quadratic (non-affine) elements from a straight-sided mesh: the vertices
+    and the midpoints of every element's straight edges are mapped by a smooth
+    warp, so each element's edges become curves through the warped midpoints.
+    Returns the mesh with warped vertices and mid [E][n_edges][dim] (the
+    edge-midpoint nodes, element by element; shared edges get equal nodes)."""
+    X = np.asarray(mesh.coords, dtype=np.float64)
+    P = X[mesh.conn]                                            # [E][dim+1][dim]
+    pairs = edge_pairs(mesh.dim)
+    M = np.stack([0.5 * (P[:, a] + P[:, b]) for a, b in pairs], axis=1)
+    curved = Mesh(mesh.dim, _warp(X, eps).astype(dtype), mesh.conn, mesh.sliver)
+    return curved, _warp(M, eps).astype(dtype)
+
+
+def workload_curved_tets(n: int = 64, k: int = 6, eps: float = 0.05):
+    """n^3 Kuhn cube, jitter 0.15 h, no slivers, warped into quadratic elements."""
+    base = cube_tet_mesh(n, 0.15, rng_for(k), 0.0, np.float32)
+    return curved_mesh(base, eps)
+
+
 @dataclass
 class BatchItem:
     form: int
