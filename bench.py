@@ -836,6 +836,65 @@ def run_multiphysics(args):
     print(json.dumps(out), flush=True)
 
 
+def run_iso(args):
+    """The Laplacian on non-affine (quadratic-geometry) elements, Eqs. 16-19:
+    the 128^3 jittered cube warped into curved tets, P1 and P2, forward."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    import paper_1103_0066_gb300 as fem
+    from paper_1103_0066_gb300 import meshgen as mg
+
+    dev = torch.device("cuda:0")
+    mesh, mid_h = mg.workload_curved_tets(args.mesh_n)
+    E, V = mesh.n_elem, mesh.n_vert
+    coords, conn = torch.from_numpy(mesh.coords).to(dev), torch.from_numpy(mesh.conn).to(dev)
+    mid = torch.from_numpy(mid_h).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = hbm_peak()
+    res = {}
+    for name, form, n in (("p1", fem.LAPLACE_P1_ISO, 4), ("p2", fem.LAPLACE_P2_ISO, 10)):
+        A = torch.empty((E, n, n), device=dev)
+
+        def step():
+            fem.integrate_fwd_iso(coords, conn, mid, form, out=A)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1) / args.steps
+        rng = np.random.default_rng(11)
+        idx = np.unique(np.concatenate([rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
+        Ar, _ = oracle.integrate_iso(3, form - 5, mesh.conn[idx], mesh.coords, mid_h[idx])
+        Ag = A[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
+        num = np.abs(Ag - Ar).reshape(len(idx), -1).max(1)
+        byts = E * (16 + 72 + 4 * n * n) + V * 12
+        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
+                     "frac_of_peak": byts / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": byts,
+                     "max_rel_err_vs_fp64": float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())}
+        del A
+    r = res["p1"]
+    out = {"metric": METRIC, "value": r["elements_per_s"], "unit": "elements/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": r["ms"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"Laplacian on quadratic-geometry tets (Eqs. 16-19): {args.mesh_n}^3 jittered "
+                                  f"cube warped by a smooth map ({E:,} tets), P1 and P2, FP32, forward",
+                      "elements": E, "l2": "no flush"},
+           "roofline": {"bound": "hbm", "kernel": "fem_fwd_iso_kernel<3,LAPLACE_P1_ISO>", "achieved": r["GB/s"],
+                        "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],
+                        "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
+                        "algorithmic_bytes": r["algorithmic_bytes"]},
+           "paths": res, "gpu_launches": 2 * args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint64(args):
     """Forward + adjoint of the P1 Laplacian on the 64^3 sliver cube with a
     lognormal coefficient (dcoords and dcoef), both reductions."""
@@ -942,12 +1001,13 @@ def main():
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
     ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64",
-                                           "assemble128", "multiphysics128"],
+                                           "assemble128", "multiphysics128", "iso128"],
                     default="tet128",
                     help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
                          "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
                          "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh; "
-                         "assemble128: global CSR assembly; multiphysics128: three blocks on one mesh")
+                         "assemble128: global CSR assembly; multiphysics128: three blocks on one mesh; "
+                         "iso128: non-affine elements")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
@@ -968,6 +1028,8 @@ def main():
         run_assemble(args)
     elif args.workload == "multiphysics128":
         run_multiphysics(args)
+    elif args.workload == "iso128":
+        run_iso(args)
     else:
         run_ours(args)
 

@@ -62,7 +62,9 @@ typedef enum {
   FEM_LAPLACE_P2 = 1,    /* same form, P2 Lagrange elements */
   FEM_ELASTIC_P1 = 2,    /* eps(v):eps(u), Eq. 10 scaled by the 1/4 of Eqs. 14 and 24, P1 vector elements */
   FEM_LAPLACE_P1_W1 = 3, /* int w grad v . grad u with w in P1 (Eqs. 20-23), P1 elements */
-  FEM_LAPLACE_P2_W1 = 4  /* the same with P2 elements: K gains the coefficient's index (Eq. 21) */
+  FEM_LAPLACE_P2_W1 = 4, /* the same with P2 elements: K gains the coefficient's index (Eq. 21) */
+  FEM_LAPLACE_P1_ISO = 5, /* the Laplacian on non-affine (quadratic-geometry) elements, Eqs. 16-19, P1 */
+  FEM_LAPLACE_P2_ISO = 6  /* the same with P2 elements (fem_integrate_fwd_iso only) */
 } fem_form;
 
 typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
@@ -144,6 +146,21 @@ FEM_API fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K_ho
  * Asynchronous on `stream`.  n_elem == 0 is a no-op. */
 FEM_API fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
                              int32_t out_dtype, const fem_options* options, void* stream);
+
+/* Forward integration on non-affine elements (Eqs. 16-19), forms
+ * FEM_LAPLACE_P1_ISO / FEM_LAPLACE_P2_ISO, FP32 coordinates and output.  Each
+ * element has quadratic geometry: its d+1 vertices and its edge-midpoint nodes
+ *   mid : device FP32 [n_elem][d(d+1)/2][dim], edges in the P2 order
+ *         (0,1),(0,2),(1,2) / (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)
+ * J^{-1} is projected onto P1 by its values at the vertices (Eq. 17) and |J|
+ * is |det J| at the centroid, so G^{(k mu),(l nu)} = w |J| J^{-1}_{mu a,k}
+ * J^{-1}_{nu a,l} is contracted with K^{ij}_{(k mu),(l nu)} = int_ref lambda_k
+ * lambda_l d_mu phi_i d_nu phi_j (Eqs. 18-19).  The Jacobian steps run in
+ * plain FP32 (options->jac FEM_JAC_AUTO or FEM_JAC_F32).  coef: [n_elem] or
+ * NULL; A: [n_elem][n][n] FP32.  Straight-sided elements (mid at the edge
+ * midpoints) give the affine result. */
+FEM_API fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef,
+                                         float* A, const fem_options* options, void* stream);
 
 /* Test hook for the Jacobian steps (Eqs. 5, 8): per element det J (detJ,
  * device FP64 [n_elem]; the compensated mode returns its double-float value)

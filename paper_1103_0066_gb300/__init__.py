@@ -21,13 +21,14 @@ import torch
 from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
                       F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2, LAPLACE_P1_W1, LAPLACE_P2_W1,
+                      LAPLACE_P1_ISO, LAPLACE_P2_ISO,
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM)
 
 __all__ = ["Mesh", "Batch", "Assembly", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
            "BATCH_PER_ITEM", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
-           "LAPLACE_P2_W1", "JAC_AUTO",
+           "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "integrate_fwd_iso", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
            "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
 
@@ -89,6 +90,24 @@ def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float
                               dev_err.data_ptr() if dev_err is not None else 0)
     cp = _coef_ptr(coef, coords.shape[0], "[V]") if w1 else _coef_ptr(coef, E)
     nat.fem_integrate_fwd(m, form, cp, out.data_ptr(), od, opts, _stream_ptr(stream))
+    return out
+
+
+def integrate_fwd_iso(coords, conn, mid, form=LAPLACE_P1_ISO, coef=None, out=None, dev_err=None, stream=None):
+    """fem_integrate_fwd_iso: element matrices [E][n][n] of the Laplacian on
+    non-affine elements with edge-midpoint nodes mid [E][d(d+1)/2][d] (FP32)."""
+    m = _mesh_struct(coords, conn)
+    n, _, _ = form_info(form, m.dim)
+    E = conn.shape[0]
+    ne = m.dim * (m.dim + 1) // 2
+    if mid.dtype != torch.float32 or not mid.is_contiguous() or tuple(mid.shape) != (E, ne, m.dim) or not mid.is_cuda:
+        raise ValueError(f"mid must be a contiguous CUDA float32 tensor [E][{ne}][{m.dim}]")
+    if out is None:
+        out = torch.empty((E, n, n), dtype=torch.float32, device=coords.device)
+    elif out.shape != (E, n, n) or not out.is_contiguous() or out.dtype != torch.float32:
+        raise ValueError("out must be a contiguous float32 [E][n][n] tensor")
+    opts = nat.options_struct(JAC_AUTO, CONTRACT_F32, 0, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
+    nat.fem_integrate_fwd_iso(m, form, mid.data_ptr(), _coef_ptr(coef, E), out.data_ptr(), opts, _stream_ptr(stream))
     return out
 
 

@@ -14,7 +14,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libfem_gb300.so")
 
 FEM_OK, FEM_ERR_ARG, FEM_ERR_UNSUPPORTED, FEM_ERR_WORKSPACE, FEM_ERR_CUDA = range(5)
-LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, LAPLACE_P1_W1, LAPLACE_P2_W1 = 0, 1, 2, 3, 4
+LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, LAPLACE_P1_W1, LAPLACE_P2_W1, LAPLACE_P1_ISO, LAPLACE_P2_ISO = range(7)
 F32, F64 = 0, 1
 JAC_AUTO, JAC_F64, JAC_COMP_F32, JAC_F32 = 0, 1, 2, 3
 CONTRACT_F32, CONTRACT_BF16X3 = 0, 1
@@ -27,7 +27,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
-           "fem_assembly_pattern", "fem_assemble")
+           "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM = 0, 1, 2, 3
 DEVERR_TIMEOUT = 4
@@ -81,6 +81,7 @@ def load():
             "fem_form_info": ([I32, I32, P, P, P], ctypes.c_int),
             "fem_reference_tensor": ([I32, I32, P, SZ], ctypes.c_int),
             "fem_integrate_fwd": ([MP, I32, P, P, I32, OP, P], ctypes.c_int),
+            "fem_integrate_fwd_iso": ([MP, I32, P, P, P, OP, P], ctypes.c_int),
             "fem_geometry": ([MP, P, OP, P, P, P], ctypes.c_int),
             "fem_bwd_workspace_size": ([MP, I32, OP, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
@@ -148,6 +149,12 @@ def fem_integrate_fwd(mesh: FemMesh, form: int, coef_ptr: int, A_ptr: int, out_d
                       opts: FemOptions, stream: int) -> None:
     check(load().fem_integrate_fwd(ctypes.byref(mesh), form, coef_ptr or None, A_ptr or None,
                                    out_dtype, ctypes.byref(opts), stream or None))
+
+
+def fem_integrate_fwd_iso(mesh: FemMesh, form: int, mid_ptr: int, coef_ptr: int, A_ptr: int, opts: FemOptions,
+                          stream: int) -> None:
+    check(load().fem_integrate_fwd_iso(ctypes.byref(mesh), form, mid_ptr or None, coef_ptr or None, A_ptr or None,
+                                       ctypes.byref(opts), stream or None))
 
 
 def fem_geometry(mesh: FemMesh, coef_ptr: int, opts: FemOptions, det_ptr: int, G_ptr: int,

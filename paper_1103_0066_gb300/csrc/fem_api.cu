@@ -58,12 +58,14 @@ fem_status check_options(const fem_options* o) {
 }
 
 int form_rows(int form, int dim) {
-  const int nb = (form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1) ? (dim + 1) * (dim + 2) / 2 : dim + 1;
+  const bool p2 = form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1 || form == FEM_LAPLACE_P2_ISO;
+  const int nb = p2 ? (dim + 1) * (dim + 2) / 2 : dim + 1;
   return nb * (form == FEM_ELASTIC_P1 ? dim : 1);
 }
 
-bool valid_form(int form) { return form >= FEM_LAPLACE_P1 && form <= FEM_LAPLACE_P2_W1; }
+bool valid_form(int form) { return form >= FEM_LAPLACE_P1 && form <= FEM_LAPLACE_P2_ISO; }
 bool coef_p1(int form) { return form == FEM_LAPLACE_P1_W1 || form == FEM_LAPLACE_P2_W1; }
+bool non_affine(int form) { return form == FEM_LAPLACE_P1_ISO || form == FEM_LAPLACE_P2_ISO; }
 
 int resolve_jac(int jac, bool coord_f64, bool out_f64) {
   if (jac == FEM_JAC_AUTO) return (coord_f64 || out_f64) ? fem::JAC_F64 : fem::JAC_COMP;
@@ -112,11 +114,13 @@ const char* fem_last_error(void) { return g_msg; }
 fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den) {
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
   if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim must be 2 or 3");
-  const int np = form == FEM_ELASTIC_P1 ? dim * dim : dim;
+  const int np = form == FEM_ELASTIC_P1 ? dim * dim : non_affine(form) ? (dim + 1) * dim : dim;
   if (n) *n = form_rows(form, dim);
   if (n_geom) *n_geom = np * (np + 1) / 2 * (coef_p1(form) ? dim + 1 : 1);
   if (den)
-    *den = coef_p1(form) ? (dim == 2 ? 120 : 720) : (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
+    *den = non_affine(form) ? (dim == 2 ? 720 : 5040)
+           : coef_p1(form)  ? (dim == 2 ? 120 : 720)
+                            : (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
   return ok();
 }
 
@@ -132,12 +136,16 @@ fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K, size_t ca
     if (form == FEM_ELASTIC_P1) copy_ref<2, fem::ELASTIC_P1>(K);
     if (form == FEM_LAPLACE_P1_W1) copy_ref<2, fem::LAPLACE_P1_W1>(K);
     if (form == FEM_LAPLACE_P2_W1) copy_ref<2, fem::LAPLACE_P2_W1>(K);
+    if (form == FEM_LAPLACE_P1_ISO) copy_ref<2, fem::LAPLACE_P1_ISO>(K);
+    if (form == FEM_LAPLACE_P2_ISO) copy_ref<2, fem::LAPLACE_P2_ISO>(K);
   } else {
     if (form == FEM_LAPLACE_P1) copy_ref<3, fem::LAPLACE_P1>(K);
     if (form == FEM_LAPLACE_P2) copy_ref<3, fem::LAPLACE_P2>(K);
     if (form == FEM_ELASTIC_P1) copy_ref<3, fem::ELASTIC_P1>(K);
     if (form == FEM_LAPLACE_P1_W1) copy_ref<3, fem::LAPLACE_P1_W1>(K);
     if (form == FEM_LAPLACE_P2_W1) copy_ref<3, fem::LAPLACE_P2_W1>(K);
+    if (form == FEM_LAPLACE_P1_ISO) copy_ref<3, fem::LAPLACE_P1_ISO>(K);
+    if (form == FEM_LAPLACE_P2_ISO) copy_ref<3, fem::LAPLACE_P2_ISO>(K);
   }
   return ok();
 }
@@ -147,6 +155,7 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
+  if (non_affine(form)) return fail(FEM_ERR_ARG, "non-affine forms take their edge nodes: fem_integrate_fwd_iso");
   if (out_dtype != FEM_F32 && out_dtype != FEM_F64) return fail(FEM_ERR_ARG, "out_dtype out of range");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
@@ -192,6 +201,37 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   return ok();
 }
 
+fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef, float* A,
+                                 const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (!non_affine(form)) return fail(FEM_ERR_ARG, "form must be FEM_LAPLACE_P1_ISO or FEM_LAPLACE_P2_ISO");
+  if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "non-affine elements take FP32 coordinates");
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F32)
+    return fail(FEM_ERR_UNSUPPORTED, "non-affine elements compute their Jacobians in FP32");
+  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "non-affine elements contract in FP32");
+  if (mesh->n_elem == 0) return ok();
+  if (!A || !mid) return fail(FEM_ERR_ARG, "A or mid is NULL");
+  fem::FwdLaunch L{};
+  L.dim = mesh->dim;
+  L.form = form;
+  L.jac = fem::JAC_F32;
+  L.conn = mesh->conn;
+  L.coords = mesh->coords;
+  L.coef = coef;
+  L.A = A;
+  L.n_elem = mesh->n_elem;
+  L.n_vert = mesh->n_vert;
+  L.dev_err = o->dev_err;
+  L.ctas_per_sm = o->ctas_per_sm;
+  L.stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = fem::launch_fwd_iso(L, mid);
+  if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_fwd_iso launch");
+  return ok();
+}
+
 fem_status fem_geometry(const fem_mesh* mesh, const float* coef, const fem_options* options, double* detJ,
                         float* G, void* stream) {
   fem_status s = check_mesh(mesh);
@@ -225,7 +265,8 @@ fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (coef_p1(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the per-element-coefficient forms");
+  if (coef_p1(form) || non_affine(form))
+    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (!bytes) return fail(FEM_ERR_ARG, "bytes is NULL");
@@ -258,7 +299,8 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (coef_p1(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the per-element-coefficient forms");
+  if (coef_p1(form) || non_affine(form))
+    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");

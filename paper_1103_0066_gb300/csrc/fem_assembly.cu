@@ -307,7 +307,7 @@ fem_status asm_fail(fem_status s, const char* msg) {
 // Block size of the assembled matrix for a form: 1 (scalar P1 forms), d (P1
 // elasticity), 0 (not assembled: P2 unknowns include the edges).
 int asm_block(int form, int dim) {
-  if (form == FEM_LAPLACE_P1 || form == FEM_LAPLACE_P1_W1) return 1;
+  if (form == FEM_LAPLACE_P1 || form == FEM_LAPLACE_P1_W1 || form == FEM_LAPLACE_P1_ISO) return 1;
   if (form == FEM_ELASTIC_P1) return dim;
   return 0;
 }
@@ -317,7 +317,7 @@ fem_status asm_check(const fem_mesh* mesh, int form) {
   if ((mesh->dim != 2 && mesh->dim != 3) || mesh->n_elem < 0 || mesh->n_vert < 0 || mesh->n_vert > INT32_MAX ||
       (mesh->n_elem > 0 && !mesh->conn))
     return asm_fail(FEM_ERR_ARG, "invalid mesh (dim 2/3, counts, conn)");
-  if (form < FEM_LAPLACE_P1 || form > FEM_LAPLACE_P2_W1) return asm_fail(FEM_ERR_ARG, "form out of range");
+  if (form < FEM_LAPLACE_P1 || form > FEM_LAPLACE_P2_ISO) return asm_fail(FEM_ERR_ARG, "form out of range");
   if (asm_block(form, mesh->dim) == 0)
     return asm_fail(FEM_ERR_UNSUPPORTED, "assembly serves the P1 forms (vertex unknowns)");
   if (mesh->n_elem * (mesh->dim + 1) * (mesh->dim + 1) > INT32_MAX)

@@ -30,33 +30,53 @@
 //     and the geometric tensor becomes w_k G^{mu nu} (Eq. 22), so the
 //     contraction runs over (d+1) x d(d+1)/2 slots, slot k * NGB + g.
 //
+//   LAPLACE_P1_ISO / LAPLACE_P2_ISO : the Laplacian on non-affine elements
+//     (Eqs. 16-19): J^{-1} is projected onto P1 by its vertex values, so G
+//     gains the vertex indices, G^{(k mu),(l nu)} = |J| J^{-1}_{mu a,k} J^{-1}_{nu a,l},
+//     and K^{ij}_{(k mu),(l nu)} = int_ref lambda_k lambda_l d_mu phi_i d_nu phi_j;
+//     the slot (k mu) ranges over (d+1) d values and G is folded over the
+//     symmetric pairs of slots like elasticity's.
+//
 // Integer scaling: every entry is stored as K' * DEN with DEN = (d+2)! (twice
-// that for elasticity; (d+3)! for the P1-coefficient forms, whose integrands
-// have one more linear factor), using  int_ref lambda^a = a! / (|a| + d)!.
+// that for elasticity; (d+3)! for the P1-coefficient forms and (d+4)! for the
+// non-affine forms, whose integrands have one or two more linear factors),
+// using  int_ref lambda^a = a! / (|a| + d)!.
 #pragma once
 #include <cstdint>
 
 namespace fem {
 
-enum FormId : int { LAPLACE_P1 = 0, LAPLACE_P2 = 1, ELASTIC_P1 = 2, LAPLACE_P1_W1 = 3, LAPLACE_P2_W1 = 4 };
+enum FormId : int {
+  LAPLACE_P1 = 0,
+  LAPLACE_P2 = 1,
+  ELASTIC_P1 = 2,
+  LAPLACE_P1_W1 = 3,
+  LAPLACE_P2_W1 = 4,
+  LAPLACE_P1_ISO = 5,
+  LAPLACE_P2_ISO = 6
+};
 
 template <int D, int FORM>
 struct FormTraits {
   static_assert(D == 2 || D == 3, "dimension");
-  static constexpr bool W1 = FORM == LAPLACE_P1_W1 || FORM == LAPLACE_P2_W1;  // P1 coefficient
-  static constexpr int BASE = FORM == LAPLACE_P1_W1 ? LAPLACE_P1 : FORM == LAPLACE_P2_W1 ? LAPLACE_P2 : FORM;
+  static constexpr bool W1 = FORM == LAPLACE_P1_W1 || FORM == LAPLACE_P2_W1;     // P1 coefficient
+  static constexpr bool ISO = FORM == LAPLACE_P1_ISO || FORM == LAPLACE_P2_ISO;  // non-affine elements
+  static constexpr int BASE = (FORM == LAPLACE_P1_W1 || FORM == LAPLACE_P1_ISO)   ? LAPLACE_P1
+                              : (FORM == LAPLACE_P2_W1 || FORM == LAPLACE_P2_ISO) ? LAPLACE_P2
+                                                                                  : FORM;
   static constexpr int NV = D + 1;                                // vertices
   static constexpr int DEG = BASE == LAPLACE_P2 ? 2 : 1;
   static constexpr int NB = DEG == 1 ? D + 1 : (D + 1) * (D + 2) / 2;  // scalar basis
   static constexpr int NC = FORM == ELASTIC_P1 ? D : 1;           // components
   static constexpr int N = NB * NC;                               // rows of A_e
   static constexpr int NN = N * N;
-  static constexpr int NP = FORM == ELASTIC_P1 ? D * D : D;       // range of one G slot
+  static constexpr int NP = FORM == ELASTIC_P1 ? D * D : ISO ? (D + 1) * D : D;  // range of one G slot
   static constexpr int NGB = NP * (NP + 1) / 2;                   // folded G entries of the base form
   static constexpr int NW = W1 ? NV : 1;                          // coefficient values per element
   static constexpr int NG = NW * NGB;                             // contraction slots
   static constexpr int NT = N * (N + 1) / 2;                      // unique A entries
-  static constexpr int DEN = W1 ? (D == 2 ? 120 : 720) : (D == 2 ? 24 : 120) * (FORM == ELASTIC_P1 ? 2 : 1);
+  static constexpr int DEN = ISO ? (D == 2 ? 720 : 5040)
+                             : W1 ? (D == 2 ? 120 : 720) : (D == 2 ? 24 : 120) * (FORM == ELASTIC_P1 ? 2 : 1);
 };
 
 // index of the pair (p, q), p <= q, in row-major upper-triangle order
@@ -135,6 +155,29 @@ constexpr int integrate_lam_lin_lin(int k, const Lin& p, const Lin& q) {
   return s;
 }
 
+// (d+4)! * int_ref lambda_k lambda_l (p)(q) dxi: four homogeneous linear
+// factors; (d+4)! int_ref of a degree-4 monomial is the product of the
+// factorials of its exponents.
+template <int D>
+constexpr int integrate_lam2_lin_lin(int k, int l, const Lin& p, const Lin& q) {
+  int s = 0;
+  for (int a = 0; a <= D; ++a)
+    for (int b = 0; b <= D; ++b) {
+      const int pa = p.c[a] + p.c0, qb = q.c[b] + q.c0;
+      if (pa == 0 || qb == 0) continue;
+      int cnt[4] = {0, 0, 0, 0};
+      ++cnt[k];
+      ++cnt[l];
+      ++cnt[a];
+      ++cnt[b];
+      int m = 1;
+      for (int t = 0; t <= D; ++t)
+        for (int f = 2; f <= cnt[t]; ++f) m *= f;
+      s += pa * qb * m;
+    }
+  return s;
+}
+
 template <int D, int FORM>
 struct RefTensor {
   using T = FormTraits<D, FORM>;
@@ -153,7 +196,21 @@ constexpr RefTensor<D, FORM> make_ref_tensor() {
         for (int j = 0; j < T::NB; ++j)
           kref[mu][nu][i][j] = integrate_lin_lin<D>(basis_deriv<D, T::DEG>(i, mu),
                                                     basis_deriv<D, T::DEG>(j, nu));
-  if constexpr (T::W1) {
+  if constexpr (T::ISO) {
+    // slot p = k * D + mu; folded over p <= q
+    for (int pp = 0; pp < T::NP; ++pp)
+      for (int qq = pp; qq < T::NP; ++qq) {
+        const int g = pair_index(pp, qq, T::NP);
+        const int k = pp / D, mu = pp % D, l = qq / D, nu = qq % D;
+        for (int i = 0; i < T::NB; ++i)
+          for (int j = 0; j < T::NB; ++j) {
+            int v = integrate_lam2_lin_lin<D>(k, l, basis_deriv<D, T::DEG>(i, mu), basis_deriv<D, T::DEG>(j, nu));
+            if (pp != qq)
+              v += integrate_lam2_lin_lin<D>(l, k, basis_deriv<D, T::DEG>(i, nu), basis_deriv<D, T::DEG>(j, mu));
+            r.v[g][i][j] = v;
+          }
+      }
+  } else if constexpr (T::W1) {
     for (int k = 0; k <= D; ++k)
       for (int mu = 0; mu < D; ++mu)
         for (int nu = mu; nu < D; ++nu) {

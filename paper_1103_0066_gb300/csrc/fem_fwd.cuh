@@ -137,6 +137,94 @@ __device__ __forceinline__ int gather_regs(const CT* coords, int64_t n_vert, int
   return GF_ELEM | GF_OK;
 }
 
+// Contraction of a lane's folded G with K (immediates) and the tile's store:
+// the swizzled stage and its TMA tensor store (TMA), else the stage and the
+// warp's coalesced read-out.
+template <int D, int FORM, class CT, class OT, bool TMA = false>
+__device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, int64_t tile, int lane,
+                                                   const OT (&Gf)[FormTraits<D, FORM>::NG], OT* st,
+                                                   const CUtensorMap* tmap) {
+  using FT = FormTraits<D, FORM>;
+  using PL = FwdPlan<D, FORM, CT, OT>;
+  constexpr int NN = FT::NN;
+  constexpr int SST = PL::SST;
+  const int64_t e0 = tile * 32;
+  const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
+  OT* dst = p.A + e0 * NN;
+  if constexpr (PL::SWZ16) {
+    // rows as float4 chunks, chunk index XOR-swizzled with (lane >> 1) & 3
+    RegSink<4, float> rs;
+    contract<D, FORM>(Gf, rs);
+    const int sw = (lane >> 1) & 3;
+    float* row = st + lane * 16;
+    if constexpr (TMA) {
+      if (lane == 0) bulk_wait_read<1>();  // the store that last read this stage (two tiles ago) is done
+      __syncwarp();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      *reinterpret_cast<float4*>(row + 4 * (r ^ sw)) =
+          make_float4(rs.a[4 * r], rs.a[4 * r + 1], rs.a[4 * r + 2], rs.a[4 * r + 3]);
+    if constexpr (TMA) {
+      fence_proxy_async_smem();  // the rows are visible to the tensor store
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(tmap, 0, int(e0), smem_u32(st));
+        bulk_commit();
+      }
+      return;
+    }
+    __syncwarp();
+    // chunk c = lane + 32 r holds element (lane >> 2) + 8 r, row lane & 3
+    const float* src = st + 16 * (lane >> 2) + 4 * ((lane & 3) ^ ((lane >> 3) & 3));
+    if (p.vec_store) {
+      float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int c = lane + 32 * r;
+        if (c < 4 * cnt) __stcs(d4 + c, *reinterpret_cast<const float4*>(src + 128 * r));
+      }
+    } else {
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int c = lane + 32 * r;
+        if (c < 4 * cnt) {
+          const float4 v = *reinterpret_cast<const float4*>(src + 128 * r);
+          __stcs(dst + 4 * c, v.x);
+          __stcs(dst + 4 * c + 1, v.y);
+          __stcs(dst + 4 * c + 2, v.z);
+          __stcs(dst + 4 * c + 3, v.w);
+        }
+      }
+    }
+  } else {
+    StageSink<FT::N, SST, OT> sink{st + lane * SST};
+    contract<D, FORM>(Gf, sink);
+    __syncwarp();
+    bool done = false;
+    if constexpr (sizeof(OT) == 4 && NN % 4 == 0) {
+      if (p.vec_store) {
+        const int nq = cnt * (NN / 4);
+        for (int q = lane; q < nq; q += 32) {
+          const int idx = 4 * q;
+          const int el = idx / NN;
+          const OT* s = st + el * SST + (idx - el * NN);
+          __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(s[0], s[1], s[2], s[3]));
+        }
+        done = true;
+      }
+    }
+    if (!done) {
+      const int nw = cnt * NN;
+      for (int idx = lane; idx < nw; idx += 32) {
+        const int el = idx / NN;
+        __stcs(dst + idx, st[el * SST + (idx - el * NN)]);
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // The element's coefficient: one value (per-element coefficient) or the
 // d+1 vertex values of a P1 coefficient (gathered like the coordinates).
 template <int NW>
@@ -190,81 +278,7 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
   } else if (flags & GF_ELEM) {
     err |= DEVERR_CONN;
   }
-  const int64_t e0 = tile * 32;
-  const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
-  OT* dst = p.A + e0 * NN;
-  if constexpr (PL::SWZ16) {
-    // rows as float4 chunks, chunk index XOR-swizzled with (lane >> 1) & 3
-    RegSink<4, float> rs;
-    contract<D, FORM>(Gf, rs);
-    const int sw = (lane >> 1) & 3;
-    float* row = st + lane * 16;
-    if constexpr (TMA) {
-      if (lane == 0) bulk_wait_read<1>();  // the store that last read this stage (two tiles ago) is done
-      __syncwarp();
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-      *reinterpret_cast<float4*>(row + 4 * (r ^ sw)) =
-          make_float4(rs.a[4 * r], rs.a[4 * r + 1], rs.a[4 * r + 2], rs.a[4 * r + 3]);
-    if constexpr (TMA) {
-      fence_proxy_async_smem();  // the rows are visible to the tensor store
-      __syncwarp();
-      if (lane == 0) {
-        tma_store_2d(tmap, 0, int(e0), smem_u32(st));
-        bulk_commit();
-      }
-      return err;
-    }
-    __syncwarp();
-    // chunk c = lane + 32 r holds element (lane >> 2) + 8 r, row lane & 3
-    const float* src = st + 16 * (lane >> 2) + 4 * ((lane & 3) ^ ((lane >> 3) & 3));
-    if (p.vec_store) {
-      float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int c = lane + 32 * r;
-        if (c < 4 * cnt) __stcs(d4 + c, *reinterpret_cast<const float4*>(src + 128 * r));
-      }
-    } else {
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int c = lane + 32 * r;
-        if (c < 4 * cnt) {
-          const float4 v = *reinterpret_cast<const float4*>(src + 128 * r);
-          __stcs(dst + 4 * c, v.x);
-          __stcs(dst + 4 * c + 1, v.y);
-          __stcs(dst + 4 * c + 2, v.z);
-          __stcs(dst + 4 * c + 3, v.w);
-        }
-      }
-    }
-  } else {
-    StageSink<FT::N, SST, OT> sink{st + lane * SST};
-    contract<D, FORM>(Gf, sink);
-    __syncwarp();
-    bool done = false;
-    if constexpr (sizeof(OT) == 4 && NN % 4 == 0) {
-      if (p.vec_store) {
-        const int nq = cnt * (NN / 4);
-        for (int q = lane; q < nq; q += 32) {
-          const int idx = 4 * q;
-          const int el = idx / NN;
-          const OT* s = st + el * SST + (idx - el * NN);
-          __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(s[0], s[1], s[2], s[3]));
-        }
-        done = true;
-      }
-    }
-    if (!done) {
-      const int nw = cnt * NN;
-      for (int idx = lane; idx < nw; idx += 32) {
-        const int el = idx / NN;
-        __stcs(dst + idx, st[el * SST + (idx - el * NN)]);
-      }
-    }
-  }
-  __syncwarp();
+  fwd_contract_store<D, FORM, CT, OT, TMA>(p, tile, lane, Gf, st, tmap);
   return err;
 }
 

@@ -1,0 +1,191 @@
+// fem_fwd_iso.cu -- forward integration of the Laplacian on non-affine
+// (quadratic-geometry) elements, Eqs. 16-19.
+//
+// Each element is given by its d+1 vertices (conn, coords) and the d(d+1)/2
+// edge-midpoint nodes of its quadratic geometry map (mid, element by
+// element).  Per lane (one element):
+//   1. the nodes relative to vertex 0 (so the map's derivatives see small
+//      differences, not absolute coordinates);
+//   2. J at every vertex k from the derivatives of the quadratic geometry
+//      basis there (small integers, compile time), its adjugate and det, and
+//      J^{-1}_k = adj / det -- the values the projection of Eq. 17 interpolates;
+//   3. |J| = |det J| at the centroid (Eq. 17 keeps |J| outside the integral);
+//   4. G^{(k mu),(l nu)} = w |J| / DEN  sum_a J^{-1}_{mu a,k} J^{-1}_{nu a,l}
+//      over the folded slot pairs (Eq. 18), then the same immediate-operand
+//      contraction with K^{ij}_{(k mu),(l nu)} and the same tile store as the
+//      affine kernel (Eq. 19).
+// The Jacobian steps run in plain FP32: this path serves curved, non-sliver
+// elements; an element with a singular J at a vertex or at the centroid is
+// flagged degenerate and gets A = 0.
+#include "fem_fwd.cuh"
+
+namespace fem {
+
+namespace {
+
+// d psi_a / d xi_mu of the quadratic geometry basis (vertices, then edges in
+// the P2 order) at reference vertex k (k <= D), or (D + 1) times it at the
+// centroid (k = D + 1); all integers.
+template <int D>
+constexpr int geo_dpsi(int a, int mu, int k) {
+  if (a <= D) {
+    if (k <= D) return (a == k ? 3 : -1) * dlam(a, mu);
+    return (3 - D) * dlam(a, mu);  // (D+1) * (4/(D+1) - 1)
+  }
+  int t = a - (D + 1);
+  for (int p = 0; p <= D; ++p)
+    for (int q = p + 1; q <= D; ++q) {
+      if (t == 0) {
+        if (k <= D) return 4 * ((p == k ? dlam(q, mu) : 0) + (q == k ? dlam(p, mu) : 0));
+        return 4 * (dlam(p, mu) + dlam(q, mu));
+      }
+      --t;
+    }
+  return 0;
+}
+
+constexpr int n_geo(int D) { return (D + 1) * (D + 2) / 2; }
+
+// e[mu][al] = sum_a geo_dpsi(a, mu, K) * node_a[al] with node 0 at the origin.
+template <int D, int K>
+__device__ __forceinline__ void geo_jacobian(const float (&nd)[n_geo(D)][D], float (&e)[D][D]) {
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+    for (int al = 0; al < D; ++al) {
+      float s = 0.f;
+#pragma unroll
+      for (int a = 1; a < n_geo(D); ++a) {
+        const int c = geo_dpsi<D>(a, mu, K);
+        if (c != 0) s = fmaf(float(c), nd[a][al], s);
+      }
+      e[mu][al] = s;
+    }
+}
+
+template <int D>
+__device__ __forceinline__ float det_adj(const float (&e)[D][D], float (&adj)[D][D]) {
+  adjugate(e, adj);
+  float det = 0.f;
+#pragma unroll
+  for (int al = 0; al < D; ++al) det = fmaf(e[0][al], adj[0][al], det);
+  return det;
+}
+
+template <int D, int K>
+__device__ __forceinline__ bool vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D]) {
+  float e[D][D], adj[D][D];
+  geo_jacobian<D, K>(nd, e);
+  const float det = det_adj<D>(e, adj);
+  const float r = __frcp_rn(det);
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+    for (int al = 0; al < D; ++al) ji[K][mu][al] = adj[mu][al] * r;  // (J^{-1})_{mu al} at vertex K
+  return det != 0.f;
+}
+
+template <int D, int... Ks>
+__device__ __forceinline__ bool all_vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D],
+                                                std::integer_sequence<int, Ks...>) {
+  return (vertex_jinv<D, Ks>(nd, ji) & ...);
+}
+
+template <int D, int FORM>
+__global__ void __launch_bounds__(128) fem_fwd_iso_kernel(FwdParams<float, float> p, const float* __restrict__ mid) {
+  using FT = FormTraits<D, FORM>;
+  using PL = FwdPlan<D, FORM, float, float>;
+  constexpr int NE = D * (D + 1) / 2, NP = FT::NP;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  float* st = reinterpret_cast<float*>(smem_raw + size_t(warp) * PL::per_warp);
+  const int64_t ntiles = (p.n_elem + 31) / 32;
+  int err = 0;
+  for (int64_t t = int64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += int64_t(gridDim.x) * nwarps) {
+    const int64_t e = t * 32 + lane;
+    int v[D + 1];
+    float X[D + 1][D];
+    load_conn<D>(p.conn, e, p.n_elem, p.vec_conn, v);
+    const int flags = gather_regs<D>(p.coords, p.n_vert, e, p.n_elem, v, X);
+    float Gf[FT::NG];
+#pragma unroll
+    for (int g = 0; g < FT::NG; ++g) Gf[g] = 0.f;
+    if (flags & GF_OK) {
+      float nd[n_geo(D)][D];  // geometry nodes relative to vertex 0
+#pragma unroll
+      for (int a = 0; a <= D; ++a)
+#pragma unroll
+        for (int al = 0; al < D; ++al) nd[a][al] = X[a][al] - X[0][al];
+      const float* m = mid + e * (NE * D);
+#pragma unroll
+      for (int q = 0; q < NE; ++q)
+#pragma unroll
+        for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = __ldcs(m + q * D + al) - X[0][al];
+      float ji[D + 1][D][D];
+      bool ok = all_vertex_jinv<D>(nd, ji, std::make_integer_sequence<int, D + 1>{});
+      float ec[D][D], adjc[D][D];
+      geo_jacobian<D, D + 1>(nd, ec);  // (D + 1) J at the centroid
+      float detc = det_adj<D>(ec, adjc);
+      detc *= D == 2 ? (1.f / 9.f) : (1.f / 64.f);  // det scales by (D + 1)^D
+      ok &= detc != 0.f;
+      if (!ok) {
+        err |= DEVERR_DEGENERATE;
+      } else {
+        const float w = (p.coef && e < p.n_elem) ? __ldg(p.coef + e) : 1.f;
+        const float scale = w * fabsf(detc) * (1.f / float(FT::DEN));
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp)
+#pragma unroll
+          for (int qq = pp; qq < NP; ++qq) {
+            float s = 0.f;
+#pragma unroll
+            for (int al = 0; al < D; ++al) s = fmaf(ji[pp / D][pp % D][al], ji[qq / D][qq % D][al], s);
+            Gf[pair_index(pp, qq, NP)] = scale * s;
+          }
+      }
+    } else if (flags & GF_ELEM) {
+      err |= DEVERR_CONN;
+    }
+    fwd_contract_store<D, FORM, float, float, false>(p, t, lane, Gf, st, nullptr);
+  }
+  err = __reduce_or_sync(0xffffffffu, err);
+  if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
+}
+
+template <int D, int FORM>
+cudaError_t launch_iso_t(const FwdLaunch& L, const float* mid) {
+  using PL = FwdPlan<D, FORM, float, float>;
+  FwdParams<float, float> p;
+  p.conn = L.conn;
+  p.coords = static_cast<const float*>(L.coords);
+  p.coef = L.coef;
+  p.A = static_cast<float*>(L.A);
+  p.n_elem = L.n_elem;
+  p.n_vert = L.n_vert;
+  p.dev_err = L.dev_err;
+  p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
+  p.vec_store = (reinterpret_cast<uintptr_t>(L.A) % 16 == 0);
+  auto kern = fem_fwd_iso_kernel<D, FORM>;
+  const int warps = 4;
+  const size_t smem = size_t(warps) * PL::per_warp;
+  cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (st != cudaSuccess) return st;
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), warps, smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, warps * 32, smem, L.stream>>>(p, mid);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_fwd_iso(const FwdLaunch& L, const float* mid) {
+  if (L.dim == 2) {
+    if (L.form == LAPLACE_P1_ISO) return launch_iso_t<2, LAPLACE_P1_ISO>(L, mid);
+    if (L.form == LAPLACE_P2_ISO) return launch_iso_t<2, LAPLACE_P2_ISO>(L, mid);
+  } else {
+    if (L.form == LAPLACE_P1_ISO) return launch_iso_t<3, LAPLACE_P1_ISO>(L, mid);
+    if (L.form == LAPLACE_P2_ISO) return launch_iso_t<3, LAPLACE_P2_ISO>(L, mid);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace fem

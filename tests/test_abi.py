@@ -59,6 +59,39 @@ def test_reference_tensor_p1_coefficient(fem, orc, dim, form):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [5, 6])
+def test_reference_tensor_non_affine(fem, orc, dim, form):
+    """Eqs. 18-19: A = G^{(k mu),(l nu)} K^{ij}_{(k mu),(l nu)} with the library's
+    K and G = |det J(centroid)| J^{-1}_k J^{-1}_l^T built here from the quadratic
+    geometry map equals the oracle's quadrature on curved elements."""
+    K, den = fem.reference_tensor(form, dim)
+    K = K.numpy().astype(np.float64)
+    n, ng, _ = fem.form_info(form, dim)
+    npair = (dim + 1) * dim
+    assert ng == npair * (npair + 1) // 2 and den == (720 if dim == 2 else 5040)
+    rng = np.random.default_rng(14)
+    edges = [(a, b) for a in range(dim + 1) for b in range(a + 1, dim + 1)]
+    for _ in range(6):
+        X = np.vstack([np.zeros(dim), np.eye(dim)]) + 0.1 * rng.standard_normal((dim + 1, dim))
+        M = np.array([0.5 * (X[a] + X[b]) for a, b in edges]) + 0.05 * rng.standard_normal((len(edges), dim))
+        nodes = np.vstack([X, M])
+
+        def jac(xi):  # J[alpha][mu] of the quadratic map
+            _, g = orc.basis(dim, 2, xi)
+            return nodes.T @ g
+
+        verts = [np.zeros(dim)] + [np.eye(dim)[k] for k in range(dim)]
+        Ji = [np.linalg.inv(jac(v)) for v in verts]            # Ji[k][mu][alpha]
+        detc = abs(np.linalg.det(jac(np.full(dim, 1.0 / (dim + 1)))))
+        slots = [(k, mu) for k in range(dim + 1) for mu in range(dim)]
+        G = [detc * Ji[slots[p][0]][slots[p][1]] @ Ji[slots[q][0]][slots[q][1]]
+             for p in range(npair) for q in range(p, npair)]
+        A = np.einsum("g,gij->ij", np.array(G), K) / den
+        Ar, _, _ = orc.element_matrix_iso(dim, form - 5, X, M)
+        assert np.abs(A - Ar).max() < 1e-12 * np.abs(Ar).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
 def test_form_info(fem, dim):
     assert fem.form_info(LP1, dim) == (dim + 1, dim * (dim + 1) // 2, 24 if dim == 2 else 120)
     nb2 = (dim + 1) * (dim + 2) // 2
@@ -145,7 +178,7 @@ def test_host_detected_errors(fem):
     assert lib.fem_bwd_workspace_size(ctypes.byref(m), LP1, None, ctypes.byref(b)) == nat.FEM_OK
     assert b.value >= 4 * (101 + 40) + 4 * 10 * 4 * 3
     with pytest.raises(fem.FemError):
-        fem.nat.fem_form_info(5, 3)
+        fem.nat.fem_form_info(7, 3)
 
 
 def test_tensor_core_combinations_rejected_on_host(fem):

@@ -1,0 +1,75 @@
+"""GPU parity of the Laplacian on non-affine (quadratic-geometry) elements,
+Eqs. 16-19, against the FP64 oracle (-m gpu).  Per element, every element:
+max_ij |A_gpu - A_ref| <= 1e-5 max_ij |A_ref| (FP32 Jacobian steps on curved,
+non-sliver elements)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1103_0066_gb300 import meshgen as mg
+from conftest import rel_err_per_element
+
+pytestmark = pytest.mark.gpu
+LP1, LP2, ISO1, ISO2 = 0, 1, 5, 6
+DEV = "cuda:0"
+TOL = 1e-5
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _curved(dim, eps=0.05, seed=41):
+    base = (mg.square_tri_mesh(13, 0.2, mg.rng_for(seed), np.float32) if dim == 2
+            else mg.cube_tet_mesh(7, 0.15, mg.rng_for(seed), 0.0, np.float32))
+    return mg.curved_mesh(base, eps)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [ISO1, ISO2])
+def test_iso_matches_oracle(gfem, orc, dim, form):
+    mesh, mid = _curved(dim)
+    coef = mg.lognormal_coef(mg.rng_for(42), mesh.n_elem)
+    A = gfem.integrate_fwd_iso(_t(mesh.coords), _t(mesh.conn), _t(mid), form, _t(coef))
+    torch.cuda.synchronize()
+    Ar, fl = orc.integrate_iso(dim, form - 5, mesh.conn, mesh.coords, mid, coef)
+    assert not fl.any()
+    err = rel_err_per_element(A.cpu().numpy(), Ar)
+    assert err.max() <= TOL, (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [ISO1, ISO2])
+def test_iso_straight_sides_give_affine(gfem, orc, dim, form):
+    mesh, _ = _curved(dim, eps=0.0)
+    mid = np.stack([0.5 * (mesh.coords[mesh.conn[:, a]] + mesh.coords[mesh.conn[:, b]])
+                    for a, b in mg.edge_pairs(dim)], axis=1).astype(np.float32)
+    A = gfem.integrate_fwd_iso(_t(mesh.coords), _t(mesh.conn), _t(mid), form)
+    Ar, _ = orc.integrate(dim, form - 5, mesh.conn, mesh.coords)
+    assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL
+
+
+@pytest.mark.parametrize("E", [1, 31, 33, 257])
+def test_iso_ragged_tails_and_flags(gfem, orc, E):
+    mesh, mid = _curved(3)
+    conn = mesh.conn[:E].copy()
+    m = mid[:E]
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    if E > 5:
+        conn[5, 1] = mesh.n_vert + 7
+    A = gfem.integrate_fwd_iso(_t(mesh.coords), _t(conn), _t(m), ISO2, dev_err=err)
+    Ar, fl = orc.integrate_iso(3, LP2, conn, mesh.coords, m)
+    assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL
+    if E > 5:
+        assert fl[5] == 1 and int(err.item()) & 1 and torch.all(A[5] == 0)
+
+
+def test_iso_argument_errors(gfem):
+    mesh, mid = _curved(2)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    with pytest.raises(gfem.FemError):
+        gfem.integrate_fwd(coords, conn, ISO1)          # needs its edge nodes
+    with pytest.raises(ValueError):
+        gfem.integrate_fwd_iso(coords, conn, _t(mid[:, :2]), ISO1)
+    with pytest.raises(gfem.FemError):
+        gfem.integrate_fwd_iso(coords, conn, _t(mid), LP1)   # not a non-affine form
