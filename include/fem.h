@@ -289,22 +289,25 @@ FEM_API void fem_batch_destroy(fem_batch* batch);
  * (c, c') of entry (v, w) sums A_e[(c,i),(c',j)] over the elements with
  * conn[e][i] = v, conn[e][j] = w, local unknown (c, i) being row c*(d+1) + i
  * of A_e).  The P2 forms are not assembled (FEM_ERR_UNSUPPORTED): their
- * unknowns include the edges.  Every entry is the sum of its element
- * contributions in increasing element order, so values are bitwise
- * reproducible.  Rows have at most 255 columns and 128 incident elements
- * (FEM_ERR_UNSUPPORTED otherwise). */
+ * unknowns include the edges.  Every entry is a sum in a fixed order, so
+ * values are bitwise reproducible: for the scalar forms, per 32-element tile
+ * the tile's contributions in element order, then those tile sums in tile
+ * order; for the blocks, all contributions in element order. */
 
 /* Device workspace bytes of the assembly maps of this mesh (depends on the
  * connectivity only; the capacity of the column array is every entry distinct). */
 FEM_API fem_status fem_assembly_workspace_size(const fem_mesh* mesh, int32_t form, size_t* bytes);
 
 /* Builds the row pattern (row_ptr [n_vert+1], col_idx [nnz], columns increasing)
- * and the incidence maps into `ws` (device, caller owned, 256-byte aligned),
- * once per connectivity, on `stream`, which it synchronizes; *nnz (may be NULL)
- * receives the number of nonzero entries (blocks).  A connectivity entry outside
- * [0, n_vert) is FEM_ERR_ARG. */
+ * and the assembly maps into `ws` (device, caller owned, 256-byte aligned),
+ * once per connectivity, on `stream`, which it synchronizes.  *nnz receives the
+ * number of nonzero entries (blocks); *n_records the number of tile records of
+ * the scalar forms (the distinct entries of every 32-element tile; 0 for
+ * blocks).  Either output may be NULL.  A connectivity entry outside
+ * [0, n_vert) is FEM_ERR_ARG; an element that repeats a vertex, or a vertex
+ * with more than 128 elements or 255 neighbours, FEM_ERR_UNSUPPORTED. */
 FEM_API fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size_t ws_bytes, int64_t* nnz,
-                                      void* stream);
+                                      int64_t* n_records, void* stream);
 
 /* Device pointers to the pattern inside a built workspace (row_ptr [n_vert+1],
  * col_idx [nnz]); either output may be NULL. */

@@ -155,7 +155,8 @@ class Assembly:
         self.bytes = nat.fem_assembly_workspace_size(self.m, form)
         self.buf = torch.empty(max(self.bytes, 256), dtype=torch.uint8, device=coords.device)
         self._keep = (coords, conn)
-        self.nnz = nat.fem_assembly_build(self.m, form, self.buf.data_ptr(), self.bytes, _stream_ptr(stream))
+        self.nnz, self.n_records = nat.fem_assembly_build(self.m, form, self.buf.data_ptr(), self.bytes,
+                                                          _stream_ptr(stream))
         rp, ci = nat.fem_assembly_pattern(self.m, form, self.buf.data_ptr(), self.bytes)
         V = coords.shape[0]
         base = self.buf.data_ptr()

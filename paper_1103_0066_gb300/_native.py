@@ -97,7 +97,8 @@ def load():
             "fem_batch_errors": ([P, ctypes.POINTER(I32), P], ctypes.c_int),
             "fem_batch_destroy": ([P], None),
             "fem_assembly_workspace_size": ([MP, I32, ctypes.POINTER(SZ)], ctypes.c_int),
-            "fem_assembly_build": ([MP, I32, P, SZ, ctypes.POINTER(ctypes.c_int64), P], ctypes.c_int),
+            "fem_assembly_build": ([MP, I32, P, SZ, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P],
+                                   ctypes.c_int),
             "fem_assembly_pattern": ([MP, I32, P, SZ, ctypes.POINTER(P), ctypes.POINTER(P)], ctypes.c_int),
             "fem_assemble": ([MP, I32, P, P, SZ, P, P], ctypes.c_int),
         }
@@ -238,10 +239,11 @@ def fem_assembly_workspace_size(mesh: FemMesh, form: int) -> int:
     return b.value
 
 
-def fem_assembly_build(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int, stream: int) -> int:
-    nnz = ctypes.c_int64()
-    check(load().fem_assembly_build(ctypes.byref(mesh), form, ws_ptr, ws_bytes, ctypes.byref(nnz), stream or None))
-    return nnz.value
+def fem_assembly_build(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int, stream: int):
+    nnz, nrec = ctypes.c_int64(), ctypes.c_int64()
+    check(load().fem_assembly_build(ctypes.byref(mesh), form, ws_ptr, ws_bytes, ctypes.byref(nnz), ctypes.byref(nrec),
+                                    stream or None))
+    return nnz.value, nrec.value
 
 
 def fem_assembly_pattern(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int):

@@ -13,17 +13,33 @@
 //                distinct ones (the row's columns, increasing), and stores for
 //                every incidence t and local vertex j the position of
 //                conn[e][j] among them (colpos, one byte)
-// Assembly (fem_assemble): one thread per row walks its incidences in
-// increasing element order and adds the element's row i into the row's
-// columns, accumulating in shared memory (rows of up to kFastCols columns) or
-// in place in the output.  Every matrix entry is thus the sum of its element
-// contributions in increasing element order: bitwise reproducible.
+// Scalar forms, tile records (built once per connectivity, after the pattern):
+//   per 32-element tile (one warp): the tile's distinct vertices ("runs", R_t
+//   of them) and every slot's run index (one byte); the distinct (row run,
+//   column run) cells the tile touches, each one RECORD (records numbered in
+//   tile order), and the entry -> records CSR (eoff, rec_list) -- the tile /
+//   record scheme of the adjoint's reduction, keyed by matrix entry.
+// Assembly of the scalar forms (fem_assemble):
+//   1. one warp per tile reads its element matrices coalesced into shared
+//      memory and adds them, element by element, into a dense R_t x R_t tile
+//      matrix (an element's cells are distinct, so a step has no conflicts);
+//      each cell is the sum of its contributions in element order.  The cells
+//      are written as records, in tile order (tiles with R_t above kTileRuns
+//      take an exact per-record scan of the tile instead);
+//   2. one thread per entry sums its records (gathered through rec_list) in
+//      tile order.
+// Every entry is therefore a fixed-order sum, bitwise reproducible.
+// P1 elasticity (d x d blocks) takes the row kernel: one thread per row walks
+// its incidences in increasing element order and adds the element's rows into
+// the row's columns, accumulating in shared memory (rows of up to kFastCols
+// columns) or in place in the output.
 #include <cuda_runtime.h>
 
 #include <cstdint>
 
 #include "../../include/fem.h"
 #include "fem_internal.h"
+#include "fem_pipe.cuh"
 
 namespace fem {
 
@@ -34,8 +50,12 @@ constexpr int kMaxCols = 255;   // distinct columns per row (one-byte positions)
 constexpr int kFastCols = 32;   // rows accumulated in shared memory
 constexpr int kPatWarps = 4;
 constexpr int kAsmThreads = 64;
+constexpr int kTileRuns = 40;  // dense tile matrix side (distinct vertices of a 32-element tile)
+constexpr int kTileCap = 128;  // slots of a 32-element tile (tets: 4 per element)
+constexpr int kCellCap = 512;  // contributions of a 32-element tile (tets: 16 per element)
+constexpr int kHalvesDisjoint = 0x100;  // tile_runs flag: elements 0-15 and 16-31 share no cell
 
-enum : int { ASM_ROW_TOO_LONG = 1, ASM_BAD_VERTEX = 2 };
+enum : int { ASM_ROW_TOO_LONG = 1, ASM_BAD_VERTEX = 2, ASM_REPEATED_VERTEX = 4 };
 
 __global__ void check_conn_kernel(const int32_t* __restrict__ conn, int64_t n, int64_t n_vert, int32_t* flag) {
   int bad = 0;
@@ -222,9 +242,316 @@ __global__ void __launch_bounds__(kAsmThreads)
   }
 }
 
+// ------------------------------------------------------------------ tile records (scalar forms)
+
+// Sorts n_pow2 keys in shared memory (bitonic, one warp).
+template <class K>
+__device__ __forceinline__ void warp_bitonic(K* key, int P, int lane) {
+  for (int k2 = 2; k2 <= P; k2 <<= 1)
+    for (int jj = k2 >> 1; jj > 0; jj >>= 1) {
+      for (int i = lane; i < P; i += 32) {
+        const int ixj = i ^ jj;
+        if (ixj > i) {
+          const bool up = (i & k2) == 0;
+          const K x = key[i], y = key[ixj];
+          if ((x > y) == up) {
+            key[i] = y;
+            key[ixj] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+}
+
+// One warp per 32-element tile.  PASS 1 counts the tile's cells (records);
+// PASS 2 writes the slot run indices, R_t, each record's cell (r_v * R_t + r_w)
+// and its matrix entry (CSR position of (v, w)).
+template <int NV, bool WRITE>
+__global__ void __launch_bounds__(kPatWarps * 32)
+    tile_cells_kernel(const int32_t* __restrict__ conn, int64_t n_elem, const int32_t* __restrict__ row_ptr,
+                      const int32_t* __restrict__ col_idx, int32_t* tile_nrec, const int32_t* __restrict__ tile_rec,
+                      uint32_t* run_word, uint16_t* tile_runs, uint16_t* rec_cell, int32_t* rec_entry, int32_t* flag) {
+  __shared__ uint64_t skey_s[kPatWarps][kTileCap];
+  __shared__ uint32_t ckey_s[kPatWarps][kCellCap];
+  __shared__ int32_t runv_s[kPatWarps][kTileCap];
+  __shared__ uint8_t runi_s[kPatWarps][kTileCap];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint64_t* skey = skey_s[warp];
+  uint32_t* ckey = ckey_s[warp];
+  int32_t* runv = runv_s[warp];
+  uint8_t* runi = runi_s[warp];
+  constexpr int NS = 32 * NV;                  // slots of a full tile
+  constexpr int PS = NS <= 64 ? 64 : 128;      // power of two >= NS (and >= 32)
+  constexpr int NC = 32 * NV * NV;             // contributions of a full tile
+  constexpr int PC = NC <= 256 ? 256 : 512;
+  const int64_t ntiles = (n_elem + 31) / 32;
+  const int64_t stride = int64_t(gridDim.x) * kPatWarps;
+  for (int64_t t = int64_t(blockIdx.x) * kPatWarps + warp; t < ntiles; t += stride) {
+    const int64_t e0 = t * 32;
+    const int ne = int(n_elem - e0 < 32 ? n_elem - e0 : 32);
+    const int ns = ne * NV;
+    // 1. slots sorted by (vertex, slot): runs and run index per slot
+    for (int i = lane; i < PS; i += 32) {
+      uint64_t k = ~0ull;
+      if (i < ns) k = (uint64_t(uint32_t(conn[e0 * NV + i])) << 16) | uint64_t(i);
+      skey[i] = k;
+    }
+    __syncwarp();
+    warp_bitonic(skey, PS, lane);
+    int nr = 0;
+    for (int r = 0; r < ns; r += 32) {
+      const int i = r + lane;
+      const bool head = i < ns && (i == 0 || (skey[i] >> 16) != (skey[i - 1] >> 16));
+      const uint32_t bal = __ballot_sync(0xffffffffu, head);
+      const uint32_t upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);  // lanes <= this one
+      const int run = nr + __popc(bal & upto) - 1;  // heads up to this position, minus one
+      if (head) runv[run] = int32_t(skey[i] >> 16);
+      if (i < ns) runi[int(skey[i] & 0xFFFF)] = uint8_t(run);
+      nr += __popc(bal);
+    }
+    __syncwarp();
+    // 2. cells of the tile's contributions, in (row run, column run) order; the
+    //    key keeps the element (low 6 bits) to tell whether the two half-tiles
+    //    (elements 0-15, 16-31) share a cell
+    const int ncell = ne * NV * NV;
+    int rep = 0;
+    for (int c = lane; c < PC; c += 32) {
+      uint32_t k = 0xFFFFFFFFu;
+      if (c < ncell) {
+        const int el = c / (NV * NV), ij = c % (NV * NV), i = ij / NV, j = ij % NV;
+        const int ri = runi[el * NV + i], rj = runi[el * NV + j];
+        if (i != j && ri == rj) rep = 1;  // an element repeats a vertex
+        k = (uint32_t(ri * nr + rj) << 6) | uint32_t(el);
+      }
+      ckey[c] = k;
+    }
+    if (__any_sync(0xffffffffu, rep) && lane == 0) atomicOr(flag, ASM_REPEATED_VERTEX);
+    __syncwarp();
+    warp_bitonic(ckey, PC, lane);
+    int nu = 0, shared = 0;
+    for (int r = 0; r < ncell; r += 32) {
+      const int i = r + lane;
+      const bool head = i < ncell && (i == 0 || (ckey[i] >> 6) != (ckey[i - 1] >> 6));
+      // within a cell the elements ascend: the halves meet where a lower-half
+      // element is followed by an upper-half one
+      if (i + 1 < ncell && (ckey[i] >> 6) == (ckey[i + 1] >> 6) && (ckey[i] & 63u) < 16u && (ckey[i + 1] & 63u) >= 16u)
+        shared = 1;
+      const uint32_t bal = __ballot_sync(0xffffffffu, head);
+      if constexpr (WRITE) {
+        if (head) {
+          const int32_t rec = tile_rec[t] + nu + __popc(bal & ((1u << lane) - 1u));
+          const uint32_t cell = ckey[i] >> 6;
+          const int32_t v = runv[cell / nr], w = runv[cell % nr];
+          int lo = row_ptr[v], hi = row_ptr[v + 1];  // position of w in row v
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col_idx[mid] < w)
+              lo = mid + 1;
+            else
+              hi = mid;
+          }
+          rec_cell[t * kCellCap + (rec - tile_rec[t])] = uint16_t(cell);  // the tile's 512-entry slot
+          rec_entry[rec] = lo;
+        }
+      }
+      nu += __popc(bal);
+    }
+    shared = __any_sync(0xffffffffu, shared);
+    if constexpr (!WRITE) {
+      if (lane == 0) tile_nrec[t] = nu;
+    } else {
+      uint32_t wd = 0;
+      if (lane < ne) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) wd |= uint32_t(runi[lane * NV + k]) << (8 * k);
+      }
+      run_word[t * 32 + lane] = wd;
+      if (lane == 0) tile_runs[t] = uint16_t(nr | (shared ? 0 : kHalvesDisjoint));
+    }
+    __syncwarp();  // the buffers are refilled for the next tile
+  }
+}
+
+// Step 1 of the scalar assembly: one warp per tile, pipelined over its tiles.
+// The next tile's element matrices arrive by 16-byte cp.async into the other
+// half of a double-buffered stage while this tile is summed.  Every lane
+// first writes its element's cell indices (cells[l][ij], shared memory); the
+// record cells of the dense tile are zeroed; then the contributions are added
+// element by element (each element's cells are distinct) -- two elements per
+// step, l and l + 16, when the tile's halves share no cell -- and the records
+// are read out in tile order.
+template <int NV>
+struct TilePlan {
+  static constexpr int NN = NV * NV;
+  static constexpr int SST = NV == 4 ? 16 : NN;                      // stage row (floats)
+  static constexpr size_t stage = size_t(32) * SST * 4;              // one tile of A
+  static constexpr size_t rcell = size_t(kCellCap) * 2;              // one tile's record cells
+  static constexpr size_t cells = size_t(32) * 17 * 4;               // u32 [32][17]: odd stride, no conflicts
+  static constexpr size_t dense = size_t(kTileRuns) * kTileRuns * 4;
+  static constexpr size_t per_warp = 2 * stage + 2 * rcell + cells + dense;
+  static constexpr size_t smem = kPatWarps * per_warp;
+};
+
+template <int NV>
+__device__ __forceinline__ void copy_tile_A(const float* A, int64_t n_elem, int64_t t, int lane, float* dst,
+                                            int vec) {
+  constexpr int NN = NV * NV;
+  const int64_t e0 = t * 32;
+  if (e0 >= n_elem) return;
+  const int ne = int(n_elem - e0 < 32 ? n_elem - e0 : 32);
+  const float* src = A + e0 * NN;
+  if constexpr (NV == 4) {
+    if (vec) {  // 64-byte rows of a 16-byte-aligned A: contiguous 16-byte chunks
+      for (int q = lane; q < ne * 4; q += 32) cp_async<16>(dst + 4 * q, src + 4 * q);
+      return;
+    }
+  }
+  for (int q = lane; q < ne * NN; q += 32) cp_async<4>(dst + q, src + q);
+}
+
+// The first rn record cells of tile t (16-byte chunks of its 512-entry slot).
+__device__ __forceinline__ void copy_tile_cells(const uint16_t* rec_cell, int64_t t, int rn, int lane, uint16_t* dst) {
+  const uint16_t* src = rec_cell + t * kCellCap;
+  for (int q = lane; q < (rn + 7) / 8; q += 32) cp_async<16>(dst + 8 * q, src + 8 * q);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kPatWarps * 32)
+    tile_assemble_kernel(const float* __restrict__ A, int64_t n_elem, const uint32_t* __restrict__ run_word,
+                         const uint16_t* __restrict__ tile_runs, const int32_t* __restrict__ tile_rec,
+                         const uint16_t* __restrict__ rec_cell, float* __restrict__ records, int vec) {
+  using TP = TilePlan<NV>;
+  constexpr int NN = TP::NN, SST = TP::SST;
+  extern __shared__ __align__(128) unsigned char tsm[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned char* wb = tsm + size_t(warp) * TP::per_warp;
+  float* stage = reinterpret_cast<float*>(wb);                                   // [2][32][SST]
+  uint16_t* rcs = reinterpret_cast<uint16_t*>(wb + 2 * TP::stage);               // [2][512]
+  uint32_t* cells = reinterpret_cast<uint32_t*>(wb + 2 * TP::stage + 2 * TP::rcell);
+  float* dense = reinterpret_cast<float*>(wb + 2 * TP::stage + 2 * TP::rcell + TP::cells);
+  const int64_t ntiles = (n_elem + 31) / 32;
+  const int64_t S = int64_t(gridDim.x) * kPatWarps;
+  int64_t t = int64_t(blockIdx.x) * kPatWarps + warp;
+  if (t >= ntiles) return;
+  // pipeline: tile metadata two tiles ahead, A / record cells / runs one tile ahead
+  auto meta = [&](int64_t tt, int& tr, int32_t& rb, int32_t& rn) {
+    tr = 0, rb = 0, rn = 0;
+    if (tt < ntiles) {
+      tr = __ldg(tile_runs + tt);
+      rb = __ldg(tile_rec + tt);
+      rn = __ldg(tile_rec + tt + 1) - rb;
+    }
+  };
+  int trc, trn, tr2;
+  int32_t rbc, rnc, rbn, rnn, rb2, rn2;
+  meta(t, trc, rbc, rnc);
+  meta(t + S, trn, rbn, rnn);
+  copy_tile_A<NV>(A, n_elem, t, lane, stage, vec);
+  copy_tile_cells(rec_cell, t, rnc, lane, rcs);
+  cp_async_commit();
+  uint32_t rwc = __ldg(run_word + t * 32 + lane);
+  for (int it = 0; t < ntiles; ++it, t += S) {
+    const int sc = it & 1;
+    const int64_t tn = t + S;
+    meta(tn + S, tr2, rb2, rn2);
+    uint32_t rwn = 0;
+    if (tn < ntiles) {
+      copy_tile_A<NV>(A, n_elem, tn, lane, stage + (sc ^ 1) * 32 * SST, vec);
+      copy_tile_cells(rec_cell, tn, rnn, lane, rcs + (sc ^ 1) * kCellCap);
+      rwn = __ldg(run_word + tn * 32 + lane);
+    }
+    cp_async_commit();
+    const int64_t e0 = t * 32;
+    const int ne = int(n_elem - e0 < 32 ? n_elem - e0 : 32);
+    const int nr = trc & 0xFF;
+    const bool halves = (trc & kHalvesDisjoint) && ne == 32;
+    const float* st = stage + sc * 32 * SST;
+    const uint16_t* rc = rcs + sc * kCellCap;
+    if (nr <= kTileRuns && lane < ne) {
+#pragma unroll
+      for (int ij = 0; ij < NN; ++ij)
+        cells[lane * 17 + ij] = ((rwc >> (8 * (ij / NV))) & 0xFFu) * uint32_t(nr) + ((rwc >> (8 * (ij % NV))) & 0xFFu);
+    }
+    cp_async_wait<1>();
+    __syncwarp();  // this tile's A and record cells (copied by every lane) and the cell indices are in place
+    if (nr <= kTileRuns) {
+      for (int r = lane; r < rnc; r += 32) dense[rc[r]] = 0.f;
+      __syncwarp();
+      if (halves) {
+        const int h = lane >> 4, ij = lane & 15;
+        for (int l0 = 0; l0 < 16; ++l0) {
+          const int l = l0 + 16 * h;
+          if (ij < NN) dense[cells[l * 17 + ij]] += st[l * SST + ij];
+          __syncwarp();
+        }
+      } else {
+        for (int l = 0; l < ne; ++l) {  // element order
+          if (lane < NN) dense[cells[l * 17 + lane]] += st[l * SST + lane];
+          __syncwarp();
+        }
+      }
+      for (int r = lane; r < rnc; r += 32) records[rbc + r] = dense[rc[r]];  // tile order
+    } else {
+      // more distinct vertices than the dense tile holds: scan the tile per record
+      for (int r0 = 0; r0 < rnc; r0 += 32) {  // warp-uniform, so the shuffles see every lane
+        const int r = r0 + lane;
+        const bool live = r < rnc;
+        const int cell = live ? int(rc[r]) : -1;
+        float acc = 0.f;
+        for (int l = 0; l < ne; ++l) {
+          const uint32_t w = __shfl_sync(0xffffffffu, rwc, l);
+#pragma unroll
+          for (int ij = 0; ij < NN; ++ij)
+            if (int((w >> (8 * (ij / NV))) & 0xFFu) * nr + int((w >> (8 * (ij % NV))) & 0xFFu) == cell)
+              acc += st[l * SST + ij];
+        }
+        if (live) records[rbc + r] = acc;
+      }
+    }
+    __syncwarp();  // the stage, record cells, cells and dense tile are refilled
+    trc = trn, rbc = rbn, rnc = rnn, rwc = rwn;
+    trn = tr2, rbn = rb2, rnn = rn2;
+  }
+  cp_async_wait<0>();
+}
+
+// Step 2: val[k] = sum of the records of entry k (rec_list[eoff[k] .. eoff[k+1]),
+// increasing record index = tile order).  The records of neighbouring entries
+// lie in the same few tiles, so the gathers mostly hit the caches; four
+// record indices, then four records, are loaded before they are added.
+__global__ void entry_reduce_kernel(const int32_t* __restrict__ eoff, const int32_t* __restrict__ nnz_ptr,
+                                    const int32_t* __restrict__ rec_list, const float* __restrict__ records,
+                                    float* __restrict__ val) {
+  const int64_t nnz = *nnz_ptr;  // row_ptr[n_vert]
+  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < nnz; k += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t b = __ldg(eoff + k), e = __ldg(eoff + k + 1);
+    float acc = 0.f;
+    for (int32_t m0 = b; m0 < e; m0 += 4) {
+      int32_t idx[4];
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) idx[u] = m0 + u < e ? __ldg(rec_list + m0 + u) : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) x[u] = m0 + u < e ? __ldg(records + idx[u]) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (m0 + u < e) acc += x[u];
+    }
+    val[k] = acc;
+  }
+}
+
 struct AsmLayout {
   int32_t *inc_off, *inc, *row_ptr, *col_idx, *cursor, *partials, *flag;
   uint8_t* colpos;
+  // tile records (scalar forms)
+  uint32_t* run_word;
+  uint16_t* tile_runs;
+  int32_t *tile_rec, *rec_entry, *rec_list, *eoff, *cursor2, *partials2;
+  uint16_t* rec_cell;
+  float* records;
+  int64_t n_tiles, rec_cap;
   size_t bytes;
 };
 
@@ -232,6 +559,9 @@ size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 AsmLayout asm_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
   const int64_t nv = dim + 1;
+  const int64_t T = (n_elem + 31) / 32;
+  const int64_t cap = n_elem * nv * nv;  // contributions: bounds the entries and the records
+  const int64_t big = (T > cap ? T : cap) + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t o = off;
@@ -242,10 +572,20 @@ AsmLayout asm_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
   const size_t o_inc = take(sizeof(int32_t) * size_t(n_elem * nv));
   const size_t o_colpos = take(size_t(n_elem * nv * nv));
   const size_t o_row_ptr = take(sizeof(int32_t) * size_t(n_vert + 1));
-  const size_t o_col = take(sizeof(int32_t) * size_t(n_elem * nv * nv));  // capacity: every entry distinct
+  const size_t o_col = take(sizeof(int32_t) * size_t(cap));  // capacity: every entry distinct
   const size_t o_cursor = take(sizeof(int32_t) * size_t(n_vert + 1));
   const size_t o_part = take(sizeof(int32_t) * scan_partials_count(n_vert + 1));
   const size_t o_flag = take(sizeof(int32_t) * 4);
+  const size_t o_run = take(sizeof(uint32_t) * size_t(T * 32));
+  const size_t o_truns = take(sizeof(uint16_t) * size_t(T));
+  const size_t o_trec = take(sizeof(int32_t) * size_t(T + 1));
+  const size_t o_cell = take(sizeof(uint16_t) * size_t(T * kCellCap));  // 512 cells per tile, tile-strided
+  const size_t o_rentry = take(sizeof(int32_t) * size_t(cap));
+  const size_t o_rlist = take(sizeof(int32_t) * size_t(cap));
+  const size_t o_eoff = take(sizeof(int32_t) * size_t(cap + 1));
+  const size_t o_records = take(sizeof(float) * size_t(cap));
+  const size_t o_cursor2 = take(sizeof(int32_t) * size_t(big));
+  const size_t o_part2 = take(sizeof(int32_t) * scan_partials_count(big));
   AsmLayout L{};
   char* b = static_cast<char*>(base);
   L.inc_off = reinterpret_cast<int32_t*>(b + o_inc_off);
@@ -256,8 +596,25 @@ AsmLayout asm_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
   L.cursor = reinterpret_cast<int32_t*>(b + o_cursor);
   L.partials = reinterpret_cast<int32_t*>(b + o_part);
   L.flag = reinterpret_cast<int32_t*>(b + o_flag);
+  L.run_word = reinterpret_cast<uint32_t*>(b + o_run);
+  L.tile_runs = reinterpret_cast<uint16_t*>(b + o_truns);
+  L.tile_rec = reinterpret_cast<int32_t*>(b + o_trec);
+  L.rec_cell = reinterpret_cast<uint16_t*>(b + o_cell);
+  L.rec_entry = reinterpret_cast<int32_t*>(b + o_rentry);
+  L.rec_list = reinterpret_cast<int32_t*>(b + o_rlist);
+  L.eoff = reinterpret_cast<int32_t*>(b + o_eoff);
+  L.records = reinterpret_cast<float*>(b + o_records);
+  L.cursor2 = reinterpret_cast<int32_t*>(b + o_cursor2);
+  L.partials2 = reinterpret_cast<int32_t*>(b + o_part2);
+  L.n_tiles = T;
+  L.rec_cap = cap;
   L.bytes = off;
   return L;
+}
+
+__global__ void fill_neg_kernel(int32_t* p, int64_t n) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = -1;
 }
 
 unsigned grid_of(int64_t n, int per_block) {
@@ -276,6 +633,36 @@ cudaError_t launch_pattern(int dim, const int32_t* conn, int64_t n_vert, const A
   else
     row_pattern_kernel<4, WRITE><<<g, kPatWarps * 32, 0, st>>>(conn, L.inc_off, L.inc, n_vert, L.cursor, L.row_ptr,
                                                                 L.col_idx, L.colpos, L.flag);
+  return cudaGetLastError();
+}
+
+template <bool WRITE>
+cudaError_t launch_tile_cells(int dim, const int32_t* conn, int64_t n_elem, const AsmLayout& L, cudaStream_t st) {
+  const unsigned g = grid_of(L.n_tiles, kPatWarps);
+  if (dim == 2)
+    tile_cells_kernel<3, WRITE><<<g, kPatWarps * 32, 0, st>>>(conn, n_elem, L.row_ptr, L.col_idx, L.cursor2,
+                                                               L.tile_rec, L.run_word, L.tile_runs, L.rec_cell,
+                                                               L.rec_entry, L.flag);
+  else
+    tile_cells_kernel<4, WRITE><<<g, kPatWarps * 32, 0, st>>>(conn, n_elem, L.row_ptr, L.col_idx, L.cursor2,
+                                                               L.tile_rec, L.run_word, L.tile_runs, L.rec_cell,
+                                                               L.rec_entry, L.flag);
+  return cudaGetLastError();
+}
+
+template <int NV>
+cudaError_t launch_tile_assemble_t(const AsmLayout& L, const float* A, int64_t n_elem, int64_t n_vert, float* val,
+                                   cudaStream_t st) {
+  const size_t smem = TilePlan<NV>::smem;
+  auto kern = tile_assemble_kernel<NV>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
+  kern<<<pipeline_grid(reinterpret_cast<const void*>(kern), kPatWarps, smem, n_elem, 0), kPatWarps * 32, smem, st>>>(
+      A, n_elem, L.run_word, L.tile_runs, L.tile_rec, L.rec_cell, L.records,
+      int(reinterpret_cast<uintptr_t>(A) % 16 == 0));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  entry_reduce_kernel<<<grid_of(L.rec_cap, 256), 256, 0, st>>>(L.eoff, L.row_ptr + n_vert, L.rec_list, L.records,
+                                                                val);
   return cudaGetLastError();
 }
 
@@ -338,7 +725,7 @@ fem_status fem_assembly_workspace_size(const fem_mesh* mesh, int32_t form, size_
 }
 
 fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size_t ws_bytes, int64_t* nnz,
-                              void* stream) {
+                              int64_t* n_records, void* stream) {
   fem_status s = asm_check(mesh, form);
   if (s != FEM_OK) return s;
   const fem::AsmLayout L = fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, ws);
@@ -360,10 +747,25 @@ fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size
   if (e == cudaSuccess && V > 0) e = fem::launch_pattern<false>(mesh->dim, mesh->conn, V, L, st);
   if (e == cudaSuccess) e = fem::launch_exclusive_scan(L.cursor, V, L.partials, L.row_ptr, st);
   if (e == cudaSuccess && V > 0) e = fem::launch_pattern<true>(mesh->dim, mesh->conn, V, L, st);
-  int32_t host[2] = {0, 0};
+  int32_t host[2] = {0, 0}, nrec = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&host[0], L.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&host[1], L.row_ptr + V, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // tile records of the scalar forms: cells per 32-element tile, entry-major records
+  if (e == cudaSuccess && host[0] == 0 && asm_block(form, mesh->dim) == 1 && mesh->n_elem > 0) {
+    e = fem::launch_tile_cells<false>(mesh->dim, mesh->conn, mesh->n_elem, L, st);
+    if (e == cudaSuccess) e = fem::launch_exclusive_scan(L.cursor2, L.n_tiles, L.partials2, L.tile_rec, st);
+    if (e == cudaSuccess) {
+      fem::fill_neg_kernel<<<fem::grid_of(L.rec_cap, 256), 256, 0, st>>>(L.rec_entry, L.rec_cap);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = fem::launch_tile_cells<true>(mesh->dim, mesh->conn, mesh->n_elem, L, st);
+    if (e == cudaSuccess)
+      e = fem::launch_key_csr(L.rec_entry, L.rec_cap, host[1], L.eoff, L.rec_list, L.cursor2, L.partials2, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&host[0], L.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nrec, L.tile_rec + L.n_tiles, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
   if (e != cudaSuccess) {
     fem::set_last_error("fem_assembly_build: %s", cudaGetErrorString(e));
     return FEM_ERR_CUDA;
@@ -371,7 +773,9 @@ fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size
   if (host[0] & fem::ASM_BAD_VERTEX) return asm_fail(FEM_ERR_ARG, "a connectivity entry is outside [0, n_vert)");
   if (host[0] & fem::ASM_ROW_TOO_LONG)
     return asm_fail(FEM_ERR_UNSUPPORTED, "a vertex has more than 128 incident elements or 255 neighbours");
+  if (host[0] & fem::ASM_REPEATED_VERTEX) return asm_fail(FEM_ERR_UNSUPPORTED, "an element repeats a vertex");
   if (nnz) *nnz = host[1];
+  if (n_records) *n_records = nrec;
   return FEM_OK;
 }
 
@@ -399,7 +803,10 @@ fem_status fem_assemble(const fem_mesh* mesh, int32_t form, const float* A, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int B = asm_block(form, mesh->dim);
   cudaError_t e;
-  if (mesh->dim == 2)
+  if (B == 1 && mesh->n_elem > 0)  // scalar forms: tile records, then the per-entry sums
+    e = mesh->dim == 2 ? fem::launch_tile_assemble_t<3>(L, A, mesh->n_elem, mesh->n_vert, values, st)
+                       : fem::launch_tile_assemble_t<4>(L, A, mesh->n_elem, mesh->n_vert, values, st);
+  else if (mesh->dim == 2)
     e = B == 1 ? fem::launch_assemble_t<3, 1>(L, A, mesh->n_vert, values, st)
                : fem::launch_assemble_t<3, 2>(L, A, mesh->n_vert, values, st);
   else

@@ -1,9 +1,11 @@
 """GPU parity of the global assembly (-m gpu).
 
 * The pattern (row_ptr, col_idx) equals the oracle's CSR structure exactly.
-* The values equal, bit for bit, a float32 sum of the same GPU element matrices
-  in increasing element order (numpy's unbuffered np.add.at in element-major
-  order): the summation order the library defines.
+* The values equal, bit for bit, float32 sums of the same GPU element matrices
+  in the order the library defines (numpy's unbuffered np.add.at): for the
+  scalar forms, per 32-element tile the contributions in element order, then
+  those tile sums in tile order; for P1 elasticity's blocks, all contributions
+  in element order.
 * Against the FP64 oracle (oracle element matrices, assembled by the oracle):
   per row v, max |a_gpu - a_ref| <= 1e-5 * sum over the elements e at v of
   max |A_e| -- the element tolerance carried through the sum (a row of a
@@ -84,7 +86,17 @@ def test_assembly_bitwise_and_oracle(gfem, orc, dim, form):
                 vi, vj = g[e, I] // b, g[e, J] // b
                 slot[e, I, J] = pos[(vi, vj)] * b * b + (g[e, I] % b) * b + g[e, J] % b
     ref32 = np.zeros(asm.nnz * b * b, np.float32)
-    np.add.at(ref32, slot.ravel(), Ah.reshape(-1))
+    if b == 1:
+        ent = slot.reshape(-1)
+        tile = np.repeat(np.arange(mesh.n_elem) // 32, n * n)
+        keys, inv = np.unique(tile * ref32.size + ent, return_inverse=True)
+        part = np.zeros(keys.size, np.float32)
+        np.add.at(part, inv, Ah.reshape(-1))              # per (tile, entry), element order
+        np.add.at(ref32, keys % ref32.size, part)          # keys ascend: tile order per entry
+        assert asm.n_records == keys.size                  # one record per distinct (tile, entry)
+    else:
+        assert asm.n_records == 0
+        np.add.at(ref32, slot.ravel(), Ah.reshape(-1))
     got = vals.cpu().numpy().reshape(-1)
     assert np.array_equal(got, ref32)
     # FP64 oracle, per row
