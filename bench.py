@@ -44,15 +44,24 @@ KERNEL_SOURCES = {
                                                    "fem_forms.cuh", "fem_pipe.cuh", "fem_internal.h",
                                                    "fem_geometry.cu"),
     "vertex_reduce_kernel<3>": ("fem_incidence.cu", "fem_internal.h"),
+    "fem_assemble<LAPLACE_P1>": ("fem_assembly.cu", "fem_pipe.cuh", "fem_internal.h"),
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
-NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1281.5e6, "src": "5f653bc691601701"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 983.0e6, "src": "a0fce85e3765de45"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.8e6, "src": "c0c9bd793c40989a"},
+NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1281.4e6, "src": "f65a6a9b6a41e47b"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 983.0e6, "src": "34ee1eacc17e71c8"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.7e6, "src": "0e7a977875b65b8a"},
+    # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
+    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2394.4e6, "src": "481d084af2a808db"},
 }
+
+
+def ncu_traffic(name: str):
+    """Captured DRAM bytes per launch of `name`, or None once its sources changed."""
+    tr = NCU_TRAFFIC.get(name)
+    return tr["bytes_per_launch"] if tr and tr.get("src") == kernel_src_hash(name) else None
 
 
 def kernel_src_hash(name: str) -> str:
@@ -285,8 +294,7 @@ def run_ours(args):
     kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
              "reduce": "vertex_reduce_kernel<3>"}
     h = {k: kernel_src_hash(v) for k, v in kname.items()}
-    tr = NCU_TRAFFIC.get(kname[dom])  # valid only for the sources it was captured with
-    traffic = tr["bytes_per_launch"] if tr and tr.get("src") == h[dom] else None
+    traffic = ncu_traffic(kname[dom])  # valid only for the sources it was captured with
     ach = byts[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth",
@@ -748,15 +756,16 @@ def run_assemble(args):
            "config": {"workload": f"global CSR assembly of the P1 Laplacian element matrices, {args.mesh_n}^3 "
                                   f"Kuhn cube with 5% slivers ({E:,} tets, {V:,} vertices, {nnz:,} nonzeros, "
                                   f"{R2:,} tile records), "
-                                  "deterministic (element order)",
-                      "elements": E, "nnz": nnz, "l2": "no flush: 1.4 GB moved per step"},
-           "roofline": {"bound": "hbm", "kernel": "tile_assemble_kernel<4> + entry_reduce_kernel", "achieved": gbs,
-                        "peak": peak,
+                                  "deterministic (per 32-element tile in element order, then in tile order)",
+                      "elements": E, "nnz": nnz, "l2": f"no flush: {byts / 1e9:.1f} GB moved per step"},
+           "roofline": {"bound": "hbm", "kernel": "fem_assemble<LAPLACE_P1> (tile pass + entry pass, one call)",
+                        "achieved": gbs, "peak": peak,
                         "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
-                        "traffic": None, "algorithmic_bytes": byts},
+                        "traffic": ncu_traffic("fem_assemble<LAPLACE_P1>"), "algorithmic_bytes": byts},
            "forward_ms": fwd_ms, "build_ms": build_ms, "max_row_err_vs_fp64": err,
            "error_metric": "per row v: max |a - a_fp64| / (sum over the elements at v of max |A_e|)",
-           "error_sample": f"all entries of {len(rows):,} random rows", "gpu_launches": args.steps}
+           "error_sample": f"all entries of {len(rows):,} random rows",
+           "gpu_launches": 2 * args.steps}  # tile pass + entry pass per call
     print(json.dumps(out), flush=True)
 
 

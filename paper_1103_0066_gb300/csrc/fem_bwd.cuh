@@ -102,6 +102,16 @@ __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, 
   if constexpr (PL::VEC) {
     if (p.vec_dA) {
       constexpr int Q = NN / 4;
+      if constexpr (32 % Q == 0) {
+        if (cnt == 32) {  // full tile: chunk lane + 32 i is chunk lane % Q of row lane / Q + i (32 / Q)
+          constexpr int RPI = 32 / Q;
+          float* d = dslot + (lane / Q) * PL::DST + 4 * (lane % Q);
+          const float* s = src + 4 * lane;
+#pragma unroll
+          for (int i = 0; i < Q; ++i) cp_async<16>(d + i * RPI * PL::DST, s + 128 * i);
+          return;
+        }
+      }
       const int nq = cnt * Q;
       for (int q = lane; q < nq; q += 32) {
         const int el = q / Q;
