@@ -345,6 +345,7 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     L.n_elem = mesh->n_elem;
     L.n_vert = mesh->n_vert;
     L.dev_err = o->dev_err;
+    L.warps = o->warps_per_cta;
     L.ctas_per_sm = o->ctas_per_sm;
     L.stream = st;
     e = fem::launch_bwd_elem(L);

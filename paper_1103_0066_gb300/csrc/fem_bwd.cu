@@ -24,12 +24,14 @@ static cudaError_t launch_bwd_t(const BwdLaunch& L) {
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_dA = reinterpret_cast<uintptr_t>(L.dA) % 16 == 0;
   auto kern = fem_bwd_elem_kernel<D, FORM, JAC, ATOMIC>;
-  const size_t smem = PL::smem;
+  constexpr int max_warps = BwdShape<D, FORM, JAC>::threads / 32;  // the kernel's launch bounds
+  const int want = L.warps > 0 ? L.warps : max_warps;
+  const int warps = clamp_warps(want < max_warps ? want : max_warps, PL::per_warp);
+  const size_t smem = size_t(warps) * PL::per_warp;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
-  const unsigned grid =
-      pipeline_grid(reinterpret_cast<const void*>(kern), PL::WARPS, smem, L.n_elem, L.ctas_per_sm);
-  kern<<<grid, kTileElems, smem, L.stream>>>(p);
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), warps, smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, warps * 32, smem, L.stream>>>(p);
   return cudaGetLastError();
 }
 

@@ -82,12 +82,23 @@ struct BwdPlan {
   static constexpr int NV = D + 1;
   static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
   static constexpr int XP = D == 3 ? 4 : 2;  // padded floats per staged slot (one vector store)
-  static constexpr int WARPS = kTileElems / 32;
   static constexpr size_t da_slot = align_up(size_t(32) * DST * 4, 128);    // one tile of dA rows
   static constexpr size_t da_bytes = 2 * da_slot;                           // per warp, double buffered
   static constexpr size_t xs_bytes = align_up(size_t(NSW) * XP * 4, 128);   // per warp
   static constexpr size_t per_warp = da_bytes + xs_bytes;
-  static constexpr size_t smem = WARPS * per_warp;
+};
+
+// CTA shape of the adjoint element kernel.  The kernel has no CTA-wide
+// barrier, so the CTA size only sets how finely the register file is shared
+// out.  The compensated 3D P1 Laplacian runs one-warp CTAs with at least 24
+// resident per SM, which holds it to 80 registers without spills: 25 warps
+// per SM fit, against 20 at its natural 93 registers in 4-warp CTAs.  The
+// other instantiations keep 4-warp CTAs and the compiler's register choice.
+template <int D, int FORM, int JAC>
+struct BwdShape {
+  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && JAC == JAC_COMP);
+  static constexpr int threads = tight ? 32 : kTileElems;
+  static constexpr int min_ctas = tight ? 24 : 1;
 };
 
 // Asynchronous copy of a tile's contiguous dA into the padded stage slot.
@@ -360,17 +371,19 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
 }
 
 template <int D, int FORM, int JAC, bool ATOMIC>
-__global__ void __launch_bounds__(kTileElems) fem_bwd_elem_kernel(BwdParams p) {
+__global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, FORM, JAC>::min_ctas)
+    fem_bwd_elem_kernel(BwdParams p) {
   using PL = BwdPlan<D, FORM>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   unsigned char* wbase = smem_raw + size_t(warp) * PL::per_warp;
   float* dslots = reinterpret_cast<float*>(wbase);               // [2][32][DST]
   float* xs = reinterpret_cast<float*>(wbase + PL::da_bytes);    // [32 (d+1)][XP]
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
   const int64_t ntiles = (p.n_elem + 31) / 32;
-  const int64_t S = int64_t(gridDim.x) * PL::WARPS;  // warp-tile stride
-  int64_t t = int64_t(blockIdx.x) * PL::WARPS + warp;
+  const int64_t S = int64_t(gridDim.x) * nwarps;  // warp-tile stride
+  int64_t t = int64_t(blockIdx.x) * nwarps + warp;
   if (t >= ntiles) return;  // warp-uniform: the kernel has no CTA-wide barrier
   int err = 0;
   int v1[D + 1], v2[D + 1], vc[D + 1];

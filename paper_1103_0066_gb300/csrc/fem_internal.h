@@ -56,7 +56,7 @@ struct BwdLaunch {
   float* records;
   int64_t n_elem, n_vert;
   int32_t* dev_err;
-  int ctas_per_sm;
+  int warps, ctas_per_sm;  // warps <= 0: the default
   cudaStream_t stream;
 };
 
