@@ -25,7 +25,7 @@ from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENER
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM)
 
-__all__ = ["Mesh", "Batch", "Assembly", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
+__all__ = ["Mesh", "Batch", "Assembly", "HostStep", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
            "BATCH_PER_ITEM", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
            "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "integrate_fwd_iso", "JAC_AUTO",
@@ -210,6 +210,89 @@ def adjoint_reduce(coords, conn, ws: Workspace, dcoords, stream=None):
     m = _mesh_struct(coords, conn)
     nat.fem_adjoint_reduce(m, ws.buf.data_ptr(), ws.bytes, dcoords.data_ptr(), _stream_ptr(stream))
     return dcoords
+
+
+class HostStep:
+    """Forward and adjoint of one mesh whose inputs and outputs live in pinned
+    host memory, with the host <-> device copies overlapped with the kernels.
+
+    run() copies coords, conn and dA in, integrates A = G:K (Eq. 6) and the
+    deterministic adjoint, and copies A and dcoords out.  The elements go in
+    slices of `chunk` elements:
+
+    * a copy-in stream sends the coordinates, then each slice's connectivity
+      and dA;
+    * the caller's stream integrates each slice's A as soon as its
+      connectivity has arrived (elements are independent);
+    * a copy-out stream returns each slice's A as soon as it is written.
+
+    The adjoint needs every slice's dA, so it and the reduction run after the
+    last slice, then dcoords goes out.  Copies in the two directions and the
+    kernels overlap; the results equal the device path's bit for bit.  The
+    caller's stream waits for the copies out, so an event recorded on it after
+    run() marks the step's end."""
+
+    def __init__(self, n_vert, n_elem, dim=3, form=LAPLACE_P1, chunk=1 << 20, device="cuda"):
+        if form not in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1):
+            raise ValueError("HostStep takes LAPLACE_P1, LAPLACE_P2 or ELASTIC_P1")
+        dev = torch.device(device)
+        n, _, _ = form_info(form, dim)
+        self.form, self.dim, self.n = form, dim, n
+        self.chunk = max(32, (int(chunk) + 31) // 32 * 32)
+        self.coords = torch.empty((n_vert, dim), dtype=torch.float32, device=dev)
+        self.conn = torch.empty((n_elem, dim + 1), dtype=torch.int32, device=dev)
+        self.dA = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
+        self.A = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
+        self.dcoords = torch.empty((n_vert, dim), dtype=torch.float32, device=dev)
+        self.copy_in = torch.cuda.Stream(dev)
+        self.copy_out = torch.cuda.Stream(dev)
+        self.ws = None  # built on the first run: it depends on the connectivity
+
+    @staticmethod
+    def _check(t, like, name):
+        if t.is_cuda or not t.is_pinned() or t.shape != like.shape or t.dtype != like.dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous pinned host tensor {tuple(like.shape)} {like.dtype}")
+
+    def run(self, coords_h, conn_h, dA_h, A_h, dcoords_h, rebuild=False):
+        """One step; rebuild=True rebuilds the adjoint's incidence (new connectivity)."""
+        for t, like, name in ((coords_h, self.coords, "coords"), (conn_h, self.conn, "conn"),
+                              (dA_h, self.dA, "dA"), (A_h, self.A, "A"), (dcoords_h, self.dcoords, "dcoords")):
+            self._check(t, like, name)
+        main = torch.cuda.current_stream(self.coords.device)
+        E, C = self.conn.shape[0], self.chunk
+        self.copy_in.wait_stream(main)  # the previous step no longer reads the device inputs
+        with torch.cuda.stream(self.copy_in):
+            self.coords.copy_(coords_h, non_blocking=True)
+        slices = [(e0, min(E, e0 + C)) for e0 in range(0, E, C)]
+        arrived, written = [], []
+        for e0, e1 in slices:
+            with torch.cuda.stream(self.copy_in):
+                self.conn[e0:e1].copy_(conn_h[e0:e1], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.copy_in)
+                self.dA[e0:e1].copy_(dA_h[e0:e1], non_blocking=True)
+            arrived.append(ev)
+        if self.ws is None or rebuild:
+            main.wait_stream(self.copy_in)
+            self.ws = Workspace(self.coords, self.conn, self.form, main)
+        for (e0, e1), ev in zip(slices, arrived):
+            main.wait_event(ev)
+            integrate_fwd(self.coords, self.conn[e0:e1], self.form, out=self.A[e0:e1], stream=main)
+            done = torch.cuda.Event()
+            done.record(main)
+            written.append(done)
+        for (e0, e1), done in zip(slices, written):
+            self.copy_out.wait_event(done)
+            with torch.cuda.stream(self.copy_out):
+                A_h[e0:e1].copy_(self.A[e0:e1], non_blocking=True)
+        main.wait_stream(self.copy_in)  # every dA slice is in
+        integrate_bwd(self.coords, self.conn, self.form, self.dA, ws=self.ws, need_dcoef=False,
+                      dcoords=self.dcoords, stream=main)
+        self.copy_out.wait_stream(main)
+        with torch.cuda.stream(self.copy_out):
+            dcoords_h.copy_(self.dcoords, non_blocking=True)
+        main.wait_stream(self.copy_out)
+        return A_h, dcoords_h
 
 
 class _IntegrateFn(torch.autograd.Function):

@@ -183,7 +183,7 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   L.n_elem = mesh->n_elem;
   L.n_vert = mesh->n_vert;
   L.dev_err = o->dev_err;
-  L.warps = o->warps_per_cta ? o->warps_per_cta : 4;
+  L.warps = o->warps_per_cta;  // 0: the kernel's default
   L.ctas_per_sm = o->ctas_per_sm;
   L.stream = static_cast<cudaStream_t>(stream);
   cudaError_t e;

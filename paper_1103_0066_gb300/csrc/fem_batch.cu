@@ -603,7 +603,7 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
       L.n_elem = M.n_elem;
       L.n_vert = M.n_vert;
       L.dev_err = &b->d_ctr->err;
-      L.warps = 4;
+      L.warps = 0;  // the kernel's default
       L.stream = st;
       e = L.dim == 2 ? fem::launch_fwd_d2(L)
                      : (it.form == FEM_ELASTIC_P1 ? fem::launch_fwd_d3_ela(L) : fem::launch_fwd_d3_lap(L));

@@ -45,6 +45,22 @@ constexpr int stage_stride() {
 }
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// CTA shape of the forward kernel.  Warps never wait for one another, so the
+// CTA size only sets how finely the register file is shared out.  The
+// compensated 3D P1 Laplacian in FP32 runs one-warp CTAs with at least 24
+// resident per SM, which holds it to 80 registers without spills (25 warps per
+// SM against 20 at its natural 90 registers in 4-warp CTAs).  The other
+// instantiations take up to 16 warps per CTA (4 by default) and the
+// compiler's register choice.
+template <int D, int FORM, int JAC, class CT, class OT>
+struct FwdShape {
+  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && JAC == JAC_COMP && sizeof(CT) == 4 &&
+                                 sizeof(OT) == 4);
+  static constexpr int threads = tight ? 32 : 512;
+  static constexpr int min_ctas = tight ? 24 : 1;
+  static constexpr int default_warps = tight ? 1 : 4;
+};
+
 // Shared-memory plan of one warp.
 template <int D, int FORM, class CT, class OT>
 struct FwdPlan {
@@ -308,7 +324,8 @@ __device__ __forceinline__ void fwd_step(const FwdParams<CT, OT>& p, int64_t t, 
 }
 
 template <int D, int FORM, int JAC, class CT, class OT, bool TMA>
-__global__ void __launch_bounds__(512) fem_fwd_kernel(FwdParams<CT, OT> p, const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(FwdShape<D, FORM, JAC, CT, OT>::threads, FwdShape<D, FORM, JAC, CT, OT>::min_ctas)
+    fem_fwd_kernel(FwdParams<CT, OT> p, const __grid_constant__ CUtensorMap tmap) {
   using PL = FwdPlan<D, FORM, CT, OT>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -367,8 +384,10 @@ cudaError_t launch_fwd_t(const FwdLaunch& L) {
       kern = fem_fwd_kernel<D, FORM, JAC, CT, OT, true>;
     }
   }
+  using SH = FwdShape<D, FORM, JAC, CT, OT>;
   const size_t per_warp = tma ? PL::tma_per_warp : PL::per_warp;
-  const int warps = clamp_warps(L.warps, per_warp);
+  const int want = L.warps > 0 ? L.warps : SH::default_warps;
+  const int warps = clamp_warps(want < SH::threads / 32 ? want : SH::threads / 32, per_warp);
   const size_t smem = size_t(warps) * per_warp + (tma ? 1024 : 0);
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
