@@ -46,18 +46,22 @@ constexpr int stage_stride() {
 constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // CTA shape of the forward kernel.  Warps never wait for one another, so the
-// CTA size only sets how finely the register file is shared out.  The
-// compensated 3D P1 Laplacian in FP32 runs one-warp CTAs with at least 24
-// resident per SM, which holds it to 80 registers without spills (25 warps per
-// SM against 20 at its natural 90 registers in 4-warp CTAs).  The other
-// instantiations take up to 16 warps per CTA (4 by default) and the
-// compiler's register choice.
+// CTA size only sets how finely the register file is shared out.  The 3D P1
+// Laplacian in FP32 with the compensated Jacobian runs one-warp CTAs with at
+// least 24 resident per SM, which holds it to 80 registers without spills
+// (25 warps per SM against 20 at its natural 90 in 4-warp CTAs; 9% faster).
+// The same at 96 registers made P1 elasticity and the P2 Laplacian with a P1
+// coefficient 1-5% slower, so the other instantiations take up to 16 warps
+// per CTA (4 by default) and the compiler's register choice.
 template <int D, int FORM, int JAC, class CT, class OT>
 struct FwdShape {
-  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && JAC == JAC_COMP && sizeof(CT) == 4 &&
-                                 sizeof(OT) == 4);
+  static constexpr int tight_ctas() {
+    if (!(D == 3 && JAC == JAC_COMP && sizeof(CT) == 4 && sizeof(OT) == 4)) return 0;
+    return FORM == LAPLACE_P1 ? 24 : 0;
+  }
+  static constexpr bool tight = tight_ctas() > 0;
   static constexpr int threads = tight ? 32 : 512;
-  static constexpr int min_ctas = tight ? 24 : 1;
+  static constexpr int min_ctas = tight ? tight_ctas() : 1;
   static constexpr int default_warps = tight ? 1 : 4;
 };
 
@@ -153,13 +157,12 @@ __device__ __forceinline__ int gather_regs(const CT* coords, int64_t n_vert, int
   return GF_ELEM | GF_OK;
 }
 
-// Contraction of a lane's folded G with K (immediates) and the tile's store:
-// the swizzled stage and its TMA tensor store (TMA), else the stage and the
-// warp's coalesced read-out.
-template <int D, int FORM, class CT, class OT, bool TMA = false>
-__device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, int64_t tile, int lane,
-                                                   const OT (&Gf)[FormTraits<D, FORM>::NG], OT* st,
-                                                   const CUtensorMap* tmap) {
+// A lane's element matrix and the tile's store: fill(sink) hands every unique
+// entry (i <= j) to sink.put<i, j>(value); then the swizzled stage and its TMA
+// tensor store (TMA), else the stage and the warp's coalesced read-out.
+template <int D, int FORM, class CT, class OT, bool TMA, class Fill>
+__device__ __forceinline__ void fwd_fill_store(const FwdParams<CT, OT>& p, int64_t tile, int lane, Fill&& fill,
+                                               OT* st, const CUtensorMap* tmap) {
   using FT = FormTraits<D, FORM>;
   using PL = FwdPlan<D, FORM, CT, OT>;
   constexpr int NN = FT::NN;
@@ -170,7 +173,7 @@ __device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, i
   if constexpr (PL::SWZ16) {
     // rows as float4 chunks, chunk index XOR-swizzled with (lane >> 1) & 3
     RegSink<4, float> rs;
-    contract<D, FORM>(Gf, rs);
+    fill(rs);
     const int sw = (lane >> 1) & 3;
     float* row = st + lane * 16;
     if constexpr (TMA) {
@@ -215,7 +218,7 @@ __device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, i
     }
   } else {
     StageSink<FT::N, SST, OT> sink{st + lane * SST};
-    contract<D, FORM>(Gf, sink);
+    fill(sink);
     __syncwarp();
     bool done = false;
     if constexpr (sizeof(OT) == 4 && NN % 4 == 0) {
@@ -239,6 +242,14 @@ __device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, i
     }
   }
   __syncwarp();
+}
+
+// Contraction of a lane's folded G with K (immediates), then the tile's store.
+template <int D, int FORM, class CT, class OT, bool TMA = false>
+__device__ __forceinline__ void fwd_contract_store(const FwdParams<CT, OT>& p, int64_t tile, int lane,
+                                                   const OT (&Gf)[FormTraits<D, FORM>::NG], OT* st,
+                                                   const CUtensorMap* tmap) {
+  fwd_fill_store<D, FORM, CT, OT, TMA>(p, tile, lane, [&](auto& sink) { contract<D, FORM>(Gf, sink); }, st, tmap);
 }
 
 // The element's coefficient: one value (per-element coefficient) or the

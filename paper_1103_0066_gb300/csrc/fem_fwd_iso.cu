@@ -11,9 +11,11 @@
 //      J^{-1}_k = adj / det -- the values the projection of Eq. 17 interpolates;
 //   3. |J| = |det J| at the centroid (Eq. 17 keeps |J| outside the integral);
 //   4. G^{(k mu),(l nu)} = w |J| / DEN  sum_a J^{-1}_{mu a,k} J^{-1}_{nu a,l}
-//      over the folded slot pairs (Eq. 18), then the same immediate-operand
-//      contraction with K^{ij}_{(k mu),(l nu)} and the same tile store as the
-//      affine kernel (Eq. 19).
+//      over the folded slot pairs (Eq. 18), each entry added into the
+//      accumulators of A as soon as it is formed (A_ij += K^{ij}_g G_g with K
+//      as immediates, g in increasing order: the sums of the G-first
+//      contraction, without holding all of G in registers), then the same
+//      tile store as the affine kernel (Eq. 19).
 // The Jacobian steps run in plain FP32: this path serves curved, non-sliver
 // elements; an element with a singular J at a vertex or at the centroid is
 // flagged degenerate and gets A = 0.
@@ -91,11 +93,64 @@ __device__ __forceinline__ bool all_vertex_jinv(const float (&nd)[n_geo(D)][D], 
   return (vertex_jinv<D, Ks>(nd, ji) & ...);
 }
 
+// acc[T] += K'[G][T] * gv over the unique entries T of A (zero terms generate no code).
+template <int D, int FORM, int G, int T>
+__device__ __forceinline__ void kscatter(float* acc, float gv) {
+  using FT = FormTraits<D, FORM>;
+  constexpr int k = Ref<D, FORM>::K.v[G][tri_row(T, FT::N)][tri_col(T, FT::N)];
+  if constexpr (k == 1) {
+    acc[T] += gv;
+  } else if constexpr (k == -1) {
+    acc[T] -= gv;
+  } else if constexpr (k != 0) {
+    acc[T] = fmaf(gv, float(k), acc[T]);
+  }
+}
+
+template <int D, int FORM, int G, int... Ts>
+__device__ __forceinline__ void scatter_g(float* acc, float gv, std::integer_sequence<int, Ts...>) {
+  (kscatter<D, FORM, G, Ts>(acc, gv), ...);
+}
+
+// G_g for the slot pair g = (p, q), p <= q, p = (k mu): scale * sum_a Jinv_{mu a,k} Jinv_{nu a,l}.
+template <int D, int FORM, int G>
+__device__ __forceinline__ void iso_term(const float (&ji)[D + 1][D][D], float scale, float* acc) {
+  using FT = FormTraits<D, FORM>;
+  constexpr int pp = tri_row(G, FT::NP), qq = tri_col(G, FT::NP);
+  float s = 0.f;
+#pragma unroll
+  for (int al = 0; al < D; ++al) s = fmaf(ji[pp / D][pp % D][al], ji[qq / D][qq % D][al], s);
+  scatter_g<D, FORM, G>(acc, scale * s, std::make_integer_sequence<int, FT::NT>{});
+}
+
+template <int D, int FORM, int... Gs>
+__device__ __forceinline__ void iso_accumulate(const float (&ji)[D + 1][D][D], float scale, float* acc,
+                                               std::integer_sequence<int, Gs...>) {
+  (iso_term<D, FORM, Gs>(ji, scale, acc), ...);
+}
+
+template <int D, int FORM, class Sink, int... Ts>
+__device__ __forceinline__ void put_all(Sink& sink, const float* acc, std::integer_sequence<int, Ts...>) {
+  using FT = FormTraits<D, FORM>;
+  (sink.template put<tri_row(Ts, FT::N), tri_col(Ts, FT::N)>(acc[Ts]), ...);
+}
+
+// CTA shape: warps never wait for one another.  The 3D P1 form runs one-warp
+// CTAs with at least 20 resident per SM, which holds it to 96 registers
+// without spills (21 warps per SM against 16 at 128 registers).
 template <int D, int FORM>
-__global__ void __launch_bounds__(128) fem_fwd_iso_kernel(FwdParams<float, float> p, const float* __restrict__ mid) {
+struct IsoShape {
+  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1_ISO);
+  static constexpr int threads = tight ? 32 : 128;
+  static constexpr int min_ctas = tight ? 20 : 1;
+};
+
+template <int D, int FORM>
+__global__ void __launch_bounds__(IsoShape<D, FORM>::threads, IsoShape<D, FORM>::min_ctas)
+    fem_fwd_iso_kernel(FwdParams<float, float> p, const float* __restrict__ mid) {
   using FT = FormTraits<D, FORM>;
   using PL = FwdPlan<D, FORM, float, float>;
-  constexpr int NE = D * (D + 1) / 2, NP = FT::NP;
+  constexpr int NE = D * (D + 1) / 2;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   float* st = reinterpret_cast<float*>(smem_raw + size_t(warp) * PL::per_warp);
@@ -107,9 +162,9 @@ __global__ void __launch_bounds__(128) fem_fwd_iso_kernel(FwdParams<float, float
     float X[D + 1][D];
     load_conn<D>(p.conn, e, p.n_elem, p.vec_conn, v);
     const int flags = gather_regs<D>(p.coords, p.n_vert, e, p.n_elem, v, X);
-    float Gf[FT::NG];
-#pragma unroll
-    for (int g = 0; g < FT::NG; ++g) Gf[g] = 0.f;
+    float ji[D + 1][D][D];
+    float scale = 0.f;
+    bool ok = false;
     if (flags & GF_OK) {
       float nd[n_geo(D)][D];  // geometry nodes relative to vertex 0
 #pragma unroll
@@ -121,8 +176,7 @@ __global__ void __launch_bounds__(128) fem_fwd_iso_kernel(FwdParams<float, float
       for (int q = 0; q < NE; ++q)
 #pragma unroll
         for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = __ldcs(m + q * D + al) - X[0][al];
-      float ji[D + 1][D][D];
-      bool ok = all_vertex_jinv<D>(nd, ji, std::make_integer_sequence<int, D + 1>{});
+      ok = all_vertex_jinv<D>(nd, ji, std::make_integer_sequence<int, D + 1>{});
       float ec[D][D], adjc[D][D];
       geo_jacobian<D, D + 1>(nd, ec);  // (D + 1) J at the centroid
       float detc = det_adj<D>(ec, adjc);
@@ -132,21 +186,21 @@ __global__ void __launch_bounds__(128) fem_fwd_iso_kernel(FwdParams<float, float
         err |= DEVERR_DEGENERATE;
       } else {
         const float w = (p.coef && e < p.n_elem) ? __ldg(p.coef + e) : 1.f;
-        const float scale = w * fabsf(detc) * (1.f / float(FT::DEN));
-#pragma unroll
-        for (int pp = 0; pp < NP; ++pp)
-#pragma unroll
-          for (int qq = pp; qq < NP; ++qq) {
-            float s = 0.f;
-#pragma unroll
-            for (int al = 0; al < D; ++al) s = fmaf(ji[pp / D][pp % D][al], ji[qq / D][qq % D][al], s);
-            Gf[pair_index(pp, qq, NP)] = scale * s;
-          }
+        scale = w * fabsf(detc) * (1.f / float(FT::DEN));
       }
     } else if (flags & GF_ELEM) {
       err |= DEVERR_CONN;
     }
-    fwd_contract_store<D, FORM, float, float, false>(p, t, lane, Gf, st, nullptr);
+    fwd_fill_store<D, FORM, float, float, false>(
+        p, t, lane,
+        [&](auto& sink) {
+          float acc[FT::NT];
+#pragma unroll
+          for (int i = 0; i < FT::NT; ++i) acc[i] = 0.f;
+          if (ok) iso_accumulate<D, FORM>(ji, scale, acc, std::make_integer_sequence<int, FT::NG>{});
+          put_all<D, FORM>(sink, acc, std::make_integer_sequence<int, FT::NT>{});
+        },
+        st, nullptr);
   }
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
@@ -166,7 +220,7 @@ cudaError_t launch_iso_t(const FwdLaunch& L, const float* mid) {
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_store = (reinterpret_cast<uintptr_t>(L.A) % 16 == 0);
   auto kern = fem_fwd_iso_kernel<D, FORM>;
-  const int warps = 4;
+  const int warps = IsoShape<D, FORM>::threads / 32;
   const size_t smem = size_t(warps) * PL::per_warp;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
