@@ -78,7 +78,11 @@ template <int D, int FORM>
 struct BwdPlan {
   static constexpr int NN = FormTraits<D, FORM>::NN;
   static constexpr bool VEC = (NN % 4 == 0);
-  static constexpr int DST = VEC ? NN + 4 : (NN | 1);  // dA row stride in the stage
+  // 4x4 rows: unpadded, 16-byte chunk c of row r at chunk c ^ ((r >> 1) & 3),
+  // so that both the copy (four lanes per row) and the row reads (a lane per
+  // row) are free of bank conflicts; other sizes: padded rows.
+  static constexpr bool SWZ = (NN == 16);
+  static constexpr int DST = SWZ ? 16 : (VEC ? NN + 4 : (NN | 1));  // dA row stride in the stage
   static constexpr int NV = D + 1;
   static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
   static constexpr int XP = D == 3 ? 4 : 2;  // padded floats per staged slot (one vector store)
@@ -101,7 +105,7 @@ struct BwdShape {
   static constexpr int min_ctas = tight ? 24 : 1;
 };
 
-// Asynchronous copy of a tile's contiguous dA into the padded stage slot.
+// Asynchronous copy of a tile's contiguous dA into the stage slot.
 template <int D, int FORM>
 __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, int lane, float* dslot) {
   using PL = BwdPlan<D, FORM>;
@@ -113,6 +117,20 @@ __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, 
   if constexpr (PL::VEC) {
     if (p.vec_dA) {
       constexpr int Q = NN / 4;
+      if constexpr (PL::SWZ) {
+        if (cnt == 32) {  // chunk lane + 32 i: row lane / 4 + 8 i, chunk lane % 4, swizzle (lane >> 3) & 3
+          float* d = dslot + (lane >> 2) * 16 + 4 * ((lane & 3) ^ ((lane >> 3) & 3));
+          const float* s = src + 4 * lane;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) cp_async<16>(d + i * 128, s + 128 * i);
+          return;
+        }
+        for (int q = lane; q < cnt * 4; q += 32) {
+          const int el = q >> 2;
+          cp_async<16>(dslot + el * 16 + 4 * ((q & 3) ^ ((el >> 1) & 3)), src + 4 * q);
+        }
+        return;
+      }
       if constexpr (32 % Q == 0) {
         if (cnt == 32) {  // full tile: chunk lane + 32 i is chunk lane % Q of row lane / Q + i (32 / Q)
           constexpr int RPI = 32 / Q;
@@ -134,21 +152,25 @@ __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, 
   const int nw = cnt * NN;
   for (int idx = lane; idx < nw; idx += 32) {
     const int el = idx / NN;
-    cp_async<4>(dslot + el * PL::DST + (idx - el * NN), src + idx);
+    int w = idx - el * NN;
+    if constexpr (PL::SWZ) w = 4 * ((w >> 2) ^ ((el >> 1) & 3)) + (w & 3);
+    cp_async<4>(dslot + el * PL::DST + w, src + idx);
   }
 }
 
-// Upper triangle of sym(dA) from a staged row: 16-byte reads when the row is
-// 16-byte aligned and small enough to hold in registers, scalar reads otherwise.
+// Upper triangle of sym(dA) from a staged row (row = lane): 16-byte reads when
+// the row is 16-byte aligned and small enough to hold in registers, scalar
+// reads otherwise.
 template <int D, int FORM>
 __device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTraits<D, FORM>::NT]) {
   using FT = FormTraits<D, FORM>;
   constexpr int N = FT::N, NN = FT::NN;
   if constexpr (NN % 4 == 0 && NN <= 36) {
     float r[NN];
+    const int sw = BwdPlan<D, FORM>::SWZ ? ((threadIdx.x & 31) >> 1) & 3 : 0;
 #pragma unroll
     for (int q = 0; q < NN / 4; ++q) {
-      const float4 v = reinterpret_cast<const float4*>(drow)[q];
+      const float4 v = reinterpret_cast<const float4*>(drow)[q ^ sw];
       r[4 * q] = v.x;
       r[4 * q + 1] = v.y;
       r[4 * q + 2] = v.z;
