@@ -338,7 +338,7 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     const bool recs = dcoords && !atomic;
     L.tile_rec = recs ? W.tile_rec : nullptr;
     L.rank = recs ? W.rank : nullptr;
-    L.rec_end = recs ? W.rec_end : nullptr;
+    L.rec_span = recs ? W.rec_span : nullptr;
     L.rec_dest = recs ? W.rec_dest : nullptr;
     L.records = recs ? W.records : nullptr;
     L.dcoords = dcoords;

@@ -46,7 +46,7 @@ struct BatchMesh {
   float* dcoef;
   const int32_t* tile_rec;  // per 32-element record tile
   const uint32_t* rank;
-  const uint8_t* rec_end;
+  const uint16_t* rec_span;
   const int32_t* rec_dest;
   const int32_t* voff;
   float* records;  // vertex-major
@@ -113,7 +113,7 @@ __device__ __forceinline__ BwdParams bwd_params(const BatchMesh& M, int vec_conn
   bp.dA = M.dA;
   bp.tile_rec = (M.flags & BM_REC) ? M.tile_rec : nullptr;
   bp.rank = M.rank;
-  bp.rec_end = M.rec_end;
+  bp.rec_span = M.rec_span;
   bp.rec_dest = M.rec_dest;
   bp.records = M.records;
   bp.dcoef = M.dcoef;
@@ -146,13 +146,13 @@ __device__ __forceinline__ int warp_bwd(const BatchMesh& M, const BwdParams& bp,
                                         const float (&X)[D + 1][D], const int (&v)[D + 1], const float* dstage,
                                         float* xs, const WarpRec& wr) {
   const bool rec = (M.flags & BM_REC) != 0;
-  const RecAhead ah = rec ? load_rec_ahead(M.rec_end, M.rec_dest, wr.rb, wr.rn, lane) : RecAhead{0, 0};
+  const RecAhead ah = rec ? load_rec_ahead(M.rec_span, M.rec_dest, wr.rb, wr.rn, lane) : RecAhead{0u, 0};
   const int err = bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, w, X,
                                                             dstage + lane * BwdPlan<D, FORM>::DST, v,
                                                             rec ? xs : nullptr, wr.rk);
   if (rec) {
     __syncwarp();
-    warp_records<D>(xs, M.rec_end, M.rec_dest, wr.rb, wr.rn, ah, M.records, lane);
+    warp_records<D>(xs, M.rec_span, M.rec_dest, wr.rb, wr.rn, ah, M.records, lane);
   }
   return err;
 }
@@ -623,7 +623,7 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
       L.dcoef = it.dcoef;
       L.tile_rec = rec ? W.tile_rec : nullptr;
       L.rank = rec ? W.rank : nullptr;
-      L.rec_end = rec ? W.rec_end : nullptr;
+      L.rec_span = rec ? W.rec_span : nullptr;
       L.rec_dest = rec ? W.rec_dest : nullptr;
       L.records = rec ? W.records : nullptr;
       L.dcoords = it.dcoords;
@@ -755,7 +755,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
       b->item_ws[size_t(i)] = W;
       M.tile_rec = W.tile_rec;
       M.rank = W.rank;
-      M.rec_end = W.rec_end;
+      M.rec_span = W.rec_span;
       M.rec_dest = W.rec_dest;
       M.voff = W.voff;
       M.records = W.records;

@@ -13,7 +13,7 @@ static cudaError_t launch_bwd_t(const BwdLaunch& L) {
   p.dA = L.dA;
   p.tile_rec = ATOMIC ? nullptr : L.tile_rec;
   p.rank = L.rank;
-  p.rec_end = L.rec_end;
+  p.rec_span = L.rec_span;
   p.rec_dest = L.rec_dest;
   p.records = L.records;
   p.dcoef = L.dcoef;

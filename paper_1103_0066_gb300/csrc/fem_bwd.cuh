@@ -16,14 +16,15 @@
 // Each warp runs the forward kernel's three-stage pipeline over tiles of 32
 // elements (connectivity two tiles ahead; coordinates, slot ranks and the
 // tile's record range one tile ahead in registers) and copies its upstream dA
-// (contiguous) with 16-byte cp.async into a padded stage.  In the deterministic
-// mode each lane writes the (d+1) vertex contributions of its element into the
-// warp's slot stage at their ranks in the tile's (vertex, slot) order (built
-// once per mesh), so the contributions to one vertex form a contiguous run;
-// lane r then sums run r in order into RECORD r of the tile, and the segmented
-// reduction adds the few records of each vertex.  Warps never wait for one
-// another.  The atomic variant adds each contribution into dcoords with
-// red.global.add.
+// (contiguous) with 16-byte cp.async into a stage.  In the deterministic mode
+// each lane writes the (d+1) vertex contributions of its element into the
+// warp's slot stage at their stage positions (built once per mesh): the
+// contributions to one vertex form a contiguous run, the runs follow the
+// tile's vertex order, and on tets each run starts at a position congruent to
+// its record index mod 8.  Lane r then sums run r in order into RECORD r of
+// the tile, and the segmented reduction adds the few records of each vertex.
+// Warps never wait for one another.  The atomic variant adds each
+// contribution into dcoords with red.global.add.
 #pragma once
 #include "fem_core.cuh"
 #include "fem_fwd.cuh"
@@ -61,8 +62,8 @@ struct BwdParams {
   const float* coef;
   const float* dA;
   const int32_t* tile_rec;  // first record of each 32-element tile (null: no coordinate records)
-  const uint32_t* rank;     // per element: byte k = rank of slot k in its tile's (vertex, slot) order
-  const uint8_t* rec_end;   // per record: end of its run in that order
+  const uint32_t* rank;     // per element: byte k = stage position of slot k (runs in (vertex, slot) order)
+  const uint16_t* rec_span; // per record: start | length << 8 of its run in the stage
   const int32_t* rec_dest;  // per record: its row in the vertex-major records array
   float* records;           // [R][D], vertex-major
   float* dcoef;
@@ -85,10 +86,11 @@ struct BwdPlan {
   static constexpr int DST = SWZ ? 16 : (VEC ? NN + 4 : (NN | 1));  // dA row stride in the stage
   static constexpr int NV = D + 1;
   static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
+  static constexpr int XCAP = D == 3 ? kStageCap3 : NSW;  // stage positions (aligned runs on tets)
   static constexpr int XP = D == 3 ? 4 : 2;  // padded floats per staged slot (one vector store)
   static constexpr size_t da_slot = align_up(size_t(32) * DST * 4, 128);    // one tile of dA rows
   static constexpr size_t da_bytes = 2 * da_slot;                           // per warp, double buffered
-  static constexpr size_t xs_bytes = align_up(size_t(NSW) * XP * 4, 128);   // per warp
+  static constexpr size_t xs_bytes = align_up(size_t(XCAP) * XP * 4, 128);  // per warp
   static constexpr size_t per_warp = da_bytes + xs_bytes;
 };
 
@@ -183,42 +185,40 @@ __device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTrai
 }
 
 // Records of one warp's 32-element tile.  Record r (r < rn) sums the staged
-// contributions at positions [end(r-1), end(r)) of the tile's (vertex, slot)
-// order -- the slots of its vertex, in increasing slot order -- and writes row
-// rec_dest[rb + r] of the vertex-major records.  end0 = rec_end[rb + lane] and
-// dest0 = rec_dest[rb + lane] for lane < rn (loaded ahead by the caller),
+// contributions of its run -- the slots of its vertex, in increasing slot
+// order, at stage positions [start, start + length) -- and writes row
+// rec_dest[rb + r] of the vertex-major records.  span0 = rec_span[rb + lane]
+// and dest0 = rec_dest[rb + lane] for lane < rn (loaded ahead by the caller),
 // anything for the other lanes.
 struct RecAhead {
-  int end0, dest0;
+  uint32_t span0;
+  int dest0;
 };
 
-__device__ __forceinline__ RecAhead load_rec_ahead(const uint8_t* rec_end, const int32_t* rec_dest, int32_t rb,
+__device__ __forceinline__ RecAhead load_rec_ahead(const uint16_t* rec_span, const int32_t* rec_dest, int32_t rb,
                                                    int32_t rn, int lane) {
-  RecAhead a{0, 0};
+  RecAhead a{0u, 0};
   if (lane < rn) {
-    a.end0 = int(__ldg(rec_end + rb + lane));
+    a.span0 = __ldg(rec_span + rb + lane);
     a.dest0 = __ldg(rec_dest + rb + lane);
   }
   return a;
 }
 
 template <int D>
-__device__ __forceinline__ void warp_records(const float* xs, const uint8_t* rec_end, const int32_t* rec_dest,
+__device__ __forceinline__ void warp_records(const float* xs, const uint16_t* rec_span, const int32_t* rec_dest,
                                              int32_t rb, int32_t rn, RecAhead ah, float* records, int lane) {
   constexpr int XP = D == 3 ? 4 : 2;
-  int prev = 0;  // end of the record before lane 0's
   for (int r0 = 0; r0 < rn; r0 += 32) {
     const int r = r0 + lane;
     const bool live = r < rn;
-    const int end = r0 == 0 ? ah.end0 : (live ? int(__ldg(rec_end + rb + r)) : 0);
+    const uint32_t span = r0 == 0 ? ah.span0 : (live ? uint32_t(__ldg(rec_span + rb + r)) : 0u);
     const int dest = r0 == 0 ? ah.dest0 : (live ? __ldg(rec_dest + rb + r) : 0);
-    int beg = __shfl_up_sync(0xffffffffu, end, 1);
-    if (lane == 0) beg = prev;
-    prev = __shfl_sync(0xffffffffu, end, 31);
+    const int beg = int(span & 0xFFu);
     // Runs have different lengths; the warp steps to its longest run in
     // blocks of 8 predicated loads, so the loads of a lane are in flight
     // together.  Each run is still summed in increasing position order.
-    const int len = live ? end - beg : 0;
+    const int len = live ? int(span >> 8) : 0;
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
     float acc[D];
 #pragma unroll
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   const int nwarps = blockDim.x >> 5;
   unsigned char* wbase = smem_raw + size_t(warp) * PL::per_warp;
   float* dslots = reinterpret_cast<float*>(wbase);               // [2][32][DST]
-  float* xs = reinterpret_cast<float*>(wbase + PL::da_bytes);    // [32 (d+1)][XP]
+  float* xs = reinterpret_cast<float*>(wbase + PL::da_bytes);    // [XCAP][XP]
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
   const int64_t ntiles = (p.n_elem + 31) / 32;
   const int64_t S = int64_t(gridDim.x) * nwarps;  // warp-tile stride
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
       rnn = __ldg(p.tile_rec + tn + 1) - rbn;
     }
     // this tile's record ends and destinations: in flight while the element math runs
-    const RecAhead ah = rec ? load_rec_ahead(p.rec_end, p.rec_dest, rb, rn, lane) : RecAhead{0, 0};
+    const RecAhead ah = rec ? load_rec_ahead(p.rec_span, p.rec_dest, rb, rn, lane) : RecAhead{0u, 0};
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();  // dA rows were copied by other lanes
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
                                                   vc, rec ? xs : nullptr, rkcur);
     if (rec) {
       __syncwarp();  // every lane's contributions are staged
-      warp_records<D>(xs, p.rec_end, p.rec_dest, rb, rn, ah, p.records, lane);
+      warp_records<D>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
     }
     __syncwarp();  // the slot stage is rewritten next tile, the dA slot two tiles later
     fcur = fnext;

@@ -210,12 +210,9 @@ __device__ __forceinline__ bool is_head(const uint64_t* key, int i) {
   return v != kNoVertex && (i == 0 || (key[i - 1] >> 16) != v);
 }
 
-// Pass 1: the rank of every slot of each tile and the tile's record count.
-// Slots of the tile past the last element keep ranks too (zero contributions
-// are written there and never read).
+// Pass 1: the record count of each tile (its distinct vertices).
 __global__ void __launch_bounds__(kBuildThreads)
-    tile_sort_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
-                     uint8_t* rank, int32_t* nrec) {
+    tile_sort_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles, int32_t* nrec) {
   __shared__ uint64_t keys[kBuildThreads / 32][kSortCap];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* key = keys[warp];
@@ -227,12 +224,7 @@ __global__ void __launch_bounds__(kBuildThreads)
 #pragma unroll
     for (int q = 0; q < kKeysPerLane; ++q) {
       const int i = lane + 32 * q;
-      if (i < ns) {
-        const int slot = int(key[i] & 0xFFFF);
-        // element slot / nv of the tile, local vertex slot % nv; 4 bytes per element
-        rank[(tile * kRecTile + slot / nv) * 4 + slot % nv] = uint8_t(i);
-        c += is_head(key, i) ? 1 : 0;
-      }
+      if (i < ns) c += is_head(key, i) ? 1 : 0;
     }
     c = __reduce_add_sync(0xffffffffu, c);
     if (lane == 0) nrec[tile] = c;
@@ -240,41 +232,95 @@ __global__ void __launch_bounds__(kBuildThreads)
   }
 }
 
-// Pass 2: record ends (end of each record's run in the tile's order) and
-// record vertices.
+// Pass 2: per tile, its records (one per distinct vertex, in vertex order),
+// the stage position (rank) of every slot, each record's span (start and
+// length of its run in the stage) and vertex.  The slots of a record are
+// consecutive positions in increasing slot order.  With pad = 8 the run of
+// local record r starts at the first free position p with p = r (mod 8): the
+// adjoint sums record r in lane r, position by position, so the eight lanes of
+// a quarter warp then read eight different 16-byte bank groups at every step.
+// A tile whose padded stage would exceed cap positions, and every tile when
+// pad = 0, packs the runs back to back.  Slots of absent elements (past
+// n_elem) take the positions after the last run; zeros are written there and
+// never read.
 __global__ void __launch_bounds__(kBuildThreads)
     tile_records_kernel(const int32_t* conn, int nv, int64_t n_elem, int64_t n_vert, int64_t n_tiles,
-                        const int32_t* tile_rec, uint8_t* rec_end, int32_t* rec_vertex) {
+                        const int32_t* tile_rec, int pad, int cap, uint8_t* rank, uint16_t* rec_span,
+                        int32_t* rec_vertex) {
   __shared__ uint64_t keys[kBuildThreads / 32][kSortCap];
+  __shared__ int16_t cstart[kBuildThreads / 32][kSortCap + 1];  // packed start of each record, + end
+  __shared__ int16_t ostart[kBuildThreads / 32][kSortCap + 1];  // stage start of each record, + end
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint64_t* key = keys[warp];
+  int16_t* cs = cstart[warp];
+  int16_t* os = ostart[warp];
+  const int ns = kRecTile * nv;
   const int64_t stride = int64_t(gridDim.x) * (kBuildThreads / 32);
   for (int64_t tile = blockIdx.x * int64_t(kBuildThreads / 32) + warp; tile < n_tiles; tile += stride) {
     warp_sorted_keys(conn, nv, n_elem, n_vert, tile, key);
+    const int32_t rb = tile_rec[tile], rn = tile_rec[tile + 1] - rb;
     // lane owns the consecutive entries [kKeysPerLane * lane, kKeysPerLane * (lane + 1))
-    int heads = 0;
+    int heads = 0, valid = 0;
 #pragma unroll
-    for (int q = 0; q < kKeysPerLane; ++q) heads += is_head(key, kKeysPerLane * lane + q) ? 1 : 0;
+    for (int q = 0; q < kKeysPerLane; ++q) {
+      const int i = kKeysPerLane * lane + q;
+      heads += is_head(key, i) ? 1 : 0;
+      valid += (key[i] >> 16) != kNoVertex ? 1 : 0;
+    }
     int incl = heads;  // inclusive warp scan of the head counts
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, off);
       if (lane >= off) incl += y;
     }
-    int32_t r = tile_rec[tile] + incl - heads - 1;  // record of the entry before the lane's first
+    const int n_valid = __reduce_add_sync(0xffffffffu, valid);
+    const int lr0 = incl - heads - 1;  // local record of the entry before the lane's first
+    int lr = lr0;
 #pragma unroll
     for (int q = 0; q < kKeysPerLane; ++q) {
       const int i = kKeysPerLane * lane + q;
-      const uint64_t v = key[i] >> 16;
-      if (v == kNoVertex) continue;
-      if (is_head(key, i)) {
-        ++r;
-        rec_vertex[r] = int32_t(v);
+      if (is_head(key, i)) cs[++lr] = int16_t(i);
+    }
+    if (lane == 0) cs[rn] = int16_t(n_valid);
+    __syncwarp();
+    if (lane == 0) {  // stage starts: padded if they fit, else packed
+      int o = 0;
+      if (pad > 0) {
+        for (int r = 0; r < rn; ++r) {
+          o += (r - o) & (pad - 1);
+          os[r] = int16_t(o);
+          o += cs[r + 1] - cs[r];
+        }
       }
-      const bool last = (i + 1 == kSortCap) || ((key[i + 1] >> 16) != v);
-      if (last) rec_end[r] = uint8_t(i + 1);
+      if (pad == 0 || o + (ns - n_valid) > cap) {
+        for (int r = 0; r < rn; ++r) os[r] = cs[r];
+        o = n_valid;
+      }
+      os[rn] = int16_t(o);
     }
     __syncwarp();
+    lr = lr0;
+#pragma unroll
+    for (int q = 0; q < kKeysPerLane; ++q) {
+      const int i = kKeysPerLane * lane + q;
+      if (i >= ns) continue;
+      const uint64_t v = key[i] >> 16;
+      const int slot = int(key[i] & 0xFFFF);
+      int pos;
+      if (v != kNoVertex) {
+        if (is_head(key, i)) {
+          ++lr;
+          rec_vertex[rb + lr] = int32_t(v);
+          rec_span[rb + lr] = uint16_t(os[lr] | ((cs[lr + 1] - cs[lr]) << 8));
+        }
+        pos = os[lr] + (i - cs[lr]);
+      } else {
+        pos = os[rn] + (i - n_valid);
+      }
+      // element slot / nv of the tile, local vertex slot % nv; 4 bytes per element
+      rank[(tile * kRecTile + slot / nv) * 4 + slot % nv] = uint8_t(pos);
+    }
+    __syncwarp();  // the key and start buffers are refilled for the next tile
   }
 }
 
@@ -342,7 +388,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   };
   const size_t o_tile_rec = take(sizeof(int32_t) * size_t(n_tiles + 1));
   const size_t o_rank = take(sizeof(uint32_t) * size_t(n_tiles * kRecTile));
-  const size_t o_rec_end = take(sizeof(uint8_t) * size_t(r_max));
+  const size_t o_rec_span = take(sizeof(uint16_t) * size_t(r_max));
   const size_t o_rec_dest = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_rec_vertex = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_voff = take(sizeof(int32_t) * size_t(n_vert + 1));
@@ -354,7 +400,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
     char* b = static_cast<char*>(base);
     ws->tile_rec = reinterpret_cast<int32_t*>(b + o_tile_rec);
     ws->rank = reinterpret_cast<uint32_t*>(b + o_rank);
-    ws->rec_end = reinterpret_cast<uint8_t*>(b + o_rec_end);
+    ws->rec_span = reinterpret_cast<uint16_t*>(b + o_rec_span);
     ws->rec_dest = reinterpret_cast<int32_t*>(b + o_rec_dest);
     ws->rec_vertex = reinterpret_cast<int32_t*>(b + o_rec_vertex);
     ws->voff = reinterpret_cast<int32_t*>(b + o_voff);
@@ -395,12 +441,13 @@ cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem,
   const int64_t tb = (n_tiles + kBuildThreads / 32 - 1) / (kBuildThreads / 32);
   const unsigned tg = unsigned(tb < 4 * 65535 ? (tb > 0 ? tb : 1) : 4 * 65535);
   // tile records; record slots past the last record keep vertex -1
-  tile_sort_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles,
-                                                     reinterpret_cast<uint8_t*>(ws.rank), ws.cursor);
+  tile_sort_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.cursor);
   exclusive_scan(ws.cursor, n_tiles, ws.partials, ws.tile_rec, stream);
   fill_i32<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.rec_vertex, r_max, -1);
   tile_records_kernel<<<tg, kBuildThreads, 0, stream>>>(conn, nv, n_elem, n_vert, n_tiles, ws.tile_rec,
-                                                         ws.rec_end, ws.rec_vertex);
+                                                         dim == 3 ? 8 : 0, dim == 3 ? kStageCap3 : kRecTile * nv,
+                                                         reinterpret_cast<uint8_t*>(ws.rank), ws.rec_span,
+                                                         ws.rec_vertex);
   // vertex -> records CSR
   launch_key_csr(ws.rec_vertex, r_max, n_vert, ws.voff, ws.vrec, ws.cursor, ws.partials, stream);
   dest_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.voff, n_vert, ws.vrec, ws.rec_dest);

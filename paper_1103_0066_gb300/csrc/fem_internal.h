@@ -38,6 +38,9 @@ constexpr int kTileElems = 128;
 // Elements per record tile of the deterministic reduction: one warp's 32
 // elements, so a warp forms its records without any CTA-wide barrier.
 constexpr int kRecTile = 32;
+// Positions of a tet tile's slot stage: the 128 slots with each record's run
+// aligned for conflict-free reads (see tile_records_kernel).
+constexpr int kStageCap3 = 256;
 
 // Adjoint element pass (FP32 coordinates).
 struct BwdLaunch {
@@ -51,7 +54,7 @@ struct BwdLaunch {
   // deterministic: tile records (null when only dcoef is wanted)
   const int32_t* tile_rec;
   const uint32_t* rank;
-  const uint8_t* rec_end;
+  const uint16_t* rec_span;
   const int32_t* rec_dest;
   float* records;
   int64_t n_elem, n_vert;
@@ -61,14 +64,14 @@ struct BwdLaunch {
 };
 
 // Workspace of the deterministic adjoint (see fem_incidence.cu):
-// [tile_rec T+1][rank T*32 u32][rec_end R u8][rec_dest R][rec_vertex R][voff V+1]
+// [tile_rec T+1][rank T*32 u32][rec_span R u16][rec_dest R][rec_vertex R][voff V+1]
 // [vrec R][cursor][scan partials][records R*d]   with T = ceil(E/32) record
 // tiles and R <= E*(d+1) records; records are stored vertex-major (record r at
 // rec_dest[r]), so the records of vertex v are records[voff[v], voff[v+1]).
 struct BwdWorkspace {
   int32_t* tile_rec;
   uint32_t* rank;  // per element: byte k = rank of its local vertex k in its tile's (vertex, slot) order
-  uint8_t* rec_end;
+  uint16_t* rec_span;  // per record: start | length << 8 of its run in the tile's slot stage
   int32_t* rec_dest;  // per record: its position in the vertex-major record array
   int32_t* rec_vertex;
   int32_t* voff;

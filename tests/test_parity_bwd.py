@@ -60,48 +60,71 @@ def test_deterministic_is_bitwise_reproducible(gfem):
 
 def test_tile_records_structure(gfem):
     """Workspace of the deterministic reduction: each 32-element record tile has
-    one record per distinct vertex; every slot's rank is its position in the
-    tile's (vertex, slot) order; each record ends where its vertex's run of
-    slots ends; and rec_dest places the records of every vertex, in record
-    order, in that vertex's run [voff[v], voff[v+1]) of the vertex-major array."""
-    mesh = _mesh(3, 5)
-    coords, conn = _t(mesh.coords), _t(mesh.conn)
-    ws = gfem.Workspace(coords, conn)
-    E, NV, TS = mesh.n_elem, 4, 32
-    T = (E + TS - 1) // TS
-    al = lambda x: ((x + 255) // 256) * 256
-    raw = ws.buf.cpu().numpy()
-    tile_rec = raw[: 4 * (T + 1)].view(np.int32)
-    o_rank = al(4 * (T + 1))
-    rank = raw[o_rank: o_rank + 4 * T * TS].reshape(T * TS, 4)
-    o_end = al(o_rank + 4 * T * TS)
-    R = int(tile_rec[T])
-    rec_end = raw[o_end: o_end + R]
-    o_dest = al(o_end + NV * E)
-    rec_dest = raw[o_dest: o_dest + 4 * R].view(np.int32)
-    o_voff = al(al(o_dest + 4 * NV * E) + 4 * NV * E)
-    voff = raw[o_voff: o_voff + 4 * (mesh.n_vert + 1)].view(np.int32)
-    flat = mesh.conn.ravel()
-    assert tile_rec[0] == 0
-    assert np.array_equal(np.sort(rec_dest), np.arange(R))      # a permutation of the records
-    rec_vtx = np.empty(R, np.int64)
-    for t in range(T):
-        slots = np.arange(t * TS * NV, min((t + 1) * TS * NV, NV * E))
-        verts = flat[slots]
-        local = slots - t * TS * NV
-        order = local[np.lexsort((local, verts))]              # slots in (vertex, slot) order
-        rk = rank[t * TS + local // NV, local % NV].astype(np.int64)
-        assert np.array_equal(rk[order], np.arange(len(slots)))  # rank = position in that order
-        u, counts = np.unique(verts, return_counts=True)
-        assert tile_rec[t + 1] - tile_rec[t] == len(u)
-        ends = rec_end[tile_rec[t]: tile_rec[t + 1]].astype(np.int64)
-        assert np.array_equal(ends, np.cumsum(counts))
-        rec_vtx[tile_rec[t]: tile_rec[t + 1]] = u
-    assert np.array_equal(np.diff(voff), np.bincount(rec_vtx, minlength=mesh.n_vert))
-    order = np.argsort(rec_dest)                                 # record stored at each row
-    assert np.array_equal(rec_vtx[order], np.repeat(np.arange(mesh.n_vert), np.diff(voff)))
-    for v in range(mesh.n_vert):                                  # record order within a vertex
-        assert np.all(np.diff(order[voff[v]: voff[v + 1]]) > 0)
+    one record per distinct vertex, in vertex order; each record's span (start,
+    length) in the tile's slot stage holds exactly the slots of its vertex, in
+    increasing slot order (the slot's rank is its stage position); the spans
+    are disjoint and ordered; on tets a padded tile starts record r at a
+    position congruent to r mod 8 (a packed one back to back); absent slots sit
+    past the last run; and rec_dest places the records of every vertex, in
+    record order, in that vertex's run [voff[v], voff[v+1]) of the
+    vertex-major array."""
+    for dim, n, cut in ((3, 5, 0), (3, 6, 37), (2, 9, 11)):
+        mesh = _mesh(dim, n)
+        if cut:  # a ragged last tile
+            mesh.conn = mesh.conn[: mesh.n_elem - cut]
+        coords, conn = _t(mesh.coords), _t(mesh.conn)
+        ws = gfem.Workspace(coords, conn)
+        E, NV, TS = mesh.n_elem, dim + 1, 32
+        cap = 256 if dim == 3 else TS * NV
+        T = (E + TS - 1) // TS
+        al = lambda x: ((x + 255) // 256) * 256
+        raw = ws.buf.cpu().numpy()
+        tile_rec = raw[: 4 * (T + 1)].view(np.int32)
+        o_rank = al(4 * (T + 1))
+        rank = raw[o_rank: o_rank + 4 * T * TS].reshape(T * TS, 4)
+        o_span = al(o_rank + 4 * T * TS)
+        R = int(tile_rec[T])
+        span = raw[o_span: o_span + 2 * R].view(np.uint16).astype(np.int64)
+        o_dest = al(o_span + 2 * NV * E)
+        rec_dest = raw[o_dest: o_dest + 4 * R].view(np.int32)
+        o_voff = al(al(o_dest + 4 * NV * E) + 4 * NV * E)
+        voff = raw[o_voff: o_voff + 4 * (mesh.n_vert + 1)].view(np.int32)
+        flat = mesh.conn.ravel()
+        assert tile_rec[0] == 0
+        assert np.array_equal(np.sort(rec_dest), np.arange(R))      # a permutation of the records
+        rec_vtx = np.empty(R, np.int64)
+        n_padded = 0
+        for t in range(T):
+            slots = np.arange(t * TS * NV, min((t + 1) * TS * NV, NV * E))
+            verts = flat[slots]
+            local = slots - t * TS * NV
+            order = local[np.lexsort((local, verts))]              # slots in (vertex, slot) order
+            u, counts = np.unique(verts, return_counts=True)
+            rb, rn = tile_rec[t], tile_rec[t + 1] - tile_rec[t]
+            assert rn == len(u)
+            beg, ln = span[rb: rb + rn] & 0xFF, span[rb: rb + rn] >> 8
+            assert np.array_equal(ln, counts)
+            assert np.all(beg[1:] >= beg[:-1] + ln[:-1])              # disjoint, in record order
+            padded = not np.array_equal(beg, np.concatenate([[0], np.cumsum(counts)[:-1]]))
+            if padded:
+                assert dim == 3 and np.all(beg % 8 == np.arange(rn) % 8)
+                n_padded += 1
+            pos = np.concatenate([b + np.arange(c) for b, c in zip(beg, ln)])
+            got = rank[t * TS + order // NV, order % NV].astype(np.int64)
+            assert np.array_equal(got, pos)                          # slot order within each run
+            absent = np.arange(len(slots), TS * NV)                  # slots past the last element
+            if len(absent):
+                ra = rank[t * TS + absent // NV, absent % NV].astype(np.int64)
+                end = beg[-1] + ln[-1]
+                assert np.array_equal(np.sort(ra), end + np.arange(len(absent))) and ra.max() < cap
+            assert pos.max() < cap
+            rec_vtx[rb: rb + rn] = u
+        assert (n_padded > 0) == (dim == 3)
+        assert np.array_equal(np.diff(voff), np.bincount(rec_vtx, minlength=mesh.n_vert))
+        order = np.argsort(rec_dest)                                 # record stored at each row
+        assert np.array_equal(rec_vtx[order], np.repeat(np.arange(mesh.n_vert), np.diff(voff)))
+        for v in range(mesh.n_vert):                                  # record order within a vertex
+            assert np.all(np.diff(order[voff[v]: voff[v + 1]]) > 0)
 
 
 def test_coefficient_only_and_coords_only(gfem, orc):
