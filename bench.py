@@ -183,15 +183,17 @@ def tet_workload(n=128, k=2):
     return mesh, dA
 
 
-def algorithmic_bytes(E, V, R, n, dim, coef):
+def algorithmic_bytes(E, V, R, n, dim, coef, saved_det=True):
     """Bytes each kernel must move (every input read once, every output written
     once, vertex arrays once).  R = records of the deterministic reduction (one
-    per distinct vertex of each 32-element tile)."""
+    per distinct vertex of each 32-element tile).  saved_det: the forward
+    writes det J (4 B per element) and the adjoint reads it."""
     nv = dim + 1
-    fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0)) + V * 4 * dim
+    sd = 4 if saved_det else 0
+    fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0) + sd) + V * 4 * dim
     # dA, connectivity, the slot ranks (one 4-byte word per element); record
-    # ends (1 B) and destinations (4 B) read, record sums (4 d B) written
-    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0)) + R * (1 + 4 + 4 * dim) + V * 4 * dim
+    # spans (2 B) and destinations (4 B) read, record sums (4 d B) written
+    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0) + sd) + R * (2 + 4 + 4 * dim) + V * 4 * dim
     # vertex-major record sums and the vertex offsets read, dcoords written
     reduce = R * 4 * dim + V * (4 + 4 * dim)
     return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
@@ -252,14 +254,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     setup_ms = (time.perf_counter() - t0) * 1e3
 
+    det = torch.empty(E, dtype=torch.float32, device=dev)  # det J kept from the forward for the adjoint
+
     def step(evs=None):
         if evs is not None:
             evs[0].record(stream)
-        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A)
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A, det_out=det)
         if evs is not None:
             evs[1].record(stream)
         fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, ws=ws, reduce=fem.REDUCE_DEFERRED,
-                          dcoords=dcoords, need_dcoef=False)
+                          dcoords=dcoords, need_dcoef=False, det=det)
         if evs is not None:
             evs[2].record(stream)
         fem.adjoint_reduce(coords, conn, ws, dcoords)
@@ -383,7 +387,7 @@ def batch_bytes(items):
         m = it["src"].mesh
         n = int(it["A"].shape[1])
         R = it.get("records", 0)
-        b = algorithmic_bytes(m.n_elem, m.n_vert, R, n, m.dim, True)
+        b = algorithmic_bytes(m.n_elem, m.n_vert, R, n, m.dim, True, saved_det=False)
         total += b["fwd"] + b["bwd_elem"] + b["reduce"]
     return total
 
@@ -543,7 +547,7 @@ def run_elastic(args):
                                         rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
         err = _sample_err(oracle, 3, fem.ELASTIC_P1, mesh, coef_h, A, idx)
         res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "max_rel_err_vs_fp64": err}
-    byts = algorithmic_bytes(E, V, 0, 12, 3, True)["fwd"]
+    byts = algorithmic_bytes(E, V, 0, 12, 3, True, saved_det=False)["fwd"]
     peak, peak_kind = hbm_peak()
     best = min(res, key=lambda k: res[k]["ms"])
     for k in res:
@@ -831,7 +835,7 @@ def run_multiphysics(args):
     R = wss[0].n_records()  # the records depend on the connectivity only
     byts = 0
     for it in items:
-        b = algorithmic_bytes(E, V, R, int(it["A"].shape[1]), 3, True)
+        b = algorithmic_bytes(E, V, R, int(it["A"].shape[1]), 3, True, saved_det=False)
         byts += b["fwd"] + b["bwd_elem"] + b["reduce"]
     peak, peak_kind = hbm_peak()
     gbs = byts / (batch_ms * 1e-3) / 1e9
@@ -931,14 +935,15 @@ def run_adjoint64(args):
     dx = torch.empty((V, 3), device=dev)
     dw = torch.empty(E, device=dev)
     ws = fem.Workspace(coords, conn)
-    nt = (E + 127) // 128
-    R = int(ws.buf[4 * nt: 4 * nt + 4].view(torch.int32).item())
+    R = ws.n_records()
+    det = torch.empty(E, device=dev)  # det J kept from the forward for the adjoint
     stream = torch.cuda.current_stream(dev)
     res = {}
     for name, reduce in (("deterministic", fem.REDUCE_DETERMINISTIC), ("atomic", fem.REDUCE_ATOMIC)):
         def step():
-            fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, coef, out=A)
-            fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, coef, ws=ws, reduce=reduce, dcoords=dx, dcoef=dw)
+            fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, coef, out=A, det_out=det)
+            fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, coef, ws=ws, reduce=reduce, dcoords=dx, dcoef=dw,
+                              det=det)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -951,7 +956,7 @@ def run_adjoint64(args):
         ms = s0.elapsed_time(s1) / args.steps
         b = algorithmic_bytes(E, V, R if reduce == 0 else 0, 4, 3, True)
         byts = b["fwd"] + (b["bwd_elem"] + b["reduce"] if reduce == 0 else
-                           E * (64 + 16 + 4 + 4) + V * 12 * 2)
+                           E * (64 + 16 + 4 + 4 + 4) + V * 12 * 2)
         res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9}
     peak, peak_kind = hbm_peak()
     d = res["deterministic"]

@@ -147,6 +147,16 @@ FEM_API fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K_ho
 FEM_API fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
                              int32_t out_dtype, const fem_options* options, void* stream);
 
+/* Forward integration that also saves det J for the adjoint (reverse mode
+ * keeps what the forward computed): as fem_integrate_fwd, and
+ *   det : device FP32 [n_elem], overwritten: det J of each element as the
+ *         Jacobian mode computed it (the compensated value by default; 0 for
+ *         an element with an invalid vertex).
+ * FP32 contraction only (FEM_ERR_UNSUPPORTED otherwise).  Pass det to
+ * fem_integrate_bwd_saved. */
+FEM_API fem_status fem_integrate_fwd_save(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
+                                          int32_t out_dtype, float* det, const fem_options* options, void* stream);
+
 /* Forward integration on non-affine elements (Eqs. 16-19), forms
  * FEM_LAPLACE_P1_ISO / FEM_LAPLACE_P2_ISO, FP32 coordinates and output.  Each
  * element has quadratic geometry: its d+1 vertices and its edge-midpoint nodes
@@ -193,6 +203,17 @@ FEM_API fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws
 FEM_API fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef,
                              const float* dA, float* dcoords, float* dcoef, void* ws,
                              size_t ws_bytes, const fem_options* options, void* stream);
+
+/* Adjoint with det J saved by fem_integrate_fwd_save on the same mesh and
+ * form (device FP32 [n_elem]): the element pass forms the edge vectors and
+ * adj(J) in FP32 and takes det J from `det` instead of recomputing it, so the
+ * compensated determinant is computed once per step.  With the default
+ * compensated Jacobian on both sides the results are bitwise those of
+ * fem_integrate_bwd; options->jac is not used.  Other arguments, the
+ * reductions and the errors as fem_integrate_bwd. */
+FEM_API fem_status fem_integrate_bwd_saved(const fem_mesh* mesh, int32_t form, const float* coef,
+                                           const float* dA, const float* det, float* dcoords, float* dcoef,
+                                           void* ws, size_t ws_bytes, const fem_options* options, void* stream);
 
 /* Second phase of a FEM_REDUCE_DEFERRED adjoint: dcoords[v] (device FP32
  * [n_vert][dim], overwritten) = sum over the incidence segment of v, in

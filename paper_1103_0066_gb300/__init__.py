@@ -74,9 +74,11 @@ def _coef_ptr(coef, E, what="[E]"):
 
 
 def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float32, jac=JAC_AUTO,
-                  contract=CONTRACT_F32, warps_per_cta=0, ctas_per_sm=0, dev_err=None, stream=None):
+                  contract=CONTRACT_F32, warps_per_cta=0, ctas_per_sm=0, dev_err=None, stream=None, det_out=None):
     """fem_integrate_fwd: element matrices [E][n][n] (not differentiable; see integrate).
-    coef: [E] per-element values, or [V] vertex values for LAPLACE_P1_W1 / LAPLACE_P2_W1."""
+    coef: [E] per-element values, or [V] vertex values for LAPLACE_P1_W1 / LAPLACE_P2_W1.
+    det_out: optional float32 [E] tensor that receives det J for integrate_bwd(det=...)
+    (fem_integrate_fwd_save)."""
     m = _mesh_struct(coords, conn)
     n, _, _ = form_info(form, m.dim)
     E = conn.shape[0]
@@ -89,8 +91,17 @@ def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float
     opts = nat.options_struct(jac, contract, 0, warps_per_cta, ctas_per_sm,
                               dev_err.data_ptr() if dev_err is not None else 0)
     cp = _coef_ptr(coef, coords.shape[0], "[V]") if w1 else _coef_ptr(coef, E)
-    nat.fem_integrate_fwd(m, form, cp, out.data_ptr(), od, opts, _stream_ptr(stream))
+    if det_out is not None:
+        _check_det(det_out, E)
+        nat.fem_integrate_fwd_save(m, form, cp, out.data_ptr(), od, det_out.data_ptr(), opts, _stream_ptr(stream))
+    else:
+        nat.fem_integrate_fwd(m, form, cp, out.data_ptr(), od, opts, _stream_ptr(stream))
     return out
+
+
+def _check_det(det, E):
+    if not (det.is_cuda and det.dtype == torch.float32 and det.is_contiguous() and det.numel() == E):
+        raise ValueError("det must be a contiguous CUDA float32 tensor [E]")
 
 
 def integrate_fwd_iso(coords, conn, mid, form=LAPLACE_P1_ISO, coef=None, out=None, dev_err=None, stream=None):
@@ -177,8 +188,9 @@ class Assembly:
 
 def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None,
                   reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dcoef=True, jac=JAC_AUTO,
-                  warps_per_cta=0, ctas_per_sm=0, dcoords=None, dcoef=None, dev_err=None, stream=None):
-    """fem_integrate_bwd: (dcoords [V][d] or None, dcoef [E] or None) for the upstream dA."""
+                  warps_per_cta=0, ctas_per_sm=0, dcoords=None, dcoef=None, dev_err=None, stream=None, det=None):
+    """fem_integrate_bwd: (dcoords [V][d] or None, dcoef [E] or None) for the upstream dA.
+    det: det J saved by integrate_fwd(det_out=...) (fem_integrate_bwd_saved)."""
     m = _mesh_struct(coords, conn)
     E, V = conn.shape[0], coords.shape[0]
     if dA.dtype != torch.float32 or not dA.is_contiguous():
@@ -198,10 +210,15 @@ def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None
         ws_ptr, ws_bytes = ws.buf.data_ptr(), ws.bytes
     opts = nat.options_struct(jac, 0, reduce, warps_per_cta, ctas_per_sm,
                               dev_err.data_ptr() if dev_err is not None else 0)
-    nat.fem_integrate_bwd(m, form, _coef_ptr(coef, E), dA.data_ptr(),
-                          dcoords.data_ptr() if dcoords is not None else 0,
-                          dcoef.data_ptr() if dcoef is not None else 0, ws_ptr, ws_bytes, opts,
-                          _stream_ptr(stream))
+    dx_ptr = dcoords.data_ptr() if dcoords is not None else 0
+    dw_ptr = dcoef.data_ptr() if dcoef is not None else 0
+    if det is not None:
+        _check_det(det, E)
+        nat.fem_integrate_bwd_saved(m, form, _coef_ptr(coef, E), dA.data_ptr(), det.data_ptr(), dx_ptr, dw_ptr,
+                                    ws_ptr, ws_bytes, opts, _stream_ptr(stream))
+    else:
+        nat.fem_integrate_bwd(m, form, _coef_ptr(coef, E), dA.data_ptr(), dx_ptr, dw_ptr, ws_ptr, ws_bytes, opts,
+                              _stream_ptr(stream))
     return dcoords, dcoef
 
 
@@ -217,7 +234,8 @@ class HostStep:
     host memory, with the host <-> device copies overlapped with the kernels.
 
     run() copies coords, conn and dA in, integrates A = G:K (Eq. 6) and the
-    deterministic adjoint, and copies A and dcoords out.  The elements go in
+    deterministic adjoint (with det J kept from the forward), and copies A and
+    dcoords out.  The elements go in
     slices of `chunk` elements:
 
     * a copy-in stream sends the coordinates, then each slice's connectivity
@@ -244,6 +262,7 @@ class HostStep:
         self.dA = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
         self.A = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
         self.dcoords = torch.empty((n_vert, dim), dtype=torch.float32, device=dev)
+        self.det = torch.empty(n_elem, dtype=torch.float32, device=dev)  # det J, forward -> adjoint
         self.copy_in = torch.cuda.Stream(dev)
         self.copy_out = torch.cuda.Stream(dev)
         self.ws = None  # built on the first run: it depends on the connectivity
@@ -277,7 +296,8 @@ class HostStep:
             self.ws = Workspace(self.coords, self.conn, self.form, main)
         for (e0, e1), ev in zip(slices, arrived):
             main.wait_event(ev)
-            integrate_fwd(self.coords, self.conn[e0:e1], self.form, out=self.A[e0:e1], stream=main)
+            integrate_fwd(self.coords, self.conn[e0:e1], self.form, out=self.A[e0:e1], stream=main,
+                          det_out=self.det[e0:e1])
             done = torch.cuda.Event()
             done.record(main)
             written.append(done)
@@ -287,7 +307,7 @@ class HostStep:
                 A_h[e0:e1].copy_(self.A[e0:e1], non_blocking=True)
         main.wait_stream(self.copy_in)  # every dA slice is in
         integrate_bwd(self.coords, self.conn, self.form, self.dA, ws=self.ws, need_dcoef=False,
-                      dcoords=self.dcoords, stream=main)
+                      dcoords=self.dcoords, stream=main, det=self.det)
         self.copy_out.wait_stream(main)
         with torch.cuda.stream(self.copy_out):
             dcoords_h.copy_(self.dcoords, non_blocking=True)
@@ -298,7 +318,12 @@ class HostStep:
 class _IntegrateFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, coords, coef, mesh, form, jac, reduce):
-        A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac)
+        # det J is kept for the adjoint when it can take it (FP32 coordinates, affine form)
+        keep = (coords.dtype == torch.float32 and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1)
+                and jac in (JAC_AUTO, JAC_COMP_F32))
+        det = torch.empty(mesh.conn.shape[0], dtype=torch.float32, device=coords.device) if keep else None
+        A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac, det_out=det)
+        ctx.det = det
         ctx.save_for_backward(coords, coef if coef is not None else torch.empty(0))
         ctx.mesh, ctx.form, ctx.jac, ctx.reduce = mesh, form, jac, reduce
         ctx.has_coef = coef is not None
@@ -313,7 +338,7 @@ class _IntegrateFn(torch.autograd.Function):
         ws = ctx.mesh.workspace(ctx.form) if (need_x and ctx.reduce == REDUCE_DETERMINISTIC) else None
         dx, dw = integrate_bwd(coords.detach(), ctx.mesh.conn, ctx.form, dA.contiguous().float(), coef,
                                ws=ws, reduce=ctx.reduce, need_dcoords=need_x, need_dcoef=need_w,
-                               jac=ctx.jac)
+                               jac=ctx.jac, det=ctx.det)
         return dx, dw, None, None, None, None
 
 

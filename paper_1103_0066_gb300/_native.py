@@ -27,7 +27,8 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
-           "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso")
+           "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
+           "fem_integrate_bwd_saved")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM = 0, 1, 2, 3
 DEVERR_TIMEOUT = 4
@@ -82,6 +83,8 @@ def load():
             "fem_reference_tensor": ([I32, I32, P, SZ], ctypes.c_int),
             "fem_integrate_fwd": ([MP, I32, P, P, I32, OP, P], ctypes.c_int),
             "fem_integrate_fwd_iso": ([MP, I32, P, P, P, OP, P], ctypes.c_int),
+            "fem_integrate_fwd_save": ([MP, I32, P, P, I32, P, OP, P], ctypes.c_int),
+            "fem_integrate_bwd_saved": ([MP, I32, P, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
             "fem_geometry": ([MP, P, OP, P, P, P], ctypes.c_int),
             "fem_bwd_workspace_size": ([MP, I32, OP, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
@@ -152,6 +155,12 @@ def fem_integrate_fwd(mesh: FemMesh, form: int, coef_ptr: int, A_ptr: int, out_d
                                    out_dtype, ctypes.byref(opts), stream or None))
 
 
+def fem_integrate_fwd_save(mesh: FemMesh, form: int, coef_ptr: int, A_ptr: int, out_dtype: int, det_ptr: int,
+                           opts: FemOptions, stream: int) -> None:
+    check(load().fem_integrate_fwd_save(ctypes.byref(mesh), form, coef_ptr or None, A_ptr or None, out_dtype,
+                                        det_ptr or None, ctypes.byref(opts), stream or None))
+
+
 def fem_integrate_fwd_iso(mesh: FemMesh, form: int, mid_ptr: int, coef_ptr: int, A_ptr: int, opts: FemOptions,
                           stream: int) -> None:
     check(load().fem_integrate_fwd_iso(ctypes.byref(mesh), form, mid_ptr or None, coef_ptr or None, A_ptr or None,
@@ -184,6 +193,13 @@ def fem_integrate_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoo
 def fem_adjoint_reduce(mesh: FemMesh, ws_ptr: int, ws_bytes: int, dcoords_ptr: int, stream: int) -> None:
     check(load().fem_adjoint_reduce(ctypes.byref(mesh), ws_ptr or None, ws_bytes, dcoords_ptr or None,
                                     stream or None))
+
+
+def fem_integrate_bwd_saved(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, det_ptr: int, dcoords_ptr: int,
+                            dcoef_ptr: int, ws_ptr: int, ws_bytes: int, opts: FemOptions, stream: int) -> None:
+    check(load().fem_integrate_bwd_saved(ctypes.byref(mesh), form, coef_ptr or None, dA_ptr or None, det_ptr or None,
+                                         dcoords_ptr or None, dcoef_ptr or None, ws_ptr or None, ws_bytes,
+                                         ctypes.byref(opts), stream or None))
 
 
 def fem_integrate_bwd_noalloc(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoords_ptr: int,

@@ -150,8 +150,8 @@ fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K, size_t ca
   return ok();
 }
 
-fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
-                             int32_t out_dtype, const fem_options* options, void* stream) {
+static fem_status integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A, int32_t out_dtype,
+                                float* det_out, const fem_options* options, void* stream) {
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
@@ -186,6 +186,7 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
   L.warps = o->warps_per_cta;  // 0: the kernel's default
   L.ctas_per_sm = o->ctas_per_sm;
   L.stream = static_cast<cudaStream_t>(stream);
+  L.det_out = det_out;
   cudaError_t e;
   if (tc)
     e = fem::launch_fwd_tc(L);
@@ -199,6 +200,22 @@ fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* co
     e = fem::launch_fwd_d3_lap(L);
   if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_fwd launch");
   return ok();
+}
+
+fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A, int32_t out_dtype,
+                             const fem_options* options, void* stream) {
+  return integrate_fwd(mesh, form, coef, A, out_dtype, nullptr, options, stream);
+}
+
+fem_status fem_integrate_fwd_save(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
+                                  int32_t out_dtype, float* det, const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  const fem_options* o = options ? options : &kDefaults;
+  if (o->contract != FEM_CONTRACT_F32)
+    return fail(FEM_ERR_UNSUPPORTED, "fem_integrate_fwd_save contracts in FP32");
+  if (mesh->n_elem > 0 && !det) return fail(FEM_ERR_ARG, "det is NULL");
+  return integrate_fwd(mesh, form, coef, A, out_dtype, det, options, stream);
 }
 
 fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef, float* A,
@@ -293,9 +310,9 @@ fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, 
   return ok();
 }
 
-fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
-                             float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
-                             const fem_options* options, void* stream) {
+static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
+                                const float* det_in, float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
+                                const fem_options* options, void* stream) {
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
@@ -348,6 +365,7 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     L.warps = o->warps_per_cta;
     L.ctas_per_sm = o->ctas_per_sm;
     L.stream = st;
+    L.det_in = det_in;
     e = fem::launch_bwd_elem(L);
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd element launch");
   }
@@ -356,6 +374,21 @@ fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* co
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd reduction launch");
   }
   return ok();
+}
+
+fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
+                             float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
+                             const fem_options* options, void* stream) {
+  return integrate_bwd(mesh, form, coef, dA, nullptr, dcoords, dcoef, ws, ws_bytes, options, stream);
+}
+
+fem_status fem_integrate_bwd_saved(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
+                                   const float* det, float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
+                                   const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (mesh->n_elem > 0 && !det) return fail(FEM_ERR_ARG, "det is NULL");
+  return integrate_bwd(mesh, form, coef, dA, det, dcoords, dcoef, ws, ws_bytes, options, stream);
 }
 
 fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes, float* dcoords,

@@ -23,6 +23,7 @@ static cudaError_t launch_bwd_t(const BwdLaunch& L) {
   p.dev_err = L.dev_err;
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_dA = reinterpret_cast<uintptr_t>(L.dA) % 16 == 0;
+  p.det = L.det_in;
   auto kern = fem_bwd_elem_kernel<D, FORM, JAC, ATOMIC>;
   constexpr int max_warps = BwdShape<D, FORM, JAC>::threads / 32;  // the kernel's launch bounds
   const int want = L.warps > 0 ? L.warps : max_warps;
@@ -37,6 +38,8 @@ static cudaError_t launch_bwd_t(const BwdLaunch& L) {
 
 template <int D, int FORM>
 static cudaError_t launch_bwd_form(const BwdLaunch& L) {
+  if (L.det_in)  // det J saved by the forward
+    return L.atomic ? launch_bwd_t<D, FORM, JAC_SAVED, true>(L) : launch_bwd_t<D, FORM, JAC_SAVED, false>(L);
   switch (L.jac) {
     case JAC_COMP:
       return L.atomic ? launch_bwd_t<D, FORM, JAC_COMP, true>(L) : launch_bwd_t<D, FORM, JAC_COMP, false>(L);

@@ -73,6 +73,7 @@ struct BwdParams {
   int32_t* dev_err;
   int vec_conn;
   int vec_dA;
+  const float* det = nullptr;  // [n_elem] det J saved by the forward (JAC_SAVED)
 };
 
 template <int D, int FORM>
@@ -102,7 +103,7 @@ struct BwdPlan {
 // other instantiations keep 4-warp CTAs and the compiler's register choice.
 template <int D, int FORM, int JAC>
 struct BwdShape {
-  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && JAC == JAC_COMP);
+  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && (JAC == JAC_COMP || JAC == JAC_SAVED));
   static constexpr int threads = tight ? 32 : kTileElems;
   static constexpr int min_ctas = tight ? 24 : 1;
 };
@@ -253,7 +254,8 @@ __device__ __forceinline__ void warp_records(const float* xs, const uint16_t* re
 template <int D, int FORM, int JAC, bool ATOMIC>
 __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags, float w,
                                                 const float (&X)[D + 1][D], const float* drow,
-                                                const int (&vc)[D + 1], float* xs, uint32_t rk) {
+                                                const int (&vc)[D + 1], float* xs, uint32_t rk,
+                                                float det_saved = 0.f) {
   using FT = FormTraits<D, FORM>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
   constexpr int N = FT::N, NV = FT::NV;
@@ -268,7 +270,12 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
   bool ok = false;
   if (flags & GF_OK) {
     Jac<D, GT> jac;
-    if (!jacobian<D, JAC>(X, jac)) {
+    bool nondeg;
+    if constexpr (JAC == JAC_SAVED)
+      nondeg = jacobian_saved<D>(X, det_saved, jac);
+    else
+      nondeg = jacobian<D, JAC>(X, jac);
+    if (!nondeg) {
       err |= DEVERR_DEGENERATE;
     } else {
       ok = true;
@@ -414,6 +421,8 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
   copy_dA_async<D, FORM>(p, t, lane, dslots);
   float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  float dcur = 0.f;  // saved det J (JAC_SAVED)
+  if constexpr (JAC == JAC_SAVED) dcur = t * 32 + lane < p.n_elem ? __ldg(p.det + t * 32 + lane) : 0.f;
   uint32_t rkcur = 0;
   int32_t rb = 0, rn = 0;  // first record and record count of tile t
   if (rec) {
@@ -432,6 +441,8 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
     copy_dA_async<D, FORM>(p, tn, lane, dslots + sn * 32 * PL::DST);
     const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+    float dnext = 0.f;
+    if constexpr (JAC == JAC_SAVED) dnext = en < p.n_elem ? __ldg(p.det + en) : 0.f;
     uint32_t rknext = 0;
     int32_t rbn = 0, rnn = 0;
     if (rec && tn < ntiles) {
@@ -445,7 +456,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     cp_async_wait<1>();
     __syncwarp();  // dA rows were copied by other lanes
     err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslots + (sc * 32 + lane) * PL::DST,
-                                                  vc, rec ? xs : nullptr, rkcur);
+                                                  vc, rec ? xs : nullptr, rkcur, dcur);
     if (rec) {
       __syncwarp();  // every lane's contributions are staged
       warp_records<D>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
@@ -453,6 +464,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     __syncwarp();  // the slot stage is rewritten next tile, the dA slot two tiles later
     fcur = fnext;
     wcur = wnext;
+    dcur = dnext;
     rkcur = rknext;
     rb = rbn;
     rn = rnn;

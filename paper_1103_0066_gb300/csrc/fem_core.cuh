@@ -20,6 +20,9 @@
 //              For sliver elements det J cancels catastrophically in plain FP32;
 //              this keeps its relative error near (few eps^2) / (height ratio).
 //   JAC_F32  : plain FP32 (for error studies).
+//   JAC_SAVED: the adjoint with det J saved by the forward: FP32 edge vectors
+//              and adjugate (the hi parts of the compensated mode), det J as
+//              given.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -29,7 +32,7 @@
 
 namespace fem {
 
-enum JacMode : int { JAC_F64 = 1, JAC_COMP = 2, JAC_F32 = 3 };
+enum JacMode : int { JAC_F64 = 1, JAC_COMP = 2, JAC_F32 = 3, JAC_SAVED = 4 };
 enum DevErr : int { DEVERR_CONN = 1, DEVERR_DEGENERATE = 2, DEVERR_TIMEOUT = 4 };
 
 // ---------------------------------------------------------------- error-free transforms
@@ -65,6 +68,15 @@ struct Jac {
   double det_hp; // det J to the precision the mode reaches (double-float value in JAC_COMP)
 };
 
+// x * y - z * w with the rounding spelled out (one product rounded, then a
+// fused multiply-add), so that every kernel forms the same bits.
+__device__ __forceinline__ float cross_term(float x, float y, float z, float w) {
+  return __fmaf_rn(x, y, -__fmul_rn(z, w));
+}
+__device__ __forceinline__ double cross_term(double x, double y, double z, double w) {
+  return __fma_rn(x, y, -__dmul_rn(z, w));
+}
+
 // adjugate rows from edge vectors (d det / d e_mu = adj[mu])
 template <class GT>
 __device__ __forceinline__ void adjugate(const GT (&e)[3][3], GT (&adj)[3][3]) {
@@ -72,9 +84,9 @@ __device__ __forceinline__ void adjugate(const GT (&e)[3][3], GT (&adj)[3][3]) {
   for (int mu = 0; mu < 3; ++mu) {
     const GT* a = e[(mu + 1) % 3];
     const GT* b = e[(mu + 2) % 3];
-    adj[mu][0] = a[1] * b[2] - a[2] * b[1];
-    adj[mu][1] = a[2] * b[0] - a[0] * b[2];
-    adj[mu][2] = a[0] * b[1] - a[1] * b[0];
+    adj[mu][0] = cross_term(a[1], b[2], a[2], b[1]);
+    adj[mu][1] = cross_term(a[2], b[0], a[0], b[2]);
+    adj[mu][2] = cross_term(a[0], b[1], a[1], b[0]);
   }
 }
 template <class GT>
@@ -157,6 +169,20 @@ __device__ __forceinline__ bool jacobian(const CT (&X)[D + 1][D], Jac<D, GT>& j)
     j.det_hp = double(p) + (double(err) + double(corr));
     return det != 0.f;
   }
+}
+
+// Edge vectors and adjugate in FP32 with det J given (saved by the forward);
+// false when det J == 0.
+template <int D>
+__device__ __forceinline__ bool jacobian_saved(const float (&X)[D + 1][D], float det, Jac<D, float>& j) {
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+    for (int a = 0; a < D; ++a) j.e[mu][a] = __fsub_rn(X[mu + 1][a], X[0][a]);
+  adjugate(j.e, j.adj);
+  j.det = det;
+  j.det_hp = double(det);
+  return det != 0.f;
 }
 
 // ---------------------------------------------------------------- geometric tensor

@@ -37,6 +37,7 @@ struct FwdParams {
   int32_t* dev_err;
   int vec_conn;   // conn rows are 16-byte aligned int4 (tets)
   int vec_store;  // A is 16-byte aligned
+  float* det_out = nullptr;  // [n_elem] det J saved for the adjoint, or null
 };
 
 template <int NN>
@@ -290,6 +291,7 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
     Jac<D, GT> jac;
     const bool nondeg = jacobian<D, JAC>(X, jac);
     err |= nondeg ? 0 : DEVERR_DEGENERATE;
+    if (p.det_out) __stcs(p.det_out + tile * 32 + lane, float(jac.det));
     const float w0 = FT::W1 ? 1.f : w.v[0];  // a P1 coefficient multiplies the slots below
     GT scale;  // zero for a degenerate element: its matrix is written as zeros
     if constexpr (sizeof(GT) == 4)
@@ -304,6 +306,7 @@ __device__ __forceinline__ int fwd_compute_tile(const FwdParams<CT, OT>& p, int6
       for (int g = 0; g < FT::NGB; ++g) Gf[k * FT::NGB + g] = OT(FT::W1 ? GT(w.v[k]) * Gt[g] : Gt[g]);
   } else if (flags & GF_ELEM) {
     err |= DEVERR_CONN;
+    if (p.det_out) __stcs(p.det_out + tile * 32 + lane, 0.f);
   }
   fwd_contract_store<D, FORM, CT, OT, TMA>(p, tile, lane, Gf, st, tmap);
   return err;
@@ -386,6 +389,7 @@ cudaError_t launch_fwd_t(const FwdLaunch& L) {
   p.dev_err = L.dev_err;
   p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
   p.vec_store = (reinterpret_cast<uintptr_t>(L.A) % 16 == 0);
+  p.det_out = L.det_out;
   CUtensorMap tmap{};
   bool tma = false;
   auto kern = fem_fwd_kernel<D, FORM, JAC, CT, OT, false>;

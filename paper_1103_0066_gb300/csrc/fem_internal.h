@@ -19,6 +19,7 @@ struct FwdLaunch {
   int32_t* dev_err;
   int warps, ctas_per_sm;
   cudaStream_t stream;
+  float* det_out = nullptr;  // det J saved for the adjoint (fem_fwd_kernel only)
 };
 
 struct GeoLaunch {
@@ -61,6 +62,7 @@ struct BwdLaunch {
   int32_t* dev_err;
   int warps, ctas_per_sm;  // warps <= 0: the default
   cudaStream_t stream;
+  const float* det_in = nullptr;  // det J saved by the forward: the JAC_SAVED element pass
 };
 
 // Workspace of the deterministic adjoint (see fem_incidence.cu):

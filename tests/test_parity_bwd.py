@@ -198,3 +198,35 @@ def test_full_adjoint_64_cube(gfem, orc):
         dx, dw = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), ws=ws, reduce=reduce)
         assert _rel(dx.cpu().numpy(), gx) <= TOL
         assert _rel(dw.cpu().numpy(), gw) <= TOL
+
+
+@pytest.mark.parametrize("dim,form", [(3, LP1), (3, EP1), (2, LP1), (3, LP2)])
+def test_saved_det_is_bitwise_the_same(gfem, dim, form):
+    """fem_integrate_fwd_save returns the same A plus det J; the adjoint with
+    that det (fem_integrate_bwd_saved) equals fem_integrate_bwd bit for bit
+    (dcoef always; dcoords with the deterministic reduction, and to rounding
+    with the atomic one, whose order varies from run to run), and det J is
+    the compensated determinant of the geometry hook (its double-float value)
+    to within one FP32 rounding."""
+    mesh = _mesh(dim)
+    n = {LP1: dim + 1, LP2: (dim + 1) * (dim + 2) // 2, EP1: dim * (dim + 1)}[form]
+    coef = _t(mg.lognormal_coef(mg.rng_for(61), mesh.n_elem))
+    dA = _t(mg.upstream(mg.rng_for(62), mesh.n_elem, n))
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    det = torch.empty(mesh.n_elem, device="cuda")
+    A0 = gfem.integrate_fwd(coords, conn, form, coef)
+    A1 = gfem.integrate_fwd(coords, conn, form, coef, det_out=det)
+    assert torch.equal(A0, A1)
+    dref, _ = gfem.geometry(coords, conn)
+    assert torch.all((det.double() - dref).abs() <= 2.0 ** -23 * dref.abs())
+    ws = gfem.Workspace(coords, conn)
+    for reduce in (0, 1):
+        a = gfem.integrate_bwd(coords, conn, form, dA, coef, ws=ws, reduce=reduce)
+        b = gfem.integrate_bwd(coords, conn, form, dA, coef, ws=ws, reduce=reduce, det=det)
+        assert torch.equal(a[1], b[1])
+        if reduce == 0:
+            assert torch.equal(a[0], b[0])
+        else:
+            assert _rel(b[0].cpu().numpy(), a[0].cpu().numpy().astype(np.float64)) <= 1e-6
+    with pytest.raises(ValueError):
+        gfem.integrate_bwd(coords, conn, form, dA, coef, det=det[:-1])
