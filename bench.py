@@ -40,7 +40,7 @@ FALLBACK_HBM_GBS = 6800.0
 KERNEL_SOURCES = {
     "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": ("fem_fwd.cuh", "fem_fwd_d3_lap.cu", "fem_core.cuh", "fem_forms.cuh",
                                               "fem_pipe.cuh", "fem_internal.h", "fem_geometry.cu"),
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": ("fem_bwd.cuh", "fem_bwd.cu", "fem_fwd.cuh", "fem_core.cuh",
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": ("fem_bwd.cuh", "fem_bwd.cu", "fem_fwd.cuh", "fem_core.cuh",
                                                    "fem_forms.cuh", "fem_pipe.cuh", "fem_internal.h",
                                                    "fem_geometry.cu"),
     "vertex_reduce_kernel<3>": ("fem_incidence.cu", "fem_internal.h"),
@@ -50,9 +50,9 @@ KERNEL_SOURCES = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1281.4e6, "src": "f65a6a9b6a41e47b"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 983.0e6, "src": "34ee1eacc17e71c8"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.7e6, "src": "0e7a977875b65b8a"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1350.7e6, "src": "4580434c0d808b7b"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1d5b65641d781b93"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.4e6, "src": "09b6b11fb5543c5b"},
     # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
     "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2394.4e6, "src": "481d084af2a808db"},
 }
@@ -295,7 +295,7 @@ def run_ours(args):
     byts = algorithmic_bytes(E, V, R, 4, 3, False)
     peak, peak_kind = hbm_peak()
     dom = max(per, key=per.get)
-    kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_COMP>",
+    kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>",
              "reduce": "vertex_reduce_kernel<3>"}
     h = {k: kernel_src_hash(v) for k, v in kname.items()}
     traffic = ncu_traffic(kname[dom])  # valid only for the sources it was captured with
@@ -346,8 +346,8 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"3D P1 Laplacian, {args.mesh_n}^3 Kuhn cube, 6 tets/cell, jitter 0.15h, "
                                f"5% slivers ({E:,} tets, {V:,} vertices); FP32 coords and 4x4 FP32 element "
-                               "matrices, compensated-FP32 Jacobian; step = forward + adjoint "
-                               "(deterministic segmented reduction), dA ~ N(0,1)",
+                               "matrices, compensated-FP32 Jacobian; step = forward (saving det J) + "
+                               "adjoint (deterministic segmented reduction), dA ~ N(0,1)",
                    "elements": E, "vertices": V, "form": "laplace_p1", "dim": 3,
                    "l2": "no flush: inputs/outputs (~2.7 GB per step) far exceed the 129 MB L2",
                    "parallelism": f"{ws_n} independent replicas (elements shard with no collective)"},
