@@ -230,3 +230,25 @@ def test_saved_det_is_bitwise_the_same(gfem, dim, form):
             assert _rel(b[0].cpu().numpy(), a[0].cpu().numpy().astype(np.float64)) <= 1e-6
     with pytest.raises(ValueError):
         gfem.integrate_bwd(coords, conn, form, dA, coef, det=det[:-1])
+
+
+@pytest.mark.parametrize("reduce", [0, 1])
+def test_adjoint_device_errors(gfem, orc, reduce):
+    """An element with an out-of-range vertex (FEM_DEVERR_CONN) and one with a
+    repeated vertex (det J = 0, FEM_DEVERR_DEGENERATE) contribute nothing:
+    dcoef is 0 there, and dcoords equals the oracle's reverse mode over the
+    other elements, for both reductions."""
+    mesh = _mesh(3)
+    conn = mesh.conn.copy()
+    conn[5, 2] = mesh.n_vert + 3
+    conn[9, 1] = conn[9, 0]
+    coef = mg.lognormal_coef(mg.rng_for(63), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(64), mesh.n_elem, 4)
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    dx, dw = gfem.integrate_bwd(_t(mesh.coords), _t(conn), LP1, _t(dA), _t(coef), reduce=reduce, dev_err=err)
+    assert int(err.item()) == gfem.DEVERR_CONN | gfem.DEVERR_DEGENERATE
+    keep = np.setdiff1d(np.arange(mesh.n_elem), [5, 9])
+    gx, gw = orc.integrate_vjp(3, LP1, mesh.conn[keep], mesh.coords, dA[keep], coef[keep])
+    assert _rel(dx.cpu().numpy(), gx) <= TOL
+    dwh = dw.cpu().numpy()
+    assert dwh[5] == 0 and dwh[9] == 0 and _rel(dwh[keep], gw) <= TOL
