@@ -135,14 +135,18 @@ __device__ __forceinline__ void put_all(Sink& sink, const float* acc, std::integ
   (sink.template put<tri_row(Ts, FT::N), tri_col(Ts, FT::N)>(acc[Ts]), ...);
 }
 
-// CTA shape: warps never wait for one another.  The 3D P1 form runs one-warp
+// CTA shape: warps never wait for one another, so the CTA size only sets how
+// finely the register file is shared out.  On tets the P1 form runs one-warp
 // CTAs with at least 20 resident per SM, which holds it to 96 registers
-// without spills (21 warps per SM against 16 at 128 registers).
+// without spills (21 warps per SM against 16 at 128 registers); the P2 form
+// with at least 16, which holds its 55 accumulators and four inverse
+// Jacobians to 128 registers without spills (16 warps per SM, against 8 at
+// the 245 registers it takes unbounded).
 template <int D, int FORM>
 struct IsoShape {
-  static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1_ISO);
+  static constexpr bool tight = (D == 3);
   static constexpr int threads = tight ? 32 : 128;
-  static constexpr int min_ctas = tight ? 20 : 1;
+  static constexpr int min_ctas = tight ? (FORM == LAPLACE_P1_ISO ? 20 : 16) : 1;
 };
 
 template <int D, int FORM>
