@@ -875,11 +875,13 @@ def run_iso(args):
     stream = torch.cuda.current_stream(dev)
     peak, peak_kind = hbm_peak()
     res = {}
-    for name, form, n in (("p1", fem.LAPLACE_P1_ISO, 4), ("p2", fem.LAPLACE_P2_ISO, 10)):
+    for name, form, n, contract in (("p1", fem.LAPLACE_P1_ISO, 4, fem.CONTRACT_F32),
+                                    ("p2", fem.LAPLACE_P2_ISO, 10, fem.CONTRACT_F32),
+                                    ("p2_tensor_core", fem.LAPLACE_P2_ISO, 10, fem.CONTRACT_BF16X3)):
         A = torch.empty((E, n, n), device=dev)
 
         def step():
-            fem.integrate_fwd_iso(coords, conn, mid, form, out=A)
+            fem.integrate_fwd_iso(coords, conn, mid, form, out=A, contract=contract)
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
@@ -905,13 +907,14 @@ def run_iso(args):
            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": r["ms"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"Laplacian on quadratic-geometry tets (Eqs. 16-19): {args.mesh_n}^3 jittered "
-                                  f"cube warped by a smooth map ({E:,} tets), P1 and P2, FP32, forward",
+                                  f"cube warped by a smooth map ({E:,} tets), P1 and P2 (FP32 contraction; P2 also "
+                                  "split-BF16 on the tensor cores), forward",
                       "elements": E, "l2": "no flush"},
            "roofline": {"bound": "hbm", "kernel": "fem_fwd_iso_kernel<3,LAPLACE_P1_ISO>", "achieved": r["GB/s"],
                         "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],
                         "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                         "algorithmic_bytes": r["algorithmic_bytes"]},
-           "paths": res, "gpu_launches": 2 * args.steps}
+           "paths": res, "gpu_launches": 3 * args.steps}
     print(json.dumps(out), flush=True)
 
 

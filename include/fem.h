@@ -166,9 +166,12 @@ FEM_API fem_status fem_integrate_fwd_save(const fem_mesh* mesh, int32_t form, co
  * is |det J| at the centroid, so G^{(k mu),(l nu)} = w |J| J^{-1}_{mu a,k}
  * J^{-1}_{nu a,l} is contracted with K^{ij}_{(k mu),(l nu)} = int_ref lambda_k
  * lambda_l d_mu phi_i d_nu phi_j (Eqs. 18-19).  The Jacobian steps run in
- * plain FP32 (options->jac FEM_JAC_AUTO or FEM_JAC_F32).  coef: [n_elem] or
- * NULL; A: [n_elem][n][n] FP32.  Straight-sided elements (mid at the edge
- * midpoints) give the affine result. */
+ * plain FP32 (options->jac FEM_JAC_AUTO or FEM_JAC_F32).  The contraction is
+ * FP32 (FEM_CONTRACT_F32), or for FEM_LAPLACE_P2_ISO split-BF16 on the tensor
+ * cores (FEM_CONTRACT_BF16X3: G in three BF16 terms, K exact, FP32
+ * accumulation).  coef: [n_elem] or NULL; A: [n_elem][n][n] FP32.
+ * Straight-sided elements (mid at the edge midpoints) give the affine
+ * result. */
 FEM_API fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef,
                                          float* A, const fem_options* options, void* stream);
 

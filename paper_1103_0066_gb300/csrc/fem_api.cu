@@ -228,7 +228,9 @@ fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float
   if ((s = check_options(o)) != FEM_OK) return s;
   if (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F32)
     return fail(FEM_ERR_UNSUPPORTED, "non-affine elements compute their Jacobians in FP32");
-  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "non-affine elements contract in FP32");
+  const bool tc = o->contract == FEM_CONTRACT_BF16X3;
+  if (o->contract != FEM_CONTRACT_F32 && !(tc && form == FEM_LAPLACE_P2_ISO))
+    return fail(FEM_ERR_UNSUPPORTED, "non-affine elements contract in FP32, or P2 on the tensor cores (BF16X3)");
   if (mesh->n_elem == 0) return ok();
   if (!A || !mid) return fail(FEM_ERR_ARG, "A or mid is NULL");
   fem::FwdLaunch L{};
@@ -244,7 +246,7 @@ fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, const float
   L.dev_err = o->dev_err;
   L.ctas_per_sm = o->ctas_per_sm;
   L.stream = static_cast<cudaStream_t>(stream);
-  cudaError_t e = fem::launch_fwd_iso(L, mid);
+  cudaError_t e = tc ? fem::launch_fwd_iso_tc(L, mid) : fem::launch_fwd_iso(L, mid);
   if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_fwd_iso launch");
   return ok();
 }

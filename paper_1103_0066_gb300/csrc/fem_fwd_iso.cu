@@ -20,78 +20,11 @@
 // elements; an element with a singular J at a vertex or at the centroid is
 // flagged degenerate and gets A = 0.
 #include "fem_fwd.cuh"
+#include "fem_iso.cuh"
 
 namespace fem {
 
 namespace {
-
-// d psi_a / d xi_mu of the quadratic geometry basis (vertices, then edges in
-// the P2 order) at reference vertex k (k <= D), or (D + 1) times it at the
-// centroid (k = D + 1); all integers.
-template <int D>
-constexpr int geo_dpsi(int a, int mu, int k) {
-  if (a <= D) {
-    if (k <= D) return (a == k ? 3 : -1) * dlam(a, mu);
-    return (3 - D) * dlam(a, mu);  // (D+1) * (4/(D+1) - 1)
-  }
-  int t = a - (D + 1);
-  for (int p = 0; p <= D; ++p)
-    for (int q = p + 1; q <= D; ++q) {
-      if (t == 0) {
-        if (k <= D) return 4 * ((p == k ? dlam(q, mu) : 0) + (q == k ? dlam(p, mu) : 0));
-        return 4 * (dlam(p, mu) + dlam(q, mu));
-      }
-      --t;
-    }
-  return 0;
-}
-
-constexpr int n_geo(int D) { return (D + 1) * (D + 2) / 2; }
-
-// e[mu][al] = sum_a geo_dpsi(a, mu, K) * node_a[al] with node 0 at the origin.
-template <int D, int K>
-__device__ __forceinline__ void geo_jacobian(const float (&nd)[n_geo(D)][D], float (&e)[D][D]) {
-#pragma unroll
-  for (int mu = 0; mu < D; ++mu)
-#pragma unroll
-    for (int al = 0; al < D; ++al) {
-      float s = 0.f;
-#pragma unroll
-      for (int a = 1; a < n_geo(D); ++a) {
-        const int c = geo_dpsi<D>(a, mu, K);
-        if (c != 0) s = fmaf(float(c), nd[a][al], s);
-      }
-      e[mu][al] = s;
-    }
-}
-
-template <int D>
-__device__ __forceinline__ float det_adj(const float (&e)[D][D], float (&adj)[D][D]) {
-  adjugate(e, adj);
-  float det = 0.f;
-#pragma unroll
-  for (int al = 0; al < D; ++al) det = fmaf(e[0][al], adj[0][al], det);
-  return det;
-}
-
-template <int D, int K>
-__device__ __forceinline__ bool vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D]) {
-  float e[D][D], adj[D][D];
-  geo_jacobian<D, K>(nd, e);
-  const float det = det_adj<D>(e, adj);
-  const float r = __frcp_rn(det);
-#pragma unroll
-  for (int mu = 0; mu < D; ++mu)
-#pragma unroll
-    for (int al = 0; al < D; ++al) ji[K][mu][al] = adj[mu][al] * r;  // (J^{-1})_{mu al} at vertex K
-  return det != 0.f;
-}
-
-template <int D, int... Ks>
-__device__ __forceinline__ bool all_vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D],
-                                                std::integer_sequence<int, Ks...>) {
-  return (vertex_jinv<D, Ks>(nd, ji) & ...);
-}
 
 // acc[T] += K'[G][T] * gv over the unique entries T of A (zero terms generate no code).
 template <int D, int FORM, int G, int T>
@@ -170,28 +103,9 @@ __global__ void __launch_bounds__(IsoShape<D, FORM>::threads, IsoShape<D, FORM>:
     float scale = 0.f;
     bool ok = false;
     if (flags & GF_OK) {
-      float nd[n_geo(D)][D];  // geometry nodes relative to vertex 0
-#pragma unroll
-      for (int a = 0; a <= D; ++a)
-#pragma unroll
-        for (int al = 0; al < D; ++al) nd[a][al] = X[a][al] - X[0][al];
-      const float* m = mid + e * (NE * D);
-#pragma unroll
-      for (int q = 0; q < NE; ++q)
-#pragma unroll
-        for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = __ldcs(m + q * D + al) - X[0][al];
-      ok = all_vertex_jinv<D>(nd, ji, std::make_integer_sequence<int, D + 1>{});
-      float ec[D][D], adjc[D][D];
-      geo_jacobian<D, D + 1>(nd, ec);  // (D + 1) J at the centroid
-      float detc = det_adj<D>(ec, adjc);
-      detc *= D == 2 ? (1.f / 9.f) : (1.f / 64.f);  // det scales by (D + 1)^D
-      ok &= detc != 0.f;
-      if (!ok) {
-        err |= DEVERR_DEGENERATE;
-      } else {
-        const float w = (p.coef && e < p.n_elem) ? __ldg(p.coef + e) : 1.f;
-        scale = w * fabsf(detc) * (1.f / float(FT::DEN));
-      }
+      const float w = (p.coef && e < p.n_elem) ? __ldg(p.coef + e) : 1.f;
+      ok = iso_geometry<D, FORM>(X, mid + e * (NE * D), w, ji, scale);
+      if (!ok) err |= DEVERR_DEGENERATE;
     } else if (flags & GF_ELEM) {
       err |= DEVERR_CONN;
     }

@@ -93,6 +93,8 @@ cudaError_t launch_fwd_d3_ela(const FwdLaunch& L);
 cudaError_t launch_fwd_tc(const FwdLaunch& L);  // split-bf16 tensor-core contraction
 cudaError_t launch_fwd_w1(const FwdLaunch& L);  // Laplacian with a P1 (vertex) coefficient
 cudaError_t launch_fwd_iso(const FwdLaunch& L, const float* mid);  // non-affine (quadratic-geometry) elements
+// The P2 non-affine forward with the tensor-core contraction (fem_tc_iso.cu).
+cudaError_t launch_fwd_iso_tc(const FwdLaunch& L, const float* mid);
 cudaError_t launch_geometry(const GeoLaunch& L);
 cudaError_t launch_bwd_elem(const BwdLaunch& L);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,

@@ -1,0 +1,380 @@
+// fem_tc.cuh -- forward integration with the G:K contraction on the 5th-generation
+// tensor cores (tcgen05, TMEM accumulators) in split-BF16 arithmetic.
+//
+// Per CTA tile of 128 elements (one element per thread) the contraction of
+// Eq. 6 is the dense product  D[e][t] = sum_k Ahat[e][k] B[k][t]  where
+//   t = (i, j), i <= j, runs over the unique entries of A_e (NT of them,
+//       padded to N, a multiple of 16),
+//   Ahat[e] = [ g1 | g2 | g3 ]: the folded geometric tensor G_e split exactly
+//       into three bf16 terms, g1 = bf16(G), g2 = bf16(G - g1),
+//       g3 = bf16(G - g1 - g2) (|G - g1 - g2 - g3| <= 2^-27 |G|), each term
+//       zero-padded to KT, a multiple of 16 (K = 3 KT),
+//   B[k][t] = K'[k mod KT][i][j] * DEN, small integers, exact in bf16.
+// The MMA (tcgen05.mma kind::f16, M = 128, N, K = 16 per step, FP32
+// accumulation in TMEM) is issued by one thread; its completion is signalled
+// on an mbarrier.  Each warp then reads its 32 rows of D with tcgen05.ld
+// (lane = element), mirrors (i, j) -> (j, i) into its shared-memory stage and
+// stores the tile with coalesced 16-byte stores, as the FP32 kernel does.
+// Operands live in shared memory in the canonical no-swizzle K-major layout:
+// 8x16-byte core matrices, K-adjacent cores LBO bytes apart, M/N-adjacent cores
+// SBO bytes apart.  All waits are bounded: on a timeout the kernel flags
+// FEM_DEVERR_TIMEOUT, stops, waits (bounded) for the tensor core and frees TMEM.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "fem_core.cuh"
+#include "fem_fwd.cuh"
+#include "fem_internal.h"
+#include "fem_pipe.cuh"
+
+namespace fem {
+
+template <int D, int FORM>
+struct TcPlan {
+  using FT = FormTraits<D, FORM>;
+  static constexpr int M = kTileElems;                   // 128 rows (elements)
+  static constexpr int NT = FT::NT;                      // unique outputs
+  static constexpr int N = (NT + 15) / 16 * 16;          // MMA N
+  static constexpr int KT = (FT::NG + 15) / 16 * 16;     // one bf16 term of G, padded
+  static constexpr int K = 3 * KT;
+  static constexpr int KSTEPS = K / 16;
+  static constexpr int MC = M / 8, NC = N / 8, KC = K / 8;  // core-matrix counts
+  static constexpr uint32_t A_LBO = MC * 128, A_SBO = 128;  // A cores: (kc * MC + mc) * 128
+  static constexpr uint32_t B_LBO = NC * 128, B_SBO = 128;  // B cores: (kc * NC + nc) * 128
+  static constexpr size_t a_bytes = size_t(M) * K * 2;
+  static constexpr size_t b_bytes = size_t(N) * K * 2;
+  static constexpr int SST = stage_stride<FT::NN>();
+  static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);  // aliases the A tile
+  static constexpr size_t region_bytes = stage_bytes > a_bytes ? stage_bytes : align_up(a_bytes, 128);
+  static constexpr size_t smem = align_up(b_bytes, 128) + region_bytes + 128;     // + mbarrier, TMEM slot
+  static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  static_assert(N >= 16 && N <= 256 && K % 16 == 0, "MMA shape");
+};
+
+// ------------------------------------------------------------------ tcgen05 / mbarrier
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFF) >> 4);          // bits  0-13 start address
+  d |= uint64_t((lbo >> 4) & 0x3FFF) << 16;       // bits 16-29 leading (K) byte offset
+  d |= uint64_t((sbo >> 4) & 0x3FFF) << 32;       // bits 32-45 stride (M/N) byte offset
+  d |= uint64_t(1) << 46;                         // bits 46-48 fixed 0b001
+  return d;                                       // base offset 0, no swizzle (bits 61-63 = 0)
+}
+
+template <int M, int N>
+constexpr uint32_t idesc_bf16_f32() {
+  return (1u << 4)                 // D format: F32
+         | (1u << 7)               // A format: BF16
+         | (1u << 10)              // B format: BF16
+         | (0u << 15) | (0u << 16) // A, B K-major
+         | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// Bounded wait for the completion of the mbarrier phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+        "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int q = 0; q < 16; ++q) r[q] = __uint_as_float(u[q]);
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// ------------------------------------------------------------------ operand staging
+
+// bf16 bits of a float, round to nearest even
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
+
+// B[k][t] in the core-matrix layout, written once per CTA; KRef::k<D, FORM>(g, i, j)
+// gives K'_g^{ij} * DEN.
+template <int D, int FORM, class KRef>
+__device__ void tc_fill_b(unsigned char* sb) {
+  using TP = TcPlan<D, FORM>;
+  using FT = FormTraits<D, FORM>;
+  for (int idx = threadIdx.x; idx < TP::N * TP::K; idx += blockDim.x) {
+    const int t = idx / TP::K, k = idx % TP::K;
+    const int g = k % TP::KT;
+    int val = 0;
+    if (t < TP::NT && g < FT::NG) val = KRef::template k<D, FORM>(g, tri_row(t, FT::N), tri_col(t, FT::N));
+    const uint32_t off = uint32_t((k / 8) * TP::NC + t / 8) * 128u + uint32_t(t % 8) * 16u + uint32_t(k % 8) * 2u;
+    *reinterpret_cast<uint16_t*>(sb + off) = bf16_bits(float(val));
+  }
+}
+
+// Row m of the A tile: the three bf16 terms of G (zero padded) in the core layout.
+// A 16-byte chunk covers 8 consecutive k of one term (KT is a multiple of 16).
+template <int D, int FORM>
+__device__ __forceinline__ void tc_store_a_row(unsigned char* sa, int m, const float (&G)[FormTraits<D, FORM>::NG]) {
+  using TP = TcPlan<D, FORM>;
+  using FT = FormTraits<D, FORM>;
+  constexpr int KW = TP::KT / 2;  // packed bf16 pairs per term
+  uint32_t w[3][KW];
+#pragma unroll
+  for (int q = 0; q < KW; ++q) {
+    uint32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int g = 2 * q + half;
+      if (g < FT::NG) {
+        const float x = G[g];
+        const uint16_t h0 = bf16_bits(x);
+        const float r1 = x - bf16_value(h0);  // exact
+        const uint16_t h1 = bf16_bits(r1);
+        const float r2 = r1 - bf16_value(h1);  // exact
+        const uint16_t h2 = bf16_bits(r2);
+        (half ? hi : lo)[0] = h0;
+        (half ? hi : lo)[1] = h1;
+        (half ? hi : lo)[2] = h2;
+      }
+    }
+#pragma unroll
+    for (int term = 0; term < 3; ++term) w[term][q] = lo[term] | (hi[term] << 16);
+  }
+  const uint32_t rowoff = uint32_t(m / 8) * 128u + uint32_t(m % 8) * 16u;
+#pragma unroll
+  for (int kc = 0; kc < TP::KC; ++kc) {
+    const int term = (kc * 8) / TP::KT, q0 = ((kc * 8) % TP::KT) / 2;
+    *reinterpret_cast<uint4*>(sa + uint32_t(kc) * TP::A_LBO + rowoff) =
+        make_uint4(w[term][q0], w[term][q0 + 1], w[term][q0 + 2], w[term][q0 + 3]);
+  }
+}
+
+// Writes the 16 accumulator columns of chunk C (unique entries t = 16C + q) to
+// both (i, j) and (j, i) of the element's stage row; indices are compile-time.
+template <int N, int NT, int C, int... Qs>
+__device__ __forceinline__ void tc_mirror_chunk(const float (&r)[16], float* row, std::integer_sequence<int, Qs...>) {
+  (
+      [&] {
+        constexpr int t = C * 16 + Qs;
+        if constexpr (t < NT) {
+          constexpr int i = tri_row(t, N), j = tri_col(t, N);
+          row[i * N + j] = r[Qs];
+          if constexpr (i != j) row[j * N + i] = r[Qs];
+        }
+      }(),
+      ...);
+}
+
+template <int D, int FORM, int C>
+__device__ __forceinline__ void tc_epilogue_chunks(uint32_t tl, float* row) {
+  using TP = TcPlan<D, FORM>;
+  if constexpr (C < TP::N / 16) {
+    float r[16];
+    tmem_ld16(tl + uint32_t(C * 16), r);
+    tmem_ld_wait();
+    tc_mirror_chunk<FormTraits<D, FORM>::N, TP::NT, C>(r, row, std::make_integer_sequence<int, 16>{});
+    tc_epilogue_chunks<D, FORM, C + 1>(tl, row);
+  }
+}
+
+// Geo::tile_g<D, FORM>(p, mid, e, X, w, G) forms element e's folded G (zero on
+// return for an element it flags) and returns its device-error bits.
+template <int D, int FORM, class Geo, class KRef>
+__global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float, float> p, const float* mid) {
+  using TP = TcPlan<D, FORM>;
+  using FT = FormTraits<D, FORM>;
+  constexpr int N = FT::N, NN = FT::NN, SST = TP::SST;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* sb = smem_raw;                                      // B operand
+  unsigned char* region = smem_raw + align_up(TP::b_bytes, 128);     // A tile, then output stages
+  uint64_t* mbar_ptr = reinterpret_cast<uint64_t*>(region + TP::region_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(region + TP::region_bytes + 16);
+  int* abort_flag = reinterpret_cast<int*>(region + TP::region_bytes + 32);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t mbar = smem_u32(mbar_ptr);
+  const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
+  if (int64_t(blockIdx.x) >= nct) return;  // CTA-uniform, before any TMEM allocation
+
+  // set-up: B operand, mbarrier, TMEM accumulator
+  tc_fill_b<D, FORM, KRef>(sb);
+  if (tid == 0) {
+    mbar_init(mbar);
+    *abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "n"(TP::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = idesc_bf16_f32<TP::M, TP::N>();
+  int err = 0;
+  uint32_t phase = 0;
+
+  int v[D + 1];
+  float Xc[D + 1][D];
+  int64_t T = blockIdx.x;
+  const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(p.conn) % 16 == 0);
+  load_conn<D>(p.conn, T * kTileElems + tid, p.n_elem, vec_conn, v);
+  int fcur = gather_regs<D>(p.coords, p.n_vert, T * kTileElems + tid, p.n_elem, v, Xc);
+  float wcur = (p.coef && T * kTileElems + tid < p.n_elem) ? __ldg(p.coef + T * kTileElems + tid) : 1.f;
+  for (; T < nct; T += gridDim.x) {
+    // prefetch the next tile's connectivity and coordinates
+    const int64_t en = (T + gridDim.x) * kTileElems + tid;
+    float Xn[D + 1][D];
+    int vn[D + 1];
+    load_conn<D>(p.conn, en, p.n_elem, vec_conn, vn);
+    const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vn, Xn);
+    const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+    // geometric tensor of this thread's element -> bf16 split into the A tile
+    float G[FT::NG];
+#pragma unroll
+    for (int g = 0; g < FT::NG; ++g) G[g] = 0.f;
+    if (fcur & GF_OK) {
+      err |= Geo::template tile_g<D, FORM>(p, mid, T * kTileElems + tid, Xc, wcur, G);
+    } else if (fcur & GF_ELEM) {
+      err |= DEVERR_CONN;
+    }
+    tc_store_a_row<D, FORM>(region, tid, G);
+    fence_proxy_async_smem();  // generic-proxy writes of A -> tensor-core reads
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sa = smem_u32(region), sbb = smem_u32(sb);
+#pragma unroll
+      for (int s = 0; s < TP::KSTEPS; ++s) {
+        const uint64_t ad = smem_desc(sa + uint32_t(2 * s) * TP::A_LBO, TP::A_LBO, TP::A_SBO);
+        const uint64_t bd = smem_desc(sbb + uint32_t(2 * s) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
+        mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
+      }
+      mma_commit(mbar);
+      if (!mbar_wait(mbar, phase)) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) {  // `phase` is still the pending one: teardown waits on it
+      err |= DEVERR_TIMEOUT;
+      break;
+    }
+    phase ^= 1u;
+    tc_fence_after();
+    // epilogue: this warp's 32 rows of D -> mirrored stage -> coalesced stores
+    float* st = reinterpret_cast<float*>(region) + warp * 32 * SST;
+    float* row = st + lane * SST;
+    tc_epilogue_chunks<D, FORM, 0>(tmem + (uint32_t(warp * 32) << 16), row);
+    __syncwarp();
+    const int64_t e0 = T * kTileElems + warp * 32;
+    if (e0 < p.n_elem) {
+      const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
+      float* dst = p.A + e0 * NN;
+      if (p.vec_store && NN % 4 == 0) {
+        const int nq = cnt * (NN / 4);
+        for (int q = lane; q < nq; q += 32) {
+          const int idx = 4 * q;
+          const int el = idx / NN;
+          const float* s = st + el * SST + (idx - el * NN);
+          __stcs(reinterpret_cast<float4*>(dst) + q, make_float4(s[0], s[1], s[2], s[3]));
+        }
+      } else {
+        const int nw = cnt * NN;
+        for (int idx = lane; idx < nw; idx += 32) {
+          const int el = idx / NN;
+          __stcs(dst + idx, st[el * SST + (idx - el * NN)]);
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // stages (aliasing the A tile) and TMEM are reused by the next tile
+    tc_fence_after();
+    fcur = fnext;
+    wcur = wnext;
+#pragma unroll
+    for (int k = 0; k <= D; ++k)
+#pragma unroll
+      for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+  }
+  // teardown: after an abort, give the tensor core a bounded chance to finish first
+  if (*abort_flag && tid == 0) mbar_wait(mbar, phase);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(TP::TMEM_COLS)
+                 : "memory");
+  }
+  err = __reduce_or_sync(0xffffffffu, err);
+  if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
+}
+
+// G of an affine element with the compensated Jacobian (Eq. 8 / Eq. 15).
+struct TcGeoAffine {
+  template <int D, int FORM>
+  __device__ __forceinline__ static int tile_g(const FwdParams<float, float>&, const float*, int64_t,
+                                               const float (&X)[D + 1][D], float w,
+                                               float (&G)[FormTraits<D, FORM>::NG]) {
+    using FT = FormTraits<D, FORM>;
+    Jac<D, float> jac;
+    const bool nondeg = jacobian<D, JAC_COMP>(X, jac);
+    const float scale = nondeg ? __fdividef(w, dev_abs(jac.det) * float(FT::DEN)) : 0.f;
+    geometric_tensor<D, FORM>(jac.adj, scale, G);
+    return nondeg ? 0 : DEVERR_DEGENERATE;
+  }
+};
+
+template <int D, int FORM, class Geo, class KRef>
+cudaError_t launch_tc_t(const FwdLaunch& L, const float* mid) {
+  using TP = TcPlan<D, FORM>;
+  FwdParams<float, float> p;
+  p.conn = L.conn;
+  p.coords = static_cast<const float*>(L.coords);
+  p.coef = L.coef;
+  p.A = static_cast<float*>(L.A);
+  p.n_elem = L.n_elem;
+  p.n_vert = L.n_vert;
+  p.dev_err = L.dev_err;
+  p.vec_conn = 0;
+  p.vec_store = reinterpret_cast<uintptr_t>(L.A) % 16 == 0;
+  auto kern = fem_fwd_tc_kernel<D, FORM, Geo, KRef>;
+  cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), TP::smem);
+  if (st != cudaSuccess) return st;
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), 4, TP::smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, kTileElems, TP::smem, L.stream>>>(p, mid);
+  return cudaGetLastError();
+}
+
+}  // namespace fem

@@ -73,3 +73,32 @@ def test_iso_argument_errors(gfem):
         gfem.integrate_fwd_iso(coords, conn, _t(mid[:, :2]), ISO1)
     with pytest.raises(gfem.FemError):
         gfem.integrate_fwd_iso(coords, conn, _t(mid), LP1)   # not a non-affine form
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("E", [None, 1, 129, 300])
+def test_iso_p2_tensor_cores(gfem, orc, dim, E):
+    """The P2 contraction on the tensor cores (split-BF16 G, exact BF16 K, FP32
+    accumulation): the same per-element tolerance against the FP64 oracle,
+    ragged 128-element tiles, an invalid vertex flagged and zeroed."""
+    mesh, mid = _curved(dim)
+    conn, m = mesh.conn, mid
+    if E is not None:
+        conn, m = conn[:E].copy(), mid[:E]
+        if E > 5:
+            conn[5, 1] = mesh.n_vert + 7
+    coef = mg.lognormal_coef(mg.rng_for(43), conn.shape[0])
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    A = gfem.integrate_fwd_iso(_t(mesh.coords), _t(conn), _t(m), ISO2, _t(coef), dev_err=err,
+                               contract=gfem.CONTRACT_BF16X3)
+    Ar, fl = orc.integrate_iso(dim, LP2, conn, mesh.coords, m, coef)
+    assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL
+    assert int(err.item()) == (1 if fl.any() else 0)
+    if fl.any():
+        assert torch.all(A[5] == 0)
+
+
+def test_iso_tensor_cores_only_for_p2(gfem):
+    mesh, mid = _curved(3)
+    with pytest.raises(gfem.FemError):
+        gfem.integrate_fwd_iso(_t(mesh.coords), _t(mesh.conn), _t(mid), ISO1, contract=gfem.CONTRACT_BF16X3)
