@@ -54,7 +54,7 @@ NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_la
     "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1d5b65641d781b93"},
     "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.4e6, "src": "09b6b11fb5543c5b"},
     # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
-    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2394.4e6, "src": "481d084af2a808db"},
+    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2394.4e6, "src": "0c2d53d7d432a421"},
 }
 
 
