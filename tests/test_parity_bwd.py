@@ -64,7 +64,7 @@ def test_tile_records_structure(gfem):
     length) in the tile's slot stage holds exactly the slots of its vertex, in
     increasing slot order (the slot's rank is its stage position); the spans
     are disjoint and ordered; on tets a padded tile starts record r at a
-    position congruent to r mod 8 (a packed one back to back); absent slots sit
+    position congruent to 3r mod 8 (a packed one back to back); absent slots sit
     past the last run; and rec_dest places the records of every vertex, in
     record order, in that vertex's run [voff[v], voff[v+1]) of the
     vertex-major array."""
@@ -107,7 +107,7 @@ def test_tile_records_structure(gfem):
             assert np.all(beg[1:] >= beg[:-1] + ln[:-1])              # disjoint, in record order
             padded = not np.array_equal(beg, np.concatenate([[0], np.cumsum(counts)[:-1]]))
             if padded:
-                assert dim == 3 and np.all(beg % 8 == np.arange(rn) % 8)
+                assert dim == 3 and np.all(beg % 8 == (3 * np.arange(rn)) % 8)
                 n_padded += 1
             pos = np.concatenate([b + np.arange(c) for b, c in zip(beg, ln)])
             got = rank[t * TS + order // NV, order % NV].astype(np.int64)
