@@ -50,7 +50,8 @@ constexpr int kMaxCols = 255;   // distinct columns per row (one-byte positions)
 constexpr int kFastCols = 32;   // rows accumulated in shared memory
 constexpr int kPatWarps = 4;
 constexpr int kAsmThreads = 64;
-constexpr int kTileRuns = 40;  // dense tile matrix side (distinct vertices of a 32-element tile)
+constexpr int kTileRuns = 36;  // dense tile matrix side (distinct vertices of a 32-element tile)
+constexpr int kTileWarps = 1;  // warps per CTA of the tile pass (no CTA-wide barrier: finest sharing of shared memory)
 constexpr int kTileCap = 128;  // slots of a 32-element tile (tets: 4 per element)
 constexpr int kCellCap = 512;  // contributions of a 32-element tile (tets: 16 per element)
 constexpr int kHalvesDisjoint = 0x100;  // tile_runs flag: elements 0-15 and 16-31 share no cell
@@ -390,7 +391,7 @@ struct TilePlan {
   static constexpr size_t cells = size_t(32) * 17 * 4;               // u32 [32][17]: odd stride, no conflicts
   static constexpr size_t dense = size_t(kTileRuns) * kTileRuns * 4;
   static constexpr size_t per_warp = 2 * stage + 2 * rcell + cells + dense;
-  static constexpr size_t smem = kPatWarps * per_warp;
+  static constexpr size_t smem = kTileWarps * per_warp;
 };
 
 template <int NV>
@@ -417,7 +418,7 @@ __device__ __forceinline__ void copy_tile_cells(const uint16_t* rec_cell, int64_
 }
 
 template <int NV>
-__global__ void __launch_bounds__(kPatWarps * 32)
+__global__ void __launch_bounds__(kTileWarps * 32)
     tile_assemble_kernel(const float* __restrict__ A, int64_t n_elem, const uint32_t* __restrict__ run_word,
                          const uint16_t* __restrict__ tile_runs, const int32_t* __restrict__ tile_rec,
                          const uint16_t* __restrict__ rec_cell, float* __restrict__ records, int vec) {
@@ -431,8 +432,8 @@ __global__ void __launch_bounds__(kPatWarps * 32)
   uint32_t* cells = reinterpret_cast<uint32_t*>(wb + 2 * TP::stage + 2 * TP::rcell);
   float* dense = reinterpret_cast<float*>(wb + 2 * TP::stage + 2 * TP::rcell + TP::cells);
   const int64_t ntiles = (n_elem + 31) / 32;
-  const int64_t S = int64_t(gridDim.x) * kPatWarps;
-  int64_t t = int64_t(blockIdx.x) * kPatWarps + warp;
+  const int64_t S = int64_t(gridDim.x) * kTileWarps;
+  int64_t t = int64_t(blockIdx.x) * kTileWarps + warp;
   if (t >= ntiles) return;
   // pipeline: tile metadata two tiles ahead, A / record cells / runs one tile ahead
   auto meta = [&](int64_t tt, int& tr, int32_t& rb, int32_t& rn) {
@@ -657,7 +658,7 @@ cudaError_t launch_tile_assemble_t(const AsmLayout& L, const float* A, int64_t n
   auto kern = tile_assemble_kernel<NV>;
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
-  kern<<<pipeline_grid(reinterpret_cast<const void*>(kern), kPatWarps, smem, n_elem, 0), kPatWarps * 32, smem, st>>>(
+  kern<<<pipeline_grid(reinterpret_cast<const void*>(kern), kTileWarps, smem, n_elem, 0), kTileWarps * 32, smem, st>>>(
       A, n_elem, L.run_word, L.tile_runs, L.tile_rec, L.rec_cell, L.records,
       int(reinterpret_cast<uintptr_t>(A) % 16 == 0));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
