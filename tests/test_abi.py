@@ -192,3 +192,22 @@ def test_tensor_core_combinations_rejected_on_host(fem):
     assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 1, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
     tc32 = nat.options_struct(jac=nat.JAC_F32, contract=nat.CONTRACT_BF16X3)
     assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 0, ctypes.byref(tc32), None) == nat.FEM_ERR_UNSUPPORTED
+
+
+def test_saved_det_and_iso_contract_errors_on_host(fem):
+    """fem_integrate_fwd_save / fem_integrate_bwd_saved refuse a NULL det and
+    the tensor-core contraction; fem_integrate_fwd_iso takes BF16X3 only for
+    the P2 form.  All detected on the host, before any launch."""
+    nat = fem.nat
+    lib = nat.load()
+    A = ctypes.c_void_p(0x3000)
+    m = _mesh(fem)
+    opts = nat.options_struct()
+    assert lib.fem_integrate_fwd_save(ctypes.byref(m), LP1, None, A, 0, None, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    tc = nat.options_struct(contract=nat.CONTRACT_BF16X3)
+    assert lib.fem_integrate_fwd_save(ctypes.byref(m), EP1, None, A, 0, A, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_integrate_bwd_saved(ctypes.byref(m), LP1, None, A, None, A, None, None, 0, None, None) == nat.FEM_ERR_ARG
+    assert lib.fem_integrate_bwd_saved(ctypes.byref(m), 3, None, A, A, A, None, None, 0, None, None) == nat.FEM_ERR_UNSUPPORTED
+    me = _mesh(fem, n_elem=0)
+    assert lib.fem_integrate_fwd_save(ctypes.byref(me), LP1, None, None, 0, None, None, None) == nat.FEM_OK
+    assert lib.fem_integrate_fwd_iso(ctypes.byref(m), 5, A, None, A, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED

@@ -16,16 +16,17 @@ def _pinned(a):
     return torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
 
 
-@pytest.mark.parametrize("chunk", [1000, 1 << 20])
-def test_host_step_equals_device_path(gfem, chunk):
+@pytest.mark.parametrize("chunk,form", [(1000, 0), (1 << 20, 0), (700, 2)])
+def test_host_step_equals_device_path(gfem, chunk, form):
     mesh = mg.cube_tet_mesh(9, 0.15, mg.rng_for(91), 0.05, np.float32)
     E, V = mesh.n_elem, mesh.n_vert
-    dA = np.random.default_rng(92).standard_normal((E, 4, 4)).astype(np.float32)
+    n = 4 if form == 0 else 12
+    dA = np.random.default_rng(92).standard_normal((E, n, n)).astype(np.float32)
     coords, conn = torch.from_numpy(mesh.coords).to(DEV), torch.from_numpy(mesh.conn).to(DEV)
-    A_ref = gfem.integrate_fwd(coords, conn, gfem.LAPLACE_P1)
-    dx_ref, _ = gfem.integrate_bwd(coords, conn, gfem.LAPLACE_P1, torch.from_numpy(dA).to(DEV), need_dcoef=False)
-    hs = gfem.HostStep(V, E, 3, gfem.LAPLACE_P1, chunk=chunk, device=DEV)
-    A_h = torch.empty((E, 4, 4)).pin_memory()
+    A_ref = gfem.integrate_fwd(coords, conn, form)
+    dx_ref, _ = gfem.integrate_bwd(coords, conn, form, torch.from_numpy(dA).to(DEV), need_dcoef=False)
+    hs = gfem.HostStep(V, E, 3, form, chunk=chunk, device=DEV)
+    A_h = torch.empty((E, n, n)).pin_memory()
     dx_h = torch.empty((V, 3)).pin_memory()
     for _ in range(2):  # the second run reuses the incidence
         A_h.zero_()

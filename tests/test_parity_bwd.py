@@ -252,3 +252,21 @@ def test_adjoint_device_errors(gfem, orc, reduce):
     assert _rel(dx.cpu().numpy(), gx) <= TOL
     dwh = dw.cpu().numpy()
     assert dwh[5] == 0 and dwh[9] == 0 and _rel(dwh[keep], gw) <= TOL
+
+
+@pytest.mark.parametrize("dim,form,out", [(2, 3, torch.float32), (3, 4, torch.float32), (3, LP1, torch.float64),
+                                          (2, LP2, torch.float32)])
+def test_fwd_save_other_paths(gfem, dim, form, out):
+    """det J is written by every forward path fem_integrate_fwd_save serves (the
+    P1-coefficient forms, FP64 output, triangles) and A is unchanged."""
+    mesh = _mesh(dim)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    w1 = form in (3, 4)
+    coef = _t(mg.lognormal_coef(mg.rng_for(65), mesh.n_vert if w1 else mesh.n_elem))
+    det = torch.full((mesh.n_elem,), float("nan"), device="cuda")
+    A0 = gfem.integrate_fwd(coords, conn, form, coef, out_dtype=out)
+    A1 = gfem.integrate_fwd(coords, conn, form, coef, out_dtype=out, det_out=det)
+    assert torch.equal(A0, A1)
+    jac = gfem.JAC_F64 if out == torch.float64 else gfem.JAC_AUTO
+    dref, _ = gfem.geometry(coords, conn, jac=jac)
+    assert torch.all((det.double() - dref).abs() <= 2.0 ** -23 * dref.abs())
