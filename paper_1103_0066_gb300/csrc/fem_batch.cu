@@ -502,6 +502,7 @@ struct fem_batch {
   std::vector<Group> groups;  // non-empty kinds, largest work first
   std::vector<fem_batch_item> items;        // the caller's items (per-item mode)
   std::vector<fem::BwdWorkspace> item_ws;  // their record workspaces (valid when the item has records)
+  std::vector<float*> item_det;            // det J from the forward for the adjoint (per-item mode), or null
   cudaStream_t aux[6] = {};
   cudaEvent_t fork = nullptr, join[6] = {};
   ~fem_batch() {
@@ -547,6 +548,12 @@ size_t item_ws_bytes(const fem_batch_item& it) {
   return fem::bwd_workspace_layout(it.mesh.dim, it.mesh.n_elem, it.mesh.n_vert, true, nullptr, nullptr);
 }
 
+// det J of every element, kept by the per-item forward for the per-item adjoint
+// when an item has both.
+size_t item_det_bytes(const fem_batch_item& it) {
+  return (it.A && it.dA && (it.dcoords || it.dcoef)) ? sizeof(float) * size_t(it.mesh.n_elem) : 0;
+}
+
 // [descriptors, caller order][descriptors, grouped by kind][counters]
 size_t head_bytes(int32_t n, size_t* kdesc_off, size_t* ctr_off, size_t* ctr_bytes) {
   const size_t desc_bytes = al256(sizeof(fem::BatchMesh) * size_t(n));
@@ -586,6 +593,9 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
   for (size_t k = 0; k < b->items.size() && e == cudaSuccess; ++k) {
     const fem_batch_item& it = b->items[k];
     const fem::BatchMesh& M = b->desc[k];
+    // both passes in this run: the forward keeps det J for the adjoint (same bits)
+    float* det = ((phases & FEM_PHASE_FWD) && (phases & FEM_PHASE_BWD) && (M.flags & fem::BM_FWD) &&
+                  (M.flags & fem::BM_BWD)) ? b->item_det[k] : nullptr;
     if (M.n_elem == 0) {
       if ((phases & FEM_PHASE_BWD) && (M.flags & fem::BM_REC) && M.n_vert > 0)
         e = fem::launch_zero_f32(it.dcoords, M.n_vert * it.mesh.dim, st);  // no element: dcoords = 0
@@ -605,6 +615,7 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
       L.dev_err = &b->d_ctr->err;
       L.warps = 0;  // the kernel's default
       L.stream = st;
+      L.det_out = det;
       e = L.dim == 2 ? fem::launch_fwd_d2(L)
                      : (it.form == FEM_ELASTIC_P1 ? fem::launch_fwd_d3_ela(L) : fem::launch_fwd_d3_lap(L));
     }
@@ -631,6 +642,7 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
       L.n_vert = M.n_vert;
       L.dev_err = &b->d_ctr->err;
       L.stream = st;
+      L.det_in = det;
       e = fem::launch_bwd_elem(L);
       if (e == cudaSuccess && rec) e = fem::launch_vertex_reduce(it.mesh.dim, W, M.n_vert, it.dcoords, st);
     }
@@ -685,7 +697,7 @@ fem_status fem_batch_workspace_size(const fem_batch_item* items, int32_t n_items
   }
   size_t ko, co, cb;
   size_t total = head_bytes(n_items, &ko, &co, &cb);
-  for (int i = 0; i < n_items; ++i) total += al256(item_ws_bytes(items[i]));
+  for (int i = 0; i < n_items; ++i) total += al256(item_ws_bytes(items[i])) + al256(item_det_bytes(items[i]));
   *bytes = total;
   return FEM_OK;
 }
@@ -714,6 +726,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   b->desc.resize(size_t(n_items));
   b->items.assign(items, items + n_items);
   b->item_ws.assign(size_t(n_items), fem::BwdWorkspace{});
+  b->item_det.assign(size_t(n_items), nullptr);
   size_t kdesc_off = 0, ctr_off = 0;
   size_t off = head_bytes(n_items, &kdesc_off, &ctr_off, &b->ctr_bytes);
   char* base = static_cast<char*>(ws);
@@ -760,6 +773,10 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
       M.voff = W.voff;
       M.records = W.records;
       off += al256(wsb);
+    }
+    if (const size_t db = item_det_bytes(it)) {
+      b->item_det[size_t(i)] = reinterpret_cast<float*>(base + off);
+      off += al256(db);
     }
   }
   for (int i = 0; i < n_items; ++i) {  // reduction items follow all tiles

@@ -96,15 +96,16 @@ struct BwdPlan {
 };
 
 // CTA shape of the adjoint element kernel.  The kernel has no CTA-wide
-// barrier, so the CTA size only sets how finely the register file is shared
-// out.  The compensated 3D P1 Laplacian runs one-warp CTAs with at least 24
-// resident per SM, which holds it to 80 registers without spills: 25 warps
-// per SM fit, against 20 at its natural 93 registers in 4-warp CTAs.  The
-// other instantiations keep 4-warp CTAs and the compiler's register choice.
+// barrier, so the CTA size only sets how finely the register file and shared
+// memory are shared out.  On tets every form runs one-warp CTAs: the P2
+// Laplacian's 30 KB per warp then packs 7 warps per SM instead of one 4-warp
+// CTA.  The compensated 3D P1 Laplacian also asks for at least 24 resident
+// per SM, which holds it to 80 registers without spills: 24 warps per SM,
+// against 20 at its natural 93 registers.  Triangles keep 4-warp CTAs.
 template <int D, int FORM, int JAC>
 struct BwdShape {
   static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && (JAC == JAC_COMP || JAC == JAC_SAVED));
-  static constexpr int threads = tight ? 32 : kTileElems;
+  static constexpr int threads = D == 3 ? 32 : kTileElems;
   static constexpr int min_ctas = tight ? 24 : 1;
 };
 
