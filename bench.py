@@ -51,11 +51,11 @@ KERNEL_SOURCES = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1350.7e6, "src": "4580434c0d808b7b"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1d5b65641d781b93"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.4e6, "src": "09b6b11fb5543c5b"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1350.0e6, "src": "d04e098e10738dc0"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.1e6, "src": "b81f7e1ca57e8aac"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.5e6, "src": "4f52f33a20ea977f"},
     # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
-    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2394.4e6, "src": "0c2d53d7d432a421"},
+    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2393.8e6, "src": "d83d2b05bb51b497"},
 }
 
 
