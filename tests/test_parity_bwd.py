@@ -270,3 +270,37 @@ def test_fwd_save_other_paths(gfem, dim, form, out):
     jac = gfem.JAC_F64 if out == torch.float64 else gfem.JAC_AUTO
     dref, _ = gfem.geometry(coords, conn, jac=jac)
     assert torch.all((det.double() - dref).abs() <= 2.0 ** -23 * dref.abs())
+
+
+def test_full_size_step_sampled(gfem, orc):
+    """The benchmark step at full size: 128^3 Kuhn cube with 5% slivers
+    (12,582,912 tets), forward saving det J, deterministic adjoint with it, in
+    the bench's launch configuration.  dcoords is checked at a random sample of
+    vertices, each against the oracle's reverse mode over all of its incident
+    elements; A on a stratified element sample."""
+    mesh = mg.workload_tet_slivers(128)
+    E, V = mesh.n_elem, mesh.n_vert
+    dA_h = mg.upstream(mg.rng_for(66), E, 4)
+    coords, conn, dA = _t(mesh.coords), _t(mesh.conn), _t(dA_h)
+    det = torch.empty(E, device="cuda")
+    A = gfem.integrate_fwd(coords, conn, LP1, det_out=det)
+    ws = gfem.Workspace(coords, conn)
+    dx, _ = gfem.integrate_bwd(coords, conn, LP1, dA, ws=ws, reduce=gfem.REDUCE_DEFERRED, need_dcoef=False,
+                               det=det)
+    gfem.adjoint_reduce(coords, conn, ws, dx)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(67)
+    verts = rng.choice(V, 3000, replace=False)
+    hit = np.zeros(V, bool)
+    hit[verts] = True
+    el = np.where(hit[mesh.conn].any(1))[0]                    # every element incident to a sampled vertex
+    gx, _ = orc.integrate_vjp(3, LP1, mesh.conn[el], mesh.coords, dA_h[el])
+    got = dx.cpu().numpy()[verts].astype(np.float64)
+    ref = gx[verts]
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= TOL * scale
+    idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 5000, replace=False),
+                                    rng.choice(E, 5000, replace=False), np.arange(E - 40, E)]))
+    Ar, _ = orc.integrate(3, LP1, mesh.conn[idx], mesh.coords)
+    Ag = A[torch.from_numpy(idx).to("cuda")].double().cpu().numpy()
+    assert (np.abs(Ag - Ar).reshape(len(idx), -1).max(1) / np.abs(Ar).reshape(len(idx), -1).max(1)).max() <= TOL

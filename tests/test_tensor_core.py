@@ -56,3 +56,24 @@ def test_tensor_core_degenerate_and_conn_errors(gfem):
     A = gfem.integrate_fwd(_t(X), _t(conn), EP1, contract=gfem.CONTRACT_BF16X3, dev_err=err).cpu().numpy()
     assert int(err.item()) == gfem.DEVERR_CONN | gfem.DEVERR_DEGENERATE
     assert np.all(A[1::3] == 0) and np.all(A[2::3] == 0) and np.abs(A[0]).max() > 0
+
+
+def test_full_size_elasticity_sampled(gfem, orc):
+    """128^3 sliver cube (12,582,912 tets), P1 elasticity with a lognormal
+    coefficient: the FP32 and the tensor-core paths at full size, each on a
+    stratified sample of elements (slivers, regular, the ragged last tiles)."""
+    mesh = mg.workload_tet_slivers(128)
+    E = mesh.n_elem
+    coef_h = mg.lognormal_coef(mg.rng_for(68), E)
+    coords, conn, coef = _t(mesh.coords), _t(mesh.conn), _t(coef_h)
+    rng = np.random.default_rng(69)
+    idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 5000, replace=False),
+                                    rng.choice(E, 5000, replace=False), np.arange(E - 200, E)]))
+    Ar, fl = orc.integrate(3, EP1, mesh.conn[idx], mesh.coords, coef_h[idx])
+    assert not fl.any()
+    sel = torch.from_numpy(idx).to(DEV)
+    for contract in (gfem.CONTRACT_F32, gfem.CONTRACT_BF16X3):
+        A = gfem.integrate_fwd(coords, conn, EP1, coef, contract=contract)
+        Ag = A[sel].cpu().numpy()
+        del A
+        assert rel_err_per_element(Ag, Ar).max() <= TOL
