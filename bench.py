@@ -454,7 +454,8 @@ def run_batch(args):
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
         mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
-                      fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item"}
+                      fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item",
+                      fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent"}
         per_mode = {}
         for mode in mode_names:  # each mode at full occupancy, chunk 1, in a CUDA graph
             bt.set_config(32, 1, mode)
@@ -479,7 +480,8 @@ def run_batch(args):
         err = bt.errors(stream=stream)
     peak, peak_kind = hbm_peak()
     kinds = {(it["src"].mesh.dim, it["form"]) for it in items if it["src"].mesh.n_elem > 0}
-    launches = {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 3 * len(items)}.get(cfg[2], len(kinds))
+    launches = {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 3 * len(items),
+                fem.BATCH_PER_ITEM_CONCURRENT: 3 * len(items)}.get(cfg[2], len(kinds))
     byts = batch_bytes(items)
     ach = byts / (batch_ms * 1e-3) / 1e9
     out = {
@@ -492,7 +494,8 @@ def run_batch(args):
                    "elements": E, "meshes": len(items),
                    "l2": "no flush: ~%.1f GB moved per step" % (byts / 1e9)},
         "roofline": {"bound": "hbm", "kernel": {fem.BATCH_SINGLE: "fem_batch_kernel",
-                                                fem.BATCH_PER_ITEM: "per-mesh kernels"}.get(
+                                                fem.BATCH_PER_ITEM: "per-mesh kernels",
+                                                fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on six streams"}.get(
                          cfg[2], "fem_batch_kind_kernel (all kinds)"), "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},
@@ -856,7 +859,8 @@ def run_multiphysics(args):
            "comparison_ms": {"per_form_eager": eager_ms, "batched_graph": batch_ms},
            "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": cfg[2]},
            "device_errors": err,
-           "gpu_launches": args.steps * {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 9}.get(cfg[2], 3)}
+           "gpu_launches": args.steps * {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 9,
+                                         fem.BATCH_PER_ITEM_CONCURRENT: 9}.get(cfg[2], 3)}
     print(json.dumps(out), flush=True)
 
 

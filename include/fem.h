@@ -242,11 +242,16 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
  *   FEM_BATCH_PER_ITEM    each item through the single-mesh kernels of
  *                         fem_integrate_fwd / fem_integrate_bwd (the better
  *                         choice for a few large meshes), on `stream`
+ *   FEM_BATCH_PER_ITEM_CONCURRENT  the same, the items spread over six
+ *                         streams (longest first, each to the least loaded;
+ *                         event fork/join on `stream`, graph-capturable), so
+ *                         small meshes run beside large ones
  * Every mode gives the same result bits as the per-mesh entry points. */
 #define FEM_BATCH_SINGLE 0
 #define FEM_BATCH_GROUPED 1
 #define FEM_BATCH_GROUPED_CONCURRENT 2
 #define FEM_BATCH_PER_ITEM 3
+#define FEM_BATCH_PER_ITEM_CONCURRENT 4
 
 #define FEM_PHASE_FWD 1 /* forward element matrices into item.A */
 #define FEM_PHASE_BWD 2 /* adjoint of item.dA into item.dcoords / item.dcoef */

@@ -30,7 +30,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
            "fem_integrate_bwd_saved")
 PHASE_FWD, PHASE_BWD = 1, 2
-BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM = 0, 1, 2, 3
+BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
 NOALLOC_SCRATCH_BYTES = 32 << 20
 

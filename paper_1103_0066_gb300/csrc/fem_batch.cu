@@ -13,8 +13,11 @@
 // reports FEM_DEVERR_TIMEOUT when it gives up.  The per-tile code is the
 // per-mesh kernels' (fwd_compute_tile, bwd_compute_tile, warp_records).
 //
-// Per-item mode (FEM_BATCH_PER_ITEM): every item through the single-mesh
-// kernels, on the records this batch built.
+// Per-item modes (FEM_BATCH_PER_ITEM, FEM_BATCH_PER_ITEM_CONCURRENT): every
+// item through the single-mesh kernels, on the records this batch built; in
+// order on one stream, or spread over kItemLanes streams (longest items first,
+// each to the least loaded lane) so that small items fill the gaps of large
+// ones.
 //
 // Grouped modes (FEM_BATCH_GROUPED, FEM_BATCH_GROUPED_CONCURRENT): the same
 // item scheme per (dim, form) kind, one kind-specialised pipelined kernel per
@@ -64,6 +67,7 @@ struct BatchCounters {
 };
 
 constexpr int kRedVerts = 2048;  // vertices per reduction item
+constexpr int kItemLanes = 6;    // streams of the per-item concurrent mode
 constexpr uint32_t kSpinLimit = 1u << 24;
 
 // Shared memory of one batch warp: a stage shared by the forward tile and the
@@ -505,10 +509,19 @@ struct fem_batch {
   std::vector<float*> item_det;            // det J from the forward for the adjoint (per-item mode), or null
   cudaStream_t aux[6] = {};
   cudaEvent_t fork = nullptr, join[6] = {};
+  // per-item concurrent mode: lane of every item; lanes 1.. run on item_aux
+  std::vector<int> item_lane;
+  cudaStream_t item_aux[5] = {};
+  cudaEvent_t item_join[5] = {};
+  int n_lanes = 1;
   ~fem_batch() {
     for (cudaStream_t s : aux)
       if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : join)
+      if (e) cudaEventDestroy(e);
+    for (cudaStream_t s : item_aux)
+      if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : item_join)
       if (e) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
   }
@@ -588,11 +601,19 @@ cudaError_t launch_group(fem_batch* b, const fem_batch::Group& g, int phases, in
   return fem::kind_launch(g.kind, L, st);
 }
 
-cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
+cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st0, bool concurrent) {
   cudaError_t e = cudaSuccess;
+  const bool fan = concurrent && b->n_lanes > 1;
+  if (fan) {  // fork: every lane starts after the work already on st0
+    if ((e = cudaEventRecord(b->fork, st0)) != cudaSuccess) return e;
+    for (int l = 1; l < b->n_lanes; ++l)
+      if ((e = cudaStreamWaitEvent(b->item_aux[l - 1], b->fork, 0)) != cudaSuccess) return e;
+  }
   for (size_t k = 0; k < b->items.size() && e == cudaSuccess; ++k) {
     const fem_batch_item& it = b->items[k];
     const fem::BatchMesh& M = b->desc[k];
+    const int lane = fan ? b->item_lane[k] : 0;
+    cudaStream_t st = lane == 0 ? st0 : b->item_aux[lane - 1];
     // both passes in this run: the forward keeps det J for the adjoint (same bits)
     float* det = ((phases & FEM_PHASE_FWD) && (phases & FEM_PHASE_BWD) && (M.flags & fem::BM_FWD) &&
                   (M.flags & fem::BM_BWD)) ? b->item_det[k] : nullptr;
@@ -647,13 +668,20 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st) {
       if (e == cudaSuccess && rec) e = fem::launch_vertex_reduce(it.mesh.dim, W, M.n_vert, it.dcoords, st);
     }
   }
+  if (fan && e == cudaSuccess) {  // join every lane back into st0
+    for (int l = 1; l < b->n_lanes && e == cudaSuccess; ++l) {
+      e = cudaEventRecord(b->item_join[l - 1], b->item_aux[l - 1]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st0, b->item_join[l - 1], 0);
+    }
+  }
   return e;
 }
 
 cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, int mode, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
   if (e != cudaSuccess) return e;
-  if (mode == FEM_BATCH_PER_ITEM) return launch_per_item(b, phases, st);
+  if (mode == FEM_BATCH_PER_ITEM || mode == FEM_BATCH_PER_ITEM_CONCURRENT)
+    return launch_per_item(b, phases, st, mode == FEM_BATCH_PER_ITEM_CONCURRENT);
   if (mode == FEM_BATCH_SINGLE) {
     const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
     fem::fem_batch_kernel<<<unsigned(grid_for(ctas_per_sm, total, chunk)), fem::kTileElems, b->smem, st>>>(
@@ -680,7 +708,7 @@ cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, i
 }
 
 bool valid_config(int ctas_per_sm, int chunk, int mode) {
-  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_PER_ITEM && chunk >= 1 && chunk <= 64 &&
+  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_PER_ITEM_CONCURRENT && chunk >= 1 && chunk <= 64 &&
          ctas_per_sm >= 1 && ctas_per_sm <= 32;
 }
 
@@ -819,6 +847,31 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   std::stable_sort(b->groups.begin(), b->groups.end(),
                    [](const fem_batch::Group& x, const fem_batch::Group& y) { return x.work > y.work; });
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  // per-item lanes: longest items first, each to the least loaded lane (bytes of
+  // A or dA per element stand for an item's work)
+  b->n_lanes = n_items > 1 ? std::min(n_items, fem::kItemLanes) : 1;
+  for (int l = 1; l < b->n_lanes && e == cudaSuccess; ++l) {
+    e = cudaStreamCreateWithFlags(&b->item_aux[l - 1], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->item_join[l - 1], cudaEventDisableTiming);
+  }
+  {
+    std::vector<int> order(static_cast<size_t>(n_items));
+    std::vector<double> work(static_cast<size_t>(n_items)), load(static_cast<size_t>(b->n_lanes), 0.0);
+    for (int i = 0; i < n_items; ++i) {
+      order[size_t(i)] = i;
+      const int nv = items[i].mesh.dim + 1;
+      const int n = items[i].form == FEM_LAPLACE_P1 ? nv
+                    : items[i].form == FEM_LAPLACE_P2 ? nv * (nv + 1) / 2 : (nv - 1) * nv;
+      work[size_t(i)] = double(items[i].mesh.n_elem) * double(n * n + 8);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[size_t(x)] > work[size_t(y)]; });
+    b->item_lane.assign(size_t(n_items), 0);
+    for (int i : order) {
+      const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
+      b->item_lane[size_t(i)] = l;
+      load[size_t(l)] += work[size_t(i)];
+    }
+  }
   for (size_t k = 1; k < b->groups.size() && e == cudaSuccess; ++k) {
     e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
@@ -876,13 +929,14 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
   int best_c = b->ctas_per_sm, best_k = b->chunk, best_m = b->mode;
   const int chunks[] = {1, 2, 4, 8};
   cudaError_t err = cudaSuccess;
-  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_PER_ITEM && err == cudaSuccess; ++mode) {
+  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_PER_ITEM_CONCURRENT && err == cudaSuccess; ++mode) {
     const bool grouped = mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT;
+    const bool per_item = mode == FEM_BATCH_PER_ITEM || mode == FEM_BATCH_PER_ITEM_CONCURRENT;
     if (grouped && b->groups.empty()) continue;
-    const int c_hi = mode == FEM_BATCH_PER_ITEM ? 1 : b->max_ctas_per_sm;  // per item: no grid or chunk to tune
+    const int c_hi = per_item ? 1 : b->max_ctas_per_sm;  // per item: no grid or chunk to tune
     for (int c = 1; c <= c_hi && err == cudaSuccess; ++c)
       for (int k : chunks) {
-        if (mode == FEM_BATCH_PER_ITEM && k != 1) continue;
+        if (per_item && k != 1) continue;
         err = launch_batch(b, phases, c, k, mode, st);  // warm-up
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {

@@ -42,12 +42,13 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-MODES = ["single", "grouped", "concurrent", "per_item"]
+MODES = ["single", "grouped", "concurrent", "per_item", "per_item_concurrent"]
 
 
 def _mode(gfem, name):
     return {"single": gfem.BATCH_SINGLE, "grouped": gfem.BATCH_GROUPED,
-            "concurrent": gfem.BATCH_GROUPED_CONCURRENT, "per_item": gfem.BATCH_PER_ITEM}[name]
+            "concurrent": gfem.BATCH_GROUPED_CONCURRENT, "per_item": gfem.BATCH_PER_ITEM,
+            "per_item_concurrent": gfem.BATCH_PER_ITEM_CONCURRENT}[name]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -100,9 +101,12 @@ def test_batch_graph_capture_and_tuning(gfem, mode):
     ref = [(it["A"].clone(), it["dcoords"].clone()) for it in items]
     cfg = batch.tune()
     assert cfg[0] >= 1 and cfg[1] >= 1 and cfg[2] in (gfem.BATCH_SINGLE, gfem.BATCH_GROUPED,
-                                                       gfem.BATCH_GROUPED_CONCURRENT, gfem.BATCH_PER_ITEM)
+                                                       gfem.BATCH_GROUPED_CONCURRENT, gfem.BATCH_PER_ITEM,
+                                                       gfem.BATCH_PER_ITEM_CONCURRENT)
     if mode == "concurrent":  # fork/join side streams inside the capture
         batch.set_config(cfg[0], cfg[1], gfem.BATCH_GROUPED_CONCURRENT)
+    if mode == "per_item_concurrent":
+        batch.set_config(1, 1, gfem.BATCH_PER_ITEM_CONCURRENT)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
