@@ -495,7 +495,7 @@ def run_batch(args):
                    "l2": "no flush: ~%.1f GB moved per step" % (byts / 1e9)},
         "roofline": {"bound": "hbm", "kernel": {fem.BATCH_SINGLE: "fem_batch_kernel",
                                                 fem.BATCH_PER_ITEM: "per-mesh kernels",
-                                                fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on six streams"}.get(
+                                                fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on ten streams"}.get(
                          cfg[2], "fem_batch_kind_kernel (all kinds)"), "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},

@@ -242,7 +242,7 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
  *   FEM_BATCH_PER_ITEM    each item through the single-mesh kernels of
  *                         fem_integrate_fwd / fem_integrate_bwd (the better
  *                         choice for a few large meshes), on `stream`
- *   FEM_BATCH_PER_ITEM_CONCURRENT  the same, the items spread over six
+ *   FEM_BATCH_PER_ITEM_CONCURRENT  the same, the items spread over ten
  *                         streams (longest first, each to the least loaded;
  *                         event fork/join on `stream`, graph-capturable), so
  *                         small meshes run beside large ones
