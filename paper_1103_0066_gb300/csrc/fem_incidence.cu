@@ -11,12 +11,14 @@
 // the mesh, so dcoords is bitwise reproducible.
 //
 // Built once per connectivity (fem_incidence_build), one warp per tile:
-//   per tile : bitonic sort of (vertex, slot) keys -> the rank of every slot
-//              in that order (one byte; the element pass writes each
-//              contribution at its rank, so a record is a contiguous run) and
-//              the record count; exclusive scan of the counts -> first record
-//              of each tile; record ends (one byte, end of the run) and record
-//              vertices
+//   per tile : bitonic sort of (vertex, slot) keys -> the record count (pass
+//              1); exclusive scan of the counts -> first record of each tile;
+//              then (pass 2) every slot's stage position (one byte: the
+//              element pass writes each contribution there, so a record is a
+//              contiguous run), each record's span (start | length << 8) and
+//              vertex.  On tets the runs start at positions congruent to 3r
+//              mod 8 in a 256-position stage, which keeps the record loop's
+//              shared reads free of bank conflicts.
 //   global   : vertex -> records CSR (count, scan, fill, per-segment sort),
 //              then each record's position in it (rec_dest): the element pass
 //              writes record r straight to records[rec_dest[r]], so the

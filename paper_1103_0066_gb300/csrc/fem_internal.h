@@ -72,7 +72,7 @@ struct BwdLaunch {
 // rec_dest[r]), so the records of vertex v are records[voff[v], voff[v+1]).
 struct BwdWorkspace {
   int32_t* tile_rec;
-  uint32_t* rank;  // per element: byte k = rank of its local vertex k in its tile's (vertex, slot) order
+  uint32_t* rank;  // per element: byte k = stage position of its local vertex k (runs in (vertex, slot) order)
   uint16_t* rec_span;  // per record: start | length << 8 of its run in the tile's slot stage
   int32_t* rec_dest;  // per record: its position in the vertex-major record array
   int32_t* rec_vertex;
