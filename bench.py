@@ -51,9 +51,9 @@ KERNEL_SOURCES = {
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube from one ncu launch-list capture.
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1350.0e6, "src": "d04e098e10738dc0"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.1e6, "src": "b81f7e1ca57e8aac"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.5e6, "src": "4f52f33a20ea977f"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1349.6e6, "src": "df0ffcaa0a6fd82e"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1669d2556ed01ef5"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.5e6, "src": "f814c9fb2f7de961"},
     # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
     "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2393.8e6, "src": "d83d2b05bb51b497"},
 }
