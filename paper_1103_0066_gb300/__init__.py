@@ -106,7 +106,7 @@ def _check_det(det, E):
 
 
 def integrate_fwd_iso(coords, conn, mid, form=LAPLACE_P1_ISO, coef=None, out=None, dev_err=None, stream=None,
-                      contract=CONTRACT_F32):
+                      contract=CONTRACT_F32, ctas_per_sm=0):
     """fem_integrate_fwd_iso: element matrices [E][n][n] of the Laplacian on
     non-affine elements with edge-midpoint nodes mid [E][d(d+1)/2][d] (FP32).
     contract=CONTRACT_BF16X3 runs the P2 contraction on the tensor cores."""
@@ -120,7 +120,7 @@ def integrate_fwd_iso(coords, conn, mid, form=LAPLACE_P1_ISO, coef=None, out=Non
         out = torch.empty((E, n, n), dtype=torch.float32, device=coords.device)
     elif out.shape != (E, n, n) or not out.is_contiguous() or out.dtype != torch.float32:
         raise ValueError("out must be a contiguous float32 [E][n][n] tensor")
-    opts = nat.options_struct(JAC_AUTO, contract, 0, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
+    opts = nat.options_struct(JAC_AUTO, contract, 0, 0, ctas_per_sm, dev_err.data_ptr() if dev_err is not None else 0)
     nat.fem_integrate_fwd_iso(m, form, mid.data_ptr(), _coef_ptr(coef, E), out.data_ptr(), opts, _stream_ptr(stream))
     return out
 
