@@ -153,24 +153,16 @@ __device__ __forceinline__ void tc_store_a_row(unsigned char* sa, int m, const f
   uint32_t w[3][KW];
 #pragma unroll
   for (int q = 0; q < KW; ++q) {
-    uint32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const int g = 2 * q + half;
-      if (g < FT::NG) {
-        const float x = G[g];
-        const uint16_t h0 = bf16_bits(x);
-        const float r1 = x - bf16_value(h0);  // exact
-        const uint16_t h1 = bf16_bits(r1);
-        const float r2 = r1 - bf16_value(h1);  // exact
-        const uint16_t h2 = bf16_bits(r2);
-        (half ? hi : lo)[0] = h0;
-        (half ? hi : lo)[1] = h1;
-        (half ? hi : lo)[2] = h2;
-      }
-    }
-#pragma unroll
-    for (int term = 0; term < 3; ++term) w[term][q] = lo[term] | (hi[term] << 16);
+    // two G entries at once: h = bf16x2(x), r = x - h exactly, then the same on r
+    const float x0 = 2 * q < FT::NG ? G[2 * q] : 0.f, x1 = 2 * q + 1 < FT::NG ? G[2 * q + 1] : 0.f;
+    const __nv_bfloat162 h0 = __floats2bfloat162_rn(x0, x1);
+    const float r0 = x0 - __low2float(h0), r1 = x1 - __high2float(h0);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(r0, r1);
+    const float s0 = r0 - __low2float(h1), s1 = r1 - __high2float(h1);
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(s0, s1);
+    w[0][q] = *reinterpret_cast<const uint32_t*>(&h0);
+    w[1][q] = *reinterpret_cast<const uint32_t*>(&h1);
+    w[2][q] = *reinterpret_cast<const uint32_t*>(&h2);
   }
   const uint32_t rowoff = uint32_t(m / 8) * 128u + uint32_t(m % 8) * 16u;
 #pragma unroll
