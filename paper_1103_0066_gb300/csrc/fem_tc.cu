@@ -1,8 +1,42 @@
 // fem_tc.cu -- the tensor-core contraction (fem_tc.cuh) for the affine forms it
 // serves: P2 Laplacian and P1 elasticity on triangles and tetrahedra.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "fem_tc.cuh"
 
 namespace fem {
+
+namespace {
+PFN_cuTensorMapEncodeTiled_v12000 tc_map_encoder() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+}  // namespace
+
+bool encode_tc_rows_map(CUtensorMap* map, const void* base, int64_t rows, int cols) {
+  if (!base || rows <= 0 || rows > (int64_t(1) << 32) || reinterpret_cast<uintptr_t>(base) % 16 != 0 ||
+      (cols * 4) % 16 != 0)
+    return false;
+  PFN_cuTensorMapEncodeTiled_v12000 fn = tc_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cuuint64_t(cols), cuuint64_t(rows)};
+  const cuuint64_t strides[1] = {cuuint64_t(cols) * 4};  // bytes between rows
+  const cuuint32_t box[2] = {32, 32};                    // 128-byte row segments of one warp's 32 elements
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 // Reference tensors of the forms the tensor-core kernel serves, in constant memory.
 __constant__ RefTensor<3, ELASTIC_P1> kTcK3e = make_ref_tensor<3, ELASTIC_P1>();

@@ -48,8 +48,14 @@ struct TcPlan {
   static constexpr size_t b_bytes = size_t(N) * K * 2;
   static constexpr int SST = stage_stride<FT::NN>();
   static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);  // aliases the A tile
-  static constexpr size_t region_bytes = stage_bytes > a_bytes ? stage_bytes : align_up(a_bytes, 128);
-  static constexpr size_t smem = align_up(b_bytes, 128) + region_bytes + 128;     // + mbarrier, TMEM slot
+  // TMA epilogue: per warp, NN / 32 boxes (rounded up) of 32 rows x 128 bytes
+  // with the 128-byte swizzle (1024-byte aligned)
+  static constexpr int BOXES = (FT::NN + 31) / 32;
+  static constexpr size_t tma_stage_bytes = size_t(4) * BOXES * 4096;
+  static constexpr size_t stage_max = stage_bytes > tma_stage_bytes ? stage_bytes : tma_stage_bytes;
+  static constexpr size_t region_bytes = stage_max > a_bytes ? stage_max : align_up(a_bytes, 1024);
+  static constexpr size_t b_region = align_up(b_bytes, 1024);  // keeps the region 1024-byte aligned
+  static constexpr size_t smem = b_region + region_bytes + 128 + 1024;  // + mbarrier, TMEM slot, alignment slack
   static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   static_assert(N >= 16 && N <= 256 && K % 16 == 0, "MMA shape");
 };
@@ -201,16 +207,54 @@ __device__ __forceinline__ void tc_epilogue_chunks(uint32_t tl, float* row) {
   }
 }
 
+// The N accumulator columns of this thread's TMEM lane (unique entries t of
+// the element matrix, t < NT), loaded 16 at a time.
+template <int N, int... Cs>
+__device__ __forceinline__ void tc_load_all(uint32_t tl, float (&r)[N], std::integer_sequence<int, Cs...>) {
+  (
+      [&] {
+        float c[16];
+        tmem_ld16(tl + uint32_t(Cs * 16), c);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) r[Cs * 16 + q] = c[q];
+      }(),
+      ...);
+  tmem_ld_wait();
+}
+
+// Unique-entry index of A[i][j] (symmetric: the (min, max) entry); entries
+// past the matrix (the padding of its last chunk) read entry 0.
+constexpr int tc_tri_index(int k, int n) {
+  return k >= n * n ? 0 : ((k / n) <= (k % n) ? pair_index(k / n, k % n, n) : pair_index(k % n, k / n, n));
+}
+
+// This thread's element row-major matrix as 16-byte chunks into its row of the
+// swizzled stage: chunk c lies in box c / 8 at 16-byte slot (c % 8) ^ sw of
+// the thread's 128-byte row (compile-time gather from the registers).
+template <int N, int NT, int... Cs>
+__device__ __forceinline__ void tc_stage_rows(const float (&r)[((NT + 15) / 16) * 16], unsigned char* row, int sw,
+                                              std::integer_sequence<int, Cs...>) {
+  (([&] {
+     *reinterpret_cast<float4*>(row + (Cs / 8) * 4096 + 16 * ((Cs % 8) ^ sw)) =
+         make_float4(r[tc_tri_index(4 * Cs, N)], r[tc_tri_index(4 * Cs + 1, N)], r[tc_tri_index(4 * Cs + 2, N)],
+                     r[tc_tri_index(4 * Cs + 3, N)]);
+   }()),
+   ...);
+}
+
 // Geo::tile_g<D, FORM>(p, mid, e, X, w, G) forms element e's folded G (zero on
 // return for an element it flags) and returns its device-error bits.
-template <int D, int FORM, class Geo, class KRef>
-__global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float, float> p, const float* mid) {
+template <int D, int FORM, class Geo, class KRef, bool TMA>
+__global__ void __launch_bounds__(kTileElems)
+    fem_fwd_tc_kernel(FwdParams<float, float> p, const float* mid, const __grid_constant__ CUtensorMap tmap) {
   using TP = TcPlan<D, FORM>;
   using FT = FormTraits<D, FORM>;
   constexpr int N = FT::N, NN = FT::NN, SST = TP::SST;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw_tc[];
+  // 1024-byte aligned base: the swizzled TMA stage follows the shared address
+  unsigned char* smem_raw = smem_raw_tc + ((1024u - (smem_u32(smem_raw_tc) & 1023u)) & 1023u);
   unsigned char* sb = smem_raw;                                      // B operand
-  unsigned char* region = smem_raw + align_up(TP::b_bytes, 128);     // A tile, then output stages
+  unsigned char* region = smem_raw + TP::b_region;                   // A tile, then output stages
   uint64_t* mbar_ptr = reinterpret_cast<uint64_t*>(region + TP::region_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(region + TP::region_bytes + 16);
   int* abort_flag = reinterpret_cast<int*>(region + TP::region_bytes + 32);
@@ -264,6 +308,12 @@ __global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float,
     } else if (fcur & GF_ELEM) {
       err |= DEVERR_CONN;
     }
+    if constexpr (TMA) {
+      // the previous tile's tensor stores drained while G was formed; every
+      // warp's stage has been read before any thread overwrites it with A
+      if (lane == 0) bulk_wait_read<0>();
+      __syncthreads();
+    }
     tc_store_a_row<D, FORM>(region, tid, G);
     fence_proxy_async_smem();  // generic-proxy writes of A -> tensor-core reads
     tc_fence_before();
@@ -287,12 +337,30 @@ __global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float,
     }
     phase ^= 1u;
     tc_fence_after();
+    const int64_t e0 = T * kTileElems + warp * 32;
+    if constexpr (TMA) {
+      // epilogue: this thread's TMEM lane -> registers -> its row's 16-byte
+      // chunks in the 128-byte-swizzled stage (chunk c of box b at c ^ (row & 7):
+      // conflict-free) -> one TMA tensor store per box, rows and columns past
+      // the array clipped
+      unsigned char* wst = region + size_t(warp) * TP::BOXES * 4096;
+      float r[TP::N];
+      tc_load_all<TP::N>(tmem + (uint32_t(warp * 32) << 16), r, std::make_integer_sequence<int, TP::N / 16>{});
+      tc_stage_rows<N, TP::NT>(r, wst + lane * 128, lane & 7, std::make_integer_sequence<int, (NN + 3) / 4>{});
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0 && e0 < p.n_elem) {
+#pragma unroll
+        for (int b = 0; b < TP::BOXES; ++b) tma_store_2d(&tmap, 32 * b, int(e0), smem_u32(wst + b * 4096));
+        bulk_commit();
+      }
+      __syncwarp();
+    } else {
     // epilogue: this warp's 32 rows of D -> mirrored stage -> coalesced stores
     float* st = reinterpret_cast<float*>(region) + warp * 32 * SST;
     float* row = st + lane * SST;
     tc_epilogue_chunks<D, FORM, 0>(tmem + (uint32_t(warp * 32) << 16), row);
     __syncwarp();
-    const int64_t e0 = T * kTileElems + warp * 32;
     if (e0 < p.n_elem) {
       const int cnt = int(p.n_elem - e0 < 32 ? p.n_elem - e0 : 32);
       float* dst = p.A + e0 * NN;
@@ -312,15 +380,21 @@ __global__ void __launch_bounds__(kTileElems) fem_fwd_tc_kernel(FwdParams<float,
         }
       }
     }
-    tc_fence_before();
-    __syncthreads();  // stages (aliasing the A tile) and TMEM are reused by the next tile
-    tc_fence_after();
+    }
+    if constexpr (!TMA) {
+      tc_fence_before();
+      __syncthreads();  // the stage (aliasing the A tile) is reused by the next tile
+      tc_fence_after();
+    }
     fcur = fnext;
     wcur = wnext;
 #pragma unroll
     for (int k = 0; k <= D; ++k)
 #pragma unroll
       for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+  }
+  if constexpr (TMA) {
+    if (lane == 0) bulk_wait<0>();  // this warp's tensor stores are complete
   }
   // teardown: after an abort, give the tensor core a bounded chance to finish first
   if (*abort_flag && tid == 0) mbar_wait(mbar, phase);
@@ -349,6 +423,11 @@ struct TcGeoAffine {
     return nondeg ? 0 : DEVERR_DEGENERATE;
   }
 };
+
+// Host: tensor map of a row-major [rows][cols] FP32 array (cols * 4 bytes a
+// multiple of 16) in boxes of 32 columns x 32 rows with the 128-byte swizzle;
+// false when it cannot be described (fem_tc.cu).
+bool encode_tc_rows_map(CUtensorMap* map, const void* base, int64_t rows, int cols);
 
 // CTAs of 128 threads that fit on an SM by registers (allocated per warp in
 // units of 8 per thread), shared memory (with the per-block reservation) and
@@ -388,12 +467,14 @@ cudaError_t launch_tc_t(const FwdLaunch& L, const float* mid) {
   p.dev_err = L.dev_err;
   p.vec_conn = 0;
   p.vec_store = reinterpret_cast<uintptr_t>(L.A) % 16 == 0;
-  auto kern = fem_fwd_tc_kernel<D, FORM, Geo, KRef>;
+  CUtensorMap tmap{};
+  const bool tma = encode_tc_rows_map(&tmap, L.A, L.n_elem, TcPlan<D, FORM>::FT::NN);
+  auto kern = tma ? fem_fwd_tc_kernel<D, FORM, Geo, KRef, true> : fem_fwd_tc_kernel<D, FORM, Geo, KRef, false>;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), TP::smem);
   if (st != cudaSuccess) return st;
   const int per_sm = L.ctas_per_sm > 0 ? L.ctas_per_sm : tc_ctas_per_sm(reinterpret_cast<const void*>(kern), TP::smem);
   const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), 4, TP::smem, L.n_elem, per_sm);
-  kern<<<grid, kTileElems, TP::smem, L.stream>>>(p, mid);
+  kern<<<grid, kTileElems, TP::smem, L.stream>>>(p, mid, tmap);
   return cudaGetLastError();
 }
 
