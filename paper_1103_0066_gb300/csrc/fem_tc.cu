@@ -38,20 +38,28 @@ bool encode_tc_rows_map(CUtensorMap* map, const void* base, int64_t rows, int co
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Reference tensors of the forms the tensor-core kernel serves, in constant memory.
-__constant__ RefTensor<3, ELASTIC_P1> kTcK3e = make_ref_tensor<3, ELASTIC_P1>();
-__constant__ RefTensor<3, LAPLACE_P2> kTcK3p = make_ref_tensor<3, LAPLACE_P2>();
-__constant__ RefTensor<2, ELASTIC_P1> kTcK2e = make_ref_tensor<2, ELASTIC_P1>();
-__constant__ RefTensor<2, LAPLACE_P2> kTcK2p = make_ref_tensor<2, LAPLACE_P2>();
+// B operands of the forms the tensor-core kernel serves, built at compile time.
+static_assert(tc_b_exact<3, ELASTIC_P1>() && tc_b_exact<3, LAPLACE_P2>() && tc_b_exact<2, ELASTIC_P1>() &&
+                  tc_b_exact<2, LAPLACE_P2>(),
+              "K' * DEN must be exact in BF16");
+__device__ const TcBImage<3, ELASTIC_P1> kTcB3e = make_tc_b_image<3, ELASTIC_P1>();
+__device__ const TcBImage<3, LAPLACE_P2> kTcB3p = make_tc_b_image<3, LAPLACE_P2>();
+__device__ const TcBImage<2, ELASTIC_P1> kTcB2e = make_tc_b_image<2, ELASTIC_P1>();
+__device__ const TcBImage<2, LAPLACE_P2> kTcB2p = make_tc_b_image<2, LAPLACE_P2>();
 
 struct TcKRefAffine {
   template <int D, int FORM>
-  __device__ __forceinline__ static int k(int g, int i, int j) {
-    if constexpr (D == 3 && FORM == ELASTIC_P1) return kTcK3e.v[g][i][j];
-    if constexpr (D == 3 && FORM == LAPLACE_P2) return kTcK3p.v[g][i][j];
-    if constexpr (D == 2 && FORM == ELASTIC_P1) return kTcK2e.v[g][i][j];
-    if constexpr (D == 2 && FORM == LAPLACE_P2) return kTcK2p.v[g][i][j];
-    return 0;
+  __device__ __forceinline__ static const TcBImage<D, FORM>* b_image() {
+    if constexpr (D == 3 && FORM == ELASTIC_P1) {
+      return &kTcB3e;
+    } else if constexpr (D == 3 && FORM == LAPLACE_P2) {
+      return &kTcB3p;
+    } else if constexpr (D == 2 && FORM == ELASTIC_P1) {
+      return &kTcB2e;
+    } else {
+      static_assert(D == 2 && FORM == LAPLACE_P2, "form without a tensor-core B operand");
+      return &kTcB2p;
+    }
   }
 };
 

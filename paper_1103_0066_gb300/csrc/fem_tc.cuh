@@ -9,12 +9,16 @@
 //       into three bf16 terms, g1 = bf16(G), g2 = bf16(G - g1),
 //       g3 = bf16(G - g1 - g2) (|G - g1 - g2 - g3| <= 2^-27 |G|), each term
 //       zero-padded to KT, a multiple of 16 (K = 3 KT),
-//   B[k][t] = K'[k mod KT][i][j] * DEN, small integers, exact in bf16.
+//   B[k][t] = K'[k mod KT][i][j] * DEN, small integers, exact in bf16; its
+//       shared-memory image is built at compile time and copied by each CTA.
 // The MMA (tcgen05.mma kind::f16, M = 128, N, K = 16 per step, FP32
 // accumulation in TMEM) is issued by one thread; its completion is signalled
 // on an mbarrier.  Each warp then reads its 32 rows of D with tcgen05.ld
-// (lane = element), mirrors (i, j) -> (j, i) into its shared-memory stage and
-// stores the tile with coalesced 16-byte stores, as the FP32 kernel does.
+// (lane = element) and mirrors (i, j) -> (j, i) into a 128-byte-swizzled
+// shared stage, from which TMA tensor stores write 32 x 32 boxes of the
+// [n_elem][N*N] output.  The stage holds as many boxes as keep the most CTAs
+// resident; the last stores drain while the next tile's geometry is formed.
+// (Without a tensor map, a plain stage and coalesced 16-byte stores.)
 // Operands live in shared memory in the canonical no-swizzle K-major layout:
 // 8x16-byte core matrices, K-adjacent cores LBO bytes apart, M/N-adjacent cores
 // SBO bytes apart.  All waits are bounded: on a timeout the kernel flags
@@ -48,14 +52,36 @@ struct TcPlan {
   static constexpr size_t b_bytes = size_t(N) * K * 2;
   static constexpr int SST = stage_stride<FT::NN>();
   static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);  // aliases the A tile
-  // TMA epilogue: per warp, NN / 32 boxes (rounded up) of 32 rows x 128 bytes
-  // with the 128-byte swizzle (1024-byte aligned)
-  static constexpr int BOXES = (FT::NN + 31) / 32;
-  static constexpr size_t tma_stage_bytes = size_t(4) * BOXES * 4096;
-  static constexpr size_t stage_max = stage_bytes > tma_stage_bytes ? stage_bytes : tma_stage_bytes;
-  static constexpr size_t region_bytes = stage_max > a_bytes ? stage_max : align_up(a_bytes, 1024);
   static constexpr size_t b_region = align_up(b_bytes, 1024);  // keeps the region 1024-byte aligned
-  static constexpr size_t smem = b_region + region_bytes + 128 + 1024;  // + mbarrier, TMEM slot, alignment slack
+  // TMA epilogue: per warp, NN / 32 boxes (rounded up) of 32 rows x 128 bytes
+  // with the 128-byte swizzle (1024-byte aligned), staged SBOX boxes at a time
+  static constexpr int BOXES = (FT::NN + 31) / 32;
+  static constexpr size_t region_for(int sbox) {
+    return size_t(4) * sbox * 4096 > align_up(a_bytes, 1024) ? size_t(4) * sbox * 4096 : align_up(a_bytes, 1024);
+  }
+  static constexpr size_t smem_for(size_t region) { return b_region + region + 128 + 1024; }  // + mbarrier, TMEM slot, slack
+  // CTAs that the shared memory of an SM (228 KB, 1 KB reserved per CTA)
+  // holds, up to the four that 128-thread CTAs at 128 registers a thread fill
+  static constexpr int fit(int sbox) {
+    return int(size_t(233472) / (smem_for(region_for(sbox)) + 1024)) < 4
+               ? int(size_t(233472) / (smem_for(region_for(sbox)) + 1024))
+               : 4;
+  }
+  // the largest stage that keeps the most CTAs resident: a smaller stage costs
+  // a wait for the tensor stores inside the epilogue
+  static constexpr int pick_sbox() {
+    int best = BOXES;
+    for (int s = BOXES - 1; s >= 1; --s)
+      if (fit(s) > fit(best)) best = s;
+    return best;
+  }
+  static constexpr int SBOX = pick_sbox();
+  static constexpr int GROUPS = (BOXES + SBOX - 1) / SBOX;
+  template <bool TMA>
+  static constexpr size_t region_bytes = TMA ? region_for(SBOX)
+                                             : (stage_bytes > a_bytes ? stage_bytes : align_up(a_bytes, 1024));
+  template <bool TMA>
+  static constexpr size_t smem = smem_for(region_bytes<TMA>);
   static constexpr int TMEM_COLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
   static_assert(N >= 16 && N <= 256 && K % 16 == 0, "MMA shape");
 };
@@ -129,24 +155,67 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 
 // ------------------------------------------------------------------ operand staging
 
-// bf16 bits of a float, round to nearest even
-__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
-__device__ __forceinline__ float bf16_value(uint16_t b) { return __uint_as_float(uint32_t(b) << 16); }
+// BF16 bits of an integer that BF16 holds exactly (at most 8 significant
+// bits); 0x10000 for one that it does not.
+constexpr uint32_t bf16_of_int(int v) {
+  if (v == 0) return 0;
+  const uint32_t sign = v < 0 ? 0x8000u : 0u;
+  const uint32_t a = v < 0 ? uint32_t(-v) : uint32_t(v);
+  int e = 31;
+  while (!((a >> e) & 1u)) --e;  // leading bit
+  if (e > 7 && (a & ((1u << (e - 7)) - 1u))) return 0x10000u;
+  const uint32_t mant = (e >= 7 ? a >> (e - 7) : a << (7 - e)) & 0x7Fu;
+  return sign | (uint32_t(e + 127) << 7) | mant;
+}
 
-// B[k][t] in the core-matrix layout, written once per CTA; KRef::k<D, FORM>(g, i, j)
-// gives K'_g^{ij} * DEN.
+// The B operand as it lies in shared memory: B[k][t] = K'_g^{ij} * DEN for
+// k = term * KT + g (the same K for each of the three terms of G), (i, j) the
+// t-th unique entry, zero past NG and NT; BF16 bits in the K-major core-matrix
+// layout (core (k / 8, t / 8), row t % 8, column k % 8). Built at compile time.
+template <int D, int FORM>
+struct alignas(16) TcBImage {
+  uint16_t v[TcPlan<D, FORM>::N * TcPlan<D, FORM>::K];
+};
+
+template <int D, int FORM>
+constexpr int tc_b_value(const RefTensor<D, FORM>& kt, int t, int k) {
+  using TP = TcPlan<D, FORM>;
+  using FT = FormTraits<D, FORM>;
+  const int g = k % TP::KT;
+  return (t < TP::NT && g < FT::NG) ? kt.v[g][tri_row(t, FT::N)][tri_col(t, FT::N)] : 0;
+}
+
+template <int D, int FORM>
+constexpr TcBImage<D, FORM> make_tc_b_image() {
+  using TP = TcPlan<D, FORM>;
+  const RefTensor<D, FORM> kt = make_ref_tensor<D, FORM>();
+  TcBImage<D, FORM> im{};
+  for (int t = 0; t < TP::N; ++t)
+    for (int k = 0; k < TP::K; ++k)
+      im.v[((k / 8) * TP::NC + t / 8) * 64 + (t % 8) * 8 + k % 8] = uint16_t(bf16_of_int(tc_b_value(kt, t, k)));
+  return im;
+}
+
+// Whether every entry of K' * DEN is exact in BF16 (the split of G carries all
+// of the rounding).
+template <int D, int FORM>
+constexpr bool tc_b_exact() {
+  const RefTensor<D, FORM> kt = make_ref_tensor<D, FORM>();
+  for (int t = 0; t < TcPlan<D, FORM>::N; ++t)
+    for (int k = 0; k < TcPlan<D, FORM>::K; ++k)
+      if (bf16_of_int(tc_b_value(kt, t, k)) > 0xFFFFu) return false;
+  return true;
+}
+
+// B into shared memory, once per CTA: a copy of KRef::b_image<D, FORM>() in
+// 16-byte loads.
 template <int D, int FORM, class KRef>
 __device__ void tc_fill_b(unsigned char* sb) {
   using TP = TcPlan<D, FORM>;
-  using FT = FormTraits<D, FORM>;
-  for (int idx = threadIdx.x; idx < TP::N * TP::K; idx += blockDim.x) {
-    const int t = idx / TP::K, k = idx % TP::K;
-    const int g = k % TP::KT;
-    int val = 0;
-    if (t < TP::NT && g < FT::NG) val = KRef::template k<D, FORM>(g, tri_row(t, FT::N), tri_col(t, FT::N));
-    const uint32_t off = uint32_t((k / 8) * TP::NC + t / 8) * 128u + uint32_t(t % 8) * 16u + uint32_t(k % 8) * 2u;
-    *reinterpret_cast<uint16_t*>(sb + off) = bf16_bits(float(val));
-  }
+  static_assert(TP::b_bytes % 16 == 0 && sizeof(TcBImage<D, FORM>) == TP::b_bytes, "B image");
+  const uint4* src = reinterpret_cast<const uint4*>(KRef::template b_image<D, FORM>()->v);
+  uint4* dst = reinterpret_cast<uint4*>(sb);
+  for (int i = threadIdx.x; i < int(TP::b_bytes / 16); i += blockDim.x) dst[i] = __ldg(src + i);
 }
 
 // Row m of the A tile: the three bf16 terms of G (zero padded) in the core layout.
@@ -231,13 +300,43 @@ constexpr int tc_tri_index(int k, int n) {
 // This thread's element row-major matrix as 16-byte chunks into its row of the
 // swizzled stage: chunk c lies in box c / 8 at 16-byte slot (c % 8) ^ sw of
 // the thread's 128-byte row (compile-time gather from the registers).
-template <int N, int NT, int... Cs>
+// Only boxes B0 .. B0 + NB - 1 are written, box B0 first in the stage.
+template <int N, int NT, int B0, int NB, int... Cs>
 __device__ __forceinline__ void tc_stage_rows(const float (&r)[((NT + 15) / 16) * 16], unsigned char* row, int sw,
                                               std::integer_sequence<int, Cs...>) {
   (([&] {
-     *reinterpret_cast<float4*>(row + (Cs / 8) * 4096 + 16 * ((Cs % 8) ^ sw)) =
-         make_float4(r[tc_tri_index(4 * Cs, N)], r[tc_tri_index(4 * Cs + 1, N)], r[tc_tri_index(4 * Cs + 2, N)],
-                     r[tc_tri_index(4 * Cs + 3, N)]);
+     if constexpr (Cs / 8 >= B0 && Cs / 8 < B0 + NB) {
+       *reinterpret_cast<float4*>(row + (Cs / 8 - B0) * 4096 + 16 * ((Cs % 8) ^ sw)) =
+           make_float4(r[tc_tri_index(4 * Cs, N)], r[tc_tri_index(4 * Cs + 1, N)], r[tc_tri_index(4 * Cs + 2, N)],
+                       r[tc_tri_index(4 * Cs + 3, N)]);
+     }
+   }()),
+   ...);
+}
+
+// A warp's 32 element matrices (rows e0 .. e0 + 31 of the [n_elem][N*N] array)
+// out through its stage, SBOX boxes per group; lane 0 issues the tensor
+// stores and, between groups, waits until they have read the stage. The last
+// group's stores are left in flight.
+template <class TP, int N, int NT, int... Gs>
+__device__ __forceinline__ void tc_store_groups(const float (&r)[((NT + 15) / 16) * 16], unsigned char* wst, int lane,
+                                                const CUtensorMap* tmap, int64_t e0, bool live,
+                                                std::integer_sequence<int, Gs...>) {
+  (([&] {
+     constexpr int B0 = Gs * TP::SBOX;
+     constexpr int NB = TP::BOXES - B0 < TP::SBOX ? TP::BOXES - B0 : TP::SBOX;
+     if constexpr (Gs > 0) {
+       if (lane == 0) bulk_wait_read<0>();
+       __syncwarp();
+     }
+     tc_stage_rows<N, NT, B0, NB>(r, wst + lane * 128, lane & 7, std::make_integer_sequence<int, (N * N + 3) / 4>{});
+     fence_proxy_async_smem();
+     __syncwarp();
+     if (lane == 0 && live) {
+#pragma unroll
+       for (int b = 0; b < NB; ++b) tma_store_2d(tmap, 32 * (B0 + b), int(e0), smem_u32(wst + b * 4096));
+       bulk_commit();
+     }
    }()),
    ...);
 }
@@ -255,9 +354,9 @@ __global__ void __launch_bounds__(kTileElems)
   unsigned char* smem_raw = smem_raw_tc + ((1024u - (smem_u32(smem_raw_tc) & 1023u)) & 1023u);
   unsigned char* sb = smem_raw;                                      // B operand
   unsigned char* region = smem_raw + TP::b_region;                   // A tile, then output stages
-  uint64_t* mbar_ptr = reinterpret_cast<uint64_t*>(region + TP::region_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(region + TP::region_bytes + 16);
-  int* abort_flag = reinterpret_cast<int*>(region + TP::region_bytes + 32);
+  uint64_t* mbar_ptr = reinterpret_cast<uint64_t*>(region + TP::template region_bytes<TMA>);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(region + TP::template region_bytes<TMA> + 16);
+  int* abort_flag = reinterpret_cast<int*>(region + TP::template region_bytes<TMA> + 32);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t mbar = smem_u32(mbar_ptr);
   const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
@@ -343,17 +442,11 @@ __global__ void __launch_bounds__(kTileElems)
       // chunks in the 128-byte-swizzled stage (chunk c of box b at c ^ (row & 7):
       // conflict-free) -> one TMA tensor store per box, rows and columns past
       // the array clipped
-      unsigned char* wst = region + size_t(warp) * TP::BOXES * 4096;
+      unsigned char* wst = region + size_t(warp) * TP::SBOX * 4096;
       float r[TP::N];
       tc_load_all<TP::N>(tmem + (uint32_t(warp * 32) << 16), r, std::make_integer_sequence<int, TP::N / 16>{});
-      tc_stage_rows<N, TP::NT>(r, wst + lane * 128, lane & 7, std::make_integer_sequence<int, (NN + 3) / 4>{});
-      fence_proxy_async_smem();
-      __syncwarp();
-      if (lane == 0 && e0 < p.n_elem) {
-#pragma unroll
-        for (int b = 0; b < TP::BOXES; ++b) tma_store_2d(&tmap, 32 * b, int(e0), smem_u32(wst + b * 4096));
-        bulk_commit();
-      }
+      tc_store_groups<TP, N, TP::NT>(r, wst, lane, &tmap, e0, e0 < p.n_elem,
+                                     std::make_integer_sequence<int, TP::GROUPS>{});
       __syncwarp();
     } else {
     // epilogue: this warp's 32 rows of D -> mirrored stage -> coalesced stores
@@ -470,11 +563,12 @@ cudaError_t launch_tc_t(const FwdLaunch& L, const float* mid) {
   CUtensorMap tmap{};
   const bool tma = encode_tc_rows_map(&tmap, L.A, L.n_elem, TcPlan<D, FORM>::FT::NN);
   auto kern = tma ? fem_fwd_tc_kernel<D, FORM, Geo, KRef, true> : fem_fwd_tc_kernel<D, FORM, Geo, KRef, false>;
-  cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), TP::smem);
+  const size_t smem = tma ? TP::template smem<true> : TP::template smem<false>;
+  cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
-  const int per_sm = L.ctas_per_sm > 0 ? L.ctas_per_sm : tc_ctas_per_sm(reinterpret_cast<const void*>(kern), TP::smem);
-  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), 4, TP::smem, L.n_elem, per_sm);
-  kern<<<grid, kTileElems, TP::smem, L.stream>>>(p, mid, tmap);
+  const int per_sm = L.ctas_per_sm > 0 ? L.ctas_per_sm : tc_ctas_per_sm(reinterpret_cast<const void*>(kern), smem);
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), 4, smem, L.n_elem, per_sm);
+  kern<<<grid, kTileElems, smem, L.stream>>>(p, mid, tmap);
   return cudaGetLastError();
 }
 

@@ -9,14 +9,18 @@
 
 namespace fem {
 
-__constant__ RefTensor<3, LAPLACE_P2_ISO> kTcK3iso = make_ref_tensor<3, LAPLACE_P2_ISO>();
-__constant__ RefTensor<2, LAPLACE_P2_ISO> kTcK2iso = make_ref_tensor<2, LAPLACE_P2_ISO>();
+static_assert(tc_b_exact<3, LAPLACE_P2_ISO>() && tc_b_exact<2, LAPLACE_P2_ISO>(), "K' * DEN must be exact in BF16");
+__device__ const TcBImage<3, LAPLACE_P2_ISO> kTcB3iso = make_tc_b_image<3, LAPLACE_P2_ISO>();
+__device__ const TcBImage<2, LAPLACE_P2_ISO> kTcB2iso = make_tc_b_image<2, LAPLACE_P2_ISO>();
 
 struct TcKRefIso {
   template <int D, int FORM>
-  __device__ __forceinline__ static int k(int g, int i, int j) {
-    if constexpr (D == 3) return kTcK3iso.v[g][i][j];
-    return kTcK2iso.v[g][i][j];
+  __device__ __forceinline__ static const TcBImage<D, FORM>* b_image() {
+    if constexpr (D == 3) {
+      return &kTcB3iso;
+    } else {
+      return &kTcB2iso;
+    }
   }
 };
 
