@@ -77,3 +77,23 @@ def test_full_size_elasticity_sampled(gfem, orc):
         Ag = A[sel].cpu().numpy()
         del A
         assert rel_err_per_element(Ag, Ar).max() <= TOL
+
+
+@pytest.mark.parametrize("dim,form", [(3, EP1), (2, LP2)])
+def test_tensor_core_unaligned_output_same_bits(gfem, dim, form):
+    """An output 4 bytes off a 16-byte boundary has no tensor map: the kernel
+    takes its plain stage and scalar stores. Only the epilogue's data movement
+    differs, so the bits equal the TMA path's."""
+    if dim == 3:
+        mesh = mg.cube_tet_mesh(5, 0.15, mg.rng_for(75), 0.05, np.float32)
+    else:
+        mesh = mg.square_tri_mesh(17, 0.2, mg.rng_for(75), np.float32)
+    n = (dim + 1) * dim if form == EP1 else (dim + 1) * (dim + 2) // 2
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    A = gfem.integrate_fwd(coords, conn, form, contract=gfem.CONTRACT_BF16X3)
+    buf = torch.full((mesh.n_elem * n * n + 1,), float("nan"), device=DEV)
+    out = buf[1:].view(mesh.n_elem, n, n)
+    assert out.data_ptr() % 16 == 4
+    B = gfem.integrate_fwd(coords, conn, form, contract=gfem.CONTRACT_BF16X3, out=out)
+    torch.cuda.synchronize()
+    assert B.data_ptr() == out.data_ptr() and torch.equal(A, B)
