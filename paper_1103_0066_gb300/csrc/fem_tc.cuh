@@ -5,9 +5,11 @@
 // Eq. 6 is the dense product  D[e][t] = sum_k Ahat[e][k] B[k][t]  where
 //   t = (i, j), i <= j, runs over the unique entries of A_e (NT of them,
 //       padded to N, a multiple of 16),
-//   Ahat[e] = [ g1 | g2 | g3 ]: the folded geometric tensor G_e split exactly
+//   Ahat[e] = [ g1 | g2 | g3 ]: the folded geometric tensor G_e split
 //       into three bf16 terms, g1 = bf16(G), g2 = bf16(G - g1),
-//       g3 = bf16(G - g1 - g2) (|G - g1 - g2 - g3| <= 2^-27 |G|), each term
+//       g3 = bf16(G - g1 - g2) (each rounding to bf16's 8-bit significand
+//       leaves at most 2^-8 of what it rounds, so |G - g1 - g2 - g3| <=
+//       2^-24 |G|, FP32's own unit roundoff), each term
 //       zero-padded to KT, a multiple of 16 (K = 3 KT),
 //   B[k][t] = K'[k mod KT][i][j] * DEN, small integers, exact in bf16; its
 //       shared-memory image is built at compile time and copied by each CTA.

@@ -1,8 +1,9 @@
 """Split-BF16 tensor-core contraction (tcgen05) against the FP64 oracle (-m gpu).
 
-The three-term bf16 split of G leaves at most 2^-27 |G| per entry and K is
-exact in bf16, so the per-element tolerance is the FP32 one, 1e-5 relative to
-max |A_e|, on every element including slivers."""
+Each rounding to bf16's 8-bit significand leaves at most 2^-8 of what it
+rounds, so the three-term split of G leaves at most 2^-24 |G| per entry (FP32's
+own unit roundoff), and K is exact in bf16: the per-element tolerance is the
+FP32 one, 1e-5 relative to max |A_e|, on every element including slivers."""
 import numpy as np
 import pytest
 import torch
