@@ -320,12 +320,13 @@ class HostStep:
 
 class _IntegrateFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, coords, coef, mesh, form, jac, reduce):
-        # det J is kept for the adjoint when it can take it (FP32 coordinates, affine form)
+    def forward(ctx, coords, coef, mesh, form, jac, reduce, contract):
+        # det J is kept for the adjoint when it can take it (FP32 coordinates, affine
+        # form, FP32 contraction)
         keep = (coords.dtype == torch.float32 and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1)
-                and jac in (JAC_AUTO, JAC_COMP_F32))
+                and jac in (JAC_AUTO, JAC_COMP_F32) and contract == CONTRACT_F32)
         det = torch.empty(mesh.conn.shape[0], dtype=torch.float32, device=coords.device) if keep else None
-        A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac, det_out=det)
+        A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac, contract=contract, det_out=det)
         ctx.det = det
         ctx.save_for_backward(coords, coef if coef is not None else torch.empty(0))
         ctx.mesh, ctx.form, ctx.jac, ctx.reduce = mesh, form, jac, reduce
@@ -342,7 +343,7 @@ class _IntegrateFn(torch.autograd.Function):
         dx, dw = integrate_bwd(coords.detach(), ctx.mesh.conn, ctx.form, dA.contiguous().float(), coef,
                                ws=ws, reduce=ctx.reduce, need_dcoords=need_x, need_dcoef=need_w,
                                jac=ctx.jac, det=ctx.det)
-        return dx, dw, None, None, None, None
+        return dx, dw, None, None, None, None, None
 
 
 class Mesh:
@@ -362,17 +363,21 @@ class Mesh:
             self._ws["ws"] = Workspace(self.coords.detach(), self.conn, form)
         return self._ws["ws"]
 
-    def integrate(self, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC, coords=None):
-        """Element matrices, differentiable with respect to coords and coef."""
+    def integrate(self, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC, coords=None,
+                  contract=CONTRACT_F32):
+        """Element matrices, differentiable with respect to coords and coef.
+
+        contract=CONTRACT_BF16X3 contracts the forward on the tensor cores (P2 and
+        elasticity); the adjoint is the FP32 one either way."""
         x = self.coords if coords is None else coords
         if x.dtype != torch.float32 and (x.requires_grad or (coef is not None and coef.requires_grad)):
             raise ValueError("the adjoint takes float32 coordinates")
-        return _IntegrateFn.apply(x, coef, self, form, jac, reduce)
+        return _IntegrateFn.apply(x, coef, self, form, jac, reduce, contract)
 
 
-def integrate(coords, conn, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC):
+def integrate(coords, conn, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC, contract=CONTRACT_F32):
     """Differentiable element matrices for a one-off mesh (builds the incidence on first backward)."""
-    return Mesh(coords, conn).integrate(form, coef, jac, reduce)
+    return Mesh(coords, conn).integrate(form, coef, jac, reduce, contract=contract)
 
 
 class Batch:

@@ -9,6 +9,7 @@ import pytest
 import torch
 
 from paper_1103_0066_gb300 import meshgen as mg
+from conftest import rel_err_per_element
 
 pytestmark = pytest.mark.gpu
 LP1, LP2, EP1 = 0, 1, 2
@@ -149,6 +150,26 @@ def test_autograd_function(gfem, orc):
     gx, gw = orc.integrate_vjp(3, EP1, mesh.conn, mesh.coords, dA, coef0)
     assert _rel(x.grad.cpu().numpy(), gx) <= TOL
     assert _rel(w.grad.cpu().numpy(), gw) <= TOL
+
+
+def test_autograd_tensor_core_forward(gfem, orc):
+    """fem.integrate(..., contract=BF16X3): the forward on the tensor cores within
+    the FP32 tolerance of the oracle; the adjoint is the FP32 one, so the
+    deterministic gradients equal the FP32-contract ones bit for bit."""
+    mesh = _mesh(3)
+    coef0 = mg.lognormal_coef(mg.rng_for(47), mesh.n_elem)
+    dA = _t(mg.upstream(mg.rng_for(48), mesh.n_elem, 12))
+    grads = {}
+    for contract in (gfem.CONTRACT_F32, gfem.CONTRACT_BF16X3):
+        x = _t(mesh.coords).requires_grad_(True)
+        w = _t(coef0).requires_grad_(True)
+        A = gfem.integrate(x, _t(mesh.conn), EP1, w, contract=contract)
+        (A * dA).sum().backward()
+        grads[contract] = (A.detach(), x.grad, w.grad)
+    Ar, _ = orc.integrate(3, EP1, mesh.conn, mesh.coords, coef0)
+    assert rel_err_per_element(grads[gfem.CONTRACT_BF16X3][0].cpu().numpy(), Ar).max() <= TOL
+    assert torch.equal(grads[gfem.CONTRACT_F32][1], grads[gfem.CONTRACT_BF16X3][1])
+    assert torch.equal(grads[gfem.CONTRACT_F32][2], grads[gfem.CONTRACT_BF16X3][2])
 
 
 def test_adjoint_against_fp64_finite_differences(gfem, orc):
