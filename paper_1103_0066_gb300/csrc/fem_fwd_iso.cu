@@ -11,10 +11,11 @@
 //      J^{-1}_k = adj / det -- the values the projection of Eq. 17 interpolates;
 //   3. |J| = |det J| at the centroid (Eq. 17 keeps |J| outside the integral);
 //   4. G^{(k mu),(l nu)} = w |J| / DEN  sum_a J^{-1}_{mu a,k} J^{-1}_{nu a,l}
-//      over the folded slot pairs (Eq. 18), each entry added into the
-//      accumulators of A as soon as it is formed (A_ij += K^{ij}_g G_g with K
-//      as immediates, g in increasing order: the sums of the G-first
-//      contraction, without holding all of G in registers), then the same
+//      over the folded slot pairs (Eq. 18), each entry (without the common
+//      factor w |J| / DEN) added into the accumulators of A as soon as it is
+//      formed (A_ij += K^{ij}_g G_g with K as immediates, g in increasing
+//      order: the sums of the G-first contraction, without holding all of G
+//      in registers), the factor applied once per entry of A, then the same
 //      tile store as the affine kernel (Eq. 19).
 // The Jacobian steps run in plain FP32: this path serves curved, non-sliver
 // elements; an element with a singular J at a vertex or at the centroid is
@@ -45,21 +46,26 @@ __device__ __forceinline__ void scatter_g(float* acc, float gv, std::integer_seq
   (kscatter<D, FORM, G, Ts>(acc, gv), ...);
 }
 
-// G_g for the slot pair g = (p, q), p <= q, p = (k mu): scale * sum_a Jinv_{mu a,k} Jinv_{nu a,l}.
+// G_g / scale for the slot pair g = (p, q), p <= q, p = (k mu):
+// sum_a Jinv_{mu a,k} Jinv_{nu a,l}.
 template <int D, int FORM, int G>
-__device__ __forceinline__ void iso_term(const float (&ji)[D + 1][D][D], float scale, float* acc) {
+__device__ __forceinline__ void iso_term(const float (&ji)[D + 1][D][D], float* acc) {
   using FT = FormTraits<D, FORM>;
   constexpr int pp = tri_row(G, FT::NP), qq = tri_col(G, FT::NP);
   float s = 0.f;
 #pragma unroll
   for (int al = 0; al < D; ++al) s = fmaf(ji[pp / D][pp % D][al], ji[qq / D][qq % D][al], s);
-  scatter_g<D, FORM, G>(acc, scale * s, std::make_integer_sequence<int, FT::NT>{});
+  scatter_g<D, FORM, G>(acc, s, std::make_integer_sequence<int, FT::NT>{});
 }
 
+// acc = scale * sum_g K_g G_g / scale: the common factor scale = w |J| / DEN
+// once per entry of A rather than once per G entry.
 template <int D, int FORM, int... Gs>
 __device__ __forceinline__ void iso_accumulate(const float (&ji)[D + 1][D][D], float scale, float* acc,
                                                std::integer_sequence<int, Gs...>) {
-  (iso_term<D, FORM, Gs>(ji, scale, acc), ...);
+  (iso_term<D, FORM, Gs>(ji, acc), ...);
+#pragma unroll
+  for (int t = 0; t < FormTraits<D, FORM>::NT; ++t) acc[t] *= scale;
 }
 
 template <int D, int FORM, class Sink, int... Ts>

@@ -11,21 +11,14 @@
 namespace fem {
 
 // d psi_a / d xi_mu of the quadratic geometry basis (vertices, then edges in
-// the P2 order) at reference vertex k (k <= D), or (D + 1) times it at the
-// centroid (k = D + 1); all integers.
+// the P2 order) at reference vertex k (k <= D); all integers.
 template <int D>
 constexpr int geo_dpsi(int a, int mu, int k) {
-  if (a <= D) {
-    if (k <= D) return (a == k ? 3 : -1) * dlam(a, mu);
-    return (3 - D) * dlam(a, mu);  // (D+1) * (4/(D+1) - 1)
-  }
+  if (a <= D) return (a == k ? 3 : -1) * dlam(a, mu);
   int t = a - (D + 1);
   for (int p = 0; p <= D; ++p)
     for (int q = p + 1; q <= D; ++q) {
-      if (t == 0) {
-        if (k <= D) return 4 * ((p == k ? dlam(q, mu) : 0) + (q == k ? dlam(p, mu) : 0));
-        return 4 * (dlam(p, mu) + dlam(q, mu));
-      }
+      if (t == 0) return 4 * ((p == k ? dlam(q, mu) : 0) + (q == k ? dlam(p, mu) : 0));
       --t;
     }
   return 0;
@@ -59,10 +52,16 @@ __device__ __forceinline__ float det_adj(const float (&e)[D][D], float (&adj)[D]
   return det;
 }
 
+// J^{-1} at vertex K into ji[K]; J at vertex K added into esum.
 template <int D, int K>
-__device__ __forceinline__ bool vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D]) {
+__device__ __forceinline__ bool vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D],
+                                            float (&esum)[D][D]) {
   float e[D][D], adj[D][D];
   geo_jacobian<D, K>(nd, e);
+#pragma unroll
+  for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+    for (int al = 0; al < D; ++al) esum[mu][al] = K == 0 ? e[mu][al] : esum[mu][al] + e[mu][al];
   const float det = det_adj<D>(e, adj);
   const float r = __frcp_rn(det);
 #pragma unroll
@@ -74,8 +73,8 @@ __device__ __forceinline__ bool vertex_jinv(const float (&nd)[n_geo(D)][D], floa
 
 template <int D, int... Ks>
 __device__ __forceinline__ bool all_vertex_jinv(const float (&nd)[n_geo(D)][D], float (&ji)[D + 1][D][D],
-                                                std::integer_sequence<int, Ks...>) {
-  return (vertex_jinv<D, Ks>(nd, ji) & ...);
+                                                float (&esum)[D][D], std::integer_sequence<int, Ks...>) {
+  return (vertex_jinv<D, Ks>(nd, ji, esum) & ...);
 }
 
 // One element's inverse Jacobians at its vertices (ji[k][mu][al] = (J^{-1})_{mu al}
@@ -95,9 +94,10 @@ __device__ __forceinline__ bool iso_geometry(const float (&X)[D + 1][D], const f
   for (int q = 0; q < NE; ++q)
 #pragma unroll
     for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = __ldcs(m + q * D + al) - X[0][al];
-  bool ok = all_vertex_jinv<D>(nd, ji, std::make_integer_sequence<int, D + 1>{});
+  // J is affine in xi (psi quadratic), so the sum of the vertex Jacobians is
+  // (D + 1) J at the centroid
   float ec[D][D], adjc[D][D];
-  geo_jacobian<D, D + 1>(nd, ec);  // (D + 1) J at the centroid
+  bool ok = all_vertex_jinv<D>(nd, ji, ec, std::make_integer_sequence<int, D + 1>{});
   float detc = det_adj<D>(ec, adjc);
   detc *= D == 2 ? (1.f / 9.f) : (1.f / 64.f);  // det scales by (D + 1)^D
   ok &= detc != 0.f;
