@@ -392,12 +392,15 @@ __global__ void __launch_bounds__(kTileElems)
   load_conn<D>(p.conn, T * kTileElems + tid, p.n_elem, vec_conn, v);
   int fcur = gather_regs<D>(p.coords, p.n_vert, T * kTileElems + tid, p.n_elem, v, Xc);
   float wcur = (p.coef && T * kTileElems + tid < p.n_elem) ? __ldg(p.coef + T * kTileElems + tid) : 1.f;
+  int vn[D + 1];  // the next tile's connectivity, loaded a tile before its gather
+  load_conn<D>(p.conn, (T + gridDim.x) * kTileElems + tid, p.n_elem, vec_conn, vn);
   for (; T < nct; T += gridDim.x) {
-    // prefetch the next tile's connectivity and coordinates
+    // prefetch: connectivity two tiles ahead, the next tile's coordinates
+    // (its connectivity arrived during the previous tile)
     const int64_t en = (T + gridDim.x) * kTileElems + tid;
+    int vnn[D + 1];
+    load_conn<D>(p.conn, en + int64_t(gridDim.x) * kTileElems, p.n_elem, vec_conn, vnn);
     float Xn[D + 1][D];
-    int vn[D + 1];
-    load_conn<D>(p.conn, en, p.n_elem, vec_conn, vn);
     const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vn, Xn);
     const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
     // geometric tensor of this thread's element -> bf16 split into the A tile
@@ -484,9 +487,11 @@ __global__ void __launch_bounds__(kTileElems)
     fcur = fnext;
     wcur = wnext;
 #pragma unroll
-    for (int k = 0; k <= D; ++k)
+    for (int k = 0; k <= D; ++k) {
+      vn[k] = vnn[k];
 #pragma unroll
       for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+    }
   }
   if constexpr (TMA) {
     if (lane == 0) bulk_wait<0>();  // this warp's tensor stores are complete
