@@ -53,7 +53,8 @@ struct TcPlan {
   static constexpr size_t a_bytes = size_t(M) * K * 2;
   static constexpr size_t b_bytes = size_t(N) * K * 2;
   static constexpr int SST = stage_stride<FT::NN>();
-  static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);  // aliases the A tile
+  // the plain epilogue's stage (without a tensor map), aliasing the A tile
+  static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);
   static constexpr size_t b_region = align_up(b_bytes, 1024);  // keeps the region 1024-byte aligned
   // TMA epilogue: per warp, NN / 32 boxes (rounded up) of 32 rows x 128 bytes
   // with the 128-byte swizzle (1024-byte aligned), staged SBOX boxes at a time
@@ -530,10 +531,11 @@ struct TcGeoAffine {
 bool encode_tc_rows_map(CUtensorMap* map, const void* base, int64_t rows, int cols);
 
 // CTAs of 128 threads that fit on an SM by registers (allocated per warp in
-// units of 8 per thread), shared memory (with the per-block reservation) and
-// threads.  The occupancy API reports one for these kernels where two fit and
-// run side by side (measured 1.5x faster).
-inline int tc_ctas_per_sm(const void* kern, size_t smem) {
+// units of 8 per thread), shared memory (with the per-block reservation),
+// threads and TMEM columns (512 per SM: a CTA beyond them would wait in
+// tcgen05.alloc until another finished).  The occupancy API reports one for
+// these kernels where two fit and run side by side (measured 1.5x faster).
+inline int tc_ctas_per_sm(const void* kern, size_t smem, int tmem_cols) {
   cudaFuncAttributes fa{};
   int dev = 0, regs = 0, shm = 0, rsv = 0, thr = 0, blk = 0;
   if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
@@ -550,7 +552,8 @@ inline int tc_ctas_per_sm(const void* kern, size_t smem) {
   const int by_regs = regs_per_warp > 0 ? regs / regs_per_warp / warps : blk;
   const int by_smem = int(size_t(shm) / (smem + fa.sharedSizeBytes + size_t(rsv)));
   const int by_thr = thr / kTileElems;
-  const int n = std::min(std::min(by_regs, by_smem), std::min(by_thr, blk));
+  const int by_tmem = 512 / tmem_cols;  // TMEM columns of an SM
+  const int n = std::min(std::min(std::min(by_regs, by_smem), std::min(by_thr, blk)), by_tmem);
   return n < 1 ? 1 : n;
 }
 
@@ -573,7 +576,8 @@ cudaError_t launch_tc_t(const FwdLaunch& L, const float* mid) {
   const size_t smem = tma ? TP::template smem<true> : TP::template smem<false>;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (st != cudaSuccess) return st;
-  const int per_sm = L.ctas_per_sm > 0 ? L.ctas_per_sm : tc_ctas_per_sm(reinterpret_cast<const void*>(kern), smem);
+  const int per_sm =
+      L.ctas_per_sm > 0 ? L.ctas_per_sm : tc_ctas_per_sm(reinterpret_cast<const void*>(kern), smem, TP::TMEM_COLS);
   const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), 4, smem, L.n_elem, per_sm);
   kern<<<grid, kTileElems, smem, L.stream>>>(p, mid, tmap);
   return cudaGetLastError();
