@@ -595,9 +595,11 @@ def run_coef_p1(args):
     A = torch.empty((E, 10, 10), device=dev)
     stream = torch.cuda.current_stream(dev)
     res = {}
-    for name, form, coef in (("p1_coefficient", fem.LAPLACE_P2_W1, wv), ("p0_coefficient", fem.LAPLACE_P2, we)):
+    for name, form, coef, contract in (("p1_coefficient", fem.LAPLACE_P2_W1, wv, fem.CONTRACT_F32),
+                                       ("p0_coefficient", fem.LAPLACE_P2, we, fem.CONTRACT_F32),
+                                       ("p1_coefficient_tensor_core", fem.LAPLACE_P2_W1, wv, fem.CONTRACT_BF16X3)):
         def step():
-            fem.integrate_fwd(coords, conn, form, coef, out=A)
+            fem.integrate_fwd(coords, conn, form, coef, out=A, contract=contract)
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
@@ -609,7 +611,7 @@ def run_coef_p1(args):
         torch.cuda.synchronize()
         ms = s0.elapsed_time(s1) / args.steps
         res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3)}
-        if name == "p1_coefficient":
+        if name != "p0_coefficient":
             rng = np.random.default_rng(8)
             idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 20000, replace=False),
                                             rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
@@ -619,6 +621,7 @@ def run_coef_p1(args):
             res[name]["max_rel_err_vs_fp64"] = float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())
             res[name]["error_sample"] = f"{len(idx):,} elements (20,000 slivers, 20,000 uniform, the last 40)"
     byts = {"p1_coefficient": E * (16 + 400) + V * (12 + 4), "p0_coefficient": E * (16 + 400 + 4) + V * 12}
+    byts["p1_coefficient_tensor_core"] = byts["p1_coefficient"]
     peak, peak_kind = hbm_peak()
     for k in res:
         res[k]["GB/s"] = byts[k] / (res[k]["ms"] * 1e-3) / 1e9

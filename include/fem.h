@@ -56,7 +56,8 @@ typedef enum {
  * coefficient w_e; the _W1 forms take a P1 coefficient w = sum_k w_k lambda_k
  * given by its values at the mesh vertices (Eqs. 20-23), so `coef` is
  * [n_vert] for them.  The _W1 forms have a forward path only (no adjoint, no
- * batched or tensor-core path: FEM_ERR_UNSUPPORTED). */
+ * batched path: FEM_ERR_UNSUPPORTED); FEM_LAPLACE_P2_W1 also contracts on the
+ * tensor cores. */
 typedef enum {
   FEM_LAPLACE_P1 = 0,    /* Eqs. 2-8 with P1 Lagrange elements */
   FEM_LAPLACE_P2 = 1,    /* same form, P2 Lagrange elements */
@@ -80,7 +81,9 @@ typedef enum {
 /* Arithmetic of the G:K contraction. */
 typedef enum {
   FEM_CONTRACT_F32 = 0,   /* FP32 FMAs with K as compile-time immediates (sparse) */
-  FEM_CONTRACT_BF16X3 = 1 /* tensor cores: G split into three bf16 terms, FP32 accumulate */
+  FEM_CONTRACT_BF16X3 = 1 /* tensor cores: G split into three bf16 terms, FP32 accumulate; P2 Laplacian
+                             (per-element or P1 coefficient) and P1 elasticity, FP32 coordinates and
+                             output, compensated Jacobian (curved P2: fem_integrate_fwd_iso) */
 } fem_contract;
 
 /* Vertex reduction of the adjoint. */

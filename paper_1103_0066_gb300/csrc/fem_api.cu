@@ -165,11 +165,11 @@ static fem_status integrate_fwd(const fem_mesh* mesh, int32_t form, const float*
   if ((cf64 || of64) && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
     return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates or FP64 output need FEM_JAC_F64");
   const bool tc = o->contract == FEM_CONTRACT_BF16X3;
-  if (tc && (form == FEM_LAPLACE_P1 || coef_p1(form) || cf64 || of64 ||
+  if (tc && (form == FEM_LAPLACE_P1 || form == FEM_LAPLACE_P1_W1 || cf64 || of64 ||
              (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
     return fail(FEM_ERR_UNSUPPORTED,
-                "the tensor-core contraction serves P2 and elasticity (per-element coefficient) with FP32 "
-                "coordinates and output and the compensated Jacobian");
+                "the tensor-core contraction serves the P2 Laplacian (per-element or P1 coefficient) and "
+                "elasticity with FP32 coordinates and output and the compensated Jacobian");
   fem::FwdLaunch L{};
   L.dim = mesh->dim;
   L.form = form;

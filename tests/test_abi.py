@@ -192,6 +192,8 @@ def test_tensor_core_combinations_rejected_on_host(fem):
     assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 1, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
     tc32 = nat.options_struct(jac=nat.JAC_F32, contract=nat.CONTRACT_BF16X3)
     assert lib.fem_integrate_fwd(ctypes.byref(m), EP1, None, A, 0, ctypes.byref(tc32), None) == nat.FEM_ERR_UNSUPPORTED
+    # P1 with a P1 coefficient has none either (P2 with one has)
+    assert lib.fem_integrate_fwd(ctypes.byref(m), 3, None, A, 0, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
 
 
 def test_saved_det_and_iso_contract_errors_on_host(fem):

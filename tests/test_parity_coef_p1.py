@@ -91,6 +91,41 @@ def test_coef_p1_bad_connectivity_and_no_coefficient(gfem, orc):
     assert rel_err_per_element(A1.cpu().numpy(), A0.cpu().numpy().astype(np.float64)).max() <= 1e-6
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_coef_p1_tensor_cores(gfem, orc, dim):
+    """P2 with a P1 coefficient contracted on the tensor cores: the arity-3 K
+    times DEN is exact in BF16 and G = w_k G_g is split into three BF16 terms
+    (at most 2^-24 |G| left per entry), so the FP32 tolerance holds on every
+    element, slivers included."""
+    mesh = _mesh(dim)
+    w = _wvert(mesh.n_vert)
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    A = gfem.integrate_fwd(_t(mesh.coords), _t(mesh.conn), LP2W, _t(w), contract=gfem.CONTRACT_BF16X3,
+                           dev_err=err)
+    torch.cuda.synchronize()
+    assert int(err.item()) == 0
+    Ar, fl = orc.integrate_w1(dim, LP2, mesh.conn, mesh.coords, w)
+    assert not fl.any()
+    e = rel_err_per_element(A.cpu().numpy(), Ar)
+    assert e.max() <= TOL32, (e.max(), int(e.argmax()))
+    if dim == 3:
+        assert e[mesh.sliver].max() <= TOL32
+
+
+@pytest.mark.parametrize("E", [1, 127, 129, 1000])
+def test_coef_p1_tensor_cores_ragged_and_no_coefficient(gfem, orc, E):
+    mesh = _mesh(3, seed=35)
+    conn = mesh.conn[:E]
+    w = _wvert(mesh.n_vert, 36)
+    Ar, _ = orc.integrate_w1(3, LP2, conn, mesh.coords, w)
+    A = gfem.integrate_fwd(_t(mesh.coords), _t(conn), LP2W, _t(w), contract=gfem.CONTRACT_BF16X3)
+    assert rel_err_per_element(A.cpu().numpy(), Ar).max() <= TOL32
+    # no coefficient: w = 1, the P2 Laplacian
+    Ar1, _ = orc.integrate(3, LP2, conn, mesh.coords)
+    A1 = gfem.integrate_fwd(_t(mesh.coords), _t(conn), LP2W, None, contract=gfem.CONTRACT_BF16X3)
+    assert rel_err_per_element(A1.cpu().numpy(), Ar1).max() <= TOL32
+
+
 def test_coef_p1_unsupported_paths(gfem):
     mesh = _mesh(3)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
@@ -98,6 +133,6 @@ def test_coef_p1_unsupported_paths(gfem):
     with pytest.raises(gfem.FemError):
         gfem.integrate_bwd(coords, conn, LP2W, torch.zeros(mesh.n_elem, 10, 10, device=DEV), w)
     with pytest.raises(gfem.FemError):
-        gfem.integrate_fwd(coords, conn, LP2W, w, contract=gfem.CONTRACT_BF16X3)
+        gfem.integrate_fwd(coords, conn, LP1W, w, contract=gfem.CONTRACT_BF16X3)  # P1: no tensor-core path
     with pytest.raises(ValueError):
         gfem.integrate_fwd(coords, conn, LP2W, _t(np.ones(mesh.n_elem, np.float32)))  # [E], not [V]
