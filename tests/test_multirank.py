@@ -1,5 +1,6 @@
-"""The multi-process (N > 1) host path of bench.py on CPU with the gloo backend,
-world size 2, rendezvous on 127.0.0.1 (no GPU).
+"""The multi-process (N > 1) host paths on CPU with the gloo backend, world
+size 2, rendezvous on 127.0.0.1 (no GPU): bench.py's harness, and the
+exchange step of one mesh split across ranks by elements.
 
 bench.py shards by replica: every rank integrates its own copy of the mesh
 (elements are independent units, weak scaling), with no collective on the
@@ -47,6 +48,69 @@ def test_dist_helpers_gloo_world2(tmp_path):
     for r in range(2):
         d = json.load(open(tmp_path / f"rank{r}.json"))
         assert d["max"] == 3.0 and d["backend"] == "gloo"
+
+
+def test_element_ranges_partition_the_mesh():
+    from paper_1103_0066_gb300.shard import element_range
+    for n in (0, 1, 31, 32, 33, 1000, 12582912):
+        for world in (1, 2, 3, 4, 8):
+            rs = [element_range(n, world, r) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == n
+            assert all(rs[r][1] == rs[r + 1][0] for r in range(world - 1))
+            sizes = [b - a for a, b in rs]
+            assert max(sizes) - min(sizes) <= 1 and min(sizes) >= 0
+    with pytest.raises(ValueError):
+        element_range(10, 2, 2)
+
+
+def _shard_main(rank, world, port, out_dir):
+    """One rank of the sharded adjoint on CPU: the oracle's reverse mode over
+    this rank's element slice stands in for the slice's kernels, and the
+    package's exchange adds the ranks' partial vertex gradients."""
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "LOCAL_RANK": str(rank), "WORLD_SIZE": str(world)})
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1103_0066_gb300 import meshgen as mg
+    from paper_1103_0066_gb300.shard import element_range, exchange_dcoords
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(81), 0.05, np.float32)
+    dA = mg.upstream(mg.rng_for(82), mesh.n_elem, 4)
+    w = mg.lognormal_coef(mg.rng_for(83), mesh.n_elem)
+    e0, e1 = element_range(mesh.n_elem, world, rank)
+    gx, gw = oracle.integrate_vjp(3, 0, mesh.conn[e0:e1], mesh.coords, dA[e0:e1], w[e0:e1])
+    dx = exchange_dcoords(torch.from_numpy(gx))
+    np.save(os.path.join(out_dir, f"dx{rank}.npy"), dx.numpy())
+    np.save(os.path.join(out_dir, f"dw{rank}.npy"), gw)
+    dist.destroy_process_group()
+
+
+def test_sharded_adjoint_exchange_gloo_world2(tmp_path):
+    """Two ranks, one mesh split by elements: after the exchange both ranks hold
+    the whole mesh's vertex gradient (the single-process oracle's, up to the
+    order of the FP64 sums), and each rank's coefficient gradient is its rows."""
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_1103_0066_gb300 import meshgen as mg
+    oracle.build()
+    port = _free_port()
+    mp.start_processes(_shard_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(81), 0.05, np.float32)
+    dA = mg.upstream(mg.rng_for(82), mesh.n_elem, 4)
+    w = mg.lognormal_coef(mg.rng_for(83), mesh.n_elem)
+    gx, gw = oracle.integrate_vjp(3, 0, mesh.conn, mesh.coords, dA, w)
+    dx0, dx1 = np.load(tmp_path / "dx0.npy"), np.load(tmp_path / "dx1.npy")
+    assert np.array_equal(dx0, dx1)
+    assert np.abs(dx0 - gx).max() <= 1e-12 * np.abs(gx).max()
+    shared = np.intersect1d(mesh.conn[: mesh.n_elem // 2], mesh.conn[mesh.n_elem // 2:])
+    assert shared.size > 0  # the split does cut through vertices: the exchange is needed
+    assert np.array_equal(np.concatenate([np.load(tmp_path / "dw0.npy"), np.load(tmp_path / "dw1.npy")]), gw)
 
 
 def test_reference_arm_under_torchrun_prints_once():

@@ -172,6 +172,35 @@ def test_autograd_tensor_core_forward(gfem, orc):
     assert torch.equal(grads[gfem.CONTRACT_F32][2], grads[gfem.CONTRACT_BF16X3][2])
 
 
+def test_sharded_slices_sum_to_the_whole_adjoint(gfem, orc):
+    """One mesh split by elements as N ranks would split it (here one after
+    another on one GPU, no collective): the slices' partial vertex gradients
+    from the kernels add up to the whole mesh's gradient within the FP32
+    tolerance, and their coefficient gradients are its rows bit for bit.  On
+    one rank (no process group) ShardedMesh is integrate_bwd itself."""
+    from paper_1103_0066_gb300.shard import ShardedMesh, element_range
+    mesh = _mesh(3)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    coef = _t(mg.lognormal_coef(mg.rng_for(91), mesh.n_elem))
+    dA = _t(mg.upstream(mg.rng_for(92), mesh.n_elem, 4))
+    dx, dw = gfem.integrate_bwd(coords, conn, LP1, dA, coef)
+    gx, _ = orc.integrate_vjp(3, LP1, mesh.conn, mesh.coords, dA.cpu().numpy(), coef.cpu().numpy())
+    for world in (2, 3):
+        acc = np.zeros((mesh.n_vert, 3))
+        for r in range(world):
+            e0, e1 = element_range(mesh.n_elem, world, r)
+            px, pw = gfem.integrate_bwd(coords, conn[e0:e1].contiguous(), LP1, dA[e0:e1].contiguous(), coef[e0:e1])
+            acc += px.double().cpu().numpy()
+            assert torch.equal(pw, dw[e0:e1])
+        assert _rel(acc, gx) <= TOL
+    sm = ShardedMesh(coords, conn, LP1)
+    assert (sm.world, sm.e0, sm.e1) == (1, 0, mesh.n_elem)
+    sx, sw = sm.integrate_bwd(dA, coef)
+    torch.cuda.synchronize()
+    assert torch.equal(sx, dx) and torch.equal(sw, dw)
+    assert torch.equal(sm.integrate_fwd(coef), gfem.integrate_fwd(coords, conn, LP1, coef))
+
+
 def test_adjoint_against_fp64_finite_differences(gfem, orc):
     """4^3 mesh with slivers: the GPU gradient against FP64 central differences of
     the oracle's forward, per-vertex step 1e-4 x the smallest incident height."""
