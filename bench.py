@@ -968,10 +968,30 @@ def run_adjoint64(args):
         s1.record(stream)
         torch.cuda.synchronize()
         ms = s0.elapsed_time(s1) / args.steps
+        # the same step captured once in a CUDA graph and replayed: no host
+        # launch work between the kernels
+        g = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            step()  # warm on the capturing stream
+        stream.wait_stream(side)
+        with torch.cuda.graph(g):
+            step()
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms = s0.elapsed_time(s1) / args.steps
         b = algorithmic_bytes(E, V, R if reduce == 0 else 0, 4, 3, True)
         byts = b["fwd"] + (b["bwd_elem"] + b["reduce"] if reduce == 0 else
                            E * (64 + 16 + 4 + 4 + 4) + V * 12 * 2)
-        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9}
+        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
+                     "graph_ms": graph_ms, "graph_GB/s": byts / (graph_ms * 1e-3) / 1e9}
     peak, peak_kind = hbm_peak()
     d = res["deterministic"]
     out = {"metric": METRIC, "value": d["elements_per_s"], "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
