@@ -53,7 +53,7 @@ KERNEL_SOURCES = {
 NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
     "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1349.6e6, "src": "df0ffcaa0a6fd82e"},
     "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1669d2556ed01ef5"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.5e6, "src": "f814c9fb2f7de961"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.2e6, "src": "641d31086653a833"},
     # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
     "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2393.9e6, "src": "8f8dded890714508"},
 }

@@ -339,7 +339,9 @@ __global__ void dest_kernel(const int32_t* voff, int64_t n_vert, const int32_t* 
 }
 
 // dcoords[v] = sum of the records of v (a contiguous run of the vertex-major
-// record array) in increasing record order.
+// record array) in increasing record order.  The records come in blocks of 8
+// predicated loads, all in flight before the block's additions (a vertex has
+// a handful of records: one block, one round trip).
 template <int D>
 __global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const float* __restrict__ records,
                                      int64_t n_vert, float* __restrict__ dcoords) {
@@ -349,10 +351,17 @@ __global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const flo
     float acc[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = 0.f;
-#pragma unroll 4
-    for (int32_t k = b; k < e; ++k) {
+    for (int32_t k0 = b; k0 < e; k0 += 8) {
+      float r[8][D];
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] += __ldg(records + int64_t(k) * D + a);
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int a = 0; a < D; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(k0 + u) * D + a) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < e)
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc[a] += r[u][a];
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
