@@ -53,8 +53,8 @@ def exchange_dcoords(partial: torch.Tensor, group=None) -> torch.Tensor:
 
 class ShardedMesh:
     """This rank's slice of a mesh: coords [V][d] (whole) and conn [E][d+1]
-    (whole; only rows e0..e1-1 are used), with the adjoint workspace of the
-    slice built once."""
+    (whole; only rows e0..e1-1 are used).  The adjoint workspace of the slice
+    is built on the first integrate_bwd and kept."""
 
     def __init__(self, coords: torch.Tensor, conn: torch.Tensor, form: int, group=None):
         self.group = group
@@ -64,7 +64,7 @@ class ShardedMesh:
         self.coords = coords
         self.conn = conn[self.e0:self.e1].contiguous()
         self.form = form
-        self.ws = Workspace(coords, self.conn, form)
+        self.ws = None
 
     def local(self, a: torch.Tensor | None) -> torch.Tensor | None:
         """Rows e0..e1-1 of a per-element array of the whole mesh."""
@@ -72,12 +72,15 @@ class ShardedMesh:
 
     def integrate_fwd(self, coef=None, **kw) -> torch.Tensor:
         """A_e of this rank's elements ([e1 - e0][n][n]); coef: this rank's
-        rows (per-element coefficient)."""
+        rows of a per-element coefficient, or the whole [V] vertex values of a
+        P1 coefficient (the _W1 forms)."""
         return integrate_fwd(self.coords, self.conn, self.form, coef, **kw)
 
     def integrate_bwd(self, dA: torch.Tensor, coef=None, need_dcoef=True, **kw):
         """(dcoords [V][d] of the whole mesh, summed over the ranks; dcoef of
         this rank's elements) for this rank's upstream dA ([e1 - e0][n][n])."""
+        if self.ws is None:
+            self.ws = Workspace(self.coords, self.conn, self.form)
         dx, dw = integrate_bwd(self.coords, self.conn, self.form, dA, coef, ws=self.ws,
                                reduce=REDUCE_DETERMINISTIC, need_dcoef=need_dcoef, **kw)
         return exchange_dcoords(dx, self.group), dw
