@@ -1,5 +1,5 @@
 """The multi-process (N > 1) host paths on CPU with the gloo backend, world
-size 2, rendezvous on 127.0.0.1 (no GPU): bench.py's harness, and the
+sizes 2 and 3, rendezvous on 127.0.0.1 (no GPU): bench.py's harness, and the
 exchange step of one mesh split across ranks by elements.
 
 bench.py shards by replica: every rank integrates its own copy of the mesh
@@ -89,10 +89,12 @@ def _shard_main(rank, world, port, out_dir):
     dist.destroy_process_group()
 
 
-def test_sharded_adjoint_exchange_gloo_world2(tmp_path):
-    """Two ranks, one mesh split by elements: after the exchange both ranks hold
-    the whole mesh's vertex gradient (the single-process oracle's, up to the
-    order of the FP64 sums), and each rank's coefficient gradient is its rows."""
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_adjoint_exchange_gloo(tmp_path, world):
+    """world ranks, one mesh split by elements: after the exchange every rank
+    holds the whole mesh's vertex gradient (the single-process oracle's, up to
+    the order of the FP64 sums), and each rank's coefficient gradient is its
+    rows."""
     import numpy as np
     import torch.multiprocessing as mp
 
@@ -100,17 +102,18 @@ def test_sharded_adjoint_exchange_gloo_world2(tmp_path):
     from paper_1103_0066_gb300 import meshgen as mg
     oracle.build()
     port = _free_port()
-    mp.start_processes(_shard_main, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    mp.start_processes(_shard_main, args=(world, port, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
     mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(81), 0.05, np.float32)
     dA = mg.upstream(mg.rng_for(82), mesh.n_elem, 4)
     w = mg.lognormal_coef(mg.rng_for(83), mesh.n_elem)
     gx, gw = oracle.integrate_vjp(3, 0, mesh.conn, mesh.coords, dA, w)
-    dx0, dx1 = np.load(tmp_path / "dx0.npy"), np.load(tmp_path / "dx1.npy")
-    assert np.array_equal(dx0, dx1)
-    assert np.abs(dx0 - gx).max() <= 1e-12 * np.abs(gx).max()
+    dx = [np.load(tmp_path / f"dx{r}.npy") for r in range(world)]
+    assert all(np.array_equal(dx[0], d) for d in dx[1:])
+    assert np.abs(dx[0] - gx).max() <= 1e-12 * np.abs(gx).max()
     shared = np.intersect1d(mesh.conn[: mesh.n_elem // 2], mesh.conn[mesh.n_elem // 2:])
     assert shared.size > 0  # the split does cut through vertices: the exchange is needed
-    assert np.array_equal(np.concatenate([np.load(tmp_path / "dw0.npy"), np.load(tmp_path / "dw1.npy")]), gw)
+    assert np.array_equal(np.concatenate([np.load(tmp_path / f"dw{r}.npy") for r in range(world)]), gw)
 
 
 def test_reference_arm_under_torchrun_prints_once():
