@@ -7,13 +7,17 @@ mesh: forward integration (gather, Jacobian, G, G:K, coalesced stores) and
 the adjoint for an upstream dA ~ N(0,1) (element pass + deterministic
 segmented vertex reduction).
 
-Prints ONE JSON line (rank 0).  Timing: W untimed warm-up steps, then K steps
-bracketed by barrier + synchronize, CUDA events on the launching stream,
-max over ranks.  The working set (~2.7 GB) is far larger than L2, so no L2
-flush is needed between steps.
+Prints ONE JSON line (rank 0).  Timing: W untimed warm-up steps, then timed
+regions of exactly K steps, each bracketed by barrier + synchronize, CUDA
+events on the launching stream, max over ranks; the region is repeated until
+the repeats span at least one second of device time (nvidia-smi clocks are
+sampled throughout), and the line reports the median per-step time with its
+spread.  The working set (~2.7 GB) is far larger than L2, so no L2 flush is
+needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload tet128|elastic128|adjoint64]
+                  [--workload tet128|tet128_shuffled|batch96|elastic128|adjoint64|coef_p1|
+                              tri64_fp64|assemble128|multiphysics128|iso128] [--shard]
 """
 from __future__ import annotations
 
@@ -49,8 +53,8 @@ KERNEL_SOURCES = {
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# 128^3 sliver cube from one ncu launch-list capture.
-NCU_TRAFFIC = {  # profiles/tet128_laplace_p1_fwd_adjoint_launches.md, tet128_laplace_p1_assembly_launches.md
+# 128^3 sliver cube from one ncu launch-list capture of the bench command.
+NCU_TRAFFIC = {
     "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1349.6e6, "src": "df0ffcaa0a6fd82e"},
     "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1669d2556ed01ef5"},
     "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.2e6, "src": "641d31086653a833"},
@@ -175,6 +179,45 @@ def max_over_ranks(pg, x: float, dev) -> float:
     return float(t.item())
 
 
+# ------------------------------------------------------------------ timing
+
+MIN_TIMED_MS = 1000.0  # repeats of the K-step timed region span at least this much device time
+
+
+def measure(step, K, stream, dev, pg=None, min_ms=MIN_TIMED_MS, max_repeats=400, label=None):
+    """Times exactly K calls of step(rep, k) per timed region: barrier and
+    synchronize, an event on `stream`, the K steps, an event, synchronize and
+    barrier; the region's duration is the max over ranks.  The region is
+    repeated until the repeats span at least min_ms of device time, with
+    nvidia-smi clock samples taken throughout.  Returns the median, min and
+    max ms per step over the repeats, the repeat count and the clocks."""
+    import torch
+    clocks = ClockSampler(dev.index if dev.index is not None else 0)
+    clocks.start()
+    time.sleep(0.3)
+    per, total = [], 0.0
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    while len(per) < max_repeats and (total < min_ms or len(per) < 3):
+        rep = len(per)
+        barrier(pg, dev)
+        torch.cuda.synchronize()
+        s0.record(stream)
+        for k in range(K):
+            step(rep, k)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        barrier(pg, dev)
+        ms = max_over_ranks(pg, s0.elapsed_time(s1), dev)
+        per.append(ms / K)
+        total += ms
+    clk = clocks.stop()
+    out = {"ms_per_step": statistics.median(per), "ms_min": min(per), "ms_max": max(per), "repeats": len(per),
+           "timed_ms": total, "clocks": clk}
+    if label:
+        out["label"] = label
+    return out
+
+
 # ------------------------------------------------------------------ workloads
 
 def tet_workload(n=128, k=2):
@@ -241,12 +284,27 @@ def run_ours(args):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    shuffled = args.workload == "tet128_shuffled"
+    shard = args.shard and ws_n > 1
 
-    mesh, dA_h = tet_workload(args.mesh_n)
-    E, V = mesh.n_elem, mesh.n_vert
+    if shuffled:
+        from paper_1103_0066_gb300 import meshgen as mg
+        mesh = mg.workload_tet_shuffled(args.mesh_n)
+        dA_h = mg.upstream(mg.rng_for(12), mesh.n_elem, 4)
+    else:
+        mesh, dA_h = tet_workload(args.mesh_n)
+    E_all, V = mesh.n_elem, mesh.n_vert
     coords = torch.from_numpy(mesh.coords).to(dev)
-    conn = torch.from_numpy(mesh.conn).to(dev)
-    dA = torch.from_numpy(dA_h).to(dev)
+    conn_all = torch.from_numpy(mesh.conn).to(dev)
+    dA_all = torch.from_numpy(dA_h).to(dev)
+    if shard:  # this rank's contiguous element range of the one mesh
+        from paper_1103_0066_gb300.shard import element_range, exchange_dcoords
+        e0, e1 = element_range(E_all, ws_n, rank)
+    else:
+        e0, e1 = 0, E_all
+    conn = conn_all[e0:e1].contiguous()
+    dA = dA_all[e0:e1].contiguous()
+    E = e1 - e0
     A = torch.empty((E, 4, 4), dtype=torch.float32, device=dev)
     dcoords = torch.empty((V, 3), dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
@@ -256,8 +314,13 @@ def run_ours(args):
     setup_ms = (time.perf_counter() - t0) * 1e3
 
     det = torch.empty(E, dtype=torch.float32, device=dev)  # det J kept from the forward for the adjoint
+    ev_store = []  # per-kernel events of the timed steps (fwd | bwd_elem | reduce | exchange)
 
-    def step(evs=None):
+    def step(rep=None, k=None):
+        evs = None
+        if rep is not None and len(ev_store) < 4000:
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(5 if shard else 4)]
+            ev_store.append(evs)
         if evs is not None:
             evs[0].record(stream)
         fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A, det_out=det)
@@ -270,90 +333,91 @@ def run_ours(args):
         fem.adjoint_reduce(coords, conn, ws, dcoords)
         if evs is not None:
             evs[3].record(stream)
+        if shard:  # the path's one exchange: the partial vertex gradients summed over the ranks
+            exchange_dcoords(dcoords)
+            if evs is not None:
+                evs[4].record(stream)
 
     for _ in range(args.warmup):
         step()
     K = args.steps
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(dev.index if dev.index is not None else 0)
-    clocks.start()
-    time.sleep(0.3)
-    barrier(pg, dev)
+    m = measure(step, K, stream, dev, pg)
     torch.cuda.synchronize()
-    start.record(stream)
-    for k in range(K):
-        step(evs[k])
-    end.record(stream)
-    torch.cuda.synchronize()
-    barrier(pg, dev)
-    clk = clocks.stop()
-    total_ms = max_over_ranks(pg, start.elapsed_time(end), dev)
-    per = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in evs]))
-           for i, name in enumerate(("fwd", "bwd_elem", "reduce"))}
+    names = ("fwd", "bwd_elem", "reduce") + (("exchange",) if shard else ())
+    per = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev_store]))
+           for i, name in enumerate(names)}
+    ms_step = m["ms_per_step"]
 
     R = ws.n_records()
     byts = algorithmic_bytes(E, V, R, 4, 3, False)
     peak, peak_kind = hbm_peak()
-    dom = max(per, key=per.get)
+    dom = max(("fwd", "bwd_elem", "reduce"), key=per.get)
     kname = {"fwd": "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>", "bwd_elem": "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>",
              "reduce": "vertex_reduce_kernel<3>"}
     h = {k: kernel_src_hash(v) for k, v in kname.items()}
-    traffic = ncu_traffic(kname[dom])  # valid only for the sources it was captured with
+    traffic = None if (shuffled or shard) else ncu_traffic(kname[dom])  # captured on the cell-major mesh
     ach = byts[dom] / (per[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": kname[dom], "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+                "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth (burst)",
                 "frac_of_nominal": ach / NOMINAL_HBM_GBS, "nominal_gbs": NOMINAL_HBM_GBS,
-                "traffic": traffic, "algorithmic_bytes": byts[dom]}
+                "traffic": traffic, "algorithmic_bytes": byts[dom],
+                "duration_ms": per[dom], "timing": "CUDA events around the kernel on its launching stream, "
+                                                    f"mean over {len(ev_store)} timed steps"}
     kernels = {k: {"ms": per[k], "GB/s": byts[k] / (per[k] * 1e-3) / 1e9,
                    "frac_of_peak": byts[k] / (per[k] * 1e-3) / 1e9 / peak,
-                   "frac_of_nominal": byts[k] / (per[k] * 1e-3) / 1e9 / NOMINAL_HBM_GBS} for k in per}
+                   "frac_of_nominal": byts[k] / (per[k] * 1e-3) / 1e9 / NOMINAL_HBM_GBS} for k in byts}
+    if shard:
+        kernels["exchange"] = {"ms": per["exchange"], "bytes": V * 12, "what": "all-reduce of dcoords [V][3]"}
     fwd_eps = E / (per["fwd"] * 1e-3)
-    ms_step = total_ms / K
-    value = ws_n * E / (ms_step * 1e-3)
+    value = (E_all if shard else ws_n * E_all) / (ms_step * 1e-3)
 
     # end to end through the public API: pinned host buffers, copies in the timed region
-    e2e_steps = 0 if args.no_e2e else max(3, min(K, 10))
-    coords_h = torch.from_numpy(mesh.coords).pin_memory()
-    conn_h = torch.from_numpy(mesh.conn).pin_memory()
-    dA_hp = torch.from_numpy(dA_h).pin_memory()
-    A_h = torch.empty_like(A, device="cpu").pin_memory()
-    dc_h = torch.empty_like(dcoords, device="cpu").pin_memory()
+    e2e = None
+    if not args.no_e2e and not shard:
+        coords_h = torch.from_numpy(mesh.coords).pin_memory()
+        conn_h = torch.from_numpy(mesh.conn).pin_memory()
+        dA_hp = torch.from_numpy(dA_h).pin_memory()
+        A_h = torch.empty_like(A, device="cpu").pin_memory()
+        dc_h = torch.empty_like(dcoords, device="cpu").pin_memory()
+        # HostStep: per slice of elements, copies in, the forward and copies out
+        # overlap on three streams; the adjoint follows the last slice
+        hs = fem.HostStep(V, E, 3, fem.LAPLACE_P1, device=dev)
 
-    # HostStep: per slice of elements, copies in, the forward and copies out
-    # overlap on three streams; the adjoint follows the last slice
-    hs = fem.HostStep(V, E, 3, fem.LAPLACE_P1, device=dev)
-
-    def e2e_step():
-        hs.run(coords_h, conn_h, dA_hp, A_h, dc_h)
-
-    e2e_ms = float("nan")
-    if e2e_steps:
+        def e2e_step(rep=None, k=None):
+            hs.run(coords_h, conn_h, dA_hp, A_h, dc_h)
         e2e_step()
         torch.cuda.synchronize()
-        barrier(pg, dev)
-        s2, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s2.record(stream)
-        for _ in range(e2e_steps):
-            e2e_step()
-        e2.record(stream)
-        torch.cuda.synchronize()
-        e2e_ms = max_over_ranks(pg, s2.elapsed_time(e2), dev) / e2e_steps
-    e2e_match = bool(torch.equal(A_h, A.cpu()) and torch.equal(dc_h, dcoords.cpu())) if e2e_steps else None
-    h2d = coords_h.numel() * 4 + conn_h.numel() * 4 + dA_hp.numel() * 4
-    d2h = A_h.numel() * 4 + dc_h.numel() * 4
+        e2e_steps = max(3, min(K, 10))
+        me = measure(e2e_step, e2e_steps, stream, dev, pg)
+        match = bool(torch.equal(A_h, A.cpu()) and torch.equal(dc_h, dcoords.cpu()))
+        h2d = coords_h.numel() * 4 + conn_h.numel() * 4 + dA_hp.numel() * 4
+        d2h = A_h.numel() * 4 + dc_h.numel() * 4
+        e2e = {"value": ws_n * E / (me["ms_per_step"] * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": me["ms_per_step"], "ms_min": me["ms_min"],
+               "ms_max": me["ms_max"], "steps": e2e_steps, "repeats": me["repeats"], "clocks": me["clocks"],
+               "path": f"HostStep.run: pinned host buffers, {hs.chunk:,}-element slices, copies in, forward "
+                       "and copies out overlapped on three streams, then the adjoint and dcoords out",
+               "bitwise_equal_to_device_path": match}
 
+    order = "elements in random order, vertices renumbered at random" if shuffled else "cell-major element order"
+    par = (f"{ws_n} ranks each integrating a contiguous element range of the one mesh; dcoords summed by an "
+           "NCCL all-reduce inside each step" if shard else
+           f"{ws_n} independent replicas (elements shard with no collective)")
     out = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws_n, "steps": K,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "strong" if shard else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"3D P1 Laplacian, {args.mesh_n}^3 Kuhn cube, 6 tets/cell, jitter 0.15h, "
-                               f"5% slivers ({E:,} tets, {V:,} vertices); FP32 coords and 4x4 FP32 element "
-                               "matrices, compensated-FP32 Jacobian; step = forward (saving det J) + "
+                               f"5% slivers ({E_all:,} tets, {V:,} vertices), {order}; FP32 coords and 4x4 FP32 "
+                               "element matrices, compensated-FP32 Jacobian; step = forward (saving det J) + "
                                "adjoint (deterministic segmented reduction), dA ~ N(0,1)",
-                   "elements": E, "vertices": V, "form": "laplace_p1", "dim": 3,
+                   "elements": E_all, "vertices": V, "form": "laplace_p1", "dim": 3,
+                   "element_order": "random" if shuffled else "cell-major",
                    "l2": "no flush: inputs/outputs (~2.7 GB per step) far exceed the 129 MB L2",
-                   "parallelism": f"{ws_n} independent replicas (elements shard with no collective)"},
+                   "parallelism": par},
+        "timing": {"repeats": m["repeats"], "ms_per_step_min": m["ms_min"], "ms_per_step_max": m["ms_max"],
+                   "timed_ms": m["timed_ms"], "statistic": "median over repeats of K-step timed regions"},
         "roofline": roofline,
         "kernels": kernels,
         "fwd": {"elements_per_s": fwd_eps, "gflops_paper_convention": fwd_eps * 288 / 1e9,
@@ -363,18 +427,13 @@ def run_ours(args):
                         "frac_of_peak": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / peak,
                         "frac_of_nominal": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
         "setup": {"incidence_build_ms": setup_ms, "records": R, "slots": 4 * E},
-        "e2e": {"value": ws_n * E / (e2e_ms * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
-                "path": f"HostStep.run: pinned host buffers, {hs.chunk:,}-element slices, copies in, forward "
-                        "and copies out overlapped on three streams, then the adjoint and dcoords out",
-                "bitwise_equal_to_device_path": e2e_match},
-        "gpu_launches": 3 * K,
-        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 3 * K,  # per K-step timed region (NCCL's all-reduce not counted)
+        "gpu_launches_all_repeats": 3 * K * m["repeats"],
+        "clocks": m["clocks"],
         "kernel_src_hash": h,
     }
-    if not e2e_steps:
-        out["e2e"] = None
-    if rank == 0 and ws_n == 1 and not args.no_cpu:
+    if rank == 0 and ws_n == 1 and not args.no_cpu and not shuffled:
         cpu, err = cpu_baseline_leg(mesh, dA_h, A, dcoords, args.cpu_sample)
         out["cpu_baseline"] = cpu
         out["error_vs_fp64"] = err
@@ -399,7 +458,10 @@ def batch_bytes(items):
 def run_batch(args):
     """96 meshes of log-uniform size in [1e3, 2e6] elements, six (shape, form)
     kinds, forward + adjoint: per-mesh eager launches, the same launches in one
-    CUDA graph, and the tuned persistent batched launch in a CUDA graph."""
+    CUDA graph, each batched mode in a CUDA graph, and the tuned batched launch
+    in a CUDA graph.  Every variant does the same work (each adjoint takes det J
+    from its forward); the tuned launch's outputs are compared with the
+    per-mesh ones bit for bit outside the timed regions."""
     import torch
 
     import __graft_entry__
@@ -421,36 +483,34 @@ def run_batch(args):
                       "dcoef": torch.empty(m.n_elem, device=dev), "src": b})
     E = sum(it["src"].mesh.n_elem for it in items)
     wss = [fem.Workspace(it["coords"], it["conn"], it["form"]) for it in items]
+    dets = [torch.empty(it["src"].mesh.n_elem, device=dev) for it in items]
     for it, ws in zip(items, wss):
         it["records"] = ws.n_records()
     stream = torch.cuda.Stream(dev)
 
-    def per_mesh():
-        for it, ws in zip(items, wss):
-            fem.integrate_fwd(it["coords"], it["conn"], it["form"], it["coef"], out=it["A"], stream=stream)
+    def per_mesh(rep=None, k=None):  # det J kept from each forward for its adjoint, as the batch does
+        for it, ws, det in zip(items, wss, dets):
+            fem.integrate_fwd(it["coords"], it["conn"], it["form"], it["coef"], out=it["A"], stream=stream,
+                              det_out=det)
             fem.integrate_bwd(it["coords"], it["conn"], it["form"], it["dA"], it["coef"], ws=ws,
-                              dcoords=it["dcoords"], dcoef=it["dcoef"], stream=stream)
+                              dcoords=it["dcoords"], dcoef=it["dcoef"], stream=stream, det=det)
 
-    def timed(fn, steps):
+    def timed(fn, label):
         for _ in range(args.warmup):
             fn()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(steps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / steps
+        return measure(lambda rep, k: fn(), args.steps, stream, dev, label=label)
 
     with torch.cuda.stream(stream):
-        eager_ms = timed(per_mesh, args.steps)
+        eager = timed(per_mesh, "per-mesh eager")
+        torch.cuda.synchronize()
+        ref = [(it["A"].clone(), it["dcoords"].clone(), it["dcoef"].clone()) for it in items]
         g1 = torch.cuda.CUDAGraph()
         per_mesh()
         torch.cuda.synchronize()
         with torch.cuda.graph(g1, stream=stream):
             per_mesh()
-        graph_ms = timed(g1.replay, args.steps)
+        graph = timed(g1.replay, "per-mesh graph")
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
         mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
@@ -464,20 +524,26 @@ def run_batch(args):
             gm = torch.cuda.CUDAGraph()
             with torch.cuda.graph(gm, stream=stream):
                 bt.run(stream=stream)
-            per_mode[mode_names[mode]] = timed(gm.replay, args.steps)
+            r = timed(gm.replay, mode_names[mode])
+            per_mode[mode_names[mode]] = {"ms": r["ms_per_step"], "ms_min": r["ms_min"], "ms_max": r["ms_max"],
+                                          "clocks": r["clocks"]}
             del gm
         bt.set_config(*cfg)
+        for it in items:  # outputs poisoned, then written by the tuned launch alone
+            it["A"].fill_(float("nan"))
+            it["dcoords"].fill_(float("nan"))
+            it["dcoef"].fill_(float("nan"))
         bt.run(stream=stream)
         torch.cuda.synchronize()
         g2 = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g2, stream=stream):
             bt.run(stream=stream)
-        clocks = ClockSampler(0)
-        clocks.start()
-        time.sleep(0.3)
-        batch_ms = timed(g2.replay, args.steps)
-        clk = clocks.stop()
+        tuned = timed(g2.replay, "tuned batch graph")
+        torch.cuda.synchronize()
         err = bt.errors(stream=stream)
+    bitwise = all(torch.equal(it["A"], a) and torch.equal(it["dcoords"], x) and torch.equal(it["dcoef"], w)
+                  for it, (a, x, w) in zip(items, ref))
+    batch_ms = tuned["ms_per_step"]
     peak, peak_kind = hbm_peak()
     kinds = {(it["src"].mesh.dim, it["form"]) for it in items if it["src"].mesh.n_elem > 0}
     launches = {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 3 * len(items),
@@ -490,20 +556,25 @@ def run_batch(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"96 meshes, element counts log-uniform in [1e3, 2e6] x {args.batch_scale}, "
                                "tri/tet x P1/P2 Laplacian/P1 elasticity, lognormal coefficient, forward + "
-                               "adjoint (deterministic), tuned persistent launch(es) in a CUDA graph",
+                               "adjoint (deterministic, det J kept from the forward in every variant), tuned "
+                               "batched launch in a CUDA graph",
                    "elements": E, "meshes": len(items),
                    "l2": "no flush: ~%.1f GB moved per step" % (byts / 1e9)},
+        "timing": {"repeats": tuned["repeats"], "ms_per_step_min": tuned["ms_min"],
+                   "ms_per_step_max": tuned["ms_max"], "statistic": "median over repeats of K-step timed regions"},
         "roofline": {"bound": "hbm", "kernel": {fem.BATCH_SINGLE: "fem_batch_kernel",
                                                 fem.BATCH_PER_ITEM: "per-mesh kernels",
                                                 fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on ten streams"}.get(
                          cfg[2], "fem_batch_kind_kernel (all kinds)"), "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},
-        "comparison_ms": {"per_mesh_eager": eager_ms, "per_mesh_graph": graph_ms, "batched_graph": batch_ms,
-                          "batched_mode_untuned": per_mode},
-        "speedup_vs_eager": eager_ms / batch_ms, "speedup_vs_graph": graph_ms / batch_ms,
+        "comparison_ms": {"per_mesh_eager": eager["ms_per_step"], "per_mesh_graph": graph["ms_per_step"],
+                          "batched_graph": batch_ms, "batched_mode_untuned": per_mode},
+        "comparison_clocks": {"per_mesh_eager": eager["clocks"], "per_mesh_graph": graph["clocks"]},
+        "speedup_vs_eager": eager["ms_per_step"] / batch_ms, "speedup_vs_graph": graph["ms_per_step"] / batch_ms,
         "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": mode_names[cfg[2]]},
-        "gpu_launches": launches * args.steps, "device_errors": err, "clocks": clk,
+        "bitwise_equal_to_per_mesh": bitwise,
+        "gpu_launches": launches * args.steps, "device_errors": err, "clocks": tuned["clocks"],
     }
     print(json.dumps(out), flush=True)
 
@@ -542,18 +613,14 @@ def run_elastic(args):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1) / args.steps
+        r = measure(lambda rep, k: step(), args.steps, stream, dev)
+        ms = r["ms_per_step"]
         rng = np.random.default_rng(7)
         idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 20000, replace=False),
                                         rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
         err = _sample_err(oracle, 3, fem.ELASTIC_P1, mesh, coef_h, A, idx)
-        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "max_rel_err_vs_fp64": err}
+        res[name] = {"ms": ms, "ms_min": r["ms_min"], "ms_max": r["ms_max"], "repeats": r["repeats"],
+                     "clocks": r["clocks"], "elements_per_s": E / (ms * 1e-3), "max_rel_err_vs_fp64": err}
     byts = algorithmic_bytes(E, V, 0, 12, 3, True, saved_det=False)["fwd"]
     peak, peak_kind = hbm_peak()
     best = min(res, key=lambda k: res[k]["ms"])
@@ -569,7 +636,7 @@ def run_elastic(args):
            "roofline": {"bound": "hbm", "kernel": best, "achieved": res[best]["GB/s"], "peak": peak, "unit": "GB/s",
                         "frac": res[best]["frac_of_peak"], "peak_kind": f"{peak_kind} copy bandwidth",
                         "traffic": None, "algorithmic_bytes": byts},
-           "paths": res, "gpu_launches": args.steps}
+           "paths": res, "gpu_launches": args.steps, "clocks": res[best]["clocks"]}
     print(json.dumps(out), flush=True)
 
 
@@ -603,14 +670,10 @@ def run_coef_p1(args):
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1) / args.steps
-        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3)}
+        r = measure(lambda rep, k: step(), args.steps, stream, dev)
+        ms = r["ms_per_step"]
+        res[name] = {"ms": ms, "ms_min": r["ms_min"], "ms_max": r["ms_max"], "repeats": r["repeats"],
+                     "clocks": r["clocks"], "elements_per_s": E / (ms * 1e-3)}
         if name != "p0_coefficient":
             rng = np.random.default_rng(8)
             idx = np.unique(np.concatenate([rng.choice(np.where(mesh.sliver)[0], 20000, replace=False),
@@ -637,7 +700,7 @@ def run_coef_p1(args):
                         "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],
                         "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                         "algorithmic_bytes": byts["p1_coefficient"]},
-           "paths": res, "gpu_launches": args.steps}
+           "paths": res, "gpu_launches": args.steps, "clocks": r["clocks"]}
     print(json.dumps(out), flush=True)
 
 
@@ -666,25 +729,16 @@ def run_tri64_fp64(args):
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        eager_us = s0.elapsed_time(s1) / args.steps * 1e3
+        re = measure(lambda rep, k: step(), args.steps, stream, dev, min_ms=200.0)
+        eager_us = re["ms_per_step"] * 1e3
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             for _ in range(100):
                 step()
         g.replay()
         torch.cuda.synchronize()
-        s0.record(stream)
-        for _ in range(max(1, args.steps // 100)):
-            g.replay()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        graph_us = s0.elapsed_time(s1) / (100 * max(1, args.steps // 100)) * 1e3
+        rg = measure(lambda rep, k: g.replay(), max(1, args.steps // 100), stream, dev)
+        graph_us = rg["ms_per_step"] / 100 * 1e3
     Ar, _ = oracle.integrate(2, oracle.LAPLACE_P1, mesh.conn, mesh.coords)
     Ag = A.cpu().numpy()
     err = float((np.abs(Ag - Ar).reshape(mesh.n_elem, -1).max(1) / np.abs(Ar).reshape(mesh.n_elem, -1).max(1)).max())
@@ -695,8 +749,13 @@ def run_tri64_fp64(args):
            "config": {"workload": "2D P1 Laplacian, 64x64 jittered square (8,192 triangles), FP64 coordinates "
                                   "and 3x3 FP64 element matrices, forward; launch-bound",
                       "elements": E, "l2": "inputs and outputs (0.8 MB) are L2-resident"},
-           "us_per_launch": {"eager": eager_us, "cuda_graph": graph_us},
-           "max_rel_err_vs_fp64_oracle": err, "roofline": None, "gpu_launches": args.steps}
+           "us_per_launch": {"eager": eager_us, "cuda_graph": graph_us,
+                             "eager_spread_us": [re["ms_min"] * 1e3, re["ms_max"] * 1e3],
+                             "cuda_graph_spread_us": [rg["ms_min"] * 10, rg["ms_max"] * 10]},
+           "timing": {"eager_repeats": re["repeats"], "graph_repeats": rg["repeats"],
+                      "statistic": "median over repeats of timed regions"},
+           "max_rel_err_vs_fp64_oracle": err, "roofline": None, "gpu_launches": args.steps,
+           "clocks": rg["clocks"], "eager_clocks": re["clocks"]}
     print(json.dumps(out), flush=True)
 
 
@@ -727,16 +786,11 @@ def run_assemble(args):
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / args.steps
+        return measure(lambda rep, k: fn(), args.steps, stream, dev)
 
-    asm_ms = timed(lambda: asm.assemble(A, out=vals))
-    fwd_ms = timed(lambda: fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A))
+    ra = timed(lambda: asm.assemble(A, out=vals))
+    rf = timed(lambda: fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A))
+    asm_ms, fwd_ms = ra["ms_per_step"], rf["ms_per_step"]
     # rows checked against the FP64 oracle: every row of a sample of vertices
     rng = np.random.default_rng(9)
     rows = np.unique(rng.choice(V, 2000, replace=False))
@@ -781,6 +835,9 @@ def run_assemble(args):
            "forward_ms": fwd_ms, "build_ms": build_ms, "max_row_err_vs_fp64": err,
            "error_metric": "per row v: max |a - a_fp64| / (sum over the elements at v of max |A_e|)",
            "error_sample": f"all entries of {len(rows):,} random rows",
+           "timing": {"repeats": ra["repeats"], "ms_per_step_min": ra["ms_min"], "ms_per_step_max": ra["ms_max"],
+                      "statistic": "median over repeats of K-step timed regions"},
+           "clocks": ra["clocks"], "forward_clocks": rf["clocks"],
            "gpu_launches": 2 * args.steps}  # tile pass + entry pass per call
     print(json.dumps(out), flush=True)
 
@@ -813,26 +870,23 @@ def run_multiphysics(args):
         wss.append(fem.Workspace(coords, conn, form))
     stream = torch.cuda.Stream(dev)
 
-    def per_form():
-        for it, ws in zip(items, wss):
-            fem.integrate_fwd(coords, conn, it["form"], coef, out=it["A"], stream=stream)
+    dets = [torch.empty(E, device=dev) for _ in items]
+
+    def per_form():  # det J kept from each forward for its adjoint, as the batch does
+        for it, ws, det in zip(items, wss, dets):
+            fem.integrate_fwd(coords, conn, it["form"], coef, out=it["A"], stream=stream, det_out=det)
             fem.integrate_bwd(coords, conn, it["form"], it["dA"], coef, ws=ws, dcoords=it["dcoords"],
-                              dcoef=it["dcoef"], stream=stream)
+                              dcoef=it["dcoef"], stream=stream, det=det)
 
     def timed(fn):
         for _ in range(max(3, args.warmup)):
             fn()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            fn()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        return s0.elapsed_time(s1) / args.steps
+        return measure(lambda rep, k: fn(), args.steps, stream, dev)
 
     with torch.cuda.stream(stream):
-        eager_ms = timed(per_form)
+        re = timed(per_form)
+        eager_ms = re["ms_per_step"]
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
         bt.run(stream=stream)
@@ -840,7 +894,8 @@ def run_multiphysics(args):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
             bt.run(stream=stream)
-        batch_ms = timed(g.replay)
+        rb = timed(g.replay)
+        batch_ms = rb["ms_per_step"]
         err = bt.errors(stream=stream)
     R = wss[0].n_records()  # the records depend on the connectivity only
     byts = 0
@@ -860,6 +915,9 @@ def run_multiphysics(args):
                         "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                         "traffic": None, "algorithmic_bytes": byts},
            "comparison_ms": {"per_form_eager": eager_ms, "batched_graph": batch_ms},
+           "timing": {"repeats": rb["repeats"], "ms_per_step_min": rb["ms_min"], "ms_per_step_max": rb["ms_max"],
+                      "statistic": "median over repeats of K-step timed regions"},
+           "clocks": rb["clocks"], "per_form_clocks": re["clocks"],
            "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": cfg[2]},
            "device_errors": err,
            "gpu_launches": args.steps * {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 9,
@@ -896,20 +954,16 @@ def run_iso(args):
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1) / args.steps
+        r = measure(lambda rep, k: step(), args.steps, stream, dev)
+        ms = r["ms_per_step"]
         rng = np.random.default_rng(11)
         idx = np.unique(np.concatenate([rng.choice(E, 20000, replace=False), np.arange(E - 40, E)]))
         Ar, _ = oracle.integrate_iso(3, form - 5, mesh.conn[idx], mesh.coords, mid_h[idx])
         Ag = A[torch.from_numpy(idx).to(dev)].double().cpu().numpy()
         num = np.abs(Ag - Ar).reshape(len(idx), -1).max(1)
         byts = E * (16 + 72 + 4 * n * n) + V * 12
-        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
+        res[name] = {"ms": ms, "ms_min": r["ms_min"], "ms_max": r["ms_max"], "repeats": r["repeats"],
+                     "clocks": r["clocks"], "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
                      "frac_of_peak": byts / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": byts,
                      "max_rel_err_vs_fp64": float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())}
         del A
@@ -925,7 +979,7 @@ def run_iso(args):
                         "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],
                         "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                         "algorithmic_bytes": r["algorithmic_bytes"]},
-           "paths": res, "gpu_launches": 3 * args.steps}
+           "paths": res, "gpu_launches": args.steps, "clocks": r["clocks"]}
     print(json.dumps(out), flush=True)
 
 
@@ -961,13 +1015,8 @@ def run_adjoint64(args):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        for _ in range(args.steps):
-            step()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        ms = s0.elapsed_time(s1) / args.steps
+        r = measure(lambda rep, k: step(), args.steps, stream, dev)
+        ms = r["ms_per_step"]
         # the same step captured once in a CUDA graph and replayed: no host
         # launch work between the kernels
         g = torch.cuda.CUDAGraph()
@@ -981,17 +1030,15 @@ def run_adjoint64(args):
         for _ in range(3):
             g.replay()
         torch.cuda.synchronize()
-        s0.record(stream)
-        for _ in range(args.steps):
-            g.replay()
-        s1.record(stream)
-        torch.cuda.synchronize()
-        graph_ms = s0.elapsed_time(s1) / args.steps
+        rg = measure(lambda rep, k: g.replay(), args.steps, stream, dev)
+        graph_ms = rg["ms_per_step"]
         b = algorithmic_bytes(E, V, R if reduce == 0 else 0, 4, 3, True)
         byts = b["fwd"] + (b["bwd_elem"] + b["reduce"] if reduce == 0 else
                            E * (64 + 16 + 4 + 4 + 4) + V * 12 * 2)
-        res[name] = {"ms": ms, "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
-                     "graph_ms": graph_ms, "graph_GB/s": byts / (graph_ms * 1e-3) / 1e9}
+        res[name] = {"ms": ms, "ms_min": r["ms_min"], "ms_max": r["ms_max"], "repeats": r["repeats"],
+                     "clocks": r["clocks"], "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
+                     "graph_ms": graph_ms, "graph_ms_min": rg["ms_min"], "graph_ms_max": rg["ms_max"],
+                     "graph_clocks": rg["clocks"], "graph_GB/s": byts / (graph_ms * 1e-3) / 1e9}
     peak, peak_kind = hbm_peak()
     d = res["deterministic"]
     out = {"metric": METRIC, "value": d["elements_per_s"], "unit": "elements/s", "n_gpus": 1, "steps": args.steps,
@@ -1002,7 +1049,7 @@ def run_adjoint64(args):
                       "elements": E, "l2": "working set ~0.5 GB, L2 not flushed"},
            "roofline": {"bound": "hbm", "kernel": "step", "achieved": d["GB/s"], "peak": peak, "unit": "GB/s",
                         "frac": d["GB/s"] / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None},
-           "reductions": res, "gpu_launches": 3 * args.steps}
+           "reductions": res, "gpu_launches": 3 * args.steps, "clocks": d["clocks"]}
     print(json.dumps(out), flush=True)
 
 
@@ -1055,15 +1102,19 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
-    ap.add_argument("--workload", choices=["tet128", "batch96", "elastic128", "adjoint64", "coef_p1", "tri64_fp64",
-                                           "assemble128", "multiphysics128", "iso128"],
+    ap.add_argument("--workload", choices=["tet128", "tet128_shuffled", "batch96", "elastic128", "adjoint64",
+                                           "coef_p1", "tri64_fp64", "assemble128", "multiphysics128", "iso128"],
                     default="tet128",
-                    help="tet128: the headline 128^3 sliver cube (forward + adjoint); batch96: the mixed "
+                    help="tet128: the headline 128^3 sliver cube (forward + adjoint); tet128_shuffled: the same "
+                         "mesh with its elements in random order and its vertices renumbered; batch96: the mixed "
                          "96-mesh batch; elastic128: elasticity FP32 vs tensor cores; adjoint64: 64^3 adjoint; "
                          "coef_p1: P2 Laplacian with a P1 coefficient; tri64_fp64: the FP64 triangle mesh; "
                          "assemble128: global CSR assembly; multiphysics128: three blocks on one mesh; "
                          "iso128: non-affine elements")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: the ranks split ONE mesh by element ranges and sum dcoords with an all-reduce "
+                         "inside each step (strong scaling); default: N independent replicas (weak scaling)")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps

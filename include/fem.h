@@ -258,7 +258,7 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
 
 #define FEM_PHASE_FWD 1 /* forward element matrices into item.A */
 #define FEM_PHASE_BWD 2 /* adjoint of item.dA into item.dcoords / item.dcoef */
-#define FEM_DEVERR_TIMEOUT 4 /* a bounded wait in a batched launch gave up (results incomplete) */
+#define FEM_DEVERR_TIMEOUT 4 /* a bounded wait in a batched launch gave up (that mesh's dcoords not written) */
 
 /* One mesh of a batch (FP32 coordinates).  Pointers are device memory owned
  * by the caller and must stay valid while the batch exists; NULL disables the
@@ -309,6 +309,19 @@ FEM_API fem_status fem_batch_run(fem_batch* batch, int32_t phases, void* stream)
 /* Device error word of the last fem_batch_run (FEM_DEVERR_* bits), copied
  * synchronously to *err_host. */
 FEM_API fem_status fem_batch_errors(const fem_batch* batch, int32_t* err_host, void* stream);
+
+/* Failure injection for tests of the bounded waits (FEM_BATCH_SINGLE and the
+ * grouped modes; the per-item modes have no wait).  Host only: it rewrites the
+ * uploaded descriptor of `item` so that its reduction items wait for
+ * n_tiles + extra_tiles counted tiles instead of n_tiles (the tiles actually
+ * run are unchanged), and bounds every wait of later fem_batch_run calls at
+ * spin_limit polls of about 64 ns (0 = the default, about 2^24 polls).  With
+ * extra_tiles > 0 those waits give up: the run completes, the item's dcoords
+ * is not written and fem_batch_errors reports FEM_DEVERR_TIMEOUT.
+ * extra_tiles = 0 and spin_limit = 0 restore normal runs.  Synchronizes
+ * `stream`. */
+FEM_API fem_status fem_batch_inject_wait(fem_batch* batch, int32_t item, int64_t extra_tiles, uint32_t spin_limit,
+                                         void* stream);
 
 /* Releases the host object (the caller frees the workspace). */
 FEM_API void fem_batch_destroy(fem_batch* batch);
@@ -371,7 +384,13 @@ FEM_API fem_status fem_assemble(const fem_mesh* mesh, int32_t form, const float*
  *     rejected with FEM_ERR_UNSUPPORTED before anything is launched.
  *   - options->reduce other than FEM_REDUCE_DETERMINISTIC: FEM_ERR_UNSUPPORTED.
  *   - The first call on a device looks up the array's device address there
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ *     that first call before any stream capture.  cudaDeviceReset (or any
+ *     reset of the device's primary context) invalidates the kept address:
+ *     once this entry point has run on a device, do not reset that device.
+ *   - Every refusal (bad argument, unsupported combination, a mesh too large
+ *     for the array) is returned before the array is touched or anything is
+ *     launched.
  *   - All calls share the one array: calls whose GPU work may overlap (other
  *     streams, other host threads on the same device) race and corrupt each
  *     other's results.  Serialize them on one stream. */

@@ -434,6 +434,12 @@ class Batch:
     def errors(self, stream=None) -> int:
         return nat.fem_batch_errors(self.handle, _stream_ptr(stream))
 
+    def inject_wait(self, item, extra_tiles, spin_limit=0, stream=None):
+        """Test hook (fem_batch_inject_wait): item's reduction waits for
+        extra_tiles more tiles than exist, each wait bounded by spin_limit
+        polls; inject_wait(item, 0) restores normal runs."""
+        nat.fem_batch_inject_wait(self.handle, item, extra_tiles, spin_limit, _stream_ptr(stream))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:

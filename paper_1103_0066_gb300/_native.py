@@ -26,7 +26,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
            "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
-           "fem_batch_errors", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
+           "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
            "fem_integrate_bwd_saved")
 PHASE_FWD, PHASE_BWD = 1, 2
@@ -98,6 +98,7 @@ def load():
             "fem_batch_set_config": ([P, I32, I32, I32], ctypes.c_int),
             "fem_batch_run": ([P, I32, P], ctypes.c_int),
             "fem_batch_errors": ([P, ctypes.POINTER(I32), P], ctypes.c_int),
+            "fem_batch_inject_wait": ([P, I32, I64, ctypes.c_uint32, P], ctypes.c_int),
             "fem_batch_destroy": ([P], None),
             "fem_assembly_workspace_size": ([MP, I32, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_assembly_build": ([MP, I32, P, SZ, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), P],
@@ -243,6 +244,10 @@ def fem_batch_errors(handle: int, stream: int) -> int:
     e = ctypes.c_int32()
     check(load().fem_batch_errors(handle, ctypes.byref(e), stream or None))
     return e.value
+
+
+def fem_batch_inject_wait(handle: int, item: int, extra_tiles: int, spin_limit: int, stream: int) -> None:
+    check(load().fem_batch_inject_wait(handle, item, extra_tiles, spin_limit, stream or None))
 
 
 def fem_batch_destroy(handle: int) -> None:

@@ -74,6 +74,26 @@ int resolve_jac(int jac, bool coord_f64, bool out_f64) {
   return fem::JAC_F32;
 }
 
+// Every check of an adjoint call that needs no workspace: the mesh, the form,
+// the options and the pointers.  A refused call launches nothing.
+fem_status bwd_args(const fem_mesh* mesh, int32_t form, const fem_options* o, const float* dA,
+                    const float* dcoords) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
+  if (coef_p1(form) || non_affine(form))
+    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");
+  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  if (o->reduce == FEM_REDUCE_DEFERRED && !dcoords)
+    return fail(FEM_ERR_ARG, "FEM_REDUCE_DEFERRED needs dcoords (written by fem_adjoint_reduce)");
+  if (mesh->n_elem > 0 && !dA) return fail(FEM_ERR_ARG, "dA is NULL");
+  return FEM_OK;
+}
+
 template <int D, int FORM>
 void copy_ref(int32_t* K) {
   using FT = fem::FormTraits<D, FORM>;
@@ -86,6 +106,11 @@ void copy_ref(int32_t* K) {
 }  // namespace
 
 namespace fem {
+int32_t bwd_preflight(const fem_mesh* mesh, int32_t form, const fem_options* options, const float* dA,
+                      const float* dcoords) {
+  return bwd_args(mesh, form, options ? options : &kDefaults, dA, dcoords);
+}
+
 void set_last_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -315,28 +340,17 @@ fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, 
 static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
                                 const float* det_in, float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
                                 const fem_options* options, void* stream) {
-  fem_status s = check_mesh(mesh);
-  if (s != FEM_OK) return s;
-  if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (coef_p1(form) || non_affine(form))
-    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
   const fem_options* o = options ? options : &kDefaults;
-  if ((s = check_options(o)) != FEM_OK) return s;
-  if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");
-  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
-  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
-    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  fem_status s = bwd_args(mesh, form, o, dA, dcoords);
+  if (s != FEM_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool atomic = o->reduce == FEM_REDUCE_ATOMIC;
-  if (o->reduce == FEM_REDUCE_DEFERRED && !dcoords)
-    return fail(FEM_ERR_ARG, "FEM_REDUCE_DEFERRED needs dcoords (written by fem_adjoint_reduce)");
   fem::BwdWorkspace W{};
   if (dcoords && !atomic) {
     const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W);
     if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
   }
-  if (mesh->n_elem > 0 && !dA) return fail(FEM_ERR_ARG, "dA is NULL");
   if (!dcoords && !dcoef) return ok();
   cudaError_t e;
   if (dcoords && atomic) {

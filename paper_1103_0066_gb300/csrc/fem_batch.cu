@@ -54,6 +54,7 @@ struct BatchMesh {
   const int32_t* voff;
   float* records;  // vertex-major
   int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space (all meshes)
+  int64_t wait_tiles;           // tiles counted done before the mesh's reduction items run (= n_tiles)
   int64_t red_begin, n_red;     // reduction items (all meshes)
   int64_t ktile_begin, kred_begin;  // the same within its kind group (grouped launches)
 };
@@ -68,7 +69,7 @@ struct BatchCounters {
 
 constexpr int kRedVerts = 2048;  // vertices per reduction item
 constexpr int kItemLanes = 10;   // streams of the per-item concurrent mode (4: 2.14 ms, 6: 2.01, 10: 1.97, 16: 1.98 on the 96-mesh batch)
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr uint32_t kSpinLimit = 1u << 24;  // default bound of a reduction item's wait (about a second)
 
 // Shared memory of one batch warp: a stage shared by the forward tile and the
 // dA rows, then the slot stage of the warp's records (sized for tets).
@@ -212,7 +213,7 @@ __device__ void batch_reduce(const BatchMesh& M, int64_t r) {
 __global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* __restrict__ desc, int n_items,
                                                                int64_t n_tile_items, int64_t n_total,
                                                                BatchCounters* ctr, int phases, int chunk,
-                                                               size_t stage_bytes) {
+                                                               size_t stage_bytes, uint32_t spin_limit) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_item;
   int err = 0;
@@ -241,21 +242,25 @@ __global__ void __launch_bounds__(kTileElems) fem_batch_kernel(const BatchMesh* 
         const int64_t ir = it - n_tile_items;
         const int m = find_mesh(desc, n_items, ir, true);
         const BatchMesh& M = desc[m];
+        __shared__ int s_timeout;
         if (threadIdx.x == 0) {
           const volatile int32_t* done = ctr->done + m;
           uint32_t spins = 0;
-          while (*done < M.n_tiles && spins < kSpinLimit) {
+          while (*done < M.wait_tiles && spins < spin_limit) {
             __nanosleep(64);
             ++spins;
           }
-          if (*done < M.n_tiles) atomicOr(&ctr->err, DEVERR_TIMEOUT);
+          s_timeout = *done < M.wait_tiles;
           __threadfence();
         }
         __syncthreads();
-        if (M.kind < 3)
+        if (s_timeout) {  // the mesh's records are incomplete: its dcoords are not written
+          err |= DEVERR_TIMEOUT;
+        } else if (M.kind < 3) {
           batch_reduce<2>(M, ir - M.red_begin);
-        else
+        } else {
           batch_reduce<3>(M, ir - M.red_begin);
+        }
         __syncthreads();
       }
     }
@@ -355,7 +360,8 @@ __device__ __forceinline__ void kind_tile(const BatchMesh& M, const KindItem<D>&
 template <int D, int FORM>
 __global__ void __launch_bounds__(kTileElems)
     fem_batch_kind_kernel(const BatchMesh* __restrict__ desc, int n, int m_base, int64_t n_tile_items,
-                          int64_t n_total, BatchCounters* ctr, int slot, int phases, int chunk) {
+                          int64_t n_total, BatchCounters* ctr, int slot, int phases, int chunk,
+                          uint32_t spin_limit) {
   using KP = KindPlan<D, FORM>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ long long s_next;
@@ -399,11 +405,11 @@ __global__ void __launch_bounds__(kTileElems)
       if (tid == 0) {
         const volatile int32_t* done = ctr->done + m_base + m;
         uint32_t spins = 0;
-        while (*done < M.n_tiles && spins < kSpinLimit) {
+        while (*done < M.wait_tiles && spins < spin_limit) {
           __nanosleep(64);
           ++spins;
         }
-        s_timeout = *done < M.n_tiles;
+        s_timeout = *done < M.wait_tiles;
         __threadfence();
       }
       __syncthreads();
@@ -441,6 +447,7 @@ struct KindLaunch {
   BatchCounters* ctr;
   int slot, phases, chunk;
   int64_t grid;
+  uint32_t spin_limit;
 };
 
 template <int D, int FORM>
@@ -457,7 +464,7 @@ cudaError_t kind_setup_t(int* occ, size_t* smem) {
 template <int D, int FORM>
 cudaError_t kind_launch_t(const KindLaunch& L, cudaStream_t st) {
   fem_batch_kind_kernel<D, FORM><<<unsigned(L.grid), kTileElems, KindPlan<D, FORM>::smem, st>>>(
-      L.desc, L.n, L.m_base, L.n_tile_items, L.n_total, L.ctr, L.slot, L.phases, L.chunk);
+      L.desc, L.n, L.m_base, L.n_tile_items, L.n_total, L.ctr, L.slot, L.phases, L.chunk, L.spin_limit);
   return cudaGetLastError();
 }
 
@@ -491,6 +498,7 @@ struct fem_batch {
   int n_items = 0;
   std::vector<fem::BatchMesh> desc;   // caller's order (single-kernel mode)
   std::vector<fem::BatchMesh> kdesc;  // grouped by kind, kind-local item ranges
+  std::vector<int> kpos;              // position of each item's descriptor in kdesc (-1: in no group)
   fem::BatchMesh* d_desc = nullptr;
   fem::BatchMesh* d_kdesc = nullptr;
   fem::BatchCounters* d_ctr = nullptr;
@@ -498,6 +506,7 @@ struct fem_batch {
   int64_t n_tile_items = 0, n_total_fwd = 0, n_total = 0;
   size_t stage_bytes = 0, smem = 0;
   int ctas_per_sm = 0, chunk = 1, max_ctas_per_sm = 1, mode = FEM_BATCH_SINGLE;
+  uint32_t spin_limit = fem::kSpinLimit;  // bound of the reduction items' waits (fem_batch_inject_wait)
   struct Group {
     int kind, first, count;
     int64_t n_tile_items, n_total, work;
@@ -598,6 +607,7 @@ cudaError_t launch_group(fem_batch* b, const fem_batch::Group& g, int phases, in
   L.phases = phases;
   L.chunk = chunk;
   L.grid = grid_for(std::min(ctas_per_sm, g.occ), total, chunk);
+  L.spin_limit = b->spin_limit;
   return fem::kind_launch(g.kind, L, st);
 }
 
@@ -685,7 +695,7 @@ cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, i
   if (mode == FEM_BATCH_SINGLE) {
     const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
     fem::fem_batch_kernel<<<unsigned(grid_for(ctas_per_sm, total, chunk)), fem::kTileElems, b->smem, st>>>(
-        b->d_desc, b->n_items, b->n_tile_items, total, b->d_ctr, phases, chunk, b->stage_bytes);
+        b->d_desc, b->n_items, b->n_tile_items, total, b->d_ctr, phases, chunk, b->stage_bytes, b->spin_limit);
     return cudaGetLastError();
   }
   if (mode == FEM_BATCH_GROUPED || b->groups.size() < 2) {
@@ -755,6 +765,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   b->items.assign(items, items + n_items);
   b->item_ws.assign(size_t(n_items), fem::BwdWorkspace{});
   b->item_det.assign(size_t(n_items), nullptr);
+  b->kpos.assign(size_t(n_items), -1);
   size_t kdesc_off = 0, ctr_off = 0;
   size_t off = head_bytes(n_items, &kdesc_off, &ctr_off, &b->ctr_bytes);
   char* base = static_cast<char*>(ws);
@@ -780,6 +791,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
     M.flags = (it.A ? fem::BM_FWD : 0) | ((it.dA && (it.dcoords || it.dcoef)) ? fem::BM_BWD : 0) |
               ((it.dA && it.dcoords) ? fem::BM_REC : 0);
     M.n_tiles = (M.n_elem + fem::kTileElems - 1) / fem::kTileElems;
+    M.wait_tiles = M.n_tiles;
     M.tile_begin = tiles;
     tiles += M.n_tiles;
     stage = std::max(stage, fem::stage_bytes_for_kind(M.kind));
@@ -823,8 +835,10 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   for (int kind = 0; kind < 6 && e == cudaSuccess; ++kind) {
     fem_batch::Group g{kind, int(b->kdesc.size()), 0, 0, 0, 0, 1};
     int64_t kt = 0, kr = 0;
-    for (const auto& M0 : b->desc) {
+    for (size_t i = 0; i < b->desc.size(); ++i) {
+      const fem::BatchMesh& M0 = b->desc[i];
       if (M0.kind != kind) continue;
+      b->kpos[i] = int(b->kdesc.size());
       fem::BatchMesh M = M0;
       M.ktile_begin = kt;
       kt += M.n_tiles;
@@ -1004,6 +1018,30 @@ fem_status fem_batch_errors(const fem_batch* b, int32_t* err_host, void* stream)
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) {
     fem::set_last_error("fem_batch_errors: %s", cudaGetErrorString(e));
+    return FEM_ERR_CUDA;
+  }
+  return FEM_OK;
+}
+
+fem_status fem_batch_inject_wait(fem_batch* b, int32_t item, int64_t extra_tiles, uint32_t spin_limit,
+                                 void* stream) {
+  if (!b || item < 0 || item >= b->n_items || extra_tiles < 0) {
+    fem::set_last_error("fem_batch_inject_wait: bad batch, item or extra_tiles");
+    return FEM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t want = b->desc[size_t(item)].n_tiles + extra_tiles;
+  b->desc[size_t(item)].wait_tiles = want;
+  if (b->kpos[size_t(item)] >= 0) b->kdesc[size_t(b->kpos[size_t(item)])].wait_tiles = want;
+  b->spin_limit = spin_limit ? spin_limit : fem::kSpinLimit;
+  cudaError_t e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(fem::BatchMesh) * b->desc.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && !b->kdesc.empty())
+    e = cudaMemcpyAsync(b->d_kdesc, b->kdesc.data(), sizeof(fem::BatchMesh) * b->kdesc.size(),
+                        cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables are reused by later calls
+  if (e != cudaSuccess) {
+    fem::set_last_error("fem_batch_inject_wait: %s", cudaGetErrorString(e));
     return FEM_ERR_CUDA;
   }
   return FEM_OK;

@@ -115,6 +115,19 @@ cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert
 // Records the reason reported by fem_last_error() for the calling thread.
 void set_last_error(const char* fmt, ...);
 
+}  // namespace fem
+
+struct fem_mesh;
+struct fem_options;
+
+namespace fem {
+
+// Every check of fem_integrate_bwd that needs no workspace (mesh, form,
+// options, dA and the deferred-mode dcoords), with the same status and
+// fem_last_error() message; 0 (FEM_OK) when the call may proceed.
+int32_t bwd_preflight(const fem_mesh* mesh, int32_t form, const fem_options* options, const float* dA,
+                      const float* dcoords);
+
 // Device facts of the current device (cached per device).
 int device_sm_count();
 size_t device_smem_optin();

@@ -64,12 +64,15 @@ fem_status fem_integrate_bwd_noalloc(const fem_mesh* mesh, int32_t form, const f
     fem::set_last_error("fem_integrate_bwd_noalloc always uses the deterministic reduction");
     return FEM_ERR_UNSUPPORTED;
   }
+  // Every refusal comes before the scratch array is touched: a refused call
+  // launches nothing and leaves the array as the last accepted call left it.
+  fem_status s = static_cast<fem_status>(fem::bwd_preflight(mesh, form, &o, dA, dcoords));
+  if (s != FEM_OK) return s;
   if (!dcoords) {  // only the coefficient gradient: no scratch is involved
     return fem_integrate_bwd(mesh, form, coef, dA, nullptr, dcoef, nullptr, 0, &o, stream);
   }
   size_t need = 0;
-  fem_status s = fem_bwd_workspace_size(mesh, form, &o, &need);
-  if (s != FEM_OK) return s;
+  if ((s = fem_bwd_workspace_size(mesh, form, &o, &need)) != FEM_OK) return s;
   if (need > FEM_NOALLOC_SCRATCH_BYTES) {
     fem::set_last_error(
         "mesh needs %zu bytes of scratch, more than the %u built in; use fem_integrate_bwd with a "

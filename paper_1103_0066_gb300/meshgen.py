@@ -182,6 +182,28 @@ def check_orientation(mesh: Mesh) -> None:
     assert np.all(det > 0), f"{int((det <= 0).sum())} inverted or flat elements"
 
 
+def shuffled(mesh: Mesh, rng: np.random.Generator, elements: bool = True,
+             vertices: bool = True) -> tuple[Mesh, np.ndarray]:
+    """The same mesh with its elements in a seeded random order and its
+    vertices renumbered at random.  Each element keeps its local vertex order,
+    so orientation and every element matrix are unchanged; only the order in
+    which elements come and the numbers of their vertices differ.  This is how
+    a mesh from an unstructured mesh generator looks to the kernels:
+    consecutive elements share few vertices, so a 32-element tile touches up
+    to 4 x 32 distinct vertices and the coordinate gather loses its locality.
+
+    Returns (mesh, order): new element k is old element order[k] (apply it to
+    any per-element array, e.g. coef[order])."""
+    E, V = mesh.n_elem, mesh.n_vert
+    order = rng.permutation(E) if elements else np.arange(E)
+    new_id = rng.permutation(V) if vertices else np.arange(V)   # old vertex v -> new_id[v]
+    coords = np.empty_like(mesh.coords)
+    coords[new_id] = mesh.coords
+    conn = new_id[mesh.conn[order]].astype(np.int32)
+    sliver = None if mesh.sliver is None else mesh.sliver[order]
+    return Mesh(mesh.dim, coords, np.ascontiguousarray(conn), sliver), order
+
+
 def lognormal_coef(rng: np.random.Generator, E: int) -> np.ndarray:
     return np.exp(rng.standard_normal(E)).astype(np.float32)
 
@@ -242,6 +264,12 @@ def curved_mesh(mesh: Mesh, eps: float = 0.05, dtype=np.float32) -> tuple[Mesh, 
     return curved, _warp(M, eps).astype(dtype)
 
 
+def workload_tet_shuffled(n: int = 128, k: int = 2, ks: int = 12) -> Mesh:
+    """The 128^3 sliver cube of workload_tet_slivers with its elements in a
+    random order and its vertices renumbered at random (seed 11030066 + ks)."""
+    return shuffled(workload_tet_slivers(n, k), rng_for(ks))[0]
+
+
 def workload_curved_tets(n: int = 64, k: int = 6, eps: float = 0.05):
     """n^3 Kuhn cube, jitter 0.15 h, no slivers, warped into quadratic elements."""
     base = cube_tet_mesh(n, 0.15, rng_for(k), 0.0, np.float32)
@@ -268,9 +296,11 @@ def _first_elements(mesh: Mesh, E: int) -> Mesh:
 
 
 def mixed_batch(n_meshes: int = 96, e_lo: float = 1e3, e_hi: float = 2e6, k: int = 5,
-                scale: float = 1.0) -> list[BatchItem]:
+                scale: float = 1.0, shuffle: bool = False) -> list[BatchItem]:
     """96 meshes, E_m = round(exp(U(ln e_lo, ln e_hi))) (times ``scale`` for
-    shrunken test batches), kinds cycling over a seeded shuffle of BATCH_KINDS."""
+    shrunken test batches), kinds cycling over a seeded shuffle of BATCH_KINDS.
+    shuffle=True puts each mesh's elements in a random order and renumbers its
+    vertices (``shuffled``)."""
     rng = rng_for(k)
     sizes = np.round(np.exp(rng.uniform(math.log(e_lo), math.log(e_hi), size=n_meshes)))
     sizes = np.maximum(1, np.round(sizes * scale)).astype(np.int64)
@@ -286,6 +316,8 @@ def mixed_batch(n_meshes: int = 96, e_lo: float = 1e3, e_hi: float = 2e6, k: int
             nc = max(1, math.ceil((E / 6.0) ** (1.0 / 3.0)))
             full = cube_tet_mesh(nc, 0.15, rng, 0.0, np.float32)
         mesh = _first_elements(full, E)
+        if shuffle:
+            mesh = shuffled(mesh, rng)[0]
         n = form_n(form, dim)
         items.append(BatchItem(form, mesh, lognormal_coef(rng, E), upstream(rng, E, n)))
     return items

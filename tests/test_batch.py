@@ -184,3 +184,39 @@ def test_multiphysics_blocks_share_one_mesh(gfem):
         A_ref = gfem.integrate_fwd(coords, conn, it["form"], coef)
         dx_ref, dw_ref = gfem.integrate_bwd(coords, conn, it["form"], it["dA"], coef)
         assert torch.equal(it["A"], A_ref) and torch.equal(it["dcoords"], dx_ref) and torch.equal(it["dcoef"], dw_ref)
+
+
+@pytest.mark.parametrize("mode", ["single", "grouped", "concurrent"])
+def test_bounded_wait_expires_and_the_next_run_is_correct(gfem, mode):
+    """Failure detection without a GPU fault.  On the host, one mesh's
+    descriptor is rewritten so that its reduction items wait for one tile more
+    than the mesh has, and every wait is bounded at 2,000 polls (about 0.1 ms).
+    The run completes, reports FEM_DEVERR_TIMEOUT, leaves that mesh's dcoords
+    unwritten and every other output as in a normal run.  After the injection
+    is lifted, the next run on the same GPU is correct again."""
+    items = _items(scale=0.002, n_meshes=12)
+    batch = gfem.Batch(items)
+    batch.set_config(2, 1, _mode(gfem, mode))
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.errors() == 0
+    ref = [(it["A"].clone(), it["dcoords"].clone(), it["dcoef"].clone()) for it in items]
+    victim = max(range(len(items)), key=lambda k: items[k]["src"].mesh.n_elem)
+    batch.inject_wait(victim, extra_tiles=1, spin_limit=2000)
+    for it in items:
+        it["dcoords"].fill_(float("nan"))
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.errors() & gfem.nat.DEVERR_TIMEOUT
+    for k, (it, (A0, x0, w0)) in enumerate(zip(items, ref)):
+        assert torch.equal(it["A"], A0) and torch.equal(it["dcoef"], w0)
+        if k == victim:
+            assert torch.isnan(it["dcoords"]).all()       # its records were never summed
+        else:
+            assert torch.equal(it["dcoords"], x0)
+    batch.inject_wait(victim, 0, 0)
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.errors() == 0
+    for it, (A0, x0, w0) in zip(items, ref):
+        assert torch.equal(it["A"], A0) and torch.equal(it["dcoords"], x0) and torch.equal(it["dcoef"], w0)

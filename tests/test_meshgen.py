@@ -41,3 +41,28 @@ def test_mixed_batch_recipe():
         n = mg.form_n(it.form, it.mesh.dim)
         assert it.dA.shape == (it.mesh.n_elem, n, n)
         assert it.mesh.conn.max() < it.mesh.n_vert
+
+
+def test_shuffled_mesh_is_a_relabelling():
+    """Element k of the shuffled mesh is element order[k] of the original, with
+    the same vertex positions in the same local order (so every element matrix
+    is unchanged), and a shuffled tet mesh's 32-element tiles touch far more
+    distinct vertices than the cell-major ones (more than the 36 of the
+    assembly's dense tile in most tiles)."""
+    m = mg.cube_tet_mesh(8, 0.15, mg.rng_for(2), 0.05, np.float32)
+    s, order = mg.shuffled(m, mg.rng_for(12))
+    assert s.n_elem == m.n_elem and s.n_vert == m.n_vert
+    assert np.array_equal(s.coords[s.conn], m.coords[m.conn[order]])
+    assert np.array_equal(s.sliver, m.sliver[order])
+    assert sorted(map(tuple, np.sort(s.coords, 0))) == sorted(map(tuple, np.sort(m.coords, 0)))
+    mg.check_orientation(s)
+
+    def distinct_per_tile(mesh):
+        T = mesh.n_elem // 32
+        return np.array([np.unique(mesh.conn[32 * t:32 * t + 32]).size for t in range(T)])
+    assert np.mean(distinct_per_tile(m) <= 36) > 0.95
+    d = distinct_per_tile(s)
+    assert np.mean(d > 36) > 0.9 and d.max() > 100
+    b = mg.mixed_batch(n_meshes=6, scale=0.002, shuffle=True)
+    b0 = mg.mixed_batch(n_meshes=6, scale=0.002)
+    assert [x.mesh.n_elem for x in b] == [x.mesh.n_elem for x in b0]

@@ -2,11 +2,13 @@
 
 fem_integrate_bwd_noalloc is for callers that cannot allocate device memory:
 it takes no workspace and works inside a scratch array built into the library.
-This test calls it through the C ABI twice in a row and checks both results
-against the regular entry point, fem_integrate_bwd with a caller-allocated
-workspace, within the adjoint tests' tolerance (1e-5 of the largest entry).
-It also checks that a mesh too large for the built-in array is refused before
-anything runs.  It lives in its own file so that it is collected last.
+These tests call it through the C ABI twice in a row and compare each result
+with the regular entry point, fem_integrate_bwd with a caller-allocated
+workspace.  Both run the same incidence build, element pass and
+deterministic reduction on the same inputs, so the results must be equal bit
+for bit; any stale scratch left by an earlier call would break that.  A large
+mesh followed by a smaller one, a coefficient-gradient-only call and calls
+refused before anything runs are covered too.  The file is collected last.
 """
 import ctypes
 
@@ -17,7 +19,6 @@ import torch
 from paper_1103_0066_gb300 import meshgen as mg
 
 pytestmark = pytest.mark.gpu
-TOL = 1e-5
 DEV = "cuda:0"
 
 
@@ -25,32 +26,29 @@ def _t(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def _rel(a, b):
-    a = a.double().cpu().numpy()
-    b = b.double().cpu().numpy()
-    return float(np.abs(a - b).max() / np.abs(b).max())
-
-
-def _noalloc(fem, coords, conn, form, dA, coef):
+def _noalloc(fem, coords, conn, form, dA, coef, want_dcoords=True):
     nat = fem.nat
     m = fem._mesh_struct(coords, conn)
-    dx = torch.full((coords.shape[0], coords.shape[1]), float("nan"), device=DEV)
+    dx = torch.full((coords.shape[0], coords.shape[1]), float("nan"), device=DEV) if want_dcoords else None
     dw = torch.full((conn.shape[0],), float("nan"), device=DEV)
     st = nat.load().fem_integrate_bwd_noalloc(
         ctypes.byref(m), form, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
-        ctypes.c_void_p(dx.data_ptr()), ctypes.c_void_p(dw.data_ptr()), ctypes.byref(nat.options_struct()),
-        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        ctypes.c_void_p(dx.data_ptr() if dx is not None else 0), ctypes.c_void_p(dw.data_ptr()),
+        ctypes.byref(nat.options_struct()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == nat.FEM_OK, nat.load().fem_last_error().decode()
     torch.cuda.synchronize()
     return dx, dw
 
 
+def _case(dim, n, seed):
+    if dim == 3:
+        return mg.cube_tet_mesh(n, 0.15, mg.rng_for(seed), 0.05, np.float32)
+    return mg.square_tri_mesh(n, 0.2, mg.rng_for(seed), np.float32)
+
+
 @pytest.mark.parametrize("dim,form", [(3, 0), (3, 2), (2, 1)])
 def test_noalloc_matches_workspace_entry_point(gfem, dim, form):
-    if dim == 3:
-        mesh = mg.cube_tet_mesh(9, 0.15, mg.rng_for(61), 0.05, np.float32)   # 4,374 tets, slivers
-    else:
-        mesh = mg.square_tri_mesh(20, 0.2, mg.rng_for(61), np.float32)       # 800 triangles
+    mesh = _case(dim, 9 if dim == 3 else 20, 61)   # 4,374 tets with slivers / 800 triangles
     n = mg.form_n(form, dim)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
     coef = _t(mg.lognormal_coef(mg.rng_for(62), mesh.n_elem))
@@ -58,14 +56,62 @@ def test_noalloc_matches_workspace_entry_point(gfem, dim, form):
         dA = _t(mg.upstream(mg.rng_for(63 + call), mesh.n_elem, n))
         ref_x, ref_w = gfem.integrate_bwd(coords, conn, form, dA, coef)
         got_x, got_w = _noalloc(gfem, coords, conn, form, dA, coef)
-        assert _rel(got_x, ref_x) <= TOL
-        assert _rel(got_w, ref_w) <= TOL
+        assert torch.equal(got_x, ref_x)
+        assert torch.equal(got_w, ref_w)
 
 
-def test_noalloc_refuses_meshes_beyond_its_scratch(gfem):
+def test_noalloc_larger_then_smaller_mesh(gfem):
+    """A large mesh fills much of the scratch array; a smaller one right after
+    must not read anything the large one left behind."""
+    big, small = _case(3, 28, 64), _case(3, 5, 65)        # 131,712 and 750 tets (+ slivers)
+    for mesh in (big, small, big):
+        coords, conn = _t(mesh.coords), _t(mesh.conn)
+        coef = _t(mg.lognormal_coef(mg.rng_for(66), mesh.n_elem))
+        dA = _t(mg.upstream(mg.rng_for(67), mesh.n_elem, 4))
+        ref_x, ref_w = gfem.integrate_bwd(coords, conn, 0, dA, coef)
+        got_x, got_w = _noalloc(gfem, coords, conn, 0, dA, coef)
+        assert torch.equal(got_x, ref_x) and torch.equal(got_w, ref_w)
+
+
+def test_noalloc_coefficient_gradient_only(gfem):
+    mesh = _case(3, 6, 68)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    coef = _t(mg.lognormal_coef(mg.rng_for(69), mesh.n_elem))
+    dA = _t(mg.upstream(mg.rng_for(70), mesh.n_elem, 4))
+    _, ref_w = gfem.integrate_bwd(coords, conn, 0, dA, coef, need_dcoords=False)
+    got_x, got_w = _noalloc(gfem, coords, conn, 0, dA, coef, want_dcoords=False)
+    assert got_x is None and torch.equal(got_w, ref_w)
+
+
+def test_noalloc_refusals_launch_nothing(gfem):
+    """Refused calls return before the scratch array is touched: a mesh too
+    large for it, FP64 coordinates and a tensor-core contraction (the adjoint is
+    FP32 only).  The pointers of the first case are never dereferenced.  A
+    valid call afterwards still matches the workspace entry point bit for bit."""
     nat = gfem.nat
+    lib = nat.load()
     big = nat.mesh_struct(3, 0, 10_000_000, 2_000_000, 0x1000, 0x2000)  # never launched
-    st = nat.load().fem_integrate_bwd_noalloc(ctypes.byref(big), 0, None, ctypes.c_void_p(0x3000),
-                                              ctypes.c_void_p(0x4000), None, None, None)
+    st = lib.fem_integrate_bwd_noalloc(ctypes.byref(big), 0, None, ctypes.c_void_p(0x3000),
+                                       ctypes.c_void_p(0x4000), None, None, None)
     assert st == nat.FEM_ERR_UNSUPPORTED
-    assert "caller-allocated workspace" in nat.load().fem_last_error().decode()
+    assert "caller-allocated workspace" in lib.fem_last_error().decode()
+    mesh = _case(3, 5, 71)
+    coords64, conn = _t(mesh.coords.astype(np.float64)), _t(mesh.conn)
+    dA = _t(mg.upstream(mg.rng_for(72), mesh.n_elem, 4))
+    dx = torch.zeros((mesh.n_vert, 3), device=DEV)
+    m64 = gfem._mesh_struct(coords64, conn)
+    st = lib.fem_integrate_bwd_noalloc(ctypes.byref(m64), 0, None, ctypes.c_void_p(dA.data_ptr()),
+                                       ctypes.c_void_p(dx.data_ptr()), None, None, None)
+    assert st == nat.FEM_ERR_UNSUPPORTED and "FP32 coordinates" in lib.fem_last_error().decode()
+    coords = _t(mesh.coords)
+    m32 = gfem._mesh_struct(coords, conn)
+    tc = nat.options_struct(contract=nat.CONTRACT_BF16X3)
+    st = lib.fem_integrate_bwd_noalloc(ctypes.byref(m32), 0, None, ctypes.c_void_p(dA.data_ptr()),
+                                       ctypes.c_void_p(dx.data_ptr()), None, ctypes.byref(tc), None)
+    assert st == nat.FEM_ERR_UNSUPPORTED and "FP32" in lib.fem_last_error().decode()
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(dx) == 0  # nothing was written
+    coef = _t(mg.lognormal_coef(mg.rng_for(73), mesh.n_elem))
+    ref_x, ref_w = gfem.integrate_bwd(coords, conn, 0, dA, coef)
+    got_x, got_w = _noalloc(gfem, coords, conn, 0, dA, coef)
+    assert torch.equal(got_x, ref_x) and torch.equal(got_w, ref_w)
