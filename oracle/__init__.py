@@ -12,6 +12,10 @@ What it computes (Knepley & Terrel, Sec. 3):
     Eq. 10 scaled by the 1/4 of Eq. 14 / Eq. 24 (elasticity eps:eps), times a
     per-element constant coefficient (piecewise-constant case of Eq. 20).
   * ``integrate_vjp``: the hand-derived reverse mode of the same steps.
+  * ``integrate_div`` / ``integrate_div_vjp``: the coupling block of a
+    multiphysics pair, B = int q div v with q in P1 and v in [P1]^d or
+    [P2]^d (Sec. 6's blocks of coupled systems; Eq. 1 with one derivative in
+    K), by the same quadrature, and its reverse mode.
   * ``simplex_rule`` / ``basis`` / ``element_matrix``: the building blocks,
     exposed so the tests can pin each one separately.
 """
@@ -71,7 +75,12 @@ def _load():
         lib.orc_integrate_w1.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
         lib.orc_element_matrix_iso.argtypes = [I, I, P, P, D, I, P, P]
         lib.orc_integrate_iso.argtypes = [I, I, I64, I64, P, P, P, P, I, P, P, I]
-        for name in ("orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
+        lib.orc_element_matrix_div.argtypes = [I, I, P, D, I, P, P]
+        lib.orc_element_vjp_div.argtypes = [I, I, P, D, I, P, P, P]
+        lib.orc_integrate_div.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
+        lib.orc_integrate_div_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
+        for name in ("orc_element_matrix_div", "orc_element_vjp_div", "orc_integrate_div",
+                     "orc_integrate_div_vjp", "orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
                      "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
                      "orc_integrate_vjp", "orc_element_matrix_w1", "orc_integrate_w1",
                      "orc_element_matrix_iso", "orc_integrate_iso"):
@@ -258,6 +267,69 @@ def integrate_vjp(dim: int, form: int, conn, coords, dA, coef=None, q: int = 3,
     nt = max_threads() if nthreads is None else nthreads
     rc = _load().orc_integrate_vjp(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(cf), q,
                                    _ptr(dA), _ptr(dcoords), _ptr(dcoef), nt)
+    if rc < 0:
+        raise ValueError("bad vjp request")
+    return dcoords, dcoef
+
+
+def div_shape(dim: int, vdeg: int):
+    """(rows, columns) of the coupling block: d+1 P1 rows, d * n_basis(vdeg) columns."""
+    return dim + 1, dim * _load().orc_n_basis(dim, vdeg)
+
+
+def element_matrix_div(dim: int, vdeg: int, X, coef: float = 1.0, q: int = 3):
+    """Coupling block B [d+1][d * nbv] of one element: B_{i,(c,j)} = int coef
+    phi_i d psi_j / d x_c (phi P1, psi P`vdeg`, column c * nbv + j).  Returns
+    (B, det J, flags)."""
+    X = _f64(X)
+    B = np.zeros(div_shape(dim, vdeg))
+    det = np.zeros(1)
+    rc = _load().orc_element_matrix_div(dim, vdeg, _ptr(X), float(coef), q, _ptr(B), _ptr(det))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return B, float(det[0]), rc
+
+
+def element_vjp_div(dim: int, vdeg: int, X, Bbar, coef: float = 1.0, q: int = 3):
+    X = _f64(X)
+    Bbar = _f64(Bbar)
+    Xbar = np.zeros_like(X)
+    cbar = np.zeros(1)
+    rc = _load().orc_element_vjp_div(dim, vdeg, _ptr(X), float(coef), q, _ptr(Bbar), _ptr(Xbar), _ptr(cbar))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return Xbar, float(cbar[0])
+
+
+def integrate_div(dim: int, vdeg: int, conn, coords, coef=None, q: int = 3, nthreads: int | None = None):
+    """Coupling blocks B [E][d+1][d * nbv] (FP64) and per-element flags."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    E, V = conn.shape[0], coords.shape[0]
+    cf = None if coef is None else _f64(coef)
+    B = np.zeros((E,) + div_shape(dim, vdeg))
+    flags = np.zeros(E, dtype=np.int32)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_div(dim, vdeg, E, V, _ptr(conn), _ptr(coords), _ptr(cf), q, _ptr(B), _ptr(flags), nt)
+    if rc < 0:
+        raise ValueError("bad integrate request")
+    return B, flags
+
+
+def integrate_div_vjp(dim: int, vdeg: int, conn, coords, dB, coef=None, q: int = 3, nthreads: int | None = None):
+    """Reverse mode of integrate_div: (dcoords [V][dim], dcoef [E]) for dB [E][d+1][d * nbv]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    dB = _f64(dB)
+    E, V = conn.shape[0], coords.shape[0]
+    if dB.shape != (E,) + div_shape(dim, vdeg):
+        raise ValueError("dB must be [E][d+1][d * nbv]")
+    cf = None if coef is None else _f64(coef)
+    dcoords = np.zeros((V, dim))
+    dcoef = np.zeros(E)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_div_vjp(dim, vdeg, E, V, _ptr(conn), _ptr(coords), _ptr(cf), q, _ptr(dB),
+                                       _ptr(dcoords), _ptr(dcoef), nt)
     if rc < 0:
         raise ValueError("bad vjp request")
     return dcoords, dcoef

@@ -34,6 +34,10 @@
  *     method on the Legendre recurrence) collapsed onto the simplex by the
  *     Duffy map.  q points per direction integrate degree 2q-3 (tet) exactly
  *     in the collapsed direction; q = 3 covers every form here.
+ *   * The coupling block of a multiphysics pair (Sec. 6: coupled systems
+ *     broken into blocks), B_{i,(c,j)} = int_T c_e phi_i d psi_j / d x_c with
+ *     phi the P1 scalar basis and psi the P1 or P2 basis of each component of
+ *     a vector field (orc_integrate_div): by the same quadrature and LU solve.
  *   * The reverse mode (vector-Jacobian product) is derived by hand from the
  *     same quadrature steps, in the opposite order.
  *
@@ -691,6 +695,194 @@ int orc_integrate_vjp(int dim, int form, int64_t n_elem, int64_t n_vert, const i
     if (f == 0)
       f = orc_element_vjp(dim, form, X, coef ? coef[e] : 1.0, q, Abar + e * (int64_t)n * n, xb,
                           &cb);
+    if (f != 0) {
+      for (int k = 0; k < nv * dim; ++k) xb[k] = 0.0;
+      cb = 0.0;
+    }
+    fl[e] = f;
+    if (dcoef) dcoef[e] = cb;
+    any |= f;
+  }
+  for (int64_t k = 0; k < n_vert * dim; ++k) dcoords[k] = 0.0;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    if (fl[e] & ORC_FLAG_CONN) continue;
+    for (int k = 0; k < nv; ++k) {
+      int64_t v = conn[e * nv + k];
+      for (int a = 0; a < dim; ++a) dcoords[v * dim + a] += xbar[(e * nv + k) * dim + a];
+    }
+  }
+  free(xbar);
+  free(fl);
+  return any;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coupling block of a multiphysics system                                  */
+/* ------------------------------------------------------------------------ */
+/* Sec. 6 plans systems of equations from multiphysics problems, with the weak
+ * form broken into blocks; the off-diagonal block of a pair (scalar field q,
+ * vector field v) is the bilinear form int q div v, whose analytic tensor
+ * holds a basis function times a basis-function derivative (Eq. 1 and the
+ * closing remark of Sec. 3.1).  Here, by direct quadrature:
+ *   B_{i,(c,j)} = int_T coef phi_i d psi_j / d x_c
+ * phi the P1 scalar basis (rows i = 0..d), psi the P`vdeg` basis of each
+ * component c of the vector field (columns c * nbv + j, component-major).
+ * B is [(d+1)][d * nbv] row-major.  Returns 0 or ORC_FLAG_DEGENERATE (B
+ * zeroed) when det J == 0. */
+int orc_element_matrix_div(int dim, int vdeg, const double* X, double coef, int q, double* B, double* detJ_out) {
+  int nq = dim + 1, nbv = orc_n_basis(dim, vdeg);
+  if (nbv < 0 || dim < 2 || dim > 3) return -1;
+  int ncol = dim * nbv;
+  memset(B, 0, sizeof(double) * nq * ncol);
+  double J[3][3], Jt[3][3];
+  jacobian(dim, X, J);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Jt[a][b] = J[b][a];
+  lu3 fJt;
+  lu_factor(dim, Jt, &fJt);
+  if (detJ_out) *detJ_out = fJt.det;
+  if (fJt.det == 0.0) return ORC_FLAG_DEGENERATE;
+  double absdet = fabs(fJt.det);
+  double pts[ORC_MAXPTS * 3], wts[ORC_MAXPTS];
+  int np = orc_simplex_rule(dim, q, pts, wts);
+  if (np < 0) return -1;
+  for (int p = 0; p < np; ++p) {
+    double phi[ORC_MAXB], gphi[ORC_MAXB * 3], psi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3];
+    orc_basis(dim, 1, pts + p * dim, phi, gphi);
+    orc_basis(dim, vdeg, pts + p * dim, psi, gref);
+    physical_gradients(dim, &fJt, nbv, gref, g);
+    double scale = wts[p] * absdet * coef;
+    for (int i = 0; i < nq; ++i)
+      for (int c = 0; c < dim; ++c)
+        for (int j = 0; j < nbv; ++j) B[i * ncol + c * nbv + j] += scale * phi[i] * g[j][c];
+  }
+  return 0;
+}
+
+/* Reverse mode of orc_element_matrix_div: given Bbar = dL/dB, returns Xbar =
+ * dL/dX [(d+1)*d] and *cbar = dL/dcoef.  Per quadrature point, with s =
+ * |det J|, c = coef and the integrand I = sum Bbar_{i,(a,j)} phi_i g_j[a]:
+ *   gbar_j[a] += w s c sum_i Bbar_{i,(a,j)} phi_i,   sbar += w c I,   cbar += w s I
+ * and then, as in orc_element_vjp, with B = J^{-1}:
+ *   Bbar[mu][a] += sum_j gref_j[mu] gbar_j[a],   Jbar = -B^T Bbar B^T + sbar s B^T. */
+int orc_element_vjp_div(int dim, int vdeg, const double* X, double coef, int q, const double* Bbar_in, double* Xbar,
+                        double* cbar) {
+  int nq = dim + 1, nbv = orc_n_basis(dim, vdeg);
+  if (nbv < 0 || dim < 2 || dim > 3) return -1;
+  int ncol = dim * nbv, nv = dim + 1;
+  for (int k = 0; k < nv * dim; ++k) Xbar[k] = 0.0;
+  *cbar = 0.0;
+  double J[3][3], Jt[3][3];
+  jacobian(dim, X, J);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Jt[a][b] = J[b][a];
+  lu3 fJt;
+  lu_factor(dim, Jt, &fJt);
+  if (fJt.det == 0.0) return ORC_FLAG_DEGENERATE;
+  double s = fabs(fJt.det);
+  lu3 fJ;
+  lu_factor(dim, J, &fJ);
+  double Binv[3][3] = {{0}};
+  for (int k = 0; k < dim; ++k) {
+    double e[3] = {0, 0, 0};
+    e[k] = 1.0;
+    lu_solve(&fJ, e);
+    for (int r = 0; r < dim; ++r) Binv[r][k] = e[r];
+  }
+  double pts[ORC_MAXPTS * 3], wts[ORC_MAXPTS];
+  int np = orc_simplex_rule(dim, q, pts, wts);
+  if (np < 0) return -1;
+  double sbar = 0.0, Mbar[3][3] = {{0}};
+  for (int p = 0; p < np; ++p) {
+    double phi[ORC_MAXB], gphi[ORC_MAXB * 3], psi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3];
+    double gbar[ORC_MAXB][3];
+    orc_basis(dim, 1, pts + p * dim, phi, gphi);
+    orc_basis(dim, vdeg, pts + p * dim, psi, gref);
+    physical_gradients(dim, &fJt, nbv, gref, g);
+    memset(gbar, 0, sizeof(gbar));
+    double wq = wts[p], integrand = 0.0;
+    for (int i = 0; i < nq; ++i)
+      for (int a = 0; a < dim; ++a)
+        for (int j = 0; j < nbv; ++j) {
+          double bb = Bbar_in[i * ncol + a * nbv + j];
+          integrand += bb * phi[i] * g[j][a];
+          gbar[j][a] += wq * s * coef * bb * phi[i];
+        }
+    sbar += wq * coef * integrand;
+    *cbar += wq * s * integrand;
+    for (int j = 0; j < nbv; ++j)
+      for (int mu = 0; mu < dim; ++mu)
+        for (int a = 0; a < dim; ++a) Mbar[mu][a] += gref[j * dim + mu] * gbar[j][a];
+  }
+  double Jbar[3][3] = {{0}};
+  for (int a = 0; a < dim; ++a)
+    for (int mu = 0; mu < dim; ++mu) {
+      double acc = 0.0;
+      for (int k = 0; k < dim; ++k)
+        for (int l = 0; l < dim; ++l) acc += Binv[k][a] * Mbar[k][l] * Binv[mu][l];
+      Jbar[a][mu] = -acc + sbar * s * Binv[mu][a];
+    }
+  for (int a = 0; a < dim; ++a) {
+    double col = 0.0;
+    for (int mu = 0; mu < dim; ++mu) {
+      Xbar[(mu + 1) * dim + a] = Jbar[a][mu];
+      col += Jbar[a][mu];
+    }
+    Xbar[a] = -col;
+  }
+  return 0;
+}
+
+/* B[e] [(d+1)][d * nbv] for every element (coef may be NULL = 1); flags as in
+ * orc_integrate. */
+int orc_integrate_div(int dim, int vdeg, int64_t n_elem, int64_t n_vert, const int32_t* conn, const double* coords,
+                      const double* coef, int q, double* B, int32_t* flags, int nthreads) {
+  int nbv = orc_n_basis(dim, vdeg);
+  if (nbv < 0 || dim < 2 || dim > 3) return -1;
+  int64_t nb = (int64_t)(dim + 1) * dim * nbv;
+  int any = 0;
+  if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12];
+    double* Be = B + e * nb;
+    int f = gather(dim, n_vert, conn + e * (dim + 1), coords, X);
+    if (f == 0) {
+      f = orc_element_matrix_div(dim, vdeg, X, coef ? coef[e] : 1.0, q, Be, NULL);
+    } else {
+      memset(Be, 0, sizeof(double) * nb);
+    }
+    if (flags) flags[e] = f;
+    any |= f;
+  }
+  return any;
+}
+
+/* Reverse mode of orc_integrate_div over a mesh: Bbar [E][(d+1)][d * nbv] ->
+ * dcoords [V][d] (overwritten; per-vertex sums in element order) and dcoef
+ * [E] (may be NULL).  Flagged elements contribute nothing. */
+int orc_integrate_div_vjp(int dim, int vdeg, int64_t n_elem, int64_t n_vert, const int32_t* conn,
+                          const double* coords, const double* coef, int q, const double* Bbar, double* dcoords,
+                          double* dcoef, int nthreads) {
+  int nbv = orc_n_basis(dim, vdeg);
+  if (nbv < 0 || dim < 2 || dim > 3) return -1;
+  int64_t nb = (int64_t)(dim + 1) * dim * nbv;
+  int nv = dim + 1;
+  double* xbar = (double*)malloc(sizeof(double) * (size_t)(n_elem > 0 ? n_elem : 1) * nv * dim);
+  int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_elem > 0 ? n_elem : 1));
+  if (!xbar || !fl) {
+    free(xbar);
+    free(fl);
+    return -2;
+  }
+  if (nthreads < 1) nthreads = 1;
+  int any = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12], cb = 0.0;
+    double* xb = xbar + e * nv * dim;
+    int f = gather(dim, n_vert, conn + e * nv, coords, X);
+    if (f == 0) f = orc_element_vjp_div(dim, vdeg, X, coef ? coef[e] : 1.0, q, Bbar + e * nb, xb, &cb);
     if (f != 0) {
       for (int k = 0; k < nv * dim; ++k) xb[k] = 0.0;
       cb = 0.0;
