@@ -227,17 +227,18 @@ def tet_workload(n=128, k=2):
     return mesh, dA
 
 
-def algorithmic_bytes(E, V, R, n, dim, coef, saved_det=True):
+def algorithmic_bytes(E, V, R, n, dim, coef, saved_det=True, nn=None):
     """Bytes each kernel must move (every input read once, every output written
     once, vertex arrays once).  R = records of the deterministic reduction (one
     per distinct vertex of each 32-element tile).  saved_det: the forward
     writes det J (4 B per element) and the adjoint reads it."""
     nv = dim + 1
     sd = 4 if saved_det else 0
-    fwd = E * (4 * nv + 4 * n * n + (4 if coef else 0) + sd) + V * 4 * dim
+    nn = n * n if nn is None else nn  # entries of one element block (rows x cols)
+    fwd = E * (4 * nv + 4 * nn + (4 if coef else 0) + sd) + V * 4 * dim
     # dA, connectivity, the slot ranks (one 4-byte word per element); record
     # spans (2 B) and destinations (4 B) read, record sums (4 d B) written
-    bwd_elem = E * (4 * n * n + 4 * nv + 4 + (8 if coef else 0) + sd) + R * (2 + 4 + 4 * dim) + V * 4 * dim
+    bwd_elem = E * (4 * nn + 4 * nv + 4 + (8 if coef else 0) + sd) + R * (2 + 4 + 4 * dim) + V * 4 * dim
     # vertex-major record sums and the vertex offsets read, dcoords written
     reduce = R * 4 * dim + V * (4 + 4 * dim)
     return {"fwd": fwd, "bwd_elem": bwd_elem, "reduce": reduce}
@@ -426,9 +427,10 @@ def run_ours(args):
                         "GB/s": sum(byts.values()) / (ms_step * 1e-3) / 1e9,
                         "frac_of_peak": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / peak,
                         "frac_of_nominal": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
-        "setup": {"incidence_build_ms": setup_ms, "records": R, "slots": 4 * E},
+        "setup": {"incidence_build_ms": setup_ms, "records": R, "slots": 4 * E,
+                  "record_layout": {0: "vertex-major", 1: "tile order"}.get(ws.record_layout(), "?")},
         "e2e": e2e,
-        "gpu_launches": 3 * K,  # per K-step timed region (NCCL's all-reduce not counted)
+        "gpu_launches": 3 * K,  # per K-step timed region: forward, element pass, reduction
         "gpu_launches_all_repeats": 3 * K * m["repeats"],
         "clocks": m["clocks"],
         "kernel_src_hash": h,
@@ -843,10 +845,13 @@ def run_assemble(args):
 
 
 def run_multiphysics(args):
-    """Diagonal blocks of a coupled system on the 128^3 sliver cube: P1
-    elasticity (displacement), P1 Laplacian and P2 Laplacian (two scalar
-    fields), forward + adjoint, as three items of one tuned batched launch in a
-    CUDA graph, against the same blocks launched per form."""
+    """The blocks of a coupled thermo-elastic system on the 128^3 sliver cube
+    (Sec. 6: coupled systems broken into blocks): P1 elasticity for the
+    displacement u, the P1 Laplacian for the temperature T, their coupling
+    block int T div v (DIV_P1P1), and a second scalar field's P2 Laplacian;
+    forward + adjoint, as four items of one tuned batched launch in a CUDA
+    graph, against the same blocks launched per form.  The batch's outputs are
+    compared with the per-form ones bit for bit outside the timed regions."""
     import torch
 
     import __graft_entry__
@@ -861,11 +866,12 @@ def run_multiphysics(args):
     coef = torch.from_numpy(mg.lognormal_coef(mg.rng_for(3), E)).to(dev)
     gen = torch.Generator(device=dev).manual_seed(5)
     items, wss = [], []
-    for form in (fem.ELASTIC_P1, fem.LAPLACE_P1, fem.LAPLACE_P2):
-        n = mg.form_n(form, 3)
+    forms = (fem.ELASTIC_P1, fem.LAPLACE_P1, fem.DIV_P1P1, fem.LAPLACE_P2)
+    for form in forms:
+        rows, cols = fem.form_shape(form, 3)
         items.append({"coords": coords, "conn": conn, "form": form, "coef": coef,
-                      "A": torch.empty((E, n, n), device=dev),
-                      "dA": torch.randn((E, n, n), device=dev, generator=gen),
+                      "A": torch.empty((E, rows, cols), device=dev),
+                      "dA": torch.randn((E, rows, cols), device=dev, generator=gen),
                       "dcoords": torch.empty((V, 3), device=dev), "dcoef": torch.empty(E, device=dev)})
         wss.append(fem.Workspace(coords, conn, form))
     stream = torch.cuda.Stream(dev)
@@ -887,8 +893,13 @@ def run_multiphysics(args):
     with torch.cuda.stream(stream):
         re = timed(per_form)
         eager_ms = re["ms_per_step"]
+        torch.cuda.synchronize()
+        ref = [(it["A"].clone(), it["dcoords"].clone(), it["dcoef"].clone()) for it in items]
         bt = fem.Batch(items, stream=stream)
         cfg = bt.tune(stream=stream)
+        for it in items:
+            it["A"].fill_(float("nan"))
+            it["dcoords"].fill_(float("nan"))
         bt.run(stream=stream)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
@@ -897,31 +908,37 @@ def run_multiphysics(args):
         rb = timed(g.replay)
         batch_ms = rb["ms_per_step"]
         err = bt.errors(stream=stream)
+    bitwise = all(torch.equal(it["A"], a) and torch.equal(it["dcoords"], x) and torch.equal(it["dcoef"], w)
+                  for it, (a, x, w) in zip(items, ref))
     R = wss[0].n_records()  # the records depend on the connectivity only
     byts = 0
     for it in items:
-        b = algorithmic_bytes(E, V, R, int(it["A"].shape[1]), 3, True, saved_det=False)
+        rows, cols = it["A"].shape[1], it["A"].shape[2]
+        b = algorithmic_bytes(E, V, R, 0, 3, True, saved_det=False, nn=rows * cols)
         byts += b["fwd"] + b["bwd_elem"] + b["reduce"]
     peak, peak_kind = hbm_peak()
     gbs = byts / (batch_ms * 1e-3) / 1e9
-    out = {"metric": METRIC, "value": 3 * E / (batch_ms * 1e-3), "unit": "elements/s", "n_gpus": 1,
+    mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
+                  fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item",
+                  fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent"}
+    out = {"metric": METRIC, "value": len(items) * E / (batch_ms * 1e-3), "unit": "elements/s", "n_gpus": 1,
            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": batch_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": f"three diagonal blocks (P1 elasticity, P1 and P2 Laplacian) of a coupled system "
-                                  f"on the {args.mesh_n}^3 sliver cube ({E:,} tets), lognormal coefficient, forward + "
-                                  "adjoint, one tuned batched launch in a CUDA graph",
-                      "elements": E, "blocks": 3, "l2": "no flush"},
-           "roofline": {"bound": "hbm", "kernel": "fem_batch_kind_kernel", "achieved": gbs, "peak": peak,
-                        "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
+           "config": {"workload": f"four blocks of a coupled thermo-elastic system on the {args.mesh_n}^3 sliver "
+                                  f"cube ({E:,} tets): P1 elasticity, P1 Laplacian, the coupling block int T div v "
+                                  "(4 x 12), and a P2 Laplacian; lognormal coefficient, forward + adjoint, one "
+                                  "tuned batched launch in a CUDA graph",
+                      "elements": E, "blocks": len(items), "l2": "no flush"},
+           "roofline": {"bound": "hbm", "kernel": "per-item kernels of the tuned batch", "achieved": gbs,
+                        "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_kind": f"{peak_kind} copy bandwidth",
                         "traffic": None, "algorithmic_bytes": byts},
            "comparison_ms": {"per_form_eager": eager_ms, "batched_graph": batch_ms},
            "timing": {"repeats": rb["repeats"], "ms_per_step_min": rb["ms_min"], "ms_per_step_max": rb["ms_max"],
                       "statistic": "median over repeats of K-step timed regions"},
            "clocks": rb["clocks"], "per_form_clocks": re["clocks"],
-           "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": cfg[2]},
-           "device_errors": err,
-           "gpu_launches": args.steps * {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 9,
-                                         fem.BATCH_PER_ITEM_CONCURRENT: 9}.get(cfg[2], 3)}
+           "tuned_config": {"ctas_per_sm": cfg[0], "chunk": cfg[1], "mode": mode_names.get(cfg[2], cfg[2])},
+           "bitwise_equal_to_per_form": bitwise, "device_errors": err,
+           "gpu_launches": args.steps * 4 * len(items)}
     print(json.dumps(out), flush=True)
 
 

@@ -65,7 +65,18 @@ typedef enum {
   FEM_LAPLACE_P1_W1 = 3, /* int w grad v . grad u with w in P1 (Eqs. 20-23), P1 elements */
   FEM_LAPLACE_P2_W1 = 4, /* the same with P2 elements: K gains the coefficient's index (Eq. 21) */
   FEM_LAPLACE_P1_ISO = 5, /* the Laplacian on non-affine (quadratic-geometry) elements, Eqs. 16-19, P1 */
-  FEM_LAPLACE_P2_ISO = 6  /* the same with P2 elements (fem_integrate_fwd_iso only) */
+  FEM_LAPLACE_P2_ISO = 6, /* the same with P2 elements (fem_integrate_fwd_iso only) */
+  /* Coupling blocks of a multiphysics pair (Sec. 6: coupled systems broken
+   * into blocks): B_{i,(c,j)} = int_T w phi_i d psi_j / d x_c, i.e. int w q div v
+   * for a scalar field q in P1 and a vector field v.  Rows i = 0..d (the P1
+   * basis), columns c * nbv + j (the vector basis, component-major), so the
+   * element blocks are RECTANGULAR [n_elem][d+1][d * nbv] (fem_form_shape).
+   * G^{mu c} = w |J| J^{-1}_{mu c} and K^{ij}_mu = int_ref lambda_i d_mu psi_j
+   * (Eq. 1 with a value and a derivative).  FP32 coordinates and output, the
+   * compensated Jacobian (for the sign of det J) and the FP32 contraction;
+   * forward, fem_integrate_fwd_save and the adjoint (both reductions). */
+  FEM_DIV_P1P1 = 7, /* v in [P1]^d: 4 x 12 blocks on tets, 3 x 6 on triangles */
+  FEM_DIV_P2P1 = 8  /* v in [P2]^d (the Taylor-Hood pair): 4 x 30 on tets, 3 x 12 on triangles */
 } fem_form;
 
 typedef enum { FEM_F32 = 0, FEM_F64 = 1 } fem_dtype;
@@ -135,16 +146,24 @@ FEM_API const char* fem_last_error(void);
  * scale of fem_reference_tensor.  Any output pointer may be NULL. */
 FEM_API fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom, int32_t* den);
 
+/* Host.  Rows and columns of a form's element blocks: rows == cols == n for
+ * every form but the coupling forms (d+1 rows, d * nbv columns).  Either
+ * output may be NULL. */
+FEM_API fem_status fem_form_shape(int32_t form, int32_t dim, int32_t* rows, int32_t* cols);
+
 /* Host.  The reference tensor K of Eq. 7 (Eq. 14 with the symmetric gradient
  * for elasticity), folded over the symmetric G slots and scaled to exact
  * integers: K_host[g][i][j] = den * K'_g^{ij}, with A_e^{ij} = sum_g G_g K'_g^{ij}.
- * K_host: host int32 array of at least n_geom*n*n entries (cap = entries). */
+ * K_host: host int32 array of at least n_geom*rows*cols entries (cap =
+ * entries).  For the coupling forms g = mu * d + c (G_g = w |J| J^{-1}_{mu c},
+ * not folded) and K_host[g][i][c' * nbv + j] = den K^{ij}_mu when c' == c, else 0. */
 FEM_API fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K_host, size_t cap);
 
 /* Forward element integration, Sec. 4 / Eq. 6: A[e] = G_e : K for every element.
  *   coef : device FP32 [n_elem] per-element coefficient w_e, or NULL (w = 1);
  *          for the _W1 forms FP32 [n_vert] vertex values of the P1 coefficient
- *   A    : device [n_elem][n][n] of out_dtype (overwritten)
+ *   A    : device [n_elem][rows][cols] of out_dtype (overwritten); rows = cols = n
+ *          except for the coupling forms (fem_form_shape)
  *   FP64 output or FP64 coordinates compute the Jacobian steps in FP64.
  * Asynchronous on `stream`.  n_elem == 0 is a no-op. */
 FEM_API fem_status fem_integrate_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A,
@@ -198,6 +217,20 @@ FEM_API fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, co
  * it must precede fem_integrate_bwd with FEM_REDUCE_DETERMINISTIC. */
 FEM_API fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, void* stream);
 
+/* Record layouts of a built adjoint workspace (fem_incidence_info). */
+#define FEM_RECORDS_VERTEX_MAJOR 0 /* record rows grouped by vertex: the element pass writes each
+                                      record to its vertex's rows (elements in spatial order) */
+#define FEM_RECORDS_TILE_ORDER 1   /* records stay in tile order and the reduction gathers them
+                                      (elements or vertices in no spatial order) */
+
+/* Host query of a workspace built by fem_incidence_build (synchronizes
+ * `stream`): *n_records = the records of the deterministic reduction (one per
+ * distinct vertex of each 32-element tile) and *layout = the FEM_RECORDS_*
+ * layout the build chose from the mesh's locality (the result bits do not
+ * depend on it).  Either output may be NULL. */
+FEM_API fem_status fem_incidence_info(const fem_mesh* mesh, const void* ws, size_t ws_bytes, int64_t* n_records,
+                                      int32_t* layout, void* stream);
+
 /* Adjoint of fem_integrate_fwd (FP32 coordinates): for the upstream
  * dA = dL/dA (device FP32 [n_elem][n][n]) computes
  *   dcoords = dL/dcoords  (device FP32 [n_vert][dim], overwritten; may be NULL)
@@ -249,7 +282,11 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
  *                         streams (longest first, each to the least loaded;
  *                         event fork/join on `stream`, graph-capturable), so
  *                         small meshes run beside large ones
- * Every mode gives the same result bits as the per-mesh entry points. */
+ * Every mode gives the same result bits as the per-mesh entry points.
+ * Items may also be coupling blocks (FEM_DIV_P1P1, FEM_DIV_P2P1); a batch
+ * holding one runs the per-item modes only (fem_batch_set_config refuses the
+ * others with FEM_ERR_UNSUPPORTED; the tuner and the default pick among the
+ * per-item modes). */
 #define FEM_BATCH_SINGLE 0
 #define FEM_BATCH_GROUPED 1
 #define FEM_BATCH_GROUPED_CONCURRENT 2
@@ -268,8 +305,8 @@ typedef struct fem_batch_item {
   int32_t form;
   int32_t reserved; /* must be 0 */
   const float* coef; /* [n_elem] or NULL */
-  float* A;          /* [n_elem][n][n] */
-  const float* dA;   /* [n_elem][n][n] */
+  float* A;          /* [n_elem][rows][cols] (fem_form_shape) */
+  const float* dA;   /* [n_elem][rows][cols] */
   float* dcoords;    /* [n_vert][dim] (deterministic reduction) */
   float* dcoef;      /* [n_elem] */
 } fem_batch_item;

@@ -21,7 +21,7 @@ import torch
 from . import _native as nat
 from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENERATE, ELASTIC_P1, F32,
                       F64, JAC_AUTO, JAC_COMP_F32, JAC_F32, JAC_F64, LAPLACE_P1, LAPLACE_P2, LAPLACE_P1_W1, LAPLACE_P2_W1,
-                      LAPLACE_P1_ISO, LAPLACE_P2_ISO,
+                      LAPLACE_P1_ISO, LAPLACE_P2_ISO, DIV_P1P1, DIV_P2P1,
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM,
                       BATCH_PER_ITEM_CONCURRENT)
@@ -29,7 +29,8 @@ from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENER
 __all__ = ["Mesh", "Batch", "Assembly", "HostStep", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
            "BATCH_PER_ITEM", "BATCH_PER_ITEM_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
-           "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "integrate_fwd_iso", "JAC_AUTO",
+           "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "DIV_P1P1", "DIV_P2P1", "form_shape",
+           "integrate_fwd_iso", "JAC_AUTO",
            "JAC_F64", "JAC_COMP_F32", "JAC_F32", "CONTRACT_F32", "CONTRACT_BF16X3",
            "REDUCE_DETERMINISTIC", "REDUCE_ATOMIC", "REDUCE_DEFERRED", "adjoint_reduce", "DEVERR_CONN", "DEVERR_DEGENERATE", "F32", "F64"]
 
@@ -39,10 +40,17 @@ def form_info(form: int, dim: int):
     return nat.fem_form_info(form, dim)
 
 
+def form_shape(form: int, dim: int):
+    """(rows, cols) of the form's element blocks: (n, n), or (d+1, d * nbv) for
+    the coupling forms DIV_P1P1 / DIV_P2P1."""
+    return nat.fem_form_shape(form, dim)
+
+
 def reference_tensor(form: int, dim: int):
-    """Folded reference tensor K' * den as an int32 CPU tensor [n_geom][n][n] (host call)."""
-    n, ng, den = form_info(form, dim)
-    K = torch.empty((ng, n, n), dtype=torch.int32)
+    """Folded reference tensor K' * den as an int32 CPU tensor [n_geom][rows][cols] (host call)."""
+    _, ng, den = form_info(form, dim)
+    rows, cols = form_shape(form, dim)
+    K = torch.empty((ng, rows, cols), dtype=torch.int32)
     nat.fem_reference_tensor(form, dim, K.data_ptr(), K.numel())
     return K, den
 
@@ -81,13 +89,13 @@ def integrate_fwd(coords, conn, form, coef=None, out=None, out_dtype=torch.float
     det_out: optional float32 [E] tensor that receives det J for integrate_bwd(det=...)
     (fem_integrate_fwd_save)."""
     m = _mesh_struct(coords, conn)
-    n, _, _ = form_info(form, m.dim)
+    rows, cols = form_shape(form, m.dim)
     E = conn.shape[0]
     w1 = form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
     if out is None:
-        out = torch.empty((E, n, n), dtype=out_dtype, device=coords.device)
-    elif out.shape != (E, n, n) or not out.is_contiguous():
-        raise ValueError("out must be a contiguous [E][n][n] tensor")
+        out = torch.empty((E, rows, cols), dtype=out_dtype, device=coords.device)
+    elif out.shape != (E, rows, cols) or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous [E][{rows}][{cols}] tensor")
     od = F64 if out.dtype == torch.float64 else F32
     opts = nat.options_struct(jac, contract, 0, warps_per_cta, ctas_per_sm,
                               dev_err.data_ptr() if dev_err is not None else 0)
@@ -144,13 +152,16 @@ class Workspace:
         opts = nat.options_struct()
         self.bytes = nat.fem_bwd_workspace_size(self.m, form, opts)
         self.buf = torch.empty(max(self.bytes, 1), dtype=torch.uint8, device=coords.device)
+        self.stream = stream
         nat.fem_incidence_build(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(stream))
 
     def n_records(self) -> int:
-        """Records of the deterministic reduction: the first word past the
-        per-tile record offsets (32-element record tiles).  Synchronizes."""
-        T = (self.m.n_elem + 31) // 32
-        return int(self.buf[4 * T: 4 * T + 4].view(torch.int32).item())
+        """Records of the deterministic reduction (fem_incidence_info; synchronizes)."""
+        return nat.fem_incidence_info(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(self.stream))[0]
+
+    def record_layout(self) -> int:
+        """nat.RECORDS_VERTEX_MAJOR or nat.RECORDS_TILE_ORDER, as the build chose it."""
+        return nat.fem_incidence_info(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(self.stream))[1]
 
 
 class Assembly:
@@ -196,8 +207,8 @@ def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None
     det: det J saved by integrate_fwd(det_out=...) (fem_integrate_bwd_saved)."""
     m = _mesh_struct(coords, conn)
     E, V = conn.shape[0], coords.shape[0]
-    if dA.dtype != torch.float32 or not dA.is_contiguous():
-        raise ValueError("dA must be a contiguous float32 tensor")
+    if dA.dtype != torch.float32 or not dA.is_contiguous() or tuple(dA.shape) != (E,) + form_shape(form, m.dim):
+        raise ValueError("dA must be a contiguous float32 tensor shaped like the forward's output")
     if need_dcoords and dcoords is None:
         dcoords = torch.empty((V, m.dim), dtype=torch.float32, device=coords.device)
     if need_dcoef and dcoef is None:
@@ -323,7 +334,7 @@ class _IntegrateFn(torch.autograd.Function):
     def forward(ctx, coords, coef, mesh, form, jac, reduce, contract):
         # det J is kept for the adjoint when it can take it (FP32 coordinates, affine
         # form, FP32 contraction)
-        keep = (coords.dtype == torch.float32 and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1)
+        keep = (coords.dtype == torch.float32 and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, DIV_P1P1, DIV_P2P1)
                 and jac in (JAC_AUTO, JAC_COMP_F32) and contract == CONTRACT_F32)
         det = torch.empty(mesh.conn.shape[0], dtype=torch.float32, device=coords.device) if keep else None
         A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac, contract=contract, det_out=det)

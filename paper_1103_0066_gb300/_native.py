@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_PKG, "libfem_gb300.so")
 
 FEM_OK, FEM_ERR_ARG, FEM_ERR_UNSUPPORTED, FEM_ERR_WORKSPACE, FEM_ERR_CUDA = range(5)
 LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, LAPLACE_P1_W1, LAPLACE_P2_W1, LAPLACE_P1_ISO, LAPLACE_P2_ISO = range(7)
+DIV_P1P1, DIV_P2P1 = 7, 8
 F32, F64 = 0, 1
 JAC_AUTO, JAC_F64, JAC_COMP_F32, JAC_F32 = 0, 1, 2, 3
 CONTRACT_F32, CONTRACT_BF16X3 = 0, 1
@@ -22,9 +23,9 @@ REDUCE_DETERMINISTIC, REDUCE_ATOMIC, REDUCE_DEFERRED = 0, 1, 2
 DEVERR_CONN, DEVERR_DEGENERATE = 1, 2
 
 # every symbol include/fem.h declares
-EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info",
+EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info", "fem_form_shape",
            "fem_reference_tensor", "fem_integrate_fwd", "fem_geometry", "fem_bwd_workspace_size",
-           "fem_incidence_build", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
+           "fem_incidence_build", "fem_incidence_info", "fem_integrate_bwd", "fem_adjoint_reduce", "fem_integrate_bwd_noalloc",
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
@@ -32,6 +33,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
+RECORDS_VERTEX_MAJOR, RECORDS_TILE_ORDER = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
@@ -80,6 +82,7 @@ def load():
             "fem_status_string": ([ctypes.c_int], ctypes.c_char_p),
             "fem_last_error": ([], ctypes.c_char_p),
             "fem_form_info": ([I32, I32, P, P, P], ctypes.c_int),
+            "fem_form_shape": ([I32, I32, P, P], ctypes.c_int),
             "fem_reference_tensor": ([I32, I32, P, SZ], ctypes.c_int),
             "fem_integrate_fwd": ([MP, I32, P, P, I32, OP, P], ctypes.c_int),
             "fem_integrate_fwd_iso": ([MP, I32, P, P, P, OP, P], ctypes.c_int),
@@ -88,6 +91,7 @@ def load():
             "fem_geometry": ([MP, P, OP, P, P, P], ctypes.c_int),
             "fem_bwd_workspace_size": ([MP, I32, OP, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
+            "fem_incidence_info": ([MP, P, SZ, ctypes.POINTER(I64), ctypes.POINTER(I32), P], ctypes.c_int),
             "fem_integrate_bwd": ([MP, I32, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
             "fem_adjoint_reduce": ([MP, P, SZ, P, P], ctypes.c_int),
             "fem_integrate_bwd_noalloc": ([MP, I32, P, P, P, P, OP, P], ctypes.c_int),
@@ -146,6 +150,12 @@ def fem_form_info(form: int, dim: int):
     return n.value, ng.value, den.value
 
 
+def fem_form_shape(form: int, dim: int):
+    r, c = ctypes.c_int32(), ctypes.c_int32()
+    check(load().fem_form_shape(form, dim, ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
 def fem_reference_tensor(form: int, dim: int, out_ptr: int, cap: int) -> None:
     check(load().fem_reference_tensor(form, dim, out_ptr, cap))
 
@@ -182,6 +192,13 @@ def fem_bwd_workspace_size(mesh: FemMesh, form: int, opts: FemOptions) -> int:
 
 def fem_incidence_build(mesh: FemMesh, ws_ptr: int, ws_bytes: int, stream: int) -> None:
     check(load().fem_incidence_build(ctypes.byref(mesh), ws_ptr or None, ws_bytes, stream or None))
+
+
+def fem_incidence_info(mesh: FemMesh, ws_ptr: int, ws_bytes: int, stream: int):
+    n, lay = ctypes.c_int64(), ctypes.c_int32()
+    check(load().fem_incidence_info(ctypes.byref(mesh), ws_ptr or None, ws_bytes, ctypes.byref(n), ctypes.byref(lay),
+                                    stream or None))
+    return n.value, lay.value
 
 
 def fem_integrate_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, dcoords_ptr: int,

@@ -57,13 +57,21 @@ fem_status check_options(const fem_options* o) {
   return FEM_OK;
 }
 
+bool coupling(int form) { return form == FEM_DIV_P1P1 || form == FEM_DIV_P2P1; }
+
 int form_rows(int form, int dim) {
+  if (coupling(form)) return dim + 1;
   const bool p2 = form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1 || form == FEM_LAPLACE_P2_ISO;
   const int nb = p2 ? (dim + 1) * (dim + 2) / 2 : dim + 1;
   return nb * (form == FEM_ELASTIC_P1 ? dim : 1);
 }
 
-bool valid_form(int form) { return form >= FEM_LAPLACE_P1 && form <= FEM_LAPLACE_P2_ISO; }
+int form_cols(int form, int dim) {
+  if (!coupling(form)) return form_rows(form, dim);
+  return dim * (form == FEM_DIV_P2P1 ? (dim + 1) * (dim + 2) / 2 : dim + 1);
+}
+
+bool valid_form(int form) { return form >= FEM_LAPLACE_P1 && form <= FEM_DIV_P2P1; }
 bool coef_p1(int form) { return form == FEM_LAPLACE_P1_W1 || form == FEM_LAPLACE_P2_W1; }
 bool non_affine(int form) { return form == FEM_LAPLACE_P1_ISO || form == FEM_LAPLACE_P2_ISO; }
 
@@ -92,6 +100,20 @@ fem_status bwd_args(const fem_mesh* mesh, int32_t form, const fem_options* o, co
     return fail(FEM_ERR_ARG, "FEM_REDUCE_DEFERRED needs dcoords (written by fem_adjoint_reduce)");
   if (mesh->n_elem > 0 && !dA) return fail(FEM_ERR_ARG, "dA is NULL");
   return FEM_OK;
+}
+
+// K_host[g = mu * D + c][i][c' * NBV + j] = DEN K^{ij}_mu delta_{c c'}: the
+// coupling block as sum_g G_g K_g with G_{mu c} = w |J| J^{-1}_{mu c}.
+template <int D, int VDEG>
+void copy_div_ref(int32_t* K) {
+  using T = fem::DivTraits<D, VDEG>;
+  constexpr auto R = fem::make_div_ref<D, VDEG>();
+  for (int mu = 0; mu < D; ++mu)
+    for (int c = 0; c < D; ++c)
+      for (int i = 0; i < T::NQ; ++i)
+        for (int cc = 0; cc < D; ++cc)
+          for (int j = 0; j < T::NBV; ++j)
+            K[((mu * D + c) * T::NQ + i) * T::NCOL + cc * T::NBV + j] = cc == c ? R.v[mu][i][j] : 0;
 }
 
 template <int D, int FORM>
@@ -141,11 +163,19 @@ fem_status fem_form_info(int32_t form, int32_t dim, int32_t* n, int32_t* n_geom,
   if (dim != 2 && dim != 3) return fail(FEM_ERR_ARG, "dim must be 2 or 3");
   const int np = form == FEM_ELASTIC_P1 ? dim * dim : non_affine(form) ? (dim + 1) * dim : dim;
   if (n) *n = form_rows(form, dim);
-  if (n_geom) *n_geom = np * (np + 1) / 2 * (coef_p1(form) ? dim + 1 : 1);
+  if (n_geom) *n_geom = coupling(form) ? dim * dim : np * (np + 1) / 2 * (coef_p1(form) ? dim + 1 : 1);
   if (den)
     *den = non_affine(form) ? (dim == 2 ? 720 : 5040)
            : coef_p1(form)  ? (dim == 2 ? 120 : 720)
-                            : (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);
+                            : (dim == 2 ? 24 : 120) * (form == FEM_ELASTIC_P1 ? 2 : 1);  // coupling: (d+2)!
+  return ok();
+}
+
+fem_status fem_form_shape(int32_t form, int32_t dim, int32_t* rows, int32_t* cols) {
+  fem_status s = fem_form_info(form, dim, nullptr, nullptr, nullptr);
+  if (s != FEM_OK) return s;
+  if (rows) *rows = form_rows(form, dim);
+  if (cols) *cols = form_cols(form, dim);
   return ok();
 }
 
@@ -154,7 +184,15 @@ fem_status fem_reference_tensor(int32_t form, int32_t dim, int32_t* K, size_t ca
   fem_status s = fem_form_info(form, dim, &n, &ng, nullptr);
   if (s != FEM_OK) return s;
   if (!K) return fail(FEM_ERR_ARG, "K is NULL");
-  if (cap < size_t(ng) * n * n) return fail(FEM_ERR_ARG, "K capacity %zu < %d", cap, ng * n * n);
+  const int nc = form_cols(form, dim);
+  if (cap < size_t(ng) * n * nc) return fail(FEM_ERR_ARG, "K capacity %zu < %d", cap, ng * n * nc);
+  if (coupling(form)) {
+    if (dim == 2)
+      form == FEM_DIV_P1P1 ? copy_div_ref<2, 1>(K) : copy_div_ref<2, 2>(K);
+    else
+      form == FEM_DIV_P1P1 ? copy_div_ref<3, 1>(K) : copy_div_ref<3, 2>(K);
+    return ok();
+  }
   if (dim == 2) {
     if (form == FEM_LAPLACE_P1) copy_ref<2, fem::LAPLACE_P1>(K);
     if (form == FEM_LAPLACE_P2) copy_ref<2, fem::LAPLACE_P2>(K);
@@ -190,6 +228,10 @@ static fem_status integrate_fwd(const fem_mesh* mesh, int32_t form, const float*
   if ((cf64 || of64) && o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F64)
     return fail(FEM_ERR_UNSUPPORTED, "FP64 coordinates or FP64 output need FEM_JAC_F64");
   const bool tc = o->contract == FEM_CONTRACT_BF16X3;
+  if (coupling(form) && (cf64 || of64 || tc || (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
+    return fail(FEM_ERR_UNSUPPORTED,
+                "the coupling forms take FP32 coordinates and output, the compensated Jacobian and the FP32 "
+                "contraction");
   if (tc && (form == FEM_LAPLACE_P1 || form == FEM_LAPLACE_P1_W1 || cf64 || of64 ||
              (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32)))
     return fail(FEM_ERR_UNSUPPORTED,
@@ -213,7 +255,9 @@ static fem_status integrate_fwd(const fem_mesh* mesh, int32_t form, const float*
   L.stream = static_cast<cudaStream_t>(stream);
   L.det_out = det_out;
   cudaError_t e;
-  if (tc)
+  if (coupling(form))
+    e = fem::launch_div_fwd(L);
+  else if (tc)
     e = fem::launch_fwd_tc(L);
   else if (coef_p1(form))
     e = fem::launch_fwd_w1(L);
@@ -337,6 +381,25 @@ fem_status fem_incidence_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, 
   return ok();
 }
 
+fem_status fem_incidence_info(const fem_mesh* mesh, const void* ws, size_t ws_bytes, int64_t* n_records,
+                              int32_t* layout, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  fem::BwdWorkspace W{};
+  const size_t need =
+      fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, const_cast<void*>(ws), &W);
+  if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+  int32_t h[2] = {0, 0};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(&h[0], W.tile_rec + W.n_tiles, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h[1], W.mode, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "fem_incidence_info");
+  if (n_records) *n_records = h[0];
+  if (layout) *layout = h[1];
+  return ok();
+}
+
 static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
                                 const float* det_in, float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
                                 const fem_options* options, void* stream) {
@@ -382,7 +445,7 @@ static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float*
     L.ctas_per_sm = o->ctas_per_sm;
     L.stream = st;
     L.det_in = det_in;
-    e = fem::launch_bwd_elem(L);
+    e = coupling(form) ? fem::launch_div_bwd(L) : fem::launch_bwd_elem(L);
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd element launch");
   }
   if (dcoords && o->reduce == FEM_REDUCE_DETERMINISTIC) {

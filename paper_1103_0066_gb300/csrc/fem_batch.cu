@@ -52,7 +52,9 @@ struct BatchMesh {
   const uint16_t* rec_span;
   const int32_t* rec_dest;
   const int32_t* voff;
-  float* records;  // vertex-major
+  const int32_t* vrec;  // records of each vertex (tile-order layout)
+  const int32_t* rec_mode;  // record layout (kRecVertexMajor or kRecTileOrder)
+  float* records;
   int64_t tile_begin, n_tiles;  // element tiles of this mesh in the item space (all meshes)
   int64_t wait_tiles;           // tiles counted done before the mesh's reduction items run (= n_tiles)
   int64_t red_begin, n_red;     // reduction items (all meshes)
@@ -196,14 +198,16 @@ template <int D>
 __device__ void batch_reduce(const BatchMesh& M, int64_t r) {
   const int64_t v0 = r * kRedVerts;
   const int64_t v1 = v0 + kRedVerts < M.n_vert ? v0 + kRedVerts : M.n_vert;
+  const bool gather = __ldg(M.rec_mode) == kRecTileOrder;
   for (int64_t v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
     const int32_t b = M.voff[v], e = M.voff[v + 1];
     float acc[D];
 #pragma unroll
     for (int a = 0; a < D; ++a) acc[a] = 0.f;
     for (int32_t k = b; k < e; ++k) {
+      const int64_t row = gather ? M.vrec[k] : k;  // same increasing record order either way
 #pragma unroll
-      for (int a = 0; a < D; ++a) acc[a] += __ldcg(M.records + int64_t(k) * D + a);
+      for (int a = 0; a < D; ++a) acc[a] += __ldcg(M.records + row * D + a);
     }
 #pragma unroll
     for (int a = 0; a < D; ++a) M.dcoords[v * D + a] = acc[a];
@@ -506,6 +510,7 @@ struct fem_batch {
   int64_t n_tile_items = 0, n_total_fwd = 0, n_total = 0;
   size_t stage_bytes = 0, smem = 0;
   int ctas_per_sm = 0, chunk = 1, max_ctas_per_sm = 1, mode = FEM_BATCH_SINGLE;
+  bool has_coupling = false;  // a coupling-block item: the per-item modes only
   uint32_t spin_limit = fem::kSpinLimit;  // bound of the reduction items' waits (fem_batch_inject_wait)
   struct Group {
     int kind, first, count;
@@ -553,7 +558,9 @@ fem_status check_items(const fem_batch_item* items, int32_t n) {
       fem::set_last_error("batch item %d: invalid mesh (dim 2/3, FP32 coordinates, non-NULL arrays)", i);
       return FEM_ERR_ARG;
     }
-    if (it.form < FEM_LAPLACE_P1 || it.form > FEM_ELASTIC_P1 || it.reserved != 0) {
+    const bool form_ok = (it.form >= FEM_LAPLACE_P1 && it.form <= FEM_ELASTIC_P1) || it.form == FEM_DIV_P1P1 ||
+                         it.form == FEM_DIV_P2P1;
+    if (!form_ok || it.reserved != 0) {
       fem::set_last_error("batch item %d: invalid form or reserved field", i);
       return FEM_ERR_ARG;
     }
@@ -647,8 +654,11 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st0, bool con
       L.warps = 0;  // the kernel's default
       L.stream = st;
       L.det_out = det;
-      e = L.dim == 2 ? fem::launch_fwd_d2(L)
-                     : (it.form == FEM_ELASTIC_P1 ? fem::launch_fwd_d3_ela(L) : fem::launch_fwd_d3_lap(L));
+      if (it.form == FEM_DIV_P1P1 || it.form == FEM_DIV_P2P1)
+        e = fem::launch_div_fwd(L);
+      else
+        e = L.dim == 2 ? fem::launch_fwd_d2(L)
+                       : (it.form == FEM_ELASTIC_P1 ? fem::launch_fwd_d3_ela(L) : fem::launch_fwd_d3_lap(L));
     }
     if (e == cudaSuccess && (phases & FEM_PHASE_BWD) && (M.flags & fem::BM_BWD)) {
       const bool rec = (M.flags & fem::BM_REC) != 0;
@@ -674,7 +684,7 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st0, bool con
       L.dev_err = &b->d_ctr->err;
       L.stream = st;
       L.det_in = det;
-      e = fem::launch_bwd_elem(L);
+      e = (it.form == FEM_DIV_P1P1 || it.form == FEM_DIV_P2P1) ? fem::launch_div_bwd(L) : fem::launch_bwd_elem(L);
       if (e == cudaSuccess && rec) e = fem::launch_vertex_reduce(it.mesh.dim, W, M.n_vert, it.dcoords, st);
     }
   }
@@ -778,7 +788,11 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
     const fem_batch_item& it = items[i];
     fem::BatchMesh& M = b->desc[size_t(i)];
     std::memset(&M, 0, sizeof(M));
-    M.kind = (it.mesh.dim - 2) * 3 + it.form;
+    // the persistent kernels serve the six square (dim, form) kinds; a coupling
+    // block (kind -1) runs through the per-item modes only
+    const bool cpl = it.form == FEM_DIV_P1P1 || it.form == FEM_DIV_P2P1;
+    M.kind = cpl ? -1 : (it.mesh.dim - 2) * 3 + it.form;
+    b->has_coupling |= cpl;
     M.n_elem = it.mesh.n_elem;
     M.n_vert = it.mesh.n_vert;
     M.conn = it.mesh.conn;
@@ -794,7 +808,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
     M.wait_tiles = M.n_tiles;
     M.tile_begin = tiles;
     tiles += M.n_tiles;
-    stage = std::max(stage, fem::stage_bytes_for_kind(M.kind));
+    if (!cpl) stage = std::max(stage, fem::stage_bytes_for_kind(M.kind));
     const size_t wsb = item_ws_bytes(it);
     if (wsb) {
       fem::BwdWorkspace W{};
@@ -811,6 +825,8 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
       M.rec_span = W.rec_span;
       M.rec_dest = W.rec_dest;
       M.voff = W.voff;
+      M.vrec = W.vrec;
+      M.rec_mode = W.mode;
       M.records = W.records;
       off += al256(wsb);
     }
@@ -873,10 +889,16 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
     std::vector<double> work(static_cast<size_t>(n_items)), load(static_cast<size_t>(b->n_lanes), 0.0);
     for (int i = 0; i < n_items; ++i) {
       order[size_t(i)] = i;
-      const int nv = items[i].mesh.dim + 1;
-      const int n = items[i].form == FEM_LAPLACE_P1 ? nv
-                    : items[i].form == FEM_LAPLACE_P2 ? nv * (nv + 1) / 2 : (nv - 1) * nv;
-      work[size_t(i)] = double(items[i].mesh.n_elem) * double(n * n + 8);
+      const int nv = items[i].mesh.dim + 1, d = nv - 1;
+      int nn = 0;  // entries of one element block
+      switch (items[i].form) {
+        case FEM_LAPLACE_P1: nn = nv * nv; break;
+        case FEM_LAPLACE_P2: nn = (nv * (nv + 1) / 2) * (nv * (nv + 1) / 2); break;
+        case FEM_ELASTIC_P1: nn = d * nv * d * nv; break;
+        case FEM_DIV_P1P1: nn = nv * d * nv; break;
+        default: nn = nv * d * (nv * (nv + 1) / 2); break;
+      }
+      work[size_t(i)] = double(items[i].mesh.n_elem) * double(nn + 8);
     }
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[size_t(x)] > work[size_t(y)]; });
     b->item_lane.assign(size_t(n_items), 0);
@@ -910,7 +932,8 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   for (const auto& g : b->groups) b->max_ctas_per_sm = std::max(b->max_ctas_per_sm, g.occ);
   b->ctas_per_sm = b->max_ctas_per_sm;
   b->chunk = 1;
-  b->mode = b->groups.empty() ? FEM_BATCH_SINGLE : FEM_BATCH_GROUPED;
+  b->mode = b->has_coupling ? FEM_BATCH_PER_ITEM_CONCURRENT
+            : b->groups.empty() ? FEM_BATCH_SINGLE : FEM_BATCH_GROUPED;
   *out = b;
   return FEM_OK;
 }
@@ -947,6 +970,7 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
     const bool grouped = mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT;
     const bool per_item = mode == FEM_BATCH_PER_ITEM || mode == FEM_BATCH_PER_ITEM_CONCURRENT;
     if (grouped && b->groups.empty()) continue;
+    if (!per_item && b->has_coupling) continue;  // the persistent kernels serve the square kinds
     const int c_hi = per_item ? 1 : b->max_ctas_per_sm;  // per item: no grid or chunk to tune
     for (int c = 1; c <= c_hi && err == cudaSuccess; ++c)
       for (int k : chunks) {
@@ -999,6 +1023,10 @@ fem_status fem_batch_set_config(fem_batch* b, int32_t ctas_per_sm, int32_t chunk
     fem::set_last_error("fem_batch_set_config: bad batch or configuration (ctas_per_sm 1..32, chunk 1..64, "
                         "mode FEM_BATCH_*)");
     return FEM_ERR_ARG;
+  }
+  if (b->has_coupling && mode != FEM_BATCH_PER_ITEM && mode != FEM_BATCH_PER_ITEM_CONCURRENT) {
+    fem::set_last_error("fem_batch_set_config: a batch with a coupling-block item runs the per-item modes only");
+    return FEM_ERR_UNSUPPORTED;
   }
   if ((mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT) && b->groups.empty())
     mode = FEM_BATCH_SINGLE;

@@ -64,8 +64,8 @@ struct BwdParams {
   const int32_t* tile_rec;  // first record of each 32-element tile (null: no coordinate records)
   const uint32_t* rank;     // per element: byte k = stage position of slot k (runs in (vertex, slot) order)
   const uint16_t* rec_span; // per record: start | length << 8 of its run in the stage
-  const int32_t* rec_dest;  // per record: its row in the vertex-major records array
-  float* records;           // [R][D], vertex-major
+  const int32_t* rec_dest;  // per record: its row in the records array (the identity in tile order)
+  float* records;           // [R][D]
   float* dcoef;
   float* dcoords;  // atomic mode
   int64_t n_elem;

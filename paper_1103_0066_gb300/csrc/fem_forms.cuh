@@ -53,7 +53,9 @@ enum FormId : int {
   LAPLACE_P1_W1 = 3,
   LAPLACE_P2_W1 = 4,
   LAPLACE_P1_ISO = 5,
-  LAPLACE_P2_ISO = 6
+  LAPLACE_P2_ISO = 6,
+  DIV_P1P1 = 7,  // coupling block int q div v, q in P1, v in [P1]^d
+  DIV_P2P1 = 8   // the same with v in [P2]^d (the Taylor-Hood pair)
 };
 
 template <int D, int FORM>
@@ -255,6 +257,50 @@ constexpr RefTensor<D, FORM> make_ref_tensor() {
 template <int D, int FORM>
 struct Ref {
   static constexpr RefTensor<D, FORM> K = make_ref_tensor<D, FORM>();
+};
+
+// ---------------------------------------------------------------- coupling blocks
+// The off-diagonal block of a multiphysics pair (a scalar field q in P1 and a
+// vector field v in [P_VDEG]^d), B = int w q div v:
+//   B_{i,(c,j)} = int_T w phi_i d psi_j / d x_c = sum_mu G^{mu c} K^{ij}_mu
+//   G^{mu c}    = w |J| J^{-1}_{mu c} = w sgn(det J) adj(J)_{mu c}
+//   K^{ij}_mu   = int_ref lambda_i d_mu psi_j
+// (Eq. 1 with one basis-function value and one derivative in K, as Sec. 3.1
+// allows for any multilinear form).  Rows i = 0..d, columns c * NBV + j
+// (component-major).  G needs no division by det J: only its sign.  K is
+// stored scaled by DEN = (d+2)! as exact integers.
+template <int D, int VDEG>
+struct DivTraits {
+  static_assert(D == 2 || D == 3, "dimension");
+  static constexpr int NQ = D + 1;                                    // rows (P1 scalar basis)
+  static constexpr int NBV = VDEG == 1 ? D + 1 : (D + 1) * (D + 2) / 2;  // basis of one component
+  static constexpr int NCOL = D * NBV;
+  static constexpr int NN = NQ * NCOL;
+  static constexpr int NG = D * D;                                    // G slots g = mu * D + c
+  static constexpr int DEN = D == 2 ? 24 : 120;
+};
+
+template <int D, int VDEG>
+struct DivRefTensor {
+  int v[D][D + 1][DivTraits<D, VDEG>::NBV];  // K^{ij}_mu * DEN
+};
+
+template <int D, int VDEG>
+constexpr DivRefTensor<D, VDEG> make_div_ref() {
+  DivRefTensor<D, VDEG> r{};
+  for (int mu = 0; mu < D; ++mu)
+    for (int i = 0; i <= D; ++i) {
+      Lin li{0, {0, 0, 0, 0}};
+      li.c[i] = 1;
+      for (int j = 0; j < DivTraits<D, VDEG>::NBV; ++j)
+        r.v[mu][i][j] = integrate_lin_lin<D>(li, basis_deriv<D, VDEG>(j, mu));
+    }
+  return r;
+}
+
+template <int D, int VDEG>
+struct DivRef {
+  static constexpr DivRefTensor<D, VDEG> K = make_div_ref<D, VDEG>();
 };
 
 }  // namespace fem

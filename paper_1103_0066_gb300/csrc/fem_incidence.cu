@@ -338,13 +338,55 @@ __global__ void dest_kernel(const int32_t* voff, int64_t n_vert, const int32_t* 
     rec_dest[vrec[k]] = int32_t(k);
 }
 
+// Locality of the vertex-major layout: counts the records whose vertex-major
+// row lies within kNearRows rows of the previous record's (record r - 1 of
+// the same tile).  When most records are near, the element pass's record
+// writes land in a few neighbouring sectors per tile; otherwise (elements in
+// no spatial order, or vertices numbered at random) they scatter over the
+// whole record array and every write is a partial-sector update.
+constexpr int32_t kNearRows = 64;
+
+__global__ void locality_kernel(const int32_t* tile_rec, int64_t n_tiles, const int32_t* rec_dest, int32_t* near) {
+  int32_t c = 0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n_tiles; t += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t rb = tile_rec[t], re = tile_rec[t + 1];
+    for (int32_t r = rb + 1; r < re; ++r) {
+      const int32_t d = rec_dest[r] - rec_dest[r - 1];
+      c += (d >= -kNearRows && d <= kNearRows) ? 1 : 0;
+    }
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(near, c);
+}
+
+// The layout decision, on the device: vertex-major when at least half of the
+// records (beyond each tile's first) are near their predecessor, else tile
+// order with rec_dest[r] = r.
+__global__ void choose_layout_kernel(const int32_t* tile_rec, int64_t n_tiles, const int32_t* near, int32_t* mode,
+                                     int32_t* rec_dest) {
+  const int32_t R = tile_rec[n_tiles];
+  const int32_t pairs = R - int32_t(n_tiles);
+  const int32_t m = (2 * int64_t(*near) >= int64_t(pairs)) ? kRecVertexMajor : kRecTileOrder;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *mode = m;
+  if (m == kRecTileOrder)
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < R; r += int64_t(gridDim.x) * blockDim.x)
+      rec_dest[r] = int32_t(r);
+}
+
 // dcoords[v] = sum of the records of v (a contiguous run of the vertex-major
 // record array) in increasing record order.  The records come in blocks of 8
 // predicated loads, all in flight before the block's additions (a vertex has
 // a handful of records: one block, one round trip).
+// dcoords[v] = the sum of the records of v in increasing record order.
+// Vertex-major layout: they are rows [voff[v], voff[v+1]), read in blocks of
+// 8 predicated loads, all in flight before the block's additions (a vertex
+// has a handful of records: one block, one round trip).  Tile-order layout:
+// they are rows vrec[voff[v] .. voff[v+1]) -- the same order, so the same
+// bits -- read as four indices, then four records, per step.  The layout word
+// is read once; the branch is uniform over the grid.
 template <int D>
-__global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const float* __restrict__ records,
-                                     int64_t n_vert, float* __restrict__ dcoords) {
+__device__ __forceinline__ void reduce_direct(const int32_t* __restrict__ voff, const float* __restrict__ records,
+                                              int64_t n_vert, float* __restrict__ dcoords) {
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
     const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
@@ -366,6 +408,46 @@ __global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const flo
 #pragma unroll
     for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
   }
+}
+
+template <int D>
+__device__ __forceinline__ void reduce_gather(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
+                                              const float* __restrict__ records, int64_t n_vert,
+                                              float* __restrict__ dcoords) {
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
+       v += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
+    float acc[D];
+#pragma unroll
+    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int32_t k0 = b; k0 < e; k0 += 4) {
+      int32_t row[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) row[u] = k0 + u < e ? __ldg(vrec + k0 + u) : 0;
+      float r[4][D];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int a = 0; a < D; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(row[u]) * D + a) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k0 + u < e)
+#pragma unroll
+          for (int a = 0; a < D; ++a) acc[a] += r[u][a];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
+  }
+}
+
+template <int D>
+__global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
+                                     const int32_t* __restrict__ mode, const float* __restrict__ records,
+                                     int64_t n_vert, float* __restrict__ dcoords) {
+  if (__ldg(mode) == kRecTileOrder)
+    reduce_gather<D>(voff, vrec, records, n_vert, dcoords);
+  else
+    reduce_direct<D>(voff, records, n_vert, dcoords);
 }
 
 unsigned grid_for(int64_t n, int block) {
@@ -409,6 +491,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   const size_t o_vrec = take(sizeof(int32_t) * size_t(r_max));
   const size_t o_cursor = take(sizeof(int32_t) * size_t(n_cnt + 1));
   const size_t o_part = take(sizeof(int32_t) * size_t(nb + 1));
+  const size_t o_mode = take(sizeof(int32_t) * 2);  // layout word, locality count
   const size_t o_records = with_scratch ? take(sizeof(float) * size_t(r_max * dim)) : off;
   if (ws) {
     char* b = static_cast<char*>(base);
@@ -421,6 +504,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
     ws->vrec = reinterpret_cast<int32_t*>(b + o_vrec);
     ws->cursor = reinterpret_cast<int32_t*>(b + o_cursor);
     ws->partials = reinterpret_cast<int32_t*>(b + o_part);
+    ws->mode = reinterpret_cast<int32_t*>(b + o_mode);
     ws->records = with_scratch ? reinterpret_cast<float*>(b + o_records) : nullptr;
     ws->n_tiles = n_tiles;
     ws->bytes = off;
@@ -465,6 +549,11 @@ cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem,
   // vertex -> records CSR
   launch_key_csr(ws.rec_vertex, r_max, n_vert, ws.voff, ws.vrec, ws.cursor, ws.partials, stream);
   dest_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.voff, n_vert, ws.vrec, ws.rec_dest);
+  // record layout: vertex-major rows when the writes keep their locality, else tile order
+  fill_i32<<<1, 32, 0, stream>>>(ws.mode + 1, 1, 0);
+  locality_kernel<<<grid_for(n_tiles, 256), 256, 0, stream>>>(ws.tile_rec, n_tiles, ws.rec_dest, ws.mode + 1);
+  choose_layout_kernel<<<grid_for(r_max, 256), 256, 0, stream>>>(ws.tile_rec, n_tiles, ws.mode + 1, ws.mode,
+                                                                   ws.rec_dest);
   return cudaGetLastError();
 }
 
@@ -480,9 +569,11 @@ cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert
   const int block = 256;
   const int64_t g = (n_vert + block - 1) / block;
   if (dim == 2)
-    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.records, n_vert, dcoords);
+    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert,
+                                                                dcoords);
   else
-    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.records, n_vert, dcoords);
+    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert,
+                                                                dcoords);
   return cudaGetLastError();
 }
 

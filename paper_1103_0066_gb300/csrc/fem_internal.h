@@ -67,7 +67,7 @@ struct BwdLaunch {
 
 // Workspace of the deterministic adjoint (see fem_incidence.cu):
 // [tile_rec T+1][rank T*32 u32][rec_span R u16][rec_dest R][rec_vertex R][voff V+1]
-// [vrec R][cursor][scan partials][records R*d]   with T = ceil(E/32) record
+// [vrec R][cursor][scan partials][mode][records R*d]   with T = ceil(E/32) record
 // tiles and R <= E*(d+1) records; records are stored vertex-major (record r at
 // rec_dest[r]), so the records of vertex v are records[voff[v], voff[v+1]).
 struct BwdWorkspace {
@@ -80,10 +80,19 @@ struct BwdWorkspace {
   int32_t* vrec;
   int32_t* cursor;
   int32_t* partials;
+  int32_t* mode;  // record layout chosen by the build: kRecVertexMajor or kRecTileOrder (one word)
   float* records;
   int64_t n_tiles;
   size_t bytes;
 };
+// Record layouts.  Vertex-major: record r is row rec_dest[r], the rows of
+// vertex v are [voff[v], voff[v+1]) and the reduction reads them in place.
+// Tile order (rec_dest[r] = r): the element pass writes each tile's records
+// contiguously and the reduction gathers the records of vertex v through
+// vrec[voff[v] .. voff[v+1]).  Both sum a vertex's records in increasing
+// record order, so dcoords has the same bits either way.
+constexpr int32_t kRecVertexMajor = 0;
+constexpr int32_t kRecTileOrder = 1;
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
                             BwdWorkspace* ws);
 
@@ -96,6 +105,9 @@ cudaError_t launch_fwd_iso(const FwdLaunch& L, const float* mid);  // non-affine
 // The P2 non-affine forward with the tensor-core contraction (fem_tc_iso.cu).
 cudaError_t launch_fwd_iso_tc(const FwdLaunch& L, const float* mid);
 cudaError_t launch_geometry(const GeoLaunch& L);
+// The coupling blocks int w q div v (fem_coupling.cu): forward and adjoint element pass.
+cudaError_t launch_div_fwd(const FwdLaunch& L);
+cudaError_t launch_div_bwd(const BwdLaunch& L);
 cudaError_t launch_bwd_elem(const BwdLaunch& L);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream);

@@ -136,6 +136,33 @@ def test_reference_tensor_reproduces_quadrature(fem, orc, dim, form):
         assert int((K != 0).sum()) == 513
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("vdeg", [1, 2])
+def test_coupling_shape_and_reference_tensor(fem, orc, dim, vdeg):
+    """The coupling blocks int q div v: fem_form_shape gives (d+1, d * nbv), and
+    B = sum_g G_g K_g / den with G_{mu c} = |J| J^{-1}_{mu c} (numpy) and the
+    library's K equals the oracle's direct quadrature."""
+    form = 6 + vdeg
+    nbv = dim + 1 if vdeg == 1 else (dim + 1) * (dim + 2) // 2
+    assert fem.form_shape(form, dim) == (dim + 1, dim * nbv) == orc.div_shape(dim, vdeg)
+    assert fem.form_shape(LP2, dim) == (fem.form_info(LP2, dim)[0],) * 2
+    n, ng, den = fem.form_info(form, dim)
+    assert (n, ng, den) == (dim + 1, dim * dim, 24 if dim == 2 else 120)
+    K, den = fem.reference_tensor(form, dim)
+    K = K.numpy().astype(np.float64)
+    assert K.shape == (dim * dim, dim + 1, dim * nbv)
+    rng = np.random.default_rng(13)
+    for trial in range(8):
+        X = rng.standard_normal((dim + 1, dim)) if trial else np.vstack([np.zeros(dim), np.eye(dim)])
+        J = (X[1:] - X[0]).T
+        if abs(np.linalg.det(J)) < 0.05:
+            continue
+        G = (abs(np.linalg.det(J)) * np.linalg.inv(J)).ravel()      # g = mu * d + c
+        B = np.einsum("g,gij->ij", G, K) / den
+        Br, _, _ = orc.element_matrix_div(dim, vdeg, X)
+        assert np.abs(B - Br).max() < 1e-12 * np.abs(Br).max()
+
+
 def _mesh(fem, dim=3, dtype=0, n_elem=10, conn=0x1000, coords=0x2000):
     return fem.nat.mesh_struct(dim, dtype, 100, n_elem, conn, coords)
 
@@ -152,7 +179,7 @@ def test_host_detected_errors(fem):
     m = _mesh(fem, dim=4)
     assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
     m = _mesh(fem)
-    assert lib.fem_integrate_fwd(ctypes.byref(m), 7, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
+    assert lib.fem_integrate_fwd(ctypes.byref(m), 9, None, A, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
     assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, A, 5, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
     # NULL output / NULL conn with elements
     assert lib.fem_integrate_fwd(ctypes.byref(m), LP1, None, None, 0, ctypes.byref(opts), None) == nat.FEM_ERR_ARG
@@ -178,7 +205,7 @@ def test_host_detected_errors(fem):
     assert lib.fem_bwd_workspace_size(ctypes.byref(m), LP1, None, ctypes.byref(b)) == nat.FEM_OK
     assert b.value >= 4 * (101 + 40) + 4 * 10 * 4 * 3
     with pytest.raises(fem.FemError):
-        fem.nat.fem_form_info(7, 3)
+        fem.nat.fem_form_info(9, 3)
 
 
 def test_tensor_core_combinations_rejected_on_host(fem):

@@ -122,6 +122,8 @@ def test_tile_records_structure(gfem):
             rec_vtx[rb: rb + rn] = u
         assert (n_padded > 0) == (dim == 3)
         assert np.array_equal(np.diff(voff), np.bincount(rec_vtx, minlength=mesh.n_vert))
+        n_rec, layout = gfem.nat.fem_incidence_info(ws.m, ws.buf.data_ptr(), ws.bytes, 0)
+        assert n_rec == R and layout == gfem.nat.RECORDS_VERTEX_MAJOR   # cell-major meshes keep their locality
         order = np.argsort(rec_dest)                                 # record stored at each row
         assert np.array_equal(rec_vtx[order], np.repeat(np.arange(mesh.n_vert), np.diff(voff)))
         for v in range(mesh.n_vert):                                  # record order within a vertex

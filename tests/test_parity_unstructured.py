@@ -120,6 +120,61 @@ def test_adjoint_unstructured(gfem, orc, dim, form):
     assert det_x is not None
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tile_order_records_parity(gfem, orc, dim):
+    """A shuffled mesh large enough that the vertex-major record rows would
+    scatter (12^3 tets, 60^2 triangles): the build keeps the records in tile
+    order (rec_dest is the identity) and the reduction gathers them.  Both
+    reductions and the saved-det adjoint against the oracle; the deterministic
+    result is reproducible."""
+    mesh = _mesh(dim, 12 if dim == 3 else 60)
+    coef = mg.lognormal_coef(mg.rng_for(116), mesh.n_elem)
+    dA = mg.upstream(mg.rng_for(117), mesh.n_elem, dim + 1)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    ws = gfem.Workspace(coords, conn)
+    assert ws.record_layout() == gfem.nat.RECORDS_TILE_ORDER
+    E, NV = mesh.n_elem, dim + 1
+    T = (E + 31) // 32
+    al = lambda x: ((x + 255) // 256) * 256
+    raw = ws.buf.cpu().numpy()
+    o_dest = al(al(al(4 * (T + 1)) + 4 * T * 32) + 2 * NV * E)
+    R = ws.n_records()
+    assert np.array_equal(raw[o_dest: o_dest + 4 * R].view(np.int32), np.arange(R))
+    gx, gw = orc.integrate_vjp(dim, LP1, mesh.conn, mesh.coords, dA, coef)
+    det = torch.empty(E, device=DEV)
+    gfem.integrate_fwd(coords, conn, LP1, _t(coef), det_out=det)
+    dx, dw = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), ws=ws)
+    assert _rel(dx.cpu().numpy(), gx) <= TOL and _rel(dw.cpu().numpy(), gw) <= TOL
+    sx, _ = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), ws=ws, det=det)
+    ax, _ = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), reduce=1)
+    again, _ = gfem.integrate_bwd(coords, conn, LP1, _t(dA), _t(coef), ws=gfem.Workspace(coords, conn))
+    assert torch.equal(sx, dx) and torch.equal(again, dx)
+    assert _rel(ax.cpu().numpy(), gx) <= TOL
+
+
+def test_record_layouts_give_the_same_bits(gfem):
+    """The same mesh, once with cell-major elements and vertices (vertex-major
+    records) and once with only its vertices renumbered at random (tile-order
+    records: the record tiles are the same, but their vertex-major rows
+    scatter): dcoords, mapped back to the original vertex numbers, is equal
+    bit for bit, because both layouts sum each vertex's records in increasing
+    record order."""
+    base = mg.cube_tet_mesh(9, 0.15, mg.rng_for(113), 0.05, np.float32)
+    renum, _ = mg.shuffled(base, mg.rng_for(114), elements=False, vertices=True)
+    dA = _t(mg.upstream(mg.rng_for(115), base.n_elem, 4))
+    out = []
+    for m in (base, renum):
+        coords, conn = _t(m.coords), _t(m.conn)
+        ws = gfem.Workspace(coords, conn)
+        dx, _ = gfem.integrate_bwd(coords, conn, LP1, dA, ws=ws, need_dcoef=False)
+        out.append((dx.cpu().numpy(), ws.record_layout()))
+    assert out[0][1] == gfem.nat.RECORDS_VERTEX_MAJOR and out[1][1] == gfem.nat.RECORDS_TILE_ORDER
+    # vertex v of base is vertex new_id[v] of renum; recover new_id from the coordinates
+    key = {tuple(x): i for i, x in enumerate(renum.coords.tolist())}
+    new_id = np.array([key[tuple(x)] for x in base.coords.tolist()])
+    assert np.array_equal(out[1][0][new_id], out[0][0])
+
+
 def test_deferred_reduction_and_sharded_slices_unstructured(gfem, orc):
     mesh = _mesh(3, 8)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
