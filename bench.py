@@ -184,7 +184,7 @@ def max_over_ranks(pg, x: float, dev) -> float:
 MIN_TIMED_MS = 1000.0  # repeats of the K-step timed region span at least this much device time
 
 
-def measure(step, K, stream, dev, pg=None, min_ms=MIN_TIMED_MS, max_repeats=400, label=None):
+def measure(step, K, stream, dev, pg=None, min_ms=None, max_repeats=400, label=None):
     """Times exactly K calls of step(rep, k) per timed region: barrier and
     synchronize, an event on `stream`, the K steps, an event, synchronize and
     barrier; the region's duration is the max over ranks.  The region is
@@ -192,6 +192,8 @@ def measure(step, K, stream, dev, pg=None, min_ms=MIN_TIMED_MS, max_repeats=400,
     nvidia-smi clock samples taken throughout.  Returns the median, min and
     max ms per step over the repeats, the repeat count and the clocks."""
     import torch
+    if min_ms is None:
+        min_ms = MIN_TIMED_MS
     clocks = ClockSampler(dev.index if dev.index is not None else 0)
     clocks.start()
     time.sleep(0.3)
@@ -1110,6 +1112,7 @@ def run_reference(args):
 
 
 def main():
+    global MIN_TIMED_MS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -1129,12 +1132,15 @@ def main():
                          "assemble128: global CSR assembly; multiphysics128: three blocks on one mesh; "
                          "iso128: non-affine elements")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="element-count scale of the batch96 meshes")
+    ap.add_argument("--min-timed-ms", type=float, default=MIN_TIMED_MS,
+                    help="repeat the K-step timed region until it spans this much device time (at least 3 repeats)")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: the ranks split ONE mesh by element ranges and sum dcoords with an all-reduce "
                          "inside each step (strong scaling); default: N independent replicas (weak scaling)")
     ap.add_argument("--ref-sample", type=int, default=262_144)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    MIN_TIMED_MS = args.min_timed_ms
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch96":

@@ -367,7 +367,7 @@ class Mesh:
 
     @property
     def dim(self):
-        return self.coords.shape[1]
+        return self.conn.shape[1] - 1
 
     def workspace(self, form=LAPLACE_P1) -> Workspace:
         if "ws" not in self._ws:

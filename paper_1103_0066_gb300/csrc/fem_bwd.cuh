@@ -302,21 +302,27 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
       for (int g = 0; g < FT::NG; ++g) dcoef = fmaf(dG[g], G0[g], dcoef);
       const float L = w * dcoef;
       const float c2 = 2.f * w * scale0;
-      // 3. adjoint of G with respect to adj(J)
+      // 3. adjoint of G with respect to adj(J): adjb = c2 S adj, with S the
+      // symmetric matrix of dG (off-diagonal entries halved); c2 is folded
+      // into S once
       float adjb[D][D];
       if constexpr (FORM != ELASTIC_P1) {
+        float Sc[D][D];
+#pragma unroll
+        for (int r = 0; r < D; ++r)
+#pragma unroll
+          for (int nu = r; nu < D; ++nu) {
+            Sc[r][nu] = (r == nu ? c2 : 0.5f * c2) * dG[pair_index(r, nu, D)];
+            Sc[nu][r] = Sc[r][nu];
+          }
 #pragma unroll
         for (int r = 0; r < D; ++r)
 #pragma unroll
           for (int a = 0; a < D; ++a) {
-            float acc = 0.f;
+            float acc = Sc[r][0] * adj[0][a];
 #pragma unroll
-            for (int nu = 0; nu < D; ++nu) {
-              const float Srn = (r == nu) ? dG[pair_index(r, nu, D)]
-                                          : 0.5f * dG[pair_index(r < nu ? r : nu, r < nu ? nu : r, D)];
-              acc = fmaf(Srn, adj[nu][a], acc);
-            }
-            adjb[r][a] = c2 * acc;
+            for (int nu = 1; nu < D; ++nu) acc = fmaf(Sc[r][nu], adj[nu][a], acc);
+            adjb[r][a] = acc;
           }
       } else {
         constexpr int NP = FT::NP;
@@ -335,26 +341,32 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
       // 4. |det J| term and 5. adjugate pulled back to the edge vectors
       float eb[D][D];
       const float Ld = -__fdividef(L, det);
-#pragma unroll
-      for (int mu = 0; mu < D; ++mu)
-#pragma unroll
-        for (int a = 0; a < D; ++a) eb[mu][a] = Ld * adj[mu][a];
       if constexpr (D == 3) {
+        // adj_mu = e_{mu+1} x e_{mu+2}, so edge nu collects
+        //   d e_nu = Ld adj_nu + e_{nu+1} x adjb_{nu+2} + adjb_{nu+1} x e_{nu+2}
+        // (indices mod 3), each component as one chain of fused multiply-adds
 #pragma unroll
-        for (int mu = 0; mu < 3; ++mu) {
-          const int i1 = (mu + 1) % 3, i2 = (mu + 2) % 3;
-          const float* a = ed[i1];
-          const float* b = ed[i2];
-          const float* cb = adjb[mu];
-          // d a += b x cb ; d b += cb x a
-          eb[i1][0] += b[1] * cb[2] - b[2] * cb[1];
-          eb[i1][1] += b[2] * cb[0] - b[0] * cb[2];
-          eb[i1][2] += b[0] * cb[1] - b[1] * cb[0];
-          eb[i2][0] += cb[1] * a[2] - cb[2] * a[1];
-          eb[i2][1] += cb[2] * a[0] - cb[0] * a[2];
-          eb[i2][2] += cb[0] * a[1] - cb[1] * a[0];
+        for (int nu = 0; nu < 3; ++nu) {
+          const float* ea = ed[(nu + 1) % 3];
+          const float* eb2 = ed[(nu + 2) % 3];
+          const float* ga = adjb[(nu + 2) % 3];
+          const float* gb = adjb[(nu + 1) % 3];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const int c1 = (c + 1) % 3, c2i = (c + 2) % 3;
+            float t = Ld * adj[nu][c];
+            t = fmaf(ea[c1], ga[c2i], t);
+            t = fmaf(-ea[c2i], ga[c1], t);
+            t = fmaf(gb[c1], eb2[c2i], t);
+            t = fmaf(-gb[c2i], eb2[c1], t);
+            eb[nu][c] = t;
+          }
         }
       } else {
+#pragma unroll
+        for (int mu = 0; mu < D; ++mu)
+#pragma unroll
+          for (int a = 0; a < D; ++a) eb[mu][a] = Ld * adj[mu][a];
         eb[1][1] += adjb[0][0];
         eb[1][0] -= adjb[0][1];
         eb[0][1] -= adjb[1][0];

@@ -116,6 +116,81 @@ def test_sharded_adjoint_exchange_gloo(tmp_path, world):
     assert np.array_equal(np.concatenate([np.load(tmp_path / f"dw{r}.npy") for r in range(world)]), gw)
 
 
+def _sharded_class_main(rank, world, port, out_dir):
+    """One rank running the ShardedMesh class itself on CPU tensors: its slice
+    kernels (integrate_fwd, Workspace, integrate_bwd of the package) are
+    replaced by the oracle, so the class's own logic -- the element range, the
+    slice of the connectivity and of the per-element arrays, the workspace kept
+    between calls and the exchange over the process group -- runs as it does
+    on GPUs."""
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "LOCAL_RANK": str(rank), "WORLD_SIZE": str(world)})
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_1103_0066_gb300 import meshgen as mg
+    from paper_1103_0066_gb300 import shard
+    calls = {"ws": 0}
+
+    class CpuWorkspace:
+        def __init__(self, coords, conn, form):
+            calls["ws"] += 1
+
+    def cpu_fwd(coords, conn, form, coef=None, **kw):
+        A, _ = oracle.integrate(3, form, conn.numpy(), coords.numpy(), None if coef is None else coef.numpy())
+        return torch.from_numpy(A)
+
+    def cpu_bwd(coords, conn, form, dA, coef=None, ws=None, reduce=0, need_dcoef=True, **kw):
+        assert isinstance(ws, CpuWorkspace) and reduce == 0
+        gx, gw = oracle.integrate_vjp(3, form, conn.numpy(), coords.numpy(), dA.numpy(),
+                                      None if coef is None else coef.numpy())
+        return torch.from_numpy(gx), (torch.from_numpy(gw) if need_dcoef else None)
+    shard.Workspace, shard.integrate_fwd, shard.integrate_bwd = CpuWorkspace, cpu_fwd, cpu_bwd
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(84), 0.05, np.float32)
+    dA = torch.from_numpy(mg.upstream(mg.rng_for(85), mesh.n_elem, 4).astype(np.float64))
+    w = torch.from_numpy(mg.lognormal_coef(mg.rng_for(86), mesh.n_elem).astype(np.float64))
+    sm = shard.ShardedMesh(torch.from_numpy(mesh.coords.astype(np.float64)), torch.from_numpy(mesh.conn), 0)
+    assert (sm.world, sm.rank) == (world, rank)
+    A = sm.integrate_fwd(sm.local(w))
+    for _ in range(2):  # the workspace is built once and kept
+        dx, dw = sm.integrate_bwd(sm.local(dA).contiguous(), sm.local(w))
+    assert calls["ws"] == 1
+    np.save(os.path.join(out_dir, f"cA{rank}.npy"), A.numpy())
+    np.save(os.path.join(out_dir, f"cdx{rank}.npy"), dx.numpy())
+    np.save(os.path.join(out_dir, f"cdw{rank}.npy"), dw.numpy())
+    dist.destroy_process_group()
+
+
+def test_sharded_mesh_class_runs_at_world_size_2(tmp_path):
+    """ShardedMesh over two gloo ranks: the forward rows and coefficient
+    gradients of the ranks concatenate to the whole mesh's, and after the
+    exchange both ranks hold the whole mesh's vertex gradient."""
+    import numpy as np
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_1103_0066_gb300 import meshgen as mg
+    oracle.build()
+    world = 2
+    port = _free_port()
+    mp.start_processes(_sharded_class_main, args=(world, port, str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    mesh = mg.cube_tet_mesh(4, 0.15, mg.rng_for(84), 0.05, np.float32)
+    dA = mg.upstream(mg.rng_for(85), mesh.n_elem, 4).astype(np.float64)
+    w = mg.lognormal_coef(mg.rng_for(86), mesh.n_elem).astype(np.float64)
+    A, _ = oracle.integrate(3, 0, mesh.conn, mesh.coords, w)
+    gx, gw = oracle.integrate_vjp(3, 0, mesh.conn, mesh.coords, dA, w)
+    assert np.array_equal(np.concatenate([np.load(tmp_path / f"cA{r}.npy") for r in range(world)]), A)
+    assert np.array_equal(np.concatenate([np.load(tmp_path / f"cdw{r}.npy") for r in range(world)]), gw)
+    dx = [np.load(tmp_path / f"cdx{r}.npy") for r in range(world)]
+    assert np.array_equal(dx[0], dx[1])
+    assert np.abs(dx[0] - gx).max() <= 1e-12 * np.abs(gx).max()
+
+
 def test_reference_arm_under_torchrun_prints_once():
     """--impl reference launched like the N = 2 bench: rank 0 alone times the
     oracle and prints one JSON line; the other rank exits 0 without work."""
