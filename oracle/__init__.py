@@ -11,7 +11,9 @@ What it computes (Knepley & Terrel, Sec. 3):
   * ``integrate``: element matrices by quadrature of Eqs. 3-5 (Laplacian) and of
     Eq. 10 scaled by the 1/4 of Eq. 14 / Eq. 24 (elasticity eps:eps), times a
     per-element constant coefficient (piecewise-constant case of Eq. 20).
-  * ``integrate_vjp``: the hand-derived reverse mode of the same steps.
+  * ``integrate_vjp``: the hand-derived reverse mode of the same steps;
+    ``integrate_w1_vjp`` that of the P1-coefficient Laplacian (Eqs. 20-23),
+    with the gradient of the coefficient's vertex values.
   * ``integrate_div`` / ``integrate_div_vjp``: the coupling block of a
     multiphysics pair, B = int q div v with q in P1 and v in [P1]^d or
     [P2]^d (Sec. 6's blocks of coupled systems; Eq. 1 with one derivative in
@@ -75,11 +77,14 @@ def _load():
         lib.orc_integrate_w1.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
         lib.orc_element_matrix_iso.argtypes = [I, I, P, P, D, I, P, P]
         lib.orc_integrate_iso.argtypes = [I, I, I64, I64, P, P, P, P, I, P, P, I]
+        lib.orc_element_vjp_w1.argtypes = [I, I, P, P, I, P, P, P]
+        lib.orc_integrate_w1_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
         lib.orc_element_matrix_div.argtypes = [I, I, P, D, I, P, P]
         lib.orc_element_vjp_div.argtypes = [I, I, P, D, I, P, P, P]
         lib.orc_integrate_div.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
         lib.orc_integrate_div_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
-        for name in ("orc_element_matrix_div", "orc_element_vjp_div", "orc_integrate_div",
+        for name in ("orc_element_vjp_w1", "orc_integrate_w1_vjp", "orc_element_matrix_div", "orc_element_vjp_div",
+                     "orc_integrate_div",
                      "orc_integrate_div_vjp", "orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
                      "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
                      "orc_integrate_vjp", "orc_element_matrix_w1", "orc_integrate_w1",
@@ -178,6 +183,36 @@ def integrate_w1(dim: int, form: int, conn, coords, wvert, q: int = 3, nthreads:
     if rc < 0:
         raise ValueError("bad integrate request")
     return A, flags
+
+
+def element_vjp_w1(dim: int, form: int, X, wv, Abar, q: int = 3):
+    """Reverse mode of element_matrix_w1: (Xbar [dim+1][dim], wbar [dim+1])."""
+    X = _f64(X)
+    wv = _f64(wv)
+    Abar = _f64(Abar)
+    Xbar = np.zeros_like(X)
+    wbar = np.zeros(dim + 1)
+    rc = _load().orc_element_vjp_w1(dim, form, _ptr(X), _ptr(wv), q, _ptr(Abar), _ptr(Xbar), _ptr(wbar))
+    if rc < 0:
+        raise ValueError("bad element request")
+    return Xbar, wbar
+
+
+def integrate_w1_vjp(dim: int, form: int, conn, coords, wvert, dA, q: int = 3, nthreads: int | None = None):
+    """Reverse mode of integrate_w1: (dcoords [V][dim], dwvert [V]) for dA [E][n][n]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    wvert = _f64(wvert)
+    dA = _f64(dA)
+    E, V = conn.shape[0], coords.shape[0]
+    dcoords = np.zeros((V, dim))
+    dw = np.zeros(V)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_w1_vjp(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(wvert), q, _ptr(dA),
+                                      _ptr(dcoords), _ptr(dw), nt)
+    if rc < 0:
+        raise ValueError("bad vjp request")
+    return dcoords, dw
 
 
 def element_matrix_iso(dim: int, form: int, X, mid, coef: float = 1.0, q: int = 4):

@@ -903,3 +903,145 @@ int orc_integrate_div_vjp(int dim, int vdeg, int64_t n_elem, int64_t n_vert, con
   free(fl);
   return any;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of the P1-coefficient Laplacian (Eqs. 20-23)               */
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of orc_element_matrix_w1: given Abar = dL/dA, returns Xbar =
+ * dL/dX [(d+1)*d] and wbar[d+1] = dL/dw_k for the vertex values w_k of the
+ * coefficient c(xi) = sum_k w_k lambda_k(xi).  Per quadrature point, with
+ * s = |det J| and I = sum_ij Abar_ij g_i.g_j:
+ *   wbar_k += w_q s lambda_k I,   sbar += w_q c I,
+ *   gbar_i += w_q s c sum_j (Abar_ij + Abar_ji) g_j
+ * then, as in orc_element_vjp, with B = J^{-1}:
+ *   Bbar[mu][a] += sum_i gref_i[mu] gbar_i[a],   Jbar = -B^T Bbar B^T + sbar s B^T. */
+int orc_element_vjp_w1(int dim, int form, const double* X, const double* wv, int q, const double* Abar,
+                       double* Xbar, double* wbar) {
+  if (form == ORC_ELASTIC_P1 || !wv) return -1;
+  int n = orc_form_n(form, dim);
+  if (n < 0) return -1;
+  int deg = form_degree(form), nb = orc_n_basis(dim, deg), nv = dim + 1;
+  for (int k = 0; k < nv * dim; ++k) Xbar[k] = 0.0;
+  for (int k = 0; k < nv; ++k) wbar[k] = 0.0;
+  double J[3][3], Jt[3][3];
+  jacobian(dim, X, J);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) Jt[a][b] = J[b][a];
+  lu3 fJt;
+  lu_factor(dim, Jt, &fJt);
+  if (fJt.det == 0.0) return ORC_FLAG_DEGENERATE;
+  double s = fabs(fJt.det);
+  lu3 fJ;
+  lu_factor(dim, J, &fJ);
+  double B[3][3] = {{0}};
+  for (int k = 0; k < dim; ++k) {
+    double e[3] = {0, 0, 0};
+    e[k] = 1.0;
+    lu_solve(&fJ, e);
+    for (int r = 0; r < dim; ++r) B[r][k] = e[r];
+  }
+  double pts[ORC_MAXPTS * 3], wts[ORC_MAXPTS];
+  int np = orc_simplex_rule(dim, q, pts, wts);
+  if (np < 0) return -1;
+  double sbar = 0.0, Bbar[3][3] = {{0}};
+  for (int p = 0; p < np; ++p) {
+    const double* xi = pts + p * dim;
+    double lam[4];
+    lam[0] = 1.0;
+    for (int k = 1; k <= dim; ++k) {
+      lam[k] = xi[k - 1];
+      lam[0] -= xi[k - 1];
+    }
+    double c = 0.0;
+    for (int k = 0; k < nv; ++k) c += wv[k] * lam[k];
+    double phi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3], gbar[ORC_MAXB][3];
+    orc_basis(dim, deg, xi, phi, gref);
+    physical_gradients(dim, &fJt, nb, gref, g);
+    memset(gbar, 0, sizeof(gbar));
+    double wq = wts[p], integrand = 0.0;
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double gg = 0.0;
+        for (int a = 0; a < dim; ++a) gg += g[i][a] * g[j][a];
+        integrand += Abar[i * n + j] * gg;
+        double sym = Abar[i * n + j] + Abar[j * n + i];
+        for (int a = 0; a < dim; ++a) gbar[i][a] += wq * s * c * sym * g[j][a];
+      }
+    sbar += wq * c * integrand;
+    for (int k = 0; k < nv; ++k) wbar[k] += wq * s * lam[k] * integrand;
+    for (int i = 0; i < nb; ++i)
+      for (int mu = 0; mu < dim; ++mu)
+        for (int a = 0; a < dim; ++a) Bbar[mu][a] += gref[i * dim + mu] * gbar[i][a];
+  }
+  double Jbar[3][3] = {{0}};
+  for (int a = 0; a < dim; ++a)
+    for (int mu = 0; mu < dim; ++mu) {
+      double acc = 0.0;
+      for (int k = 0; k < dim; ++k)
+        for (int l = 0; l < dim; ++l) acc += B[k][a] * Bbar[k][l] * B[mu][l];
+      Jbar[a][mu] = -acc + sbar * s * B[mu][a];
+    }
+  for (int a = 0; a < dim; ++a) {
+    double col = 0.0;
+    for (int mu = 0; mu < dim; ++mu) {
+      Xbar[(mu + 1) * dim + a] = Jbar[a][mu];
+      col += Jbar[a][mu];
+    }
+    Xbar[a] = -col;
+  }
+  return 0;
+}
+
+/* Reverse mode of orc_integrate_w1 over a mesh: Abar [E][n][n] -> dcoords
+ * [V][d] and dwvert [V] (both overwritten; per-vertex sums in element order).
+ * Flagged elements contribute nothing. */
+int orc_integrate_w1_vjp(int dim, int form, int64_t n_elem, int64_t n_vert, const int32_t* conn,
+                         const double* coords, const double* wvert, int q, const double* Abar, double* dcoords,
+                         double* dwvert, int nthreads) {
+  int n = orc_form_n(form, dim);
+  if (n < 0 || form == ORC_ELASTIC_P1 || !wvert) return -1;
+  int nv = dim + 1;
+  double* xbar = (double*)malloc(sizeof(double) * (size_t)(n_elem > 0 ? n_elem : 1) * nv * dim);
+  double* wb = (double*)malloc(sizeof(double) * (size_t)(n_elem > 0 ? n_elem : 1) * nv);
+  int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_elem > 0 ? n_elem : 1));
+  if (!xbar || !wb || !fl) {
+    free(xbar);
+    free(wb);
+    free(fl);
+    return -2;
+  }
+  if (nthreads < 1) nthreads = 1;
+  int any = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12], wv[4];
+    const int32_t* ce = conn + e * nv;
+    double* xb = xbar + e * nv * dim;
+    double* w = wb + e * nv;
+    int f = gather(dim, n_vert, ce, coords, X);
+    if (f == 0) {
+      for (int k = 0; k < nv; ++k) wv[k] = wvert[ce[k]];
+      f = orc_element_vjp_w1(dim, form, X, wv, q, Abar + e * (int64_t)n * n, xb, w);
+    }
+    if (f != 0) {
+      for (int k = 0; k < nv * dim; ++k) xb[k] = 0.0;
+      for (int k = 0; k < nv; ++k) w[k] = 0.0;
+    }
+    fl[e] = f;
+    any |= f;
+  }
+  for (int64_t k = 0; k < n_vert * dim; ++k) dcoords[k] = 0.0;
+  for (int64_t k = 0; k < n_vert; ++k) dwvert[k] = 0.0;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    if (fl[e] & ORC_FLAG_CONN) continue;
+    for (int k = 0; k < nv; ++k) {
+      int64_t v = conn[e * nv + k];
+      for (int a = 0; a < dim; ++a) dcoords[v * dim + a] += xbar[(e * nv + k) * dim + a];
+      dwvert[v] += wb[e * nv + k];
+    }
+  }
+  free(xbar);
+  free(wb);
+  free(fl);
+  return any;
+}

@@ -156,3 +156,65 @@ def test_w1_mesh_driver_gathers_vertex_values(orc):
     for e in (0, 7, mesh.n_elem - 1):
         Ae, _, _ = orc.element_matrix_w1(3, LP2, mesh.coords[conn[e]], wvert[conn[e]])
         assert np.array_equal(A[e], Ae)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [0, 1])
+def test_w1_vjp_pins(orc, dim, form):
+    """Reverse mode of the P1-coefficient Laplacian (Eqs. 20-23): the
+    coordinate and coefficient gradients against FP64 central differences of
+    the forward, and identities that hold exactly -- translation invariance,
+    homogeneity sum_k x_k . xbar_k = (d-2) L, and linearity in w:
+    sum_k w_k wbar_k = L."""
+    rng = np.random.default_rng(20 + dim + 3 * form)
+    X = np.vstack([np.zeros(dim), np.eye(dim)]) + 0.25 * rng.standard_normal((dim + 1, dim))
+    if np.linalg.det(X[1:] - X[0]) < 0:
+        X[[1, 2]] = X[[2, 1]]
+    wv = np.exp(rng.standard_normal(dim + 1))
+    n = orc.form_n(form, dim)
+    Abar = rng.standard_normal((n, n))
+    Xbar, wbar = orc.element_vjp_w1(dim, form, X, wv, Abar)
+    L = np.sum(Abar * orc.element_matrix_w1(dim, form, X, wv)[0])
+    h = 1e-6
+    fdx = np.zeros_like(X)
+    for k in range(dim + 1):
+        for a in range(dim):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[k, a] += h
+            Xm[k, a] -= h
+            fdx[k, a] = (np.sum(Abar * orc.element_matrix_w1(dim, form, Xp, wv)[0])
+                         - np.sum(Abar * orc.element_matrix_w1(dim, form, Xm, wv)[0])) / (2 * h)
+    fdw = np.zeros(dim + 1)
+    hw = 0.5  # L is linear in w: a large step is exact and keeps roundoff out
+    for k in range(dim + 1):
+        wp, wm = wv.copy(), wv.copy()
+        wp[k] += hw
+        wm[k] -= hw
+        fdw[k] = (np.sum(Abar * orc.element_matrix_w1(dim, form, X, wp)[0])
+                  - np.sum(Abar * orc.element_matrix_w1(dim, form, X, wm)[0])) / (2 * hw)
+    assert np.abs(Xbar - fdx).max() <= 1e-7 * np.abs(fdx).max()
+    assert np.abs(wbar - fdw).max() <= 1e-7 * np.abs(fdw).max()
+    assert np.abs(Xbar.sum(0)).max() <= 1e-12 * np.abs(Xbar).max()
+    assert abs(np.sum(X * Xbar) - (dim - 2) * L) <= 1e-12 * max(1.0, abs(L))
+    assert abs(np.dot(wv, wbar) - L) <= 1e-12 * max(1.0, abs(L))
+    # constant coefficient: the coordinate gradient is the per-element-coefficient one
+    Xc, _ = orc.element_vjp_w1(dim, form, X, np.full(dim + 1, 1.7), Abar)
+    Xr, _ = orc.element_vjp(dim, form, X, Abar, coef=1.7)
+    assert np.abs(Xc - Xr).max() <= 1e-12 * np.abs(Xr).max()
+
+
+def test_w1_vjp_mesh_driver(orc):
+    from paper_1103_0066_gb300 import meshgen as mg
+    m = mg.cube_tet_mesh(3, 0.15, mg.rng_for(24), 0.05, np.float32)
+    wv = mg.lognormal_coef(mg.rng_for(25), m.n_vert).astype(np.float64)
+    dA = np.random.default_rng(26).standard_normal((m.n_elem, 10, 10))
+    gx, gw = orc.integrate_w1_vjp(3, 1, m.conn, m.coords, wv, dA)
+    rx, rw = np.zeros_like(gx), np.zeros_like(gw)
+    for e in range(m.n_elem):
+        xb, wb = orc.element_vjp_w1(3, 1, m.coords[m.conn[e]].astype(np.float64), wv[m.conn[e]], dA[e])
+        np.add.at(rx, m.conn[e], xb)
+        np.add.at(rw, m.conn[e], wb)
+    assert np.allclose(gx, rx, rtol=1e-12, atol=1e-14 * np.abs(rx).max())
+    assert np.allclose(gw, rw, rtol=1e-12, atol=1e-14 * np.abs(rw).max())
+    A, _ = orc.integrate_w1(3, 1, m.conn, m.coords, wv)
+    assert abs(np.dot(wv, gw) - np.sum(dA * A)) <= 1e-11 * np.abs(dA * A).sum()
