@@ -687,8 +687,43 @@ def run_coef_p1(args):
             num = np.abs(Ag - Ar).reshape(len(idx), -1).max(1)
             res[name]["max_rel_err_vs_fp64"] = float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())
             res[name]["error_sample"] = f"{len(idx):,} elements (20,000 slivers, 20,000 uniform, the last 40)"
+    # forward + adjoint of the P1-coefficient form: coordinate gradient and the
+    # gradient of the coefficient's vertex values (deterministic, det J kept)
+    dA = torch.randn((E, 10, 10), device=dev, generator=torch.Generator(device=dev).manual_seed(13))
+    det = torch.empty(E, device=dev)
+    dx = torch.empty((V, 3), device=dev)
+    dwv = torch.empty(V, device=dev)
+    ws = fem.Workspace(coords, conn, fem.LAPLACE_P2_W1)
+    R = ws.n_records()
+
+    def step_adj():
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P2_W1, wv, out=A, det_out=det)
+        fem.integrate_bwd(coords, conn, fem.LAPLACE_P2_W1, dA, wv, ws=ws, dcoords=dx, dcoef=dwv, det=det)
+    for _ in range(max(3, args.warmup)):
+        step_adj()
+    torch.cuda.synchronize()
+    ra = measure(lambda rep, k: step_adj(), args.steps, stream, dev)
+    res["p1_coefficient_fwd_adjoint"] = {"ms": ra["ms_per_step"], "ms_min": ra["ms_min"], "ms_max": ra["ms_max"],
+                                         "repeats": ra["repeats"], "clocks": ra["clocks"],
+                                         "elements_per_s": E / (ra["ms_per_step"] * 1e-3)}
+    rng = np.random.default_rng(14)
+    verts = rng.choice(V, 300, replace=False)
+    hit = np.zeros(V, bool)
+    hit[verts] = True
+    el = np.where(hit[mesh.conn].any(1))[0]
+    gx, gw = oracle.integrate_w1_vjp(3, oracle.LAPLACE_P2, mesh.conn[el], mesh.coords, wv_h,
+                                     dA[torch.from_numpy(el).to(dev)].cpu().numpy())
+    res["p1_coefficient_fwd_adjoint"]["max_rel_err_vs_fp64"] = {
+        "dcoords": float(np.abs(dx.cpu().numpy()[verts] - gx[verts]).max() / np.abs(gx[verts]).max()),
+        "dcoef_vertex_values": float(np.abs(dwv.cpu().numpy()[verts] - gw[verts]).max() / np.abs(gw[verts]).max()),
+        "sample": "300 random vertices, against the oracle's reverse mode over all their incident elements"}
     byts = {"p1_coefficient": E * (16 + 400) + V * (12 + 4), "p0_coefficient": E * (16 + 400 + 4) + V * 12}
     byts["p1_coefficient_tensor_core"] = byts["p1_coefficient"]
+    # forward (saving det J) + element pass (dA, conn, slot positions, det J; per
+    # record span, destination and a 16-byte record) + reduction (records,
+    # vertex offsets; dcoords and the coefficient gradient written)
+    byts["p1_coefficient_fwd_adjoint"] = (E * (16 + 400 + 4) + V * (12 + 4) + E * (400 + 16 + 4 + 4) + R * (2 + 4 + 16)
+                                          + V * (12 + 4) + R * 16 + V * (4 + 12 + 4))
     peak, peak_kind = hbm_peak()
     for k in res:
         res[k]["GB/s"] = byts[k] / (res[k]["ms"] * 1e-3) / 1e9

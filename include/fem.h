@@ -55,9 +55,9 @@ typedef enum {
 /* Weak forms (Sec. 3).  The first three take an optional per-element
  * coefficient w_e; the _W1 forms take a P1 coefficient w = sum_k w_k lambda_k
  * given by its values at the mesh vertices (Eqs. 20-23), so `coef` is
- * [n_vert] for them.  The _W1 forms have a forward path only (no adjoint, no
- * batched path: FEM_ERR_UNSUPPORTED); FEM_LAPLACE_P2_W1 also contracts on the
- * tensor cores. */
+ * [n_vert] for them, and their adjoint's dcoef is the gradient of those vertex
+ * values, [n_vert].  The _W1 forms have no batched path (FEM_ERR_UNSUPPORTED);
+ * FEM_LAPLACE_P2_W1 also contracts on the tensor cores. */
 typedef enum {
   FEM_LAPLACE_P1 = 0,    /* Eqs. 2-8 with P1 Lagrange elements */
   FEM_LAPLACE_P2 = 1,    /* same form, P2 Lagrange elements */
@@ -232,9 +232,16 @@ FEM_API fem_status fem_incidence_info(const fem_mesh* mesh, const void* ws, size
                                       int32_t* layout, void* stream);
 
 /* Adjoint of fem_integrate_fwd (FP32 coordinates): for the upstream
- * dA = dL/dA (device FP32 [n_elem][n][n]) computes
+ * dA = dL/dA (device FP32 [n_elem][rows][cols]) computes
  *   dcoords = dL/dcoords  (device FP32 [n_vert][dim], overwritten; may be NULL)
- *   dcoef   = dL/dcoef    (device FP32 [n_elem], overwritten; may be NULL)
+ *   dcoef   = dL/dcoef    (device FP32 [n_elem], overwritten; may be NULL);
+ *             for the _W1 forms [n_vert], the gradient of the coefficient's
+ *             vertex values, summed over the elements at each vertex like
+ *             dcoords (so it uses the workspace with the deterministic
+ *             reduction even when dcoords is NULL)
+ * The _W1 forms take the compensated Jacobian and the deterministic or atomic
+ * reduction (FEM_REDUCE_DEFERRED: FEM_ERR_UNSUPPORTED); their workspace
+ * (fem_bwd_workspace_size with the form) holds records of dim + 1 components.
  * through dG = dA K^T, then d|J| and d adj(J), then the vertex sums.
  * Deterministic reduction: bitwise reproducible, needs the built incidence in ws.
  * Atomic reduction: ws may be NULL.  Deferred: the element pass only (dcoords

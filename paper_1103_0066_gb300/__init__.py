@@ -203,22 +203,25 @@ class Assembly:
 def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None,
                   reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dcoef=True, jac=JAC_AUTO,
                   warps_per_cta=0, ctas_per_sm=0, dcoords=None, dcoef=None, dev_err=None, stream=None, det=None):
-    """fem_integrate_bwd: (dcoords [V][d] or None, dcoef [E] or None) for the upstream dA.
+    """fem_integrate_bwd: (dcoords [V][d] or None, dcoef or None) for the upstream dA.
+    dcoef is [E] for a per-element coefficient, [V] (the gradient of the
+    coefficient's vertex values) for LAPLACE_P1_W1 / LAPLACE_P2_W1.
     det: det J saved by integrate_fwd(det_out=...) (fem_integrate_bwd_saved)."""
     m = _mesh_struct(coords, conn)
     E, V = conn.shape[0], coords.shape[0]
+    w1 = form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
     if dA.dtype != torch.float32 or not dA.is_contiguous() or tuple(dA.shape) != (E,) + form_shape(form, m.dim):
         raise ValueError("dA must be a contiguous float32 tensor shaped like the forward's output")
     if need_dcoords and dcoords is None:
         dcoords = torch.empty((V, m.dim), dtype=torch.float32, device=coords.device)
     if need_dcoef and dcoef is None:
-        dcoef = torch.empty(E, dtype=torch.float32, device=coords.device)
+        dcoef = torch.empty(V if w1 else E, dtype=torch.float32, device=coords.device)
     if not need_dcoords:
         dcoords = None
     if not need_dcoef:
         dcoef = None
     ws_ptr, ws_bytes = 0, 0
-    if dcoords is not None and reduce in (REDUCE_DETERMINISTIC, REDUCE_DEFERRED):
+    if reduce in (REDUCE_DETERMINISTIC, REDUCE_DEFERRED) and (dcoords is not None or (w1 and dcoef is not None)):
         if ws is None:
             ws = Workspace(coords, conn, form, stream)
         ws_ptr, ws_bytes = ws.buf.data_ptr(), ws.bytes
@@ -226,12 +229,13 @@ def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None
                               dev_err.data_ptr() if dev_err is not None else 0)
     dx_ptr = dcoords.data_ptr() if dcoords is not None else 0
     dw_ptr = dcoef.data_ptr() if dcoef is not None else 0
+    cp = _coef_ptr(coef, V, "[V]") if w1 else _coef_ptr(coef, E)
     if det is not None:
         _check_det(det, E)
-        nat.fem_integrate_bwd_saved(m, form, _coef_ptr(coef, E), dA.data_ptr(), det.data_ptr(), dx_ptr, dw_ptr,
+        nat.fem_integrate_bwd_saved(m, form, cp, dA.data_ptr(), det.data_ptr(), dx_ptr, dw_ptr,
                                     ws_ptr, ws_bytes, opts, _stream_ptr(stream))
     else:
-        nat.fem_integrate_bwd(m, form, _coef_ptr(coef, E), dA.data_ptr(), dx_ptr, dw_ptr, ws_ptr, ws_bytes, opts,
+        nat.fem_integrate_bwd(m, form, cp, dA.data_ptr(), dx_ptr, dw_ptr, ws_ptr, ws_bytes, opts,
                               _stream_ptr(stream))
     return dcoords, dcoef
 
@@ -334,7 +338,8 @@ class _IntegrateFn(torch.autograd.Function):
     def forward(ctx, coords, coef, mesh, form, jac, reduce, contract):
         # det J is kept for the adjoint when it can take it (FP32 coordinates, affine
         # form, FP32 contraction)
-        keep = (coords.dtype == torch.float32 and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, DIV_P1P1, DIV_P2P1)
+        keep = (coords.dtype == torch.float32
+                and form in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1, DIV_P1P1, DIV_P2P1, LAPLACE_P1_W1, LAPLACE_P2_W1)
                 and jac in (JAC_AUTO, JAC_COMP_F32) and contract == CONTRACT_F32)
         det = torch.empty(mesh.conn.shape[0], dtype=torch.float32, device=coords.device) if keep else None
         A = integrate_fwd(coords, mesh.conn, form, coef, jac=jac, contract=contract, det_out=det)
@@ -350,7 +355,9 @@ class _IntegrateFn(torch.autograd.Function):
         coef = coef if ctx.has_coef else None
         need_x = ctx.needs_input_grad[0]
         need_w = ctx.has_coef and ctx.needs_input_grad[1]
-        ws = ctx.mesh.workspace(ctx.form) if (need_x and ctx.reduce == REDUCE_DETERMINISTIC) else None
+        w1 = ctx.form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
+        ws = (ctx.mesh.workspace(ctx.form) if ((need_x or (w1 and need_w)) and ctx.reduce == REDUCE_DETERMINISTIC)
+              else None)
         dx, dw = integrate_bwd(coords.detach(), ctx.mesh.conn, ctx.form, dA.contiguous().float(), coef,
                                ws=ws, reduce=ctx.reduce, need_dcoords=need_x, need_dcoef=need_w,
                                jac=ctx.jac, det=ctx.det)
@@ -370,9 +377,11 @@ class Mesh:
         return self.conn.shape[1] - 1
 
     def workspace(self, form=LAPLACE_P1) -> Workspace:
-        if "ws" not in self._ws:
-            self._ws["ws"] = Workspace(self.coords.detach(), self.conn, form)
-        return self._ws["ws"]
+        # the P1-coefficient forms' records carry one more component: a larger workspace
+        key = "w1" if form in (LAPLACE_P1_W1, LAPLACE_P2_W1) else "ws"
+        if key not in self._ws:
+            self._ws[key] = Workspace(self.coords.detach(), self.conn, form)
+        return self._ws[key]
 
     def integrate(self, form, coef=None, jac=JAC_AUTO, reduce=REDUCE_DETERMINISTIC, coords=None,
                   contract=CONTRACT_F32):

@@ -82,6 +82,17 @@ int resolve_jac(int jac, bool coord_f64, bool out_f64) {
   return fem::JAC_F32;
 }
 
+// Components of an adjoint record: the vertex gradient, plus the gradient of
+// the coefficient's vertex values for the P1-coefficient forms.
+int record_components(int form, int dim) { return dim + (coef_p1(form) ? 1 : 0); }
+
+// Whether an adjoint call reduces through the workspace's records: the
+// deterministic and deferred reductions of dcoords, and of dcoef when it holds
+// vertex values (P1-coefficient forms).
+bool bwd_uses_records(int form, bool has_dcoords, bool has_dcoef, int reduce) {
+  return reduce != FEM_REDUCE_ATOMIC && (has_dcoords || (coef_p1(form) && has_dcoef));
+}
+
 // Every check of an adjoint call that needs no workspace: the mesh, the form,
 // the options and the pointers.  A refused call launches nothing.
 fem_status bwd_args(const fem_mesh* mesh, int32_t form, const fem_options* o, const float* dA,
@@ -89,9 +100,11 @@ fem_status bwd_args(const fem_mesh* mesh, int32_t form, const fem_options* o, co
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (coef_p1(form) || non_affine(form))
-    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
+  if (non_affine(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine forms");
   if ((s = check_options(o)) != FEM_OK) return s;
+  if (coef_p1(form) && ((o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32) || o->reduce == FEM_REDUCE_DEFERRED))
+    return fail(FEM_ERR_UNSUPPORTED,
+                "the P1-coefficient adjoint takes the compensated Jacobian and the deterministic or atomic reduction");
   if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint takes FP32 coordinates");
   if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
   if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
@@ -131,6 +144,10 @@ namespace fem {
 int32_t bwd_preflight(const fem_mesh* mesh, int32_t form, const fem_options* options, const float* dA,
                       const float* dcoords) {
   return bwd_args(mesh, form, options ? options : &kDefaults, dA, dcoords);
+}
+
+bool bwd_needs_workspace(int32_t form, bool has_dcoords, bool has_dcoef, int32_t reduce) {
+  return bwd_uses_records(form, has_dcoords, has_dcoef, reduce);
 }
 
 void set_last_error(const char* fmt, ...) {
@@ -353,8 +370,7 @@ fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (coef_p1(form) || non_affine(form))
-    return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine per-element-coefficient forms");
+  if (non_affine(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (!bytes) return fail(FEM_ERR_ARG, "bytes is NULL");
@@ -362,7 +378,8 @@ fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_
     return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
   *bytes = o->reduce == FEM_REDUCE_ATOMIC
                ? 0
-               : fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, nullptr, nullptr);
+               : fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, nullptr, nullptr,
+                                           record_components(form, mesh->dim));
   return ok();
 }
 
@@ -408,9 +425,12 @@ static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float*
   if (s != FEM_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const bool atomic = o->reduce == FEM_REDUCE_ATOMIC;
+  const bool w1 = coef_p1(form);  // dcoef holds the gradient of the coefficient's vertex values
+  const bool recs = bwd_uses_records(form, dcoords != nullptr, dcoef != nullptr, o->reduce);
   fem::BwdWorkspace W{};
-  if (dcoords && !atomic) {
-    const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W);
+  if (recs) {
+    const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W,
+                                                  record_components(form, mesh->dim));
     if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
   }
@@ -420,18 +440,21 @@ static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float*
     e = fem::launch_zero_f32(dcoords, mesh->n_vert * mesh->dim, st);
     if (e != cudaSuccess) return cuda_fail(e, "zeroing dcoords");
   }
+  if (w1 && dcoef && atomic) {
+    e = fem::launch_zero_f32(dcoef, mesh->n_vert, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing dcoef");
+  }
   if (mesh->n_elem > 0) {
     fem::BwdLaunch L{};
     L.dim = mesh->dim;
     L.form = form;
     L.jac = resolve_jac(o->jac, false, false);
-    L.atomic = (dcoords && atomic) ? 1 : 0;
+    L.atomic = ((dcoords || (w1 && dcoef)) && atomic) ? 1 : 0;
     L.conn = mesh->conn;
     L.coords = static_cast<const float*>(mesh->coords);
     L.coef = coef;
     L.dA = dA;
     L.dcoef = dcoef;
-    const bool recs = dcoords && !atomic;
     L.tile_rec = recs ? W.tile_rec : nullptr;
     L.rank = recs ? W.rank : nullptr;
     L.rec_span = recs ? W.rec_span : nullptr;
@@ -448,8 +471,8 @@ static fem_status integrate_bwd(const fem_mesh* mesh, int32_t form, const float*
     e = coupling(form) ? fem::launch_div_bwd(L) : fem::launch_bwd_elem(L);
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd element launch");
   }
-  if (dcoords && o->reduce == FEM_REDUCE_DETERMINISTIC) {
-    e = fem::launch_vertex_reduce(mesh->dim, W, mesh->n_vert, dcoords, st);
+  if (recs && o->reduce == FEM_REDUCE_DETERMINISTIC) {
+    e = fem::launch_vertex_reduce(mesh->dim, W, mesh->n_vert, dcoords, st, w1 ? dcoef : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd reduction launch");
   }
   return ok();

@@ -154,7 +154,7 @@ __device__ __forceinline__ int warp_bwd(const BatchMesh& M, const BwdParams& bp,
                                         float* xs, const WarpRec& wr) {
   const bool rec = (M.flags & BM_REC) != 0;
   const RecAhead ah = rec ? load_rec_ahead(M.rec_span, M.rec_dest, wr.rb, wr.rn, lane) : RecAhead{0u, 0};
-  const int err = bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, w, X,
+  const int err = bwd_compute_tile<D, FORM, JAC_COMP, false>(bp, t, lane, f, Coef<1>{{w}}, X,
                                                             dstage + lane * BwdPlan<D, FORM>::DST, v,
                                                             rec ? xs : nullptr, wr.rk);
   if (rec) {

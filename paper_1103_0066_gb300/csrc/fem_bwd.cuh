@@ -88,7 +88,10 @@ struct BwdPlan {
   static constexpr int NV = D + 1;
   static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
   static constexpr int XCAP = D == 3 ? kStageCap3 : NSW;  // stage positions (aligned runs on tets)
-  static constexpr int XP = D == 3 ? 4 : 2;  // padded floats per staged slot (one vector store)
+  // components of a slot contribution: the vertex gradient, plus the
+  // coefficient gradient for the P1-coefficient forms (Eqs. 20-23)
+  static constexpr int NC = D + (FormTraits<D, FORM>::W1 ? 1 : 0);
+  static constexpr int XP = NC > 2 ? 4 : 2;  // padded floats per staged slot (one vector store)
   static constexpr size_t da_slot = align_up(size_t(32) * DST * 4, 128);    // one tile of dA rows
   static constexpr size_t da_bytes = 2 * da_slot;                           // per warp, double buffered
   static constexpr size_t xs_bytes = align_up(size_t(XCAP) * XP * 4, 128);  // per warp
@@ -207,10 +210,10 @@ __device__ __forceinline__ RecAhead load_rec_ahead(const uint16_t* rec_span, con
   return a;
 }
 
-template <int D>
+template <int D, int NC = D>
 __device__ __forceinline__ void warp_records(const float* xs, const uint16_t* rec_span, const int32_t* rec_dest,
                                              int32_t rb, int32_t rn, RecAhead ah, float* records, int lane) {
-  constexpr int XP = D == 3 ? 4 : 2;
+  constexpr int XP = NC > 2 ? 4 : 2;
   for (int r0 = 0; r0 < rn; r0 += 32) {
     const int r = r0 + lane;
     const bool live = r < rn;
@@ -222,19 +225,20 @@ __device__ __forceinline__ void warp_records(const float* xs, const uint16_t* re
     // together.  Each run is still summed in increasing position order.
     const int len = live ? int(span >> 8) : 0;
     const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    float acc[D];
+    float acc[NC];
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int a = 0; a < NC; ++a) acc[a] = 0.f;
     for (int m0 = 0; m0 < maxlen; m0 += 8) {
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (m0 + u < len) {
           const float* x = xs + (beg + m0 + u) * XP;
-          if constexpr (D == 3) {
+          if constexpr (XP == 4) {
             const float4 v = *reinterpret_cast<const float4*>(x);
             acc[0] += v.x;
             acc[1] += v.y;
             acc[2] += v.z;
+            if constexpr (NC == 4) acc[3] += v.w;
           } else {
             const float2 v = *reinterpret_cast<const float2*>(x);
             acc[0] += v.x;
@@ -244,29 +248,39 @@ __device__ __forceinline__ void warp_records(const float* xs, const uint16_t* re
       }
     }
     if (live) {
-      float* dst = records + int64_t(dest) * D;
+      float* dst = records + int64_t(dest) * NC;
 #pragma unroll
-      for (int a = 0; a < D; ++a) dst[a] = acc[a];
+      for (int a = 0; a < NC; ++a) dst[a] = acc[a];
     }
   }
 }
 
 // Stage 3 of the adjoint for one element per lane.
+// For the P1-coefficient forms (Eqs. 20-23) the contraction's slots are
+// w_k G_g (slot k * NGB + g): with dGw its adjoint, the base form's adjoint
+// runs on dG_g = sum_k w_k dGw_kg with w = 1, and the coefficient's vertex
+// value k collects wb_k = sum_g dGw_kg G_g, staged beside the vertex gradient.
 template <int D, int FORM, int JAC, bool ATOMIC>
-__device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags, float w,
+__device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile, int lane, int flags,
+                                                const Coef<FormTraits<D, FORM>::NW>& wv,
                                                 const float (&X)[D + 1][D], const float* drow,
                                                 const int (&vc)[D + 1], float* xs, uint32_t rk,
                                                 float det_saved = 0.f) {
   using FT = FormTraits<D, FORM>;
+  using BT = FormTraits<D, FT::BASE>;
   using GT = typename std::conditional<JAC == JAC_F64, double, float>::type;
   constexpr int N = FT::N, NV = FT::NV;
+  constexpr bool W1 = FT::W1;
   const int64_t e = tile * 32 + lane;
   int err = 0;
   float xb[NV][D];
+  float wb[NV];  // P1 coefficient: gradient of the element's vertex values
 #pragma unroll
-  for (int k = 0; k < NV; ++k)
+  for (int k = 0; k < NV; ++k) {
+    wb[k] = 0.f;
 #pragma unroll
     for (int a = 0; a < D; ++a) xb[k][a] = 0.f;
+  }
   float dcoef = 0.f;
   bool ok = false;
   if (flags & GF_OK) {
@@ -290,23 +304,45 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
         }
       const float det = float(jac.det);
       const float scale0 = __frcp_rn(dev_abs(det) * float(FT::DEN));
-      float G0[FT::NG];
-      geometric_tensor<D, FORM>(adj, scale0, G0);
+      float G0[BT::NG];
+      geometric_tensor<D, FT::BASE>(adj, scale0, G0);
       // 1. dG = transpose of the contraction applied to sym(dA)
       SymVals<FT::NT> sym;
       stage_sym<D, FORM>(drow, sym.s);
-      float dG[FT::NG];
-      contract_adjoint<D, FORM>(sym, dG);
+      float dGw[FT::NG];
+      contract_adjoint<D, FORM>(sym, dGw);
       // 2. coefficient gradient
+      float dG[BT::NG];
+      float w = 1.f;
+      if constexpr (W1) {
 #pragma unroll
-      for (int g = 0; g < FT::NG; ++g) dcoef = fmaf(dG[g], G0[g], dcoef);
+        for (int g = 0; g < BT::NG; ++g) {
+          float acc = wv.v[0] * dGw[g];
+#pragma unroll
+          for (int k = 1; k < NV; ++k) acc = fmaf(wv.v[k], dGw[k * BT::NG + g], acc);
+          dG[g] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          float acc = 0.f;
+#pragma unroll
+          for (int g = 0; g < BT::NG; ++g) acc = fmaf(dGw[k * BT::NG + g], G0[g], acc);
+          wb[k] = acc;
+        }
+      } else {
+        w = wv.v[0];
+#pragma unroll
+        for (int g = 0; g < BT::NG; ++g) dG[g] = dGw[g];
+      }
+#pragma unroll
+      for (int g = 0; g < BT::NG; ++g) dcoef = fmaf(dG[g], G0[g], dcoef);
       const float L = w * dcoef;
       const float c2 = 2.f * w * scale0;
       // 3. adjoint of G with respect to adj(J): adjb = c2 S adj, with S the
       // symmetric matrix of dG (off-diagonal entries halved); c2 is folded
       // into S once
       float adjb[D][D];
-      if constexpr (FORM != ELASTIC_P1) {
+      if constexpr (FT::BASE != ELASTIC_P1) {
         float Sc[D][D];
 #pragma unroll
         for (int r = 0; r < D; ++r)
@@ -387,25 +423,32 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
     err |= DEVERR_CONN;
   }
   if (flags & GF_ELEM) {
-    if (p.dcoef) __stcs(p.dcoef + e, dcoef);
+    if (!W1 && p.dcoef) __stcs(p.dcoef + e, dcoef);  // W1: dcoef holds vertex values (records / atomics)
     if constexpr (ATOMIC) {
       if (ok) {
 #pragma unroll
-        for (int k = 0; k < NV; ++k)
+        for (int k = 0; k < NV; ++k) {
+          if (p.dcoords)
 #pragma unroll
-          for (int a = 0; a < D; ++a) atomicAdd(p.dcoords + int64_t(vc[k]) * D + a, xb[k][a]);
+            for (int a = 0; a < D; ++a) atomicAdd(p.dcoords + int64_t(vc[k]) * D + a, xb[k][a]);
+          if (W1 && p.dcoef) atomicAdd(p.dcoef + vc[k], wb[k]);
+        }
       }
     }
   }
   if constexpr (!ATOMIC) {
     if (xs) {  // the element's slot contributions at their ranks (zeros when it is skipped)
+      constexpr int XP = BwdPlan<D, FORM>::XP;
 #pragma unroll
       for (int k = 0; k < NV; ++k) {
-        float* d = xs + ((rk >> (8 * k)) & 0xFFu) * (D == 3 ? 4 : 2);
-        if constexpr (D == 3)
-          *reinterpret_cast<float4*>(d) = make_float4(xb[k][0], xb[k][1], xb[k][2], 0.f);
-        else
+        float* d = xs + ((rk >> (8 * k)) & 0xFFu) * XP;
+        if constexpr (XP == 4) {
+          const float c2v = D == 3 ? xb[k][D - 1] : (W1 ? wb[k] : 0.f);
+          const float c3v = (D == 3 && W1) ? wb[k] : 0.f;
+          *reinterpret_cast<float4*>(d) = make_float4(xb[k][0], xb[k][1], c2v, c3v);
+        } else {
           *reinterpret_cast<float2*>(d) = make_float2(xb[k][0], xb[k][1]);
+        }
       }
     }
   }
@@ -433,7 +476,8 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
   int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
   copy_dA_async<D, FORM>(p, t, lane, dslots);
-  float wcur = (p.coef && t * 32 + lane < p.n_elem) ? __ldg(p.coef + t * 32 + lane) : 1.f;
+  Coef<FormTraits<D, FORM>::NW> wcur, wnext;
+  load_coef<D, FORM>(p.coef, t * 32 + lane, p.n_elem, p.n_vert, v1, wcur);
   float dcur = 0.f;  // saved det J (JAC_SAVED)
   if constexpr (JAC == JAC_SAVED) dcur = t * 32 + lane < p.n_elem ? __ldg(p.det + t * 32 + lane) : 0.f;
   uint32_t rkcur = 0;
@@ -453,7 +497,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     load_conn<D>(p.conn, (tn + S) * 32 + lane, p.n_elem, p.vec_conn, v2);
     const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
     copy_dA_async<D, FORM>(p, tn, lane, dslots + sn * 32 * PL::DST);
-    const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+    load_coef<D, FORM>(p.coef, en, p.n_elem, p.n_vert, v1, wnext);
     float dnext = 0.f;
     if constexpr (JAC == JAC_SAVED) dnext = en < p.n_elem ? __ldg(p.det + en) : 0.f;
     uint32_t rknext = 0;
@@ -472,7 +516,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
                                                   vc, rec ? xs : nullptr, rkcur, dcur);
     if (rec) {
       __syncwarp();  // every lane's contributions are staged
-      warp_records<D>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
+      warp_records<D, PL::NC>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
     }
     __syncwarp();  // the slot stage is rewritten next tile, the dA slot two tiles later
     fcur = fnext;
@@ -493,5 +537,41 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
 }
+
+// Launch of one instantiation of the adjoint element kernel (host).
+template <int D, int FORM, int JAC, bool ATOMIC>
+cudaError_t launch_bwd_t(const BwdLaunch& L) {
+  using PL = BwdPlan<D, FORM>;
+  BwdParams p;
+  p.conn = L.conn;
+  p.coords = L.coords;
+  p.coef = L.coef;
+  p.dA = L.dA;
+  p.tile_rec = ATOMIC ? nullptr : L.tile_rec;
+  p.rank = L.rank;
+  p.rec_span = L.rec_span;
+  p.rec_dest = L.rec_dest;
+  p.records = L.records;
+  p.dcoef = L.dcoef;
+  p.dcoords = L.dcoords;
+  p.n_elem = L.n_elem;
+  p.n_vert = L.n_vert;
+  p.dev_err = L.dev_err;
+  p.vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(L.conn) % 16 == 0);
+  p.vec_dA = reinterpret_cast<uintptr_t>(L.dA) % 16 == 0;
+  p.det = L.det_in;
+  auto kern = fem_bwd_elem_kernel<D, FORM, JAC, ATOMIC>;
+  constexpr int max_warps = BwdShape<D, FORM, JAC>::threads / 32;  // the kernel's launch bounds
+  const int want = L.warps > 0 ? L.warps : max_warps;
+  const int warps = clamp_warps(want < max_warps ? want : max_warps, PL::per_warp);
+  const size_t smem = size_t(warps) * PL::per_warp;
+  cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (st != cudaSuccess) return st;
+  const unsigned grid = pipeline_grid(reinterpret_cast<const void*>(kern), warps, smem, L.n_elem, L.ctas_per_sm);
+  kern<<<grid, warps * 32, smem, L.stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_elem_w1(const BwdLaunch& L);  // fem_bwd_w1.cu
 
 }  // namespace fem

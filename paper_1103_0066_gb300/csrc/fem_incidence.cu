@@ -377,77 +377,88 @@ __global__ void choose_layout_kernel(const int32_t* tile_rec, int64_t n_tiles, c
 // record array) in increasing record order.  The records come in blocks of 8
 // predicated loads, all in flight before the block's additions (a vertex has
 // a handful of records: one block, one round trip).
-// dcoords[v] = the sum of the records of v in increasing record order.
+// dcoords[v] = the sum of the records of v in increasing record order (and,
+// for the P1-coefficient forms, whose records carry NC = D + 1 components,
+// dcoef[v] = the sum of their last component).
 // Vertex-major layout: they are rows [voff[v], voff[v+1]), read in blocks of
 // 8 predicated loads, all in flight before the block's additions (a vertex
 // has a handful of records: one block, one round trip).  Tile-order layout:
 // they are rows vrec[voff[v] .. voff[v+1]) -- the same order, so the same
 // bits -- read as four indices, then four records, per step.  The layout word
 // is read once; the branch is uniform over the grid.
-template <int D>
+template <int D, int NC>
+__device__ __forceinline__ void reduce_store(const float (&acc)[NC], int64_t v, float* __restrict__ dcoords,
+                                             float* __restrict__ dcoef) {
+  if (dcoords)
+#pragma unroll
+    for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
+  if constexpr (NC > D) {
+    if (dcoef) dcoef[v] = acc[D];
+  }
+}
+
+template <int D, int NC>
 __device__ __forceinline__ void reduce_direct(const int32_t* __restrict__ voff, const float* __restrict__ records,
-                                              int64_t n_vert, float* __restrict__ dcoords) {
+                                              int64_t n_vert, float* __restrict__ dcoords, float* __restrict__ dcoef) {
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
     const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
-    float acc[D];
+    float acc[NC];
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int a = 0; a < NC; ++a) acc[a] = 0.f;
     for (int32_t k0 = b; k0 < e; k0 += 8) {
-      float r[8][D];
+      float r[8][NC];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int a = 0; a < D; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(k0 + u) * D + a) : 0.f;
+        for (int a = 0; a < NC; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(k0 + u) * NC + a) : 0.f;
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (k0 + u < e)
 #pragma unroll
-          for (int a = 0; a < D; ++a) acc[a] += r[u][a];
+          for (int a = 0; a < NC; ++a) acc[a] += r[u][a];
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
+    reduce_store<D, NC>(acc, v, dcoords, dcoef);
   }
 }
 
-template <int D>
+template <int D, int NC>
 __device__ __forceinline__ void reduce_gather(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
                                               const float* __restrict__ records, int64_t n_vert,
-                                              float* __restrict__ dcoords) {
+                                              float* __restrict__ dcoords, float* __restrict__ dcoef) {
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
     const int32_t b = __ldg(voff + v), e = __ldg(voff + v + 1);
-    float acc[D];
+    float acc[NC];
 #pragma unroll
-    for (int a = 0; a < D; ++a) acc[a] = 0.f;
+    for (int a = 0; a < NC; ++a) acc[a] = 0.f;
     for (int32_t k0 = b; k0 < e; k0 += 4) {
       int32_t row[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) row[u] = k0 + u < e ? __ldg(vrec + k0 + u) : 0;
-      float r[4][D];
+      float r[4][NC];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int a = 0; a < D; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(row[u]) * D + a) : 0.f;
+        for (int a = 0; a < NC; ++a) r[u][a] = k0 + u < e ? __ldg(records + int64_t(row[u]) * NC + a) : 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (k0 + u < e)
 #pragma unroll
-          for (int a = 0; a < D; ++a) acc[a] += r[u][a];
+          for (int a = 0; a < NC; ++a) acc[a] += r[u][a];
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) dcoords[v * D + a] = acc[a];
+    reduce_store<D, NC>(acc, v, dcoords, dcoef);
   }
 }
 
-template <int D>
+template <int D, int NC>
 __global__ void vertex_reduce_kernel(const int32_t* __restrict__ voff, const int32_t* __restrict__ vrec,
                                      const int32_t* __restrict__ mode, const float* __restrict__ records,
-                                     int64_t n_vert, float* __restrict__ dcoords) {
+                                     int64_t n_vert, float* __restrict__ dcoords, float* __restrict__ dcoef) {
   if (__ldg(mode) == kRecTileOrder)
-    reduce_gather<D>(voff, vrec, records, n_vert, dcoords);
+    reduce_gather<D, NC>(voff, vrec, records, n_vert, dcoords, dcoef);
   else
-    reduce_direct<D>(voff, records, n_vert, dcoords);
+    reduce_direct<D, NC>(voff, records, n_vert, dcoords, dcoef);
 }
 
 unsigned grid_for(int64_t n, int block) {
@@ -470,7 +481,8 @@ void exclusive_scan(const int32_t* cnt, int64_t n, int32_t* partials, int32_t* o
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
-                            BwdWorkspace* ws) {
+                            BwdWorkspace* ws, int ncomp) {
+  if (ncomp <= 0) ncomp = dim;
   const int64_t nv = dim + 1;
   const int64_t n_tiles = (n_elem + kRecTile - 1) / kRecTile;
   const int64_t r_max = n_elem * nv;  // at most one record per slot
@@ -492,7 +504,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
   const size_t o_cursor = take(sizeof(int32_t) * size_t(n_cnt + 1));
   const size_t o_part = take(sizeof(int32_t) * size_t(nb + 1));
   const size_t o_mode = take(sizeof(int32_t) * 2);  // layout word, locality count
-  const size_t o_records = with_scratch ? take(sizeof(float) * size_t(r_max * dim)) : off;
+  const size_t o_records = with_scratch ? take(sizeof(float) * size_t(r_max * ncomp)) : off;
   if (ws) {
     char* b = static_cast<char*>(base);
     ws->tile_rec = reinterpret_cast<int32_t*>(b + o_tile_rec);
@@ -507,6 +519,7 @@ size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_s
     ws->mode = reinterpret_cast<int32_t*>(b + o_mode);
     ws->records = with_scratch ? reinterpret_cast<float*>(b + o_records) : nullptr;
     ws->n_tiles = n_tiles;
+    ws->ncomp = ncomp;
     ws->bytes = off;
   }
   return off;
@@ -564,16 +577,25 @@ cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t stream) {
 }
 
 cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert, float* dcoords,
-                                 cudaStream_t stream) {
+                                 cudaStream_t stream, float* dcoef) {
   if (n_vert == 0) return cudaSuccess;
   const int block = 256;
-  const int64_t g = (n_vert + block - 1) / block;
-  if (dim == 2)
-    vertex_reduce_kernel<2><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert,
-                                                                dcoords);
-  else
-    vertex_reduce_kernel<3><<<unsigned(g), block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert,
-                                                                dcoords);
+  const unsigned g = unsigned((n_vert + block - 1) / block);
+  if (dim == 2) {
+    if (ws.ncomp == 3)
+      vertex_reduce_kernel<2, 3><<<g, block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert, dcoords,
+                                                          dcoef);
+    else
+      vertex_reduce_kernel<2, 2><<<g, block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert, dcoords,
+                                                          nullptr);
+  } else {
+    if (ws.ncomp == 4)
+      vertex_reduce_kernel<3, 4><<<g, block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert, dcoords,
+                                                          dcoef);
+    else
+      vertex_reduce_kernel<3, 3><<<g, block, 0, stream>>>(ws.voff, ws.vrec, ws.mode, ws.records, n_vert, dcoords,
+                                                          nullptr);
+  }
   return cudaGetLastError();
 }
 

@@ -81,8 +81,9 @@ struct BwdWorkspace {
   int32_t* cursor;
   int32_t* partials;
   int32_t* mode;  // record layout chosen by the build: kRecVertexMajor or kRecTileOrder (one word)
-  float* records;
+  float* records;   // [R][ncomp]
   int64_t n_tiles;
+  int ncomp;        // components of a record: d, or d + 1 for the P1-coefficient forms
   size_t bytes;
 };
 // Record layouts.  Vertex-major: record r is row rec_dest[r], the rows of
@@ -93,8 +94,11 @@ struct BwdWorkspace {
 // record order, so dcoords has the same bits either way.
 constexpr int32_t kRecVertexMajor = 0;
 constexpr int32_t kRecTileOrder = 1;
+// ncomp: components of a record (0 = dim; dim + 1 for the P1-coefficient
+// forms, whose records also carry the coefficient gradient).  Everything but
+// the size of the records array is independent of it.
 size_t bwd_workspace_layout(int dim, int64_t n_elem, int64_t n_vert, bool with_scratch, void* base,
-                            BwdWorkspace* ws);
+                            BwdWorkspace* ws, int ncomp = 0);
 
 cudaError_t launch_fwd_d2(const FwdLaunch& L);
 cudaError_t launch_fwd_d3_lap(const FwdLaunch& L);
@@ -121,8 +125,10 @@ size_t scan_partials_count(int64_t n);
 // offsets[0..n] = exclusive prefix sums of cnt[0..n) (offsets[n] = total).
 cudaError_t launch_exclusive_scan(const int32_t* cnt, int64_t n, int32_t* partials, int32_t* offsets,
                                   cudaStream_t stream);
+// dcoords [n_vert][dim] (may be null) and, for records of dim + 1 components,
+// dcoef [n_vert] (may be null) from the records of the workspace.
 cudaError_t launch_vertex_reduce(int dim, const BwdWorkspace& ws, int64_t n_vert, float* dcoords,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, float* dcoef = nullptr);
 
 // Records the reason reported by fem_last_error() for the calling thread.
 void set_last_error(const char* fmt, ...);
@@ -139,6 +145,8 @@ namespace fem {
 // fem_last_error() message; 0 (FEM_OK) when the call may proceed.
 int32_t bwd_preflight(const fem_mesh* mesh, int32_t form, const fem_options* options, const float* dA,
                       const float* dcoords);
+// Whether fem_integrate_bwd reduces through the workspace for these outputs.
+bool bwd_needs_workspace(int32_t form, bool has_dcoords, bool has_dcoef, int32_t reduce);
 
 // Device facts of the current device (cached per device).
 int device_sm_count();

@@ -68,8 +68,9 @@ fem_status fem_integrate_bwd_noalloc(const fem_mesh* mesh, int32_t form, const f
   // launches nothing and leaves the array as the last accepted call left it.
   fem_status s = static_cast<fem_status>(fem::bwd_preflight(mesh, form, &o, dA, dcoords));
   if (s != FEM_OK) return s;
-  if (!dcoords) {  // only the coefficient gradient: no scratch is involved
-    return fem_integrate_bwd(mesh, form, coef, dA, nullptr, dcoef, nullptr, 0, &o, stream);
+  if (!fem::bwd_needs_workspace(form, dcoords != nullptr, dcoef != nullptr, o.reduce)) {
+    // only a per-element coefficient gradient: no scratch is involved
+    return fem_integrate_bwd(mesh, form, coef, dA, dcoords, dcoef, nullptr, 0, &o, stream);
   }
   size_t need = 0;
   if ((s = fem_bwd_workspace_size(mesh, form, &o, &need)) != FEM_OK) return s;

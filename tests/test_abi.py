@@ -236,7 +236,14 @@ def test_saved_det_and_iso_contract_errors_on_host(fem):
     tc = nat.options_struct(contract=nat.CONTRACT_BF16X3)
     assert lib.fem_integrate_fwd_save(ctypes.byref(m), EP1, None, A, 0, A, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
     assert lib.fem_integrate_bwd_saved(ctypes.byref(m), LP1, None, A, None, A, None, None, 0, None, None) == nat.FEM_ERR_ARG
-    assert lib.fem_integrate_bwd_saved(ctypes.byref(m), 3, None, A, A, A, None, None, 0, None, None) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_integrate_bwd_saved(ctypes.byref(m), 5, None, A, A, A, None, None, 0, None, None) == nat.FEM_ERR_UNSUPPORTED
+    # the P1-coefficient adjoint reduces dcoef through the workspace: missing workspace
+    assert lib.fem_integrate_bwd_saved(ctypes.byref(m), 3, None, A, A, A, None, None, 0, None, None) == nat.FEM_ERR_WORKSPACE
+    b = ctypes.c_size_t()
+    assert lib.fem_bwd_workspace_size(ctypes.byref(m), 3, None, ctypes.byref(b)) == nat.FEM_OK
+    b0 = ctypes.c_size_t()
+    assert lib.fem_bwd_workspace_size(ctypes.byref(m), LP1, None, ctypes.byref(b0)) == nat.FEM_OK
+    assert b.value > b0.value  # records of d + 1 components
     me = _mesh(fem, n_elem=0)
     assert lib.fem_integrate_fwd_save(ctypes.byref(me), LP1, None, None, 0, None, None, None) == nat.FEM_OK
     assert lib.fem_integrate_fwd_iso(ctypes.byref(m), 5, A, None, A, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED

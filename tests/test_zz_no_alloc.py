@@ -115,3 +115,25 @@ def test_noalloc_refusals_launch_nothing(gfem):
     ref_x, ref_w = gfem.integrate_bwd(coords, conn, 0, dA, coef)
     got_x, got_w = _noalloc(gfem, coords, conn, 0, dA, coef)
     assert torch.equal(got_x, ref_x) and torch.equal(got_w, ref_w)
+
+
+def test_noalloc_p1_coefficient_gradient(gfem):
+    """The P1-coefficient Laplacian, whose coefficient gradient is summed over
+    the vertices through the scratch records even without dcoords."""
+    mesh = _case(3, 8, 74)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    wv = _t(mg.lognormal_coef(mg.rng_for(75), mesh.n_vert))
+    dA = _t(mg.upstream(mg.rng_for(76), mesh.n_elem, 10))
+    ref_x, ref_w = gfem.integrate_bwd(coords, conn, 4, dA, wv)
+    nat = gfem.nat
+    m = gfem._mesh_struct(coords, conn)
+    for want_x in (True, False):
+        dx = torch.full((mesh.n_vert, 3), float("nan"), device=DEV) if want_x else None
+        dw = torch.full((mesh.n_vert,), float("nan"), device=DEV)
+        st = nat.load().fem_integrate_bwd_noalloc(
+            ctypes.byref(m), 4, ctypes.c_void_p(wv.data_ptr()), ctypes.c_void_p(dA.data_ptr()),
+            ctypes.c_void_p(dx.data_ptr() if dx is not None else 0), ctypes.c_void_p(dw.data_ptr()),
+            ctypes.byref(nat.options_struct()), None)
+        assert st == nat.FEM_OK, nat.load().fem_last_error().decode()
+        torch.cuda.synchronize()
+        assert torch.equal(dw, ref_w) and (dx is None or torch.equal(dx, ref_x))
