@@ -53,13 +53,16 @@ KERNEL_SOURCES = {
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# 128^3 sliver cube from one ncu launch-list capture of the bench command.
+# 128^3 sliver cube (12,582,912 tets).  A capture with DRAM counters stays on a
+# smaller case, so these are the 96^3 cube's figures (one ncu capture of two
+# launches each, 5,308,416 tets, 4,852,051 records) scaled by the elements per
+# launch (x 2.370): records and vertices grow in the same proportion.  The
+# forward's and the reduction's scaled figures are lower bounds: the part of
+# their output still dirty in L2 when the kernel ends does not grow with it.
 NCU_TRAFFIC = {
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1349.6e6, "src": "df0ffcaa0a6fd82e"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 1033.0e6, "src": "1669d2556ed01ef5"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 162.2e6, "src": "641d31086653a833"},
-    # tile pass (1360.1 MB) + entry pass (1034.3 MB) of one fem_assemble call
-    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2393.9e6, "src": "8f8dded890714508"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1316.4e6, "src": "978633ac72b6def2"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 958.5e6, "src": "fafe78917a5a36fb"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.3e6, "src": "8310deb034b51e68"},
 }
 
 
