@@ -385,8 +385,9 @@ def run_ours(args):
         dA_hp = torch.from_numpy(dA_h).pin_memory()
         A_h = torch.empty_like(A, device="cpu").pin_memory()
         dc_h = torch.empty_like(dcoords, device="cpu").pin_memory()
-        # HostStep: per slice of elements, copies in, the forward and copies out
-        # overlap on three streams; the adjoint follows the last slice
+        # HostStep (the C ABI's fem_host_step_run): per slice of elements, the
+        # copies in, the forward, the adjoint element pass and the copies out
+        # overlap on three streams
         hs = fem.HostStep(V, E, 3, fem.LAPLACE_P1, device=dev)
 
         def e2e_step(rep=None, k=None):
@@ -401,8 +402,9 @@ def run_ours(args):
         e2e = {"value": ws_n * E / (me["ms_per_step"] * 1e-3), "unit": "elements/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": me["ms_per_step"], "ms_min": me["ms_min"],
                "ms_max": me["ms_max"], "steps": e2e_steps, "repeats": me["repeats"], "clocks": me["clocks"],
-               "path": f"HostStep.run: pinned host buffers, {hs.chunk:,}-element slices, copies in, forward "
-                       "and copies out overlapped on three streams, then the adjoint and dcoords out",
+               "path": f"fem_host_step_run (C ABI) through HostStep.run: pinned host buffers, {hs.chunk:,}-element "
+                       "slices; copies in, forward, adjoint element pass and copies out overlapped on three "
+                       "streams, then the reduction and dcoords out",
                "bitwise_equal_to_device_path": match}
 
     order = "elements in random order, vertices renumbered at random" if shuffled else "cell-major element order"

@@ -442,6 +442,42 @@ FEM_API fem_status fem_integrate_bwd_noalloc(const fem_mesh* mesh, int32_t form,
                                              const float* dA, float* dcoords, float* dcoef,
                                              const fem_options* options, void* stream);
 
+/* ---- End-to-end step from host memory ----------------------------------
+ * One mesh whose inputs and outputs live in page-locked host memory: a step
+ * copies coords, conn and the upstream dA to the device, integrates A = G:K
+ * (Eq. 6) saving det J, runs the deterministic adjoint taking it, and copies A
+ * and dcoords back.  The elements go in slices of `chunk` elements (a multiple
+ * of 32): one copy stream sends the coordinates, then each slice's
+ * connectivity and dA; the forward of a slice starts when its connectivity
+ * has arrived, its adjoint element pass when its dA has (on steps that reuse
+ * the incidence); a second copy stream returns each slice's A once written,
+ * and dcoords after the reduction.  Results are bitwise those of
+ * fem_integrate_fwd_save + fem_integrate_bwd_saved on the device.
+ *
+ * fem_host_step_create: form FEM_LAPLACE_P1, FEM_LAPLACE_P2 or
+ *   FEM_ELASTIC_P1, dim 2 or 3, n_vert/n_elem > 0, chunk > 0 (rounded up to a
+ *   multiple of 32; 0 = 1 << 20).  Allocates the device arrays (coords, conn,
+ *   dA, A, det, dcoords and the adjoint workspace) on the current device and
+ *   two copy streams; *step owns them.  FEM_ERR_CUDA if an allocation fails.
+ * fem_host_step_run: coords [n_vert][dim] FP32, conn [n_elem][dim+1] int32,
+ *   dA [n_elem][n][n] FP32 (read); A [n_elem][n][n] FP32 and dcoords
+ *   [n_vert][dim] FP32 (written): page-locked host memory (cudaHostAlloc or
+ *   cudaHostRegister; FEM_ERR_ARG otherwise), on the step's device.  rebuild
+ *   != 0 rebuilds the incidence (a new connectivity); the first run always
+ *   builds it.  Asynchronous on `stream`: the step is done, and the host
+ *   buffers may be reused, when the work queued on `stream` so far is.  The
+ *   next run on the same step must be queued on the same stream (it reuses the
+ *   device arrays).
+ * fem_host_step_destroy: waits for the step's copy streams and frees what
+ *   create allocated; call it after `stream` has finished the last run. */
+typedef struct fem_host_step fem_host_step; /* opaque; host object */
+
+FEM_API fem_status fem_host_step_create(int32_t form, int32_t dim, int64_t n_vert, int64_t n_elem, int64_t chunk,
+                                        fem_host_step** step);
+FEM_API fem_status fem_host_step_run(fem_host_step* step, const float* coords, const int32_t* conn,
+                                     const float* dA, float* A, float* dcoords, int32_t rebuild, void* stream);
+FEM_API void fem_host_step_destroy(fem_host_step* step);
+
 #ifdef __cplusplus
 }
 #endif

@@ -249,87 +249,55 @@ def adjoint_reduce(coords, conn, ws: Workspace, dcoords, stream=None):
 
 class HostStep:
     """Forward and adjoint of one mesh whose inputs and outputs live in pinned
-    host memory, with the host <-> device copies overlapped with the kernels.
+    host memory (the C ABI's fem_host_step_*).
 
-    run() copies coords, conn and dA in, integrates A = G:K (Eq. 6) and the
-    deterministic adjoint (with det J kept from the forward), and copies A and
-    dcoords out.  The elements go in
-    slices of `chunk` elements:
-
-    * a copy-in stream sends the coordinates, then each slice's connectivity
-      and dA;
-    * the caller's stream integrates each slice's A as soon as its
-      connectivity has arrived (elements are independent);
-    * a copy-out stream returns each slice's A as soon as it is written.
-
-    The adjoint needs every slice's dA, so it and the reduction run after the
-    last slice, then dcoords goes out.  Copies in the two directions and the
-    kernels overlap; the results equal the device path's bit for bit.  The
-    caller's stream waits for the copies out, so an event recorded on it after
-    run() marks the step's end."""
+    run() copies coords, conn and dA in, integrates A = G:K (Eq. 6) saving
+    det J, runs the deterministic adjoint taking it, and copies A and dcoords
+    out.  The library splits the elements in slices of `chunk` elements: a
+    copy-in stream sends the coordinates, then each slice's connectivity and
+    dA; the caller's stream runs each slice's forward as soon as its
+    connectivity has arrived and, once the incidence is built, its adjoint
+    element pass as soon as its dA has; a copy-out stream returns each slice's
+    A as soon as it is written, and dcoords after the reduction.  The results
+    equal the device path's bit for bit.  The caller's stream waits for the
+    copies out, so an event recorded on it after run() marks the step's end."""
 
     def __init__(self, n_vert, n_elem, dim=3, form=LAPLACE_P1, chunk=1 << 20, device="cuda"):
         if form not in (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1):
             raise ValueError("HostStep takes LAPLACE_P1, LAPLACE_P2 or ELASTIC_P1")
-        dev = torch.device(device)
+        self.device = torch.device(device)
         n, _, _ = form_info(form, dim)
         self.form, self.dim, self.n = form, dim, n
+        self.n_vert, self.n_elem = int(n_vert), int(n_elem)
         self.chunk = max(32, (int(chunk) + 31) // 32 * 32)
-        self.coords = torch.empty((n_vert, dim), dtype=torch.float32, device=dev)
-        self.conn = torch.empty((n_elem, dim + 1), dtype=torch.int32, device=dev)
-        self.dA = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
-        self.A = torch.empty((n_elem, n, n), dtype=torch.float32, device=dev)
-        self.dcoords = torch.empty((n_vert, dim), dtype=torch.float32, device=dev)
-        self.det = torch.empty(n_elem, dtype=torch.float32, device=dev)  # det J, forward -> adjoint
-        self.copy_in = torch.cuda.Stream(dev)
-        self.copy_out = torch.cuda.Stream(dev)
-        self.ws = None  # built on the first run: it depends on the connectivity
+        with torch.cuda.device(self.device):
+            self._h = _native.fem_host_step_create(form, dim, self.n_vert, self.n_elem, self.chunk)
+        self._built = False
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            torch.cuda.synchronize(self.device)
+            _native.fem_host_step_destroy(h)
+            self._h = None
 
     @staticmethod
-    def _check(t, like, name):
-        if t.is_cuda or not t.is_pinned() or t.shape != like.shape or t.dtype != like.dtype or not t.is_contiguous():
-            raise ValueError(f"{name} must be a contiguous pinned host tensor {tuple(like.shape)} {like.dtype}")
+    def _check(t, shape, dtype, name):
+        if t.is_cuda or not t.is_pinned() or tuple(t.shape) != shape or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous pinned host tensor {shape} {dtype}")
 
     def run(self, coords_h, conn_h, dA_h, A_h, dcoords_h, rebuild=False):
         """One step; rebuild=True rebuilds the adjoint's incidence (new connectivity)."""
-        for t, like, name in ((coords_h, self.coords, "coords"), (conn_h, self.conn, "conn"),
-                              (dA_h, self.dA, "dA"), (A_h, self.A, "A"), (dcoords_h, self.dcoords, "dcoords")):
-            self._check(t, like, name)
-        main = torch.cuda.current_stream(self.coords.device)
-        E, C = self.conn.shape[0], self.chunk
-        self.copy_in.wait_stream(main)  # the previous step no longer reads the device inputs
-        with torch.cuda.stream(self.copy_in):
-            self.coords.copy_(coords_h, non_blocking=True)
-        slices = [(e0, min(E, e0 + C)) for e0 in range(0, E, C)]
-        arrived, written = [], []
-        for e0, e1 in slices:
-            with torch.cuda.stream(self.copy_in):
-                self.conn[e0:e1].copy_(conn_h[e0:e1], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self.copy_in)
-                self.dA[e0:e1].copy_(dA_h[e0:e1], non_blocking=True)
-            arrived.append(ev)
-        if self.ws is None or rebuild:
-            main.wait_stream(self.copy_in)
-            self.ws = Workspace(self.coords, self.conn, self.form, main)
-        for (e0, e1), ev in zip(slices, arrived):
-            main.wait_event(ev)
-            integrate_fwd(self.coords, self.conn[e0:e1], self.form, out=self.A[e0:e1], stream=main,
-                          det_out=self.det[e0:e1])
-            done = torch.cuda.Event()
-            done.record(main)
-            written.append(done)
-        for (e0, e1), done in zip(slices, written):
-            self.copy_out.wait_event(done)
-            with torch.cuda.stream(self.copy_out):
-                A_h[e0:e1].copy_(self.A[e0:e1], non_blocking=True)
-        main.wait_stream(self.copy_in)  # every dA slice is in
-        integrate_bwd(self.coords, self.conn, self.form, self.dA, ws=self.ws, need_dcoef=False,
-                      dcoords=self.dcoords, stream=main, det=self.det)
-        self.copy_out.wait_stream(main)
-        with torch.cuda.stream(self.copy_out):
-            dcoords_h.copy_(self.dcoords, non_blocking=True)
-        main.wait_stream(self.copy_out)
+        V, E, d, n = self.n_vert, self.n_elem, self.dim, self.n
+        for t, shape, dtype, name in ((coords_h, (V, d), torch.float32, "coords"),
+                                      (conn_h, (E, d + 1), torch.int32, "conn"),
+                                      (dA_h, (E, n, n), torch.float32, "dA"), (A_h, (E, n, n), torch.float32, "A"),
+                                      (dcoords_h, (V, d), torch.float32, "dcoords")):
+            self._check(t, shape, dtype, name)
+        stream = torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            _native.fem_host_step_run(self._h, coords_h.data_ptr(), conn_h.data_ptr(), dA_h.data_ptr(),
+                                      A_h.data_ptr(), dcoords_h.data_ptr(), rebuild, stream.cuda_stream)
         return A_h, dcoords_h
 
 

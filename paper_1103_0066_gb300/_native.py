@@ -29,7 +29,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
-           "fem_integrate_bwd_saved")
+           "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
@@ -109,6 +109,9 @@ def load():
                                    ctypes.c_int),
             "fem_assembly_pattern": ([MP, I32, P, SZ, ctypes.POINTER(P), ctypes.POINTER(P)], ctypes.c_int),
             "fem_assemble": ([MP, I32, P, P, SZ, P, P], ctypes.c_int),
+            "fem_host_step_create": ([I32, I32, I64, I64, I64, ctypes.POINTER(P)], ctypes.c_int),
+            "fem_host_step_run": ([P, P, P, P, P, P, I32, P], ctypes.c_int),
+            "fem_host_step_destroy": ([P], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -294,3 +297,19 @@ def fem_assemble(mesh: FemMesh, form: int, A_ptr: int, ws_ptr: int, ws_bytes: in
                  stream: int) -> None:
     check(load().fem_assemble(ctypes.byref(mesh), form, A_ptr or None, ws_ptr, ws_bytes, values_ptr or None,
                               stream or None))
+
+
+def fem_host_step_create(form: int, dim: int, n_vert: int, n_elem: int, chunk: int) -> int:
+    h = ctypes.c_void_p()
+    check(load().fem_host_step_create(form, dim, n_vert, n_elem, chunk, ctypes.byref(h)))
+    return h.value
+
+
+def fem_host_step_run(handle: int, coords_ptr: int, conn_ptr: int, dA_ptr: int, A_ptr: int, dcoords_ptr: int,
+                      rebuild: bool, stream: int) -> None:
+    check(load().fem_host_step_run(handle, coords_ptr or None, conn_ptr or None, dA_ptr or None, A_ptr or None,
+                                   dcoords_ptr or None, 1 if rebuild else 0, stream or None))
+
+
+def fem_host_step_destroy(handle: int) -> None:
+    load().fem_host_step_destroy(handle)

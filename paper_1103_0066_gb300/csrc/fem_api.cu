@@ -150,6 +150,48 @@ bool bwd_needs_workspace(int32_t form, bool has_dcoords, bool has_dcoef, int32_t
   return bwd_uses_records(form, has_dcoords, has_dcoef, reduce);
 }
 
+int32_t bwd_element_range(const fem_mesh* mesh, int32_t form, const float* dA, const float* det, void* ws,
+                          size_t ws_bytes, int64_t e0, int64_t e1, cudaStream_t stream) {
+  if (e0 < 0 || e1 > mesh->n_elem || e0 > e1 || e0 % kRecTile != 0)
+    return fail(FEM_ERR_ARG, "element range [%lld, %lld) must start on a tile of %d elements",
+                static_cast<long long>(e0), static_cast<long long>(e1), kRecTile);
+  fem::BwdWorkspace W{};
+  const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W,
+                                                record_components(form, mesh->dim));
+  if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+  if (e1 == e0) return ok();
+  const int64_t rows = form_rows(form, mesh->dim), cols = form_cols(form, mesh->dim);
+  fem::BwdLaunch L{};
+  L.dim = mesh->dim;
+  L.form = form;
+  L.jac = resolve_jac(FEM_JAC_AUTO, false, false);
+  L.atomic = 0;
+  // the element pass of elements [e0, e1) is the whole-mesh pass's restricted to
+  // their tiles: per-element and per-tile arrays start at the range, the records
+  // (indexed by the tile offsets) stay the whole mesh's
+  L.conn = mesh->conn + e0 * (mesh->dim + 1);
+  L.coords = static_cast<const float*>(mesh->coords);
+  L.coef = nullptr;
+  L.dA = dA + e0 * rows * cols;
+  L.dcoef = nullptr;
+  L.tile_rec = W.tile_rec + e0 / kRecTile;
+  L.rank = W.rank + e0;
+  L.rec_span = W.rec_span;
+  L.rec_dest = W.rec_dest;
+  L.records = W.records;
+  L.dcoords = nullptr;
+  L.n_elem = e1 - e0;
+  L.n_vert = mesh->n_vert;
+  L.dev_err = nullptr;
+  L.warps = 0;
+  L.ctas_per_sm = 0;
+  L.stream = stream;
+  L.det_in = det + e0;
+  const cudaError_t e = fem::launch_bwd_elem(L);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint element pass launch");
+  return ok();
+}
+
 void set_last_error(const char* fmt, ...) {
   va_list ap;
   va_start(ap, fmt);

@@ -147,6 +147,13 @@ int32_t bwd_preflight(const fem_mesh* mesh, int32_t form, const fem_options* opt
                       const float* dcoords);
 // Whether fem_integrate_bwd reduces through the workspace for these outputs.
 bool bwd_needs_workspace(int32_t form, bool has_dcoords, bool has_dcoef, int32_t reduce);
+// Element pass of the deferred deterministic adjoint, with det J saved by the
+// forward, over elements [e0, e1) of `mesh` (e0 a multiple of 32): writes the
+// records of those elements' tiles into the workspace built for the whole mesh.
+// Affine FP32 forms (LAPLACE_P1, LAPLACE_P2, ELASTIC_P1) without coefficient;
+// the caller has validated mesh and form.  Returns a fem_status.
+int32_t bwd_element_range(const fem_mesh* mesh, int32_t form, const float* dA, const float* det, void* ws,
+                          size_t ws_bytes, int64_t e0, int64_t e1, cudaStream_t stream);
 
 // Device facts of the current device (cached per device).
 int device_sm_count();

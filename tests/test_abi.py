@@ -247,3 +247,20 @@ def test_saved_det_and_iso_contract_errors_on_host(fem):
     me = _mesh(fem, n_elem=0)
     assert lib.fem_integrate_fwd_save(ctypes.byref(me), LP1, None, None, 0, None, None, None) == nat.FEM_OK
     assert lib.fem_integrate_fwd_iso(ctypes.byref(m), 5, A, None, A, ctypes.byref(tc), None) == nat.FEM_ERR_UNSUPPORTED
+
+
+def test_host_step_refusals_on_host(fem):
+    """fem_host_step_*: every argument refusal comes before any CUDA call."""
+    nat = fem.nat
+    lib = nat.load()
+    h = ctypes.c_void_p()
+    assert lib.fem_host_step_create(nat.DIV_P1P1, 3, 10, 10, 0, ctypes.byref(h)) == nat.FEM_ERR_UNSUPPORTED
+    assert lib.fem_host_step_create(LP1, 3, 10, 10, 0, None) == nat.FEM_ERR_ARG
+    assert lib.fem_host_step_create(LP1, 4, 10, 10, 0, ctypes.byref(h)) == nat.FEM_ERR_ARG
+    assert lib.fem_host_step_create(LP1, 3, 0, 10, 0, ctypes.byref(h)) == nat.FEM_ERR_ARG
+    assert lib.fem_host_step_create(LP1, 3, 10, 10, -1, ctypes.byref(h)) == nat.FEM_ERR_ARG
+    assert lib.fem_host_step_create(LP1, 3, 10, 1 << 30, 0, ctypes.byref(h)) == nat.FEM_ERR_UNSUPPORTED
+    assert not h.value
+    p = ctypes.c_void_p(0x3000)
+    assert lib.fem_host_step_run(None, p, p, p, p, p, 0, None) == nat.FEM_ERR_ARG
+    lib.fem_host_step_destroy(None)  # no-op
