@@ -322,6 +322,15 @@ def run_ours(args):
     det = torch.empty(E, dtype=torch.float32, device=dev)  # det J kept from the forward for the adjoint
     ev_store = []  # per-kernel events of the timed steps (fwd | bwd_elem | reduce | exchange)
 
+    # launch shapes of the forward and the adjoint element pass chosen by the
+    # autotuner on this mesh (fem_tune_fwd / fem_tune_bwd), before any timing
+    shapes = {"fwd": (0, 0, None), "bwd_elem": (0, 0, None)}
+    if not args.no_tune:
+        shapes["fwd"] = fem.tune_fwd(coords, conn, fem.LAPLACE_P1, out=A, det_out=det)
+        shapes["bwd_elem"] = fem.tune_bwd(coords, conn, fem.LAPLACE_P1, dA, ws=ws, reduce=fem.REDUCE_DEFERRED,
+                                          det=det, dcoords=dcoords)
+    (wf, cf, _), (wb, cb, _) = shapes["fwd"], shapes["bwd_elem"]
+
     def step(rep=None, k=None):
         evs = None
         if rep is not None and len(ev_store) < 4000:
@@ -329,11 +338,11 @@ def run_ours(args):
             ev_store.append(evs)
         if evs is not None:
             evs[0].record(stream)
-        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A, det_out=det)
+        fem.integrate_fwd(coords, conn, fem.LAPLACE_P1, out=A, det_out=det, warps_per_cta=wf, ctas_per_sm=cf)
         if evs is not None:
             evs[1].record(stream)
         fem.integrate_bwd(coords, conn, fem.LAPLACE_P1, dA, ws=ws, reduce=fem.REDUCE_DEFERRED,
-                          dcoords=dcoords, need_dcoef=False, det=det)
+                          dcoords=dcoords, need_dcoef=False, det=det, warps_per_cta=wb, ctas_per_sm=cb)
         if evs is not None:
             evs[2].record(stream)
         fem.adjoint_reduce(coords, conn, ws, dcoords)
@@ -435,7 +444,11 @@ def run_ours(args):
                         "frac_of_peak": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / peak,
                         "frac_of_nominal": sum(byts.values()) / (ms_step * 1e-3) / 1e9 / NOMINAL_HBM_GBS},
         "setup": {"incidence_build_ms": setup_ms, "records": R, "slots": 4 * E,
-                  "record_layout": {0: "vertex-major", 1: "tile order"}.get(ws.record_layout(), "?")},
+                  "record_layout": {0: "vertex-major", 1: "tile order"}.get(ws.record_layout(), "?"),
+                  "launch_shapes": {k: {"warps_per_cta": v[0], "ctas_per_sm": v[1], "tuned_ms": v[2],
+                                        "chosen_by": "default (--no-tune)" if v[2] is None else
+                                        "fem_tune_fwd / fem_tune_bwd on this mesh"}
+                                    for k, v in shapes.items()}},
         "e2e": e2e,
         "gpu_launches": 3 * K,  # per K-step timed region: forward, element pass, reduction
         "gpu_launches_all_repeats": 3 * K * m["repeats"],
@@ -1160,6 +1173,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu", action="store_true", help="skip the timed oracle leg")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="default launch shapes instead of the autotuner's (tet128 workloads)")
     ap.add_argument("--mesh-n", type=int, default=128, help="cells per cube edge (128 = the benchmark mesh)")
     ap.add_argument("--cpu-sample", type=int, default=12_582_912)
     ap.add_argument("--workload", choices=["tet128", "tet128_shuffled", "batch96", "elastic128", "adjoint64",

@@ -442,6 +442,32 @@ FEM_API fem_status fem_integrate_bwd_noalloc(const fem_mesh* mesh, int32_t form,
                                              const float* dA, float* dcoords, float* dcoef,
                                              const fem_options* options, void* stream);
 
+/* ---- Launch-shape autotuner of the single-mesh kernels -------------------
+ * The paper tunes its kernel's block shape (elements per block and elements
+ * computed concurrently) by measurement on its workload (Sec. 5).  These
+ * calls do the same for one mesh and form on this GPU: they time the call
+ * (CUDA events on `stream`, 2 untimed and 5 timed launches per candidate) for
+ * every candidate (warps_per_cta, ctas_per_sm) pair the kernel's compiled
+ * shape admits, and write the fastest pair into options->warps_per_cta and
+ * options->ctas_per_sm; *best_ms (may be NULL) receives its time per call.
+ * The other fields of *options are the options every candidate runs with.
+ * The default pair (0, 0) is always a candidate, so the result is never
+ * slower than the default as measured.  Candidates: warps_per_cta in
+ * {0, 1, 2, 4, 8} times ctas_per_sm in {0, 2, 4, 8, 16, 24, 32}; a kernel
+ * compiled for fewer warps per CTA (one, for the compensated 3D P1
+ * Laplacian) runs the largest count it admits.  The candidates run on the
+ * caller's buffers: A (fem_tune_fwd) and dcoords / dcoef (fem_tune_bwd) are
+ * overwritten, with the values of one call.  Synchronizes `stream`.
+ * fem_tune_fwd: arguments of fem_integrate_fwd_save (det may be NULL: then
+ *   fem_integrate_fwd is timed).
+ * fem_tune_bwd: arguments of fem_integrate_bwd_saved (det may be NULL: then
+ *   fem_integrate_bwd is timed); the workspace must be built. */
+FEM_API fem_status fem_tune_fwd(const fem_mesh* mesh, int32_t form, const float* coef, void* A, int32_t out_dtype,
+                                float* det, fem_options* options, float* best_ms, void* stream);
+FEM_API fem_status fem_tune_bwd(const fem_mesh* mesh, int32_t form, const float* coef, const float* dA,
+                                const float* det, float* dcoords, float* dcoef, void* ws, size_t ws_bytes,
+                                fem_options* options, float* best_ms, void* stream);
+
 /* ---- End-to-end step from host memory ----------------------------------
  * One mesh whose inputs and outputs live in page-locked host memory: a step
  * copies coords, conn and the upstream dA to the device, integrates A = G:K

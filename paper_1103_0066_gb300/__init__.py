@@ -247,6 +247,102 @@ def adjoint_reduce(coords, conn, ws: Workspace, dcoords, stream=None):
     return dcoords
 
 
+def tune_fwd(coords, conn, form, coef=None, out=None, jac=JAC_AUTO, det_out=None, stream=None):
+    """fem_tune_fwd: the fastest (warps_per_cta, ctas_per_sm) of integrate_fwd
+    for this mesh and form, and its time per call in ms.  `out` (allocated if
+    None) and `det_out` receive the values of one call."""
+    m = _mesh_struct(coords, conn)
+    rows, cols = form_shape(form, m.dim)
+    E = conn.shape[0]
+    if out is None:
+        out = torch.empty((E, rows, cols), dtype=torch.float32, device=coords.device)
+    w1 = form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
+    cp = _coef_ptr(coef, coords.shape[0], "[V]") if w1 else _coef_ptr(coef, E)
+    if det_out is not None:
+        _check_det(det_out, E)
+    opts = nat.options_struct(jac, 0, 0, 0, 0, 0)
+    ms = nat.fem_tune_fwd(m, form, cp, out.data_ptr(), F64 if out.dtype == torch.float64 else F32,
+                          det_out.data_ptr() if det_out is not None else 0, opts, _stream_ptr(stream))
+    return opts.warps_per_cta, opts.ctas_per_sm, ms
+
+
+def tune_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None, reduce=REDUCE_DETERMINISTIC,
+             need_dcoef=False, jac=JAC_AUTO, det=None, dcoords=None, stream=None):
+    """fem_tune_bwd: the fastest (warps_per_cta, ctas_per_sm) of integrate_bwd
+    (dcoords, and dcoef if need_dcoef) for this mesh and form, and its time
+    per call in ms."""
+    m = _mesh_struct(coords, conn)
+    E, V = conn.shape[0], coords.shape[0]
+    w1 = form in (LAPLACE_P1_W1, LAPLACE_P2_W1)
+    if dcoords is None:
+        dcoords = torch.empty((V, m.dim), dtype=torch.float32, device=coords.device)
+    dcoef = torch.empty(V if w1 else E, dtype=torch.float32, device=coords.device) if need_dcoef else None
+    if ws is None and reduce != REDUCE_ATOMIC:
+        ws = Workspace(coords, conn, form, stream)
+    ws_ptr, ws_bytes = (ws.buf.data_ptr(), ws.bytes) if ws is not None else (0, 0)
+    cp = _coef_ptr(coef, V, "[V]") if w1 else _coef_ptr(coef, E)
+    if det is not None:
+        _check_det(det, E)
+    opts = nat.options_struct(jac, 0, reduce, 0, 0, 0)
+    ms = nat.fem_tune_bwd(m, form, cp, dA.data_ptr(), det.data_ptr() if det is not None else 0, dcoords.data_ptr(),
+                          dcoef.data_ptr() if dcoef is not None else 0, ws_ptr, ws_bytes, opts, _stream_ptr(stream))
+    return opts.warps_per_cta, opts.ctas_per_sm, ms
+
+
+class TuneCache:
+    """Launch shapes chosen by tune_fwd / tune_bwd, kept in a JSON file: one
+    entry per (GPU name, phase, form, dim, Jacobian mode, floor(log2 E)), so
+    a mesh of another size in the same power-of-two bucket reuses the shape
+    without tuning.  The file is `path`, else $FEM_TUNE_CACHE, else
+    ~/.cache/paper_1103_0066_gb300/tune.json."""
+
+    def __init__(self, path=None):
+        import os
+        self.path = path or os.environ.get("FEM_TUNE_CACHE") or os.path.join(
+            os.path.expanduser("~"), ".cache", "paper_1103_0066_gb300", "tune.json")
+        self.entries = {}
+        try:
+            import json
+            with open(self.path) as f:
+                self.entries = json.load(f)
+        except (OSError, ValueError):
+            self.entries = {}
+
+    @staticmethod
+    def key(phase, form, dim, jac, n_elem, gpu_name):
+        name = gpu_name.replace(" ", "_")
+        return f"{name}/{phase}/{form}/{dim}/{jac}/{max(int(n_elem), 1).bit_length() - 1}"
+
+    def _save(self):
+        import json
+        import os
+        os.makedirs(os.path.dirname(self.path) or ".", exist_ok=True)
+        tmp = self.path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(self.entries, f, indent=1, sort_keys=True)
+        os.replace(tmp, self.path)
+
+    def fwd(self, coords, conn, form, jac=JAC_AUTO, **kw):
+        """(warps_per_cta, ctas_per_sm) for integrate_fwd, tuned on a miss."""
+        k = self.key("fwd", form, conn.shape[1] - 1, jac, conn.shape[0], torch.cuda.get_device_name(coords.device))
+        if k not in self.entries:
+            w, c, ms = tune_fwd(coords, conn, form, jac=jac, **kw)
+            self.entries[k] = {"warps_per_cta": w, "ctas_per_sm": c, "ms": ms, "n_elem": int(conn.shape[0])}
+            self._save()
+        e = self.entries[k]
+        return e["warps_per_cta"], e["ctas_per_sm"]
+
+    def bwd(self, coords, conn, form, dA, jac=JAC_AUTO, **kw):
+        """(warps_per_cta, ctas_per_sm) for integrate_bwd, tuned on a miss."""
+        k = self.key("bwd", form, conn.shape[1] - 1, jac, conn.shape[0], torch.cuda.get_device_name(coords.device))
+        if k not in self.entries:
+            w, c, ms = tune_bwd(coords, conn, form, dA, jac=jac, **kw)
+            self.entries[k] = {"warps_per_cta": w, "ctas_per_sm": c, "ms": ms, "n_elem": int(conn.shape[0])}
+            self._save()
+        e = self.entries[k]
+        return e["warps_per_cta"], e["ctas_per_sm"]
+
+
 class HostStep:
     """Forward and adjoint of one mesh whose inputs and outputs live in pinned
     host memory (the C ABI's fem_host_step_*).

@@ -29,7 +29,8 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_workspace_size", "fem_batch_create", "fem_batch_tune", "fem_batch_config", "fem_batch_set_config", "fem_batch_run",
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
-           "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy")
+           "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy", "fem_tune_fwd",
+           "fem_tune_bwd")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
@@ -112,6 +113,8 @@ def load():
             "fem_host_step_create": ([I32, I32, I64, I64, I64, ctypes.POINTER(P)], ctypes.c_int),
             "fem_host_step_run": ([P, P, P, P, P, P, I32, P], ctypes.c_int),
             "fem_host_step_destroy": ([P], None),
+            "fem_tune_fwd": ([MP, I32, P, P, I32, P, OP, ctypes.POINTER(ctypes.c_float), P], ctypes.c_int),
+            "fem_tune_bwd": ([MP, I32, P, P, P, P, P, P, SZ, OP, ctypes.POINTER(ctypes.c_float), P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -313,3 +316,20 @@ def fem_host_step_run(handle: int, coords_ptr: int, conn_ptr: int, dA_ptr: int, 
 
 def fem_host_step_destroy(handle: int) -> None:
     load().fem_host_step_destroy(handle)
+
+
+def fem_tune_fwd(mesh: FemMesh, form: int, coef_ptr: int, A_ptr: int, out_dtype: int, det_ptr: int,
+                 opts: FemOptions, stream: int) -> float:
+    ms = ctypes.c_float()
+    check(load().fem_tune_fwd(ctypes.byref(mesh), form, coef_ptr or None, A_ptr or None, out_dtype, det_ptr or None,
+                              ctypes.byref(opts), ctypes.byref(ms), stream or None))
+    return ms.value
+
+
+def fem_tune_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, det_ptr: int, dcoords_ptr: int,
+                 dcoef_ptr: int, ws_ptr: int, ws_bytes: int, opts: FemOptions, stream: int) -> float:
+    ms = ctypes.c_float()
+    check(load().fem_tune_bwd(ctypes.byref(mesh), form, coef_ptr or None, dA_ptr or None, det_ptr or None,
+                              dcoords_ptr or None, dcoef_ptr or None, ws_ptr or None, ws_bytes, ctypes.byref(opts),
+                              ctypes.byref(ms), stream or None))
+    return ms.value
