@@ -93,23 +93,30 @@ struct BwdPlan {
   static constexpr int NC = D + (FormTraits<D, FORM>::W1 ? 1 : 0);
   static constexpr int XP = NC > 2 ? 4 : 2;  // padded floats per staged slot (one vector store)
   static constexpr size_t da_slot = align_up(size_t(32) * DST * 4, 128);    // one tile of dA rows
-  static constexpr size_t da_bytes = 2 * da_slot;                           // per warp, double buffered
-  static constexpr size_t xs_bytes = align_up(size_t(XCAP) * XP * 4, 128);  // per warp
-  static constexpr size_t per_warp = da_bytes + xs_bytes;
+  static constexpr size_t da_bytes = 2 * da_slot;                           // double buffered
+  static constexpr size_t xs_bytes = align_up(size_t(XCAP) * XP * 4, 128);  // slot stage of one tile
+  // Per warp of the single-mesh kernel: [dA slot 0][xs_over][dA slot 1].  A
+  // tile's slot stage overlays its own dA slot once every lane has read its
+  // dA row -- from slot 0's base, or ending at slot 1's end -- and never
+  // reaches the other slot, where the next tile's dA is arriving.  On P1 tets
+  // that is 6 KB per warp instead of 8 (2 KB dA slots, a 4 KB stage).
+  static constexpr size_t xs_over = xs_bytes > da_slot ? xs_bytes - da_slot : 0;
+  static constexpr size_t per_warp = 2 * da_slot + xs_over;
 };
 
 // CTA shape of the adjoint element kernel.  The kernel has no CTA-wide
 // barrier, so the CTA size only sets how finely the register file and shared
 // memory are shared out.  On tets every form runs one-warp CTAs: the P2
 // Laplacian's 30 KB per warp then packs 7 warps per SM instead of one 4-warp
-// CTA.  The compensated 3D P1 Laplacian also asks for at least 24 resident
-// per SM, which holds it to 80 registers without spills: 24 warps per SM,
-// against 20 at its natural 93 registers.  Triangles keep 4-warp CTAs.
+// CTA.  The compensated 3D P1 Laplacian also asks for at least 28 resident
+// per SM, which holds it to 72 registers without spills: 28 warps per SM
+// (7 KB of shared memory each with the reserved 1 KB), against 20 at its
+// natural 93 registers.  Triangles keep 4-warp CTAs.
 template <int D, int FORM, int JAC>
 struct BwdShape {
   static constexpr bool tight = (D == 3 && FORM == LAPLACE_P1 && (JAC == JAC_COMP || JAC == JAC_SAVED));
   static constexpr int threads = D == 3 ? 32 : kTileElems;
-  static constexpr int min_ctas = tight ? 24 : 1;
+  static constexpr int min_ctas = tight ? 28 : 1;
 };
 
 // Asynchronous copy of a tile's contiguous dA into the stage slot.
@@ -437,6 +444,7 @@ __device__ __forceinline__ int bwd_compute_tile(const BwdParams& p, int64_t tile
     }
   }
   if constexpr (!ATOMIC) {
+    __syncwarp();  // every lane has read its dA row (the stage overlays it)
     if (xs) {  // the element's slot contributions at their ranks (zeros when it is skipped)
       constexpr int XP = BwdPlan<D, FORM>::XP;
 #pragma unroll
@@ -463,8 +471,9 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   unsigned char* wbase = smem_raw + size_t(warp) * PL::per_warp;
-  float* dslots = reinterpret_cast<float*>(wbase);               // [2][32][DST]
-  float* xs = reinterpret_cast<float*>(wbase + PL::da_bytes);    // [XCAP][XP]
+  // dA slot s and the slot stage of a tile whose dA is in slot s (BwdPlan)
+  auto dslot = [&](int s) { return reinterpret_cast<float*>(wbase + size_t(s) * (PL::da_slot + PL::xs_over)); };
+  auto xstage = [&](int s) { return reinterpret_cast<float*>(wbase + size_t(s) * PL::da_slot); };
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
   const int64_t ntiles = (p.n_elem + 31) / 32;
   const int64_t S = int64_t(gridDim.x) * nwarps;  // warp-tile stride
@@ -475,7 +484,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
   float Xc[D + 1][D], Xn[D + 1][D];
   load_conn<D>(p.conn, t * 32 + lane, p.n_elem, p.vec_conn, v1);
   int fcur = gather_regs<D>(p.coords, p.n_vert, t * 32 + lane, p.n_elem, v1, Xc);
-  copy_dA_async<D, FORM>(p, t, lane, dslots);
+  copy_dA_async<D, FORM>(p, t, lane, dslot(0));
   Coef<FormTraits<D, FORM>::NW> wcur, wnext;
   load_coef<D, FORM>(p.coef, t * 32 + lane, p.n_elem, p.n_vert, v1, wcur);
   float dcur = 0.f;  // saved det J (JAC_SAVED)
@@ -496,7 +505,7 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     const int sn = (i + 1) & 1, sc = i & 1;
     load_conn<D>(p.conn, (tn + S) * 32 + lane, p.n_elem, p.vec_conn, v2);
     const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, v1, Xn);
-    copy_dA_async<D, FORM>(p, tn, lane, dslots + sn * 32 * PL::DST);
+    copy_dA_async<D, FORM>(p, tn, lane, dslot(sn));
     load_coef<D, FORM>(p.coef, en, p.n_elem, p.n_vert, v1, wnext);
     float dnext = 0.f;
     if constexpr (JAC == JAC_SAVED) dnext = en < p.n_elem ? __ldg(p.det + en) : 0.f;
@@ -512,13 +521,14 @@ __global__ void __launch_bounds__(BwdShape<D, FORM, JAC>::threads, BwdShape<D, F
     cp_async_commit();
     cp_async_wait<1>();
     __syncwarp();  // dA rows were copied by other lanes
-    err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslots + (sc * 32 + lane) * PL::DST,
+    float* xs = xstage(sc);
+    err |= bwd_compute_tile<D, FORM, JAC, ATOMIC>(p, t, lane, fcur, wcur, Xc, dslot(sc) + lane * PL::DST,
                                                   vc, rec ? xs : nullptr, rkcur, dcur);
     if (rec) {
       __syncwarp();  // every lane's contributions are staged
       warp_records<D, PL::NC>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
     }
-    __syncwarp();  // the slot stage is rewritten next tile, the dA slot two tiles later
+    __syncwarp();  // the next tile's dA copy may overwrite this tile's stage
     fcur = fnext;
     wcur = wnext;
     dcur = dnext;
