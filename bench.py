@@ -60,9 +60,9 @@ KERNEL_SOURCES = {
 # forward's and the reduction's scaled figures are lower bounds: the part of
 # their output still dirty in L2 when the kernel ends does not grow with it.
 NCU_TRAFFIC = {
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1316.4e6, "src": "978633ac72b6def2"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 958.5e6, "src": "fafe78917a5a36fb"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.3e6, "src": "8310deb034b51e68"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1320.8e6, "src": "54a2386e7e624da6"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 958.9e6, "src": "efe790d0d07e631f"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.4e6, "src": "05609e44c07bd899"},
 }
 
 
