@@ -83,7 +83,9 @@ def _load():
         lib.orc_element_vjp_div.argtypes = [I, I, P, D, I, P, P, P]
         lib.orc_integrate_div.argtypes = [I, I, I64, I64, P, P, P, I, P, P, I]
         lib.orc_integrate_div_vjp.argtypes = [I, I, I64, I64, P, P, P, I, P, P, P, I]
-        for name in ("orc_element_vjp_w1", "orc_integrate_w1_vjp", "orc_element_matrix_div", "orc_element_vjp_div",
+        lib.orc_element_vjp_iso.argtypes = [I, I, P, P, D, I, P, P, P, P]
+        lib.orc_integrate_iso_vjp.argtypes = [I, I, I64, I64, P, P, P, P, I, P, P, P, P, I]
+        for name in ("orc_element_vjp_iso", "orc_integrate_iso_vjp", "orc_element_vjp_w1", "orc_integrate_w1_vjp", "orc_element_matrix_div", "orc_element_vjp_div",
                      "orc_integrate_div",
                      "orc_integrate_div_vjp", "orc_gauss_legendre01", "orc_simplex_rule", "orc_basis", "orc_n_basis",
                      "orc_form_n", "orc_element_matrix", "orc_element_vjp", "orc_integrate",
@@ -250,6 +252,43 @@ def integrate_iso(dim: int, form: int, conn, coords, mid, coef=None, q: int = 4,
     if rc < 0:
         raise ValueError("bad integrate request")
     return A, flags
+
+
+def element_vjp_iso(dim: int, form: int, X, mid, Abar, coef: float = 1.0, q: int = 4):
+    """Reverse mode of element_matrix_iso: (Xbar [dim+1][dim], midbar
+    [n_edges][dim], coefbar, flags) for Abar = dL/dA [n][n]."""
+    X = _f64(X)
+    mid = _f64(mid)
+    Abar = _f64(Abar)
+    Xbar = np.zeros_like(X)
+    midbar = np.zeros_like(mid)
+    cbar = np.zeros(1)
+    rc = _load().orc_element_vjp_iso(dim, form, _ptr(X), _ptr(mid), float(coef), q, _ptr(Abar), _ptr(Xbar),
+                                     _ptr(midbar), _ptr(cbar))
+    if rc < 0:
+        raise ValueError("bad vjp request")
+    return Xbar, midbar, float(cbar[0]), rc
+
+
+def integrate_iso_vjp(dim: int, form: int, conn, coords, mid, dA, coef=None, q: int = 4,
+                      nthreads: int | None = None):
+    """Reverse mode of integrate_iso: (dcoords [V][dim], dmid [E][n_edges][dim],
+    dcoef [E]) for dA [E][n][n]."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    coords = _f64(coords)
+    mid = _f64(mid)
+    dA = _f64(dA)
+    E, V = conn.shape[0], coords.shape[0]
+    cf = None if coef is None else _f64(coef)
+    dcoords = np.zeros((V, dim))
+    dmid = np.zeros_like(mid)
+    dcoef = np.zeros(E)
+    nt = max_threads() if nthreads is None else nthreads
+    rc = _load().orc_integrate_iso_vjp(dim, form, E, V, _ptr(conn), _ptr(coords), _ptr(mid), _ptr(cf), q, _ptr(dA),
+                                       _ptr(dcoords), _ptr(dmid), _ptr(dcoef), nt)
+    if rc < 0:
+        raise ValueError("bad vjp request")
+    return dcoords, dmid, dcoef
 
 
 def element_vjp(dim: int, form: int, X, Abar, coef: float = 1.0, q: int = 3):

@@ -39,7 +39,10 @@
  *     phi the P1 scalar basis and psi the P1 or P2 basis of each component of
  *     a vector field (orc_integrate_div): by the same quadrature and LU solve.
  *   * The reverse mode (vector-Jacobian product) is derived by hand from the
- *     same quadrature steps, in the opposite order.
+ *     same quadrature steps, in the opposite order -- for the affine forms,
+ *     the P1 coefficient, the coupling block and the non-affine elements
+ *     (orc_integrate_iso_vjp: gradients of the vertices, of the edge nodes and
+ *     of the per-element coefficient).
  *
  * Conventions shared with the library (they are conventions, not arithmetic):
  *   P1 basis lambda_0 = 1 - sum xi, lambda_k = xi_k.  P2 basis: vertex
@@ -666,6 +669,211 @@ int orc_integrate_iso(int dim, int form, int64_t n_elem, int64_t n_vert, const i
     if (flags) flags[e] = f;
     any |= f;
   }
+  return any;
+}
+
+/* Reverse mode of orc_element_matrix_iso (Eqs. 16-19), derived by hand from
+ * its steps taken backwards.  Given Abar = dL/dA [n][n]:
+ *   1. at every quadrature point p the forward adds s_p g_i.g_j into A_ij with
+ *      s_p = w_p |det J_c| coef and g_i = Ji(xi_p)^T grad_ref phi_i, so
+ *        d|det J_c| += w_p coef sum_ij Abar_ij g_i.g_j,  dcoef likewise,
+ *        gbar_i = s_p sum_j (Abar_ij + Abar_ji) g_j,
+ *        Jibar(xi_p)[mu][al] = sum_i gbar_i[al] grad_ref phi_i[mu];
+ *   2. Ji(xi) = sum_k lambda_k(xi) Jinv_k, so Jinvbar_k += lambda_k(xi_p) Jibar;
+ *   3. Jinv_k = J_k^{-1} (J_k = J at vertex k): Jbar_k = -Jinv_k^T Jinvbar_k Jinv_k^T;
+ *   4. |det J_c|: Jbar_c = sign(det J_c) d|det J_c| cof(J_c), cof = det J^{-T};
+ *   5. J(xi) = sum_a node_a grad psi_a(xi)^T: nodebar_a[al] =
+ *        sum_k sum_mu Jbar_k[al][mu] dpsi_a/dxi_mu(vertex k)
+ *        + sum_mu Jbar_c[al][mu] dpsi_a/dxi_mu(centroid).
+ * Xbar [(dim+1)*dim] gets the vertex nodes' gradients, Midbar [n_edges*dim]
+ * the edge nodes', *cbar the coefficient's (may be NULL).  Returns as
+ * orc_element_matrix_iso; a degenerate element leaves the outputs zero. */
+int orc_element_vjp_iso(int dim, int form, const double* X, const double* Mid, double coef, int q,
+                        const double* Abar, double* Xbar, double* Midbar, double* cbar) {
+  if (form == ORC_ELASTIC_P1) return -1;
+  int n = orc_form_n(form, dim);
+  if (n < 0) return -1;
+  int deg = form_degree(form), nb = orc_n_basis(dim, deg), nv = dim + 1;
+  int ne = dim == 2 ? 3 : 6, nn = nv + ne;
+  for (int k = 0; k < nv * dim; ++k) Xbar[k] = 0.0;
+  for (int k = 0; k < ne * dim; ++k) Midbar[k] = 0.0;
+  if (cbar) *cbar = 0.0;
+  double nodes[ORC_MAXB * 3];
+  for (int k = 0; k < nv * dim; ++k) nodes[k] = X[k];
+  for (int k = 0; k < ne * dim; ++k) nodes[nv * dim + k] = Mid[k];
+  double Jinv[4][3][3];
+  for (int k = 0; k < nv; ++k) {
+    double xi[3] = {0, 0, 0};
+    if (k > 0) xi[k - 1] = 1.0;
+    double J[3][3];
+    iso_jacobian(dim, nodes, xi, J);
+    lu3 f;
+    lu_factor(dim, J, &f);
+    if (f.det == 0.0) return ORC_FLAG_DEGENERATE;
+    for (int al = 0; al < dim; ++al) {
+      double b[3] = {0, 0, 0};
+      b[al] = 1.0;
+      lu_solve(&f, b);
+      for (int mu = 0; mu < dim; ++mu) Jinv[k][mu][al] = b[mu];
+    }
+  }
+  double xc[3] = {0, 0, 0};
+  for (int mu = 0; mu < dim; ++mu) xc[mu] = 1.0 / nv;
+  double Jc[3][3];
+  iso_jacobian(dim, nodes, xc, Jc);
+  double detc = det3(dim, Jc);
+  if (detc == 0.0) return ORC_FLAG_DEGENERATE;
+  double absdet = fabs(detc);
+  double pts[ORC_MAXPTS * 3], wts[ORC_MAXPTS];
+  int np = orc_simplex_rule(dim, q, pts, wts);
+  if (np < 0) return -1;
+  /* steps 1-2 */
+  double Jinvbar[4][3][3];
+  memset(Jinvbar, 0, sizeof(Jinvbar));
+  double absdet_bar = 0.0, coef_bar = 0.0;
+  for (int p = 0; p < np; ++p) {
+    const double* xi = pts + p * dim;
+    double lam[4];
+    lam[0] = 1.0;
+    for (int k = 1; k <= dim; ++k) {
+      lam[k] = xi[k - 1];
+      lam[0] -= xi[k - 1];
+    }
+    double Ji[3][3] = {{0}};
+    for (int k = 0; k < nv; ++k)
+      for (int mu = 0; mu < dim; ++mu)
+        for (int al = 0; al < dim; ++al) Ji[mu][al] += lam[k] * Jinv[k][mu][al];
+    double phi[ORC_MAXB], gref[ORC_MAXB * 3], g[ORC_MAXB][3];
+    orc_basis(dim, deg, xi, phi, gref);
+    for (int i = 0; i < nb; ++i)
+      for (int al = 0; al < dim; ++al) {
+        double s = 0.0;
+        for (int mu = 0; mu < dim; ++mu) s += Ji[mu][al] * gref[i * dim + mu];
+        g[i][al] = s;
+      }
+    double quad = 0.0; /* sum_ij Abar_ij g_i.g_j */
+    for (int i = 0; i < nb; ++i)
+      for (int j = 0; j < nb; ++j) {
+        double s = 0.0;
+        for (int a = 0; a < dim; ++a) s += g[i][a] * g[j][a];
+        quad += Abar[i * n + j] * s;
+      }
+    absdet_bar += wts[p] * coef * quad;
+    coef_bar += wts[p] * absdet * quad;
+    double sp = wts[p] * absdet * coef;
+    double gbar[ORC_MAXB][3];
+    for (int i = 0; i < nb; ++i)
+      for (int a = 0; a < dim; ++a) {
+        double s = 0.0;
+        for (int j = 0; j < nb; ++j) s += (Abar[i * n + j] + Abar[j * n + i]) * g[j][a];
+        gbar[i][a] = sp * s;
+      }
+    double Jibar[3][3] = {{0}};
+    for (int mu = 0; mu < dim; ++mu)
+      for (int al = 0; al < dim; ++al) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += gbar[i][al] * gref[i * dim + mu];
+        Jibar[mu][al] = s;
+      }
+    for (int k = 0; k < nv; ++k)
+      for (int mu = 0; mu < dim; ++mu)
+        for (int al = 0; al < dim; ++al) Jinvbar[k][mu][al] += lam[k] * Jibar[mu][al];
+  }
+  if (cbar) *cbar = coef_bar;
+  /* step 3: Jbar_k[al][mu] = -sum_{nu,be} Jinv_k[nu][al] Jinvbar_k[nu][be] Jinv_k[mu][be] */
+  double Jbar[5][3][3];
+  memset(Jbar, 0, sizeof(Jbar));
+  for (int k = 0; k < nv; ++k)
+    for (int al = 0; al < dim; ++al)
+      for (int mu = 0; mu < dim; ++mu) {
+        double s = 0.0;
+        for (int nu = 0; nu < dim; ++nu)
+          for (int be = 0; be < dim; ++be) s += Jinv[k][nu][al] * Jinvbar[k][nu][be] * Jinv[k][mu][be];
+        Jbar[k][al][mu] = -s;
+      }
+  /* step 4: cofactor of J_c by minors */
+  double sgn = detc > 0.0 ? 1.0 : -1.0;
+  for (int al = 0; al < dim; ++al)
+    for (int mu = 0; mu < dim; ++mu) {
+      double cof;
+      if (dim == 2) {
+        cof = (al == mu ? Jc[1 - al][1 - mu] : -Jc[1 - al][1 - mu]);
+      } else {
+        int r0 = (al + 1) % 3, r1 = (al + 2) % 3, c0 = (mu + 1) % 3, c1 = (mu + 2) % 3;
+        cof = Jc[r0][c0] * Jc[r1][c1] - Jc[r0][c1] * Jc[r1][c0];
+      }
+      Jbar[nv][al][mu] = sgn * absdet_bar * cof;
+    }
+  /* step 5 */
+  for (int k = 0; k <= nv; ++k) {
+    double xi[3] = {0, 0, 0};
+    if (k == nv) {
+      for (int mu = 0; mu < dim; ++mu) xi[mu] = 1.0 / nv;
+    } else if (k > 0) {
+      xi[k - 1] = 1.0;
+    }
+    double psi[ORC_MAXB], gpsi[ORC_MAXB * 3];
+    orc_basis(dim, 2, xi, psi, gpsi);
+    for (int a = 0; a < nn; ++a)
+      for (int al = 0; al < dim; ++al) {
+        double s = 0.0;
+        for (int mu = 0; mu < dim; ++mu) s += Jbar[k][al][mu] * gpsi[a * dim + mu];
+        if (a < nv)
+          Xbar[a * dim + al] += s;
+        else
+          Midbar[(a - nv) * dim + al] += s;
+      }
+  }
+  return 0;
+}
+
+/* Reverse mode of orc_integrate_iso over a mesh: given Abar [E][n][n],
+ * dcoords [V][dim] (overwritten; per-vertex sums in element order), dmid
+ * [E][n_edges][dim] (overwritten) and dcoef [E] (may be NULL).  Flagged
+ * elements contribute nothing. */
+int orc_integrate_iso_vjp(int dim, int form, int64_t n_elem, int64_t n_vert, const int32_t* conn,
+                          const double* coords, const double* mid, const double* coef, int q, const double* Abar,
+                          double* dcoords, double* dmid, double* dcoef, int nthreads) {
+  int n = orc_form_n(form, dim);
+  if (n < 0 || form == ORC_ELASTIC_P1) return -1;
+  int nv = dim + 1, ne = dim == 2 ? 3 : 6;
+  double* xbar = (double*)malloc(sizeof(double) * (size_t)(n_elem > 0 ? n_elem : 1) * nv * dim);
+  int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_elem > 0 ? n_elem : 1));
+  if (!xbar || !fl) {
+    free(xbar);
+    free(fl);
+    return -2;
+  }
+  if (nthreads < 1) nthreads = 1;
+  int any = 0;
+#pragma omp parallel for schedule(static) num_threads(nthreads) reduction(| : any)
+  for (int64_t e = 0; e < n_elem; ++e) {
+    double X[12], cb = 0.0;
+    double* xb = xbar + e * nv * dim;
+    double* mb = dmid + e * (int64_t)ne * dim;
+    int f = gather(dim, n_vert, conn + e * nv, coords, X);
+    if (f == 0)
+      f = orc_element_vjp_iso(dim, form, X, mid + e * (int64_t)ne * dim, coef ? coef[e] : 1.0, q,
+                              Abar + e * (int64_t)n * n, xb, mb, &cb);
+    if (f != 0) {
+      for (int k = 0; k < nv * dim; ++k) xb[k] = 0.0;
+      for (int k = 0; k < ne * dim; ++k) mb[k] = 0.0;
+      cb = 0.0;
+    }
+    fl[e] = f;
+    if (dcoef) dcoef[e] = cb;
+    any |= f;
+  }
+  for (int64_t k = 0; k < n_vert * dim; ++k) dcoords[k] = 0.0;
+  for (int64_t e = 0; e < n_elem; ++e) {
+    if (fl[e] & ORC_FLAG_CONN) continue;
+    for (int k = 0; k < nv; ++k) {
+      int64_t v = conn[e * nv + k];
+      for (int a = 0; a < dim; ++a) dcoords[v * dim + a] += xbar[(e * nv + k) * dim + a];
+    }
+  }
+  free(xbar);
+  free(fl);
   return any;
 }
 
