@@ -205,9 +205,10 @@ FEM_API fem_status fem_integrate_fwd_iso(const fem_mesh* mesh, int32_t form, con
 FEM_API fem_status fem_geometry(const fem_mesh* mesh, const float* coef, const fem_options* options,
                         double* detJ, float* G, void* stream);
 
-/* Bytes of device workspace fem_integrate_bwd needs for this mesh and form
- * (vertex->incidence CSR plus per-element scratch for the deterministic
- * reduction; 0 extra scratch for FEM_REDUCE_ATOMIC). */
+/* Bytes of device workspace fem_integrate_bwd (fem_integrate_bwd_iso for the
+ * non-affine forms) needs for this mesh and form (vertex->incidence CSR plus
+ * per-element scratch for the deterministic reduction; 0 extra scratch for
+ * FEM_REDUCE_ATOMIC). */
 FEM_API fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_options* options,
                                   size_t* bytes);
 
@@ -260,6 +261,27 @@ FEM_API fem_status fem_integrate_bwd(const fem_mesh* mesh, int32_t form, const f
 FEM_API fem_status fem_integrate_bwd_saved(const fem_mesh* mesh, int32_t form, const float* coef,
                                            const float* dA, const float* det, float* dcoords, float* dcoef,
                                            void* ws, size_t ws_bytes, const fem_options* options, void* stream);
+
+/* Adjoint of fem_integrate_fwd_iso (Eqs. 16-19): for the upstream dA = dL/dA
+ * (device FP32 [n_elem][n][n]) of the non-affine Laplacian (form
+ * FEM_LAPLACE_P1_ISO or FEM_LAPLACE_P2_ISO, FP32 coordinates, the plain-FP32
+ * Jacobian steps of the forward) computes
+ *   dcoords = dL/dcoords (device FP32 [n_vert][dim], overwritten; may be NULL),
+ *   dmid    = dL/dmid    (device FP32 [n_elem][d(d+1)/2][dim], the edge nodes'
+ *             gradients element by element; may be NULL),
+ *   dcoef   = dL/dcoef   (device FP32 [n_elem], per-element coefficient; may be NULL)
+ * by the forward's steps in reverse: the contraction's adjoint one folded slot
+ * pair at a time, then J^{-1} at the vertices (J^{-1} projected onto P1,
+ * Eq. 17) and |det J| at the centroid pulled back through the quadratic
+ * geometry map to the nodes.  mid, coef: as fem_integrate_fwd_iso.  The
+ * reductions of dcoords as fem_integrate_bwd (the deterministic one through
+ * the workspace of fem_bwd_workspace_size / fem_incidence_build with this
+ * form; FEM_REDUCE_DEFERRED leaves dcoords to fem_adjoint_reduce).  Elements
+ * that are degenerate (J singular at a vertex or at the centroid) or have an
+ * invalid vertex contribute zeros and set the device error bits. */
+FEM_API fem_status fem_integrate_bwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef,
+                                         const float* dA, float* dcoords, float* dmid, float* dcoef, void* ws,
+                                         size_t ws_bytes, const fem_options* options, void* stream);
 
 /* Second phase of a FEM_REDUCE_DEFERRED adjoint: dcoords[v] (device FP32
  * [n_vert][dim], overwritten) = sum over the incidence segment of v, in

@@ -240,6 +240,38 @@ def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None
     return dcoords, dcoef
 
 
+def integrate_bwd_iso(coords, conn, mid, form, dA, coef=None, ws: Workspace | None = None,
+                      reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dmid=True, need_dcoef=False,
+                      dcoords=None, dmid=None, dcoef=None, dev_err=None, stream=None):
+    """fem_integrate_bwd_iso: (dcoords [V][d], dmid [E][d(d+1)/2][d], dcoef [E]),
+    each None when not asked for, for the upstream dA of integrate_fwd_iso."""
+    m = _mesh_struct(coords, conn)
+    E, V, d = conn.shape[0], coords.shape[0], m.dim
+    ne = d * (d + 1) // 2
+    if mid.dtype != torch.float32 or not mid.is_contiguous() or tuple(mid.shape) != (E, ne, d) or not mid.is_cuda:
+        raise ValueError(f"mid must be a contiguous CUDA float32 tensor [E][{ne}][{d}]")
+    n, _, _ = form_info(form, d)
+    if dA.dtype != torch.float32 or not dA.is_contiguous() or tuple(dA.shape) != (E, n, n):
+        raise ValueError(f"dA must be a contiguous float32 tensor [E][{n}][{n}]")
+    dev = coords.device
+    dcoords = (dcoords if dcoords is not None else torch.empty((V, d), dtype=torch.float32, device=dev)) \
+        if need_dcoords else None
+    dmid = (dmid if dmid is not None else torch.empty_like(mid)) if need_dmid else None
+    dcoef = (dcoef if dcoef is not None else torch.empty(E, dtype=torch.float32, device=dev)) if need_dcoef else None
+    ws_ptr, ws_bytes = 0, 0
+    if dcoords is not None and reduce != REDUCE_ATOMIC:
+        if ws is None:
+            ws = Workspace(coords, conn, form, stream)
+        ws_ptr, ws_bytes = ws.buf.data_ptr(), ws.bytes
+    opts = nat.options_struct(JAC_AUTO, 0, reduce, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
+    nat.fem_integrate_bwd_iso(m, form, mid.data_ptr(), _coef_ptr(coef, E), dA.data_ptr(),
+                              dcoords.data_ptr() if dcoords is not None else 0,
+                              dmid.data_ptr() if dmid is not None else 0,
+                              dcoef.data_ptr() if dcoef is not None else 0, ws_ptr, ws_bytes, opts,
+                              _stream_ptr(stream))
+    return dcoords, dmid, dcoef
+
+
 def adjoint_reduce(coords, conn, ws: Workspace, dcoords, stream=None):
     """fem_adjoint_reduce: completes a REDUCE_DEFERRED adjoint into dcoords."""
     m = _mesh_struct(coords, conn)
@@ -426,6 +458,37 @@ class _IntegrateFn(torch.autograd.Function):
                                ws=ws, reduce=ctx.reduce, need_dcoords=need_x, need_dcoef=need_w,
                                jac=ctx.jac, det=ctx.det)
         return dx, dw, None, None, None, None, None
+
+
+class _IntegrateIsoFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, coords, mid, coef, mesh, form, reduce):
+        A = integrate_fwd_iso(coords, mesh.conn, mid, form, coef)
+        ctx.save_for_backward(coords, mid, coef if coef is not None else torch.empty(0))
+        ctx.mesh, ctx.form, ctx.reduce, ctx.has_coef = mesh, form, reduce, coef is not None
+        return A
+
+    @staticmethod
+    def backward(ctx, dA):
+        coords, mid, coef = ctx.saved_tensors
+        coef = coef if ctx.has_coef else None
+        need_x, need_m = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        need_w = ctx.has_coef and ctx.needs_input_grad[2]
+        ws = ctx.mesh.workspace(ctx.form) if (need_x and ctx.reduce != REDUCE_ATOMIC) else None
+        dx, dm, dw = integrate_bwd_iso(coords.detach(), ctx.mesh.conn, mid.detach(), ctx.form,
+                                       dA.contiguous().float(), coef, ws=ws, reduce=ctx.reduce,
+                                       need_dcoords=need_x, need_dmid=need_m, need_dcoef=need_w)
+        return dx, dm, dw, None, None, None
+
+
+def integrate_iso(coords, conn, mid, form=LAPLACE_P1_ISO, coef=None, reduce=REDUCE_DETERMINISTIC, mesh=None):
+    """Element matrices of the non-affine Laplacian (Eqs. 16-19), differentiable
+    with respect to coords, mid (the edge nodes) and coef.  Pass a Mesh built
+    on (coords, conn) to reuse its adjoint workspace across calls."""
+    if coords.dtype != torch.float32 or mid.dtype != torch.float32:
+        raise ValueError("non-affine elements take float32 coordinates and edge nodes")
+    mesh = mesh if mesh is not None else Mesh(coords.detach(), conn)
+    return _IntegrateIsoFn.apply(coords, mid, coef, mesh, form, reduce)
 
 
 class Mesh:

@@ -30,7 +30,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
            "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy", "fem_tune_fwd",
-           "fem_tune_bwd")
+           "fem_tune_bwd", "fem_integrate_bwd_iso")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
@@ -89,6 +89,7 @@ def load():
             "fem_integrate_fwd_iso": ([MP, I32, P, P, P, OP, P], ctypes.c_int),
             "fem_integrate_fwd_save": ([MP, I32, P, P, I32, P, OP, P], ctypes.c_int),
             "fem_integrate_bwd_saved": ([MP, I32, P, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
+            "fem_integrate_bwd_iso": ([MP, I32, P, P, P, P, P, P, P, SZ, OP, P], ctypes.c_int),
             "fem_geometry": ([MP, P, OP, P, P, P], ctypes.c_int),
             "fem_bwd_workspace_size": ([MP, I32, OP, ctypes.POINTER(SZ)], ctypes.c_int),
             "fem_incidence_build": ([MP, P, SZ, P], ctypes.c_int),
@@ -333,3 +334,11 @@ def fem_tune_bwd(mesh: FemMesh, form: int, coef_ptr: int, dA_ptr: int, det_ptr: 
                               dcoords_ptr or None, dcoef_ptr or None, ws_ptr or None, ws_bytes, ctypes.byref(opts),
                               ctypes.byref(ms), stream or None))
     return ms.value
+
+
+def fem_integrate_bwd_iso(mesh: FemMesh, form: int, mid_ptr: int, coef_ptr: int, dA_ptr: int, dcoords_ptr: int,
+                          dmid_ptr: int, dcoef_ptr: int, ws_ptr: int, ws_bytes: int, opts: FemOptions,
+                          stream: int) -> None:
+    check(load().fem_integrate_bwd_iso(ctypes.byref(mesh), form, mid_ptr or None, coef_ptr or None, dA_ptr or None,
+                                       dcoords_ptr or None, dmid_ptr or None, dcoef_ptr or None, ws_ptr or None,
+                                       ws_bytes, ctypes.byref(opts), stream or None))

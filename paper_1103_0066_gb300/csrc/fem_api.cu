@@ -100,7 +100,8 @@ fem_status bwd_args(const fem_mesh* mesh, int32_t form, const fem_options* o, co
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (non_affine(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine forms");
+  if (non_affine(form))
+    return fail(FEM_ERR_UNSUPPORTED, "the non-affine forms take their adjoint through fem_integrate_bwd_iso");
   if ((s = check_options(o)) != FEM_OK) return s;
   if (coef_p1(form) && ((o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_COMP_F32) || o->reduce == FEM_REDUCE_DEFERRED))
     return fail(FEM_ERR_UNSUPPORTED,
@@ -412,7 +413,6 @@ fem_status fem_bwd_workspace_size(const fem_mesh* mesh, int32_t form, const fem_
   fem_status s = check_mesh(mesh);
   if (s != FEM_OK) return s;
   if (!valid_form(form)) return fail(FEM_ERR_ARG, "form out of range");
-  if (non_affine(form)) return fail(FEM_ERR_UNSUPPORTED, "the adjoint serves the affine forms");
   const fem_options* o = options ? options : &kDefaults;
   if ((s = check_options(o)) != FEM_OK) return s;
   if (!bytes) return fail(FEM_ERR_ARG, "bytes is NULL");
@@ -533,6 +533,71 @@ fem_status fem_integrate_bwd_saved(const fem_mesh* mesh, int32_t form, const flo
   if (s != FEM_OK) return s;
   if (mesh->n_elem > 0 && !det) return fail(FEM_ERR_ARG, "det is NULL");
   return integrate_bwd(mesh, form, coef, dA, det, dcoords, dcoef, ws, ws_bytes, options, stream);
+}
+
+fem_status fem_integrate_bwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef,
+                                 const float* dA, float* dcoords, float* dmid, float* dcoef, void* ws,
+                                 size_t ws_bytes, const fem_options* options, void* stream) {
+  fem_status s = check_mesh(mesh);
+  if (s != FEM_OK) return s;
+  if (!non_affine(form)) return fail(FEM_ERR_ARG, "form must be FEM_LAPLACE_P1_ISO or FEM_LAPLACE_P2_ISO");
+  if (mesh->coord_dtype != FEM_F32) return fail(FEM_ERR_UNSUPPORTED, "non-affine elements take FP32 coordinates");
+  const fem_options* o = options ? options : &kDefaults;
+  if ((s = check_options(o)) != FEM_OK) return s;
+  if (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F32)
+    return fail(FEM_ERR_UNSUPPORTED, "non-affine elements compute their Jacobians in FP32");
+  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
+  if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
+    return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
+  if (o->reduce == FEM_REDUCE_DEFERRED && !dcoords)
+    return fail(FEM_ERR_ARG, "FEM_REDUCE_DEFERRED needs dcoords (written by fem_adjoint_reduce)");
+  if (mesh->n_elem > 0 && (!dA || !mid)) return fail(FEM_ERR_ARG, "dA or mid is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool atomic = o->reduce == FEM_REDUCE_ATOMIC;
+  const bool recs = dcoords && !atomic;
+  fem::BwdWorkspace W{};
+  if (recs) {
+    const size_t need = fem::bwd_workspace_layout(mesh->dim, mesh->n_elem, mesh->n_vert, true, ws, &W);
+    if (!ws || ws_bytes < need) return fail(FEM_ERR_WORKSPACE, "workspace needs %zu bytes (got %zu)", need, ws_bytes);
+    if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(FEM_ERR_ARG, "workspace must be 256-byte aligned");
+  }
+  if (!dcoords && !dmid && !dcoef) return ok();
+  cudaError_t e;
+  if (dcoords && atomic) {
+    e = fem::launch_zero_f32(dcoords, mesh->n_vert * mesh->dim, st);
+    if (e != cudaSuccess) return cuda_fail(e, "zeroing dcoords");
+  }
+  if (mesh->n_elem > 0) {
+    fem::BwdLaunch L{};
+    L.dim = mesh->dim;
+    L.form = form;
+    L.jac = fem::JAC_F32;
+    L.atomic = atomic ? 1 : 0;
+    L.conn = mesh->conn;
+    L.coords = static_cast<const float*>(mesh->coords);
+    L.coef = coef;
+    L.dA = dA;
+    L.dcoef = dcoef;
+    L.tile_rec = recs ? W.tile_rec : nullptr;
+    L.rank = recs ? W.rank : nullptr;
+    L.rec_span = recs ? W.rec_span : nullptr;
+    L.rec_dest = recs ? W.rec_dest : nullptr;
+    L.records = recs ? W.records : nullptr;
+    L.dcoords = dcoords;
+    L.n_elem = mesh->n_elem;
+    L.n_vert = mesh->n_vert;
+    L.dev_err = o->dev_err;
+    L.warps = 0;
+    L.ctas_per_sm = o->ctas_per_sm;
+    L.stream = st;
+    e = fem::launch_bwd_iso(L, mid, dmid);
+    if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd_iso element launch");
+  }
+  if (recs && o->reduce == FEM_REDUCE_DETERMINISTIC) {
+    e = fem::launch_vertex_reduce(mesh->dim, W, mesh->n_vert, dcoords, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd_iso reduction launch");
+  }
+  return ok();
 }
 
 fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size_t ws_bytes, float* dcoords,

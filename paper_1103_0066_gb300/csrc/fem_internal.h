@@ -113,6 +113,9 @@ cudaError_t launch_geometry(const GeoLaunch& L);
 cudaError_t launch_div_fwd(const FwdLaunch& L);
 cudaError_t launch_div_bwd(const BwdLaunch& L);
 cudaError_t launch_bwd_elem(const BwdLaunch& L);
+// Adjoint element pass of the non-affine forms (LAPLACE_P1_ISO / LAPLACE_P2_ISO):
+// mid [E][d(d+1)/2][d] the edge nodes, dmid the same shape (may be null).
+cudaError_t launch_bwd_iso(const BwdLaunch& L, const float* mid, float* dmid);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t stream);
