@@ -999,7 +999,8 @@ def run_multiphysics(args):
 
 def run_iso(args):
     """The Laplacian on non-affine (quadratic-geometry) elements, Eqs. 16-19:
-    the 128^3 jittered cube warped into curved tets, P1 and P2, forward."""
+    the 128^3 jittered cube warped into curved tets, P1 and P2, forward, and
+    forward + adjoint."""
     import torch
 
     import __graft_entry__
@@ -1039,13 +1040,64 @@ def run_iso(args):
                      "frac_of_peak": byts / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": byts,
                      "max_rel_err_vs_fp64": float((num / np.abs(Ar).reshape(len(idx), -1).max(1)).max())}
         del A
+    # forward + adjoint (fem_integrate_bwd_iso: vertex gradients through the
+    # deterministic reduction, edge-node gradients per element)
+    ws = fem.Workspace(coords, conn, fem.LAPLACE_P1_ISO)
+    R = ws.n_records()
+    dx = torch.empty((V, 3), device=dev)
+    dm = torch.empty_like(mid)
+    for name, form, n in (("p1_fwd_adjoint", fem.LAPLACE_P1_ISO, 4), ("p2_fwd_adjoint", fem.LAPLACE_P2_ISO, 10)):
+        A = torch.empty((E, n, n), device=dev)
+        dA_h = mg.upstream(mg.rng_for(13), E, n)
+        dA = torch.from_numpy(dA_h).to(dev)
+
+        def step():
+            fem.integrate_fwd_iso(coords, conn, mid, form, out=A)
+            fem.integrate_bwd_iso(coords, conn, mid, form, dA, ws=ws, dcoords=dx, dmid=dm)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        r = measure(lambda rep, k: step(), args.steps, stream, dev)
+        ms = r["ms_per_step"]
+        # algorithmic bytes: the forward's, the element pass's (dA, conn, edge
+        # nodes in, edge-node gradients out, slot ranks, coordinates; per record
+        # its span, destination and sum) and the reduction's
+        fwd_b = E * (16 + 72 + 4 * n * n) + V * 12
+        bwd_b = E * (4 * n * n + 16 + 72 + 72 + 4) + R * (2 + 4 + 12) + V * 12
+        red_b = R * 12 + V * 16
+        byts = fwd_b + bwd_b + red_b
+        # errors against the oracle's reverse mode: edge-node gradients on a
+        # sample of elements, vertex gradients where every incident element is evaluated
+        rng = np.random.default_rng(14)
+        verts = rng.choice(V, 30, replace=False)
+        els = np.unique(np.concatenate([np.flatnonzero(np.isin(mesh.conn, verts).any(1)),
+                                        rng.choice(E, 3000, replace=False)]))
+        rx, rm, _ = oracle.integrate_iso_vjp(3, form - 5, mesh.conn[els], mesh.coords, mid_h[els], dA_h[els])
+        gm = dm[torch.from_numpy(els).to(dev)].double().cpu().numpy()
+        gx = dx.double().cpu().numpy()[verts]
+        # a vertex gradient is a small difference of its elements' node gradients
+        # (coefficients summing to zero): its error is measured against them
+        s_e = np.abs(rm).reshape(len(els), -1).max(1)
+        node_scale = np.abs(rx).max(1)
+        np.maximum.at(node_scale, mesh.conn[els].ravel(), np.repeat(s_e, 4))
+        res[name] = {"ms": ms, "ms_min": r["ms_min"], "ms_max": r["ms_max"], "repeats": r["repeats"],
+                     "clocks": r["clocks"], "elements_per_s": E / (ms * 1e-3), "GB/s": byts / (ms * 1e-3) / 1e9,
+                     "frac_of_peak": byts / (ms * 1e-3) / 1e9 / peak, "algorithmic_bytes": byts,
+                     "max_rel_err_vs_fp64": {"dmid": float(np.abs(gm - rm).max() / np.abs(rm).max()),
+                                             "dcoords": float((np.abs(gx - rx[verts]).max(1)
+                                                               / node_scale[verts]).max()),
+                                             "dcoords_metric": "per vertex, relative to the largest node "
+                                                               "gradient of its elements",
+                                             "sample": f"{len(els):,} elements, 30 vertices with all their elements"}}
+        del A, dA
     r = res["p1"]
     out = {"metric": METRIC, "value": r["elements_per_s"], "unit": "elements/s", "n_gpus": 1,
            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": r["ms"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"Laplacian on quadratic-geometry tets (Eqs. 16-19): {args.mesh_n}^3 jittered "
                                   f"cube warped by a smooth map ({E:,} tets), P1 and P2 (FP32 contraction; P2 also "
-                                  "split-BF16 on the tensor cores), forward",
+                                  "split-BF16 on the tensor cores), forward; and forward + adjoint (vertex and "
+                                  "edge-node gradients)",
                       "elements": E, "l2": "no flush"},
            "roofline": {"bound": "hbm", "kernel": "fem_fwd_iso_kernel<3,LAPLACE_P1_ISO>", "achieved": r["GB/s"],
                         "peak": peak, "unit": "GB/s", "frac": r["frac_of_peak"],

@@ -4,7 +4,13 @@ against the FP64 oracle's reverse mode (-m gpu).
 The gradients of L = sum dA : A with respect to the vertices (dcoords, summed
 over the elements at each vertex), the edge nodes (dmid, per element) and the
 per-element coefficient are compared element by element and vertex by vertex:
-  dcoords: max_v |g - g_ref| <= TOL * max |g_ref|
+  dcoords: per vertex, |g - g_ref| <= TOL * (the largest node gradient of the
+           elements at the vertex, edge nodes included).  A vertex's gradient
+           combines its elements' Jacobian adjoints with coefficients that sum
+           to zero; on nearly straight elements those adjoints are nearly
+           equal, so the P1 vertex gradients come out about 400 times smaller
+           than the edge-node gradients formed from the same FP32 terms, and
+           the FP32 bound scales with the terms, not with their difference
   dmid:    max |dmid - dmid_ref| over an element <= TOL * max over the mesh of |dmid_ref|
   dcoef:   per element, |dw - dw_ref| <= TOL * sum_ij |dA_ij| |A_ij| / w, the
            error bound of dw = (dA : A) / w when every entry of A carries a
@@ -38,12 +44,23 @@ def _curved(dim, eps=0.05, seed=51, n=None):
     return mg.curved_mesh(base, eps)
 
 
-def _errs(got, ref, A_ref=None, dA=None, coef=None):
+def node_scale(conn, rx, rm):
+    """Per vertex: the largest node gradient (edge nodes, and the vertex's own
+    sum) over the elements at the vertex."""
+    s_e = np.abs(rm).reshape(len(rm), -1).max(1)
+    scale = np.abs(rx).max(1)
+    ok = (conn >= 0) & (conn < len(rx))
+    np.maximum.at(scale, conn[ok], np.repeat(s_e[:, None], conn.shape[1], 1)[ok])
+    return scale
+
+
+def _errs(got, ref, A_ref=None, dA=None, coef=None, conn=None):
     dx, dm, dw = (None if g is None else g.cpu().numpy().astype(np.float64) for g in got)
     rx, rm, rw = ref
     out = {}
     if dx is not None:
-        out["dcoords"] = np.abs(dx - rx).max() / np.abs(rx).max()
+        scale = node_scale(conn, rx, rm)
+        out["dcoords"] = (np.abs(dx - rx).max(1) / np.where(scale > 0, scale, 1.0)).max()
     if dm is not None:
         out["dmid"] = np.abs(dm - rm).max() / np.abs(rm).max()
     if dw is not None:
@@ -64,7 +81,7 @@ def test_iso_adjoint_matches_oracle(gfem, orc, dim, form):
     got = gfem.integrate_bwd_iso(_t(mesh.coords), _t(mesh.conn), _t(mid), form, _t(dA), _t(coef), need_dcoef=True)
     ref = orc.integrate_iso_vjp(dim, form - 5, mesh.conn, mesh.coords, mid, dA, coef)
     A_ref, _ = orc.integrate_iso(dim, form - 5, mesh.conn, mesh.coords, mid, coef)
-    errs = _errs(got, ref, A_ref, dA, coef)
+    errs = _errs(got, ref, A_ref, dA, coef, mesh.conn)
     assert max(errs.values()) <= TOL, errs
 
 
@@ -128,7 +145,8 @@ def test_iso_adjoint_straight_sides_reduce_to_affine(gfem, dim, form):
         np.add.at(moved, mesh.conn[:, a], 0.5 * dmn[:, q])
         np.add.at(moved, mesh.conn[:, b], 0.5 * dmn[:, q])
     ref = dxa.cpu().numpy().astype(np.float64)
-    assert np.abs(moved - ref).max() <= 2 * TOL * np.abs(ref).max()
+    # the sum combines edge-node gradients far larger than the vertex ones (see above)
+    assert np.abs(moved - ref).max() <= TOL * max(np.abs(ref).max(), np.abs(dmn).max())
 
 
 @pytest.mark.parametrize("E", [1, 31, 33, 257])
@@ -147,7 +165,7 @@ def test_iso_adjoint_ragged_tails_and_flags(gfem, orc, E):
     got = gfem.integrate_bwd_iso(_t(mesh.coords), _t(conn), _t(m), ISO2, _t(dA), need_dcoef=True, dev_err=err)
     ref = orc.integrate_iso_vjp(3, LP2, conn, mesh.coords, m, dA)
     A_ref, fl = orc.integrate_iso(3, LP2, conn, mesh.coords, m)
-    errs = _errs(got, ref, A_ref, dA)
+    errs = _errs(got, ref, A_ref, dA, conn=conn)
     assert max(errs.values()) <= TOL, errs
     if E > 5:
         assert fl[5] == 1 and int(err.item()) & 1
@@ -191,4 +209,5 @@ def test_iso_adjoint_full_size_sample(gfem, orc):
     scale = (np.abs(dA[els].astype(np.float64)) * np.abs(A_ref)).reshape(len(els), -1).sum(1)
     assert (np.abs(dwn - rw) / scale).max() <= TOL
     gx = dx.cpu().numpy()[verts]
-    assert np.abs(gx - rx[verts]).max() <= TOL * np.abs(rx[verts]).max()
+    scale = node_scale(sub_conn, rx, rm)[verts]
+    assert (np.abs(gx - rx[verts]).max(1) / scale).max() <= TOL
