@@ -18,7 +18,9 @@
 //      k) d e_k[mu], vertex 0 gets minus their sum.
 // The vertex gradients take the affine adjoint's path (slot stage, tile
 // records, deterministic reduction; or red.add); the edge-node and
-// coefficient gradients are per element and are stored directly.
+// coefficient gradients are per element.  The tile's edge nodes come in, and
+// their gradients go out, through a shared-memory stage as contiguous 16-byte
+// pieces (an element's 18 floats are not 16-byte aligned on their own).
 #include "fem_bwd.cuh"
 #include "fem_iso.cuh"
 
@@ -104,6 +106,26 @@ __device__ __forceinline__ void all_vertex_pullback(const float (&ji)[D + 1][D][
   (vertex_pullback<D, Ks>(ji, dji, dec, dnd), ...);
 }
 
+// A tile's contiguous run of nf floats between global and shared memory, as
+// 16-byte pieces when both ends allow it (the edge nodes of 32 elements are
+// 2304 bytes on tets, 768 on triangles), else word by word.
+__device__ __forceinline__ void tile_load_async(float* st, const float* g, int nf, int lane) {
+  if ((reinterpret_cast<uintptr_t>(g) & 15) == 0 && (nf & 3) == 0) {
+    for (int q = lane; q < nf / 4; q += 32) cp_async<16>(st + 4 * q, g + 4 * q);
+  } else {
+    for (int q = lane; q < nf; q += 32) cp_async<4>(st + q, g + q);
+  }
+}
+
+__device__ __forceinline__ void tile_store(float* g, const float* st, int nf, int lane) {
+  if ((reinterpret_cast<uintptr_t>(g) & 15) == 0 && (nf & 3) == 0) {
+    for (int q = lane; q < nf / 4; q += 32)
+      __stcs(reinterpret_cast<float4*>(g) + q, *reinterpret_cast<const float4*>(st + 4 * q));
+  } else {
+    for (int q = lane; q < nf; q += 32) __stcs(g + q, st[q]);
+  }
+}
+
 // CTA shape: one-warp CTAs on tets (no CTA-wide barrier), each holding the
 // four inverse Jacobians, their adjoints and sym(dA) in registers.
 template <int D, int FORM>
@@ -112,10 +134,13 @@ struct IsoBwdShape {
   static constexpr int min_ctas = D == 3 ? (FORM == LAPLACE_P1_ISO ? 16 : 8) : 1;
 };
 
+// Per warp: [dA slot][slot stage][edge nodes of the tile, then their gradients].
 template <int D, int FORM>
 struct IsoBwdPlan {
   using PL = BwdPlan<D, FORM>;
-  static constexpr size_t per_warp = PL::da_slot + PL::xs_bytes;
+  static constexpr int NEF = D * D * (D + 1) / 2;  // edge-node floats per element
+  static constexpr size_t mid_bytes = align_up(size_t(32) * NEF * 4, 128);
+  static constexpr size_t per_warp = PL::da_slot + PL::xs_bytes + mid_bytes;
 };
 
 template <int D, int FORM, bool ATOMIC>
@@ -129,12 +154,15 @@ __global__ void __launch_bounds__(IsoBwdShape<D, FORM>::threads, IsoBwdShape<D, 
   unsigned char* wbase = smem_raw + size_t(warp) * IsoBwdPlan<D, FORM>::per_warp;
   float* dslot = reinterpret_cast<float*>(wbase);
   float* xs = reinterpret_cast<float*>(wbase + PL::da_slot);
+  float* ms = reinterpret_cast<float*>(wbase + PL::da_slot + PL::xs_bytes);  // [32][NE * D]
   const bool rec = !ATOMIC && p.tile_rec != nullptr;
   const int64_t ntiles = (p.n_elem + 31) / 32;
   int err = 0;
   for (int64_t t = int64_t(blockIdx.x) * nwarps + warp; t < ntiles; t += int64_t(gridDim.x) * nwarps) {
     const int64_t e = t * 32 + lane;
+    const int cnt = int(p.n_elem - t * 32 < 32 ? p.n_elem - t * 32 : 32);
     copy_dA_async<D, FORM>(p, t, lane, dslot);
+    tile_load_async(ms, mid + t * 32 * (NE * D), cnt * (NE * D), lane);
     cp_async_commit();
     int v[NV];
     float X[NV][D];
@@ -170,11 +198,11 @@ __global__ void __launch_bounds__(IsoBwdShape<D, FORM>::threads, IsoBwdShape<D, 
       for (int a = 0; a <= D; ++a)
 #pragma unroll
         for (int al = 0; al < D; ++al) nd[a][al] = X[a][al] - X[0][al];
-      const float* me = mid + e * (NE * D);
+      const float* me = ms + lane * (NE * D);
 #pragma unroll
       for (int q = 0; q < NE; ++q)
 #pragma unroll
-        for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = __ldcs(me + q * D + al) - X[0][al];
+        for (int al = 0; al < D; ++al) nd[D + 1 + q][al] = me[q * D + al] - X[0][al];
       float ji[NV][D][D], ec[D][D], adjc[D][D];
       ok = all_vertex_jinv<D>(nd, ji, ec, std::make_integer_sequence<int, NV>{});
       const float detc = det_adj<D>(ec, adjc) * (D == 2 ? (1.f / 9.f) : (1.f / 64.f));
@@ -235,13 +263,7 @@ __global__ void __launch_bounds__(IsoBwdShape<D, FORM>::threads, IsoBwdShape<D, 
     }
     if (flags & GF_ELEM) {
       if (p.dcoef) __stcs(p.dcoef + e, dw);
-      if (dmid) {
-        float* dm = dmid + e * (NE * D);
-#pragma unroll
-        for (int q = 0; q < NE; ++q)
-#pragma unroll
-          for (int al = 0; al < D; ++al) __stcs(dm + q * D + al, mb[q][al]);
-      }
+
       if constexpr (ATOMIC) {
         if (ok && p.dcoords)
 #pragma unroll
@@ -263,7 +285,16 @@ __global__ void __launch_bounds__(IsoBwdShape<D, FORM>::threads, IsoBwdShape<D, 
       __syncwarp();  // every lane's contributions are staged
       warp_records<D, PL::NC>(xs, p.rec_span, p.rec_dest, rb, rn, ah, p.records, lane);
     }
-    __syncwarp();  // the stage and the dA slot are rewritten next tile
+    if (dmid) {  // the tile's edge-node gradients through the stage, stored coalesced
+      __syncwarp();  // every lane has read its edge nodes
+#pragma unroll
+      for (int q = 0; q < NE; ++q)
+#pragma unroll
+        for (int al = 0; al < D; ++al) ms[lane * (NE * D) + q * D + al] = mb[q][al];
+      __syncwarp();
+      tile_store(dmid + t * 32 * (NE * D), ms, cnt * (NE * D), lane);
+    }
+    __syncwarp();  // the stages and the dA slot are rewritten next tile
   }
   err = __reduce_or_sync(0xffffffffu, err);
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
