@@ -20,7 +20,9 @@
 // shared stage, from which TMA tensor stores write 32 x 32 boxes of the
 // [n_elem][N*N] output.  The stage holds as many boxes as keep the most CTAs
 // resident; the last stores drain while the next tile's geometry is formed.
-// (Without a tensor map, a plain stage and coalesced 16-byte stores.)
+// (Without a tensor map, a plain stage and coalesced 16-byte stores.)  The
+// warp-specialized kernel further below runs the same steps for two tiles at
+// once: producers form tile i while consumers store tile i - 1.
 // Operands live in shared memory in the canonical no-swizzle K-major layout:
 // 8x16-byte core matrices, K-adjacent cores LBO bytes apart, M/N-adjacent cores
 // SBO bytes apart.  All waits are bounded: on a timeout the kernel flags
@@ -510,6 +512,221 @@ __global__ void __launch_bounds__(kTileElems)
   if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
 }
 
+// ------------------------------------------------------------------ warp-specialized pipeline
+// The kernel above takes each tile through geometry, split, MMA and epilogue
+// in turn.  This one overlaps them: a CTA of 8 warps where warps 0-3
+// (producers, one element per thread) form G, split it and write A tile i
+// into one of two A buffers while warps 4-7 (consumers) read the accumulator
+// of tile i - 1 from the other of two TMEM buffers and store it.  Thread 0
+// issues each tile's MMAs once its A rows are written and the consumers have
+// released that TMEM buffer.  mbarriers (all waits bounded):
+//   full[b]  -- the MMAs of the tile in buffer b completed (tcgen05.commit):
+//               the consumers may read D[b], the producers may rewrite A[b];
+//   empty[b] -- the four consumer warps read D[b] (one arrival each): the next
+//               MMAs into D[b] may start.
+// Use k of buffer b (tile i = 2k + b) waits on phase parity k & 1, so no
+// barrier ever runs more than one phase ahead of a waiter.  A timeout flags
+// FEM_DEVERR_TIMEOUT; the producers stop together at their next barrier, the
+// consumers at their next wait, and the teardown waits (bounded) for the last
+// MMAs before freeing TMEM.
+// Whether launches with a tensor map take the warp-specialized pipeline.
+constexpr bool kTcPipelined = true;
+
+template <int D, int FORM>
+struct TcWsPlan {
+  using TP = TcPlan<D, FORM>;
+  static constexpr int BOXES = TP::BOXES;
+  static constexpr size_t a_region = align_up(TP::a_bytes, 1024);
+  static constexpr size_t smem_for(int sbox) {
+    return TP::b_region + 2 * a_region + size_t(4) * sbox * 4096 + 128 + 1024;
+  }
+  static constexpr size_t kMaxSmem = 232448;  // opt-in shared memory of one CTA
+  static constexpr int pick_sbox() {
+    int s = BOXES;
+    while (s > 1 && smem_for(s) > kMaxSmem) --s;
+    return s;
+  }
+  static constexpr int SBOX = pick_sbox();
+  static constexpr int GROUPS = (BOXES + SBOX - 1) / SBOX;
+  static constexpr size_t stage_region = size_t(4) * SBOX * 4096;
+  static constexpr size_t smem = smem_for(SBOX);
+  static constexpr int TMEM_COLS = 2 * TP::N <= 32 ? 32 : (2 * TP::N <= 64 ? 64 : (2 * TP::N <= 128 ? 128 : 256));
+  static constexpr bool fits = smem <= kMaxSmem && 2 * TP::N <= 256;
+  // Whether the launcher takes this kernel.  Not for the curved elements:
+  // their G costs four inverse Jacobians per element (214 registers), and
+  // four producer warps per SM then bound the tile rate (measured 2.07 ms
+  // against 1.99 ms for two 4-warp CTAs of the kernel above on the warped
+  // 128^3 cube; elasticity 1.54 -> 1.14 ms, the P1-coefficient P2
+  // Laplacian 1.46 -> 1.36 ms).
+  static constexpr bool preferred = fits && !FormTraits<D, FORM>::ISO;
+};
+
+__device__ __forceinline__ void mbar_init_count(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+// Barrier 1 of the CTA, among its first 128 threads (the producer warps).
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, 128;\n" ::: "memory"); }
+
+template <int D, int FORM, class Geo, class KRef>
+__global__ void __launch_bounds__(2 * kTileElems, 1)
+    fem_fwd_tc_ws_kernel(FwdParams<float, float> p, const float* mid, const __grid_constant__ CUtensorMap tmap) {
+  using TP = TcPlan<D, FORM>;
+  using WP = TcWsPlan<D, FORM>;
+  using FT = FormTraits<D, FORM>;
+  extern __shared__ __align__(128) unsigned char smem_raw_ws[];
+  unsigned char* base = smem_raw_ws + ((1024u - (smem_u32(smem_raw_ws) & 1023u)) & 1023u);
+  unsigned char* sb = base;                                            // B operand
+  unsigned char* sa0 = base + TP::b_region;                            // A buffers 0, 1
+  unsigned char* stages = base + TP::b_region + 2 * WP::a_region;     // consumer warps' output stages
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + WP::stage_region);  // full[2], empty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  int* pabort = reinterpret_cast<int*>(bars + 5);  // written by thread 0 only, read after a producer barrier
+  int* cabort = pabort + 1;                        // a consumer warp timed out
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t nct = (p.n_elem + kTileElems - 1) / kTileElems;
+  if (int64_t(blockIdx.x) >= nct) return;  // CTA-uniform, before any barrier or TMEM allocation
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2);
+
+  tc_fill_b<D, FORM, KRef>(sb);
+  if (tid == 0) {
+    mbar_init_count(full0, 1);
+    mbar_init_count(full0 + 8, 1);
+    mbar_init_count(empty0, 4);
+    mbar_init_count(empty0 + 8, 4);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    *pabort = 0;
+    *cabort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "n"(WP::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  fence_proxy_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  int err = 0;
+  int issued = 0;  // thread 0: tiles whose MMAs it committed
+
+  if (warp < 4) {
+    // ---- producers: geometry, split, A tile, MMA issue (thread 0)
+    constexpr uint32_t idesc = idesc_bf16_f32<TP::M, TP::N>();
+    int v[D + 1];
+    float Xc[D + 1][D];
+    int64_t T = blockIdx.x;
+    const int vec_conn = (D == 3) && (reinterpret_cast<uintptr_t>(p.conn) % 16 == 0);
+    load_conn<D>(p.conn, T * kTileElems + tid, p.n_elem, vec_conn, v);
+    int fcur = gather_regs<D>(p.coords, p.n_vert, T * kTileElems + tid, p.n_elem, v, Xc);
+    float wcur = (p.coef && T * kTileElems + tid < p.n_elem) ? __ldg(p.coef + T * kTileElems + tid) : 1.f;
+    int vn[D + 1];
+    load_conn<D>(p.conn, (T + gridDim.x) * kTileElems + tid, p.n_elem, vec_conn, vn);
+    for (int i = 0; T < nct; ++i, T += gridDim.x) {
+      const int b = i & 1;
+      const int64_t en = (T + gridDim.x) * kTileElems + tid;
+      int vnn[D + 1];
+      load_conn<D>(p.conn, en + int64_t(gridDim.x) * kTileElems, p.n_elem, vec_conn, vnn);
+      float Xn[D + 1][D];
+      const int fnext = gather_regs<D>(p.coords, p.n_vert, en, p.n_elem, vn, Xn);
+      const float wnext = (p.coef && en < p.n_elem) ? __ldg(p.coef + en) : 1.f;
+      float G[FT::NG];
+#pragma unroll
+      for (int g = 0; g < FT::NG; ++g) G[g] = 0.f;
+      if (fcur & GF_OK) {
+        err |= Geo::template tile_g<D, FORM>(p, mid, T * kTileElems + tid, Xc, wcur, G);
+      } else if (fcur & GF_ELEM) {
+        err |= DEVERR_CONN;
+      }
+      // A[b] was last read by the MMAs of tile i - 2 (phase (i >> 1) - 1 of full[b])
+      if (i >= 2 && tid == 0 && !mbar_wait(full0 + 8 * b, uint32_t((i >> 1) - 1) & 1u)) *pabort = 1;
+      producer_sync();
+      if (*pabort) {
+        err |= DEVERR_TIMEOUT;
+        break;
+      }
+      tc_store_a_row<D, FORM>(sa0 + size_t(b) * WP::a_region, tid, G);
+      fence_proxy_async_smem();  // generic-proxy writes of A -> tensor-core reads
+      tc_fence_before();
+      producer_sync();
+      if (tid == 0) {
+        // D[b] was last read by the consumers of tile i - 2
+        if (i >= 2 && !mbar_wait(empty0 + 8 * b, uint32_t((i >> 1) - 1) & 1u)) {
+          *pabort = 1;  // seen by every producer after their next barrier
+        } else {
+          tc_fence_after();
+          const uint32_t sa = smem_u32(sa0 + size_t(b) * WP::a_region), sbb = smem_u32(sb);
+#pragma unroll
+          for (int s = 0; s < TP::KSTEPS; ++s) {
+            const uint64_t ad = smem_desc(sa + uint32_t(2 * s) * TP::A_LBO, TP::A_LBO, TP::A_SBO);
+            const uint64_t bd = smem_desc(sbb + uint32_t(2 * s) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
+            mma_bf16(tmem + uint32_t(b * TP::N), ad, bd, idesc, s > 0 ? 1u : 0u);
+          }
+          mma_commit(full0 + 8 * b);
+          ++issued;
+        }
+      }
+      fcur = fnext;
+      wcur = wnext;
+#pragma unroll
+      for (int k = 0; k <= D; ++k) {
+        vn[k] = vnn[k];
+#pragma unroll
+        for (int a = 0; a < D; ++a) Xc[k][a] = Xn[k][a];
+      }
+    }
+  } else {
+    // ---- consumers: TMEM lanes 32 cw .. 32 cw + 31 of D[b] -> swizzled stage -> TMA stores
+    const int cw = warp - 4;
+    unsigned char* wst = stages + size_t(cw) * WP::SBOX * 4096;
+    int64_t T = blockIdx.x;
+    for (int i = 0; T < nct; ++i, T += gridDim.x) {
+      const int b = i & 1;
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(full0 + 8 * b, uint32_t(i >> 1) & 1u) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
+        if (lane == 0) *cabort = 1;
+        err |= DEVERR_TIMEOUT;
+        break;
+      }
+      tc_fence_after();
+      float r[TP::N];
+      tc_load_all<TP::N>(tmem + (uint32_t(cw * 32) << 16) + uint32_t(b * TP::N), r,
+                         std::make_integer_sequence<int, TP::N / 16>{});
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8 * b);  // this warp has read its lanes of D[b]
+      const int64_t e0 = T * kTileElems + cw * 32;
+      if (lane == 0) bulk_wait_read<0>();  // the previous tile's tensor stores have read the stage
+      __syncwarp();
+      tc_store_groups<WP, FT::N, TP::NT>(r, wst, lane, &tmap, e0, e0 < p.n_elem,
+                                         std::make_integer_sequence<int, WP::GROUPS>{});
+      __syncwarp();
+    }
+    if (lane == 0) bulk_wait<0>();  // this warp's tensor stores are complete
+  }
+
+  // teardown: after a timeout, give the tensor core a bounded chance to finish the
+  // last committed MMAs before TMEM is freed
+  tc_fence_before();
+  __syncthreads();
+  if (tid == 0 && (*pabort || *cabort) && issued > 0)
+    mbar_wait(full0 + 8 * ((issued - 1) & 1), uint32_t((issued - 1) >> 1) & 1u);
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(WP::TMEM_COLS)
+                 : "memory");
+  }
+  err = __reduce_or_sync(0xffffffffu, err);
+  if (err && lane == 0 && p.dev_err) atomicOr(p.dev_err, err);
+}
+
 // G of an affine element with the compensated Jacobian (Eq. 8 / Eq. 15).
 struct TcGeoAffine {
   template <int D, int FORM>
@@ -572,6 +789,19 @@ cudaError_t launch_tc_t(const FwdLaunch& L, const float* mid) {
   p.vec_store = reinterpret_cast<uintptr_t>(L.A) % 16 == 0;
   CUtensorMap tmap{};
   const bool tma = encode_tc_rows_map(&tmap, L.A, L.n_elem, TcPlan<D, FORM>::FT::NN);
+  if constexpr (kTcPipelined && TcWsPlan<D, FORM>::preferred) {
+    if (tma) {  // the warp-specialized pipeline: one CTA of 8 warps per SM
+      using WP = TcWsPlan<D, FORM>;
+      auto wk = fem_fwd_tc_ws_kernel<D, FORM, Geo, KRef>;
+      cudaError_t st = ensure_smem(reinterpret_cast<const void*>(wk), WP::smem);
+      if (st != cudaSuccess) return st;
+      const int64_t nct = (L.n_elem + kTileElems - 1) / kTileElems;
+      int64_t grid = int64_t(L.ctas_per_sm > 0 ? L.ctas_per_sm : 1) * device_sm_count();
+      if (grid > nct) grid = nct;
+      wk<<<unsigned(grid < 1 ? 1 : grid), 2 * kTileElems, WP::smem, L.stream>>>(p, mid, tmap);
+      return cudaGetLastError();
+    }
+  }
   auto kern = tma ? fem_fwd_tc_kernel<D, FORM, Geo, KRef, true> : fem_fwd_tc_kernel<D, FORM, Geo, KRef, false>;
   const size_t smem = tma ? TP::template smem<true> : TP::template smem<false>;
   cudaError_t st = ensure_smem(reinterpret_cast<const void*>(kern), smem);
