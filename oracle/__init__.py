@@ -409,13 +409,27 @@ def integrate_div_vjp(dim: int, vdeg: int, conn, coords, dB, coef=None, q: int =
     return dcoords, dcoef
 
 
+def p2_dofs(dim: int, conn, n_vert: int):
+    """Global unknowns of the P2 basis over a mesh: the vertices 0 .. V-1,
+    then one per edge, V + k for the k-th distinct edge in increasing
+    (lower vertex, higher vertex) order.  Returns (dofs [E][n], n_unknowns)
+    with the element's unknowns in the local P2 order (vertices, then edges
+    (0,1),(0,2),...)."""
+    conn = np.asarray(conn, dtype=np.int64)
+    pairs = [(a, b) for a in range(dim + 1) for b in range(a + 1, dim + 1)]
+    lo = np.stack([np.minimum(conn[:, a], conn[:, b]) for a, b in pairs], axis=1)
+    hi = np.stack([np.maximum(conn[:, a], conn[:, b]) for a, b in pairs], axis=1)
+    uniq, inv = np.unique((lo * int(n_vert) + hi).ravel(), return_inverse=True)
+    return np.concatenate([conn, int(n_vert) + inv.reshape(lo.shape)], axis=1), int(n_vert) + len(uniq)
+
+
 def assemble(dim: int, form: int, conn, n_vert: int, A):
     """Global matrix sum_e P_e^T A_e P_e of the element matrices A [E][n][n]
     (FP64 scipy CSR over scalar unknowns): every element entry is placed at its
     global (row, column) and duplicates are summed (scipy's COO -> CSR
-    conversion).  P1 forms only: unknown v for the Laplacian; for P1 elasticity
-    the node-major unknown v*dim + c of the local unknown (c, i) = row
-    c*(dim+1) + i of A_e."""
+    conversion).  Unknown v for the P1 Laplacian; for P1 elasticity the
+    node-major unknown v*dim + c of the local unknown (c, i) = row
+    c*(dim+1) + i of A_e; for the P2 Laplacian the unknowns of p2_dofs."""
     import scipy.sparse as sps
     conn = np.asarray(conn, dtype=np.int64)
     A = np.asarray(A, dtype=np.float64)
@@ -426,8 +440,10 @@ def assemble(dim: int, form: int, conn, n_vert: int, A):
     elif form == LAPLACE_P1:
         g = conn
         N = n_vert
+    elif form == LAPLACE_P2:
+        g, N = p2_dofs(dim, conn, n_vert)
     else:
-        raise ValueError("assembly of the P1 forms only")
+        raise ValueError("assembly of the Laplacian (P1, P2) and P1 elasticity")
     n = g.shape[1]
     if A.shape != (E, n, n):
         raise ValueError("A must be [E][n][n]")

@@ -82,3 +82,53 @@ def test_assembled_elasticity_rigid_modes_and_energy(orc, dim):
     u = (x @ B.T).ravel()
     S = 0.5 * (B + B.T)
     assert abs(u @ (M @ u) - _volume(mesh) * np.sum(S * S)) <= 1e-11 * np.sum(S * S)
+
+
+LP2 = 1
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_p2_assembly_equals_brute_force(orc, dim):
+    """The P2 unknowns numbered by explicit loops (vertices, then the edges in
+    increasing (lower, higher) vertex order) and a dense sum of the element
+    matrices give the oracle's matrix."""
+    mesh = _mesh(dim)
+    A, _ = orc.integrate(dim, LP2, mesh.conn, mesh.coords)
+    M = orc.assemble(dim, LP2, mesh.conn, mesh.n_vert, A).toarray()
+    pairs = mg.edge_pairs(dim)
+    edges = sorted({(min(c[a], c[b]), max(c[a], c[b])) for c in mesh.conn.tolist() for a, b in pairs})
+    number = {ed: mesh.n_vert + k for k, ed in enumerate(edges)}
+    N = mesh.n_vert + len(edges)
+    D = np.zeros((N, N))
+    for e, c in enumerate(mesh.conn.tolist()):
+        g = c + [number[(min(c[a], c[b]), max(c[a], c[b]))] for a, b in pairs]
+        for i, gi in enumerate(g):
+            for j, gj in enumerate(g):
+                D[gi, gj] += A[e, i, j]
+    assert M.shape == (N, N)
+    assert np.abs(M - D).max() <= 1e-15 * np.abs(D).max()
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_assembled_p2_laplacian_identities(orc, dim):
+    """Symmetric, zero row sums, and the exact Dirichlet energy of a quadratic
+    field interpolated at the vertices and the edge midpoints."""
+    mesh = _mesh(dim)
+    A, _ = orc.integrate(dim, LP2, mesh.conn, mesh.coords)
+    M = orc.assemble(dim, LP2, mesh.conn, mesh.n_vert, A)
+    Md = M.toarray()
+    assert np.abs(Md - Md.T).max() <= 1e-14 * np.abs(Md).max()
+    assert np.abs(Md.sum(1)).max() <= 1e-13 * np.abs(Md).max()
+    dofs, N = orc.p2_dofs(dim, mesh.conn, mesh.n_vert)
+    pts = np.zeros((N, dim))
+    pts[:mesh.n_vert] = mesh.coords
+    for q, (a, b) in enumerate(mg.edge_pairs(dim)):
+        pts[dofs[:, dim + 1 + q]] = 0.5 * (mesh.coords[mesh.conn[:, a]] + mesh.coords[mesh.conn[:, b]])
+    # u = x_0^2 (in P2 on affine elements): int |grad u|^2 = int 4 x_0^2 over the mesh
+    u = pts[:, 0] ** 2
+    P = mesh.coords[mesh.conn]
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / (2 if dim == 2 else 6)
+    # exact int x^2 over a simplex: vol/((d+1)(d+2)) (sum x_i^2 + (sum x_i)^2) for vertex coordinates x_i
+    x0 = P[:, :, 0]
+    ex = (vol / ((dim + 1) * (dim + 2)) * ((x0 ** 2).sum(1) + x0.sum(1) ** 2)).sum()
+    assert abs(u @ (M @ u) - 4 * ex) <= 1e-12 * 4 * ex
