@@ -399,31 +399,46 @@ FEM_API void fem_batch_destroy(fem_batch* batch);
  * with d x d blocks over the same pattern (node-major unknowns v*d + c; block
  * (c, c') of entry (v, w) sums A_e[(c,i),(c',j)] over the elements with
  * conn[e][i] = v, conn[e][j] = w, local unknown (c, i) being row c*(d+1) + i
- * of A_e).  The P2 forms are not assembled (FEM_ERR_UNSUPPORTED): their
- * unknowns include the edges.  Every entry is a sum in a fixed order, so
- * values are bitwise reproducible: for the scalar forms, per 32-element tile
- * the tile's contributions in element order, then those tile sums in tile
- * order; for the blocks, all contributions in element order. */
+ * of A_e).  The P2 forms (FEM_LAPLACE_P2, FEM_LAPLACE_P2_W1,
+ * FEM_LAPLACE_P2_ISO) give CSR over the P2 unknowns: the vertices 0 .. V-1,
+ * then one unknown per edge, V + k for the k-th distinct edge in increasing
+ * (lower vertex, higher vertex) order (fem_assembly_unknowns returns their
+ * count and each element's unknowns in the local P2 order).  Every entry is a
+ * sum in a fixed order, so values are bitwise reproducible: for the scalar P1
+ * forms, per 32-element tile the tile's contributions in element order, then
+ * those tile sums in tile order; for the blocks and the P2 forms, all
+ * contributions in element order. */
 
 /* Device workspace bytes of the assembly maps of this mesh (depends on the
  * connectivity only; the capacity of the column array is every entry distinct). */
 FEM_API fem_status fem_assembly_workspace_size(const fem_mesh* mesh, int32_t form, size_t* bytes);
 
-/* Builds the row pattern (row_ptr [n_vert+1], col_idx [nnz], columns increasing)
+/* Builds the row pattern (row_ptr [n_rows+1], col_idx [nnz], columns increasing)
  * and the assembly maps into `ws` (device, caller owned, 256-byte aligned),
  * once per connectivity, on `stream`, which it synchronizes.  *nnz receives the
  * number of nonzero entries (blocks); *n_records the number of tile records of
  * the scalar forms (the distinct entries of every 32-element tile; 0 for
  * blocks).  Either output may be NULL.  A connectivity entry outside
  * [0, n_vert) is FEM_ERR_ARG; an element that repeats a vertex, or a vertex
- * with more than 128 elements or 255 neighbours, FEM_ERR_UNSUPPORTED. */
+ * with more than 128 elements or 255 neighbours (P2: an unknown with more than
+ * 255 neighbours or more than 51 incident elements on tets, 85 on triangles),
+ * FEM_ERR_UNSUPPORTED.  The P2 forms' workspace also holds the vertex graph's
+ * pattern, the edge numbers and the element unknowns. */
 FEM_API fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size_t ws_bytes, int64_t* nnz,
                                       int64_t* n_records, void* stream);
 
-/* Device pointers to the pattern inside a built workspace (row_ptr [n_vert+1],
- * col_idx [nnz]); either output may be NULL. */
+/* Device pointers to the pattern inside a built workspace (row_ptr [n_rows+1],
+ * col_idx [nnz], n_rows from fem_assembly_unknowns); either output may be NULL. */
 FEM_API fem_status fem_assembly_pattern(const fem_mesh* mesh, int32_t form, const void* ws, size_t ws_bytes,
                                         const int32_t** row_ptr, const int32_t** col_idx);
+
+/* The unknowns of a built assembly: *n_rows = the block rows of the matrix
+ * (n_vert for the P1 forms; n_vert + the edge count for the P2 forms, read
+ * from the device: this synchronizes it) and *dofs = a device pointer to each
+ * element's unknowns [n_elem][nodes] in the local order of its basis (mesh->conn
+ * for the P1 forms).  Either output may be NULL. */
+FEM_API fem_status fem_assembly_unknowns(const fem_mesh* mesh, int32_t form, const void* ws, size_t ws_bytes,
+                                         int64_t* n_rows, const int32_t** dofs);
 
 /* Assembles the FP32 element matrices A (device [n_elem][n][n], as written by
  * fem_integrate_fwd) into values (device FP32 [nnz][b][b], b = 1 or d; overwritten),

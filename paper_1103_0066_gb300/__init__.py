@@ -166,12 +166,14 @@ class Workspace:
 
 class Assembly:
     """Global sparse assembly (fem_assembly_*) of the element matrices of one
-    connectivity: CSR for the scalar P1 forms, BSR with d x d blocks for
-    ELASTIC_P1 (node-major unknowns v*d + c).
+    connectivity: CSR for the scalar forms, BSR with d x d blocks for
+    ELASTIC_P1 (node-major unknowns v*d + c).  The P2 forms' unknowns are the
+    vertices, then the edges in increasing (lower, higher) vertex order:
+    n_rows of them, dofs [E][n] each element's (device, int32).
 
-    row_ptr [V+1] and col_idx [nnz] (int32, device) describe the pattern;
+    row_ptr [n_rows+1] and col_idx [nnz] (int32, device) describe the pattern;
     assemble(A) returns the values [nnz] (or [nnz][d][d]) of sum_e P_e^T A_e P_e,
-    each entry summed in increasing element order."""
+    each entry summed in a fixed order."""
 
     def __init__(self, coords, conn, form=LAPLACE_P1, stream=None):
         self.m = _mesh_struct(coords, conn)
@@ -183,10 +185,13 @@ class Assembly:
         self.nnz, self.n_records = nat.fem_assembly_build(self.m, form, self.buf.data_ptr(), self.bytes,
                                                           _stream_ptr(stream))
         rp, ci = nat.fem_assembly_pattern(self.m, form, self.buf.data_ptr(), self.bytes)
-        V = coords.shape[0]
+        self.n_rows, dp = nat.fem_assembly_unknowns(self.m, form, self.buf.data_ptr(), self.bytes)
         base = self.buf.data_ptr()
-        self.row_ptr = self.buf[rp - base: rp - base + 4 * (V + 1)].view(torch.int32)
+        self.row_ptr = self.buf[rp - base: rp - base + 4 * (self.n_rows + 1)].view(torch.int32)
         self.col_idx = self.buf[ci - base: ci - base + 4 * self.nnz].view(torch.int32)
+        E, n = conn.shape[0], form_info(form, self.m.dim)[0] // self.block
+        self.dofs = (self.buf[dp - base: dp - base + 4 * E * n].view(torch.int32).view(E, n)
+                     if base <= dp < base + self.buf.numel() else conn)
 
     def assemble(self, A, out=None, stream=None):
         b = self.block

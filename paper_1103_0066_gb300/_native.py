@@ -30,7 +30,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
            "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy", "fem_tune_fwd",
-           "fem_tune_bwd", "fem_integrate_bwd_iso")
+           "fem_tune_bwd", "fem_integrate_bwd_iso", "fem_assembly_unknowns")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 DEVERR_TIMEOUT = 4
@@ -111,6 +111,7 @@ def load():
                                    ctypes.c_int),
             "fem_assembly_pattern": ([MP, I32, P, SZ, ctypes.POINTER(P), ctypes.POINTER(P)], ctypes.c_int),
             "fem_assemble": ([MP, I32, P, P, SZ, P, P], ctypes.c_int),
+            "fem_assembly_unknowns": ([MP, I32, P, SZ, ctypes.POINTER(I64), ctypes.POINTER(P)], ctypes.c_int),
             "fem_host_step_create": ([I32, I32, I64, I64, I64, ctypes.POINTER(P)], ctypes.c_int),
             "fem_host_step_run": ([P, P, P, P, P, P, I32, P], ctypes.c_int),
             "fem_host_step_destroy": ([P], None),
@@ -342,3 +343,9 @@ def fem_integrate_bwd_iso(mesh: FemMesh, form: int, mid_ptr: int, coef_ptr: int,
     check(load().fem_integrate_bwd_iso(ctypes.byref(mesh), form, mid_ptr or None, coef_ptr or None, dA_ptr or None,
                                        dcoords_ptr or None, dmid_ptr or None, dcoef_ptr or None, ws_ptr or None,
                                        ws_bytes, ctypes.byref(opts), stream or None))
+
+
+def fem_assembly_unknowns(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int):
+    n, d = ctypes.c_int64(), ctypes.c_void_p()
+    check(load().fem_assembly_unknowns(ctypes.byref(mesh), form, ws_ptr, ws_bytes, ctypes.byref(n), ctypes.byref(d)))
+    return n.value, d.value or 0

@@ -175,10 +175,12 @@ template <int NV, int B>
 __global__ void __launch_bounds__(kAsmThreads)
     assemble_kernel(const int32_t* __restrict__ inc_off, const int32_t* __restrict__ inc,
                     const uint8_t* __restrict__ colpos, const int32_t* __restrict__ row_ptr,
-                    const float* __restrict__ A, int64_t n_vert, float* __restrict__ val, int vec_A) {
+                    const float* __restrict__ A, int64_t n_vert, float* __restrict__ val, int vec_A,
+                    const int32_t* __restrict__ n_rows_dev) {
   constexpr int N = NV * B, BB = B * B;
   extern __shared__ float acc_s[];  // [kAsmThreads][kFastCols * BB + 1]
   float* acc = acc_s + threadIdx.x * (kFastCols * BB + 1);
+  if (n_rows_dev) n_vert = *n_rows_dev;  // rows known only on the device (P2 unknowns)
   for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert;
        v += int64_t(gridDim.x) * blockDim.x) {
     const int32_t rp = row_ptr[v];
@@ -675,7 +677,220 @@ cudaError_t launch_assemble_t(const AsmLayout& L, const float* A, int64_t n_vert
   if (e != cudaSuccess) return e;
   const int vec_A = reinterpret_cast<uintptr_t>(A) % 16 == 0;
   kern<<<grid_of(n_vert, kAsmThreads), kAsmThreads, smem, st>>>(L.inc_off, L.inc, L.colpos, L.row_ptr, A, n_vert,
-                                                                 val, vec_A);
+                                                                 val, vec_A, nullptr);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ P2 unknowns (vertices, then edges)
+//
+// The P2 basis has one unknown per vertex and one per edge.  The edges are
+// numbered from the vertex graph's pattern: row v's columns are sorted and
+// contain v, so the edges with lower vertex v are its columns above v, and
+// edge (v, w) gets V + eoff[v] + (position of w in row v) - (position of v) - 1
+// with eoff the exclusive scan of those counts: the edges in increasing
+// (lower vertex, higher vertex) order.  An element's unknowns (its vertices,
+// then its edges in the local P2 order) form the connectivity of a second
+// pattern, over the V + n_edges unknowns, which the row kernel assembles.
+
+// Arrays of the P2 assembly: the vertex graph's incidences and pattern
+// (positions per incidence), the edge offsets, the element unknowns, and the
+// unknowns' incidences and pattern.
+struct AsmP2Layout {
+  AsmLayout g1;  // vertex graph (inc_off, inc, colpos, row_ptr, col_idx, cursor, partials, flag)
+  AsmLayout g2;  // unknowns (same fields over up to V + E * n_edges rows)
+  int32_t* eoff;   // [V + 1]
+  int32_t* dofs;   // [E][n]
+  int32_t* n_rows; // one word: V + n_edges
+  int64_t rows_cap;
+  size_t bytes;
+};
+
+AsmP2Layout asm_p2_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
+  const int64_t nv = dim + 1, ne = dim * (dim + 1) / 2, n = nv + ne;
+  const int64_t rows_cap = n_vert + n_elem * ne;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = al256(off + bytes);
+    return o;
+  };
+  char* b = static_cast<char*>(base);
+  auto graph = [&](int64_t rows, int64_t per_elem, AsmLayout& G) {
+    const int64_t cap = n_elem * per_elem * per_elem;
+    const size_t o_inc_off = take(sizeof(int32_t) * size_t(rows + 1));
+    const size_t o_inc = take(sizeof(int32_t) * size_t(n_elem * per_elem));
+    const size_t o_colpos = take(size_t(cap));
+    const size_t o_row_ptr = take(sizeof(int32_t) * size_t(rows + 1));
+    const size_t o_col = take(sizeof(int32_t) * size_t(cap));
+    const size_t o_cursor = take(sizeof(int32_t) * size_t(rows + 1));
+    const size_t o_part = take(sizeof(int32_t) * scan_partials_count(rows + 1));
+    G.inc_off = reinterpret_cast<int32_t*>(b + o_inc_off);
+    G.inc = reinterpret_cast<int32_t*>(b + o_inc);
+    G.colpos = reinterpret_cast<uint8_t*>(b + o_colpos);
+    G.row_ptr = reinterpret_cast<int32_t*>(b + o_row_ptr);
+    G.col_idx = reinterpret_cast<int32_t*>(b + o_col);
+    G.cursor = reinterpret_cast<int32_t*>(b + o_cursor);
+    G.partials = reinterpret_cast<int32_t*>(b + o_part);
+  };
+  AsmP2Layout L{};
+  graph(n_vert, nv, L.g1);
+  graph(rows_cap, n, L.g2);
+  const size_t o_eoff = take(sizeof(int32_t) * size_t(n_vert + 1));
+  const size_t o_dofs = take(sizeof(int32_t) * size_t(n_elem * n));
+  const size_t o_flag = take(sizeof(int32_t) * 8);
+  L.eoff = reinterpret_cast<int32_t*>(b + o_eoff);
+  L.dofs = reinterpret_cast<int32_t*>(b + o_dofs);
+  L.g1.flag = reinterpret_cast<int32_t*>(b + o_flag);
+  L.g2.flag = L.g1.flag;
+  L.n_rows = L.g1.flag + 4;
+  L.rows_cap = rows_cap;
+  L.bytes = off;
+  return L;
+}
+
+// An element listing a vertex twice has no edge between the two: flagged.
+template <int NV>
+__global__ void check_repeat_kernel(const int32_t* __restrict__ conn, int64_t n_elem, int32_t* flag) {
+  int bad = 0;
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n_elem; e += int64_t(gridDim.x) * blockDim.x)
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+#pragma unroll
+      for (int j = i + 1; j < NV; ++j) bad |= conn[e * NV + i] == conn[e * NV + j];
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, ASM_REPEATED_VERTEX);
+}
+
+// Position of v in its own (sorted) row, or -1 for an empty row.
+__device__ __forceinline__ int diag_pos(const int32_t* __restrict__ col, int32_t b, int32_t e, int32_t v) {
+  int lo = b, hi = e;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (col[mid] < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return (lo < e && col[lo] == v) ? lo - b : -1;
+}
+
+// n_up[v] = the columns of row v above v: the edges whose lower vertex is v.
+__global__ void edge_count_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                  int64_t n_vert, int32_t* n_up) {
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert; v += int64_t(gridDim.x) * blockDim.x) {
+    const int32_t b = row_ptr[v], e = row_ptr[v + 1];
+    const int d = diag_pos(col, b, e, int32_t(v));
+    n_up[v] = d < 0 ? 0 : (e - b) - d - 1;
+  }
+}
+
+// Element unknowns in the local P2 order: each incidence (e, i) of row v
+// writes dofs[e][i] = v and, for every vertex w = conn[e][j] > v, the number
+// of edge (v, w) into the slot of local edge (min(i, j), max(i, j)): every
+// element edge is written once, by its lower vertex.
+template <int NV>
+__global__ void edge_dof_kernel(const int32_t* __restrict__ conn, const int32_t* __restrict__ inc_off,
+                                const int32_t* __restrict__ inc, const uint8_t* __restrict__ colpos,
+                                const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                const int32_t* __restrict__ eoff, int64_t n_vert, int32_t* __restrict__ dofs) {
+  constexpr int NB = NV + NV * (NV - 1) / 2;
+  for (int64_t v = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; v < n_vert; v += int64_t(gridDim.x) * blockDim.x) {
+    const int d = diag_pos(col, row_ptr[v], row_ptr[v + 1], int32_t(v));
+    const int64_t base = n_vert + eoff[v] - d - 1;
+    for (int32_t t = inc_off[v]; t < inc_off[v + 1]; ++t) {
+      const int32_t sl = inc[t];
+      const int64_t el = sl / NV;
+      const int i = sl % NV;
+      dofs[el * NB + i] = int32_t(v);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) {
+        if (j == i || conn[el * NV + j] <= v) continue;
+        const int a = i < j ? i : j, c = i < j ? j : i;
+        const int q = a * (2 * NV - a - 1) / 2 + (c - a - 1);
+        dofs[el * NB + NV + q] = int32_t(base + colpos[int64_t(t) * NV + j]);
+      }
+    }
+  }
+}
+
+__global__ void store_rows_kernel(const int32_t* __restrict__ eoff, int64_t n_vert, int32_t* n_rows) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_rows = int32_t(n_vert + eoff[n_vert]);
+}
+
+// The P2 build: vertex-graph pattern, edge numbers, element unknowns, then
+// the unknowns' pattern.  Returns the unknown count and the flags (host).
+template <int NV>
+cudaError_t launch_p2_build(const int32_t* conn, int64_t n_elem, int64_t n_vert, const AsmP2Layout& L,
+                            int32_t* rows_host, int32_t* flag_host, int32_t* nnz_host, cudaStream_t st) {
+  constexpr int NB = NV + NV * (NV - 1) / 2;
+  const AsmLayout& G1 = L.g1;
+  const AsmLayout& G2 = L.g2;
+  cudaError_t e = cudaMemsetAsync(G1.flag, 0, sizeof(int32_t) * 8, st);
+  if (e == cudaSuccess && n_elem > 0) {
+    check_conn_kernel<<<grid_of(n_elem * NV, 256), 256, 0, st>>>(conn, n_elem * NV, n_vert, G1.flag);
+    check_repeat_kernel<NV><<<grid_of(n_elem, 256), 256, 0, st>>>(conn, n_elem, G1.flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag_host, G1.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || *flag_host) return e;
+  const unsigned gv = grid_of(n_vert, kPatWarps);
+  if (e == cudaSuccess) e = launch_key_csr(conn, n_elem * NV, n_vert, G1.inc_off, G1.inc, G1.cursor, G1.partials, st);
+  if (e == cudaSuccess && n_vert > 0) {
+    row_pattern_kernel<NV, false><<<gv, kPatWarps * 32, 0, st>>>(conn, G1.inc_off, G1.inc, n_vert, G1.cursor,
+                                                                  G1.row_ptr, G1.col_idx, G1.colpos, G1.flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_exclusive_scan(G1.cursor, n_vert, G1.partials, G1.row_ptr, st);
+  if (e == cudaSuccess && n_vert > 0) {
+    row_pattern_kernel<NV, true><<<gv, kPatWarps * 32, 0, st>>>(conn, G1.inc_off, G1.inc, n_vert, G1.cursor,
+                                                                 G1.row_ptr, G1.col_idx, G1.colpos, G1.flag);
+    edge_count_kernel<<<grid_of(n_vert, 256), 256, 0, st>>>(G1.row_ptr, G1.col_idx, n_vert, G1.cursor);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_exclusive_scan(G1.cursor, n_vert, G1.partials, L.eoff, st);
+  if (e == cudaSuccess && n_vert > 0) {
+    edge_dof_kernel<NV><<<grid_of(n_vert, 256), 256, 0, st>>>(conn, G1.inc_off, G1.inc, G1.colpos, G1.row_ptr,
+                                                               G1.col_idx, L.eoff, n_vert, L.dofs);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    store_rows_kernel<<<1, 32, 0, st>>>(L.eoff, n_vert, L.n_rows);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rows_host, L.n_rows, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag_host, G1.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || *flag_host) return e;
+  const int64_t R = *rows_host;
+  const unsigned gr = grid_of(R, kPatWarps);
+  e = launch_key_csr(L.dofs, n_elem * NB, R, G2.inc_off, G2.inc, G2.cursor, G2.partials, st);
+  if (e == cudaSuccess && R > 0) {
+    row_pattern_kernel<NB, false><<<gr, kPatWarps * 32, 0, st>>>(L.dofs, G2.inc_off, G2.inc, R, G2.cursor,
+                                                                  G2.row_ptr, G2.col_idx, G2.colpos, G2.flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = launch_exclusive_scan(G2.cursor, R, G2.partials, G2.row_ptr, st);
+  if (e == cudaSuccess && R > 0) {
+    row_pattern_kernel<NB, true><<<gr, kPatWarps * 32, 0, st>>>(L.dofs, G2.inc_off, G2.inc, R, G2.cursor,
+                                                                 G2.row_ptr, G2.col_idx, G2.colpos, G2.flag);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(nnz_host, G2.row_ptr + R, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(flag_host, G1.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+template <int NB>
+cudaError_t launch_p2_assemble(const AsmP2Layout& L, const float* A, float* val, cudaStream_t st) {
+  const size_t smem = size_t(kAsmThreads) * (kFastCols + 1) * sizeof(float);
+  auto kern = assemble_kernel<NB, 1>;
+  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid_of(L.rows_cap, kAsmThreads), kAsmThreads, smem, st>>>(L.g2.inc_off, L.g2.inc, L.g2.colpos,
+                                                                     L.g2.row_ptr, A, L.rows_cap, val,
+                                                                     int(reinterpret_cast<uintptr_t>(A) % 16 == 0),
+                                                                     L.n_rows);
   return cudaGetLastError();
 }
 
@@ -692,13 +907,17 @@ fem_status asm_fail(fem_status s, const char* msg) {
   return s;
 }
 
-// Block size of the assembled matrix for a form: 1 (scalar P1 forms), d (P1
-// elasticity), 0 (not assembled: P2 unknowns include the edges).
+// Block size of the assembled matrix for a form: 1 (scalar forms), d (P1
+// elasticity), 0 (not assembled: the coupling blocks are rectangular).
 int asm_block(int form, int dim) {
   if (form == FEM_LAPLACE_P1 || form == FEM_LAPLACE_P1_W1 || form == FEM_LAPLACE_P1_ISO) return 1;
+  if (form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1 || form == FEM_LAPLACE_P2_ISO) return 1;
   if (form == FEM_ELASTIC_P1) return dim;
   return 0;
 }
+
+// P2 forms: unknowns at the vertices and the edges.
+bool asm_p2(int form) { return form == FEM_LAPLACE_P2 || form == FEM_LAPLACE_P2_W1 || form == FEM_LAPLACE_P2_ISO; }
 
 fem_status asm_check(const fem_mesh* mesh, int form) {
   if (!mesh) return asm_fail(FEM_ERR_ARG, "mesh is NULL");
@@ -707,9 +926,35 @@ fem_status asm_check(const fem_mesh* mesh, int form) {
     return asm_fail(FEM_ERR_ARG, "invalid mesh (dim 2/3, counts, conn)");
   if (form < FEM_LAPLACE_P1 || form > FEM_LAPLACE_P2_ISO) return asm_fail(FEM_ERR_ARG, "form out of range");
   if (asm_block(form, mesh->dim) == 0)
-    return asm_fail(FEM_ERR_UNSUPPORTED, "assembly serves the P1 forms (vertex unknowns)");
-  if (mesh->n_elem * (mesh->dim + 1) * (mesh->dim + 1) > INT32_MAX)
-    return asm_fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1)^2 exceeds the int32 entry range");
+    return asm_fail(FEM_ERR_UNSUPPORTED, "assembly serves the square forms");
+  const int64_t nodes = asm_p2(form) ? (mesh->dim + 1) * (mesh->dim + 2) / 2 : mesh->dim + 1;
+  if (mesh->n_elem * nodes * nodes > INT32_MAX)
+    return asm_fail(FEM_ERR_UNSUPPORTED, "n_elem * (nodes per element)^2 exceeds the int32 entry range");
+  return FEM_OK;
+}
+
+// The P2 build (fem_assembly_build for the P2 forms).
+fem_status p2_build(const fem_mesh* mesh, void* ws, size_t ws_bytes, int64_t* nnz, int64_t* n_records,
+                    cudaStream_t st) {
+  const fem::AsmP2Layout P = fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, ws);
+  if (!ws || ws_bytes < P.bytes || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
+    fem::set_last_error("assembly workspace needs %zu bytes, 256-byte aligned (got %zu)", P.bytes, ws_bytes);
+    return FEM_ERR_WORKSPACE;
+  }
+  int32_t rows = 0, flag = 0, nz = 0;
+  const cudaError_t e =
+      mesh->dim == 2 ? fem::launch_p2_build<3>(mesh->conn, mesh->n_elem, mesh->n_vert, P, &rows, &flag, &nz, st)
+                     : fem::launch_p2_build<4>(mesh->conn, mesh->n_elem, mesh->n_vert, P, &rows, &flag, &nz, st);
+  if (e != cudaSuccess) {
+    fem::set_last_error("fem_assembly_build: %s", cudaGetErrorString(e));
+    return FEM_ERR_CUDA;
+  }
+  if (flag & fem::ASM_BAD_VERTEX) return asm_fail(FEM_ERR_ARG, "a connectivity entry is outside [0, n_vert)");
+  if (flag & fem::ASM_REPEATED_VERTEX) return asm_fail(FEM_ERR_UNSUPPORTED, "an element repeats a vertex");
+  if (flag & fem::ASM_ROW_TOO_LONG)
+    return asm_fail(FEM_ERR_UNSUPPORTED, "an unknown has more than 255 neighbours or too many incident elements");
+  if (nnz) *nnz = nz;
+  if (n_records) *n_records = 0;
   return FEM_OK;
 }
 
@@ -721,7 +966,8 @@ fem_status fem_assembly_workspace_size(const fem_mesh* mesh, int32_t form, size_
   fem_status s = asm_check(mesh, form);
   if (s != FEM_OK) return s;
   if (!bytes) return asm_fail(FEM_ERR_ARG, "bytes is NULL");
-  *bytes = fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, nullptr).bytes;
+  *bytes = asm_p2(form) ? fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, nullptr).bytes
+                        : fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, nullptr).bytes;
   return FEM_OK;
 }
 
@@ -729,6 +975,7 @@ fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size
                               int64_t* n_records, void* stream) {
   fem_status s = asm_check(mesh, form);
   if (s != FEM_OK) return s;
+  if (asm_p2(form)) return p2_build(mesh, ws, ws_bytes, nnz, n_records, static_cast<cudaStream_t>(stream));
   const fem::AsmLayout L = fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, ws);
   if (!ws || ws_bytes < L.bytes || reinterpret_cast<uintptr_t>(ws) % 256 != 0) {
     fem::set_last_error("assembly workspace needs %zu bytes, 256-byte aligned (got %zu)", L.bytes, ws_bytes);
@@ -784,10 +1031,41 @@ fem_status fem_assembly_pattern(const fem_mesh* mesh, int32_t form, const void* 
                                 const int32_t** row_ptr, const int32_t** col_idx) {
   fem_status s = asm_check(mesh, form);
   if (s != FEM_OK) return s;
+  if (asm_p2(form)) {
+    const fem::AsmP2Layout P = fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, const_cast<void*>(ws));
+    if (!ws || ws_bytes < P.bytes) return asm_fail(FEM_ERR_WORKSPACE, "assembly workspace too small");
+    if (row_ptr) *row_ptr = P.g2.row_ptr;
+    if (col_idx) *col_idx = P.g2.col_idx;
+    return FEM_OK;
+  }
   const fem::AsmLayout L = fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, const_cast<void*>(ws));
   if (!ws || ws_bytes < L.bytes) return asm_fail(FEM_ERR_WORKSPACE, "assembly workspace too small");
   if (row_ptr) *row_ptr = L.row_ptr;
   if (col_idx) *col_idx = L.col_idx;
+  return FEM_OK;
+}
+
+fem_status fem_assembly_unknowns(const fem_mesh* mesh, int32_t form, const void* ws, size_t ws_bytes,
+                                 int64_t* n_rows, const int32_t** dofs) {
+  fem_status s = asm_check(mesh, form);
+  if (s != FEM_OK) return s;
+  if (!asm_p2(form)) {
+    if (n_rows) *n_rows = mesh->n_vert;
+    if (dofs) *dofs = mesh->conn;
+    return FEM_OK;
+  }
+  const fem::AsmP2Layout P = fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, const_cast<void*>(ws));
+  if (!ws || ws_bytes < P.bytes) return asm_fail(FEM_ERR_WORKSPACE, "assembly workspace too small");
+  if (n_rows) {
+    int32_t r = 0;
+    const cudaError_t e = cudaMemcpy(&r, P.n_rows, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      fem::set_last_error("fem_assembly_unknowns: %s", cudaGetErrorString(e));
+      return FEM_ERR_CUDA;
+    }
+    *n_rows = r;
+  }
+  if (dofs) *dofs = P.dofs;
   return FEM_OK;
 }
 
@@ -796,7 +1074,8 @@ fem_status fem_assemble(const fem_mesh* mesh, int32_t form, const float* A, cons
   fem_status s = asm_check(mesh, form);
   if (s != FEM_OK) return s;
   const fem::AsmLayout L = fem::asm_layout(mesh->dim, mesh->n_elem, mesh->n_vert, const_cast<void*>(ws));
-  if (!ws || ws_bytes < L.bytes || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
+  const size_t need = asm_p2(form) ? fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, nullptr).bytes : L.bytes;
+  if (!ws || ws_bytes < need || reinterpret_cast<uintptr_t>(ws) % 256 != 0)
     return asm_fail(FEM_ERR_WORKSPACE, "assembly workspace too small or unaligned");
   if (mesh->n_vert == 0) return FEM_OK;
   // without elements every row is empty and nothing is written
@@ -804,7 +1083,10 @@ fem_status fem_assemble(const fem_mesh* mesh, int32_t form, const float* A, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int B = asm_block(form, mesh->dim);
   cudaError_t e;
-  if (B == 1 && mesh->n_elem > 0)  // scalar forms: tile records, then the per-entry sums
+  if (asm_p2(form)) {  // the row kernel over the vertex and edge unknowns
+    const fem::AsmP2Layout P = fem::asm_p2_layout(mesh->dim, mesh->n_elem, mesh->n_vert, const_cast<void*>(ws));
+    e = mesh->dim == 2 ? fem::launch_p2_assemble<6>(P, A, values, st) : fem::launch_p2_assemble<10>(P, A, values, st);
+  } else if (B == 1 && mesh->n_elem > 0)  // scalar forms: tile records, then the per-entry sums
     e = mesh->dim == 2 ? fem::launch_tile_assemble_t<3>(L, A, mesh->n_elem, mesh->n_vert, values, st)
                        : fem::launch_tile_assemble_t<4>(L, A, mesh->n_elem, mesh->n_vert, values, st);
   else if (mesh->dim == 2)

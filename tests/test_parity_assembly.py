@@ -1,11 +1,13 @@
 """GPU parity of the global assembly (-m gpu).
 
-* The pattern (row_ptr, col_idx) equals the oracle's CSR structure exactly.
+* The pattern (row_ptr, col_idx) equals the oracle's CSR structure exactly;
+  for the P2 forms so do the unknowns (vertices, then edges in increasing
+  (lower, higher) vertex order) of every element.
 * The values equal, bit for bit, float32 sums of the same GPU element matrices
   in the order the library defines (numpy's unbuffered np.add.at): for the
-  scalar forms, per 32-element tile the contributions in element order, then
-  those tile sums in tile order; for P1 elasticity's blocks, all contributions
-  in element order.
+  scalar P1 forms, per 32-element tile the contributions in element order,
+  then those tile sums in tile order; for P1 elasticity's blocks and the P2
+  forms, all contributions in element order.
 * Against the FP64 oracle (oracle element matrices, assembled by the oracle):
   per row v, max |a_gpu - a_ref| <= 1e-5 * sum over the elements e at v of
   max |A_e| -- the element tolerance carried through the sum (a row of a
@@ -134,7 +136,11 @@ def test_assembly_errors_and_empty(gfem):
     mesh = _mesh(2)
     coords, conn = _t(mesh.coords), _t(mesh.conn)
     with pytest.raises(gfem.FemError):
-        gfem.Assembly(coords, conn, LP2)  # P2 unknowns include edges: unsupported
+        gfem.Assembly(coords, conn, 7)  # a coupling block is rectangular: not assembled
+    rep = mesh.conn.copy()
+    rep[4, 1] = rep[4, 0]
+    with pytest.raises(gfem.FemError):
+        gfem.Assembly(coords, _t(rep), LP2)  # an element repeating a vertex has no edge there
     bad = mesh.conn.copy()
     bad[4, 1] = mesh.n_vert + 2
     with pytest.raises(gfem.FemError):
@@ -143,3 +149,78 @@ def test_assembly_errors_and_empty(gfem):
     assert empty.nnz == 0 and torch.all(empty.row_ptr == 0)
     vals = empty.assemble(torch.empty((0, 3, 3), device=DEV))
     assert vals.numel() == 0
+
+
+def _p2_expected(dofs, A, n_rows):
+    """float32 sums of the element entries in element order (np.add.at is unbuffered, in index order)."""
+    E, n = dofs.shape
+    rows = np.repeat(dofs, n, axis=1).ravel()
+    cols = np.tile(dofs, (1, n)).ravel()
+    key = rows.astype(np.int64) * n_rows + cols
+    uk, inv = np.unique(key, return_inverse=True)
+    vals = np.zeros(len(uk), np.float32)
+    np.add.at(vals, inv, A.reshape(-1).astype(np.float32))
+    return uk // n_rows, uk % n_rows, vals
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("form", [LP2, 4, 6])
+@pytest.mark.parametrize("shuffle", [False, True])
+def test_p2_assembly_bitwise_and_oracle(gfem, orc, dim, form, shuffle):
+    """P2 Laplacian (per-element, P1-coefficient and curved): unknowns, pattern
+    and values against the oracle's P2 numbering and assembly."""
+    mesh = _mesh(dim, extra_vertices=2)
+    if shuffle:
+        mesh, _ = mg.shuffled(mesh, mg.rng_for(74))
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    V = mesh.n_vert
+    if form == LP2:
+        coef = mg.lognormal_coef(mg.rng_for(75), mesh.n_elem)
+        A = gfem.integrate_fwd(coords, conn, form, _t(coef))
+    elif form == 4:
+        A = gfem.integrate_fwd(coords, conn, form, _t(mg.lognormal_coef(mg.rng_for(76), V)))
+    else:
+        cm, mid = mg.curved_mesh(mesh, 0.03)
+        A = gfem.integrate_fwd_iso(_t(cm.coords), conn, _t(mid), form)
+    asm = gfem.Assembly(coords, conn, form)
+    vals = asm.assemble(A)
+    torch.cuda.synchronize()
+    dofs_ref, N = orc.p2_dofs(dim, mesh.conn, V)
+    assert asm.n_rows == N
+    assert np.array_equal(asm.dofs.cpu().numpy(), dofs_ref)
+    An = A.cpu().numpy()
+    M = orc.assemble(dim, LP2, mesh.conn, V, An.astype(np.float64))
+    rp, ci = asm.row_ptr.cpu().numpy(), asm.col_idx.cpu().numpy()
+    assert np.array_equal(rp, M.indptr) and np.array_equal(ci, M.indices)
+    r, c, v = _p2_expected(dofs_ref, An, N)
+    assert np.array_equal(ci, c) and np.array_equal(vals.cpu().numpy(), v)   # element order, float32: same bits
+    assert asm.nnz == len(v)
+    v2 = asm.assemble(A)
+    assert torch.equal(vals, v2)
+
+
+def test_p2_assembly_energy_of_a_quadratic(gfem):
+    """The assembled P2 Laplacian of the GPU element matrices gives the exact
+    Dirichlet energy of x_0^2 (interpolated at vertices and edge midpoints) to
+    FP32 accuracy."""
+    mesh = mg.cube_tet_mesh(6, 0.15, mg.rng_for(77), 0.0, np.float32)
+    coords, conn = _t(mesh.coords), _t(mesh.conn)
+    A = gfem.integrate_fwd(coords, conn, LP2)
+    asm = gfem.Assembly(coords, conn, LP2)
+    vals = asm.assemble(A).double().cpu().numpy()
+    dofs = asm.dofs.cpu().numpy()
+    pts = np.zeros((asm.n_rows, 3))
+    X = mesh.coords.astype(np.float64)
+    pts[:mesh.n_vert] = X
+    for q, (a, b) in enumerate(mg.edge_pairs(3)):
+        pts[dofs[:, 4 + q]] = 0.5 * (X[mesh.conn[:, a]] + X[mesh.conn[:, b]])
+    u = pts[:, 0] ** 2
+    rp, ci = asm.row_ptr.cpu().numpy(), asm.col_idx.cpu().numpy()
+    Ku = np.zeros_like(u)
+    for i in range(asm.n_rows):
+        Ku[i] = vals[rp[i]:rp[i + 1]] @ u[ci[rp[i]:rp[i + 1]]]
+    P = X[mesh.conn]
+    vol = np.abs(np.linalg.det(P[:, 1:] - P[:, :1])) / 6
+    x0 = P[:, :, 0]
+    exact = 4 * (vol / 20 * ((x0 ** 2).sum(1) + x0.sum(1) ** 2)).sum()
+    assert abs(u @ Ku - exact) <= 1e-5 * exact
