@@ -881,16 +881,69 @@ cudaError_t launch_p2_build(const int32_t* conn, int64_t n_elem, int64_t n_vert,
   return e;
 }
 
+// Rows of the P2 unknowns, 32 / NB of them per warp: lane group g (NB lanes)
+// takes its own row, which accumulates in shared memory (at most kMaxCols
+// columns).  For each incidence (e, i) of the row, in increasing element
+// order, lane j of the group adds A_e[i][j] at the column position of the
+// element's unknown j (distinct within an element); the group then stores the
+// row.  Each entry is the sum of its contributions in element order.  The
+// incidences' slots, positions and element rows are loaded NB incidences at a
+// time before their additions.
+constexpr int kRowWarps = 8;
+
+template <int NB>
+__global__ void __launch_bounds__(kRowWarps * 32)
+    assemble_rows_kernel(const int32_t* __restrict__ inc_off, const int32_t* __restrict__ inc,
+                         const uint8_t* __restrict__ colpos, const int32_t* __restrict__ row_ptr,
+                         const float* __restrict__ A, const int32_t* __restrict__ n_rows_dev,
+                         float* __restrict__ val) {
+  constexpr int G = 32 / NB;  // rows per warp
+  __shared__ float acc_s[kRowWarps][G][kMaxCols + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane / NB, j = lane - g * NB;
+  const bool member = g < G;
+  float* acc = acc_s[warp][member ? g : 0];
+  const int64_t n_rows = *n_rows_dev;
+  for (int64_t r0 = (int64_t(blockIdx.x) * kRowWarps + warp) * G; r0 < n_rows;
+       r0 += int64_t(gridDim.x) * kRowWarps * G) {
+    const int64_t r = r0 + g;
+    const bool live = member && r < n_rows;
+    const int32_t rp = live ? row_ptr[r] : 0;
+    const int len = live ? row_ptr[r + 1] - rp : 0;
+    const int32_t tb = live ? inc_off[r] : 0;
+    const int n_inc = live ? inc_off[r + 1] - tb : 0;
+    for (int c = j; c < len; c += NB) acc[c] = 0.f;
+    __syncwarp();
+    const int steps = __reduce_max_sync(0xffffffffu, n_inc);
+    // NB incidences at a time: lane j of the group loads incidence k0 + j's
+    // element slot and every incidence's column position j, then (after a
+    // shuffle of the slots) the NB element rows, then the additions in order
+    for (int k0 = 0; k0 < steps; k0 += NB) {
+      const int32_t my_sl = (k0 + j < n_inc) ? __ldg(inc + tb + k0 + j) : 0;
+      int pos[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) pos[u] = (k0 + u < n_inc) ? __ldg(colpos + (int64_t(tb) + k0 + u) * NB + j) : 0;
+      float a[NB];
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        const int32_t sl = __shfl_sync(0xffffffffu, my_sl, (member ? g * NB : 0) + u);
+        a[u] = (k0 + u < n_inc) ? __ldg(A + int64_t(sl / NB) * (NB * NB) + (sl % NB) * NB + j) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        if (k0 + u < n_inc) acc[pos[u]] += a[u];
+        __syncwarp();
+      }
+    }
+    for (int c = j; c < len; c += NB) __stcs(val + rp + c, acc[c]);
+    __syncwarp();  // the row buffers are refilled for the next rows
+  }
+}
+
 template <int NB>
 cudaError_t launch_p2_assemble(const AsmP2Layout& L, const float* A, float* val, cudaStream_t st) {
-  const size_t smem = size_t(kAsmThreads) * (kFastCols + 1) * sizeof(float);
-  auto kern = assemble_kernel<NB, 1>;
-  cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
-  if (e != cudaSuccess) return e;
-  kern<<<grid_of(L.rows_cap, kAsmThreads), kAsmThreads, smem, st>>>(L.g2.inc_off, L.g2.inc, L.g2.colpos,
-                                                                     L.g2.row_ptr, A, L.rows_cap, val,
-                                                                     int(reinterpret_cast<uintptr_t>(A) % 16 == 0),
-                                                                     L.n_rows);
+  assemble_rows_kernel<NB><<<grid_of(L.rows_cap, kRowWarps * (32 / NB)), kRowWarps * 32, 0, st>>>(
+      L.g2.inc_off, L.g2.inc, L.g2.colpos, L.g2.row_ptr, A, L.n_rows, val);
   return cudaGetLastError();
 }
 
