@@ -934,7 +934,7 @@ def run_assemble(args):
                  "algorithmic_bytes": byts2, "max_row_err_vs_fp64": err2,
                  "error_sample": f"all entries of {len(rows2)} vertex rows, against the FP64 oracle's element "
                                  "matrices summed over the library's unknowns",
-                 "kernel": "assemble_kernel<10,1> (one thread per unknown, incidences in element order)"}
+                 "kernel": "assemble_rows_kernel<10> (a row per 10-lane group, 3 rows per warp, incidences in element order)"}
     print(json.dumps(out), flush=True)
 
 
