@@ -537,7 +537,7 @@ def run_batch(args):
         cfg = bt.tune(stream=stream)
         mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
                       fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item",
-                      fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent"}
+                      fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent", fem.BATCH_PHASED: "phased"}
         per_mode = {}
         for mode in mode_names:  # each mode at full occupancy, chunk 1, in a CUDA graph
             bt.set_config(32, 1, mode)
@@ -569,7 +569,8 @@ def run_batch(args):
     peak, peak_kind = hbm_peak()
     kinds = {(it["src"].mesh.dim, it["form"]) for it in items if it["src"].mesh.n_elem > 0}
     launches = {fem.BATCH_SINGLE: 1, fem.BATCH_PER_ITEM: 3 * len(items),
-                fem.BATCH_PER_ITEM_CONCURRENT: 3 * len(items)}.get(cfg[2], len(kinds))
+                fem.BATCH_PER_ITEM_CONCURRENT: 3 * len(items),
+                fem.BATCH_PHASED: 3 * len(kinds)}.get(cfg[2], len(kinds))
     byts = batch_bytes(items)
     ach = byts / (batch_ms * 1e-3) / 1e9
     out = {
@@ -586,7 +587,8 @@ def run_batch(args):
                    "ms_per_step_max": tuned["ms_max"], "statistic": "median over repeats of K-step timed regions"},
         "roofline": {"bound": "hbm", "kernel": {fem.BATCH_SINGLE: "fem_batch_kernel",
                                                 fem.BATCH_PER_ITEM: "per-mesh kernels",
-                                                fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on ten streams"}.get(
+                                                fem.BATCH_PER_ITEM_CONCURRENT: "per-mesh kernels on ten streams",
+                                                fem.BATCH_PHASED: "multi-mesh fwd/adjoint/reduction kernels per kind"}.get(
                          cfg[2], "fem_batch_kind_kernel (all kinds)"), "achieved": ach, "peak": peak, "unit": "GB/s",
                      "frac": ach / peak, "peak_kind": f"{peak_kind} copy bandwidth", "traffic": None,
                      "algorithmic_bytes": byts},
@@ -1014,7 +1016,7 @@ def run_multiphysics(args):
     gbs = byts / (batch_ms * 1e-3) / 1e9
     mode_names = {fem.BATCH_SINGLE: "single", fem.BATCH_GROUPED: "grouped",
                   fem.BATCH_GROUPED_CONCURRENT: "grouped_concurrent", fem.BATCH_PER_ITEM: "per_item",
-                  fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent"}
+                  fem.BATCH_PER_ITEM_CONCURRENT: "per_item_concurrent", fem.BATCH_PHASED: "phased"}
     out = {"metric": METRIC, "value": len(items) * E / (batch_ms * 1e-3), "unit": "elements/s", "n_gpus": 1,
            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": batch_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",

@@ -311,6 +311,14 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
  *                         streams (longest first, each to the least loaded;
  *                         event fork/join on `stream`, graph-capturable), so
  *                         small meshes run beside large ones
+ *   FEM_BATCH_PHASED      per (dim, form) kind, three persistent launches over
+ *                         all of the kind's meshes: the forward, the adjoint
+ *                         element pass, the vertex reduction.  Each warp takes
+ *                         every S-th 32-element tile of the kind's meshes
+ *                         numbered one after the other, and the single-mesh
+ *                         kernels' pipeline runs across mesh boundaries; the
+ *                         kinds run on concurrent streams (the largest on
+ *                         `stream`; event fork/join, graph-capturable)
  * Every mode gives the same result bits as the per-mesh entry points.
  * Items may also be coupling blocks (FEM_DIV_P1P1, FEM_DIV_P2P1); a batch
  * holding one runs the per-item modes only (fem_batch_set_config refuses the
@@ -321,6 +329,7 @@ FEM_API fem_status fem_adjoint_reduce(const fem_mesh* mesh, const void* ws, size
 #define FEM_BATCH_GROUPED_CONCURRENT 2
 #define FEM_BATCH_PER_ITEM 3
 #define FEM_BATCH_PER_ITEM_CONCURRENT 4
+#define FEM_BATCH_PHASED 5
 
 #define FEM_PHASE_FWD 1 /* forward element matrices into item.A */
 #define FEM_PHASE_BWD 2 /* adjoint of item.dA into item.dcoords / item.dcoef */

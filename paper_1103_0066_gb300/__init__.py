@@ -24,10 +24,10 @@ from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENER
                       LAPLACE_P1_ISO, LAPLACE_P2_ISO, DIV_P1P1, DIV_P2P1,
                       REDUCE_ATOMIC, REDUCE_DEFERRED, REDUCE_DETERMINISTIC, PHASE_BWD, PHASE_FWD, FemError,
                       BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM,
-                      BATCH_PER_ITEM_CONCURRENT)
+                      BATCH_PER_ITEM_CONCURRENT, BATCH_PHASED)
 
 __all__ = ["Mesh", "Batch", "Assembly", "HostStep", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
-           "BATCH_PER_ITEM", "BATCH_PER_ITEM_CONCURRENT", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+           "BATCH_PER_ITEM", "BATCH_PER_ITEM_CONCURRENT", "BATCH_PHASED", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
            "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "DIV_P1P1", "DIV_P2P1", "form_shape",
            "integrate_fwd_iso", "JAC_AUTO",
@@ -574,7 +574,7 @@ class Batch:
     def config(self):
         """(CTAs per SM, work-chunk size, mode) used by run(); mode is one of
         BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM,
-        BATCH_PER_ITEM_CONCURRENT."""
+        BATCH_PER_ITEM_CONCURRENT, BATCH_PHASED."""
         return nat.fem_batch_config(self.handle)
 
     def set_config(self, ctas_per_sm, chunk, mode):

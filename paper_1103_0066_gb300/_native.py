@@ -33,6 +33,7 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_tune_bwd", "fem_integrate_bwd_iso", "fem_assembly_unknowns")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
+BATCH_PHASED = 5
 DEVERR_TIMEOUT = 4
 RECORDS_VERTEX_MAJOR, RECORDS_TILE_ORDER = 0, 1
 NOALLOC_SCRATCH_BYTES = 32 << 20

@@ -22,6 +22,11 @@
 // Grouped modes (FEM_BATCH_GROUPED, FEM_BATCH_GROUPED_CONCURRENT): the same
 // item scheme per (dim, form) kind, one kind-specialised pipelined kernel per
 // kind present, launched in order on one stream or forked onto side streams.
+//
+// Phased mode (FEM_BATCH_PHASED): per kind, the multi-mesh forward, adjoint
+// element pass and vertex reduction of fem_multi.cuh, one launch each over
+// all of the kind's meshes (kMultiMeshes at a time), the kinds forked onto
+// side streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -33,6 +38,7 @@
 #include "fem_bwd.cuh"
 #include "fem_fwd.cuh"
 #include "fem_internal.h"
+#include "fem_multi.cuh"
 
 namespace fem {
 
@@ -503,6 +509,7 @@ struct fem_batch {
   std::vector<fem::BatchMesh> desc;   // caller's order (single-kernel mode)
   std::vector<fem::BatchMesh> kdesc;  // grouped by kind, kind-local item ranges
   std::vector<int> kpos;              // position of each item's descriptor in kdesc (-1: in no group)
+  std::vector<int> kitem;             // the item of each kdesc entry
   fem::BatchMesh* d_desc = nullptr;
   fem::BatchMesh* d_kdesc = nullptr;
   fem::BatchCounters* d_ctr = nullptr;
@@ -697,11 +704,140 @@ cudaError_t launch_per_item(fem_batch* b, int phases, cudaStream_t st0, bool con
   return e;
 }
 
+// One kind's three multi-mesh launches on stream st (FEM_BATCH_PHASED): the
+// forward over the meshes that want A (keeping det J where the adjoint runs
+// in the same call), the adjoint element pass (meshes with and without a
+// saved det J in separate launches), then the vertex reduction.
+cudaError_t launch_kind_phases(fem_batch* b, const fem_batch::Group& g, int phases, cudaStream_t st) {
+  const int dim = g.kind / 3 + 2, form = g.kind % 3;
+  const bool both = (phases & FEM_PHASE_FWD) && (phases & FEM_PHASE_BWD);
+  int32_t* dev_err = &b->d_ctr->err;
+  cudaError_t e = cudaSuccess;
+  if (phases & FEM_PHASE_FWD) {
+    fem::FwdMulti P;
+    P.n = 0;
+    P.dev_err = dev_err;
+    P.tile_begin[0] = 0;
+    auto flush = [&]() {
+      if (P.n == 0 || e != cudaSuccess) return;
+      e = dim == 2 ? fem::launch_fwd_multi_d2(form, P, st) : fem::launch_fwd_multi_d3(form, P, st);
+      P.n = 0;
+    };
+    for (int j = g.first; j < g.first + g.count && e == cudaSuccess; ++j) {
+      const int i = b->kitem[size_t(j)];
+      const fem::BatchMesh& M = b->desc[size_t(i)];
+      if (!(M.flags & fem::BM_FWD) || M.n_elem == 0) continue;
+      fem::FwdParams<float, float>& p = P.p[P.n];
+      p.conn = M.conn;
+      p.coords = M.coords;
+      p.coef = M.coef;
+      p.A = M.A;
+      p.n_elem = M.n_elem;
+      p.n_vert = M.n_vert;
+      p.dev_err = dev_err;
+      p.vec_conn = (dim == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
+      p.vec_store = reinterpret_cast<uintptr_t>(M.A) % 16 == 0;
+      p.det_out = (both && (M.flags & fem::BM_BWD)) ? b->item_det[size_t(i)] : nullptr;
+      P.tile_begin[P.n + 1] = P.tile_begin[P.n] + (M.n_elem + 31) / 32;
+      if (++P.n == fem::kMultiMeshes) flush();
+    }
+    flush();
+  }
+  if (!(phases & FEM_PHASE_BWD) || e != cudaSuccess) return e;
+  for (int saved = 0; saved < 2 && e == cudaSuccess; ++saved) {
+    fem::BwdMulti P;
+    P.n = 0;
+    P.dev_err = dev_err;
+    P.tile_begin[0] = 0;
+    auto flush = [&]() {
+      if (P.n == 0 || e != cudaSuccess) return;
+      e = dim == 2 ? fem::launch_bwd_multi_d2(form, saved != 0, P, st)
+                   : fem::launch_bwd_multi_d3(form, saved != 0, P, st);
+      P.n = 0;
+    };
+    for (int j = g.first; j < g.first + g.count && e == cudaSuccess; ++j) {
+      const int i = b->kitem[size_t(j)];
+      const fem::BatchMesh& M = b->desc[size_t(i)];
+      if (!(M.flags & fem::BM_BWD) || M.n_elem == 0) continue;
+      const bool has_det = both && (M.flags & fem::BM_FWD);
+      if (has_det != (saved != 0)) continue;
+      const bool rec = (M.flags & fem::BM_REC) != 0;
+      const fem::BwdWorkspace& W = b->item_ws[size_t(i)];
+      fem::BwdParams& p = P.p[P.n];
+      p.conn = M.conn;
+      p.coords = M.coords;
+      p.coef = M.coef;
+      p.dA = M.dA;
+      p.tile_rec = rec ? W.tile_rec : nullptr;
+      p.rank = rec ? W.rank : nullptr;
+      p.rec_span = rec ? W.rec_span : nullptr;
+      p.rec_dest = rec ? W.rec_dest : nullptr;
+      p.records = rec ? W.records : nullptr;
+      p.dcoef = M.dcoef;
+      p.dcoords = M.dcoords;
+      p.n_elem = M.n_elem;
+      p.n_vert = M.n_vert;
+      p.dev_err = dev_err;
+      p.vec_conn = (dim == 3) && (reinterpret_cast<uintptr_t>(M.conn) % 16 == 0);
+      p.vec_dA = reinterpret_cast<uintptr_t>(M.dA) % 16 == 0;
+      p.det = has_det ? b->item_det[size_t(i)] : nullptr;
+      P.tile_begin[P.n + 1] = P.tile_begin[P.n] + (M.n_elem + 31) / 32;
+      if (++P.n == fem::kMultiMeshes) flush();
+    }
+    flush();
+  }
+  fem::RedMulti R;
+  R.n = 0;
+  R.blk_begin[0] = 0;
+  auto flush = [&]() {
+    if (R.n == 0 || e != cudaSuccess) return;
+    e = dim == 2 ? fem::launch_reduce_multi_d2(R, st) : fem::launch_reduce_multi_d3(R, st);
+    R.n = 0;
+  };
+  for (int j = g.first; j < g.first + g.count && e == cudaSuccess; ++j) {
+    const int i = b->kitem[size_t(j)];
+    const fem::BatchMesh& M = b->desc[size_t(i)];
+    if (!(M.flags & fem::BM_REC) || M.n_vert == 0) continue;
+    if (M.n_elem == 0) {  // no element: dcoords = 0
+      e = fem::launch_zero_f32(M.dcoords, M.n_vert * dim, st);
+      continue;
+    }
+    const fem::BwdWorkspace& W = b->item_ws[size_t(i)];
+    R.r[R.n] = fem::RedMesh{W.voff, W.vrec, W.mode, W.records, M.dcoords, M.n_vert};
+    R.blk_begin[R.n + 1] = R.blk_begin[R.n] + (M.n_vert + fem::kMultiRedBlock - 1) / fem::kMultiRedBlock;
+    if (++R.n == fem::kMultiMeshes) flush();
+  }
+  flush();
+  return e;
+}
+
+// FEM_BATCH_PHASED: the largest kind on st, the others forked onto side
+// streams and joined back.
+cudaError_t launch_phased(fem_batch* b, int phases, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  if (b->groups.size() < 2) {
+    for (const auto& g : b->groups)
+      if ((e = launch_kind_phases(b, g, phases, st)) != cudaSuccess) return e;
+    return cudaSuccess;
+  }
+  if ((e = cudaEventRecord(b->fork, st)) != cudaSuccess) return e;
+  for (size_t k = 1; k < b->groups.size(); ++k) {
+    if ((e = cudaStreamWaitEvent(b->aux[k], b->fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_kind_phases(b, b->groups[k], phases, b->aux[k])) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->join[k], b->aux[k])) != cudaSuccess) return e;
+  }
+  if ((e = launch_kind_phases(b, b->groups[0], phases, st)) != cudaSuccess) return e;
+  for (size_t k = 1; k < b->groups.size(); ++k)
+    if ((e = cudaStreamWaitEvent(st, b->join[k], 0)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
 cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, int mode, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(b->d_ctr, 0, b->ctr_bytes, st);
   if (e != cudaSuccess) return e;
   if (mode == FEM_BATCH_PER_ITEM || mode == FEM_BATCH_PER_ITEM_CONCURRENT)
     return launch_per_item(b, phases, st, mode == FEM_BATCH_PER_ITEM_CONCURRENT);
+  if (mode == FEM_BATCH_PHASED) return launch_phased(b, phases, st);
   if (mode == FEM_BATCH_SINGLE) {
     const int64_t total = (phases & FEM_PHASE_BWD) ? b->n_total : b->n_total_fwd;
     fem::fem_batch_kernel<<<unsigned(grid_for(ctas_per_sm, total, chunk)), fem::kTileElems, b->smem, st>>>(
@@ -728,7 +864,7 @@ cudaError_t launch_batch(fem_batch* b, int phases, int ctas_per_sm, int chunk, i
 }
 
 bool valid_config(int ctas_per_sm, int chunk, int mode) {
-  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_PER_ITEM_CONCURRENT && chunk >= 1 && chunk <= 64 &&
+  return mode >= FEM_BATCH_SINGLE && mode <= FEM_BATCH_PHASED && chunk >= 1 && chunk <= 64 &&
          ctas_per_sm >= 1 && ctas_per_sm <= 32;
 }
 
@@ -855,6 +991,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
       const fem::BatchMesh& M0 = b->desc[i];
       if (M0.kind != kind) continue;
       b->kpos[i] = int(b->kdesc.size());
+      b->kitem.push_back(int(i));
       fem::BatchMesh M = M0;
       M.ktile_begin = kt;
       kt += M.n_tiles;
@@ -966,15 +1103,16 @@ fem_status fem_batch_tune(fem_batch* b, int32_t phases, void* stream) {
   int best_c = b->ctas_per_sm, best_k = b->chunk, best_m = b->mode;
   const int chunks[] = {1, 2, 4, 8};
   cudaError_t err = cudaSuccess;
-  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_PER_ITEM_CONCURRENT && err == cudaSuccess; ++mode) {
-    const bool grouped = mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT;
+  for (int mode = FEM_BATCH_SINGLE; mode <= FEM_BATCH_PHASED && err == cudaSuccess; ++mode) {
+    const bool grouped = mode == FEM_BATCH_GROUPED || mode == FEM_BATCH_GROUPED_CONCURRENT || mode == FEM_BATCH_PHASED;
     const bool per_item = mode == FEM_BATCH_PER_ITEM || mode == FEM_BATCH_PER_ITEM_CONCURRENT;
+    const bool fixed = per_item || mode == FEM_BATCH_PHASED;  // no grid or chunk to tune
     if (grouped && b->groups.empty()) continue;
     if (!per_item && b->has_coupling) continue;  // the persistent kernels serve the square kinds
-    const int c_hi = per_item ? 1 : b->max_ctas_per_sm;  // per item: no grid or chunk to tune
+    const int c_hi = fixed ? 1 : b->max_ctas_per_sm;
     for (int c = 1; c <= c_hi && err == cudaSuccess; ++c)
       for (int k : chunks) {
-        if (per_item && k != 1) continue;
+        if (fixed && k != 1) continue;
         err = launch_batch(b, phases, c, k, mode, st);  // warm-up
         float ms_best = 1e30f;
         for (int rep = 0; rep < 3 && err == cudaSuccess; ++rep) {

@@ -42,13 +42,13 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-MODES = ["single", "grouped", "concurrent", "per_item", "per_item_concurrent"]
+MODES = ["single", "grouped", "concurrent", "per_item", "per_item_concurrent", "phased"]
 
 
 def _mode(gfem, name):
     return {"single": gfem.BATCH_SINGLE, "grouped": gfem.BATCH_GROUPED,
             "concurrent": gfem.BATCH_GROUPED_CONCURRENT, "per_item": gfem.BATCH_PER_ITEM,
-            "per_item_concurrent": gfem.BATCH_PER_ITEM_CONCURRENT}[name]
+            "per_item_concurrent": gfem.BATCH_PER_ITEM_CONCURRENT, "phased": gfem.BATCH_PHASED}[name]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -92,7 +92,7 @@ def test_batch_phases_separately(gfem, mode):
         assert not torch.isnan(it["dcoords"]).any() and not torch.isnan(it["dcoef"]).any()
 
 
-@pytest.mark.parametrize("mode", ["tuned", "concurrent"])
+@pytest.mark.parametrize("mode", ["tuned", "concurrent", "phased"])
 def test_batch_graph_capture_and_tuning(gfem, mode):
     items = _items(scale=0.002, n_meshes=48)
     batch = gfem.Batch(items)
@@ -102,11 +102,13 @@ def test_batch_graph_capture_and_tuning(gfem, mode):
     cfg = batch.tune()
     assert cfg[0] >= 1 and cfg[1] >= 1 and cfg[2] in (gfem.BATCH_SINGLE, gfem.BATCH_GROUPED,
                                                        gfem.BATCH_GROUPED_CONCURRENT, gfem.BATCH_PER_ITEM,
-                                                       gfem.BATCH_PER_ITEM_CONCURRENT)
+                                                       gfem.BATCH_PER_ITEM_CONCURRENT, gfem.BATCH_PHASED)
     if mode == "concurrent":  # fork/join side streams inside the capture
         batch.set_config(cfg[0], cfg[1], gfem.BATCH_GROUPED_CONCURRENT)
     if mode == "per_item_concurrent":
         batch.set_config(1, 1, gfem.BATCH_PER_ITEM_CONCURRENT)
+    if mode == "phased":  # per-kind multi-mesh launches forked onto side streams inside the capture
+        batch.set_config(1, 1, gfem.BATCH_PHASED)
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -220,3 +222,38 @@ def test_bounded_wait_expires_and_the_next_run_is_correct(gfem, mode):
     assert batch.errors() == 0
     for it, (A0, x0, w0) in zip(items, ref):
         assert torch.equal(it["A"], A0) and torch.equal(it["dcoords"], x0) and torch.equal(it["dcoef"], w0)
+
+
+def test_phased_many_meshes_per_kind_and_partial_outputs(gfem):
+    """The phased mode splits a kind's meshes into launches of at most 32, and
+    separates meshes whose adjoint takes det J from the forward from those
+    that recompute it.  70 triangle P1 meshes: some want only A, some only the
+    adjoint (no A, so no saved det J), some only dcoef (no records); every
+    output equals its per-mesh call bit for bit."""
+    src = [b for b in mg.mixed_batch(n_meshes=420, scale=0.002) if b.mesh.dim == 2 and b.form == 0][:70]
+    assert len(src) == 70
+    items = []
+    for k, b in enumerate(src):
+        m = b.mesh
+        it = {"coords": _t(m.coords), "conn": _t(m.conn), "form": 0, "coef": _t(b.coef), "src": b}
+        if k % 5 != 1:
+            it["A"] = torch.full((m.n_elem, 3, 3), float("nan"), device=DEV)
+        if k % 5 != 2:
+            it["dA"] = _t(b.dA)
+            it["dcoef"] = torch.full((m.n_elem,), float("nan"), device=DEV)
+            if k % 5 != 3:
+                it["dcoords"] = torch.full((m.n_vert, 2), float("nan"), device=DEV)
+        items.append(it)
+    batch = gfem.Batch(items)
+    batch.set_config(1, 1, gfem.BATCH_PHASED)
+    batch.run()
+    torch.cuda.synchronize()
+    assert batch.errors() == 0
+    for k, it in enumerate(items):
+        if "A" in it:
+            assert torch.equal(it["A"], gfem.integrate_fwd(it["coords"], it["conn"], 0, it["coef"])), k
+        if "dA" in it:
+            dx_ref, dw_ref = gfem.integrate_bwd(it["coords"], it["conn"], 0, it["dA"], it["coef"])
+            assert torch.equal(it["dcoef"], dw_ref), k
+            if "dcoords" in it:
+                assert torch.equal(it["dcoords"], dx_ref), k

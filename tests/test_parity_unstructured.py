@@ -195,11 +195,11 @@ def test_deferred_reduction_and_sharded_slices_unstructured(gfem, orc):
     assert _rel(acc, gx) <= TOL
 
 
-@pytest.mark.parametrize("mode", ["single", "grouped", "concurrent", "per_item", "per_item_concurrent"])
+@pytest.mark.parametrize("mode", ["single", "grouped", "concurrent", "per_item", "per_item_concurrent", "phased"])
 def test_batch_unstructured(gfem, orc, mode):
     modes = {"single": gfem.BATCH_SINGLE, "grouped": gfem.BATCH_GROUPED,
              "concurrent": gfem.BATCH_GROUPED_CONCURRENT, "per_item": gfem.BATCH_PER_ITEM,
-             "per_item_concurrent": gfem.BATCH_PER_ITEM_CONCURRENT}
+             "per_item_concurrent": gfem.BATCH_PER_ITEM_CONCURRENT, "phased": gfem.BATCH_PHASED}
     src = mg.mixed_batch(n_meshes=24, scale=0.003, shuffle=True)
     items = []
     for b in src:
