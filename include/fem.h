@@ -369,7 +369,8 @@ FEM_API fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items
 FEM_API fem_status fem_batch_tune(fem_batch* batch, int32_t phases, void* stream);
 
 /* The launch configuration in use (the tuner's choice, or the default:
- * FEM_BATCH_GROUPED at full occupancy, chunk 1).  NULL outputs are skipped. */
+ * FEM_BATCH_PHASED, or FEM_BATCH_PER_ITEM_CONCURRENT for a batch holding a
+ * coupling block; full occupancy, chunk 1).  NULL outputs are skipped. */
 FEM_API fem_status fem_batch_config(const fem_batch* batch, int32_t* ctas_per_sm, int32_t* chunk, int32_t* mode);
 
 /* Sets the launch configuration: ctas_per_sm 1..32 (capped at each kernel's

@@ -1070,7 +1070,7 @@ fem_status fem_batch_create(const fem_batch_item* items, int32_t n_items, void* 
   b->ctas_per_sm = b->max_ctas_per_sm;
   b->chunk = 1;
   b->mode = b->has_coupling ? FEM_BATCH_PER_ITEM_CONCURRENT
-            : b->groups.empty() ? FEM_BATCH_SINGLE : FEM_BATCH_GROUPED;
+            : b->groups.empty() ? FEM_BATCH_SINGLE : FEM_BATCH_PHASED;
   *out = b;
   return FEM_OK;
 }
