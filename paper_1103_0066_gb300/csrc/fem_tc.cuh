@@ -53,7 +53,8 @@ struct TcPlan {
   static constexpr uint32_t A_LBO = MC * 128, A_SBO = 128;  // A cores: (kc * MC + mc) * 128
   static constexpr uint32_t B_LBO = NC * 128, B_SBO = 128;  // B cores: (kc * NC + nc) * 128
   static constexpr size_t a_bytes = size_t(M) * K * 2;
-  static constexpr size_t b_bytes = size_t(N) * K * 2;
+  // B: K' * DEN once (KT rows); the three terms of A multiply the same B
+  static constexpr size_t b_bytes = size_t(N) * KT * 2;
   static constexpr int SST = stage_stride<FT::NN>();
   // the plain epilogue's stage (without a tensor map), aliasing the A tile
   static constexpr size_t stage_bytes = align_up(size_t(4) * 32 * SST * 4, 128);
@@ -66,11 +67,13 @@ struct TcPlan {
   }
   static constexpr size_t smem_for(size_t region) { return b_region + region + 128 + 1024; }  // + mbarrier, TMEM slot, slack
   // CTAs that the shared memory of an SM (228 KB, 1 KB reserved per CTA)
-  // holds, up to the four that 128-thread CTAs at 128 registers a thread fill
+  // holds, up to the ones the registers hold: four 128-thread CTAs at 128
+  // registers a thread, two for the curved tetrahedra's geometry (over 200)
+  static constexpr int reg_ctas = (FT::ISO && D == 3) ? 2 : 4;
   static constexpr int fit(int sbox) {
-    return int(size_t(233472) / (smem_for(region_for(sbox)) + 1024)) < 4
+    return int(size_t(233472) / (smem_for(region_for(sbox)) + 1024)) < reg_ctas
                ? int(size_t(233472) / (smem_for(region_for(sbox)) + 1024))
-               : 4;
+               : reg_ctas;
   }
   // the largest stage that keeps the most CTAs resident: a smaller stage costs
   // a wait for the tensor stores inside the epilogue
@@ -179,7 +182,7 @@ constexpr uint32_t bf16_of_int(int v) {
 // layout (core (k / 8, t / 8), row t % 8, column k % 8). Built at compile time.
 template <int D, int FORM>
 struct alignas(16) TcBImage {
-  uint16_t v[TcPlan<D, FORM>::N * TcPlan<D, FORM>::K];
+  uint16_t v[TcPlan<D, FORM>::N * TcPlan<D, FORM>::KT];
 };
 
 template <int D, int FORM>
@@ -196,7 +199,7 @@ constexpr TcBImage<D, FORM> make_tc_b_image() {
   const RefTensor<D, FORM> kt = make_ref_tensor<D, FORM>();
   TcBImage<D, FORM> im{};
   for (int t = 0; t < TP::N; ++t)
-    for (int k = 0; k < TP::K; ++k)
+    for (int k = 0; k < TP::KT; ++k)
       im.v[((k / 8) * TP::NC + t / 8) * 64 + (t % 8) * 8 + k % 8] = uint16_t(bf16_of_int(tc_b_value(kt, t, k)));
   return im;
 }
@@ -207,7 +210,7 @@ template <int D, int FORM>
 constexpr bool tc_b_exact() {
   const RefTensor<D, FORM> kt = make_ref_tensor<D, FORM>();
   for (int t = 0; t < TcPlan<D, FORM>::N; ++t)
-    for (int k = 0; k < TcPlan<D, FORM>::K; ++k)
+    for (int k = 0; k < TcPlan<D, FORM>::KT; ++k)
       if (bf16_of_int(tc_b_value(kt, t, k)) > 0xFFFFu) return false;
   return true;
 }
@@ -431,7 +434,7 @@ __global__ void __launch_bounds__(kTileElems)
 #pragma unroll
       for (int s = 0; s < TP::KSTEPS; ++s) {
         const uint64_t ad = smem_desc(sa + uint32_t(2 * s) * TP::A_LBO, TP::A_LBO, TP::A_SBO);
-        const uint64_t bd = smem_desc(sbb + uint32_t(2 * s) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
+        const uint64_t bd = smem_desc(sbb + uint32_t(2 * (s % (TP::KT / 16))) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
         mma_bf16(tmem, ad, bd, idesc, s > 0 ? 1u : 0u);
       }
       mma_commit(mbar);
@@ -663,7 +666,7 @@ __global__ void __launch_bounds__(2 * kTileElems, 1)
 #pragma unroll
           for (int s = 0; s < TP::KSTEPS; ++s) {
             const uint64_t ad = smem_desc(sa + uint32_t(2 * s) * TP::A_LBO, TP::A_LBO, TP::A_SBO);
-            const uint64_t bd = smem_desc(sbb + uint32_t(2 * s) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
+            const uint64_t bd = smem_desc(sbb + uint32_t(2 * (s % (TP::KT / 16))) * TP::B_LBO, TP::B_LBO, TP::B_SBO);
             mma_bf16(tmem + uint32_t(b * TP::N), ad, bd, idesc, s > 0 ? 1u : 0u);
           }
           mma_commit(full0 + 8 * b);

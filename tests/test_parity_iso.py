@@ -98,6 +98,32 @@ def test_iso_p2_tensor_cores(gfem, orc, dim, E):
         assert torch.all(A[5] == 0)
 
 
+@pytest.mark.parametrize("E", [None, 129, 300])
+def test_iso_tensor_core_kernels_agree(gfem, E):
+    """Curved tetrahedra on the tensor cores take the kernel with two threads
+    per element when the output is 16-byte aligned (tensor stores), and the
+    one-thread-per-element kernel otherwise: both form every G entry by the
+    same operations, so their outputs are the same bits (an invalid vertex
+    flagged and zeroed in both)."""
+    mesh, mid = _curved(3)
+    conn, m = mesh.conn, mid
+    if E is not None:
+        conn, m = conn[:E].copy(), mid[:E]
+        conn[5, 1] = mesh.n_vert + 7
+    n = conn.shape[0]
+    coef = _t(mg.lognormal_coef(mg.rng_for(44), n))
+    args = (_t(mesh.coords), _t(conn), _t(m), ISO2, coef)
+    err_a = torch.zeros(1, dtype=torch.int32, device=DEV)
+    A = gfem.integrate_fwd_iso(*args, dev_err=err_a, contract=gfem.CONTRACT_BF16X3)
+    buf = torch.full((n * 100 + 1,), float("nan"), device=DEV)
+    B = buf[1:].view(n, 10, 10)  # 4-byte offset: no tensor map, the one-thread kernel
+    assert B.data_ptr() % 16 != 0
+    err_b = torch.zeros(1, dtype=torch.int32, device=DEV)
+    gfem.integrate_fwd_iso(*args, out=B, dev_err=err_b, contract=gfem.CONTRACT_BF16X3)
+    assert torch.equal(A, B)
+    assert int(err_a.item()) == int(err_b.item())
+
+
 def test_iso_tensor_cores_only_for_p2(gfem):
     mesh, mid = _curved(3)
     with pytest.raises(gfem.FemError):
