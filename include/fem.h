@@ -536,8 +536,11 @@ FEM_API fem_status fem_tune_bwd(const fem_mesh* mesh, int32_t form, const float*
  *   dA [n_elem][n][n] FP32 (read); A [n_elem][n][n] FP32 and dcoords
  *   [n_vert][dim] FP32 (written): page-locked host memory (cudaHostAlloc or
  *   cudaHostRegister; FEM_ERR_ARG otherwise), on the step's device.  rebuild
- *   != 0 rebuilds the incidence (a new connectivity); the first run always
- *   builds it.  Asynchronous on `stream`: the step is done, and the host
+ *   != 0 copies conn in and rebuilds the incidence from it (a new
+ *   connectivity); the first run always does.  A run with rebuild == 0 keeps
+ *   the connectivity and the incidence of the last building run on the
+ *   device and does not read conn: per step, only coords and dA go in.
+ *   Asynchronous on `stream`: the step is done, and the host
  *   buffers may be reused, when the work queued on `stream` so far is.  The
  *   next run on the same step must be queued on the same stream (it reuses the
  *   device arrays).

@@ -420,7 +420,10 @@ class HostStep:
             raise ValueError(f"{name} must be a contiguous pinned host tensor {shape} {dtype}")
 
     def run(self, coords_h, conn_h, dA_h, A_h, dcoords_h, rebuild=False):
-        """One step; rebuild=True rebuilds the adjoint's incidence (new connectivity)."""
+        """One step; rebuild=True copies conn in and rebuilds the adjoint's
+        incidence (a new connectivity).  Runs with rebuild=False keep the
+        connectivity of the last building run on the device (conn_h is not
+        read); the first run always builds."""
         V, E, d, n = self.n_vert, self.n_elem, self.dim, self.n
         for t, shape, dtype, name in ((coords_h, (V, d), torch.float32, "coords"),
                                       (conn_h, (E, d + 1), torch.int32, "conn"),

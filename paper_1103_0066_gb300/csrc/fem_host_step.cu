@@ -172,8 +172,11 @@ fem_status fem_host_step_run(fem_host_step* h, const float* coords, const int32_
   e = cudaMemcpyAsync(h->coords, coords, sizeof(float) * h->n_vert * d, cudaMemcpyHostToDevice, h->copy_in);
   for (int64_t s = 0; s < n_slices && e == cudaSuccess; ++s) {
     const int64_t e0 = s * C, e1 = slice_end(s);
-    e = cudaMemcpyAsync(h->conn + e0 * (d + 1), conn + e0 * (d + 1), sizeof(int32_t) * (e1 - e0) * (d + 1),
-                        cudaMemcpyHostToDevice, h->copy_in);
+    // the connectivity goes in with the runs that build the incidence from it;
+    // the other runs reuse both (conn is not read)
+    if (build)
+      e = cudaMemcpyAsync(h->conn + e0 * (d + 1), conn + e0 * (d + 1), sizeof(int32_t) * (e1 - e0) * (d + 1),
+                          cudaMemcpyHostToDevice, h->copy_in);
     if (e == cudaSuccess) e = cudaEventRecord(h->conn_in[size_t(s)], h->copy_in);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->dA + e0 * nn, dA + e0 * nn, sizeof(float) * (e1 - e0) * nn, cudaMemcpyHostToDevice,

@@ -68,6 +68,27 @@ def test_host_step_rebuild_takes_new_connectivity(gfem):
         assert torch.equal(dx_h, dx_ref.cpu())
 
 
+def test_host_step_reuse_does_not_read_the_connectivity(gfem):
+    """A run without rebuild keeps the connectivity of the last building run
+    on the device: a connectivity buffer of zeros passed then changes nothing."""
+    mesh = mg.cube_tet_mesh(5, 0.15, mg.rng_for(97), 0.05, np.float32)
+    E, V = mesh.n_elem, mesh.n_vert
+    dA = np.random.default_rng(98).standard_normal((E, 4, 4)).astype(np.float32)
+    coords, conn = torch.from_numpy(mesh.coords).to(DEV), torch.from_numpy(mesh.conn).to(DEV)
+    A_ref = gfem.integrate_fwd(coords, conn, 0).cpu()
+    dx_ref, _ = gfem.integrate_bwd(coords, conn, 0, torch.from_numpy(dA).to(DEV), need_dcoef=False)
+    hs = gfem.HostStep(V, E, 3, chunk=256, device=DEV)
+    A_h, dx_h = torch.empty((E, 4, 4)).pin_memory(), torch.empty((V, 3)).pin_memory()
+    hs.run(_pinned(mesh.coords), _pinned(mesh.conn), _pinned(dA), A_h, dx_h)
+    zeros = _pinned(np.zeros_like(mesh.conn))
+    for _ in range(2):
+        A_h.zero_()
+        dx_h.zero_()
+        hs.run(_pinned(mesh.coords), zeros, _pinned(dA), A_h, dx_h)
+        torch.cuda.synchronize()
+        assert torch.equal(A_h, A_ref) and torch.equal(dx_h, dx_ref.cpu())
+
+
 def test_host_step_abi_refusals(gfem):
     from paper_1103_0066_gb300 import _native as nat
     with pytest.raises(nat.FemError) as ei:
