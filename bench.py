@@ -48,21 +48,22 @@ KERNEL_SOURCES = {
     "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": ("fem_bwd.cuh", "fem_bwd.cu", "fem_fwd.cuh", "fem_core.cuh",
                                                    "fem_forms.cuh", "fem_pipe.cuh", "fem_internal.h",
                                                    "fem_geometry.cu"),
-    "vertex_reduce_kernel<3>": ("fem_incidence.cu", "fem_internal.h"),
+    "vertex_reduce_kernel<3>": ("fem_incidence.cu", "fem_reduce.cuh", "fem_internal.h"),
     "fem_assemble<LAPLACE_P1>": ("fem_assembly.cu", "fem_pipe.cuh", "fem_internal.h"),
 }
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # 128^3 sliver cube (12,582,912 tets).  A capture with DRAM counters stays on a
-# smaller case, so these are the 96^3 cube's figures (one ncu capture of two
-# launches each, 5,308,416 tets, 4,852,051 records) scaled by the elements per
-# launch (x 2.370): records and vertices grow in the same proportion.  The
+# smaller case, so these are the 96^3 cube's figures (one ncu capture of one
+# launch each after three warm-up steps, 5,308,416 tets, 4,852,051 records)
+# scaled by the elements per launch (x 2.370): records and vertices grow in the
+# same proportion.  The
 # forward's and the reduction's scaled figures are lower bounds: the part of
 # their output still dirty in L2 when the kernel ends does not grow with it.
 NCU_TRAFFIC = {
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1320.8e6, "src": "54a2386e7e624da6"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 958.9e6, "src": "efe790d0d07e631f"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.4e6, "src": "05609e44c07bd899"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1320.8e6, "src": "bb819d3e0091a7e6"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 962.0e6, "src": "b3b18e6537a5f0c4"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.5e6, "src": "54eca1a421b6ef04"},
 }
 
 
