@@ -420,6 +420,62 @@ def run_ours(args):
                        "three streams, then the reduction and dcoords out",
                "bitwise_equal_to_device_path": match}
 
+    # the shuffled mesh renumbered by fem_mesh_order / fem_mesh_renumber (setup,
+    # once per mesh), then the same step in the new numbering
+    renumbered = None
+    if shuffled and not shard:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ep, vp = fem.mesh_order(coords, conn)
+        c2, k2 = fem.renumber(coords, conn, ep, vp)
+        torch.cuda.synchronize()
+        order_ms = (time.perf_counter() - t0) * 1e3
+        ws2 = fem.Workspace(c2, k2)
+        epl, vpl = ep.long(), vp.long()
+        dA2 = dA[epl].contiguous()  # dA in the new element numbering
+        A2 = torch.empty_like(A)
+        det2 = torch.empty_like(det)
+        dc2 = torch.empty_like(dcoords)
+        ev2 = []
+
+        def step2(rep=None, k=None):
+            evs = None
+            if rep is not None and len(ev2) < 4000:
+                evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev2.append(evs)
+                evs[0].record(stream)
+            fem.integrate_fwd(c2, k2, fem.LAPLACE_P1, out=A2, det_out=det2)
+            if evs is not None:
+                evs[1].record(stream)
+            fem.integrate_bwd(c2, k2, fem.LAPLACE_P1, dA2, ws=ws2, reduce=fem.REDUCE_DEFERRED, dcoords=dc2,
+                              need_dcoef=False, det=det2)
+            if evs is not None:
+                evs[2].record(stream)
+            fem.adjoint_reduce(c2, k2, ws2, dc2)
+            if evs is not None:
+                evs[3].record(stream)
+        for _ in range(args.warmup):
+            step2()
+        m2 = measure(step2, K, stream, dev, pg)
+        torch.cuda.synchronize()
+        per2 = {name: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev2]))
+                for i, name in enumerate(("fwd", "bwd_elem", "reduce"))}
+        R2 = ws2.n_records()
+        byts2 = algorithmic_bytes(E, V, R2, 4, 3, False)
+        renumbered = {
+            "what": "the shuffled mesh renumbered by fem_mesh_order + fem_mesh_renumber (Z-order of vertex "
+                    "positions and element centroids), then the same step",
+            "ms_per_step": m2["ms_per_step"], "ms_min": m2["ms_min"], "ms_max": m2["ms_max"],
+            "repeats": m2["repeats"], "clocks": m2["clocks"], "value": E / (m2["ms_per_step"] * 1e-3),
+            "kernels_ms": per2, "records": R2,
+            "record_layout": {0: "vertex-major", 1: "tile order"}.get(ws2.record_layout(), "?"),
+            "frac_of_peak": sum(byts2.values()) / (m2["ms_per_step"] * 1e-3) / 1e9 / hbm_peak()[0],
+            "setup_ms": {"order_and_renumber": order_ms},
+            "A_bitwise_equal_permuted": bool(torch.equal(A2, A[epl])),
+            "dcoords_max_rel_diff": float((dc2 - dcoords[vpl]).abs().max() / dcoords.abs().max()),
+        }
+        del A2, dA2, det2, dc2, ws2, c2, k2
+
     order = "elements in random order, vertices renumbered at random" if shuffled else "cell-major element order"
     par = (f"{ws_n} ranks each integrating a contiguous element range of the one mesh; dcoords summed by an "
            "NCCL all-reduce inside each step" if shard else
@@ -454,6 +510,7 @@ def run_ours(args):
                                         "fem_tune_fwd / fem_tune_bwd on this mesh"}
                                     for k, v in shapes.items()}},
         "e2e": e2e,
+        **({"renumbered": renumbered} if renumbered is not None else {}),
         "gpu_launches": 3 * K,  # per K-step timed region: forward, element pass, reduction
         "gpu_launches_all_repeats": 3 * K * m["repeats"],
         "clocks": m["clocks"],

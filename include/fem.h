@@ -554,6 +554,34 @@ FEM_API fem_status fem_host_step_run(fem_host_step* step, const float* coords, c
                                      const float* dA, float* A, float* dcoords, int32_t rebuild, void* stream);
 FEM_API void fem_host_step_destroy(fem_host_step* step);
 
+/* ------------------------------------------------------------------ mesh order
+ * A locality numbering for unstructured meshes (an addition beside the
+ * method).  The forward's coordinate gather and the adjoint's tile records
+ * (elements of one 32-element tile sharing vertices) profit from elements and
+ * vertices numbered along a space-filling curve; a mesh in random order loses
+ * both.  Vertices are ordered by the Z-order (Morton) code of their position,
+ * elements by the code of their centroid, quantised to a grid of 2^7 cells per
+ * axis (tetrahedra) or 2^10 (triangles) over the mesh's bounding box; equal
+ * codes keep the old order, so the result is deterministic.  An element with a
+ * vertex number out of range takes code 0.
+ *
+ * fem_mesh_order_workspace_size: bytes of device workspace (256-byte aligned)
+ *   for fem_mesh_order and fem_mesh_renumber; FP32 coordinates, dim 2 or 3.
+ * fem_mesh_order: elem_perm [n_elem] and vert_perm [n_vert] (device int32,
+ *   written): new position -> old number.  Synchronizes `stream` once per
+ *   order to check that no grid cell holds more than 1024 vertices or
+ *   elements (FEM_ERR_UNSUPPORTED otherwise: a mesh packed into few cells).
+ * fem_mesh_renumber: coords_out [n_vert][dim] = coords[vert_perm] and
+ *   conn_out [n_elem][dim+1] = the new numbers of conn[elem_perm] (device,
+ *   written; out-of-range vertex numbers are copied unchanged); the
+ *   workspace holds the inverse vertex order.  Every element keeps its
+ *   vertices in their local order, so its element matrix is unchanged. */
+FEM_API fem_status fem_mesh_order_workspace_size(const fem_mesh* mesh, size_t* bytes);
+FEM_API fem_status fem_mesh_order(const fem_mesh* mesh, void* ws, size_t ws_bytes, int32_t* elem_perm,
+                                  int32_t* vert_perm, void* stream);
+FEM_API fem_status fem_mesh_renumber(const fem_mesh* mesh, const int32_t* elem_perm, const int32_t* vert_perm,
+                                     void* ws, size_t ws_bytes, float* coords_out, int32_t* conn_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

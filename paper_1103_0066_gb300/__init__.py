@@ -27,7 +27,7 @@ from ._native import (CONTRACT_BF16X3, CONTRACT_F32, DEVERR_CONN, DEVERR_DEGENER
                       BATCH_PER_ITEM_CONCURRENT, BATCH_PHASED)
 
 __all__ = ["Mesh", "Batch", "Assembly", "HostStep", "PHASE_FWD", "PHASE_BWD", "BATCH_SINGLE", "BATCH_GROUPED", "BATCH_GROUPED_CONCURRENT",
-           "BATCH_PER_ITEM", "BATCH_PER_ITEM_CONCURRENT", "BATCH_PHASED", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
+           "BATCH_PER_ITEM", "BATCH_PER_ITEM_CONCURRENT", "BATCH_PHASED", "mesh_order", "renumber", "integrate", "integrate_fwd", "integrate_bwd", "geometry", "form_info",
            "reference_tensor", "FemError", "LAPLACE_P1", "LAPLACE_P2", "ELASTIC_P1", "LAPLACE_P1_W1",
            "LAPLACE_P2_W1", "LAPLACE_P1_ISO", "LAPLACE_P2_ISO", "DIV_P1P1", "DIV_P2P1", "form_shape",
            "integrate_fwd_iso", "JAC_AUTO",
@@ -162,6 +162,35 @@ class Workspace:
     def record_layout(self) -> int:
         """nat.RECORDS_VERTEX_MAJOR or nat.RECORDS_TILE_ORDER, as the build chose it."""
         return nat.fem_incidence_info(self.m, self.buf.data_ptr(), self.bytes, _stream_ptr(self.stream))[1]
+
+
+def mesh_order(coords, conn, stream=None):
+    """fem_mesh_order: a locality numbering of an unstructured mesh (Z-order of
+    vertex positions and element centroids).  Returns (elem_perm, vert_perm),
+    int32 CUDA tensors mapping new position -> old number."""
+    m = _mesh_struct(coords, conn)
+    ws_bytes = nat.fem_mesh_order_workspace_size(m)
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=coords.device)
+    elem_perm = torch.empty(conn.shape[0], dtype=torch.int32, device=coords.device)
+    vert_perm = torch.empty(coords.shape[0], dtype=torch.int32, device=coords.device)
+    nat.fem_mesh_order(m, ws.data_ptr(), ws_bytes, elem_perm.data_ptr(), vert_perm.data_ptr(), _stream_ptr(stream))
+    return elem_perm, vert_perm
+
+
+def renumber(coords, conn, elem_perm, vert_perm, stream=None):
+    """fem_mesh_renumber: the mesh in the new numbering, (coords[vert_perm],
+    new numbers of conn[elem_perm]); element matrices keep their values."""
+    m = _mesh_struct(coords, conn)
+    for t, n in ((elem_perm, conn.shape[0]), (vert_perm, coords.shape[0])):
+        if t.dtype != torch.int32 or not t.is_cuda or not t.is_contiguous() or t.numel() != n:
+            raise ValueError("permutations must be contiguous CUDA int32 tensors of n_elem / n_vert entries")
+    ws_bytes = nat.fem_mesh_order_workspace_size(m)
+    ws = torch.empty(max(ws_bytes, 256), dtype=torch.uint8, device=coords.device)
+    coords_out = torch.empty_like(coords)
+    conn_out = torch.empty_like(conn)
+    nat.fem_mesh_renumber(m, elem_perm.data_ptr(), vert_perm.data_ptr(), ws.data_ptr(), ws_bytes,
+                          coords_out.data_ptr(), conn_out.data_ptr(), _stream_ptr(stream))
+    return coords_out, conn_out
 
 
 class Assembly:

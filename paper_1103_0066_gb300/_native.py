@@ -30,7 +30,8 @@ EXPORTS = ("fem_version", "fem_status_string", "fem_last_error", "fem_form_info"
            "fem_batch_errors", "fem_batch_inject_wait", "fem_batch_destroy", "fem_assembly_workspace_size", "fem_assembly_build",
            "fem_assembly_pattern", "fem_assemble", "fem_integrate_fwd_iso", "fem_integrate_fwd_save",
            "fem_integrate_bwd_saved", "fem_host_step_create", "fem_host_step_run", "fem_host_step_destroy", "fem_tune_fwd",
-           "fem_tune_bwd", "fem_integrate_bwd_iso", "fem_assembly_unknowns")
+           "fem_tune_bwd", "fem_integrate_bwd_iso", "fem_assembly_unknowns", "fem_mesh_order_workspace_size",
+           "fem_mesh_order", "fem_mesh_renumber")
 PHASE_FWD, PHASE_BWD = 1, 2
 BATCH_SINGLE, BATCH_GROUPED, BATCH_GROUPED_CONCURRENT, BATCH_PER_ITEM, BATCH_PER_ITEM_CONCURRENT = 0, 1, 2, 3, 4
 BATCH_PHASED = 5
@@ -113,6 +114,9 @@ def load():
             "fem_assembly_pattern": ([MP, I32, P, SZ, ctypes.POINTER(P), ctypes.POINTER(P)], ctypes.c_int),
             "fem_assemble": ([MP, I32, P, P, SZ, P, P], ctypes.c_int),
             "fem_assembly_unknowns": ([MP, I32, P, SZ, ctypes.POINTER(I64), ctypes.POINTER(P)], ctypes.c_int),
+            "fem_mesh_order_workspace_size": ([MP, ctypes.POINTER(SZ)], ctypes.c_int),
+            "fem_mesh_order": ([MP, P, SZ, P, P, P], ctypes.c_int),
+            "fem_mesh_renumber": ([MP, P, P, P, SZ, P, P, P], ctypes.c_int),
             "fem_host_step_create": ([I32, I32, I64, I64, I64, ctypes.POINTER(P)], ctypes.c_int),
             "fem_host_step_run": ([P, P, P, P, P, P, I32, P], ctypes.c_int),
             "fem_host_step_destroy": ([P], None),
@@ -344,6 +348,22 @@ def fem_integrate_bwd_iso(mesh: FemMesh, form: int, mid_ptr: int, coef_ptr: int,
     check(load().fem_integrate_bwd_iso(ctypes.byref(mesh), form, mid_ptr or None, coef_ptr or None, dA_ptr or None,
                                        dcoords_ptr or None, dmid_ptr or None, dcoef_ptr or None, ws_ptr or None,
                                        ws_bytes, ctypes.byref(opts), stream or None))
+
+
+def fem_mesh_order_workspace_size(mesh: FemMesh) -> int:
+    b = ctypes.c_size_t()
+    check(load().fem_mesh_order_workspace_size(ctypes.byref(mesh), ctypes.byref(b)))
+    return b.value
+
+
+def fem_mesh_order(mesh: FemMesh, ws_ptr: int, ws_bytes: int, elem_perm: int, vert_perm: int, stream: int):
+    check(load().fem_mesh_order(ctypes.byref(mesh), ws_ptr, ws_bytes, elem_perm, vert_perm, stream))
+
+
+def fem_mesh_renumber(mesh: FemMesh, elem_perm: int, vert_perm: int, ws_ptr: int, ws_bytes: int, coords_out: int,
+                      conn_out: int, stream: int):
+    check(load().fem_mesh_renumber(ctypes.byref(mesh), elem_perm, vert_perm, ws_ptr, ws_bytes, coords_out, conn_out,
+                                   stream))
 
 
 def fem_assembly_unknowns(mesh: FemMesh, form: int, ws_ptr: int, ws_bytes: int):
