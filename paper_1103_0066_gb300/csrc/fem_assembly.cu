@@ -51,6 +51,13 @@ constexpr int kFastCols = 32;   // rows accumulated in shared memory
 constexpr int kPatWarps = 4;
 constexpr int kAsmThreads = 64;
 constexpr int kTileRuns = 36;  // dense tile matrix side (distinct vertices of a 32-element tile)
+// Row stride of a tile's cells, cell = row run * stride + column run: at least
+// kCellStride, so that the 16 cells of an element (4 runs x 4 runs) spread over
+// the shared-memory banks (a stride of the run count itself, near 32 on a
+// cell-major mesh, puts them in a few banks); the run count when it is larger.
+// Cells ordered by value are in (row run, column run) order either way.
+constexpr int kCellStride = 34;
+__host__ __device__ __forceinline__ int cell_stride(int nr) { return nr > kCellStride ? nr : kCellStride; }
 constexpr int kTileWarps = 1;  // warps per CTA of the tile pass (no CTA-wide barrier: finest sharing of shared memory)
 constexpr int kTileCap = 128;  // slots of a 32-element tile (tets: 4 per element)
 constexpr int kCellCap = 512;  // contributions of a 32-element tile (tets: 16 per element)
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(kPatWarps * 32)
         const int el = c / (NV * NV), ij = c % (NV * NV), i = ij / NV, j = ij % NV;
         const int ri = runi[el * NV + i], rj = runi[el * NV + j];
         if (i != j && ri == rj) rep = 1;  // an element repeats a vertex
-        k = (uint32_t(ri * nr + rj) << 6) | uint32_t(el);
+        k = (uint32_t(ri * cell_stride(nr) + rj) << 6) | uint32_t(el);
       }
       ckey[c] = k;
     }
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(kPatWarps * 32)
         if (head) {
           const int32_t rec = tile_rec[t] + nu + __popc(bal & ((1u << lane) - 1u));
           const uint32_t cell = ckey[i] >> 6;
-          const int32_t v = runv[cell / nr], w = runv[cell % nr];
+          const int32_t v = runv[cell / cell_stride(nr)], w = runv[cell % cell_stride(nr)];
           int lo = row_ptr[v], hi = row_ptr[v + 1];  // position of w in row v
           while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -471,10 +478,11 @@ __global__ void __launch_bounds__(kTileWarps * 32)
     const bool halves = (trc & kHalvesDisjoint) && ne == 32;
     const float* st = stage + sc * 32 * SST;
     const uint16_t* rc = rcs + sc * kCellCap;
+    const uint32_t ps = uint32_t(cell_stride(nr));
     if (nr <= kTileRuns && lane < ne) {
 #pragma unroll
       for (int ij = 0; ij < NN; ++ij)
-        cells[lane * 17 + ij] = ((rwc >> (8 * (ij / NV))) & 0xFFu) * uint32_t(nr) + ((rwc >> (8 * (ij % NV))) & 0xFFu);
+        cells[lane * 17 + ij] = ((rwc >> (8 * (ij / NV))) & 0xFFu) * ps + ((rwc >> (8 * (ij % NV))) & 0xFFu);
     }
     cp_async_wait<1>();
     __syncwarp();  // this tile's A and record cells (copied by every lane) and the cell indices are in place
@@ -506,7 +514,7 @@ __global__ void __launch_bounds__(kTileWarps * 32)
           const uint32_t w = __shfl_sync(0xffffffffu, rwc, l);
 #pragma unroll
           for (int ij = 0; ij < NN; ++ij)
-            if (int((w >> (8 * (ij / NV))) & 0xFFu) * nr + int((w >> (8 * (ij % NV))) & 0xFFu) == cell)
+            if (int((w >> (8 * (ij / NV))) & 0xFFu) * int(ps) + int((w >> (8 * (ij % NV))) & 0xFFu) == cell)
               acc += st[l * SST + ij];
         }
         if (live) records[rbc + r] = acc;
