@@ -188,7 +188,7 @@ unsigned grid_of(int64_t n) {
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Workspace: keys [max(E, V)], offsets and cursor [n_keys + 1] each, scan
-// partials, the box (8 ints), the inverse vertex order [V].
+// partials, the bounding box (8 ints), the inverse vertex order [V].
 struct OrderLayout {
   int32_t* keys;
   int32_t* off;
