@@ -906,7 +906,9 @@ __global__ void __launch_bounds__(kRowWarps * 32)
                          const float* __restrict__ A, const int32_t* __restrict__ n_rows_dev,
                          float* __restrict__ val) {
   constexpr int G = 32 / NB;  // rows per warp
-  __shared__ float acc_s[kRowWarps][G][kMaxCols + 1];
+  // row buffers 267 floats apart: the three rows of a warp start 11 banks apart
+  constexpr int kRowStride = kMaxCols + 12;
+  __shared__ float acc_s[kRowWarps][G][kRowStride];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane / NB, j = lane - g * NB;
   const bool member = g < G;
