@@ -278,7 +278,12 @@ FEM_API fem_status fem_integrate_bwd_saved(const fem_mesh* mesh, int32_t form, c
  * the workspace of fem_bwd_workspace_size / fem_incidence_build with this
  * form; FEM_REDUCE_DEFERRED leaves dcoords to fem_adjoint_reduce).  Elements
  * that are degenerate (J singular at a vertex or at the centroid) or have an
- * invalid vertex contribute zeros and set the device error bits. */
+ * invalid vertex contribute zeros and set the device error bits.
+ * options->contract: FEM_CONTRACT_F32, or FEM_CONTRACT_BF16X3 for
+ * FEM_LAPLACE_P2_ISO on tetrahedra with the deterministic or deferred
+ * reduction: the contraction's adjoint (sym(dA) times K' transposed) then
+ * runs on the tcgen05 tensor cores, sym(dA) split into three BF16 terms with
+ * FP32 accumulation; other combinations return FEM_ERR_UNSUPPORTED. */
 FEM_API fem_status fem_integrate_bwd_iso(const fem_mesh* mesh, int32_t form, const float* mid, const float* coef,
                                          const float* dA, float* dcoords, float* dmid, float* dcoef, void* ws,
                                          size_t ws_bytes, const fem_options* options, void* stream);

@@ -276,9 +276,11 @@ def integrate_bwd(coords, conn, form, dA, coef=None, ws: Workspace | None = None
 
 def integrate_bwd_iso(coords, conn, mid, form, dA, coef=None, ws: Workspace | None = None,
                       reduce=REDUCE_DETERMINISTIC, need_dcoords=True, need_dmid=True, need_dcoef=False,
-                      dcoords=None, dmid=None, dcoef=None, dev_err=None, stream=None):
+                      dcoords=None, dmid=None, dcoef=None, dev_err=None, stream=None, contract=CONTRACT_F32):
     """fem_integrate_bwd_iso: (dcoords [V][d], dmid [E][d(d+1)/2][d], dcoef [E]),
-    each None when not asked for, for the upstream dA of integrate_fwd_iso."""
+    each None when not asked for, for the upstream dA of integrate_fwd_iso.
+    contract=CONTRACT_BF16X3 runs the P2 contraction's adjoint on the tensor
+    cores (tetrahedra, deterministic or deferred reduction)."""
     m = _mesh_struct(coords, conn)
     E, V, d = conn.shape[0], coords.shape[0], m.dim
     ne = d * (d + 1) // 2
@@ -297,7 +299,7 @@ def integrate_bwd_iso(coords, conn, mid, form, dA, coef=None, ws: Workspace | No
         if ws is None:
             ws = Workspace(coords, conn, form, stream)
         ws_ptr, ws_bytes = ws.buf.data_ptr(), ws.bytes
-    opts = nat.options_struct(JAC_AUTO, 0, reduce, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
+    opts = nat.options_struct(JAC_AUTO, contract, reduce, 0, 0, dev_err.data_ptr() if dev_err is not None else 0)
     nat.fem_integrate_bwd_iso(m, form, mid.data_ptr(), _coef_ptr(coef, E), dA.data_ptr(),
                               dcoords.data_ptr() if dcoords is not None else 0,
                               dmid.data_ptr() if dmid is not None else 0,

@@ -546,7 +546,12 @@ fem_status fem_integrate_bwd_iso(const fem_mesh* mesh, int32_t form, const float
   if ((s = check_options(o)) != FEM_OK) return s;
   if (o->jac != FEM_JAC_AUTO && o->jac != FEM_JAC_F32)
     return fail(FEM_ERR_UNSUPPORTED, "non-affine elements compute their Jacobians in FP32");
-  if (o->contract != FEM_CONTRACT_F32) return fail(FEM_ERR_UNSUPPORTED, "the adjoint contracts in FP32");
+  const bool tc = o->contract == FEM_CONTRACT_BF16X3;
+  if (o->contract != FEM_CONTRACT_F32 &&
+      !(tc && mesh->dim == 3 && form == FEM_LAPLACE_P2_ISO && o->reduce != FEM_REDUCE_ATOMIC))
+    return fail(FEM_ERR_UNSUPPORTED,
+                "the adjoint contracts in FP32, or with FEM_CONTRACT_BF16X3 for FEM_LAPLACE_P2_ISO on tetrahedra "
+                "with the deterministic or deferred reduction");
   if (mesh->n_elem * (mesh->dim + 1) > INT32_MAX)
     return fail(FEM_ERR_UNSUPPORTED, "n_elem * (dim + 1) exceeds the int32 slot range");
   if (o->reduce == FEM_REDUCE_DEFERRED && !dcoords)
@@ -590,7 +595,7 @@ fem_status fem_integrate_bwd_iso(const fem_mesh* mesh, int32_t form, const float
     L.warps = 0;
     L.ctas_per_sm = o->ctas_per_sm;
     L.stream = st;
-    e = fem::launch_bwd_iso(L, mid, dmid);
+    e = tc ? fem::launch_bwd_iso_tc(L, mid, dmid) : fem::launch_bwd_iso(L, mid, dmid);
     if (e != cudaSuccess) return cuda_fail(e, "fem_integrate_bwd_iso element launch");
   }
   if (recs && o->reduce == FEM_REDUCE_DETERMINISTIC) {

@@ -82,9 +82,12 @@ struct BwdPlan {
   static constexpr bool VEC = (NN % 4 == 0);
   // 4x4 rows: unpadded, 16-byte chunk c of row r at chunk c ^ ((r >> 1) & 3),
   // so that both the copy (four lanes per row) and the row reads (a lane per
-  // row) are free of bank conflicts; other sizes: padded rows.
+  // row) are free of bank conflicts.  Other rows of 16-byte chunks: a stride of
+  // an odd number of chunks, so that the eight lanes of a 16-byte read phase
+  // (lane per row) reach eight different bank groups; odd-sized rows: an odd
+  // stride in words.
   static constexpr bool SWZ = (NN == 16);
-  static constexpr int DST = SWZ ? 16 : (VEC ? NN + 4 : (NN | 1));  // dA row stride in the stage
+  static constexpr int DST = SWZ ? 16 : (VEC ? ((NN / 4) % 2 ? NN : NN + 4) : (NN | 1));  // dA row stride
   static constexpr int NV = D + 1;
   static constexpr int NSW = kRecTile * NV;  // slots per record tile (one warp)
   static constexpr int XCAP = D == 3 ? kStageCap3 : NSW;  // stage positions (aligned runs on tets)
@@ -173,8 +176,32 @@ __device__ __forceinline__ void copy_dA_async(const BwdParams& p, int64_t tile, 
 }
 
 // Upper triangle of sym(dA) from a staged row (row = lane): 16-byte reads when
-// the row is 16-byte aligned and small enough to hold in registers, scalar
-// reads otherwise.
+// the row is 16-byte aligned (small rows whole into registers; larger ones a
+// chunk at a time, each entry going to its triangle slot: an upper entry
+// comes first in the row, so an off-diagonal slot is upper + lower, as
+// load_sym forms it), scalar reads otherwise.
+template <int N, int Q, int... Us>
+__device__ __forceinline__ void sym_chunk(const float4 v, float* s, std::integer_sequence<int, Us...>) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  (
+      [&] {
+        constexpr int i = (4 * Q + Us) / N, j = (4 * Q + Us) % N;
+        constexpr int lo = i < j ? i : j, hi = i < j ? j : i;
+        constexpr int T = pair_index(lo, hi, N);
+        static_assert(TriIdx<T, N>::i == lo && TriIdx<T, N>::j == hi, "triangle index");
+        if constexpr (i <= j)
+          s[T] = x[Us];
+        else
+          s[T] += x[Us];
+      }(),
+      ...);
+}
+
+template <int N, int... Qs>
+__device__ __forceinline__ void sym_chunks(const float* drow, float* s, std::integer_sequence<int, Qs...>) {
+  (sym_chunk<N, Qs>(reinterpret_cast<const float4*>(drow)[Qs], s, std::make_integer_sequence<int, 4>{}), ...);
+}
+
 template <int D, int FORM>
 __device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTraits<D, FORM>::NT]) {
   using FT = FormTraits<D, FORM>;
@@ -191,6 +218,8 @@ __device__ __forceinline__ void stage_sym(const float* drow, float (&s)[FormTrai
       r[4 * q + 3] = v.w;
     }
     load_sym<N>(r, s, std::make_integer_sequence<int, FT::NT>{});
+  } else if constexpr (NN % 4 == 0) {
+    sym_chunks<N>(drow, s, std::make_integer_sequence<int, NN / 4>{});
   } else {
     load_sym<N>(drow, s, std::make_integer_sequence<int, FT::NT>{});
   }

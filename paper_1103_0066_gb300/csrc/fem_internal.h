@@ -116,6 +116,9 @@ cudaError_t launch_bwd_elem(const BwdLaunch& L);
 // Adjoint element pass of the non-affine forms (LAPLACE_P1_ISO / LAPLACE_P2_ISO):
 // mid [E][d(d+1)/2][d] the edge nodes, dmid the same shape (may be null).
 cudaError_t launch_bwd_iso(const BwdLaunch& L, const float* mid, float* dmid);
+// The same for LAPLACE_P2_ISO on tetrahedra, deterministic or deferred, with
+// the contraction's adjoint on the tensor cores (fem_bwd_iso_tc.cu).
+cudaError_t launch_bwd_iso_tc(const BwdLaunch& L, const float* mid, float* dmid);
 cudaError_t launch_incidence_build(int dim, const int32_t* conn, int64_t n_elem, int64_t n_vert,
                                    const BwdWorkspace& ws, cudaStream_t stream);
 cudaError_t launch_zero_f32(float* p, int64_t n, cudaStream_t stream);

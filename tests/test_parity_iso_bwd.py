@@ -211,3 +211,60 @@ def test_iso_adjoint_full_size_sample(gfem, orc):
     gx = dx.cpu().numpy()[verts]
     scale = node_scale(sub_conn, rx, rm)[verts]
     assert (np.abs(gx - rx[verts]).max(1) / scale).max() <= TOL
+
+
+@pytest.mark.parametrize("E", [None, 1, 129, 300])
+def test_iso_adjoint_tensor_cores(gfem, orc, E):
+    """The curved P2 adjoint with its contraction on the tensor cores (sym(dA)
+    split into three BF16 terms, K' exact in BF16, FP32 accumulation): the same
+    tolerances against the oracle's reverse mode, over ragged 128-element CTA
+    tiles, an invalid vertex and a degenerate element flagged and zeroed;
+    reproducible bits, deferred = deterministic, and within the tolerance of
+    the FP32 adjoint."""
+    mesh, mid = _curved(3, seed=64, n=7)
+    conn, m = mesh.conn, mid
+    if E is not None:
+        conn, m = conn[:E].copy(), mid[:E].copy()
+        if E > 5:
+            conn[5, 1] = mesh.n_vert + 7
+        if E > 9:
+            conn[9, :] = conn[9, 0]
+            m[9] = mesh.coords[conn[9, 0]]
+    n_e = conn.shape[0]
+    coef = mg.lognormal_coef(mg.rng_for(65), n_e)
+    dA = np.random.default_rng(66).standard_normal((n_e, 10, 10)).astype(np.float32)
+    coords, conn_t, m_t = _t(mesh.coords), _t(conn), _t(m)
+    err = torch.zeros(1, dtype=torch.int32, device=DEV)
+    ws = gfem.Workspace(coords, conn_t, ISO2)
+    got = gfem.integrate_bwd_iso(coords, conn_t, m_t, ISO2, _t(dA), _t(coef), ws=ws, need_dcoef=True, dev_err=err,
+                                 contract=gfem.CONTRACT_BF16X3)
+    ref = orc.integrate_iso_vjp(3, LP2, conn, mesh.coords, m, dA, coef)
+    A_ref, fl = orc.integrate_iso(3, LP2, conn, mesh.coords, m, coef)
+    errs = _errs(got, ref, A_ref, dA, coef, conn)
+    assert max(errs.values()) <= TOL, errs
+    assert int(err.item()) == (int(np.bitwise_or.reduce(fl)) if fl.any() else 0)
+    if E is not None and E > 5:
+        assert torch.all(got[1][5] == 0) and float(got[2][5]) == 0.0
+    again = gfem.integrate_bwd_iso(coords, conn_t, m_t, ISO2, _t(dA), _t(coef), ws=ws, need_dcoef=True,
+                                   contract=gfem.CONTRACT_BF16X3)
+    assert all(torch.equal(a, b) for a, b in zip(got, again))
+    d = torch.empty_like(got[0])
+    gfem.integrate_bwd_iso(coords, conn_t, m_t, ISO2, _t(dA), _t(coef), ws=ws, reduce=gfem.REDUCE_DEFERRED,
+                           dcoords=d, need_dmid=False, contract=gfem.CONTRACT_BF16X3)
+    gfem.adjoint_reduce(coords, conn_t, ws, d)
+    assert torch.equal(d, got[0])
+    f32 = gfem.integrate_bwd_iso(coords, conn_t, m_t, ISO2, _t(dA), _t(coef), ws=ws, need_dcoef=True)
+    assert float((got[1] - f32[1]).abs().max()) <= TOL * float(f32[1].abs().max())
+
+
+def test_iso_adjoint_tensor_core_refusals(gfem):
+    from paper_1103_0066_gb300 import _native as nat
+    for dim, form, reduce in ((2, ISO2, gfem.REDUCE_DETERMINISTIC), (3, ISO1, gfem.REDUCE_DETERMINISTIC),
+                              (3, ISO2, gfem.REDUCE_ATOMIC)):
+        mesh, mid = _curved(dim)
+        n = gfem.form_info(form, dim)[0]
+        dA = torch.zeros((mesh.n_elem, n, n), device=DEV)
+        with pytest.raises(nat.FemError) as ei:
+            gfem.integrate_bwd_iso(_t(mesh.coords), _t(mesh.conn), _t(mid), form, dA, reduce=reduce,
+                                   contract=gfem.CONTRACT_BF16X3)
+        assert ei.value.status == nat.FEM_ERR_UNSUPPORTED
