@@ -1148,14 +1148,16 @@ def run_iso(args):
     R = ws.n_records()
     dx = torch.empty((V, 3), device=dev)
     dm = torch.empty_like(mid)
-    for name, form, n in (("p1_fwd_adjoint", fem.LAPLACE_P1_ISO, 4), ("p2_fwd_adjoint", fem.LAPLACE_P2_ISO, 10)):
+    for name, form, n, contract in (("p1_fwd_adjoint", fem.LAPLACE_P1_ISO, 4, fem.CONTRACT_F32),
+                                    ("p2_fwd_adjoint", fem.LAPLACE_P2_ISO, 10, fem.CONTRACT_F32),
+                                    ("p2_fwd_adjoint_tensor_core", fem.LAPLACE_P2_ISO, 10, fem.CONTRACT_BF16X3)):
         A = torch.empty((E, n, n), device=dev)
         dA_h = mg.upstream(mg.rng_for(13), E, n)
         dA = torch.from_numpy(dA_h).to(dev)
 
         def step():
-            fem.integrate_fwd_iso(coords, conn, mid, form, out=A)
-            fem.integrate_bwd_iso(coords, conn, mid, form, dA, ws=ws, dcoords=dx, dmid=dm)
+            fem.integrate_fwd_iso(coords, conn, mid, form, out=A, contract=contract)
+            fem.integrate_bwd_iso(coords, conn, mid, form, dA, ws=ws, dcoords=dx, dmid=dm, contract=contract)
         for _ in range(max(3, args.warmup)):
             step()
         torch.cuda.synchronize()
