@@ -61,9 +61,9 @@ KERNEL_SOURCES = {
 # forward's and the reduction's scaled figures are lower bounds: the part of
 # their output still dirty in L2 when the kernel ends does not grow with it.
 NCU_TRAFFIC = {
-    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1320.8e6, "src": "bb819d3e0091a7e6"},
-    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 962.0e6, "src": "b3b18e6537a5f0c4"},
-    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.5e6, "src": "54eca1a421b6ef04"},
+    "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1321.0e6, "src": "4a6c95b7dc30da51"},
+    "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 962.3e6, "src": "7c0682f050b938ea"},
+    "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.3e6, "src": "2fda9ba9be91ca76"},
 }
 
 
