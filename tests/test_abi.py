@@ -264,3 +264,39 @@ def test_host_step_refusals_on_host(fem):
     p = ctypes.c_void_p(0x3000)
     assert lib.fem_host_step_run(None, p, p, p, p, p, 0, None) == nat.FEM_ERR_ARG
     lib.fem_host_step_destroy(None)  # no-op
+
+
+def test_mesh_order_refusals_on_host(fem):
+    """fem_mesh_order / fem_mesh_renumber: argument refusals come before any
+    CUDA call, and the workspace size is a host computation."""
+    nat = fem.nat
+    lib = nat.load()
+    p = ctypes.c_void_p(0x3000)
+    b = ctypes.c_size_t()
+    m = _mesh(fem)
+    assert lib.fem_mesh_order_workspace_size(ctypes.byref(m), ctypes.byref(b)) == nat.FEM_OK and b.value > 0
+    assert lib.fem_mesh_order_workspace_size(None, ctypes.byref(b)) == nat.FEM_ERR_ARG
+    assert lib.fem_mesh_order_workspace_size(ctypes.byref(m), None) == nat.FEM_ERR_ARG
+    m64 = _mesh(fem, dtype=1)
+    assert lib.fem_mesh_order_workspace_size(ctypes.byref(m64), ctypes.byref(b)) == nat.FEM_ERR_UNSUPPORTED
+    m4 = _mesh(fem, dim=4)
+    assert lib.fem_mesh_order(ctypes.byref(m4), p, 1 << 30, p, p, None) == nat.FEM_ERR_ARG
+    assert lib.fem_mesh_order(ctypes.byref(m), p, 1 << 30, None, p, None) == nat.FEM_ERR_ARG
+    assert lib.fem_mesh_order(ctypes.byref(m), None, 0, p, p, None) == nat.FEM_ERR_WORKSPACE
+    assert lib.fem_mesh_renumber(ctypes.byref(m), p, p, p, 1 << 30, None, p, None) == nat.FEM_ERR_ARG
+    assert lib.fem_mesh_renumber(ctypes.byref(m), p, p, None, 0, p, p, None) == nat.FEM_ERR_WORKSPACE
+
+
+def test_iso_adjoint_contract_refusals_on_host(fem):
+    """fem_integrate_bwd_iso takes FEM_CONTRACT_BF16X3 for the P2 form on
+    tetrahedra with the deterministic or deferred reduction only."""
+    nat = fem.nat
+    lib = nat.load()
+    A = ctypes.c_void_p(0x3000)
+    tc = nat.options_struct(contract=nat.CONTRACT_BF16X3)
+    tca = nat.options_struct(contract=nat.CONTRACT_BF16X3, reduce=nat.REDUCE_ATOMIC)
+    m3, m2 = _mesh(fem), _mesh(fem, dim=2)
+    for mesh, form, opts in ((m3, nat.LAPLACE_P1_ISO, tc), (m2, nat.LAPLACE_P2_ISO, tc),
+                             (m3, nat.LAPLACE_P2_ISO, tca)):
+        assert lib.fem_integrate_bwd_iso(ctypes.byref(mesh), form, A, None, A, A, None, None, None, 0,
+                                         ctypes.byref(opts), None) == nat.FEM_ERR_UNSUPPORTED
