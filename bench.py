@@ -935,8 +935,8 @@ def run_assemble(args):
         err = max(err, max(abs(got.get(k, 0.0) - ref[k]) for k in ref) / bound[v])
     nnz, R2 = asm.nnz, asm.n_records
     T = (E + 31) // 32
-    # tile pass: A, run words, record cells, tile offsets/runs, records written;
-    # entry pass: entry offsets, record list, records read, values written
+    # tile pass: A, run words, record cells, tile offsets/runs, record slots read, records written;
+    # entry pass: entry offsets, records read (contiguous), values written
     byts = E * 64 + E * 4 + R2 * 2 + T * 6 + R2 * 4 + (nnz + 1) * 4 + R2 * 4 + R2 * 4 + nnz * 4
     peak, peak_kind = hbm_peak()
     gbs = byts / (asm_ms * 1e-3) / 1e9

@@ -17,17 +17,18 @@
 //   per 32-element tile (one warp): the tile's distinct vertices ("runs", R_t
 //   of them) and every slot's run index (one byte); the distinct (row run,
 //   column run) cells the tile touches, each one RECORD (records numbered in
-//   tile order), and the entry -> records CSR (eoff, rec_list) -- the tile /
-//   record scheme of the adjoint's reduction, keyed by matrix entry.
+//   tile order), the entry -> records CSR (eoff, rec_list) and its inverse,
+//   every record's slot in entry order (rec_dest) -- the tile / record scheme
+//   of the adjoint's reduction, keyed by matrix entry.
 // Assembly of the scalar forms (fem_assemble):
 //   1. one warp per tile reads its element matrices coalesced into shared
 //      memory and adds them, element by element, into a dense R_t x R_t tile
 //      matrix (an element's cells are distinct, so a step has no conflicts);
-//      each cell is the sum of its contributions in element order.  The cells
-//      are written as records, in tile order (tiles with R_t above kTileRuns
-//      take an exact per-record scan of the tile instead);
-//   2. one thread per entry sums its records (gathered through rec_list) in
-//      tile order.
+//      each cell is the sum of its contributions in element order.  Each cell
+//      is written as a record to its slot in entry order (tiles with R_t above
+//      kTileRuns take an exact per-record scan of the tile instead);
+//   2. one thread per entry sums its records, which lie side by side in tile
+//      order, so the pass reads them contiguously.
 // Every entry is therefore a fixed-order sum, bitwise reproducible.
 // P1 elasticity (d x d blocks) takes the row kernel: one thread per row walks
 // its incidences in increasing element order and adds the element's rows into
@@ -61,6 +62,7 @@ __host__ __device__ __forceinline__ int cell_stride(int nr) { return nr > kCellS
 constexpr int kTileWarps = 1;  // warps per CTA of the tile pass (no CTA-wide barrier: finest sharing of shared memory)
 constexpr int kTileCap = 128;  // slots of a 32-element tile (tets: 4 per element)
 constexpr int kCellCap = 512;  // contributions of a 32-element tile (tets: 16 per element)
+constexpr int kDestRegs = 8;   // record slots a lane of the tile pass holds in registers (tiles of up to 256 records)
 constexpr int kHalvesDisjoint = 0x100;  // tile_runs flag: elements 0-15 and 16-31 share no cell
 
 enum : int { ASM_ROW_TOO_LONG = 1, ASM_BAD_VERTEX = 2, ASM_REPEATED_VERTEX = 4 };
@@ -430,7 +432,8 @@ template <int NV>
 __global__ void __launch_bounds__(kTileWarps * 32)
     tile_assemble_kernel(const float* __restrict__ A, int64_t n_elem, const uint32_t* __restrict__ run_word,
                          const uint16_t* __restrict__ tile_runs, const int32_t* __restrict__ tile_rec,
-                         const uint16_t* __restrict__ rec_cell, float* __restrict__ records, int vec) {
+                         const uint16_t* __restrict__ rec_cell, const int32_t* __restrict__ rec_dest,
+                         float* __restrict__ records, int vec) {
   using TP = TilePlan<NV>;
   constexpr int NN = TP::NN, SST = TP::SST;
   extern __shared__ __align__(128) unsigned char tsm[];
@@ -461,6 +464,13 @@ __global__ void __launch_bounds__(kTileWarps * 32)
   copy_tile_cells(rec_cell, t, rnc, lane, rcs);
   cp_async_commit();
   uint32_t rwc = __ldg(run_word + t * 32 + lane);
+  // the entry-order slots of a tile's first 32 * kDestRegs records, one tile ahead
+  auto dests = [&](int32_t rb, int32_t rn, int32_t(&d)[kDestRegs]) {
+#pragma unroll
+    for (int q = 0; q < kDestRegs; ++q) d[q] = lane + 32 * q < rn ? __ldg(rec_dest + rb + lane + 32 * q) : 0;
+  };
+  int32_t dc[kDestRegs], dn[kDestRegs];
+  dests(rbc, rnc, dc);
   for (int it = 0; t < ntiles; ++it, t += S) {
     const int sc = it & 1;
     const int64_t tn = t + S;
@@ -471,6 +481,7 @@ __global__ void __launch_bounds__(kTileWarps * 32)
       copy_tile_cells(rec_cell, tn, rnn, lane, rcs + (sc ^ 1) * kCellCap);
       rwn = __ldg(run_word + tn * 32 + lane);
     }
+    dests(rbn, rnn, dn);  // rnn = 0 past the last tile
     cp_async_commit();
     const int64_t e0 = t * 32;
     const int ne = int(n_elem - e0 < 32 ? n_elem - e0 : 32);
@@ -502,7 +513,10 @@ __global__ void __launch_bounds__(kTileWarps * 32)
           __syncwarp();
         }
       }
-      for (int r = lane; r < rnc; r += 32) records[rbc + r] = dense[rc[r]];  // tile order
+#pragma unroll
+      for (int q = 0; q < kDestRegs; ++q)
+        if (lane + 32 * q < rnc) records[dc[q]] = dense[rc[lane + 32 * q]];
+      for (int r = lane + 32 * kDestRegs; r < rnc; r += 32) records[__ldg(rec_dest + rbc + r)] = dense[rc[r]];
     } else {
       // more distinct vertices than the dense tile holds: scan the tile per record
       for (int r0 = 0; r0 < rnc; r0 += 32) {  // warp-uniform, so the shuffles see every lane
@@ -517,34 +531,32 @@ __global__ void __launch_bounds__(kTileWarps * 32)
             if (int((w >> (8 * (ij / NV))) & 0xFFu) * int(ps) + int((w >> (8 * (ij % NV))) & 0xFFu) == cell)
               acc += st[l * SST + ij];
         }
-        if (live) records[rbc + r] = acc;
+        if (live) records[__ldg(rec_dest + rbc + r)] = acc;
       }
     }
     __syncwarp();  // the stage, record cells, cells and dense tile are refilled
     trc = trn, rbc = rbn, rnc = rnn, rwc = rwn;
+#pragma unroll
+    for (int q = 0; q < kDestRegs; ++q) dc[q] = dn[q];
     trn = tr2, rbn = rb2, rnn = rn2;
   }
   cp_async_wait<0>();
 }
 
-// Step 2: val[k] = sum of the records of entry k (rec_list[eoff[k] .. eoff[k+1]),
-// increasing record index = tile order).  The records of neighbouring entries
-// lie in the same few tiles, so the gathers mostly hit the caches; four
-// record indices, then four records, are loaded before they are added.
+// Step 2: val[k] = sum of the records of entry k, records[eoff[k] .. eoff[k+1])
+// in tile order: the tile pass wrote every record to its slot in entry order,
+// so neighbouring threads read neighbouring runs.  Four records are loaded
+// before they are added.
 __global__ void entry_reduce_kernel(const int32_t* __restrict__ eoff, const int32_t* __restrict__ nnz_ptr,
-                                    const int32_t* __restrict__ rec_list, const float* __restrict__ records,
-                                    float* __restrict__ val) {
+                                    const float* __restrict__ records, float* __restrict__ val) {
   const int64_t nnz = *nnz_ptr;  // row_ptr[n_vert]
   for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < nnz; k += int64_t(gridDim.x) * blockDim.x) {
     const int32_t b = __ldg(eoff + k), e = __ldg(eoff + k + 1);
     float acc = 0.f;
     for (int32_t m0 = b; m0 < e; m0 += 4) {
-      int32_t idx[4];
       float x[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) idx[u] = m0 + u < e ? __ldg(rec_list + m0 + u) : 0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = m0 + u < e ? __ldg(records + idx[u]) : 0.f;
+      for (int u = 0; u < 4; ++u) x[u] = m0 + u < e ? __ldg(records + m0 + u) : 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         if (m0 + u < e) acc += x[u];
@@ -560,6 +572,7 @@ struct AsmLayout {
   uint32_t* run_word;
   uint16_t* tile_runs;
   int32_t *tile_rec, *rec_entry, *rec_list, *eoff, *cursor2, *partials2;
+  int32_t* rec_dest;  // the records' entry-order slots; shares rec_entry's storage, which the build no longer needs
   uint16_t* rec_cell;
   float* records;
   int64_t n_tiles, rec_cap;
@@ -613,6 +626,7 @@ AsmLayout asm_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
   L.rec_cell = reinterpret_cast<uint16_t*>(b + o_cell);
   L.rec_entry = reinterpret_cast<int32_t*>(b + o_rentry);
   L.rec_list = reinterpret_cast<int32_t*>(b + o_rlist);
+  L.rec_dest = L.rec_entry;
   L.eoff = reinterpret_cast<int32_t*>(b + o_eoff);
   L.records = reinterpret_cast<float*>(b + o_records);
   L.cursor2 = reinterpret_cast<int32_t*>(b + o_cursor2);
@@ -621,6 +635,14 @@ AsmLayout asm_layout(int dim, int64_t n_elem, int64_t n_vert, void* base) {
   L.rec_cap = cap;
   L.bytes = off;
   return L;
+}
+
+// rec_dest[rec_list[p]] = p for the *n_rec records listed
+__global__ void invert_list_kernel(const int32_t* __restrict__ rec_list, const int32_t* __restrict__ n_rec,
+                                   int32_t* __restrict__ rec_dest) {
+  const int64_t n = *n_rec;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < n; p += int64_t(gridDim.x) * blockDim.x)
+    rec_dest[rec_list[p]] = int32_t(p);
 }
 
 __global__ void fill_neg_kernel(int32_t* p, int64_t n) {
@@ -669,11 +691,10 @@ cudaError_t launch_tile_assemble_t(const AsmLayout& L, const float* A, int64_t n
   cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kern), smem);
   if (e != cudaSuccess) return e;
   kern<<<pipeline_grid(reinterpret_cast<const void*>(kern), kTileWarps, smem, n_elem, 0), kTileWarps * 32, smem, st>>>(
-      A, n_elem, L.run_word, L.tile_runs, L.tile_rec, L.rec_cell, L.records,
+      A, n_elem, L.run_word, L.tile_runs, L.tile_rec, L.rec_cell, L.rec_dest, L.records,
       int(reinterpret_cast<uintptr_t>(A) % 16 == 0));
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  entry_reduce_kernel<<<grid_of(L.rec_cap, 256), 256, 0, st>>>(L.eoff, L.row_ptr + n_vert, L.rec_list, L.records,
-                                                                val);
+  entry_reduce_kernel<<<grid_of(L.rec_cap, 256), 256, 0, st>>>(L.eoff, L.row_ptr + n_vert, L.records, val);
   return cudaGetLastError();
 }
 
@@ -1073,6 +1094,10 @@ fem_status fem_assembly_build(const fem_mesh* mesh, int32_t form, void* ws, size
     if (e == cudaSuccess) e = fem::launch_tile_cells<true>(mesh->dim, mesh->conn, mesh->n_elem, L, st);
     if (e == cudaSuccess)
       e = fem::launch_key_csr(L.rec_entry, L.rec_cap, host[1], L.eoff, L.rec_list, L.cursor2, L.partials2, st);
+    if (e == cudaSuccess) {  // eoff[nnz] = the records
+      fem::invert_list_kernel<<<fem::grid_of(L.rec_cap, 256), 256, 0, st>>>(L.rec_list, L.eoff + host[1], L.rec_dest);
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&host[0], L.flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nrec, L.tile_rec + L.n_tiles, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
