@@ -389,7 +389,8 @@ __global__ void __launch_bounds__(kPatWarps * 32)
 // The next tile's element matrices arrive by 16-byte cp.async into the other
 // half of a double-buffered stage while this tile is summed.  Every lane
 // first writes its element's cell indices (cells[l][ij], shared memory); the
-// record cells of the dense tile are zeroed; then the contributions are added
+// dense tile is zero at the start of every tile (zeroed once, and each record
+// cell zeroed again as it is read out); then the contributions are added
 // element by element (each element's cells are distinct) -- two elements per
 // step, l and l + 16, when the tile's halves share no cell -- and the records
 // are read out in tile order.
@@ -471,6 +472,7 @@ __global__ void __launch_bounds__(kTileWarps * 32)
   };
   int32_t dc[kDestRegs], dn[kDestRegs];
   dests(rbc, rnc, dc);
+  for (int i = lane; i < kTileRuns * kTileRuns; i += 32) dense[i] = 0.f;
   for (int it = 0; t < ntiles; ++it, t += S) {
     const int sc = it & 1;
     const int64_t tn = t + S;
@@ -498,8 +500,6 @@ __global__ void __launch_bounds__(kTileWarps * 32)
     cp_async_wait<1>();
     __syncwarp();  // this tile's A and record cells (copied by every lane) and the cell indices are in place
     if (nr <= kTileRuns) {
-      for (int r = lane; r < rnc; r += 32) dense[rc[r]] = 0.f;
-      __syncwarp();
       if (halves) {
         const int h = lane >> 4, ij = lane & 15;
         for (int l0 = 0; l0 < 16; ++l0) {
@@ -515,8 +515,16 @@ __global__ void __launch_bounds__(kTileWarps * 32)
       }
 #pragma unroll
       for (int q = 0; q < kDestRegs; ++q)
-        if (lane + 32 * q < rnc) records[dc[q]] = dense[rc[lane + 32 * q]];
-      for (int r = lane + 32 * kDestRegs; r < rnc; r += 32) records[__ldg(rec_dest + rbc + r)] = dense[rc[r]];
+        if (lane + 32 * q < rnc) {
+          const int c = rc[lane + 32 * q];
+          records[dc[q]] = dense[c];
+          dense[c] = 0.f;
+        }
+      for (int r = lane + 32 * kDestRegs; r < rnc; r += 32) {
+        const int c = rc[r];
+        records[__ldg(rec_dest + rbc + r)] = dense[c];
+        dense[c] = 0.f;
+      }
     } else {
       // more distinct vertices than the dense tile holds: scan the tile per record
       for (int r0 = 0; r0 < rnc; r0 += 32) {  // warp-uniform, so the shuffles see every lane
@@ -545,13 +553,18 @@ __global__ void __launch_bounds__(kTileWarps * 32)
 
 // Step 2: val[k] = sum of the records of entry k, records[eoff[k] .. eoff[k+1])
 // in tile order: the tile pass wrote every record to its slot in entry order,
-// so neighbouring threads read neighbouring runs.  Four records are loaded
-// before they are added.
+// so neighbouring threads read neighbouring runs.  The next entry's bounds load
+// while this entry's records do; four records are loaded before they are added.
 __global__ void entry_reduce_kernel(const int32_t* __restrict__ eoff, const int32_t* __restrict__ nnz_ptr,
                                     const float* __restrict__ records, float* __restrict__ val) {
   const int64_t nnz = *nnz_ptr;  // row_ptr[n_vert]
-  for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < nnz; k += int64_t(gridDim.x) * blockDim.x) {
-    const int32_t b = __ldg(eoff + k), e = __ldg(eoff + k + 1);
+  const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  int32_t bn = 0, en = 0;
+  if (k < nnz) bn = __ldg(eoff + k), en = __ldg(eoff + k + 1);
+  for (; k < nnz; k += S) {
+    const int32_t b = bn, e = en;
+    if (k + S < nnz) bn = __ldg(eoff + k + S), en = __ldg(eoff + k + S + 1);
     float acc = 0.f;
     for (int32_t m0 = b; m0 < e; m0 += 4) {
       float x[4];
