@@ -553,28 +553,42 @@ __global__ void __launch_bounds__(kTileWarps * 32)
 
 // Step 2: val[k] = sum of the records of entry k, records[eoff[k] .. eoff[k+1])
 // in tile order: the tile pass wrote every record to its slot in entry order,
-// so neighbouring threads read neighbouring runs.  The next entry's bounds load
-// while this entry's records do; four records are loaded before they are added.
+// so neighbouring threads read neighbouring runs.  A thread sums two entries
+// at a time (k and k + S), four records of each loaded before they are added,
+// while the bounds of its next two entries load.
 __global__ void entry_reduce_kernel(const int32_t* __restrict__ eoff, const int32_t* __restrict__ nnz_ptr,
                                     const float* __restrict__ records, float* __restrict__ val) {
   const int64_t nnz = *nnz_ptr;  // row_ptr[n_vert]
   const int64_t S = int64_t(gridDim.x) * blockDim.x;
+  auto bounds = [&](int64_t k, int32_t& b, int32_t& e) {
+    b = 0, e = 0;
+    if (k < nnz) b = __ldg(eoff + k), e = __ldg(eoff + k + 1);
+  };
   int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-  int32_t bn = 0, en = 0;
-  if (k < nnz) bn = __ldg(eoff + k), en = __ldg(eoff + k + 1);
-  for (; k < nnz; k += S) {
-    const int32_t b = bn, e = en;
-    if (k + S < nnz) bn = __ldg(eoff + k + S), en = __ldg(eoff + k + S + 1);
-    float acc = 0.f;
-    for (int32_t m0 = b; m0 < e; m0 += 4) {
-      float x[4];
+  int32_t b0n, e0n, b1n, e1n;
+  bounds(k, b0n, e0n);
+  bounds(k + S, b1n, e1n);
+  for (; k < nnz; k += 2 * S) {
+    const int32_t b0 = b0n, e0 = e0n, b1 = b1n, e1 = e1n;
+    bounds(k + 2 * S, b0n, e0n);
+    bounds(k + 3 * S, b1n, e1n);
+    const int32_t n0 = e0 - b0, n1 = e1 - b1;
+    float acc0 = 0.f, acc1 = 0.f;
+    for (int32_t m0 = 0; m0 < n0 || m0 < n1; m0 += 4) {
+      float x0[4], x1[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) x[u] = m0 + u < e ? __ldg(records + m0 + u) : 0.f;
+      for (int u = 0; u < 4; ++u) {
+        x0[u] = m0 + u < n0 ? __ldg(records + b0 + m0 + u) : 0.f;
+        x1[u] = m0 + u < n1 ? __ldg(records + b1 + m0 + u) : 0.f;
+      }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (m0 + u < e) acc += x[u];
+      for (int u = 0; u < 4; ++u) {
+        if (m0 + u < n0) acc0 += x0[u];
+        if (m0 + u < n1) acc1 += x1[u];
+      }
     }
-    val[k] = acc;
+    val[k] = acc0;
+    if (k + S < nnz) val[k + S] = acc1;
   }
 }
 
