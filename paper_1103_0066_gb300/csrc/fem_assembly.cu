@@ -942,9 +942,9 @@ cudaError_t launch_p2_build(const int32_t* conn, int64_t n_elem, int64_t n_vert,
 // columns).  For each incidence (e, i) of the row, in increasing element
 // order, lane j of the group adds A_e[i][j] at the column position of the
 // element's unknown j (distinct within an element); the group then stores the
-// row.  Each entry is the sum of its contributions in element order.  The
-// incidences' slots, positions and element rows are loaded NB incidences at a
-// time before their additions.
+// row, zeroing the buffer behind it.  Each entry is the sum of its
+// contributions in element order.  The incidences' slots, positions and
+// element rows are loaded NB incidences at a time before their additions.
 constexpr int kRowWarps = 8;
 
 template <int NB>
@@ -961,6 +961,9 @@ __global__ void __launch_bounds__(kRowWarps * 32)
   const int g = lane / NB, j = lane - g * NB;
   const bool member = g < G;
   float* acc = acc_s[warp][member ? g : 0];
+  // the row buffers are zero at the start of every row: zeroed once here, and
+  // each column zeroed again as it is stored
+  for (int c = lane; c < G * kRowStride; c += 32) (&acc_s[warp][0][0])[c] = 0.f;
   const int64_t n_rows = *n_rows_dev;
   for (int64_t r0 = (int64_t(blockIdx.x) * kRowWarps + warp) * G; r0 < n_rows;
        r0 += int64_t(gridDim.x) * kRowWarps * G) {
@@ -970,7 +973,6 @@ __global__ void __launch_bounds__(kRowWarps * 32)
     const int len = live ? row_ptr[r + 1] - rp : 0;
     const int32_t tb = live ? inc_off[r] : 0;
     const int n_inc = live ? inc_off[r + 1] - tb : 0;
-    for (int c = j; c < len; c += NB) acc[c] = 0.f;
     __syncwarp();
     const int steps = __reduce_max_sync(0xffffffffu, n_inc);
     // NB incidences at a time: lane j of the group loads incidence k0 + j's
@@ -985,7 +987,8 @@ __global__ void __launch_bounds__(kRowWarps * 32)
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
         const int32_t sl = __shfl_sync(0xffffffffu, my_sl, (member ? g * NB : 0) + u);
-        a[u] = (k0 + u < n_inc) ? __ldg(A + int64_t(sl / NB) * (NB * NB) + (sl % NB) * NB + j) : 0.f;
+        // slot sl = e * NB + i: row i of A_e starts at e * NB * NB + i * NB = sl * NB
+        a[u] = (k0 + u < n_inc) ? __ldg(A + int64_t(sl) * NB + j) : 0.f;
       }
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
@@ -993,7 +996,10 @@ __global__ void __launch_bounds__(kRowWarps * 32)
         __syncwarp();
       }
     }
-    for (int c = j; c < len; c += NB) __stcs(val + rp + c, acc[c]);
+    for (int c = j; c < len; c += NB) {
+      __stcs(val + rp + c, acc[c]);
+      acc[c] = 0.f;
+    }
     __syncwarp();  // the row buffers are refilled for the next rows
   }
 }
