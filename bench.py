@@ -64,6 +64,8 @@ NCU_TRAFFIC = {
     "fem_bwd_elem_kernel<3,LAPLACE_P1,JAC_SAVED>": {"bytes_per_launch": 1321.0e6, "src": "4a6c95b7dc30da51"},
     "fem_fwd_kernel<3,LAPLACE_P1,JAC_COMP>": {"bytes_per_launch": 962.3e6, "src": "7c0682f050b938ea"},
     "vertex_reduce_kernel<3>": {"bytes_per_launch": 149.3e6, "src": "2fda9ba9be91ca76"},
+    # tile pass + entry pass of one call, 96^3 capture scaled by the elements (records grow alike)
+    "fem_assemble<LAPLACE_P1>": {"bytes_per_launch": 2232.3e6, "src": "2fcf5baed442a38c"},
 }
 
 
